@@ -1,0 +1,382 @@
+"""Benchmark: failureless Aho-Corasick matching throughput on one GB300.
+
+Default workload (the top point of the input-size sweep): a 1 GiB text i.i.d.
+uniform over {A,C,G,T}, 10,000 keywords of length 16-64 (half copied from the
+text's first 4 KiB, half random ACGT), dense int32 per-position ids.  One step
+= one ac_match call over the whole text (text staging, walks, dense output).
+
+Prints one JSON line (rank 0).  Under torchrun each rank matches its own copy
+of the workload on its own GPU (replicas; weak scaling) and the slowest rank's
+time counts.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+                  [--workload sweep|zipf|single] [--sweep]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GB/s text scanned (1 GB300) & % HBM roofline; batch/serve p50/p99 vs plain PFAC"
+GIB = 1 << 30
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+def make_workload(name: str, n: int | None):
+    from paper_1412_7789_gb300 import workloads as W
+
+    if name == "sweep":
+        n = n or GIB
+        text, pats = W.sweep_acgt(n)
+        desc = ("ACGT input-size sweep, top point: %d B i.i.d. uniform ACGT text, 10,000 keywords "
+                "length 16-64 (50%% copied from the first 4 KiB, 50%% random ACGT), dense int32 ids" % n)
+        out_kind = "dense"
+    elif name == "zipf":
+        n = n or GIB
+        text, pats = W.zipf_byte(n)
+        desc = ("byte alphabet: %d B Zipf(1.1) text over 256 byte values, 20,000 keywords length 4-100 "
+                "(30%% copied, 70%% Zipf-random), dense 256-wide int32 goto table, compacted (pos,id) output" % n)
+        out_kind = "compact"
+    elif name == "single":
+        text, pats = W.single_text_acgt(0, n or (1 << 20))
+        desc = "single text: %d B ACGT, 100 keywords length 8-32, dense int32 ids" % text.size
+        out_kind = "dense"
+    else:
+        raise SystemExit("unknown workload %r" % name)
+    return text, pats, desc, out_kind
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def mark(self) -> int:
+        return len(self.lines)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+
+    def summary(self, lo: int, hi: int):
+        rows = []
+        for line in self.lines[lo:hi] or self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, one core, bounded sample
+# ----------------------------------------------------------------------------
+def cpu_baseline(text: np.ndarray, pats, budget_s: float = 12.0):
+    import oracle
+
+    with oracle.Machine(pats) as m:
+        probe = min(text.size, 1 << 18)
+        t0 = time.perf_counter()
+        m.pfac_ids(text[:probe])
+        dt = max(time.perf_counter() - t0, 1e-6)
+        size = int(min(text.size, max(probe, probe * budget_s / dt)))
+        t0 = time.perf_counter()
+        m.pfac_ids(text[:size])
+        dt = time.perf_counter() - t0
+        wprobe = min(size, 1 << 22)
+        steps, longest = m.walk_steps(text[:wprobe])
+    return {"value": size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d B of the same text, one serial pass (goto/failure/output, then per-start "
+                      "longest conversion) on one host core" % size,
+            "seconds": dt, "walk_steps_per_position": steps / max(wprobe, 1), "longest_walk": longest}
+
+
+# ----------------------------------------------------------------------------
+# the reference arm: the oracle, timed on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    text, pats, desc, _ = make_workload(args.workload, args.n)
+    import oracle
+
+    with oracle.Machine(pats) as m:
+        probe = min(text.size, 1 << 18)
+        t0 = time.perf_counter()
+        m.pfac_ids(text[:probe])
+        dt = max(time.perf_counter() - t0, 1e-6)
+        # whole --steps K --warmup W run within about two minutes
+        per_step = 100.0 / max(1, args.steps + args.warmup)
+        size = int(min(text.size, max(probe, probe * per_step / dt)))
+        sample = text[:size]
+        for _ in range(args.warmup):
+            m.pfac_ids(sample)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            m.pfac_ids(sample)
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = size * len(times) / total / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": desc, "sample_bytes": size},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "first %d B of the workload's text per step" % size},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_1412_7789_gb300 import api
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    text_np, pats, desc, out_kind = make_workload(args.workload, args.n)
+    n = text_np.size
+    a = api.Automaton(pats)
+    if args.kernel == "simple":
+        a.set_kernel("simple")
+    info = a.info()
+    text = torch.from_numpy(text_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    if out_kind == "dense":
+        out = torch.empty(n, dtype=torch.int32, device=dev)
+
+        def step():
+            api.ac_match(a.handle, text, n, out, stream)
+
+        out_bytes_per_pos = 4.0
+    else:
+        cap = max(1, n // 256)
+        pos = torch.empty(cap, dtype=torch.int32, device=dev)
+        ids = torch.empty(cap, dtype=torch.int32, device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+
+        def step():
+            api.ac_match_compact(a.handle, text, n, pos, ids, cap, cnt, stream)
+
+        out_bytes_per_pos = None
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    if out_kind == "compact":
+        matches = int(cnt.item())
+        if matches > cap:
+            raise SystemExit("compact capacity too small: %d > %d" % (matches, cap))
+        algo_bytes = n + 8 * matches
+    else:
+        matches = None
+        algo_bytes = n * (1 + out_bytes_per_pos)
+
+    sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", local_rank)))
+    sampler.start()
+    time.sleep(0.3)
+    # warm the clocks up under load before the timed region
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    m0 = sampler.mark()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    m1 = sampler.mark()
+    if dist is not None:
+        dist.barrier()
+    time.sleep(0.25)
+    sampler.stop()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    t_ms = evs[0].elapsed_time(evs[-1])
+    if dist is not None:
+        tt = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    clocks = sampler.summary(m0, m1)
+
+    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    e2e = None
+    if out_kind == "dense" and not args.no_e2e:
+        ht = torch.from_numpy(text_np).pin_memory()
+        ho = torch.empty(n, dtype=torch.int32).pin_memory()
+        api.ac_match_host(a.handle, int(ht.data_ptr()), n, int(ho.data_ptr()), stream)
+        reps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            api.ac_match_host(a.handle, int(ht.data_ptr()), n, int(ho.data_ptr()), stream)
+        e2e_s = (time.perf_counter() - t0) / reps
+        e2e = {"value": world * n / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n,
+               "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * e2e_s}
+        del ht, ho
+
+    peak, peak_kind = load_peaks()
+    launch_ms = statistics.mean(per)
+    achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
+    value = world * n * args.steps / (t_ms * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": args.traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": algo_bytes,
+            "kernel": "pfac_tiled" if args.kernel != "simple" else "pfac_simple"}
+
+    extra = {"automaton": {k: info[k] for k in ("n_states", "n_classes", "index_width", "code_bits",
+                                                  "jump_depth", "stride_depth", "max_len", "table_bytes")},
+             "launch_ms_median": statistics.median(per), "launch_ms_min": min(per)}
+    if matches is not None:
+        extra["matches"] = matches
+    if args.compare_simple and out_kind == "dense" and args.kernel != "simple":
+        a.set_kernel("simple")
+        api.ac_match(a.handle, text, n, out, stream)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            api.ac_match(a.handle, text, n, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        extra["simple_kernel_gbs"] = n * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        a.set_kernel("tiled")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(text_np, pats, args.cpu_seconds)
+        extra["lookups_per_s"] = cpu["walk_steps_per_position"] * n * args.steps / (t_ms * 1e-3)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": desc, "n_bytes": n, "keywords": len(pats),
+                       "l2": "inputs larger than L2 (%.1f GB text + output per step)" % (algo_bytes / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": args.steps, "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "zipf", "single"])
+    ap.add_argument("--n", type=int, default=None, help="text bytes (default: the workload's size)")
+    ap.add_argument("--kernel", default="tiled", choices=["tiled", "simple"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--compare-simple", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per launch from an ncu capture of the current kernel")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    from paper_1412_7789_gb300 import build
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

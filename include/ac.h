@@ -1,0 +1,182 @@
+/*
+ * ac.h -- failureless Aho-Corasick (PFAC) multi-keyword matching on NVIDIA
+ * GB300 (sm_103a).  Plain C ABI: host or device pointers and sizes only.
+ *
+ * The problem (paper section II): locate the occurrences of any of a finite
+ * set of keywords in a text.  The failureless machine used on the GPU
+ * (section II, Fig. 5) has no failure transitions: every text position starts
+ * its own walk through the keyword trie (section I, Fig. 3: all characters in
+ * parallel) and stops at the first missing transition, so it reports, per
+ * start position, only the longest keyword beginning there -- sub-pattern
+ * outputs of the full machine are not reported (section II).
+ *
+ * Conventions shared by every call:
+ *   - Keyword ids are 0-based in the order given to ac_compile.  -1 = no match.
+ *     When several keywords are the same byte string, the lowest id is reported.
+ *   - Keywords and texts are raw bytes (0x00 allowed), compared exactly.
+ *   - "d_" arguments are device pointers (cudaMalloc / PyTorch CUDA tensors),
+ *     "h_" arguments host pointers.  `stream` is a cudaStream_t passed as void*
+ *     (NULL = the legacy default stream).
+ *   - Match calls are asynchronous on `stream`: they validate arguments, enqueue
+ *     work and return.  Argument errors are returned synchronously.  A failure
+ *     inside a kernel (a bounded wait that ran out) is latched in a per-device
+ *     error word read by ac_device_status().
+ *   - A handle is immutable after ac_compile and may be used from several
+ *     streams at once; it must not be destroyed while work using it is in flight.
+ *   - The caller owns texts and outputs; the handle owns its device tables.
+ */
+#ifndef AC_H
+#define AC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ac_automaton *ac_handle;
+
+typedef enum {
+    AC_OK = 0,
+    AC_ERR_INVALID_ARG = 1,     /* null pointer, bad size, wrong handle kind      */
+    AC_ERR_EMPTY_PATTERN = 2,   /* a keyword of length 0, or k == 0               */
+    AC_ERR_TOO_MANY_STATES = 3, /* more than 2^31-1 trie states                   */
+    AC_ERR_OOM = 4,             /* host or device allocation failed               */
+    AC_ERR_CUDA = 5,            /* a CUDA runtime call failed                     */
+    AC_ERR_OVERFLOW = 6,        /* compacted output: more matches than capacity   */
+    AC_ERR_BUDGET = 7,          /* request larger than the configured budget      */
+    AC_ERR_TIMEOUT = 8,         /* a bounded device-side wait ran out             */
+    AC_ERR_NOT_FOUND = 9        /* unknown id (server requests)                   */
+} ac_status;
+
+/* Which matching kernel ac_match uses (ac_set_kernel). */
+typedef enum {
+    AC_KERNEL_TILED = 0,  /* default: bulk-copied text tiles, shared-memory jump table */
+    AC_KERNEL_SIMPLE = 1  /* one thread per position walking the goto table in global
+                             memory (the design of the paper's GPU side); dense only */
+} ac_kernel;
+
+/*
+ * Build options.  Zero-initialise, or call ac_default_options.
+ *   index_width    0 = choose (16-bit entries when every state id and keyword id
+ *                  fits, else 32-bit), 16 or 32 to force (16 fails with
+ *                  AC_ERR_INVALID_ARG when the automaton does not fit).
+ *   class_compress 1 (default) = one goto column per distinct keyword byte;
+ *                  0 = 256 columns (one per byte value).
+ *   host_only      1 = build the host tables only; the handle can be inspected
+ *                  (ac_info, ac_export_tables) but match calls refuse it.
+ *                  Needs no GPU.
+ *   jump_bytes     shared-memory budget of the root jump table (0 = 128 KiB).
+ *   stride_bytes   device budget of the second-level stride table (0 = 16 MiB;
+ *                  set 1 to disable it).
+ *   dev_alloc / dev_free / alloc_ctx
+ *                  optional device allocator for the handle's tables (e.g. a
+ *                  PyTorch caching allocator); NULL = cudaMalloc / cudaFree.
+ */
+typedef struct {
+    int32_t index_width;
+    int32_t class_compress;
+    int32_t host_only;
+    uint32_t jump_bytes;
+    uint64_t stride_bytes;
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;
+} ac_options;
+
+/* Shape of a compiled automaton (ac_info). */
+typedef struct {
+    uint32_t n_keywords;   /* k                                                     */
+    uint32_t n_states;     /* trie states including the root (state 0)             */
+    uint32_t n_classes;    /* goto columns used by keyword bytes                    */
+    uint32_t row_width;    /* entries per goto-table row (n_classes + end column, padded) */
+    uint32_t index_width;  /* bits per goto-table entry: 16 or 32                   */
+    uint32_t code_bits;    /* bits per text character in the packed code stream     */
+    uint32_t jump_depth;   /* characters resolved by the root jump table (k_j)      */
+    uint32_t stride_depth; /* characters resolved by the stride table (0 = none)    */
+    uint32_t min_len;      /* shortest keyword                                      */
+    uint32_t max_len;      /* longest keyword = trie depth                          */
+    uint64_t table_bytes;  /* device bytes of goto + jump + stride tables           */
+    uint32_t depth_base_jump; /* first state id at depth jump_depth (BFS order)     */
+    uint32_t count_jump;      /* number of states at depth jump_depth               */
+} ac_info_t;
+
+void ac_default_options(ac_options *opt);
+
+/*
+ * Compile a keyword set into a device-resident automaton (paper section II:
+ * the goto function as a trie, stored as a matrix for the GPU, Fig. 5).
+ * patterns[i] points to lens[i] bytes; the bytes are copied, so the caller may
+ * free them on return.  k >= 1 and every lens[i] >= 1 (else
+ * AC_ERR_EMPTY_PATTERN).  `opt` may be NULL.  Blocks until the tables are on
+ * the device (the current CUDA device).  On success *out receives the handle.
+ */
+ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint32_t k,
+                     const ac_options *opt, ac_handle *out);
+
+/* Free a handle and its device tables.  NULL is accepted. */
+ac_status ac_destroy(ac_handle h);
+
+/* Shape of the automaton. */
+ac_status ac_info(ac_handle h, ac_info_t *info);
+
+/*
+ * Copy the host tables out (for inspection and tests), any pointer may be NULL:
+ *   cls   int16[256]    byte -> class code, -1 = byte in no keyword
+ *   goto_ int16 or int32 [n_states * row_width]; entry > 0 = child state,
+ *         entry < 0 = no transition, and the walk's result is (-entry - 2)
+ *         (the longest keyword ending on the path to this state, -1 = none);
+ *         column n_classes is always of the second kind (end of text)
+ *   depth uint32[max_len + 1]  number of states at each depth (BFS order puts
+ *         depth d at ids [sum of counts below d, ...))
+ */
+ac_status ac_export_tables(ac_handle h, int16_t *cls, void *goto_, uint32_t *depth);
+
+/*
+ * Dense matching.  d_out_ids[i] = id of the longest keyword starting at
+ * d_text[i] (within the n bytes), or -1.  d_text: n bytes, d_out_ids: n int32,
+ * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is
+ * a no-op.
+ */
+ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_out_ids, void *stream);
+
+/*
+ * Compacted matching: the matched start positions in ascending order with
+ * their ids.  Writes min(total, cap) entries to d_pos / d_ids (uint32 each) and
+ * the true total to *d_count (a device uint64).  The caller compares the total
+ * with cap and calls again with more room when it is larger.  n must be below
+ * 2^32.  Uses stream-ordered device scratch (cudaMallocAsync) per call.
+ */
+ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
+                           uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream);
+
+/* Number of matched start positions (positions whose dense id is >= 0) into
+ * the device uint64 *d_count (overwritten). */
+ac_status ac_count(ac_handle h, const uint8_t *d_text, uint64_t n, uint64_t *d_count, void *stream);
+
+/*
+ * Dense matching from and to HOST memory: copies h_text to the device, matches
+ * and copies the ids back, pipelined in chunks on `stream` (chunks overlap
+ * copies with matching; each chunk carries a max_len halo so walks never see a
+ * chunk edge).  Host buffers should be pinned (cudaHostAlloc / pin_memory) for
+ * the copies to overlap.  Synchronises `stream` before returning.
+ */
+ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t *h_out_ids, void *stream);
+
+/* Select the kernel used by ac_match for this handle (default AC_KERNEL_TILED). */
+ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
+
+/* Read and clear the calling device's kernel error word: AC_OK, or
+ * AC_ERR_TIMEOUT when a bounded wait inside a kernel ran out.  Synchronises
+ * the device. */
+ac_status ac_device_status(void);
+
+/* Static description of a status code. */
+const char *ac_status_string(ac_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AC_H */

@@ -1,0 +1,294 @@
+"""Thin Python binding of the C ABI in ``include/ac.h`` (ctypes).
+
+Argument marshalling only: every matching step runs in the CUDA library.  The
+library must have been built (``paper_1412_7789_gb300.build.build()``); when
+it is missing every call raises -- there is no fallback.
+
+PyTorch supplies device memory and streams: texts are ``torch.uint8`` CUDA
+tensors, outputs ``torch.int32`` / ``torch.uint32``-compatible tensors, and the
+stream defaults to the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+# ---- status codes (mirror of ac_status) ---------------------------------------
+AC_OK = 0
+AC_ERR_INVALID_ARG = 1
+AC_ERR_EMPTY_PATTERN = 2
+AC_ERR_TOO_MANY_STATES = 3
+AC_ERR_OOM = 4
+AC_ERR_CUDA = 5
+AC_ERR_OVERFLOW = 6
+AC_ERR_BUDGET = 7
+AC_ERR_TIMEOUT = 8
+AC_ERR_NOT_FOUND = 9
+
+AC_KERNEL_TILED = 0
+AC_KERNEL_SIMPLE = 1
+
+
+class AcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (what, ac_status_string(status), status))
+
+
+class ac_options(ctypes.Structure):
+    _fields_ = [
+        ("index_width", ctypes.c_int32),
+        ("class_compress", ctypes.c_int32),
+        ("host_only", ctypes.c_int32),
+        ("jump_bytes", ctypes.c_uint32),
+        ("stride_bytes", ctypes.c_uint64),
+        ("dev_alloc", ctypes.c_void_p),
+        ("dev_free", ctypes.c_void_p),
+        ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class ac_info_t(ctypes.Structure):
+    _fields_ = [
+        ("n_keywords", ctypes.c_uint32),
+        ("n_states", ctypes.c_uint32),
+        ("n_classes", ctypes.c_uint32),
+        ("row_width", ctypes.c_uint32),
+        ("index_width", ctypes.c_uint32),
+        ("code_bits", ctypes.c_uint32),
+        ("jump_depth", ctypes.c_uint32),
+        ("stride_depth", ctypes.c_uint32),
+        ("min_len", ctypes.c_uint32),
+        ("max_len", ctypes.c_uint32),
+        ("table_bytes", ctypes.c_uint64),
+        ("depth_base_jump", ctypes.c_uint32),
+        ("count_jump", ctypes.c_uint32),
+    ]
+
+
+_lock = threading.Lock()
+_LIB: ctypes.CDLL | None = None
+
+_H = ctypes.c_void_p
+_P = ctypes.c_void_p
+_U64 = ctypes.c_uint64
+_SIGS = {
+    "ac_default_options": (None, [ctypes.POINTER(ac_options)]),
+    "ac_compile": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32,
+                                  ctypes.POINTER(ac_options), ctypes.POINTER(_H)]),
+    "ac_destroy": (ctypes.c_int, [_H]),
+    "ac_info": (ctypes.c_int, [_H, ctypes.POINTER(ac_info_t)]),
+    "ac_export_tables": (ctypes.c_int, [_H, _P, _P, _P]),
+    "ac_match": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
+    "ac_match_compact": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
+    "ac_count": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
+    "ac_match_host": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
+    "ac_set_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ac_device_status": (ctypes.c_int, []),
+    "ac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _LIB
+    with _lock:
+        if _LIB is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(
+                    "libpfac.so is not built (expected at %s); run paper_1412_7789_gb300.build.build()" % path)
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _LIB = L
+        return _LIB
+
+
+def _check(status: int, what: str):
+    if status != AC_OK:
+        raise AcError(status, what)
+
+
+def ac_status_string(status: int) -> str:
+    try:
+        return lib().ac_status_string(status).decode()
+    except Exception:
+        return "status %d" % status
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype_bytes: int | None = None) -> int:
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype_bytes is not None and t.element_size() != dtype_bytes:
+        raise ValueError("wrong element size")
+    return int(t.data_ptr())
+
+
+# ---- C-named functions ----------------------------------------------------------
+def ac_compile(patterns, index_width: int = 0, class_compress: bool = True, host_only: bool = False,
+               jump_bytes: int = 0, stride_bytes: int = 0) -> int:
+    """Compile keywords (sequence of bytes-like) -> raw handle (int)."""
+    pats = [bytes(p) for p in patterns]
+    k = len(pats)
+    bufs = [ctypes.create_string_buffer(p, max(1, len(p))) for p in pats]
+    arr = (ctypes.c_void_p * max(1, k))(*[ctypes.cast(b, ctypes.c_void_p) for b in bufs])
+    lens = (ctypes.c_uint32 * max(1, k))(*[len(p) for p in pats])
+    opt = ac_options()
+    lib().ac_default_options(ctypes.byref(opt))
+    opt.index_width = index_width
+    opt.class_compress = 1 if class_compress else 0
+    opt.host_only = 1 if host_only else 0
+    opt.jump_bytes = jump_bytes
+    opt.stride_bytes = stride_bytes
+    h = _H()
+    _check(lib().ac_compile(arr, lens, k, ctypes.byref(opt), ctypes.byref(h)), "ac_compile")
+    return int(h.value)
+
+
+def ac_destroy(h: int):
+    _check(lib().ac_destroy(h), "ac_destroy")
+
+
+def ac_info(h: int) -> dict:
+    info = ac_info_t()
+    _check(lib().ac_info(h, ctypes.byref(info)), "ac_info")
+    return {name: getattr(info, name) for name, _ in ac_info_t._fields_}
+
+
+def ac_export_tables(h: int):
+    """(cls int16[256], goto table int16/int32 [n_states, row_width], depth counts uint32[max_len+1])."""
+    info = ac_info(h)
+    cls = np.zeros(256, dtype=np.int16)
+    dt = np.int16 if info["index_width"] == 16 else np.int32
+    G = np.zeros((info["n_states"], info["row_width"]), dtype=dt)
+    depth = np.zeros(info["max_len"] + 1, dtype=np.uint32)
+    _check(lib().ac_export_tables(h, cls.ctypes.data, G.ctypes.data, depth.ctypes.data), "ac_export_tables")
+    return cls, G, depth
+
+
+def ac_match(h: int, text, n: int, out, stream=None):
+    _check(lib().ac_match(h, _dev_ptr(text), n, _dev_ptr(out, 4), _stream_ptr(stream)), "ac_match")
+
+
+def ac_match_compact(h: int, text, n: int, pos, ids, cap: int, count, stream=None):
+    _check(lib().ac_match_compact(h, _dev_ptr(text), n, _dev_ptr(pos, 4) if cap else 0,
+                                  _dev_ptr(ids, 4) if cap else 0, cap, _dev_ptr(count, 8),
+                                  _stream_ptr(stream)), "ac_match_compact")
+
+
+def ac_count(h: int, text, n: int, count, stream=None):
+    _check(lib().ac_count(h, _dev_ptr(text), n, _dev_ptr(count, 8), _stream_ptr(stream)), "ac_count")
+
+
+def ac_match_host(h: int, text_ptr: int, n: int, out_ptr: int, stream=None):
+    """Host-buffer dense matching: text_ptr / out_ptr are host addresses."""
+    _check(lib().ac_match_host(h, text_ptr, n, out_ptr, _stream_ptr(stream)), "ac_match_host")
+
+
+def ac_set_kernel(h: int, kernel: int):
+    _check(lib().ac_set_kernel(h, kernel), "ac_set_kernel")
+
+
+def ac_device_status() -> int:
+    return int(lib().ac_device_status())
+
+
+# ---- object wrapper ----------------------------------------------------------------
+class Automaton:
+    """A compiled keyword set resident on the current CUDA device."""
+
+    def __init__(self, patterns, **kw):
+        self.patterns = [bytes(p) for p in patterns]
+        self.handle = ac_compile(self.patterns, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            ac_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self) -> dict:
+        return ac_info(self.handle)
+
+    def export_tables(self):
+        return ac_export_tables(self.handle)
+
+    def set_kernel(self, kernel: str | int):
+        if isinstance(kernel, str):
+            kernel = {"tiled": AC_KERNEL_TILED, "simple": AC_KERNEL_SIMPLE}[kernel]
+        ac_set_kernel(self.handle, kernel)
+
+    def match(self, text, out=None, stream=None):
+        import torch
+
+        n = text.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=text.device)
+        ac_match(self.handle, text, n, out, stream)
+        return out
+
+    def count(self, text, out=None, stream=None):
+        import torch
+
+        if out is None:
+            out = torch.zeros(1, dtype=torch.int64, device=text.device)
+        ac_count(self.handle, text, text.numel(), out, stream)
+        return out
+
+    def match_compact(self, text, cap: int | None = None, stream=None):
+        """(pos, ids, count): pos/ids hold min(count, cap) entries."""
+        import torch
+
+        n = text.numel()
+        if cap is None:
+            cap = max(1, n // 64)
+        pos = torch.empty(max(cap, 1), dtype=torch.int32, device=text.device)
+        ids = torch.empty(max(cap, 1), dtype=torch.int32, device=text.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=text.device)
+        ac_match_compact(self.handle, text, n, pos, ids, cap, cnt, stream)
+        return pos, ids, cnt
+
+    def match_host(self, text, out=None, stream=None):
+        """text: CPU uint8 tensor (pinned for overlap); returns a CPU int32 tensor."""
+        import torch
+
+        n = text.numel()
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, pin_memory=text.is_pinned())
+        ac_match_host(self.handle, int(text.data_ptr()), n, int(out.data_ptr()), stream)
+        return out

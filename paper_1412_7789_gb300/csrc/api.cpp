@@ -1,0 +1,364 @@
+// The C ABI declared in include/ac.h: handle lifetime, device residency of the
+// compiled tables, argument checks and dispatch to the kernels.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime_api.h>
+
+#include "ac.h"
+#include "pfac_internal.h"
+
+struct ac_automaton {
+    pfac::HostTables host;
+    pfac::DevTables dev;
+    bool host_only = false;
+    int device = 0;
+    ac_kernel kernel = AC_KERNEL_TILED;
+    pfac::Tuning tuning;
+    void *(*dev_alloc)(size_t, void *) = nullptr;
+    void (*dev_free)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    std::vector<void *> owned;  // device allocations of the tables
+
+    // staging for ac_match_host (allocated on first use)
+    std::mutex host_mu;
+    uint8_t *h2d_text[2] = {nullptr, nullptr};
+    int32_t *h2d_out[2] = {nullptr, nullptr};
+    size_t chunk = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+void *dev_malloc(ac_automaton *h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (h->dev_alloc) return h->dev_alloc(bytes, h->alloc_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_release(ac_automaton *h, void *p) {
+    if (!p) return;
+    if (h->dev_free)
+        h->dev_free(p, h->alloc_ctx);
+    else
+        cudaFree(p);
+}
+
+ac_status upload(ac_automaton *h, const void *src, size_t bytes, const void **dst) {
+    void *p = dev_malloc(h, bytes);
+    if (!p) return AC_ERR_OOM;
+    h->owned.push_back(p);
+    if (bytes && cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return AC_ERR_CUDA;
+    *dst = p;
+    return AC_OK;
+}
+
+void release_host_path(ac_automaton *h) {
+    for (int i = 0; i < 2; ++i) {
+        dev_release(h, h->h2d_text[i]);
+        dev_release(h, h->h2d_out[i]);
+        h->h2d_text[i] = nullptr;
+        h->h2d_out[i] = nullptr;
+        if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
+        if (h->ev_comp[i]) cudaEventDestroy(h->ev_comp[i]);
+        if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+        h->ev_in[i] = h->ev_comp[i] = h->ev_out[i] = nullptr;
+    }
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
+    h->s_in = h->s_out = nullptr;
+    h->chunk = 0;
+}
+
+ac_status check_device(ac_automaton *h) {
+    if (!h) return AC_ERR_INVALID_ARG;
+    if (h->host_only) return AC_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AC_ERR_CUDA;
+    if (dev != h->device) return AC_ERR_INVALID_ARG;
+    return AC_OK;
+}
+
+ac_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return AC_OK;
+    if (e == cudaErrorMemoryAllocation) return AC_ERR_OOM;
+    if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) return AC_ERR_INVALID_ARG;
+    return AC_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ac_default_options(ac_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->class_compress = 1;
+}
+
+ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint32_t k, const ac_options *opt,
+                     ac_handle *out) {
+    if (!out) return AC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (k == 0) return AC_ERR_EMPTY_PATTERN;
+    if (!patterns || !lens) return AC_ERR_INVALID_ARG;
+    ac_options o;
+    ac_default_options(&o);
+    if (opt) o = *opt;
+    if (o.index_width != 0 && o.index_width != 16 && o.index_width != 32) return AC_ERR_INVALID_ARG;
+    if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr)) return AC_ERR_INVALID_ARG;
+
+    ac_automaton *h = new (std::nothrow) ac_automaton();
+    if (!h) return AC_ERR_OOM;
+    pfac::BuildOptions bo;
+    bo.index_width = o.index_width;
+    bo.class_compress = o.class_compress ? 1 : 0;
+    if (o.jump_bytes) bo.jump_bytes = o.jump_bytes;
+    if (o.stride_bytes) bo.stride_bytes = o.stride_bytes;
+    int st = pfac::build_tables(patterns, lens, k, bo, &h->host);
+    if (st != AC_OK) {
+        delete h;
+        return static_cast<ac_status>(st);
+    }
+    h->host_only = o.host_only != 0;
+    h->dev_alloc = o.dev_alloc;
+    h->dev_free = o.dev_free;
+    h->alloc_ctx = o.alloc_ctx;
+    const pfac::HostTables &t = h->host;
+    pfac::DevTables &d = h->dev;
+    d.S = t.S;
+    d.C = t.C;
+    d.W = t.W;
+    d.gbits = t.gbits;
+    d.B = t.B;
+    d.k = t.k;
+    d.k2 = t.k2;
+    d.base_k = t.base_k;
+    d.maxlen = t.maxlen;
+    d.jbytes = static_cast<uint32_t>(t.J.size() * sizeof(int16_t));
+    if (!h->host_only) {
+        if (cudaGetDevice(&h->device) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return AC_ERR_CUDA;
+        }
+        ac_status s = upload(h, t.G.data(), t.G.size(), &d.G);
+        if (s == AC_OK) s = upload(h, t.cls.data(), 512, reinterpret_cast<const void **>(&d.cls));
+        if (s == AC_OK && !t.J.empty())
+            s = upload(h, t.J.data(), t.J.size() * sizeof(int16_t), reinterpret_cast<const void **>(&d.J));
+        if (s == AC_OK && !t.J2.empty())
+            s = upload(h, t.J2.data(), t.J2.size() * sizeof(int32_t), reinterpret_cast<const void **>(&d.J2));
+        if (s != AC_OK) {
+            ac_destroy(h);
+            return s;
+        }
+    }
+    *out = h;
+    return AC_OK;
+}
+
+ac_status ac_destroy(ac_handle h) {
+    if (!h) return AC_OK;
+    release_host_path(h);
+    for (void *p : h->owned) dev_release(h, p);
+    delete h;
+    return AC_OK;
+}
+
+ac_status ac_info(ac_handle h, ac_info_t *info) {
+    if (!h || !info) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    std::memset(info, 0, sizeof(*info));
+    info->n_keywords = t.nkw;
+    info->n_states = t.S;
+    info->n_classes = t.C;
+    info->row_width = t.W;
+    info->index_width = t.gbits;
+    info->code_bits = t.B;
+    info->jump_depth = t.k;
+    info->stride_depth = t.k2;
+    info->min_len = t.minlen;
+    info->max_len = t.maxlen;
+    info->table_bytes = t.G.size() + t.J.size() * sizeof(int16_t) + t.J2.size() * sizeof(int32_t) + 512;
+    info->depth_base_jump = t.base_k;
+    info->count_jump = t.count_k;
+    return AC_OK;
+}
+
+ac_status ac_export_tables(ac_handle h, int16_t *cls, void *goto_, uint32_t *depth) {
+    if (!h) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    if (cls) std::memcpy(cls, t.cls.data(), 256 * sizeof(int16_t));
+    if (goto_) std::memcpy(goto_, t.G.data(), t.G.size());
+    if (depth) std::memcpy(depth, t.depth_count.data(), t.depth_count.size() * sizeof(uint32_t));
+    return AC_OK;
+}
+
+ac_status ac_set_kernel(ac_handle h, ac_kernel kernel) {
+    if (!h || (kernel != AC_KERNEL_TILED && kernel != AC_KERNEL_SIMPLE)) return AC_ERR_INVALID_ARG;
+    h->kernel = kernel;
+    return AC_OK;
+}
+
+ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_out_ids, void *stream) {
+    ac_status s = check_device(h);
+    if (s != AC_OK) return s;
+    if (n == 0) return AC_OK;
+    if (!d_text || !d_out_ids) return AC_ERR_INVALID_ARG;
+    pfac::MatchRequest r;
+    r.text = d_text;
+    r.n = n;
+    r.out = d_out_ids;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (h->kernel == AC_KERNEL_SIMPLE) return cuda_status(pfac::launch_simple(h->dev, r, st));
+    return cuda_status(pfac::launch_tiled(h->dev, r, pfac::OUT_DENSE, h->tuning, st));
+}
+
+ac_status ac_count(ac_handle h, const uint8_t *d_text, uint64_t n, uint64_t *d_count, void *stream) {
+    ac_status s = check_device(h);
+    if (s != AC_OK) return s;
+    if (!d_count) return AC_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st);
+    if (e != cudaSuccess || n == 0) return cuda_status(e);
+    if (!d_text) return AC_ERR_INVALID_ARG;
+    pfac::MatchRequest r;
+    r.text = d_text;
+    r.n = n;
+    r.count = reinterpret_cast<unsigned long long *>(d_count);
+    return cuda_status(pfac::launch_tiled(h->dev, r, pfac::OUT_COUNT, h->tuning, st));
+}
+
+ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos, uint32_t *d_ids,
+                           uint64_t cap, uint64_t *d_count, void *stream) {
+    ac_status s = check_device(h);
+    if (s != AC_OK) return s;
+    if (!d_count || (cap > 0 && (!d_pos || !d_ids))) return AC_ERR_INVALID_ARG;
+    if (n > 0xFFFFFFFFull) return AC_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
+    if (!d_text) return AC_ERR_INVALID_ARG;
+    const size_t bytes = pfac::compact_scratch_bytes(h->dev, n, h->tuning);
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemsetAsync(scratch, 0, bytes, st);
+    if (e == cudaSuccess) {
+        pfac::MatchRequest r;
+        r.text = d_text;
+        r.n = n;
+        r.pos = d_pos;
+        r.ids = d_ids;
+        r.cap = cap;
+        r.count = reinterpret_cast<unsigned long long *>(d_count);
+        r.scratch = scratch;
+        r.scratch_bytes = bytes;
+        e = pfac::launch_tiled(h->dev, r, pfac::OUT_COMPACT, h->tuning, st);
+    }
+    cudaError_t e2 = cudaFreeAsync(scratch, st);
+    return cuda_status(e != cudaSuccess ? e : e2);
+}
+
+ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t *h_out_ids, void *stream) {
+    ac_status s = check_device(h);
+    if (s != AC_OK) return s;
+    if (n == 0) return AC_OK;
+    if (!h_text || !h_out_ids) return AC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(h->host_mu);
+    cudaStream_t sc = static_cast<cudaStream_t>(stream);
+    const size_t chunk = 64u << 20;
+    const size_t halo = h->host.maxlen;
+    if (h->chunk == 0) {
+        for (int i = 0; i < 2; ++i) {
+            h->h2d_text[i] = static_cast<uint8_t *>(dev_malloc(h, chunk + halo + 16));
+            h->h2d_out[i] = static_cast<int32_t *>(dev_malloc(h, (chunk + halo + 16) * sizeof(int32_t)));
+            if (!h->h2d_text[i] || !h->h2d_out[i]) {
+                release_host_path(h);
+                return AC_ERR_OOM;
+            }
+            if (cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_comp[i], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming) != cudaSuccess) {
+                release_host_path(h);
+                return AC_ERR_CUDA;
+            }
+        }
+        if (cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking) != cudaSuccess) {
+            release_host_path(h);
+            return AC_ERR_CUDA;
+        }
+        h->chunk = chunk;
+    }
+    // Every call ends with all three streams synchronised, so the events only
+    // order the chunks of this call.
+    cudaError_t e = cudaSuccess;
+    const uint64_t nchunks = (n + chunk - 1) / chunk;
+    for (uint64_t c = 0; c < nchunks && e == cudaSuccess; ++c) {
+        const int slot = static_cast<int>(c & 1);
+        const uint64_t lo = c * chunk;
+        const uint64_t hi = std::min<uint64_t>(n, lo + chunk);
+        const uint64_t hi_halo = std::min<uint64_t>(n, hi + halo);
+        // text slot is free once the kernel two chunks back has read it
+        if (c >= 2) e = cudaStreamWaitEvent(h->s_in, h->ev_comp[slot], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->h2d_text[slot], h_text + lo, hi_halo - lo, cudaMemcpyHostToDevice, h->s_in);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_in[slot], h->s_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, h->ev_in[slot], 0);
+        // output slot is free once the copy-out two chunks back has finished
+        if (e == cudaSuccess && c >= 2) e = cudaStreamWaitEvent(sc, h->ev_out[slot], 0);
+        if (e == cudaSuccess) {
+            pfac::MatchRequest r;
+            r.text = h->h2d_text[slot];
+            r.n = hi_halo - lo;
+            r.out = h->h2d_out[slot];
+            e = (h->kernel == AC_KERNEL_SIMPLE) ? pfac::launch_simple(h->dev, r, sc)
+                                                : pfac::launch_tiled(h->dev, r, pfac::OUT_DENSE, h->tuning, sc);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_comp[slot], sc);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_comp[slot], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h_out_ids + lo, h->h2d_out[slot], (hi - lo) * sizeof(int32_t),
+                                cudaMemcpyDeviceToHost, h->s_out);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_out[slot], h->s_out);
+    }
+    cudaError_t e1 = cudaStreamSynchronize(h->s_out);
+    cudaError_t e2 = cudaStreamSynchronize(sc);
+    cudaError_t e3 = cudaStreamSynchronize(h->s_in);
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3);
+    return cuda_status(e);
+}
+
+ac_status ac_device_status(void) {
+    unsigned int v = 0;
+    cudaError_t e = pfac::read_device_error(&v);
+    if (e != cudaSuccess) return AC_ERR_CUDA;
+    return v ? AC_ERR_TIMEOUT : AC_OK;
+}
+
+const char *ac_status_string(ac_status s) {
+    switch (s) {
+        case AC_OK: return "ok";
+        case AC_ERR_INVALID_ARG: return "invalid argument";
+        case AC_ERR_EMPTY_PATTERN: return "empty keyword or empty keyword set";
+        case AC_ERR_TOO_MANY_STATES: return "too many automaton states";
+        case AC_ERR_OOM: return "out of memory";
+        case AC_ERR_CUDA: return "CUDA runtime error";
+        case AC_ERR_OVERFLOW: return "more matches than output capacity";
+        case AC_ERR_BUDGET: return "request exceeds the memory budget";
+        case AC_ERR_TIMEOUT: return "a bounded device wait ran out";
+        case AC_ERR_NOT_FOUND: return "unknown id";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+// Host automaton builder: keyword set -> failureless goto table (paper section
+// II: the goto function of the pattern matching machine, stored as a matrix
+// for the GPU and used without failure transitions, Fig. 5).
+//
+// Steps, in order:
+//   1. class map: each byte that occurs in a keyword gets a code 0..C-1 (in byte
+//      order); other bytes can never extend a walk.
+//   2. trie insertion of every keyword (the goto function);
+//   3. breadth-first renumbering, children in code order, so depth d occupies
+//      a contiguous id range and the hot upper levels form a prefix;
+//   4. per state, the longest keyword that is a prefix of the state's string
+//      (the output a walk ending there reports; equal strings -> lowest id);
+//   5. the dense table, one row per state: C goto columns plus one end column,
+//      where a missing transition holds the encoded result of stopping there;
+//   6. the root jump table: the result of walking any k codes from the root,
+//      (the top k levels of the table flattened into one lookup);
+//   7. the stride table: the same for k2 codes from every depth-k state.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <unordered_map>
+
+#include "ac.h"
+#include "pfac_internal.h"
+
+namespace pfac {
+
+namespace {
+
+struct Edge {
+    uint32_t parent;
+    uint32_t code;
+    uint32_t child;
+};
+
+inline uint32_t code_bits_for(uint32_t C) { return C <= 4 ? 2u : (C <= 16 ? 4u : 8u); }
+
+template <typename T>
+inline int32_t g_at(const HostTables &h, uint64_t idx) {
+    return static_cast<int32_t>(reinterpret_cast<const T *>(h.G.data())[idx]);
+}
+
+inline int32_t goto_entry(const HostTables &h, uint32_t s, uint32_t c) {
+    uint64_t idx = static_cast<uint64_t>(s) * h.W + c;
+    return h.gbits == 16 ? g_at<int16_t>(h, idx) : g_at<int32_t>(h, idx);
+}
+
+}  // namespace
+
+int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t nkw,
+                 const BuildOptions &opt, HostTables *out) {
+    if (!out || !patterns || !lens) return AC_ERR_INVALID_ARG;
+    if (nkw == 0) return AC_ERR_EMPTY_PATTERN;
+    if (nkw > 0x7FFFFFF0u) return AC_ERR_INVALID_ARG;
+    HostTables h;
+    h.nkw = nkw;
+    uint64_t total = 0;
+    h.minlen = UINT32_MAX;
+    for (uint32_t i = 0; i < nkw; ++i) {
+        if (lens[i] == 0) return AC_ERR_EMPTY_PATTERN;
+        if (!patterns[i]) return AC_ERR_INVALID_ARG;
+        total += lens[i];
+        h.minlen = std::min(h.minlen, lens[i]);
+        h.maxlen = std::max(h.maxlen, lens[i]);
+    }
+    if (total + 1 > 0x7FFFFFFFull) return AC_ERR_TOO_MANY_STATES;
+
+    try {
+        // 1. class map
+        h.cls.assign(256, -1);
+        if (opt.class_compress) {
+            bool present[256] = {false};
+            for (uint32_t i = 0; i < nkw; ++i)
+                for (uint32_t j = 0; j < lens[i]; ++j) present[patterns[i][j]] = true;
+            int16_t c = 0;
+            for (int b = 0; b < 256; ++b)
+                if (present[b]) h.cls[b] = c++;
+            h.C = static_cast<uint32_t>(c);
+        } else {
+            for (int b = 0; b < 256; ++b) h.cls[b] = static_cast<int16_t>(b);
+            h.C = 256;
+        }
+
+        // 2. trie insertion (provisional ids in creation order)
+        std::unordered_map<uint64_t, uint32_t> child;
+        child.reserve(static_cast<size_t>(std::min<uint64_t>(total, 1ull << 26)) + 16);
+        std::vector<int32_t> kw_at{-1};   // lowest keyword id ending at each provisional state
+        std::vector<Edge> edges;
+        edges.reserve(static_cast<size_t>(std::min<uint64_t>(total, 1ull << 26)));
+        for (uint32_t id = 0; id < nkw; ++id) {
+            uint32_t s = 0;
+            for (uint32_t j = 0; j < lens[id]; ++j) {
+                uint32_t c = static_cast<uint32_t>(h.cls[patterns[id][j]]);
+                uint64_t key = (static_cast<uint64_t>(s) << 8) | c;
+                auto it = child.find(key);
+                if (it == child.end()) {
+                    uint32_t t = static_cast<uint32_t>(kw_at.size());
+                    kw_at.push_back(-1);
+                    child.emplace(key, t);
+                    edges.push_back({s, c, t});
+                    s = t;
+                } else {
+                    s = it->second;
+                }
+            }
+            if (kw_at[s] < 0) kw_at[s] = static_cast<int32_t>(id);  // ids arrive in increasing order
+        }
+        child.clear();
+        child.rehash(0);
+        const uint32_t S = static_cast<uint32_t>(kw_at.size());
+        h.S = S;
+
+        // 3. breadth-first renumbering with children in code order
+        std::vector<uint32_t> first(S + 1, 0);
+        for (const Edge &e : edges) first[e.parent + 1]++;
+        for (uint32_t s = 0; s < S; ++s) first[s + 1] += first[s];
+        std::vector<uint32_t> adj(edges.size());
+        {
+            std::vector<uint32_t> fill(first.begin(), first.end() - 1);
+            for (uint32_t i = 0; i < edges.size(); ++i) adj[fill[edges[i].parent]++] = i;
+        }
+        for (uint32_t s = 0; s < S; ++s)
+            std::sort(adj.begin() + first[s], adj.begin() + first[s + 1],
+                      [&](uint32_t a, uint32_t b) { return edges[a].code < edges[b].code; });
+        std::vector<uint32_t> order;    // new id -> provisional id
+        order.reserve(S);
+        std::vector<uint32_t> newid(S, 0);
+        std::vector<uint32_t> depth(S, 0);     // by new id
+        std::vector<uint32_t> parent(S, 0);    // by new id
+        order.push_back(0);
+        for (size_t qi = 0; qi < order.size(); ++qi) {
+            uint32_t old = order[qi];
+            for (uint32_t a = first[old]; a < first[old + 1]; ++a) {
+                const Edge &e = edges[adj[a]];
+                uint32_t nid = static_cast<uint32_t>(order.size());
+                newid[e.child] = nid;
+                depth[nid] = depth[qi] + 1;
+                parent[nid] = static_cast<uint32_t>(qi);
+                order.push_back(e.child);
+            }
+        }
+        h.depth_count.assign(h.maxlen + 1, 0);
+        for (uint32_t s = 0; s < S; ++s) h.depth_count[depth[s]]++;
+
+        // 4. longest keyword on the path to each state (BFS order: parents first)
+        std::vector<int32_t> pathbest(S, -1);
+        for (uint32_t s = 1; s < S; ++s) {
+            int32_t own = kw_at[order[s]];
+            pathbest[s] = own >= 0 ? own : pathbest[parent[s]];
+        }
+
+        // 5. dense goto table
+        h.W = (h.C + 1 <= 8) ? 8u : h.C + 1;
+        bool fits16 = (S <= 32768u) && (nkw <= 32767u);
+        if (opt.index_width == 16 && !fits16) return AC_ERR_INVALID_ARG;
+        h.gbits = (opt.index_width == 32 || !fits16) ? 32u : 16u;
+        const uint64_t cells = static_cast<uint64_t>(S) * h.W;
+        h.G.assign(cells * (h.gbits / 8), 0);
+        auto put = [&](uint64_t idx, int32_t v) {
+            if (h.gbits == 16)
+                reinterpret_cast<int16_t *>(h.G.data())[idx] = static_cast<int16_t>(v);
+            else
+                reinterpret_cast<int32_t *>(h.G.data())[idx] = v;
+        };
+        for (uint32_t s = 0; s < S; ++s) {
+            int32_t dead = encode_dead(pathbest[s]);
+            uint64_t row = static_cast<uint64_t>(s) * h.W;
+            for (uint32_t c = 0; c < h.W; ++c) put(row + c, dead);
+            uint32_t old = order[s];
+            for (uint32_t a = first[old]; a < first[old + 1]; ++a) {
+                const Edge &e = edges[adj[a]];
+                put(row + e.code, static_cast<int32_t>(newid[e.child]));
+            }
+        }
+        std::vector<Edge>().swap(edges);
+
+        // 6. root jump table
+        h.B = code_bits_for(h.C);
+        const uint32_t wl = window_limit(h.B);
+        uint32_t jentries = std::max<uint32_t>(opt.jump_bytes, 2u) / 2u;
+        uint32_t kj = 0;
+        while (kj + 1 <= h.maxlen && kj + 1 <= wl && h.B * (kj + 1) <= 16 &&
+               (1ull << (h.B * (kj + 1))) <= jentries)
+            ++kj;
+        while (kj > 0 && h.depth_count[kj] > 32768u) --kj;
+        h.k = kj;
+        std::vector<uint32_t> depth_base(h.maxlen + 2, 0);
+        for (uint32_t d = 0; d <= h.maxlen; ++d) depth_base[d + 1] = depth_base[d] + h.depth_count[d];
+        h.base_k = depth_base[kj];
+        h.count_k = h.depth_count[kj];
+        const uint32_t cmask = (1u << h.B) - 1u;
+        if (kj > 0) {
+            uint32_t nj = 1u << (h.B * kj);
+            h.J.assign(std::max<uint32_t>(nj, 8u), kJumpSlow);
+            for (uint32_t w = 0; w < nj; ++w) {
+                uint32_t s = 0;
+                int32_t e = 0;
+                bool alive = true;
+                for (uint32_t i = 0; i < kj; ++i) {
+                    uint32_t c = (w >> (h.B * i)) & cmask;
+                    int32_t t = c < h.C ? goto_entry(h, s, c) : encode_dead(pathbest[s]);
+                    if (t < 0) {
+                        e = t;
+                        alive = false;
+                        break;
+                    }
+                    s = static_cast<uint32_t>(t);
+                }
+                if (alive)
+                    h.J[w] = static_cast<int16_t>(s - h.base_k);
+                else
+                    h.J[w] = (e >= -32767) ? static_cast<int16_t>(e) : kJumpSlow;
+            }
+        }
+
+        // 7. stride table from the depth-k states
+        h.k2 = 0;
+        if (kj > 0 && opt.stride_bytes > 1) {
+            uint32_t top = std::min(h.maxlen - kj, wl - kj);
+            for (uint32_t cand = top; cand >= 2; --cand) {
+                if (h.B * cand >= 32) continue;
+                uint64_t bytes = (static_cast<uint64_t>(h.count_k) << (h.B * cand)) * 4ull;
+                if (bytes <= opt.stride_bytes) {
+                    h.k2 = cand;
+                    break;
+                }
+            }
+        }
+        if (h.k2 > 0) {
+            const uint32_t cols = 1u << (h.B * h.k2);
+            h.J2.assign(static_cast<size_t>(h.count_k) * cols, 0);
+            for (uint32_t r = 0; r < h.count_k; ++r) {
+                for (uint32_t w = 0; w < cols; ++w) {
+                    uint32_t s = h.base_k + r;
+                    int32_t e = 0;
+                    bool alive = true;
+                    for (uint32_t i = 0; i < h.k2; ++i) {
+                        uint32_t c = (w >> (h.B * i)) & cmask;
+                        int32_t t = c < h.C ? goto_entry(h, s, c) : encode_dead(pathbest[s]);
+                        if (t < 0) {
+                            e = t;
+                            alive = false;
+                            break;
+                        }
+                        s = static_cast<uint32_t>(t);
+                    }
+                    h.J2[static_cast<size_t>(r) * cols + w] = alive ? static_cast<int32_t>(s) : e;
+                }
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        return AC_ERR_OOM;
+    }
+    *out = std::move(h);
+    return AC_OK;
+}
+
+}  // namespace pfac

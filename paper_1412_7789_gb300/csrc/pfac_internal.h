@@ -1,0 +1,99 @@
+// Internal declarations shared by the builder, the kernels and the C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime_api.h>
+
+namespace pfac {
+
+// A dead goto entry encodes the result of a walk that stops at its row:
+// entry = -(id + 2), id = keyword id or -1.  Live entries are child ids > 0
+// (the root, state 0, is never a child).
+inline int32_t encode_dead(int32_t id) { return -(id + 2); }
+
+// Jump-table entries are int16; this value sends a start to the plain walk
+// (used when a result does not fit in 15 bits).
+constexpr int16_t kJumpSlow = -32768;
+
+// Longest halo staged in shared memory; walks that run past it read global memory.
+constexpr uint32_t kHaloCap = 1024;
+
+struct BuildOptions {
+    int index_width = 0;        // 0 = auto, 16, 32
+    int class_compress = 1;     // 1 = distinct keyword bytes, 0 = 256 columns
+    uint32_t jump_bytes = 128u << 10;
+    uint64_t stride_bytes = 16ull << 20;
+};
+
+// Host-side automaton: everything the kernels need, in the layout they use.
+struct HostTables {
+    uint32_t nkw = 0;        // keywords
+    uint32_t S = 0;          // states (BFS order, root = 0)
+    uint32_t C = 0;          // classes (distinct keyword bytes, or 256)
+    uint32_t W = 0;          // row width: C goto columns + 1 end column, padded
+    uint32_t gbits = 32;     // goto entry width (16 or 32)
+    uint32_t B = 8;          // bits per character code in the packed stream (2, 4, 8)
+    uint32_t k = 0;          // root jump depth (0 = no jump table)
+    uint32_t k2 = 0;         // stride depth after the jump (0 = none)
+    uint32_t base_k = 0;     // first state at depth k
+    uint32_t count_k = 0;    // states at depth k
+    uint32_t minlen = 0, maxlen = 0;
+    std::vector<int16_t> cls;        // 256: byte -> code or -1
+    std::vector<uint8_t> G;          // S * W entries of gbits
+    std::vector<int16_t> J;          // 2^(B*k) (padded to 8 entries)
+    std::vector<int32_t> J2;         // count_k << (B*k2)
+    std::vector<uint32_t> depth_count;  // maxlen + 1
+    bool identity_classes() const { return C == 256; }
+};
+
+// Returns an ac_status value.
+int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t k,
+                 const BuildOptions &opt, HostTables *out);
+
+// Largest k + k2 the kernel's 64-bit code window allows for a code width.
+inline uint32_t window_limit(uint32_t B) { return B == 2 ? 17u : (B == 4 ? 9u : 5u); }
+
+// Device view of a compiled automaton.
+struct DevTables {
+    const void *G = nullptr;         // goto table
+    const int16_t *J = nullptr;      // root jump table (device copy, for the bulk load)
+    const int32_t *J2 = nullptr;     // stride table
+    const int16_t *cls = nullptr;    // class map (256 entries)
+    uint32_t S = 0, C = 0, W = 0, gbits = 32, B = 8, k = 0, k2 = 0, base_k = 0, maxlen = 0;
+    uint32_t jbytes = 0;             // bytes of J (multiple of 16)
+};
+
+enum OutMode : int { OUT_DENSE = 0, OUT_COUNT = 1, OUT_COMPACT = 2 };
+
+struct MatchRequest {
+    const uint8_t *text = nullptr;
+    uint64_t n = 0;
+    int32_t *out = nullptr;                  // dense
+    unsigned long long *count = nullptr;     // count / compact total
+    uint32_t *pos = nullptr;                 // compact
+    uint32_t *ids = nullptr;                 // compact
+    uint64_t cap = 0;                        // compact
+    void *scratch = nullptr;                 // compact: counter + per-tile status
+    size_t scratch_bytes = 0;
+};
+
+struct Tuning {
+    int block = 512;      // threads per CTA (multiple of 32, <= 512)
+    int stages = 4;       // text stages in flight per CTA
+    int grid = 0;         // 0 = one CTA per SM
+};
+
+// Scratch bytes the compact kernel needs for a text of n bytes.
+size_t compact_scratch_bytes(const DevTables &t, uint64_t n, const Tuning &tu);
+
+cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode,
+                         const Tuning &tu, cudaStream_t stream);
+cudaError_t launch_simple(const DevTables &t, const MatchRequest &r, cudaStream_t stream);
+
+// Read and clear the device error word of the current device.
+cudaError_t read_device_error(unsigned int *value);
+
+}  // namespace pfac

@@ -1,0 +1,148 @@
+"""CPU checks of the C ABI and the host automaton builder (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_7789_gb300 import api, build, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return api.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ac.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ \*]*?\b(ac_[a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert "ac_compile" in names and "ac_match" in names and len(names) >= 12
+    raw = ctypes.CDLL(api.library_path())
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    monkeypatch.setattr(api, "_LIB", None)
+    monkeypatch.setattr(api, "library_path", lambda: "/nonexistent/libpfac.so")
+    with pytest.raises(RuntimeError):
+        api.lib()
+
+
+def test_status_strings(lib):
+    assert api.ac_status_string(0) == "ok"
+    assert "empty" in api.ac_status_string(api.AC_ERR_EMPTY_PATTERN)
+
+
+def test_rejects_bad_keyword_sets(lib):
+    with pytest.raises(api.AcError) as e:
+        api.ac_compile([b"ab", b""], host_only=True)
+    assert e.value.status == api.AC_ERR_EMPTY_PATTERN
+    with pytest.raises(api.AcError) as e:
+        api.ac_compile([], host_only=True)
+    assert e.value.status == api.AC_ERR_EMPTY_PATTERN
+    big = [bytes([i % 256, i // 256, 7]) for i in range(40000)]
+    with pytest.raises(api.AcError) as e:
+        api.ac_compile(big, index_width=16, host_only=True)
+    assert e.value.status == api.AC_ERR_INVALID_ARG
+
+
+def test_host_only_handle_refuses_matching(lib):
+    h = api.ac_compile([b"ab"], host_only=True)
+    try:
+        st = lib.ac_match(h, 1, 10, 1, 0)
+        assert st == api.AC_ERR_INVALID_ARG
+    finally:
+        api.ac_destroy(h)
+
+
+def walk_table(cls, G, C, text):
+    """Debug walker over the builder's exported table (not an oracle): follow
+    the goto entries from every start, stop at the first dead entry."""
+    n = len(text)
+    out = np.empty(n, dtype=np.int32)
+    for i in range(n):
+        s = 0
+        j = i
+        while True:
+            if j >= n or cls[text[j]] < 0:
+                e = int(G[s, C])
+                break
+            e = int(G[s, cls[text[j]]])
+            if e < 0:
+                break
+            s = e
+            j += 1
+        out[i] = -e - 2
+    return out
+
+
+CASES = [
+    ([b"he", b"she", b"his", b"hers"], b"ushers"),
+    ([b"AB", b"ABG", b"BEDE", b"ED"], b"ABEDEABGED"),
+]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_builder_structure_against_oracle(lib, seed):
+    g = np.random.Generator(np.random.PCG64(seed))
+    alphabet = [b"ACGT", b"ab", bytes(range(256)), b"abcdefghij"][seed % 4]
+    a = np.frombuffer(alphabet, dtype=np.uint8)
+    text = a[g.integers(0, a.size, size=3000)]
+    pats = [bytes(text[o:o + L]) for o, L in zip(g.integers(0, 2900, 30), g.integers(1, 20, 30))]
+    pats += [bytes(a[g.integers(0, a.size, size=int(L))]) for L in g.integers(1, 12, 30)]
+    pats += [pats[3], pats[7]]  # duplicates
+    h = api.ac_compile(pats, host_only=True)
+    try:
+        info = api.ac_info(h)
+        cls, G, depth = api.ac_export_tables(h)
+        with oracle.Machine(pats) as m:
+            assert info["n_states"] == m.n_states
+            assert np.array_equal(depth.astype(np.uint64), m.depth_counts()[: depth.size])
+            want = m.pfac_ids(text)
+        # class map: distinct keyword bytes, in byte order
+        present = sorted(set(b"".join(pats)))
+        assert info["n_classes"] == len(present)
+        assert [int(cls[b]) for b in present] == list(range(len(present)))
+        assert all(cls[b] == -1 for b in range(256) if b not in present)
+        # 16-bit entries exactly when every state id and keyword id fits
+        fits = info["n_states"] <= 32768 and len(pats) <= 32767
+        assert info["index_width"] == (16 if fits else 32)
+        # BFS order: children have larger ids, depth is non-decreasing in id
+        C = info["n_classes"]
+        starts = np.concatenate([[0], np.cumsum(depth)])
+        dep = np.repeat(np.arange(depth.size), depth)
+        child = G[:, :C]
+        for s in range(info["n_states"]):
+            kids = child[s][child[s] > 0]
+            assert np.all(dep[kids] == dep[s] + 1)
+            assert np.all(np.diff(kids) > 0)
+        assert starts[-1] == info["n_states"]
+        # every keyword's final state reports the lowest id of its string
+        assert np.array_equal(walk_table(cls, G, C, text), want)
+    finally:
+        api.ac_destroy(h)
+
+
+def test_builder_jump_and_stride_shapes(lib):
+    text, pats = workloads.sweep_acgt(1 << 14)
+    h = api.ac_compile(pats, host_only=True)
+    info = api.ac_info(h)
+    api.ac_destroy(h)
+    assert info["code_bits"] == 2 and info["jump_depth"] == 8
+    assert info["stride_depth"] == 4 and info["count_jump"] <= 32768
+    h = api.ac_compile(pats, host_only=True, stride_bytes=1, jump_bytes=64)
+    info = api.ac_info(h)
+    api.ac_destroy(h)
+    assert info["stride_depth"] == 0 and info["jump_depth"] == 2

@@ -1,0 +1,219 @@
+"""CUDA path against the CPU oracle, bit-exact, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_7789_gb300 import api, workloads
+from tests import _gpu, _pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1412_7789_gb300 import build
+
+    build.build()
+    api.lib()
+    yield
+    assert api.ac_device_status() == api.AC_OK
+
+
+def compile_(pats, **kw):
+    return api.Automaton(pats, **kw)
+
+
+@pytest.mark.parametrize("name", ["w1_ushers.txt", "w2_fig45.txt"])
+@pytest.mark.parametrize("kernel", ["tiled", "simple"])
+def test_golden(name, kernel):
+    keywords, cases = _pins.read_golden(name)
+    with compile_(keywords) as a:
+        a.set_kernel(kernel)
+        for c in cases:
+            want = np.array(c["ids"], dtype=np.int32)
+            text = np.frombuffer(c["text"], dtype=np.uint8)
+            modes = ("dense", "count", "compact") if kernel == "tiled" else ("dense",)
+            _gpu.check_all_modes(a.handle, text, want, modes=modes)
+
+
+@pytest.mark.parametrize("count", [5, 10])
+def test_paper_mode(count):
+    pats = workloads.paper_keywords(count, seed=0)
+    with compile_(pats) as a:
+        for n in (26, 1310, 16375, 40000, 53710, 671375):
+            text = workloads.paper_text(n)
+            want = _pins.paper_closed_form(n)
+            assert np.array_equal(oracle.pfac_ids(pats, text), want)
+            _gpu.check_all_modes(a.handle, text, want)
+
+
+def test_single_text_acgt_1mib():
+    text, pats = workloads.single_text_acgt(seed=0)
+    want = oracle.pfac_ids(pats, text)
+    assert oracle.count(want) > 0
+    with compile_(pats) as a:
+        _gpu.check_all_modes(a.handle, text, want)
+        a.set_kernel("simple")
+        _gpu.check_all_modes(a.handle, text, want, modes=("dense",))
+
+
+SIZES = [0, 1, 15, 16, 17, 63, 8191, 8192, 8193, 3 * 8192 + 77, 100_003]
+ALPHABETS = {
+    "ab": b"ab",                      # 2 classes   -> 2-bit codes
+    "acgt": b"ACGT",                  # 4 classes   -> 2-bit codes
+    "ten": b"abcdefghij",             # 10 classes  -> 4-bit codes
+    "forty": bytes(range(40, 80)),    # 40 classes  -> 8-bit codes, unknown bytes possible
+    "bytes": bytes(range(256)),       # 256 classes -> raw bytes
+}
+
+
+def random_case(g, alphabet: bytes, n: int, kw: int, lmax: int):
+    a = np.frombuffer(alphabet, dtype=np.uint8)
+    text = a[g.integers(0, a.size, size=n)] if n else np.zeros(0, np.uint8)
+    pats = []
+    for _ in range(kw):
+        L = int(g.integers(1, lmax + 1))
+        if n > L and g.random() < 0.5:
+            o = int(g.integers(0, n - L))
+            pats.append(bytes(text[o:o + L]))
+        else:
+            pats.append(bytes(a[g.integers(0, a.size, size=L)]))
+    return text, pats
+
+
+@pytest.mark.parametrize("alpha", sorted(ALPHABETS))
+def test_random_sizes(alpha):
+    g = np.random.Generator(np.random.PCG64(hash(alpha) % (1 << 32)))
+    for n in SIZES:
+        text, pats = random_case(g, ALPHABETS[alpha], max(n, 40), 50, 24)
+        text = text[:n]
+        want = oracle.pfac_ids(pats, text)
+        with compile_(pats) as a:
+            _gpu.check_all_modes(a.handle, text, want)
+
+
+@pytest.mark.parametrize("opts", [
+    dict(class_compress=False),
+    dict(index_width=32),
+    dict(jump_bytes=64, stride_bytes=1),
+    dict(jump_bytes=1024),
+    dict(stride_bytes=1),
+])
+def test_build_options_keep_results(opts):
+    g = np.random.Generator(np.random.PCG64(99))
+    text, pats = random_case(g, b"ACGT", 200_000, 400, 40)
+    text2, pats2 = random_case(g, bytes(range(0, 256, 3)), 50_000, 300, 30)
+    for t, p in ((text, pats), (text2, pats2)):
+        want = oracle.pfac_ids(p, t)
+        with compile_(p, **opts) as a:
+            _gpu.check_all_modes(a.handle, t, want)
+
+
+def test_longest_walk_and_edges():
+    """A run of one byte with keywords of that byte x1..x100: every start walks
+    to the end of its run (the longest walks the method has)."""
+    pats = [b"\x00" * L for L in range(1, 101)] + [b"\xff\x00", b"\x00\xff", b"\xff" * 3]
+    for n in (5, 99, 100, 101, 4096, 20_000):
+        text = np.zeros(n, dtype=np.uint8)
+        text[n // 2] = 0xFF
+        text[-1] = 0xFF
+        want = oracle.pfac_ids(pats, text)
+        with compile_(pats) as a:
+            _gpu.check_all_modes(a.handle, text, want)
+
+
+def test_keyword_longer_than_text_and_duplicates():
+    pats = [b"ACGTACGTACGTACGTACGT" * 4, b"ACG", b"ACG", b"A", b"ACGTA", b"CGTAC" * 30]
+    text = np.frombuffer(b"ACGTACGTAC", dtype=np.uint8)
+    want = oracle.pfac_ids(pats, text)
+    assert want.tolist()[:2] == [4, -1]
+    with compile_(pats) as a:
+        _gpu.check_all_modes(a.handle, text, want)
+
+
+def test_many_keywords_over_15_bits():
+    """More than 32767 keywords: 32-bit goto entries, and jump-table results
+    that do not fit 15 bits go to the plain walk."""
+    g = np.random.Generator(np.random.PCG64(5))
+    two = [bytes([a, b]) for a in range(256) for b in range(256)]
+    order = g.permutation(len(two))[:40_000]
+    pats = [two[i] for i in order] + [bytes(g.integers(0, 256, size=5).astype(np.uint8)) for _ in range(100)]
+    text = workloads.zipf_text(300_000, 3)
+    want = oracle.pfac_ids(pats, text)
+    with compile_(pats) as a:
+        assert a.info()["index_width"] == 32
+        _gpu.check_all_modes(a.handle, text, want)
+
+
+def test_unaligned_pointers():
+    import torch
+
+    g = np.random.Generator(np.random.PCG64(11))
+    text, pats = random_case(g, b"ACGT", 70_000, 200, 30)
+    with compile_(pats) as a:
+        base = _gpu.to_dev(text)
+        for off in (1, 3, 7, 13, 16):
+            for n in (0, 1, 17, 40_000, text.size - off):
+                t = base[off:off + n]
+                want = oracle.pfac_ids(pats, text[off:off + n])
+                out = torch.full((n + 8,), -7, dtype=torch.int32, device="cuda")
+                for oo in (0, 1, 2, 3):
+                    o = out[oo:oo + n]
+                    api.ac_match(a.handle, t, n, o)
+                    assert np.array_equal(o.cpu().numpy(), want), (off, n, oo)
+                _gpu.check_all_modes(a.handle, text[off:off + n], want, t=t, modes=("count", "compact"))
+
+
+@pytest.mark.parametrize("n", [4096, 65536, 1 << 20])
+def test_sweep_keywords_full(n):
+    text, pats = workloads.sweep_acgt(n)
+    want = oracle.pfac_ids(pats, text)
+    with compile_(pats) as a:
+        _gpu.check_all_modes(a.handle, text, want)
+
+
+def test_zipf_compact_and_overflow():
+    text, pats = workloads.zipf_byte(1 << 22, n_keywords=20_000)
+    want = oracle.pfac_ids(pats, text)
+    wpos, wid = oracle.compact(want)
+    assert wpos.size > 100
+    with compile_(pats) as a:
+        _gpu.check_all_modes(a.handle, text, want)
+        t = _gpu.to_dev(text)
+        cap = wpos.size // 3
+        pos, ids, total = _gpu.compact(a.handle, t, cap)
+        assert total == wpos.size and pos.size == cap
+        assert np.array_equal(pos, wpos[:cap]) and np.array_equal(ids, wid[:cap])
+        pos, ids, total = _gpu.compact(a.handle, t, 0)
+        assert total == wpos.size and pos.size == 0
+
+
+def test_sweep_full_size_sampled():
+    """The benchmark's workload and launch configuration (1 GiB ACGT text,
+    10,000 keywords), checked on sampled regions (tile seams, both ends)."""
+    import torch
+
+    text, pats = workloads.sweep_acgt(1 << 30)
+    t = _gpu.to_dev(text)
+    with compile_(pats) as a:
+        out = a.match(t)
+        torch.cuda.synchronize()
+        _gpu.regions_check(pats, text, out, _gpu.standard_regions(text.size))
+        assert int(a.count(t).item()) == int((out >= 0).sum().item())
+    del out, t
+
+
+def test_match_host_chunk_seams():
+    import torch
+
+    n = (64 << 20) + 12_345
+    text, pats = workloads.sweep_acgt(n, seed=4)
+    with compile_(pats) as a:
+        ht = torch.from_numpy(text).pin_memory()
+        got = a.match_host(ht)
+        regs = _gpu.standard_regions(n, seed=2, count=16) + [((64 << 20) - 700, (64 << 20) + 700)]
+        _gpu.regions_check(pats, text, got, regs)
+        small = text[:5000]
+        want = oracle.pfac_ids(pats, small)
+        got = a.match_host(torch.from_numpy(small.copy()))
+        assert np.array_equal(got.numpy(), want)
