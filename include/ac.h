@@ -100,6 +100,9 @@ typedef struct {
     uint64_t table_bytes;  /* device bytes of goto + jump + stride tables           */
     uint32_t depth_base_jump; /* first state id at depth jump_depth (BFS order)     */
     uint32_t count_jump;      /* number of states at depth jump_depth               */
+    int32_t class_hash_shift; /* s when (byte >> s) & 7 tells the keyword bytes apart
+                                 (at most 8 of them; bytes are then classified with
+                                 byte permutes), else -1 (class table)             */
 } ac_info_t;
 
 void ac_default_options(ac_options *opt);

@@ -68,6 +68,7 @@ class ac_info_t(ctypes.Structure):
         ("table_bytes", ctypes.c_uint64),
         ("depth_base_jump", ctypes.c_uint32),
         ("count_jump", ctypes.c_uint32),
+        ("class_hash_shift", ctypes.c_int32),
     ]
 
 

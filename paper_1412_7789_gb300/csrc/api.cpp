@@ -88,6 +88,23 @@ ac_status check_device(ac_automaton *h) {
     return AC_OK;
 }
 
+// A tiled launch with its zeroed scratch (tile counter, look-back words) in
+// stream-ordered memory, so calls on different streams never share it.
+cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode, cudaStream_t st) {
+    const size_t bytes = pfac::scratch_bytes(h->dev, r.n, mode, h->tuning);
+    void *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(scratch, 0, bytes, st);
+    if (e == cudaSuccess) {
+        r.scratch = scratch;
+        r.scratch_bytes = bytes;
+        e = pfac::launch_tiled(h->dev, r, mode, h->tuning, st);
+    }
+    const cudaError_t e2 = cudaFreeAsync(scratch, st);
+    return e != cudaSuccess ? e : e2;
+}
+
 ac_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return AC_OK;
     if (e == cudaErrorMemoryAllocation) return AC_ERR_OOM;
@@ -145,6 +162,10 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     d.base_k = t.base_k;
     d.maxlen = t.maxlen;
     d.jbytes = static_cast<uint32_t>(t.J.size() * sizeof(int16_t));
+    d.jslow = t.jslow;
+    d.hash_shift = t.hash_shift;
+    std::memcpy(d.hash_code, t.hash_code, 8);
+    std::memcpy(d.hash_byte, t.hash_byte, 8);
     if (!h->host_only) {
         if (cudaGetDevice(&h->device) != cudaSuccess) {
             cudaGetLastError();
@@ -153,6 +174,7 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
         }
         ac_status s = upload(h, t.G.data(), t.G.size(), &d.G);
         if (s == AC_OK) s = upload(h, t.cls.data(), 512, reinterpret_cast<const void **>(&d.cls));
+        if (s == AC_OK) s = upload(h, t.cls8.data(), 256, reinterpret_cast<const void **>(&d.cls8));
         if (s == AC_OK && !t.J.empty())
             s = upload(h, t.J.data(), t.J.size() * sizeof(int16_t), reinterpret_cast<const void **>(&d.J));
         if (s == AC_OK && !t.J2.empty())
@@ -191,6 +213,7 @@ ac_status ac_info(ac_handle h, ac_info_t *info) {
     info->table_bytes = t.G.size() + t.J.size() * sizeof(int16_t) + t.J2.size() * sizeof(int32_t) + 512;
     info->depth_base_jump = t.base_k;
     info->count_jump = t.count_k;
+    info->class_hash_shift = t.hash_shift;
     return AC_OK;
 }
 
@@ -220,7 +243,7 @@ ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_ou
     r.out = d_out_ids;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (h->kernel == AC_KERNEL_SIMPLE) return cuda_status(pfac::launch_simple(h->dev, r, st));
-    return cuda_status(pfac::launch_tiled(h->dev, r, pfac::OUT_DENSE, h->tuning, st));
+    return cuda_status(run_tiled(h, r, pfac::OUT_DENSE, st));
 }
 
 ac_status ac_count(ac_handle h, const uint8_t *d_text, uint64_t n, uint64_t *d_count, void *stream) {
@@ -235,7 +258,7 @@ ac_status ac_count(ac_handle h, const uint8_t *d_text, uint64_t n, uint64_t *d_c
     r.text = d_text;
     r.n = n;
     r.count = reinterpret_cast<unsigned long long *>(d_count);
-    return cuda_status(pfac::launch_tiled(h->dev, r, pfac::OUT_COUNT, h->tuning, st));
+    return cuda_status(run_tiled(h, r, pfac::OUT_COUNT, st));
 }
 
 ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos, uint32_t *d_ids,
@@ -247,25 +270,14 @@ ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint3
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
     if (!d_text) return AC_ERR_INVALID_ARG;
-    const size_t bytes = pfac::compact_scratch_bytes(h->dev, n, h->tuning);
-    void *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
-    if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMemsetAsync(scratch, 0, bytes, st);
-    if (e == cudaSuccess) {
-        pfac::MatchRequest r;
-        r.text = d_text;
-        r.n = n;
-        r.pos = d_pos;
-        r.ids = d_ids;
-        r.cap = cap;
-        r.count = reinterpret_cast<unsigned long long *>(d_count);
-        r.scratch = scratch;
-        r.scratch_bytes = bytes;
-        e = pfac::launch_tiled(h->dev, r, pfac::OUT_COMPACT, h->tuning, st);
-    }
-    cudaError_t e2 = cudaFreeAsync(scratch, st);
-    return cuda_status(e != cudaSuccess ? e : e2);
+    pfac::MatchRequest r;
+    r.text = d_text;
+    r.n = n;
+    r.pos = d_pos;
+    r.ids = d_ids;
+    r.cap = cap;
+    r.count = reinterpret_cast<unsigned long long *>(d_count);
+    return cuda_status(run_tiled(h, r, pfac::OUT_COMPACT, st));
 }
 
 ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t *h_out_ids, void *stream) {
@@ -322,7 +334,7 @@ ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t 
             r.n = hi_halo - lo;
             r.out = h->h2d_out[slot];
             e = (h->kernel == AC_KERNEL_SIMPLE) ? pfac::launch_simple(h->dev, r, sc)
-                                                : pfac::launch_tiled(h->dev, r, pfac::OUT_DENSE, h->tuning, sc);
+                                                : run_tiled(h, r, pfac::OUT_DENSE, sc);
         }
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_comp[slot], sc);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_out, h->ev_comp[slot], 0);

@@ -80,6 +80,36 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             for (int b = 0; b < 256; ++b) h.cls[b] = static_cast<int16_t>(b);
             h.C = 256;
         }
+        h.cls8.assign(256, 0xFF);
+        for (int b = 0; b < 256; ++b)
+            if (h.cls[b] >= 0) h.cls8[b] = static_cast<uint8_t>(h.cls[b]);
+        // a 3-bit hash of the byte that separates the keyword bytes lets the
+        // kernel classify four bytes at a time with byte permutes
+        h.hash_shift = -1;
+        if (h.C <= 8) {
+            for (int sh = 0; sh <= 5 && h.hash_shift < 0; ++sh) {
+                int seen[8];
+                for (int v = 0; v < 8; ++v) seen[v] = -1;
+                bool ok = true;
+                for (int b = 0; b < 256 && ok; ++b) {
+                    if (h.cls[b] < 0) continue;
+                    const int hv = (b >> sh) & 7;
+                    if (seen[hv] >= 0) ok = false;
+                    seen[hv] = b;
+                }
+                if (!ok) continue;
+                h.hash_shift = sh;
+                for (int v = 0; v < 8; ++v) {
+                    if (seen[v] >= 0) {
+                        h.hash_code[v] = static_cast<uint8_t>(h.cls[seen[v]]);
+                        h.hash_byte[v] = static_cast<uint8_t>(seen[v]);
+                    } else {
+                        h.hash_code[v] = 0;
+                        h.hash_byte[v] = static_cast<uint8_t>((v ^ 1) << sh);  // hashes to v ^ 1
+                    }
+                }
+            }
+        }
 
         // 2. trie insertion (provisional ids in creation order)
         std::unordered_map<uint64_t, uint32_t> child;
@@ -174,7 +204,10 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         }
         std::vector<Edge>().swap(edges);
 
-        // 6. root jump table
+        // 6. root jump table.  Entry for a window of k codes (first code in the
+        //    low bits): the walk's result (>= -1) when it stops inside the
+        //    window, else -(2 + s - base_k) for the depth-k state s reached;
+        //    kJumpSlow when a result does not fit 15 bits.
         h.B = code_bits_for(h.C);
         const uint32_t wl = window_limit(h.B);
         uint32_t jentries = std::max<uint32_t>(opt.jump_bytes, 2u) / 2u;
@@ -182,7 +215,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         while (kj + 1 <= h.maxlen && kj + 1 <= wl && h.B * (kj + 1) <= 16 &&
                (1ull << (h.B * (kj + 1))) <= jentries)
             ++kj;
-        while (kj > 0 && h.depth_count[kj] > 32768u) --kj;
+        while (kj > 0 && h.depth_count[kj] > kJumpMaxStates) --kj;
         h.k = kj;
         std::vector<uint32_t> depth_base(h.maxlen + 2, 0);
         for (uint32_t d = 0; d <= h.maxlen; ++d) depth_base[d + 1] = depth_base[d] + h.depth_count[d];
@@ -206,10 +239,13 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                     }
                     s = static_cast<uint32_t>(t);
                 }
-                if (alive)
-                    h.J[w] = static_cast<int16_t>(s - h.base_k);
-                else
-                    h.J[w] = (e >= -32767) ? static_cast<int16_t>(e) : kJumpSlow;
+                if (alive) {
+                    h.J[w] = static_cast<int16_t>(-2 - static_cast<int32_t>(s - h.base_k));
+                } else {
+                    const int32_t v = -e - 2;  // result of the walk
+                    h.J[w] = (v <= 32767) ? static_cast<int16_t>(v) : kJumpSlow;
+                    if (v > 32767) h.jslow = true;
+                }
             }
         }
 

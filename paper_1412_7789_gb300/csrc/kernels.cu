@@ -1,26 +1,35 @@
 // Failureless Aho-Corasick matching kernels for sm_103a.
 //
-// pfac_tiled  -- the production kernel.  One persistent CTA per SM walks the
-//                text tile by tile:
-//   * each tile of T = 16 * blockDim positions plus a halo of max-keyword-length
-//     bytes is bulk-copied (cp.async.bulk, TMA unit, no multicast) into one of
-//     `stages` shared-memory buffers, tracked by an mbarrier per stage, so
-//     several tiles are in flight while one is matched;
-//   * the tile's bytes are mapped to class codes once and packed B bits each;
-//   * every start position resolves its first k characters with ONE lookup in
-//     the root jump table (the top k levels of the goto table flattened,
-//     resident in shared memory for the whole kernel), survivors resolve k2
-//     more with one lookup in the stride table (global, L2-resident), and the
-//     rare walks that go deeper follow the goto table through L1, all walks of
-//     a thread interleaved so their loads overlap;
-//   * output: dense int32 ids (vectorised streaming stores), a count (one
-//     atomic per warp), or the compacted (pos, id) list in ascending order
-//     (block scan + decoupled look-back across tiles).
+// pfac_match -- the production kernel.  Persistent CTAs (one per SM); every
+//   warp owns a private ring of `stages` text buffers in shared memory and
+//   walks warp tiles of 1024 positions independently of the other warps (no
+//   block-wide barrier after start-up):
+//   * a warp tile plus a halo of up to max-keyword-length bytes is fetched with
+//     one bulk async copy (cp.async.bulk, the TMA unit, no multicast) that
+//     completes on the stage's mbarrier, several tiles ahead of use;
+//   * the warp maps the tile's bytes to class codes once, packed B bits each,
+//     with one "cannot extend a walk" bit per position (byte permutes on a
+//     3-bit hash for alphabets of up to 8 keyword bytes, else a byte table);
+//   * each lane takes groups of 4 consecutive positions; one shared-memory
+//     lookup in the root jump table (the top k levels of the goto table
+//     flattened; resident for the whole kernel) gives the result of most
+//     positions outright;
+//   * the positions whose walk is still alive at depth k (or whose window holds
+//     an unknown byte or the text end) go to a per-warp queue and are spread
+//     over all 32 lanes: one lookup in the stride table (k2 more levels,
+//     global, L2-resident), then, rarely, the goto table one character at a
+//     time through L1;
+//   * results are staged per pass in shared memory; output is dense int32 ids
+//     (one bulk async store per pass, or coalesced 16-byte stores at the text
+//     edges), a count (one atomic per warp), or
+//     the compacted (pos, id) list in ascending order (warp scan + decoupled
+//     look-back across half-tiles).
 // pfac_simple -- one thread per position walking the goto table in global
-//                memory: the design of the paper's GPU side (section I, Fig. 3),
-//                kept as the comparison point.
+//   memory: the design of the paper's GPU side (section I, Fig. 3), kept as the
+//   comparison point.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cstdint>
 
 #include "pfac_device.cuh"
@@ -31,82 +40,84 @@ __device__ unsigned int g_dev_error = 0;
 
 namespace {
 
-constexpr int kPPT = 16;          // positions per thread per tile (4 groups of 4)
-constexpr int kMaxStages = 8;
 constexpr int kMaxBlock = 512;
-constexpr uint32_t kHdrBytes = 1024;  // barriers, tile ids, scan scratch, class map
+constexpr int kMaxWarps = kMaxBlock / 32;
+constexpr int kMaxStages = 4;
+constexpr uint32_t kPass = 512;          // positions per pass: 32 lanes x 4 groups x 4
+constexpr uint32_t kTW = 2 * kPass;      // positions per warp tile
+// shared-memory header
+constexpr uint32_t kOffJBar = 0;
+constexpr uint32_t kOffStageBar = 64;                                   // kMaxWarps * kMaxStages * 8
+constexpr uint32_t kOffStageTile = kOffStageBar + kMaxWarps * kMaxStages * 8;
+constexpr uint32_t kOffCls = 1024;                                      // 256 x uint8
+constexpr uint32_t kOffJ = 1280;                                        // root jump table
+constexpr unsigned kFull = 0xffffffffu;
+// per-warp region: [stages][packed codes][cannot-extend bits][pass results][survivor queue]
+constexpr uint32_t kResBytes = kPass * 4;
+constexpr uint32_t kQueueBytes = kPass * 2;
 
-struct TiledParams {
+struct WarpParams {
     const uint8_t *text;
     const uint8_t *gbase;   // text rounded down to 16 bytes
     uint64_t n;
     uint32_t head;          // text - gbase
-    uint32_t T, H, SL, nstages, ntiles;
+    uint32_t SLW;           // staged bytes per warp tile (kTW + halo)
+    uint32_t nstages, ntiles;
     const void *G;
     const int16_t *Jg;
     const int32_t *J2;
-    const int16_t *clsg;
+    const uint8_t *cls8g;
     uint32_t C, W, k, k2, base_k, maxlen, jbytes;
+    int jslow;
+    int hash_shift;          // >= 0: classify with the 3-bit hash
+    uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
     int32_t *out;
     int vec_ok;
     uint32_t *cpos;
     uint32_t *cids;
     unsigned long long cap;
     unsigned long long *count;
-    unsigned long long *status;
-    unsigned int *counter;
-    uint32_t off_J, off_stage, off_packed, off_inv;
+    unsigned long long *status;  // compact: one word per half tile
+    unsigned int *counter;       // compact: next tile to claim
+    uint32_t off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue;
 };
 
-struct Smem {
-    uint64_t *bars;          // [0, nstages): text stages; [kMaxStages]: tables
-    uint32_t *stage_tile;
-    unsigned long long *red; // 34 words: warp partials, block total, tile prefix
-    int16_t *cls;
-    int16_t *J;
-    uint8_t *stages;
+struct WarpSmem {
+    const uint8_t *cls8;
+    const uint8_t *jbase;   // root jump table (byte addressed)
+    uint8_t *st;            // current stage
     uint32_t *packed;
     uint32_t *inv;
+    int32_t *res;
+    uint16_t *queue;
 };
 
-__device__ __forceinline__ Smem carve(uint8_t *smem, const TiledParams &p) {
-    Smem s;
-    s.bars = reinterpret_cast<uint64_t *>(smem);
-    s.stage_tile = reinterpret_cast<uint32_t *>(smem + 128);
-    s.red = reinterpret_cast<unsigned long long *>(smem + 192);
-    s.cls = reinterpret_cast<int16_t *>(smem + 512);
-    s.J = reinterpret_cast<int16_t *>(smem + p.off_J);
-    s.stages = smem + p.off_stage;
-    s.packed = reinterpret_cast<uint32_t *>(smem + p.off_packed);
-    s.inv = reinterpret_cast<uint32_t *>(smem + p.off_inv);
-    return s;
-}
-
-// Thread 0: start the bulk copy of `tile` (or mark the stage as the end).
-__device__ __forceinline__ void issue_stage(const TiledParams &p, const Smem &sm, uint32_t s, uint32_t tile) {
-    sm.stage_tile[s] = tile;
-    uint64_t *bar = &sm.bars[s];
+// Lane 0: start the bulk copy of warp tile `tile` into stage buffer `st`, or
+// mark the stage as the end of this warp's work.
+__device__ __forceinline__ void issue_stage(const WarpParams &p, uint64_t *bar, uint32_t *stile, uint8_t *st,
+                                            uint32_t tile) {
+    *stile = tile;
     if (tile >= p.ntiles) {
         mbar_arrive(bar);
         return;
     }
-    const uint64_t tlo = static_cast<uint64_t>(tile) * p.T;
+    const uint64_t tlo = static_cast<uint64_t>(tile) * kTW;
     const uint64_t a1 = (static_cast<uint64_t>(p.head) + 15ull) & ~15ull;
     const uint64_t a2 = (static_cast<uint64_t>(p.head) + p.n) & ~15ull;
     const uint64_t lo = tlo > a1 ? tlo : a1;
-    const uint64_t hi = (tlo + p.SL) < a2 ? (tlo + p.SL) : a2;
+    const uint64_t hi = (tlo + p.SLW) < a2 ? (tlo + p.SLW) : a2;
     if (a1 < a2 && lo < hi) {
         const uint32_t bytes = static_cast<uint32_t>(hi - lo);
         mbar_arrive_expect_tx(bar, bytes);
-        bulk_load(sm.stages + static_cast<size_t>(s) * p.SL + (lo - tlo), p.gbase + lo, bytes, bar);
+        bulk_load(st + (lo - tlo), p.gbase + lo, bytes, bar);
     } else {
         mbar_arrive(bar);
     }
 }
 
-// Warp 0: the unaligned head and tail bytes of the text that the bulk copy
-// leaves out (at most 15 each).
-__device__ __forceinline__ void load_fringe(const TiledParams &p, uint8_t *st, uint64_t tlo, int lane) {
+// The unaligned head and tail bytes of the text that the bulk copy leaves out
+// (at most 15 each): lanes 0-15 the head, 16-31 the tail.
+__device__ __forceinline__ void load_fringe(const WarpParams &p, uint8_t *st, uint64_t tlo, int lane) {
     const uint64_t head = p.head, end = head + p.n;
     const uint64_t a1 = (head + 15ull) & ~15ull, a2 = end & ~15ull;
     uint64_t lo, hi;
@@ -118,115 +129,158 @@ __device__ __forceinline__ void load_fringe(const TiledParams &p, uint8_t *st, u
         hi = end;
     }
     if (lo < tlo) lo = tlo;
-    if (hi > tlo + p.SL) hi = tlo + p.SL;
+    if (hi > tlo + p.SLW) hi = tlo + p.SLW;
     const uint64_t idx = lo + static_cast<uint64_t>(lane & 15);
     if (idx < hi) st[idx - tlo] = p.gbase[idx];
 }
 
-// Map the staged bytes to class codes (packed B bits per position) and record
-// positions that cannot extend a walk (byte in no keyword, or outside the text).
+__device__ __forceinline__ uint32_t byte_of(uint32_t w, int b) {
+    return __byte_perm(w, 0u, 0x4440u | static_cast<uint32_t>(b));
+}
+
+// Four class-table values (bytes, 0xFF = unknown byte) of the bytes of w, as one word.
+__device__ __forceinline__ uint32_t classify4(const uint8_t *cls8, uint32_t w) {
+    const uint32_t t0 = cls8[byte_of(w, 0)], t1 = cls8[byte_of(w, 1)];
+    const uint32_t t2 = cls8[byte_of(w, 2)], t3 = cls8[byte_of(w, 3)];
+    return __byte_perm(__byte_perm(t0, t1, 0x0040u), __byte_perm(t2, t3, 0x0040u), 0x5410u);
+}
+
+// Map the staged bytes to class codes (B bits each, position order) and set a
+// bit for each position that cannot extend a walk (byte in no keyword, or
+// outside the text).  Returns true when no staged position has that bit.
 template <int B>
-__device__ __forceinline__ void convert_stage(const TiledParams &p, const Smem &sm, uint8_t *st, int64_t gpb,
-                                              int tid, int nt) {
-    uint16_t *inv16 = reinterpret_cast<uint16_t *>(sm.inv);
+__device__ __forceinline__ bool convert_stage(const WarpParams &p, const WarpSmem &w, int64_t gpb, bool interior,
+                                              int lane) {
     const int64_t n = static_cast<int64_t>(p.n);
-    const uint32_t chunks = p.SL / 16;
-    for (uint32_t c = tid; c < chunks; c += nt) {
-        const uint4 v = reinterpret_cast<const uint4 *>(st)[c];
-        const int64_t gp0 = gpb + 16 * static_cast<int64_t>(c);
-        const bool inside = gp0 >= 0 && gp0 + 16 <= n;
-        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        uint32_t ib = 0;
-        uint64_t pk = 0;
-        uint32_t o[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-        for (int b = 0; b < 16; ++b) {
-            const uint32_t byte = (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-            const int cv = sm.cls[byte];
-            const bool valid = cv >= 0 && (inside || (gp0 + b >= 0 && gp0 + b < n));
-            const uint32_t code = valid ? static_cast<uint32_t>(cv) : 0u;
-            ib |= (valid ? 0u : 1u) << b;
-            if (B == 8)
-                o[b >> 2] |= code << (8 * (b & 3));
-            else
-                pk |= static_cast<uint64_t>(code) << (B * b);
-        }
-        if (B == 2) {
-            sm.packed[c] = static_cast<uint32_t>(pk);
-        } else if (B == 4) {
-            sm.packed[2 * c] = static_cast<uint32_t>(pk);
-            sm.packed[2 * c + 1] = static_cast<uint32_t>(pk >> 32);
+    const uint32_t items = p.SLW / 8;
+    uint8_t *inv8 = reinterpret_cast<uint8_t *>(w.inv);
+    uint32_t any = 0;
+    const bool hashed = (B < 8) && p.hash_shift >= 0;
+    for (uint32_t c = lane; c < items; c += 32) {
+        const uint2 v = reinterpret_cast<const uint2 *>(w.st)[c];
+        uint32_t lo, hi, ib;
+        if (hashed) {
+            // per byte h = (byte >> s) & 7 selects, with byte permutes, its code
+            // and the one keyword byte with that hash; a mismatch is an unknown byte
+            const uint32_t sh = static_cast<uint32_t>(p.hash_shift);
+            const uint32_t hl = (v.x >> sh) & 0x07070707u, hh = (v.y >> sh) & 0x07070707u;
+            const uint32_t sl = __byte_perm(hl | (hl >> 4), 0u, 0x4420u);
+            const uint32_t sg = __byte_perm(hh | (hh >> 4), 0u, 0x4420u);
+            lo = __byte_perm(p.hcode_lo, p.hcode_hi, sl);
+            hi = __byte_perm(p.hcode_lo, p.hcode_hi, sg);
+            const uint32_t xl = v.x ^ __byte_perm(p.hbyte_lo, p.hbyte_hi, sl);
+            const uint32_t xh = v.y ^ __byte_perm(p.hbyte_lo, p.hbyte_hi, sg);
+            // bit 7 of each byte of t set iff that byte of x is non-zero
+            const uint32_t tl = ((xl & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | xl;
+            const uint32_t th = ((xh & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | xh;
+            ib = (((tl & 0x80808080u) * 0x00204081u) >> 28) | ((((th & 0x80808080u) * 0x00204081u) >> 28) << 4);
         } else {
-            reinterpret_cast<uint4 *>(st)[c] = make_uint4(o[0], o[1], o[2], o[3]);
+            lo = classify4(w.cls8, v.x);
+            hi = classify4(w.cls8, v.y);
+            // gather one flag per unknown byte (class value 0xFF): bit 7 of each
+            // byte flag, moved to bits 0-3 by one multiply.  Codes below 16 never
+            // have bit 7 set; 8-bit codes compare the whole byte with 0xFF.
+            uint32_t fl = lo, fh = hi;
+            if (B == 8) {
+                fl = __vcmpeq4(lo, 0xFFFFFFFFu);
+                fh = __vcmpeq4(hi, 0xFFFFFFFFu);
+            }
+            ib = (((fl & 0x80808080u) * 0x00204081u) >> 28) | ((((fh & 0x80808080u) * 0x00204081u) >> 28) << 4);
         }
-        inv16[c] = static_cast<uint16_t>(ib);
+        if (!interior) {
+            const int64_t gp0 = gpb + 8 * static_cast<int64_t>(c);
+            if (!(gp0 >= 0 && gp0 + 8 <= n)) {
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    if (gp0 + b < 0 || gp0 + b >= n) ib |= 1u << b;
+            }
+        }
+        any |= ib;
+        if (B == 2) {
+            const uint32_t cl = ((lo & 0x03030303u) * 0x01041040u) >> 24;
+            const uint32_t ch = ((hi & 0x03030303u) * 0x01041040u) >> 24;
+            reinterpret_cast<uint16_t *>(w.packed)[c] = static_cast<uint16_t>(cl | (ch << 8));
+        } else if (B == 4) {
+            uint32_t xl = lo & 0x0F0F0F0Fu, xh = hi & 0x0F0F0F0Fu;
+            xl = (xl | (xl >> 4)) & 0x00FF00FFu;
+            xh = (xh | (xh >> 4)) & 0x00FF00FFu;
+            xl = (xl | (xl >> 8)) & 0xFFFFu;
+            xh = (xh | (xh >> 8)) & 0xFFFFu;
+            w.packed[c] = xl | (xh << 16);
+        } else {
+            reinterpret_cast<uint2 *>(w.st)[c] = make_uint2(lo, hi);
+        }
+        inv8[c] = static_cast<uint8_t>(ib);
+    }
+    return __any_sync(kFull, any != 0) == 0;
+}
+
+// Codes of positions i.. in the low bits (16 codes for B = 2, 8 for B = 4 and
+// B = 8).
+template <int B>
+__device__ __forceinline__ uint64_t code_window(const uint8_t *st, const uint32_t *packed, uint32_t i) {
+    if (B == 8) {
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(st);
+        const uint32_t w = i >> 2, sh = 8u * (i & 3u);
+        const uint32_t a = s32[w], b = s32[w + 1], c = s32[w + 2];
+        return static_cast<uint64_t>(__funnelshift_r(a, b, sh)) |
+               (static_cast<uint64_t>(__funnelshift_r(b, c, sh)) << 32);
+    } else {
+        const uint32_t bo = B * i, w = bo >> 5;
+        return __funnelshift_r(packed[w], packed[w + 1], bo & 31u);
     }
 }
 
-// Code of stage position q, false when q cannot extend a walk.
+__device__ __forceinline__ uint32_t inv_window(const uint32_t *inv, uint32_t i) {
+    const uint32_t w = i >> 5;
+    return __funnelshift_r(inv[w], inv[w + 1], i & 31u);
+}
+
+__device__ __forceinline__ int jump_at(const uint8_t *jbase, uint32_t idx) {
+    return *reinterpret_cast<const int16_t *>(jbase + 2u * idx);
+}
+
+// Code of staged position q; false when q cannot extend a walk.
 template <int B, bool INV>
-__device__ __forceinline__ bool fetch_code(const TiledParams &p, const Smem &sm, const uint8_t *st, int64_t gpb,
-                                           uint32_t q, uint32_t &c) {
-    if (q < p.SL) {
+__device__ __forceinline__ bool fetch_code(const WarpParams &p, const WarpSmem &w, int64_t gpb, uint32_t q,
+                                           uint32_t &c) {
+    if (q < p.SLW) {
         if (INV) {
-            if ((sm.inv[q >> 5] >> (q & 31u)) & 1u) return false;
+            if ((w.inv[q >> 5] >> (q & 31u)) & 1u) return false;
         } else {
             if (gpb + static_cast<int64_t>(q) >= static_cast<int64_t>(p.n)) return false;
         }
         if (B == 8)
-            c = st[q];
+            c = w.st[q];
         else
-            c = (sm.packed[(B * q) >> 5] >> ((B * q) & 31u)) & ((1u << B) - 1u);
+            c = (w.packed[(B * q) >> 5] >> ((B * q) & 31u)) & ((1u << B) - 1u);
         return true;
     }
     const int64_t gp = gpb + static_cast<int64_t>(q);
     if (gp >= static_cast<int64_t>(p.n)) return false;
-    const int v = sm.cls[__ldg(p.text + gp)];
-    if (v < 0) return false;
-    c = static_cast<uint32_t>(v);
+    const uint32_t b = __ldg(p.text + gp);
+    if (!INV) {
+        c = b;
+        return true;
+    }
+    const uint32_t v = w.cls8[b];
+    if (v == 0xFFu) return false;
+    c = v;
     return true;
 }
 
-__device__ __forceinline__ void block_exclusive_scan(unsigned long long v, unsigned long long &excl,
-                                                     unsigned long long &total, unsigned long long *red, int tid,
-                                                     int nt) {
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    unsigned long long inc = v;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += y;
-    }
-    if (lane == 31) red[warp] = inc;
-    __syncthreads();
-    if (warp == 0) {
-        const unsigned long long w = lane < nw ? red[lane] : 0ull;
-        unsigned long long wi = w;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, wi, d);
-            if (lane >= d) wi += y;
-        }
-        if (lane < nw) red[lane] = wi - w;
-        if (lane == nw - 1) red[32] = wi;
-    }
-    __syncthreads();
-    excl = red[warp] + inc - v;
-    total = red[32];
-}
-
-// Thread 0: decoupled look-back over the per-tile status words.  Returns the
-// number of matches in all earlier tiles.
-__device__ __forceinline__ unsigned long long lookback(unsigned long long *status, uint32_t tile,
+// Decoupled look-back over per-unit status words; returns the number of
+// matches in all earlier units.
+__device__ __forceinline__ unsigned long long lookback(unsigned long long *status, uint32_t unit,
                                                        unsigned long long total) {
     constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = (1ull << 62) - 1ull;
-    if (tile == 0) {
+    if (unit == 0) {
         st_relaxed(&status[0], kPre | total);
         return 0ull;
     }
-    st_relaxed(&status[tile], kAgg | total);
+    st_relaxed(&status[unit], kAgg | total);
     unsigned long long excl = 0;
-    int64_t pred = static_cast<int64_t>(tile) - 1;
+    int64_t pred = static_cast<int64_t>(unit) - 1;
     unsigned long long t0 = 0;
     while (pred >= 0) {
         const unsigned long long v = ld_relaxed(&status[pred]);
@@ -236,7 +290,7 @@ __device__ __forceinline__ unsigned long long lookback(unsigned long long *statu
             if (t0 == 0) {
                 t0 = now;
             } else if (now - t0 > kWaitNs) {
-                atomicOr(&g_dev_error, kErrLookback);
+                atomicOr(&g_dev_error, static_cast<unsigned>(kErrLookback));
                 break;
             }
             continue;
@@ -246,258 +300,380 @@ __device__ __forceinline__ unsigned long long lookback(unsigned long long *statu
         --pred;
         t0 = 0;
     }
-    st_relaxed(&status[tile], kPre | (excl + total));
+    st_relaxed(&status[unit], kPre | (excl + total));
     return excl;
 }
 
-template <int B, bool INV, typename GT, int MODE>
-__device__ __forceinline__ void match_tile(const TiledParams &p, const Smem &sm, const uint8_t *st, uint32_t tile,
-                                           int tid, int nt, unsigned long long &cnt) {
-    const GT *G = static_cast<const GT *>(p.G);
+// Finish up to SLOTS * 32 queued survivors (entries base.. of the queue, `avail`
+// of them): each lane takes SLOTS entries and advances their walks together.
+template <int B, bool INV, typename GT, int MODE, int SLOTS>
+__device__ __forceinline__ void finish_survivors(const WarpParams &p, const WarpSmem &w, int64_t gpb, bool interior,
+                                                 bool clean, uint32_t avail, uint32_t h, int lane,
+                                                 unsigned long long &cnt, uint32_t base = 0) {
     const int64_t n = static_cast<int64_t>(p.n);
-    const int64_t gpb = static_cast<int64_t>(tile) * p.T - p.head;  // text index of stage position 0
     const uint32_t k = p.k, k2 = p.k2;
     const uint32_t kmask = (1u << (B * k)) - 1u;
-    const uint32_t kbits = (1u << k) - 1u;
-    const uint32_t k2mask = (1u << (B * k2)) - 1u;
-    const uint32_t k2bits = (1u << k2) - 1u;
-
-    int res[kPPT];
-    int stt[kPPT];       // >= 0: state still walking; -1: done
-    uint32_t q[kPPT];    // stage position of the next character
-    uint64_t x[4];       // codes of the group's window, position i0 in the low bits
-    uint64_t ivx[4];     // "cannot extend" bits of the same window
-
-    // 1. root jump table: first k characters in one shared-memory lookup
+    const GT *G = static_cast<const GT *>(p.G);
+    uint32_t st4[SLOTS], q4[SLOTS], i4[SLOTS];
+    int v4[SLOTS];
+    uint32_t walking = 0, act = 0;
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
-        const uint32_t i0 = 4u * static_cast<uint32_t>(g * nt + tid);
-        if (B == 8) {
-            const uint32_t *s32 = reinterpret_cast<const uint32_t *>(st);
-            x[g] = static_cast<uint64_t>(s32[i0 >> 2]) | (static_cast<uint64_t>(s32[(i0 >> 2) + 1]) << 32);
-        } else {
-            const uint32_t bo = B * i0, w = bo >> 5, sh = bo & 31u;
-            x[g] = (static_cast<uint64_t>(sm.packed[w]) | (static_cast<uint64_t>(sm.packed[w + 1]) << 32)) >> sh;
-        }
-        if (INV) {
-            const uint32_t w = i0 >> 5, sh = i0 & 31u;
-            ivx[g] = (static_cast<uint64_t>(sm.inv[w]) | (static_cast<uint64_t>(sm.inv[w + 1]) << 32)) >> sh;
-        } else {
-            ivx[g] = 0;
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int j = 4 * g + r;
-            const int64_t gp = gpb + i0 + r;
-            res[j] = -1;
-            stt[j] = -1;
-            q[j] = i0 + r;
-            if (gp < 0 || gp >= n) continue;
-            const bool wok = (k > 0) && (INV ? (((ivx[g] >> r) & kbits) == 0) : (gp + k <= n));
-            if (!wok) {
-                stt[j] = 0;
-                continue;
-            }
-            const int e = sm.J[static_cast<uint32_t>(x[g] >> (B * r)) & kmask];
-            if (e >= 0) {
-                stt[j] = static_cast<int>(p.base_k) + e;
-                q[j] += k;
-            } else if (e == kJumpSlow) {
-                stt[j] = 0;
-            } else {
-                res[j] = decode_dead(e);
+    for (int t = 0; t < SLOTS; ++t) {
+        const uint32_t qi = lane + 32u * t;
+        v4[t] = INT_MIN;
+        st4[t] = 0;
+        q4[t] = 0;
+        i4[t] = 0;
+        if (qi < avail) {
+            act |= 1u << t;
+            const uint32_t e16 = w.queue[base + qi];
+            const uint32_t i = e16 & 0x7FFFu;
+            i4[t] = i;
+            q4[t] = i;
+            if (!(e16 >> 15)) {
+                const uint64_t x = code_window<B>(w.st, w.packed, i);
+                const uint32_t off = static_cast<uint32_t>(-jump_at(w.jbase, static_cast<uint32_t>(x) & kmask) - 2);
+                st4[t] = p.base_k + off;
+                q4[t] = i + k;
+                if (k2 > 0) {
+                    bool ok2 = interior || gpb + static_cast<int64_t>(i + k + k2) <= n;
+                    if (INV && !clean) ok2 = ok2 && ((inv_window(w.inv, i + k) & ((1u << k2) - 1u)) == 0);
+                    if (ok2) {
+                        const uint32_t w2 = static_cast<uint32_t>(x >> (B * k)) & ((1u << (B * k2)) - 1u);
+                        v4[t] = __ldg(p.J2 + ((static_cast<uint64_t>(off) << (B * k2)) | w2));
+                    }
+                }
             }
         }
     }
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if ((act >> t) & 1u) {
+            if (v4[t] == INT_MIN) {
+                walking |= 1u << t;
+            } else if (v4[t] < 0) {
+                v4[t] = decode_dead(v4[t]);
+            } else {
+                st4[t] = static_cast<uint32_t>(v4[t]);
+                q4[t] += k2;
+                v4[t] = INT_MIN;
+                walking |= 1u << t;
+            }
+        }
+    }
+    for (uint32_t step = 0; walking; ++step) {
+        if (step > p.maxlen + 1) {  // impossible for a well-formed table
+            atomicOr(&g_dev_error, static_cast<unsigned>(kErrWalk));
+#pragma unroll
+            for (int t = 0; t < SLOTS; ++t)
+                if ((walking >> t) & 1u) v4[t] = -1;
+            break;
+        }
+        int e4[SLOTS];
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            if ((walking >> t) & 1u) {
+                uint32_t c = 0;
+                const bool okc = fetch_code<B, INV>(p, w, gpb, q4[t], c);
+                // an unknown byte or the text end reads the row's end column,
+                // which always holds the result of stopping there
+                e4[t] = goto_ld(G, st4[t], p.W, okc ? c : p.C);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            if ((walking >> t) & 1u) {
+                if (e4[t] < 0) {
+                    v4[t] = decode_dead(e4[t]);
+                    walking &= ~(1u << t);
+                } else {
+                    st4[t] = static_cast<uint32_t>(e4[t]);
+                    q4[t] += 1;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if ((act >> t) & 1u) {
+            if (MODE == OUT_COUNT)
+                cnt += v4[t] >= 0 ? 1ull : 0ull;
+            else
+                w.res[i4[t] - h * kPass] = v4[t];
+        }
+    }
+}
 
-    // 2. stride table: k2 more characters for the starts still alive at depth k
-    if (k2 > 0) {
+// Flags describing a warp tile.
+enum : uint32_t { kInterior = 1u, kClean = 2u };
+
+template <int B, bool INV, typename GT, int MODE>
+__device__ __forceinline__ void match_pass(const WarpParams &p, const WarpSmem &w, int64_t gpb, uint32_t flags,
+                                           uint32_t tile, uint32_t h, int lane, unsigned long long &cnt) {
+    const int64_t n = static_cast<int64_t>(p.n);
+    const uint32_t k = p.k;
+    const uint32_t kmask = (1u << (B * k)) - 1u;
+    const bool interior = flags & kInterior;
+    const bool clean = !INV || (flags & kClean);
+    const uint32_t ibase = h * kPass + 4u * static_cast<uint32_t>(lane);
+
+    // 1. one root-jump lookup per position: the result, or (<= -2) a walk that
+    //    continues past depth k, or kJumpSlow
+    int res[16];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const uint64_t x = code_window<B>(w.st, w.packed, ibase + 128u * g);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) res[4 * g + r] = jump_at(w.jbase, static_cast<uint32_t>(x >> (B * r)) & kmask);
+    }
+    uint32_t valid = 0xFFFFu;
+    const bool fixups = !interior || !clean || k == 0;
+    if (fixups) {
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            const uint32_t i0 = 4u * static_cast<uint32_t>(g * nt + tid);
+            const uint32_t i0 = ibase + 128u * g;
+            uint32_t wi = 0;
+            if (INV) wi = inv_window(w.inv, i0);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int j = 4 * g + r;
-                if (stt[j] > 0) {
-                    const int64_t gp = gpb + i0 + r;
-                    const bool wok =
-                        INV ? (((ivx[g] >> (r + k)) & k2bits) == 0) : (gp + static_cast<int64_t>(k + k2) <= n);
-                    if (wok) {
-                        const uint32_t row = static_cast<uint32_t>(stt[j]) - p.base_k;
-                        const uint32_t w2 = static_cast<uint32_t>(x[g] >> (B * (r + k))) & k2mask;
-                        const int e2 = __ldg(p.J2 + ((static_cast<uint64_t>(row) << (B * k2)) | w2));
-                        if (e2 >= 0) {
-                            stt[j] = e2;
-                            q[j] += k2;
-                        } else {
-                            res[j] = decode_dead(e2);
-                            stt[j] = -1;
-                        }
-                    }
+                const int64_t gp = gpb + i0 + r;
+                if (gp < 0 || gp >= n) {
+                    res[j] = -1;
+                    valid &= ~(1u << j);
+                } else if (k == 0 || gp + static_cast<int64_t>(k) > n || ((wi >> r) & ((1u << k) - 1u))) {
+                    res[j] = kJumpSlow;
                 }
             }
         }
+    }
+    uint32_t sv = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sv |= (res[j] < -1 ? 1u : 0u) << j;
+    uint32_t slowm = 0;
+    if (fixups || p.jslow) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) slowm |= (res[j] == kJumpSlow ? 1u : 0u) << j;
     }
 
-    // 3. deeper walks through the goto table, all of this thread's walks
-    //    advanced together one character per round
-    bool active = false;
+    // 2. survivors into the warp's queue (position, slow flag), in lane order
+    const uint32_t c = __popc(sv);
+    uint32_t inc = c;
 #pragma unroll
-    for (int j = 0; j < kPPT; ++j) active |= stt[j] >= 0;
-    for (uint32_t round = 0; __any_sync(0xffffffffu, active); ++round) {
-        if (round > p.maxlen + 1) {  // impossible for a well-formed table
-            if (active) atomicOr(&g_dev_error, static_cast<unsigned>(kErrWalk));
-#pragma unroll
-            for (int j = 0; j < kPPT; ++j)
-                if (stt[j] >= 0) stt[j] = -1;
-            break;
-        }
-        active = false;
-#pragma unroll
-        for (int j = 0; j < kPPT; ++j) {
-            if (stt[j] >= 0) {
-                const uint32_t s = static_cast<uint32_t>(stt[j]);
-                uint32_t c = 0;
-                if (!fetch_code<B, INV>(p, sm, st, gpb, q[j], c)) {
-                    res[j] = decode_dead(goto_ld(G, s, p.W, p.C));
-                    stt[j] = -1;
-                } else {
-                    const int t = goto_ld(G, s, p.W, c);
-                    if (t < 0) {
-                        res[j] = decode_dead(t);
-                        stt[j] = -1;
-                    } else {
-                        stt[j] = t;
-                        q[j] += 1;
-                        active = true;
-                    }
-                }
-            }
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, inc, 31);
+    {
+        uint32_t o = inc - c, m = sv;
+        while (m) {
+            const uint32_t j = __ffs(m) - 1;
+            m &= m - 1;
+            const uint32_t i = ibase + ((j >> 2) << 7) + (j & 3u);
+            w.queue[o++] = static_cast<uint16_t>(i | (((slowm >> j) & 1u) << 15));
         }
     }
+    if (MODE == OUT_COUNT) {
+        uint32_t hit = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) hit |= (res[j] >= 0 ? 1u : 0u) << j;
+        cnt += __popc(hit & valid);
+    } else {
+        if (MODE == OUT_DENSE) {
+            // the previous pass's bulk store must have read the staging buffer
+            if (lane == 0) bulk_wait_read();
+            __syncwarp();
+        }
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+            reinterpret_cast<int4 *>(w.res)[32 * g + lane] =
+                make_int4(res[4 * g], res[4 * g + 1], res[4 * g + 2], res[4 * g + 3]);
+    }
+    __syncwarp();
+
+    // 3. the survivors, spread over the lanes (several per lane at a time so
+    //    their dependent loads overlap): stride table, then (rarely) the goto
+    //    table one character at a time
+    if (total <= 64) {
+        finish_survivors<B, INV, GT, MODE, 2>(p, w, gpb, interior, clean, total, h, lane, cnt);
+    } else {
+        for (uint32_t base = 0; base < total; base += 128)
+            finish_survivors<B, INV, GT, MODE, 4>(p, w, gpb, interior, clean, total - base, h, lane, cnt,
+                                                  base);
+    }
+    __syncwarp();
 
     // 4. output
-    if (MODE == OUT_DENSE) {
+    if (MODE == OUT_DENSE && interior && p.vec_ok) {
+        // the whole pass is inside the text: one bulk store of the staged ids
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+            bulk_store(p.out + gpb + h * kPass, w.res, kResBytes);
+            bulk_commit();
+        }
+    } else if (MODE == OUT_DENSE) {
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            const uint32_t i0 = 4u * static_cast<uint32_t>(g * nt + tid);
-            const int64_t gp0 = gpb + i0;
-            if (p.vec_ok && gp0 >= 0 && gp0 + 4 <= n) {
-                __stcs(reinterpret_cast<int4 *>(p.out + gp0),
-                       make_int4(res[4 * g], res[4 * g + 1], res[4 * g + 2], res[4 * g + 3]));
+            const int4 r4 = reinterpret_cast<const int4 *>(w.res)[32 * g + lane];
+            const int64_t gp0 = gpb + ibase + 128u * g;
+            if (p.vec_ok && ((valid >> (4 * g)) & 0xFu) == 0xFu) {
+                __stcs(reinterpret_cast<int4 *>(p.out + gp0), r4);
             } else {
+                const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int64_t gp = gp0 + r;
-                    if (gp >= 0 && gp < n) p.out[gp] = res[4 * g + r];
-                }
+                for (int r = 0; r < 4; ++r)
+                    if ((valid >> (4 * g + r)) & 1u) p.out[gp0 + r] = rr[r];
             }
         }
-    } else if (MODE == OUT_COUNT) {
-#pragma unroll
-        for (int j = 0; j < kPPT; ++j) cnt += res[j] >= 0 ? 1ull : 0ull;
-    } else {
-        unsigned long long mine = 0;
+    } else if (MODE == OUT_COMPACT) {
+        int rr[16];
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            unsigned long long c = 0;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) c += res[4 * g + r] >= 0 ? 1ull : 0ull;
-            mine |= c << (16 * g);
+            const int4 r4 = reinterpret_cast<const int4 *>(w.res)[32 * g + lane];
+            rr[4 * g] = r4.x;
+            rr[4 * g + 1] = r4.y;
+            rr[4 * g + 2] = r4.z;
+            rr[4 * g + 3] = r4.w;
         }
-        unsigned long long excl, total;
-        block_exclusive_scan(mine, excl, total, sm.red, tid, nt);
-        const unsigned long long tile_total =
-            (total & 0xFFFFull) + ((total >> 16) & 0xFFFFull) + ((total >> 32) & 0xFFFFull) + (total >> 48);
-        if (tid == 0) {
-            const unsigned long long pre = lookback(p.status, tile, tile_total);
-            sm.red[33] = pre;
-            if (tile == p.ntiles - 1) *p.count = pre + tile_total;
-        }
-        __syncthreads();
-        unsigned long long off = sm.red[33];
+        uint32_t mine = 0;  // 4 fields of 8 bits: matches per group (<= 4)
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
-            const uint32_t i0 = 4u * static_cast<uint32_t>(g * nt + tid);
-            unsigned long long o = off + ((excl >> (16 * g)) & 0xFFFFull);
+            uint32_t cg = 0;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) cg += ((valid >> (4 * g + r)) & 1u) && rr[4 * g + r] >= 0 ? 1u : 0u;
+            mine |= cg << (8 * g);
+        }
+        uint32_t sc = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, sc, d);
+            if (lane >= d) sc += y;
+        }
+        const uint32_t tot = __shfl_sync(kFull, sc, 31);  // fields <= 128: no carries
+        const uint32_t excl = sc - mine;
+        const unsigned long long unit_total =
+            (tot & 0xFFu) + ((tot >> 8) & 0xFFu) + ((tot >> 16) & 0xFFu) + (tot >> 24);
+        unsigned long long pre = 0;
+        const uint32_t unit = 2u * tile + h;
+        if (lane == 0) {
+            pre = lookback(p.status, unit, unit_total);
+            if (unit == 2u * p.ntiles - 1u) *p.count = pre + unit_total;
+        }
+        pre = __shfl_sync(kFull, pre, 0);
+        unsigned long long base = pre;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const uint32_t i0 = ibase + 128u * g;
+            unsigned long long o = base + ((excl >> (8 * g)) & 0xFFu);
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                if (res[4 * g + r] >= 0) {
+                if (((valid >> (4 * g + r)) & 1u) && rr[4 * g + r] >= 0) {
                     if (o < p.cap) {
                         p.cpos[o] = static_cast<uint32_t>(gpb + i0 + r);
-                        p.cids[o] = static_cast<uint32_t>(res[4 * g + r]);
+                        p.cids[o] = static_cast<uint32_t>(rr[4 * g + r]);
                     }
                     ++o;
                 }
             }
-            off += (total >> (16 * g)) & 0xFFFFull;
+            base += (tot >> (8 * g)) & 0xFFu;
         }
     }
+    __syncwarp();
 }
 
 template <int B, bool INV, typename GT, int MODE>
-__global__ void __launch_bounds__(kMaxBlock, 1) pfac_tiled(const TiledParams p) {
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_match(const WarpParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
-    const Smem sm = carve(smem, p);
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
+    uint32_t *stile = reinterpret_cast<uint32_t *>(smem + kOffStageTile) + warp * kMaxStages;
+    uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
+    WarpSmem w;
+    w.cls8 = smem + kOffCls;
+    w.jbase = smem + kOffJ;
+    w.st = wreg;
+    w.packed = reinterpret_cast<uint32_t *>(wreg + p.off_packed);
+    w.inv = reinterpret_cast<uint32_t *>(wreg + p.off_inv);
+    w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
+    w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
     const uint32_t nst = p.nstages;
 
-    if (tid == 0) {
-        for (uint32_t s = 0; s < nst; ++s) mbar_init(&sm.bars[s], 1);
-        mbar_init(&sm.bars[kMaxStages], 1);
+    if (threadIdx.x == 0) {
+        mbar_init(jbar, 1);
+        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
+        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(jbar, 256u + p.jbytes);
+        bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
+        if (p.jbytes) bulk_load(smem + kOffJ, p.Jg, p.jbytes, jbar);
+    }
+    // consecutive tiles go to different SMs (warp-major, CTA-minor numbering)
+    const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
+    // Tiles are claimed from a global counter, so a warp that meets an
+    // expensive tile (long walks) stops taking work while the others go on.
+    // The compacted output claims every tile (ordered look-back needs tiles
+    // handed out in increasing order to running warps); the other outputs
+    // hand each warp its first tile statically and claim the rest.
     auto next_tile = [&](uint32_t it) -> uint32_t {
         if (MODE == OUT_COMPACT) return atomicAdd(p.counter, 1u);
-        const uint64_t t = static_cast<uint64_t>(blockIdx.x) + static_cast<uint64_t>(it) * gridDim.x;
+        if (it == 0) return gw < p.ntiles ? static_cast<uint32_t>(gw) : 0xFFFFFFFFu;
+        const uint64_t t = GW + atomicAdd(p.counter, 1u);
         return t < p.ntiles ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
     };
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&sm.bars[kMaxStages], 512u + p.jbytes);
-        bulk_load(sm.cls, p.clsg, 512u, &sm.bars[kMaxStages]);
-        if (p.jbytes) bulk_load(sm.J, p.Jg, p.jbytes, &sm.bars[kMaxStages]);
-        for (uint32_t s = 0; s < nst; ++s) issue_stage(p, sm, s, next_tile(s));
-    }
+    if (lane == 0)
+        for (uint32_t s = 0; s < nst; ++s) issue_stage(p, &bars[s], &stile[s], wreg + s * p.SLW, next_tile(s));
 
     unsigned long long cnt = 0;
-    bool ok = mbar_wait(&sm.bars[kMaxStages], 0);
-    uint32_t it = 0;
-    for (;; ++it) {
+    bool ok = mbar_wait(jbar, 0);
+    for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % nst;
-        ok = ok && mbar_wait(&sm.bars[s], (it / nst) & 1u);
-        if (!__syncthreads_and(ok)) {
-            // A copy never completed: latch the error, let the copies this CTA
-            // still has in flight finish (bounded), and leave.
-            if (tid == 0) {
+        ok = ok && mbar_wait(&bars[s], (it / nst) & 1u);
+        if (!__all_sync(kFull, ok)) {
+            // A copy never completed: latch the error, let this warp's copies in
+            // flight finish (bounded), and leave.
+            if (lane == 0) {
+                bulk_wait_all();
                 atomicOr(&g_dev_error, static_cast<unsigned>(kErrTimeout));
-                mbar_wait(&sm.bars[kMaxStages], 0);
-                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&sm.bars[j % nst], (j / nst) & 1u);
+                mbar_wait(jbar, 0);
+                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u);
             }
             return;
         }
-        const uint32_t tile = sm.stage_tile[s];
+        const uint32_t tile = stile[s];
         if (tile >= p.ntiles) break;
-        uint8_t *st = sm.stages + static_cast<size_t>(s) * p.SL;
-        const uint64_t tlo = static_cast<uint64_t>(tile) * p.T;
-        if (tid < 32) load_fringe(p, st, tlo, tid);
-        __syncthreads();
-        if (B < 8 || INV) {
-            convert_stage<B>(p, sm, st, static_cast<int64_t>(tlo) - p.head, tid, nt);
-            __syncthreads();
+        w.st = wreg + s * p.SLW;
+        const uint64_t tlo = static_cast<uint64_t>(tile) * kTW;
+        const int64_t gpb = static_cast<int64_t>(tlo) - p.head;
+        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.SLW) <= static_cast<int64_t>(p.n);
+        if (!interior) {
+            load_fringe(p, w.st, tlo, lane);
+            __syncwarp();
         }
-        match_tile<B, INV, GT, MODE>(p, sm, st, tile, tid, nt, cnt);
-        __syncthreads();
-        if (tid == 0) {
+        uint32_t flags = interior ? kInterior : 0u;
+        if (B < 8 || INV) {
+            if (convert_stage<B>(p, w, gpb, interior, lane)) flags |= kClean;
+            __syncwarp();
+        }
+#pragma unroll 1
+        for (uint32_t h = 0; h < kTW / kPass; ++h) match_pass<B, INV, GT, MODE>(p, w, gpb, flags, tile, h, lane, cnt);
+        if (lane == 0) {
             fence_proxy_async_smem();
-            issue_stage(p, sm, s, next_tile(it + nst));
+            issue_stage(p, &bars[s], &stile[s], w.st, next_tile(it + nst));
         }
     }
 
+    if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
     if (MODE == OUT_COUNT) {
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
-        if ((tid & 31) == 0 && cnt) atomicAdd(p.count, cnt);
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
+        if (lane == 0 && cnt) atomicAdd(p.count, cnt);
     }
 }
 
@@ -538,54 +714,54 @@ __global__ void __launch_bounds__(256) pfac_simple(const uint8_t *__restrict__ t
 inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
 
 struct Geometry {
-    uint32_t T, H, SL, nstages, ntiles, off_J, off_stage, off_packed, off_inv, smem;
+    uint32_t SLW, nstages, ntiles, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue, smem;
 };
 
 bool make_geometry(const DevTables &t, uint64_t n, uint32_t head, const Tuning &tu, int max_smem, Geometry *g) {
-    const uint32_t nt = static_cast<uint32_t>(tu.block);
-    g->T = nt * kPPT;
+    const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
     uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
-    if (H < t.k + t.k2 + 4) H = t.k + t.k2 + 4;
-    g->H = align16(H);
-    g->SL = g->T + g->H;
-    const uint64_t span = n + head;
-    const uint64_t nt64 = (span + g->T - 1) / g->T;
-    if (nt64 >= 0xFFFFFFFFull) return false;
-    g->ntiles = static_cast<uint32_t>(nt64);
+    if (H < t.k + t.k2 + 8) H = t.k + t.k2 + 8;
+    H = align16(H);
+    g->SLW = kTW + H;
+    const uint64_t tiles = (n + head + kTW - 1) / kTW;
+    if (tiles >= 0x7FFFFFFFull) return false;
+    g->ntiles = static_cast<uint32_t>(tiles);
     const bool inv = t.B < 8 || t.C < 256;
-    const uint32_t packed_bytes = t.B < 8 ? align16(g->SL * t.B / 8 + 16) : 0u;
-    const uint32_t inv_bytes = inv ? align16(g->SL / 8 + 16) : 0u;
+    const uint32_t packed_bytes = t.B < 8 ? align16(g->SLW * t.B / 8 + 16) : 0u;
+    const uint32_t inv_bytes = inv ? align16(g->SLW / 8 + 16) : 0u;
     for (int st = tu.stages; st >= 2; --st) {
         g->nstages = static_cast<uint32_t>(st);
-        g->off_J = kHdrBytes;
-        g->off_stage = align16(g->off_J + t.jbytes);
-        g->off_packed = align16(g->off_stage + g->nstages * g->SL);
+        g->off_packed = g->nstages * g->SLW;
         g->off_inv = align16(g->off_packed + packed_bytes);
-        g->smem = align16(g->off_inv + inv_bytes);
+        g->off_res = align16(g->off_inv + inv_bytes);
+        g->off_queue = g->off_res + kResBytes;
+        g->warp_bytes = align16(g->off_queue + kQueueBytes);
+        g->off_warp = align16(kOffJ + t.jbytes);
+        g->smem = g->off_warp + nw * g->warp_bytes;
         if (static_cast<int>(g->smem) <= max_smem) return true;
     }
     return false;
 }
 
 template <int B, bool INV, typename GT, int MODE>
-cudaError_t launch_one(const TiledParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
+cudaError_t launch_one(const WarpParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
                        cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!configured[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(pfac_tiled<B, INV, GT, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(pfac_match<B, INV, GT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
-    pfac_tiled<B, INV, GT, MODE><<<grid, block, smem, stream>>>(p);
+    pfac_match<B, INV, GT, MODE><<<grid, block, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
 template <int B, bool INV, typename GT>
-cudaError_t launch_modes(OutMode mode, const TiledParams &p, uint32_t grid, uint32_t block, uint32_t smem,
+cudaError_t launch_modes(OutMode mode, const WarpParams &p, uint32_t grid, uint32_t block, uint32_t smem,
                          int max_smem, cudaStream_t stream) {
     switch (mode) {
         case OUT_DENSE:
@@ -598,7 +774,7 @@ cudaError_t launch_modes(OutMode mode, const TiledParams &p, uint32_t grid, uint
 }
 
 template <typename GT>
-cudaError_t launch_gt(const DevTables &t, OutMode mode, const TiledParams &p, uint32_t grid, uint32_t block,
+cudaError_t launch_gt(const DevTables &t, OutMode mode, const WarpParams &p, uint32_t grid, uint32_t block,
                       uint32_t smem, int max_smem, cudaStream_t stream) {
     if (t.B == 2) return launch_modes<2, true, GT>(mode, p, grid, block, smem, max_smem, stream);
     if (t.B == 4) return launch_modes<4, true, GT>(mode, p, grid, block, smem, max_smem, stream);
@@ -631,11 +807,12 @@ cudaError_t device_props(DeviceProps *out) {
 
 }  // namespace
 
-size_t compact_scratch_bytes(const DevTables &t, uint64_t n, const Tuning &tu) {
-    const uint64_t T = static_cast<uint64_t>(tu.block) * kPPT;
-    const uint64_t tiles = (n + 15 + T - 1) / T;
+size_t scratch_bytes(const DevTables &t, uint64_t n, OutMode mode, const Tuning &tu) {
     (void)t;
-    return static_cast<size_t>(16 + 8 * (tiles + 1));
+    (void)tu;
+    if (mode != OUT_COMPACT) return 16;
+    const uint64_t tiles = (n + 15 + kTW - 1) / kTW;
+    return static_cast<size_t>(16 + 8 * (2 * tiles + 2));
 }
 
 cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
@@ -645,26 +822,26 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     DeviceProps dp;
     cudaError_t e = device_props(&dp);
     if (e != cudaSuccess) return e;
-    TiledParams p{};
+    WarpParams p{};
     p.text = r.text;
     p.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(r.text) & 15u);
     p.gbase = r.text - p.head;
     p.n = r.n;
     Geometry g;
     if (!make_geometry(t, r.n, p.head, tu, dp.max_smem, &g)) return cudaErrorInvalidConfiguration;
-    p.T = g.T;
-    p.H = g.H;
-    p.SL = g.SL;
+    p.SLW = g.SLW;
     p.nstages = g.nstages;
     p.ntiles = g.ntiles;
-    p.off_J = g.off_J;
-    p.off_stage = g.off_stage;
+    p.off_warp = g.off_warp;
+    p.warp_bytes = g.warp_bytes;
     p.off_packed = g.off_packed;
     p.off_inv = g.off_inv;
+    p.off_res = g.off_res;
+    p.off_queue = g.off_queue;
     p.G = t.G;
     p.Jg = t.J;
     p.J2 = t.J2;
-    p.clsg = t.cls;
+    p.cls8g = t.cls8;
     p.C = t.C;
     p.W = t.W;
     p.k = t.k;
@@ -672,20 +849,27 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     p.base_k = t.base_k;
     p.maxlen = t.maxlen;
     p.jbytes = t.jbytes;
+    p.jslow = t.jslow ? 1 : 0;
+    p.hash_shift = t.hash_shift;
+    p.hcode_lo = t.hash_code[0];
+    p.hcode_hi = t.hash_code[1];
+    p.hbyte_lo = t.hash_byte[0];
+    p.hbyte_hi = t.hash_byte[1];
     p.out = r.out;
     p.vec_ok = ((reinterpret_cast<uintptr_t>(r.out) - 4u * p.head) & 15u) == 0;
     p.cpos = r.pos;
     p.cids = r.ids;
     p.cap = r.cap;
     p.count = r.count;
-    if (mode == OUT_COMPACT) {
-        if (!r.scratch || r.scratch_bytes < 16 + 8 * (static_cast<size_t>(g.ntiles) + 1))
-            return cudaErrorInvalidValue;
-        p.counter = static_cast<unsigned int *>(r.scratch);
+    const size_t need_scratch = mode == OUT_COMPACT ? 16 + 8 * (2 * static_cast<size_t>(g.ntiles) + 2) : 16;
+    if (!r.scratch || r.scratch_bytes < need_scratch) return cudaErrorInvalidValue;
+    p.counter = static_cast<unsigned int *>(r.scratch);
+    if (mode == OUT_COMPACT)
         p.status = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(r.scratch) + 16);
-    }
+    const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
     uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(dp.sms);
-    if (grid > g.ntiles) grid = g.ntiles;
+    const uint32_t need = (g.ntiles + nw - 1) / nw;
+    if (grid > need) grid = need;
     if (grid == 0) return cudaSuccess;
     if (t.gbits == 16)
         return launch_gt<int16_t>(t, mode, p, grid, static_cast<uint32_t>(tu.block), g.smem, dp.max_smem, stream);

@@ -14,12 +14,15 @@ namespace pfac {
 // (the root, state 0, is never a child).
 inline int32_t encode_dead(int32_t id) { return -(id + 2); }
 
-// Jump-table entries are int16; this value sends a start to the plain walk
-// (used when a result does not fit in 15 bits).
+// Root jump-table entries are int16: a result (>= -1) when the walk stops
+// within the window, -(2 + r) for the r-th state at depth k when it is still
+// alive there (r < kJumpMaxStates), or kJumpSlow to send the start to the
+// plain walk (a result that does not fit 15 bits).
 constexpr int16_t kJumpSlow = -32768;
+constexpr uint32_t kJumpMaxStates = 32766;
 
 // Longest halo staged in shared memory; walks that run past it read global memory.
-constexpr uint32_t kHaloCap = 1024;
+constexpr uint32_t kHaloCap = 256;
 
 struct BuildOptions {
     int index_width = 0;        // 0 = auto, 16, 32
@@ -42,6 +45,15 @@ struct HostTables {
     uint32_t count_k = 0;    // states at depth k
     uint32_t minlen = 0, maxlen = 0;
     std::vector<int16_t> cls;        // 256: byte -> code or -1
+    std::vector<uint8_t> cls8;       // 256: byte -> code, 0xFF = in no keyword (identity when C = 256)
+    bool jslow = false;              // some jump entry is kJumpSlow
+    // Small alphabets (at most 8 keyword bytes): a shift s such that
+    // (byte >> s) & 7 differs for every keyword byte, or -1.  hash_code[h] is
+    // the class code of the keyword byte with hash h, hash_byte[h] that byte
+    // (or a byte whose hash is not h, for unused h).
+    int hash_shift = -1;
+    uint8_t hash_code[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint8_t hash_byte[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<uint8_t> G;          // S * W entries of gbits
     std::vector<int16_t> J;          // 2^(B*k) (padded to 8 entries)
     std::vector<int32_t> J2;         // count_k << (B*k2)
@@ -53,8 +65,9 @@ struct HostTables {
 int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t k,
                  const BuildOptions &opt, HostTables *out);
 
-// Largest k + k2 the kernel's 64-bit code window allows for a code width.
-inline uint32_t window_limit(uint32_t B) { return B == 2 ? 17u : (B == 4 ? 9u : 5u); }
+// Largest k + k2 the kernel's code window allows for a code width (one 32-bit
+// window of 2- or 4-bit codes, one 64-bit window of 8-bit codes).
+inline uint32_t window_limit(uint32_t B) { return B == 2 ? 16u : 8u; }
 
 // Device view of a compiled automaton.
 struct DevTables {
@@ -62,8 +75,13 @@ struct DevTables {
     const int16_t *J = nullptr;      // root jump table (device copy, for the bulk load)
     const int32_t *J2 = nullptr;     // stride table
     const int16_t *cls = nullptr;    // class map (256 entries)
+    const uint8_t *cls8 = nullptr;   // byte class map (256 entries, 0xFF = unknown byte)
     uint32_t S = 0, C = 0, W = 0, gbits = 32, B = 8, k = 0, k2 = 0, base_k = 0, maxlen = 0;
     uint32_t jbytes = 0;             // bytes of J (multiple of 16)
+    bool jslow = false;
+    int hash_shift = -1;             // see HostTables
+    uint32_t hash_code[2] = {0, 0};  // hash_code bytes, little-endian
+    uint32_t hash_byte[2] = {0, 0};
 };
 
 enum OutMode : int { OUT_DENSE = 0, OUT_COUNT = 1, OUT_COMPACT = 2 };
@@ -76,18 +94,19 @@ struct MatchRequest {
     uint32_t *pos = nullptr;                 // compact
     uint32_t *ids = nullptr;                 // compact
     uint64_t cap = 0;                        // compact
-    void *scratch = nullptr;                 // compact: counter + per-tile status
+    void *scratch = nullptr;                 // zeroed: tile counter (+ compact: per-unit status)
     size_t scratch_bytes = 0;
 };
 
 struct Tuning {
     int block = 512;      // threads per CTA (multiple of 32, <= 512)
-    int stages = 4;       // text stages in flight per CTA
+    int stages = 2;       // text stages in flight per warp (2..4; fewer if shared memory is short)
     int grid = 0;         // 0 = one CTA per SM
 };
 
-// Scratch bytes the compact kernel needs for a text of n bytes.
-size_t compact_scratch_bytes(const DevTables &t, uint64_t n, const Tuning &tu);
+// Zeroed device scratch a tiled launch needs: the tile counter, plus the
+// per-unit look-back words of the compacted output.
+size_t scratch_bytes(const DevTables &t, uint64_t n, OutMode mode, const Tuning &tu);
 
 cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode,
                          const Tuning &tu, cudaStream_t stream);

@@ -146,3 +146,23 @@ def test_builder_jump_and_stride_shapes(lib):
     info = api.ac_info(h)
     api.ac_destroy(h)
     assert info["stride_depth"] == 0 and info["jump_depth"] == 2
+
+
+@pytest.mark.parametrize("alphabet,shift,bits", [
+    (b"ACGT", 0, 2),
+    (bytes([0x00, 0x01, 0x80, 0x81]), -1, 2),
+    (b"abcdefg", 0, 4),
+    (bytes([0x00, 0x08, 0x10, 0x18]), 2, 2),  # the smallest shift that separates them
+    (bytes([0x00, 0x01, 0x02, 0x80, 0x81]), -1, 4),
+    (b"abcdefghij", -1, 4),
+])
+def test_class_hash_choice(lib, alphabet, shift, bits):
+    """Alphabets of at most 8 keyword bytes get a 3-bit hash (byte >> s) & 7
+    that separates them, when one exists; the hash must be injective."""
+    pats = [bytes([b]) * 3 for b in alphabet]
+    h = api.ac_compile(pats, host_only=True)
+    info = api.ac_info(h)
+    api.ac_destroy(h)
+    assert info["class_hash_shift"] == shift and info["code_bits"] == bits
+    if shift >= 0:
+        assert len({(b >> shift) & 7 for b in alphabet}) == len(alphabet)

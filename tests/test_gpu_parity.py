@@ -59,11 +59,15 @@ def test_single_text_acgt_1mib():
 
 SIZES = [0, 1, 15, 16, 17, 63, 8191, 8192, 8193, 3 * 8192 + 77, 100_003]
 ALPHABETS = {
-    "ab": b"ab",                      # 2 classes   -> 2-bit codes
-    "acgt": b"ACGT",                  # 4 classes   -> 2-bit codes
-    "ten": b"abcdefghij",             # 10 classes  -> 4-bit codes
-    "forty": bytes(range(40, 80)),    # 40 classes  -> 8-bit codes, unknown bytes possible
-    "bytes": bytes(range(256)),       # 256 classes -> raw bytes
+    "ab": b"ab",                              # 2 classes   -> 2-bit codes, hashed
+    "acgt": b"ACGT",                          # 4 classes   -> 2-bit codes, hashed
+    "nohash4": bytes([0x00, 0x01, 0x80, 0x81]),  # 2-bit codes, class table
+    "seven": b"abcdefg",                      # 7 classes   -> 4-bit codes, hashed
+    "nohash5": bytes([0x00, 0x01, 0x02, 0x80, 0x81]),  # 4-bit codes, class table
+    "ten": b"abcdefghij",                     # 10 classes  -> 4-bit codes, class table
+    "forty": bytes(range(40, 80)),            # 40 classes  -> 8-bit codes, unknown bytes possible
+    "many": bytes(range(0, 250)),             # 250 classes -> 8-bit codes above 127
+    "bytes": bytes(range(256)),               # 256 classes -> raw bytes
 }
 
 
