@@ -67,7 +67,9 @@ typedef enum {
  *   host_only      1 = build the host tables only; the handle can be inspected
  *                  (ac_info, ac_export_tables) but match calls refuse it.
  *                  Needs no GPU.
- *   jump_bytes     shared-memory budget of the root jump table (0 = 128 KiB).
+ *   jump_bytes     shared-memory budget of the first-level table: the root filter
+ *                  (alphabets of at most 16 keyword bytes) or the root jump
+ *                  table (larger alphabets); 0 = 128 KiB.
  *   stride_bytes   device budget of the second-level stride table (0 = 16 MiB;
  *                  set 1 to disable it).
  *   dev_alloc / dev_free / alloc_ctx

@@ -91,7 +91,8 @@ ac_status check_device(ac_automaton *h) {
 // A tiled launch with its zeroed scratch (tile counter, look-back words) in
 // stream-ordered memory, so calls on different streams never share it.
 cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode, cudaStream_t st) {
-    const size_t bytes = pfac::scratch_bytes(h->dev, r.n, mode, h->tuning);
+    const size_t bytes = h->dev.filter ? pfac::filter_scratch_bytes(r.n, mode)
+                                       : pfac::scratch_bytes(h->dev, r.n, mode, h->tuning);
     void *scratch = nullptr;
     cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
     if (e != cudaSuccess) return e;
@@ -99,7 +100,8 @@ cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode,
     if (e == cudaSuccess) {
         r.scratch = scratch;
         r.scratch_bytes = bytes;
-        e = pfac::launch_tiled(h->dev, r, mode, h->tuning, st);
+        e = h->dev.filter ? pfac::launch_filter(h->dev, r, mode, h->tuning, st)
+                          : pfac::launch_tiled(h->dev, r, mode, h->tuning, st);
     }
     const cudaError_t e2 = cudaFreeAsync(scratch, st);
     return e != cudaSuccess ? e : e2;
@@ -163,6 +165,8 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     d.maxlen = t.maxlen;
     d.jbytes = static_cast<uint32_t>(t.J.size() * sizeof(int16_t));
     d.jslow = t.jslow;
+    d.filter = t.filter;
+    d.fbytes = static_cast<uint32_t>(t.F.size() * sizeof(uint32_t));
     d.hash_shift = t.hash_shift;
     std::memcpy(d.hash_code, t.hash_code, 8);
     std::memcpy(d.hash_byte, t.hash_byte, 8);
@@ -177,6 +181,10 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
         if (s == AC_OK) s = upload(h, t.cls8.data(), 256, reinterpret_cast<const void **>(&d.cls8));
         if (s == AC_OK && !t.J.empty())
             s = upload(h, t.J.data(), t.J.size() * sizeof(int16_t), reinterpret_cast<const void **>(&d.J));
+        if (s == AC_OK && !t.F.empty())
+            s = upload(h, t.F.data(), t.F.size() * sizeof(uint32_t), reinterpret_cast<const void **>(&d.F));
+        if (s == AC_OK && !t.JK.empty())
+            s = upload(h, t.JK.data(), t.JK.size() * sizeof(int32_t), reinterpret_cast<const void **>(&d.JK));
         if (s == AC_OK && !t.J2.empty())
             s = upload(h, t.J2.data(), t.J2.size() * sizeof(int32_t), reinterpret_cast<const void **>(&d.J2));
         if (s != AC_OK) {
@@ -210,7 +218,8 @@ ac_status ac_info(ac_handle h, ac_info_t *info) {
     info->stride_depth = t.k2;
     info->min_len = t.minlen;
     info->max_len = t.maxlen;
-    info->table_bytes = t.G.size() + t.J.size() * sizeof(int16_t) + t.J2.size() * sizeof(int32_t) + 512;
+    info->table_bytes = t.G.size() + t.J.size() * sizeof(int16_t) + t.J2.size() * sizeof(int32_t) +
+                        t.F.size() * sizeof(uint32_t) + t.JK.size() * sizeof(int32_t) + 768;
     info->depth_base_jump = t.base_k;
     info->count_jump = t.count_k;
     info->class_hash_shift = t.hash_shift;

@@ -12,9 +12,13 @@
 //      (the output a walk ending there reports; equal strings -> lowest id);
 //   5. the dense table, one row per state: C goto columns plus one end column,
 //      where a missing transition holds the encoded result of stopping there;
-//   6. the root jump table: the result of walking any k codes from the root,
-//      (the top k levels of the table flattened into one lookup);
-//   7. the stride table: the same for k2 codes from every depth-k state.
+//   6. the top k levels of the table flattened, for the kernels' first lookup:
+//      for small alphabets (2- or 4-bit codes) a filter bit per window of k
+//      codes (clear: the walk stops inside the window with no keyword) plus
+//      the window table (depth-k state reached, or the encoded result); for
+//      8-bit codes the root jump table (result, or depth-k state, per window);
+//   7. the stride table: the depth-(k+k2) state or the result, for k2 more
+//      codes from every depth-k state.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -204,50 +208,80 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         }
         std::vector<Edge>().swap(edges);
 
-        // 6. root jump table.  Entry for a window of k codes (first code in the
-        //    low bits): the walk's result (>= -1) when it stops inside the
-        //    window, else -(2 + s - base_k) for the depth-k state s reached;
-        //    kJumpSlow when a result does not fit 15 bits.
         h.B = code_bits_for(h.C);
         const uint32_t wl = window_limit(h.B);
-        uint32_t jentries = std::max<uint32_t>(opt.jump_bytes, 2u) / 2u;
-        uint32_t kj = 0;
-        while (kj + 1 <= h.maxlen && kj + 1 <= wl && h.B * (kj + 1) <= 16 &&
-               (1ull << (h.B * (kj + 1))) <= jentries)
-            ++kj;
-        while (kj > 0 && h.depth_count[kj] > kJumpMaxStates) --kj;
-        h.k = kj;
+        const uint32_t cmask = (1u << h.B) - 1u;
         std::vector<uint32_t> depth_base(h.maxlen + 2, 0);
         for (uint32_t d = 0; d <= h.maxlen; ++d) depth_base[d + 1] = depth_base[d] + h.depth_count[d];
-        h.base_k = depth_base[kj];
-        h.count_k = h.depth_count[kj];
-        const uint32_t cmask = (1u << h.B) - 1u;
-        if (kj > 0) {
-            uint32_t nj = 1u << (h.B * kj);
-            h.J.assign(std::max<uint32_t>(nj, 8u), kJumpSlow);
-            for (uint32_t w = 0; w < nj; ++w) {
-                uint32_t s = 0;
-                int32_t e = 0;
-                bool alive = true;
-                for (uint32_t i = 0; i < kj; ++i) {
-                    uint32_t c = (w >> (h.B * i)) & cmask;
-                    int32_t t = c < h.C ? goto_entry(h, s, c) : encode_dead(pathbest[s]);
-                    if (t < 0) {
-                        e = t;
-                        alive = false;
-                        break;
-                    }
-                    s = static_cast<uint32_t>(t);
+        // Walk `len` codes of window w (first code in the low bits) from state s:
+        // true with the state reached, or false with the encoded result where the
+        // walk stopped (codes >= C stop it like a byte in no keyword).
+        auto walk_codes = [&](uint32_t s, uint32_t w, uint32_t len, int32_t *out) -> bool {
+            for (uint32_t i = 0; i < len; ++i) {
+                const uint32_t c = (w >> (h.B * i)) & cmask;
+                const int32_t t = c < h.C ? goto_entry(h, s, c) : encode_dead(pathbest[s]);
+                if (t < 0) {
+                    *out = t;
+                    return false;
                 }
-                if (alive) {
-                    h.J[w] = static_cast<int16_t>(-2 - static_cast<int32_t>(s - h.base_k));
-                } else {
-                    const int32_t v = -e - 2;  // result of the walk
-                    h.J[w] = (v <= 32767) ? static_cast<int16_t>(v) : kJumpSlow;
-                    if (v > 32767) h.jslow = true;
+                s = static_cast<uint32_t>(t);
+            }
+            *out = static_cast<int32_t>(s);
+            return true;
+        };
+
+        if (h.B <= 4) {
+            // 6a. root filter (2- and 4-bit codes): for every window of kf codes,
+            //     one bit that is clear when the walk from the root stops inside
+            //     the window with no keyword found (the start's result is -1), and
+            //     the window table: the depth-kf state reached, or the encoded
+            //     result where the walk stopped.
+            h.filter = true;
+            uint32_t fbits = 0;  // largest window that fits the shared-memory budget
+            while (fbits < kFilterBits && (2ull << fbits) <= 8ull * opt.jump_bytes) ++fbits;
+            const uint32_t kf = std::max<uint32_t>(1u, std::min<uint32_t>(h.maxlen, fbits / h.B));
+            h.k = kf;
+            h.base_k = depth_base[kf];
+            h.count_k = h.depth_count[kf];
+            const uint32_t nwin = 1u << (h.B * kf);
+            h.F.assign(std::max<uint32_t>(nwin / 32u, 4u), 0u);
+            h.JK.assign(nwin, 0);
+            for (uint32_t w = 0; w < nwin; ++w) {
+                int32_t e = 0;
+                const bool alive = walk_codes(0, w, kf, &e);
+                h.JK[w] = e;
+                if (alive || e < -1) h.F[w >> 5] |= 1u << (w & 31u);
+            }
+        } else {
+            // 6b. root jump table (8-bit codes).  Entry for a window of k codes:
+            //     the walk's result (>= -1) when it stops inside the window, else
+            //     -(2 + s - base_k) for the depth-k state s reached; kJumpSlow
+            //     when a result does not fit 15 bits.
+            uint32_t jentries = std::max<uint32_t>(opt.jump_bytes, 2u) / 2u;
+            uint32_t kj = 0;
+            while (kj + 1 <= h.maxlen && kj + 1 <= wl && h.B * (kj + 1) <= 16 &&
+                   (1ull << (h.B * (kj + 1))) <= jentries)
+                ++kj;
+            while (kj > 0 && h.depth_count[kj] > kJumpMaxStates) --kj;
+            h.k = kj;
+            h.base_k = depth_base[kj];
+            h.count_k = h.depth_count[kj];
+            if (kj > 0) {
+                const uint32_t nj = 1u << (h.B * kj);
+                h.J.assign(std::max<uint32_t>(nj, 8u), kJumpSlow);
+                for (uint32_t w = 0; w < nj; ++w) {
+                    int32_t e = 0;
+                    if (walk_codes(0, w, kj, &e)) {
+                        h.J[w] = static_cast<int16_t>(-2 - (e - static_cast<int32_t>(h.base_k)));
+                    } else {
+                        const int32_t v = -e - 2;  // result of the walk
+                        h.J[w] = (v <= 32767) ? static_cast<int16_t>(v) : kJumpSlow;
+                        if (v > 32767) h.jslow = true;
+                    }
                 }
             }
         }
+        const uint32_t kj = h.k;
 
         // 7. stride table from the depth-k states
         h.k2 = 0;
@@ -265,24 +299,12 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         if (h.k2 > 0) {
             const uint32_t cols = 1u << (h.B * h.k2);
             h.J2.assign(static_cast<size_t>(h.count_k) * cols, 0);
-            for (uint32_t r = 0; r < h.count_k; ++r) {
+            for (uint32_t r = 0; r < h.count_k; ++r)
                 for (uint32_t w = 0; w < cols; ++w) {
-                    uint32_t s = h.base_k + r;
                     int32_t e = 0;
-                    bool alive = true;
-                    for (uint32_t i = 0; i < h.k2; ++i) {
-                        uint32_t c = (w >> (h.B * i)) & cmask;
-                        int32_t t = c < h.C ? goto_entry(h, s, c) : encode_dead(pathbest[s]);
-                        if (t < 0) {
-                            e = t;
-                            alive = false;
-                            break;
-                        }
-                        s = static_cast<uint32_t>(t);
-                    }
-                    h.J2[static_cast<size_t>(r) * cols + w] = alive ? static_cast<int32_t>(s) : e;
+                    walk_codes(h.base_k + r, w, h.k2, &e);
+                    h.J2[static_cast<size_t>(r) * cols + w] = e;
                 }
-            }
         }
     } catch (const std::bad_alloc &) {
         return AC_ERR_OOM;

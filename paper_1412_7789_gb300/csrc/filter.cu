@@ -1,0 +1,1131 @@
+// Failureless Aho-Corasick matching for small alphabets (keyword bytes mapped
+// to 2- or 4-bit codes), sm_103a.
+//
+// pfac_filter -- persistent CTAs (one per SM), every warp on its own tiles of
+// 992 positions (two passes of 496), no block-wide barrier after start-up:
+//   * a tile plus a halo is fetched with one bulk async copy (cp.async.bulk,
+//     the TMA unit, no multicast) into one of the warp's shared-memory stages,
+//     completing on that stage's mbarrier, `stages` tiles ahead of use;
+//   * per pass, lane l classifies the 16 bytes at 16 l once (byte permutes on
+//     a 3-bit hash, or the byte table), packs their codes into one word (two
+//     for 4-bit codes) and gets the next lane's word with one shuffle, so each
+//     of its 16 start positions has its window of codes in registers; lane 31
+//     only supplies the look-ahead word;
+//   * one bit per position from the root filter (resident in shared memory for
+//     the whole kernel): clear means the walk from the root stops within the
+//     first k characters with no keyword, i.e. the result is -1 -- almost every
+//     position of a text whose keywords are longer than k;
+//   * the other positions ("survivors") go to a per-warp queue spread over all
+//     lanes: one load from the window table (depth-k state or result), one from
+//     the stride table (k2 more characters), and rarely the goto table one
+//     character at a time;
+//   * dense ids: a pass whose survivors found no keyword is written by one bulk
+//     async store from a constant buffer of -1; otherwise the survivors'
+//     results are merged into a -1 staging buffer and that is stored.  Counts
+//     take one atomic per warp; the compacted list ranks the survivors that
+//     found a keyword by ballot (the queue is in position order) and places
+//     each pass with a decoupled look-back.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "pfac_device.cuh"
+
+namespace pfac {
+
+namespace {
+
+constexpr int kMaxBlock = 512;
+constexpr int kMaxWarps = kMaxBlock / 32;
+constexpr int kMaxStages = 4;
+constexpr uint32_t kOwnLanes = 31;            // lanes that own start positions in a pass
+constexpr uint32_t kPass = 16 * kOwnLanes;    // 496 positions per pass
+constexpr uint32_t kTile = 2 * kPass;         // 992 positions per warp tile
+constexpr uint32_t kCodeSpan = kTile + 16;    // positions classified per tile
+constexpr uint32_t kResWords = kPass;         // staged results per pass
+// shared-memory header
+constexpr uint32_t kOffJBar = 0;
+constexpr uint32_t kOffStageBar = 64;
+constexpr uint32_t kOffStageTile = kOffStageBar + kMaxWarps * kMaxStages * 8;
+constexpr uint32_t kOffCls = 1024;  // 256 x uint8
+constexpr uint32_t kOffF = 1280;    // root filter bits
+constexpr unsigned kFull = 0xffffffffu;
+
+struct FilterParams {
+    TextView tv;
+    const uint8_t *text;
+    uint32_t nstages;
+    const void *G;
+    const uint32_t *Fg;
+    const int32_t *JK;
+    const int32_t *J2;
+    const uint8_t *cls8g;
+    uint32_t C, W, k, k2, base_k, maxlen, fbytes;
+    int hash_shift;
+    uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
+    int32_t *out;
+    int vec_ok;
+    uint32_t *cpos;
+    uint32_t *cids;
+    unsigned long long cap;
+    unsigned long long *count;
+    unsigned long long *status;
+    unsigned int *counter;
+    unsigned int *err;
+    uint32_t off_neg1, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue;
+};
+
+struct WarpSmem {
+    const uint8_t *cls8;
+    const uint32_t *F;
+    uint8_t *st;
+    uint32_t *packed;  // codes of the tile's kCodeSpan positions, B bits each
+    uint16_t *inv;     // 16 "cannot extend a walk" bits per 16 positions
+    int32_t *res;
+    uint16_t *queue;
+    const int32_t *neg1;  // kResWords x -1, shared by the CTA's warps
+};
+
+// Classify the 4 bytes of w: their class codes (one per byte) and a word whose
+// non-zero bytes mark bytes in no keyword.
+__device__ __forceinline__ void classify_word(const FilterParams &p, const uint8_t *cls8, uint32_t w,
+                                              uint32_t &codes, uint32_t &unknown) {
+    if (p.hash_shift >= 0) {
+        // h = (byte >> s) & 7 selects, with byte permutes, the code of the one
+        // keyword byte with that hash and the byte itself; a mismatch is a byte
+        // in no keyword
+        const uint32_t sh = static_cast<uint32_t>(p.hash_shift);
+        const uint32_t hv = (w >> sh) & 0x07070707u;
+        const uint32_t sel = __byte_perm(hv | (hv >> 4), 0u, 0x4420u);
+        codes = __byte_perm(p.hcode_lo, p.hcode_hi, sel);
+        unknown = w ^ __byte_perm(p.hbyte_lo, p.hbyte_hi, sel);
+    } else {
+        const uint32_t t0 = cls8[__byte_perm(w, 0u, 0x4440u)], t1 = cls8[__byte_perm(w, 0u, 0x4441u)];
+        const uint32_t t2 = cls8[__byte_perm(w, 0u, 0x4442u)], t3 = cls8[__byte_perm(w, 0u, 0x4443u)];
+        codes = __byte_perm(__byte_perm(t0, t1, 0x0040u), __byte_perm(t2, t3, 0x0040u), 0x5410u);
+        unknown = codes & 0x80808080u;  // class value 0xFF marks a byte in no keyword
+    }
+}
+
+// One flag per non-zero byte of x (bit i for byte i).
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
+    const uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;  // bit 7 of each byte: that byte != 0
+    return ((t & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// Pack the low B bits of the 4 byte codes of `codes` (4 B bits, first byte lowest).
+template <int B>
+__device__ __forceinline__ uint32_t pack4(uint32_t codes) {
+    if (B == 2) return ((codes & 0x03030303u) * 0x01041040u) >> 24;
+    uint32_t x = codes & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    return (x | (x >> 8)) & 0xFFFFu;
+}
+
+// Codes of positions i.. (16 for B = 2, 8 for B = 4) from the packed stream.
+template <int B>
+__device__ __forceinline__ uint32_t code_window(const uint32_t *packed, uint32_t i) {
+    const uint32_t bo = B * i, w = bo >> 5;
+    return __funnelshift_r(packed[w], packed[w + 1], bo & 31u);
+}
+
+// Code of tile position q; false when q cannot extend a walk.  Positions below
+// `coded` have their codes in the packed stream already; later ones are read
+// from the text in global memory (the stage may already hold the next tile).
+template <int B>
+__device__ __forceinline__ bool fetch_code(const FilterParams &p, const WarpSmem &w, int64_t gpb, uint32_t coded,
+                                           uint32_t q, uint32_t &c) {
+    if (q < coded) {
+        if ((w.inv[q >> 4] >> (q & 15u)) & 1u) return false;
+        c = (w.packed[(B * q) >> 5] >> ((B * q) & 31u)) & ((1u << B) - 1u);
+        return true;
+    }
+    const int64_t gp = gpb + static_cast<int64_t>(q);
+    if (gp >= static_cast<int64_t>(p.tv.n)) return false;
+    const uint32_t v = w.cls8[__ldg(p.text + gp)];
+    if (v == 0xFFu) return false;
+    c = v;
+    return true;
+}
+
+// Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)):
+// their results go to the pass's staging buffer (or are counted).  Returns
+// true when this lane found a keyword.
+template <int B, typename GT, int MODE, int SLOTS, bool DIRECT = false>
+__device__ __forceinline__ bool finish_survivors(const FilterParams &p, const WarpSmem &w, int64_t gpb,
+                                                 bool interior, bool clean, uint32_t avail, uint32_t pbase,
+                                                 int lane, unsigned long long &cnt, uint32_t base,
+                                                 uint32_t coded = 0) {
+    const int64_t n = static_cast<int64_t>(p.tv.n);
+    const uint32_t k = p.k, k2 = p.k2;
+    const GT *G = static_cast<const GT *>(p.G);
+    uint32_t st[SLOTS], q[SLOTS], ii[SLOTS];
+    int v[SLOTS];
+    uint32_t act = 0, pend = 0, walking = 0;
+    uint32_t x[SLOTS];
+    // window table: depth-k state or result
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        const uint32_t qi = lane + 32u * t;
+        v[t] = INT_MIN;
+        st[t] = 0;
+        q[t] = 0;
+        ii[t] = 0;
+        x[t] = 0;
+        if (qi < avail) {
+            act |= 1u << t;
+            const uint32_t e16 = w.queue[base + qi];
+            const uint32_t i = e16 & 0x7FFFu;
+            ii[t] = i;
+            q[t] = i;
+            if (!(e16 >> 15)) {
+                x[t] = code_window<B>(w.packed, i);
+                v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
+                pend |= 1u << t;
+            }
+        }
+    }
+    // stride table for the walks still alive at depth k
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if ((pend >> t) & 1u) {
+            const int e = v[t];
+            if (e < 0) {
+                v[t] = decode_dead(e);
+                pend &= ~(1u << t);
+            } else {
+                st[t] = static_cast<uint32_t>(e);
+                q[t] = ii[t] + k;
+                v[t] = INT_MIN;
+                bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(ii[t] + k + k2) <= n);
+                if (ok2 && !clean) {
+                    const uint32_t j = ii[t] + k;
+                    const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
+                    ok2 = (wi & ((1u << k2) - 1u)) == 0;
+                }
+                if (ok2) {
+                    const uint32_t w2 = (x[t] >> (B * k)) & ((1u << (B * k2)) - 1u);
+                    v[t] = __ldg(p.J2 + ((static_cast<uint64_t>(st[t] - p.base_k) << (B * k2)) | w2));
+                } else {
+                    pend &= ~(1u << t);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if ((act >> t) & 1u) {
+            if ((pend >> t) & 1u) {
+                if (v[t] < 0) {
+                    v[t] = decode_dead(v[t]);
+                } else {
+                    st[t] = static_cast<uint32_t>(v[t]);
+                    q[t] += k2;
+                    v[t] = INT_MIN;
+                    walking |= 1u << t;
+                }
+            } else if (v[t] == INT_MIN) {
+                walking |= 1u << t;
+            }
+        }
+    }
+    // the goto table, one character at a time
+    for (uint32_t step = 0; walking; ++step) {
+        if (step > p.maxlen + 1) {  // impossible for a well-formed table
+            atomicOr(p.err, static_cast<unsigned>(kErrWalk));
+#pragma unroll
+            for (int t = 0; t < SLOTS; ++t)
+                if ((walking >> t) & 1u) v[t] = -1;
+            break;
+        }
+        int e[SLOTS];
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            if ((walking >> t) & 1u) {
+                uint32_t c = 0;
+                const bool okc = fetch_code<B>(p, w, gpb, DIRECT ? coded : pbase + kPass + 16u, q[t], c);
+                // an unknown byte or the text end reads the row's end column,
+                // which always holds the result of stopping there
+                e[t] = goto_ld(G, st[t], p.W, okc ? c : p.C);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            if ((walking >> t) & 1u) {
+                if (e[t] < 0) {
+                    v[t] = decode_dead(e[t]);
+                    walking &= ~(1u << t);
+                } else {
+                    st[t] = static_cast<uint32_t>(e[t]);
+                    q[t] += 1;
+                }
+            }
+        }
+    }
+    bool found = false;
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if ((act >> t) & 1u) {
+            found |= v[t] >= 0;
+            if (MODE == OUT_COUNT)
+                cnt += v[t] >= 0 ? 1ull : 0ull;
+            else if (DIRECT)
+                p.out[gpb + ii[t]] = v[t];
+            else
+                w.res[ii[t] - pbase] = v[t];
+        }
+    }
+    return found;
+}
+
+template <int B, typename GT, int MODE>
+__device__ __forceinline__ void filter_pass(const FilterParams &p, const WarpSmem &w, int64_t gpb, bool interior,
+                                            uint32_t tile, uint32_t h, int lane, unsigned long long &cnt,
+                                            bool &res_busy) {
+    const int64_t n = static_cast<int64_t>(p.tv.n);
+    const uint32_t k = p.k;
+    const uint32_t pbase = h * kPass;
+    const uint32_t i0 = pbase + 16u * static_cast<uint32_t>(lane);  // this lane's first position
+    const bool owner = lane < static_cast<int>(kOwnLanes);
+
+    // 1. classify this lane's 16 bytes once: packed codes and unknown-byte bits
+    const uint4 raw = *reinterpret_cast<const uint4 *>(w.st + i0);
+    uint32_t c0, c1, c2, c3, u0, u1, u2, u3;
+    classify_word(p, w.cls8, raw.x, c0, u0);
+    classify_word(p, w.cls8, raw.y, c1, u1);
+    classify_word(p, w.cls8, raw.z, c2, u2);
+    classify_word(p, w.cls8, raw.w, c3, u3);
+    uint32_t inv = 0;
+    if (u0 | u1 | u2 | u3)
+        inv = nonzero_bytes(u0) | (nonzero_bytes(u1) << 4) | (nonzero_bytes(u2) << 8) | (nonzero_bytes(u3) << 12);
+    if (!interior) {
+        const int64_t g0 = gpb + i0;
+        if (!(g0 >= 0 && g0 + 16 <= n)) {
+#pragma unroll
+            for (int b = 0; b < 16; ++b)
+                if (g0 + b < 0 || g0 + b >= n) inv |= 1u << b;
+        }
+    }
+    uint32_t plo, phi = 0;  // 16 codes: B = 2 one word, B = 4 two words
+    if (B == 2) {
+        plo = pack4<2>(c0) | (pack4<2>(c1) << 8) | (pack4<2>(c2) << 16) | (pack4<2>(c3) << 24);
+        w.packed[i0 >> 4] = plo;
+    } else {
+        plo = pack4<4>(c0) | (pack4<4>(c1) << 16);
+        phi = pack4<4>(c2) | (pack4<4>(c3) << 16);
+        w.packed[i0 >> 3] = plo;
+        w.packed[(i0 >> 3) + 1] = phi;
+    }
+    w.inv[i0 >> 4] = static_cast<uint16_t>(inv);
+    const bool clean = !__any_sync(kFull, inv != 0);
+    const uint32_t nlo = __shfl_down_sync(kFull, plo, 1);  // next lane's first codes
+    const uint32_t ninv = __shfl_down_sync(kFull, inv, 1);
+
+    // 2. root filter: one bit per start position
+    uint32_t sv = 0, slowm = 0, valid = owner ? 0xFFFFu : 0u;
+    if (owner) {
+        const uint32_t fmask = (1u << (B * k)) - 1u;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            uint32_t win;
+            if (B == 2)
+                win = __funnelshift_r(plo, nlo, 2 * r);
+            else
+                win = r < 8 ? __funnelshift_r(plo, phi, 4 * r) : __funnelshift_r(phi, nlo, 4 * (r - 8));
+            const uint32_t idx = win & fmask;
+            sv |= ((w.F[idx >> 5] >> (idx & 31u)) & 1u) << r;
+        }
+        if (!interior || !clean) {
+            const uint32_t iw = inv | (ninv << 16);
+            const uint32_t kbits = (1u << k) - 1u;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int64_t gp = gpb + i0 + r;
+                if (gp < 0 || gp >= n) {
+                    valid &= ~(1u << r);
+                } else if (gp + static_cast<int64_t>(k) > n || ((iw >> r) & kbits)) {
+                    slowm |= 1u << r;
+                }
+            }
+            sv = (sv | slowm) & valid;
+        }
+    }
+
+    // 3. survivors into the warp's queue (position | slow flag), lane order
+    const uint32_t c = __popc(sv);
+    uint32_t inc = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, inc, d);
+        if (lane >= d) inc += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, inc, 31);
+    {
+        uint32_t o = inc - c, m = sv;
+        while (m) {
+            const uint32_t r = __ffs(m) - 1;
+            m &= m - 1;
+            w.queue[o++] = static_cast<uint16_t>((i0 + r) | (((slowm >> r) & 1u) << 15));
+        }
+    }
+    if (MODE == OUT_DENSE && res_busy) {
+        if (lane == 0) bulk_wait_read();  // an earlier bulk store still reads the buffer
+        res_busy = false;
+    }
+    __syncwarp();
+
+    // 4. the survivors, spread over the lanes
+    bool found = false;
+    if (total <= 32) {
+        found = finish_survivors<B, GT, MODE, 1>(p, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
+    } else if (total <= 64) {
+        found = finish_survivors<B, GT, MODE, 2>(p, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
+    } else {
+        for (uint32_t b = 0; b < total; b += 128)
+            found |= finish_survivors<B, GT, MODE, 4>(p, w, gpb, interior, clean, total - b, pbase, lane, cnt, b);
+    }
+    found = __any_sync(kFull, found);
+    __syncwarp();
+
+    // 5. output
+    if (MODE == OUT_DENSE) {
+        if (!found && interior && p.vec_ok) {
+            // every result of the pass is -1: store the constant buffer
+            if (lane == 0) {
+                bulk_store(p.out + gpb + pbase, w.neg1, kResWords * 4);
+                bulk_commit();
+            }
+        } else {
+            // results of this lane's 16 positions: survivors' from the buffer, -1 elsewhere
+            if (owner) {
+#pragma unroll
+                for (uint32_t g = 0; g < 4; ++g) {
+                    int4 *slot = reinterpret_cast<int4 *>(w.res) + 4u * lane + g;
+                    const uint32_t m = (sv >> (4 * g)) & 0xFu;
+                    int4 r4 = make_int4(-1, -1, -1, -1);
+                    if (m) {
+                        const int4 sres = *slot;
+                        if (m & 1u) r4.x = sres.x;
+                        if (m & 2u) r4.y = sres.y;
+                        if (m & 4u) r4.z = sres.z;
+                        if (m & 8u) r4.w = sres.w;
+                    }
+                    *slot = r4;
+                }
+            }
+            __syncwarp();
+            if (interior && p.vec_ok) {
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    bulk_store(p.out + gpb + pbase, w.res, kResWords * 4);
+                    bulk_commit();
+                }
+                res_busy = true;
+            } else if (owner) {
+#pragma unroll
+                for (uint32_t g = 0; g < 4; ++g) {
+                    const int4 r4 = reinterpret_cast<const int4 *>(w.res)[4u * lane + g];
+                    const int64_t g0 = gpb + i0 + 4u * g;
+                    if (p.vec_ok && ((valid >> (4 * g)) & 0xFu) == 0xFu) {
+                        *reinterpret_cast<int4 *>(p.out + g0) = r4;
+                    } else {
+                        const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            if ((valid >> (4 * g + r)) & 1u) p.out[g0 + r] = rr[r];
+                    }
+                }
+            }
+        }
+    } else if (MODE == OUT_COMPACT) {
+        // The matches of the pass are survivors with a result >= 0, and the
+        // queue lists survivors in ascending position: rank them by ballot.
+        uint32_t unit_total = 0;
+        if (found) {
+            for (uint32_t b = 0; b < total; b += 32) {
+                const uint32_t qi = b + lane;
+                const int v = qi < total ? w.res[(w.queue[qi] & 0x7FFFu) - pbase] : -1;
+                unit_total += __popc(__ballot_sync(kFull, v >= 0));
+            }
+        }
+        unsigned long long pre = 0;
+        const uint32_t unit = 2u * tile + h;
+        if (lane == 0) {
+            pre = lookback(p.status, unit, unit_total, p.err);
+            if (unit == 2u * p.tv.ntiles - 1u) *p.count = pre + unit_total;
+        }
+        pre = __shfl_sync(kFull, pre, 0);
+        if (found) {
+            unsigned long long o = pre;
+            for (uint32_t b = 0; b < total; b += 32) {
+                const uint32_t qi = b + lane;
+                uint32_t i = 0;
+                int v = -1;
+                if (qi < total) {
+                    i = w.queue[qi] & 0x7FFFu;
+                    v = w.res[i - pbase];
+                }
+                const uint32_t m = __ballot_sync(kFull, v >= 0);
+                if (v >= 0) {
+                    const unsigned long long at = o + __popc(m & ((1u << lane) - 1u));
+                    if (at < p.cap) {
+                        p.cpos[at] = static_cast<uint32_t>(gpb + i);
+                        p.cids[at] = static_cast<uint32_t>(v);
+                    }
+                }
+                o += __popc(m);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <int B, typename GT, int MODE>
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter(const FilterParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
+    uint32_t *stile = reinterpret_cast<uint32_t *>(smem + kOffStageTile) + warp * kMaxStages;
+    uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
+    WarpSmem w;
+    w.cls8 = smem + kOffCls;
+    w.F = reinterpret_cast<const uint32_t *>(smem + kOffF);
+    w.st = wreg;
+    w.packed = reinterpret_cast<uint32_t *>(wreg + p.off_packed);
+    w.inv = reinterpret_cast<uint16_t *>(wreg + p.off_inv);
+    w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
+    w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
+    w.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
+    const uint32_t nst = p.nstages;
+
+    for (uint32_t i = threadIdx.x; i < kResWords; i += blockDim.x) reinterpret_cast<int32_t *>(smem + p.off_neg1)[i] = -1;
+    fence_proxy_async_smem();  // the constant buffer is read by bulk stores
+    if (threadIdx.x == 0) {
+        mbar_init(jbar, 1);
+        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
+        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(jbar, 256u + p.fbytes);
+        bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
+        bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
+    }
+    // Tiles are claimed from a global counter so that a warp meeting an
+    // expensive tile (long walks) stops taking work while the others go on.
+    // The compacted output claims every tile (ordered look-back needs tiles
+    // handed out in increasing order to running warps); the other outputs
+    // hand each warp its first tile statically (warp-major numbering, so
+    // neighbouring tiles land on different SMs) and claim the rest.
+    const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
+    auto next_tile = [&](uint32_t it) -> uint32_t {
+        if (MODE == OUT_COMPACT) return atomicAdd(p.counter, 1u);
+        if (it == 0) return gw < p.tv.ntiles ? static_cast<uint32_t>(gw) : 0xFFFFFFFFu;
+        const uint64_t t = GW + atomicAdd(p.counter, 1u);
+        return t < p.tv.ntiles ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+    };
+    if (lane == 0)
+        for (uint32_t s = 0; s < nst; ++s) issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, next_tile(s));
+
+    unsigned long long cnt = 0;
+    bool res_busy = false;
+    bool ok = mbar_wait(jbar, 0);
+    for (uint32_t it = 0;; ++it) {
+        const uint32_t s = it % nst;
+        ok = ok && mbar_wait(&bars[s], (it / nst) & 1u);
+        if (!__all_sync(kFull, ok)) {
+            // A copy never completed: latch the error, let this warp's copies in
+            // flight finish (bounded), and leave.
+            if (lane == 0) {
+                bulk_wait_all();
+                atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
+                mbar_wait(jbar, 0);
+                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u);
+            }
+            return;
+        }
+        const uint32_t tile = stile[s];
+        if (tile >= p.tv.ntiles) break;
+        w.st = wreg + s * p.tv.staged;
+        const uint64_t tlo = static_cast<uint64_t>(tile) * kTile;
+        const int64_t gpb = static_cast<int64_t>(tlo) - p.tv.head;
+        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.tv.staged) <= static_cast<int64_t>(p.tv.n);
+        if (!interior) {
+            load_fringe(p.tv, w.st, tlo, lane);
+            __syncwarp();
+        }
+#pragma unroll 1
+        for (uint32_t h = 0; h < kTile / kPass; ++h)
+            filter_pass<B, GT, MODE>(p, w, gpb, interior, tile, h, lane, cnt, res_busy);
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            issue_tile(p.tv, &bars[s], &stile[s], w.st, next_tile(it + nst));
+        }
+    }
+
+    if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
+    if (MODE == OUT_COUNT) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
+        if (lane == 0 && cnt) atomicAdd(p.count, cnt);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined variant (dense ids and counts).  A tile's survivors (at most one
+// per lane) stay in flight while the warp works on the next tiles: the window
+// table load is issued when the tile is filtered, the stride table load one
+// tile later, and the tile is finished and written two tiles later, so the
+// two dependent L2 round trips overlap the classification and filtering of
+// the next tiles.  A tile with more survivors than lanes (long walks) drains
+// the pipeline and is finished at once.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNoPos = 0xFFFFu;
+enum : uint32_t { kPhJK = 0, kPhJ2 = 1, kPhWalk = 2, kPhDone = 3 };
+
+struct Flight {
+    int64_t gpb;      // text index of the tile's position 0
+    uint32_t tile;    // 0xFFFFFFFF: empty
+    uint32_t interior;
+    uint32_t pos;     // this lane's survivor (tile position) or kNoPos
+    uint32_t phase;
+    uint32_t state;   // goto state of the walk
+    uint32_t q;       // tile position of the walk's next character
+    uint32_t w2;      // stride-table codes
+    uint32_t ok2;     // the stride window is usable
+    int val;          // load in flight, or the result when done
+};
+
+__device__ __forceinline__ Flight empty_flight() {
+    Flight f;
+    f.gpb = 0;
+    f.tile = 0xFFFFFFFFu;
+    f.interior = 0;
+    f.pos = kNoPos;
+    f.phase = kPhDone;
+    f.state = 0;
+    f.q = 0;
+    f.w2 = 0;
+    f.ok2 = 0;
+    f.val = -1;
+    return f;
+}
+
+// Walk the goto table from state s, reading the text from global memory.
+template <typename GT>
+__device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t *cls8, int64_t gpb, uint32_t s,
+                                           uint32_t q) {
+    const GT *G = static_cast<const GT *>(p.G);
+    for (uint32_t step = 0; step <= p.maxlen + 1; ++step) {
+        const int64_t gp = gpb + static_cast<int64_t>(q);
+        uint32_t c = p.C;  // the end column: stop here
+        if (gp < static_cast<int64_t>(p.tv.n)) {
+            const uint32_t v = cls8[__ldg(p.text + gp)];
+            if (v != 0xFFu) c = v;
+        }
+        const int t = goto_ld(G, s, p.W, c);
+        if (t < 0) return decode_dead(t);
+        s = static_cast<uint32_t>(t);
+        ++q;
+    }
+    atomicOr(p.err, static_cast<unsigned>(kErrWalk));
+    return -1;
+}
+
+// Second stage: the window-table result has arrived; issue the stride load.
+template <int B>
+__device__ __forceinline__ void flight_advance(const FilterParams &p, Flight &f) {
+    if (f.pos == kNoPos || f.phase != kPhJK) return;
+    const int e = f.val;
+    if (e < 0) {
+        f.val = decode_dead(e);
+        f.phase = kPhDone;
+        return;
+    }
+    f.state = static_cast<uint32_t>(e);
+    f.q = f.pos + p.k;
+    if (f.ok2) {
+        f.val = __ldg(p.J2 + ((static_cast<uint64_t>(f.state - p.base_k) << (B * p.k2)) | f.w2));
+        f.phase = kPhJ2;
+    } else {
+        f.phase = kPhWalk;
+    }
+}
+
+// Last stage: the stride-table result has arrived; finish the walk if needed.
+template <typename GT>
+__device__ __forceinline__ void flight_finish(const FilterParams &p, const uint8_t *cls8, Flight &f) {
+    if (f.pos == kNoPos) return;
+    if (f.phase == kPhJ2) {
+        const int e = f.val;
+        if (e < 0) {
+            f.val = decode_dead(e);
+            f.phase = kPhDone;
+            return;
+        }
+        f.state = static_cast<uint32_t>(e);
+        f.q += p.k2;
+        f.phase = kPhWalk;
+    }
+    if (f.phase == kPhWalk) {
+        f.val = walk_global<GT>(p, cls8, f.gpb, f.state, f.q);
+        f.phase = kPhDone;
+    }
+}
+
+// Write (or count) a finished tile: one bulk store of -1 when no survivor
+// found a keyword, else -1 from the position owners and the survivors' ids.
+template <int MODE>
+__device__ __forceinline__ void flight_output(const FilterParams &p, const WarpSmem &w, const Flight &f, int lane,
+                                              unsigned long long &cnt) {
+    if (f.tile == 0xFFFFFFFFu) return;
+    const bool mine = f.pos != kNoPos && f.val >= 0;
+    if (MODE == OUT_COUNT) {
+        cnt += mine ? 1ull : 0ull;
+        return;
+    }
+    const bool found = __any_sync(kFull, mine);
+    const int64_t n = static_cast<int64_t>(p.tv.n);
+    if (!found && f.interior && p.vec_ok) {
+        if (lane == 0) {
+            bulk_store(p.out + f.gpb, w.neg1, kTile * 4);
+            bulk_commit();
+            bulk_wait_read_keep8();  // bound the groups in flight
+        }
+        return;
+    }
+    if (lane < static_cast<int>(kOwnLanes)) {
+        const int4 none = make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+#pragma unroll
+            for (uint32_t g = 0; g < 4; ++g) {
+                const int64_t g0 = f.gpb + h * kPass + 16u * lane + 4u * g;
+                if (p.vec_ok && g0 >= 0 && g0 + 4 <= n) {
+                    *reinterpret_cast<int4 *>(p.out + g0) = none;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (g0 + r >= 0 && g0 + r < n) p.out[g0 + r] = -1;
+                }
+            }
+        }
+    }
+    __syncwarp();  // the -1 stores of the owners come before the survivors' ids
+    if (mine) p.out[f.gpb + f.pos] = f.val;
+}
+
+template <int B, typename GT, int MODE>
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
+    uint32_t *stile = reinterpret_cast<uint32_t *>(smem + kOffStageTile) + warp * kMaxStages;
+    uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
+    WarpSmem w;
+    w.cls8 = smem + kOffCls;
+    w.F = reinterpret_cast<const uint32_t *>(smem + kOffF);
+    w.st = wreg;
+    w.packed = reinterpret_cast<uint32_t *>(wreg + p.off_packed);
+    w.inv = reinterpret_cast<uint16_t *>(wreg + p.off_inv);
+    w.res = nullptr;
+    w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
+    w.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
+    const uint32_t nst = p.nstages;
+    const int64_t n = static_cast<int64_t>(p.tv.n);
+    const uint32_t k = p.k, k2 = p.k2;
+    const bool owner = lane < static_cast<int>(kOwnLanes);
+
+    for (uint32_t i = threadIdx.x; i < kTile; i += blockDim.x) reinterpret_cast<int32_t *>(smem + p.off_neg1)[i] = -1;
+    fence_proxy_async_smem();  // the constant buffer is read by bulk stores
+    if (threadIdx.x == 0) {
+        mbar_init(jbar, 1);
+        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
+        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(jbar, 256u + p.fbytes);
+        bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
+        bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
+    }
+    // Tiles: the first one per warp statically (warp-major numbering, so
+    // neighbouring tiles land on different SMs), the rest claimed from a global
+    // counter so that a warp held up by an expensive tile stops taking work.
+    const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
+    auto next_tile = [&](uint32_t it) -> uint32_t {
+        if (it == 0) return gw < p.tv.ntiles ? static_cast<uint32_t>(gw) : 0xFFFFFFFFu;
+        const uint64_t t = GW + atomicAdd(p.counter, 1u);
+        return t < p.tv.ntiles ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+    };
+    if (lane == 0)
+        for (uint32_t s = 0; s < nst; ++s) issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, next_tile(s));
+
+    unsigned long long cnt = 0;
+    Flight f1 = empty_flight(), f2 = empty_flight();  // one and two tiles back
+    bool ok = mbar_wait(jbar, 0);
+    for (uint32_t it = 0;; ++it) {
+        const uint32_t s = it % nst;
+        ok = ok && mbar_wait(&bars[s], (it / nst) & 1u);
+        if (!__all_sync(kFull, ok)) {
+            // A copy never completed: latch the error, let this warp's copies in
+            // flight finish (bounded), and leave.
+            if (lane == 0) {
+                bulk_wait_all();
+                atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
+                mbar_wait(jbar, 0);
+                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u);
+            }
+            return;
+        }
+        const uint32_t tile = stile[s];
+        if (tile >= p.tv.ntiles) break;
+        uint8_t *st = wreg + s * p.tv.staged;
+        const uint64_t tlo = static_cast<uint64_t>(tile) * kTile;
+        const int64_t gpb = static_cast<int64_t>(tlo) - p.tv.head;
+        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.tv.staged) <= n;
+        if (!interior) {
+            load_fringe(p.tv, st, tlo, lane);
+            __syncwarp();
+        }
+
+        // 1. classify the tile's bytes (both halves), once per byte
+        uint32_t plo[2], phi[2], inv[2];
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
+            const uint4 raw = *reinterpret_cast<const uint4 *>(st + i0);
+            uint32_t c0, c1, c2, c3, u0, u1, u2, u3;
+            classify_word(p, w.cls8, raw.x, c0, u0);
+            classify_word(p, w.cls8, raw.y, c1, u1);
+            classify_word(p, w.cls8, raw.z, c2, u2);
+            classify_word(p, w.cls8, raw.w, c3, u3);
+            uint32_t iv = 0;
+            if (u0 | u1 | u2 | u3)
+                iv = nonzero_bytes(u0) | (nonzero_bytes(u1) << 4) | (nonzero_bytes(u2) << 8) |
+                     (nonzero_bytes(u3) << 12);
+            if (!interior) {
+                const int64_t g0 = gpb + i0;
+                if (!(g0 >= 0 && g0 + 16 <= n)) {
+#pragma unroll
+                    for (int b = 0; b < 16; ++b)
+                        if (g0 + b < 0 || g0 + b >= n) iv |= 1u << b;
+                }
+            }
+            inv[h] = iv;
+            if (B == 2) {
+                plo[h] = pack4<2>(c0) | (pack4<2>(c1) << 8) | (pack4<2>(c2) << 16) | (pack4<2>(c3) << 24);
+                phi[h] = 0;
+                w.packed[i0 >> 4] = plo[h];
+            } else {
+                plo[h] = pack4<4>(c0) | (pack4<4>(c1) << 16);
+                phi[h] = pack4<4>(c2) | (pack4<4>(c3) << 16);
+                w.packed[i0 >> 3] = plo[h];
+                w.packed[(i0 >> 3) + 1] = phi[h];
+            }
+            w.inv[i0 >> 4] = static_cast<uint16_t>(iv);
+        }
+        const bool clean = !__any_sync(kFull, (inv[0] | inv[1]) != 0);
+        __syncwarp();
+        // the stage is consumed: start fetching a later tile into it
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            issue_tile(p.tv, &bars[s], &stile[s], st, next_tile(it + nst));
+        }
+
+        // 2. root filter, one bit per start position (bits 0-15: first half)
+        uint32_t sv = 0, slowm = 0;
+        uint32_t nlo[2];  // the next lane's first codes (lane 31 supplies the look-ahead)
+        nlo[0] = __shfl_down_sync(kFull, plo[0], 1);
+        nlo[1] = __shfl_down_sync(kFull, plo[1], 1);
+        if (owner) {
+            const uint32_t fmask = (1u << (B * k)) - 1u;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    uint32_t win;
+                    if (B == 2)
+                        win = __funnelshift_r(plo[h], nlo[h], 2 * r);
+                    else
+                        win = r < 8 ? __funnelshift_r(plo[h], phi[h], 4 * r)
+                                    : __funnelshift_r(phi[h], nlo[h], 4 * (r - 8));
+                    const uint32_t idx = win & fmask;
+                    sv |= ((w.F[idx >> 5] >> (idx & 31u)) & 1u) << (16 * h + r);
+                }
+            }
+        }
+        if (!interior || !clean) {
+            const uint32_t kbits = (1u << k) - 1u;
+            uint32_t valid = 0;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+                const uint32_t ninv = __shfl_down_sync(kFull, inv[h], 1);
+                const uint32_t iw = inv[h] | (ninv << 16);
+                const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int64_t gp = gpb + i0 + r;
+                    if (owner && gp >= 0 && gp < n) {
+                        valid |= 1u << (16 * h + r);
+                        if (gp + static_cast<int64_t>(k) > n || ((iw >> r) & kbits)) slowm |= 1u << (16 * h + r);
+                    }
+                }
+            }
+            sv = (sv | slowm) & valid;
+        }
+
+        // 3. survivors into the warp's queue in ascending position
+        const uint32_t c = __popc(sv & 0xFFFFu) | (__popc(sv >> 16) << 16);
+        uint32_t inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += y;
+        }
+        const uint32_t tot2 = __shfl_sync(kFull, inc, 31);
+        const uint32_t total = (tot2 & 0xFFFFu) + (tot2 >> 16);
+        {
+            const uint32_t excl = inc - c;
+            uint32_t o0 = excl & 0xFFFFu, o1 = (tot2 & 0xFFFFu) + (excl >> 16);
+            uint32_t m = sv;
+            while (m) {
+                const uint32_t b = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t h = b >> 4;
+                const uint32_t i = h * kPass + 16u * static_cast<uint32_t>(lane) + (b & 15u);
+                const uint16_t e = static_cast<uint16_t>(i | (((slowm >> b) & 1u) << 15));
+                if (h == 0)
+                    w.queue[o0++] = e;
+                else
+                    w.queue[o1++] = e;
+            }
+        }
+        __syncwarp();
+
+        if (total > 32) {
+            // 4a. many survivors: finish the tiles in flight, then this one
+            flight_advance<B>(p, f1);
+            flight_finish<GT>(p, w.cls8, f2);
+            flight_output<MODE>(p, w, f2, lane, cnt);
+            flight_finish<GT>(p, w.cls8, f1);
+            flight_output<MODE>(p, w, f1, lane, cnt);
+            f1 = empty_flight();
+            f2 = empty_flight();
+            if (MODE == OUT_DENSE) {
+                // -1 from the position owners first, then every survivor's id
+                if (owner) {
+                    const int4 none = make_int4(-1, -1, -1, -1);
+#pragma unroll
+                    for (uint32_t h = 0; h < 2; ++h) {
+#pragma unroll
+                        for (uint32_t g = 0; g < 4; ++g) {
+                            const int64_t g0 = gpb + h * kPass + 16u * lane + 4u * g;
+                            if (p.vec_ok && g0 >= 0 && g0 + 4 <= n) {
+                                *reinterpret_cast<int4 *>(p.out + g0) = none;
+                            } else {
+#pragma unroll
+                                for (int r = 0; r < 4; ++r)
+                                    if (g0 + r >= 0 && g0 + r < n) p.out[g0 + r] = -1;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            for (uint32_t b = 0; b < total; b += 128)
+                finish_survivors<B, GT, MODE, 4, true>(p, w, gpb, interior, clean, total - b, 0, lane, cnt, b,
+                                                       kCodeSpan);
+            __syncwarp();
+            continue;
+        }
+
+        // 4b. at most one survivor per lane: issue its window-table load now
+        Flight f0 = empty_flight();
+        f0.tile = tile;
+        f0.gpb = gpb;
+        f0.interior = interior ? 1u : 0u;
+        if (static_cast<uint32_t>(lane) < total) {
+            const uint32_t e16 = w.queue[lane];
+            const uint32_t i = e16 & 0x7FFFu;
+            f0.pos = i;
+            if (e16 >> 15) {
+                f0.phase = kPhWalk;  // walk from the root
+                f0.state = 0;
+                f0.q = i;
+            } else {
+                const uint32_t x = code_window<B>(w.packed, i);
+                f0.val = __ldg(p.JK + (x & ((1u << (B * k)) - 1u)));
+                f0.phase = kPhJK;
+                f0.w2 = (x >> (B * k)) & ((1u << (B * k2)) - 1u);
+                bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(i + k + k2) <= n);
+                if (ok2 && !clean) {
+                    const uint32_t j = i + k;
+                    const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
+                    ok2 = (wi & ((1u << k2) - 1u)) == 0;
+                }
+                f0.ok2 = ok2 ? 1u : 0u;
+            }
+        }
+        // 5. the tile one back: issue its stride-table loads
+        flight_advance<B>(p, f1);
+        // 6. the tile two back: finish and write it
+        flight_finish<GT>(p, w.cls8, f2);
+        flight_output<MODE>(p, w, f2, lane, cnt);
+        f2 = f1;
+        f1 = f0;
+    }
+    // drain
+    flight_advance<B>(p, f1);
+    flight_finish<GT>(p, w.cls8, f2);
+    flight_output<MODE>(p, w, f2, lane, cnt);
+    flight_finish<GT>(p, w.cls8, f1);
+    flight_output<MODE>(p, w, f1, lane, cnt);
+
+    if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
+    if (MODE == OUT_COUNT) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
+        if (lane == 0 && cnt) atomicAdd(p.count, cnt);
+    }
+}
+
+inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
+
+template <int B, typename GT, int MODE>
+cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
+                       cudaStream_t stream) {
+    static bool configured[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    void (*kernel)(const FilterParams);
+    if constexpr (MODE == OUT_COMPACT)
+        kernel = pfac_filter<B, GT, MODE>;
+    else
+        kernel = pfac_filter_pipe<B, GT, MODE>;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    kernel<<<grid, block, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+template <int B, typename GT>
+cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem,
+                         int max_smem, cudaStream_t stream) {
+    switch (mode) {
+        case OUT_DENSE:
+            return launch_one<B, GT, OUT_DENSE>(p, grid, block, smem, max_smem, stream);
+        case OUT_COUNT:
+            return launch_one<B, GT, OUT_COUNT>(p, grid, block, smem, max_smem, stream);
+        default:
+            return launch_one<B, GT, OUT_COMPACT>(p, grid, block, smem, max_smem, stream);
+    }
+}
+
+}  // namespace
+
+size_t filter_scratch_bytes(uint64_t n, OutMode mode) {
+    if (mode != OUT_COMPACT) return 16;
+    const uint64_t tiles = (n + 15 + kTile - 1) / kTile;
+    return static_cast<size_t>(16 + 8 * (2 * tiles + 2));
+}
+
+cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
+                          cudaStream_t stream) {
+    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || tu.stages < 2 || tu.stages > kMaxStages)
+        return cudaErrorInvalidValue;
+    if (t.B != 2 && t.B != 4) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    FilterParams p{};
+    p.text = r.text;
+    p.tv.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(r.text) & 15u);
+    p.tv.gbase = r.text - p.tv.head;
+    p.tv.n = r.n;
+    p.tv.tile = kTile;
+    uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
+    p.tv.staged = align16(kTile + H) > align16(kCodeSpan) ? align16(kTile + H) : align16(kCodeSpan);
+    const uint64_t tiles = (r.n + p.tv.head + kTile - 1) / kTile;
+    if (tiles >= 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    p.tv.ntiles = static_cast<uint32_t>(tiles);
+    // per-warp layout: stages, packed codes, unknown-byte bits, then for the
+    // compacted output a result buffer and a per-pass queue, else a per-tile queue
+    const bool pipe = mode != OUT_COMPACT;
+    const uint32_t packed_bytes = align16(kCodeSpan * t.B / 8 + 16);
+    const uint32_t inv_bytes = align16(kCodeSpan / 8 + 16);
+    const uint32_t res_bytes = pipe ? 0u : align16(kResWords * 4);
+    const uint32_t queue_bytes = align16((pipe ? kTile : kPass) * 2);
+    const uint32_t neg1_bytes = (pipe ? kTile : kResWords) * 4;
+    const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
+    uint32_t smem = 0;
+    bool fits = false;
+    for (int st = pipe ? 3 : tu.stages; st >= 2 && !fits; --st) {
+        p.nstages = static_cast<uint32_t>(st);
+        p.off_packed = p.nstages * p.tv.staged;
+        p.off_inv = p.off_packed + packed_bytes;
+        p.off_res = p.off_inv + inv_bytes;
+        p.off_queue = p.off_res + res_bytes;
+        p.warp_bytes = p.off_queue + queue_bytes;
+        p.off_neg1 = align16(kOffF + t.fbytes);
+        p.off_warp = align16(p.off_neg1 + neg1_bytes);
+        smem = p.off_warp + nw * p.warp_bytes;
+        fits = static_cast<int>(smem) <= max_smem;
+    }
+    if (!fits) return cudaErrorInvalidConfiguration;
+    p.G = t.G;
+    p.Fg = t.F;
+    p.JK = t.JK;
+    p.J2 = t.J2;
+    p.cls8g = t.cls8;
+    p.C = t.C;
+    p.W = t.W;
+    p.k = t.k;
+    p.k2 = t.k2;
+    p.base_k = t.base_k;
+    p.maxlen = t.maxlen;
+    p.fbytes = t.fbytes;
+    p.hash_shift = t.hash_shift;
+    p.hcode_lo = t.hash_code[0];
+    p.hcode_hi = t.hash_code[1];
+    p.hbyte_lo = t.hash_byte[0];
+    p.hbyte_hi = t.hash_byte[1];
+    p.out = r.out;
+    p.vec_ok = ((reinterpret_cast<uintptr_t>(r.out) - 4u * p.tv.head) & 15u) == 0;
+    p.cpos = r.pos;
+    p.cids = r.ids;
+    p.cap = r.cap;
+    p.count = r.count;
+    const size_t need = filter_scratch_bytes(r.n, mode);
+    if (!r.scratch || r.scratch_bytes < need) return cudaErrorInvalidValue;
+    p.counter = static_cast<unsigned int *>(r.scratch);
+    if (mode == OUT_COMPACT) p.status = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(r.scratch) + 16);
+    e = device_error_word(&p.err);
+    if (e != cudaSuccess) return e;
+    uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(sms);
+    const uint32_t need_ctas = (p.tv.ntiles + nw - 1) / nw;
+    if (grid > need_ctas) grid = need_ctas;
+    if (grid == 0) return cudaSuccess;
+    if (t.B == 2) {
+        if (t.gbits == 16) return launch_modes<2, int16_t>(mode, p, grid, tu.block, smem, max_smem, stream);
+        return launch_modes<2, int32_t>(mode, p, grid, tu.block, smem, max_smem, stream);
+    }
+    if (t.gbits == 16) return launch_modes<4, int16_t>(mode, p, grid, tu.block, smem, max_smem, stream);
+    return launch_modes<4, int32_t>(mode, p, grid, tu.block, smem, max_smem, stream);
+}
+
+}  // namespace pfac

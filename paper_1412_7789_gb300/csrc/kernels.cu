@@ -776,8 +776,7 @@ cudaError_t launch_modes(OutMode mode, const WarpParams &p, uint32_t grid, uint3
 template <typename GT>
 cudaError_t launch_gt(const DevTables &t, OutMode mode, const WarpParams &p, uint32_t grid, uint32_t block,
                       uint32_t smem, int max_smem, cudaStream_t stream) {
-    if (t.B == 2) return launch_modes<2, true, GT>(mode, p, grid, block, smem, max_smem, stream);
-    if (t.B == 4) return launch_modes<4, true, GT>(mode, p, grid, block, smem, max_smem, stream);
+    if (t.B != 8) return cudaErrorInvalidValue;  // small alphabets use the filter kernel
     if (t.C < 256) return launch_modes<8, true, GT>(mode, p, grid, block, smem, max_smem, stream);
     return launch_modes<8, false, GT>(mode, p, grid, block, smem, max_smem, stream);
 }
@@ -887,6 +886,22 @@ cudaError_t launch_simple(const DevTables &t, const MatchRequest &r, cudaStream_
         pfac_simple<int32_t><<<static_cast<unsigned>(blocks), 256, 0, stream>>>(
             r.text, r.n, static_cast<const int32_t *>(t.G), t.cls, t.W, t.C, r.out);
     return cudaGetLastError();
+}
+
+cudaError_t device_error_word(unsigned int **ptr) {
+    static unsigned int *cache[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!cache[dev]) {
+        void *a = nullptr;
+        e = cudaGetSymbolAddress(&a, g_dev_error);
+        if (e != cudaSuccess) return e;
+        cache[dev] = static_cast<unsigned int *>(a);
+    }
+    *ptr = cache[dev];
+    return cudaSuccess;
 }
 
 cudaError_t read_device_error(unsigned int *value) {

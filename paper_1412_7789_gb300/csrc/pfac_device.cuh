@@ -72,6 +72,11 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // Wait until every committed bulk store has finished reading shared memory.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 
+// Wait until all but the 8 most recent bulk-store groups have read shared memory.
+__device__ __forceinline__ void bulk_wait_read_keep8() {
+    asm volatile("cp.async.bulk.wait_group.read 8;" ::: "memory");
+}
+
 // Wait until every committed bulk store has completed.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
@@ -110,6 +115,98 @@ __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long 
 }
 
 __device__ __forceinline__ int decode_dead(int e) { return -e - 2; }
+
+// Geometry of one text as the tiled kernels see it: text = gbase + head,
+// gbase 16-byte aligned; tile t stages bytes [t * tile, t * tile + staged) of
+// gbase (the part inside the text).
+struct TextView {
+    const uint8_t *gbase;
+    uint64_t n;
+    uint32_t head;
+    uint32_t tile;     // positions per tile (multiple of 16)
+    uint32_t staged;   // bytes staged per tile (multiple of 16)
+    uint32_t ntiles;
+};
+
+// One thread: start the bulk copy of tile `t` into shared buffer `st`, or mark
+// the stage as the end of this warp's work (t >= ntiles).  Only the 16-byte
+// aligned part inside the text is copied; load_fringe fetches the rest.
+__device__ __forceinline__ void issue_tile(const TextView &v, uint64_t *bar, uint32_t *stile, uint8_t *st,
+                                           uint32_t t) {
+    *stile = t;
+    if (t >= v.ntiles) {
+        mbar_arrive(bar);
+        return;
+    }
+    const uint64_t tlo = static_cast<uint64_t>(t) * v.tile;
+    const uint64_t a1 = (static_cast<uint64_t>(v.head) + 15ull) & ~15ull;
+    const uint64_t a2 = (static_cast<uint64_t>(v.head) + v.n) & ~15ull;
+    const uint64_t lo = tlo > a1 ? tlo : a1;
+    const uint64_t hi = (tlo + v.staged) < a2 ? (tlo + v.staged) : a2;
+    if (a1 < a2 && lo < hi) {
+        const uint32_t bytes = static_cast<uint32_t>(hi - lo);
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_load(st + (lo - tlo), v.gbase + lo, bytes, bar);
+    } else {
+        mbar_arrive(bar);
+    }
+}
+
+// A warp: the unaligned head and tail bytes of the text that the bulk copy
+// leaves out (at most 15 each): lanes 0-15 the head, 16-31 the tail.
+__device__ __forceinline__ void load_fringe(const TextView &v, uint8_t *st, uint64_t tlo, int lane) {
+    const uint64_t head = v.head, end = head + v.n;
+    const uint64_t a1 = (head + 15ull) & ~15ull, a2 = end & ~15ull;
+    uint64_t lo, hi;
+    if (lane < 16) {
+        lo = head;
+        hi = a1 < end ? a1 : end;
+    } else {
+        lo = a1 > a2 ? a1 : a2;
+        hi = end;
+    }
+    if (lo < tlo) lo = tlo;
+    if (hi > tlo + v.staged) hi = tlo + v.staged;
+    const uint64_t idx = lo + static_cast<uint64_t>(lane & 15);
+    if (idx < hi) st[idx - tlo] = v.gbase[idx];
+}
+
+// Decoupled look-back over per-unit status words (flag in the top 2 bits:
+// 1 = this unit's count, 2 = inclusive prefix); returns the number of matches
+// in all earlier units.  A predecessor that never publishes ends the wait
+// after kWaitNs with the error latched in *err.
+__device__ __forceinline__ unsigned long long lookback(unsigned long long *status, uint32_t unit,
+                                                       unsigned long long total, unsigned int *err) {
+    constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = (1ull << 62) - 1ull;
+    if (unit == 0) {
+        st_relaxed(&status[0], kPre | total);
+        return 0ull;
+    }
+    st_relaxed(&status[unit], kAgg | total);
+    unsigned long long excl = 0;
+    int64_t pred = static_cast<int64_t>(unit) - 1;
+    unsigned long long t0 = 0;
+    while (pred >= 0) {
+        const unsigned long long v = ld_relaxed(&status[pred]);
+        const unsigned long long f = v >> 62;
+        if (f == 0) {
+            const unsigned long long now = global_timer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > kWaitNs) {
+                atomicOr(err, static_cast<unsigned>(kErrLookback));
+                break;
+            }
+            continue;
+        }
+        excl += v & kVal;
+        if (f == 2) break;
+        --pred;
+        t0 = 0;
+    }
+    st_relaxed(&status[unit], kPre | (excl + total));
+    return excl;
+}
 
 template <typename GT>
 __device__ __forceinline__ int goto_ld(const GT *G, uint32_t s, uint32_t W, uint32_t c) {

@@ -21,6 +21,9 @@ inline int32_t encode_dead(int32_t id) { return -(id + 2); }
 constexpr int16_t kJumpSlow = -32768;
 constexpr uint32_t kJumpMaxStates = 32766;
 
+// Window bits of the root filter (2- and 4-bit codes): 2^20 bits = 128 KiB.
+constexpr uint32_t kFilterBits = 20;
+
 // Longest halo staged in shared memory; walks that run past it read global memory.
 constexpr uint32_t kHaloCap = 256;
 
@@ -55,6 +58,9 @@ struct HostTables {
     uint8_t hash_code[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint8_t hash_byte[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<uint8_t> G;          // S * W entries of gbits
+    bool filter = false;             // B <= 4: root filter + window table instead of J
+    std::vector<uint32_t> F;         // filter bits, 2^(B*k) (at least 4 words)
+    std::vector<int32_t> JK;         // window table, 2^(B*k) entries
     std::vector<int16_t> J;          // 2^(B*k) (padded to 8 entries)
     std::vector<int32_t> J2;         // count_k << (B*k2)
     std::vector<uint32_t> depth_count;  // maxlen + 1
@@ -73,6 +79,10 @@ inline uint32_t window_limit(uint32_t B) { return B == 2 ? 16u : 8u; }
 struct DevTables {
     const void *G = nullptr;         // goto table
     const int16_t *J = nullptr;      // root jump table (device copy, for the bulk load)
+    const uint32_t *F = nullptr;     // root filter bits (device copy, for the bulk load)
+    const int32_t *JK = nullptr;     // window table (filter mode)
+    uint32_t fbytes = 0;             // bytes of F
+    bool filter = false;
     const int32_t *J2 = nullptr;     // stride table
     const int16_t *cls = nullptr;    // class map (256 entries)
     const uint8_t *cls8 = nullptr;   // byte class map (256 entries, 0xFF = unknown byte)
@@ -114,5 +124,13 @@ cudaError_t launch_simple(const DevTables &t, const MatchRequest &r, cudaStream_
 
 // Read and clear the device error word of the current device.
 cudaError_t read_device_error(unsigned int *value);
+
+// Device address of the current device's kernel error word.
+cudaError_t device_error_word(unsigned int **ptr);
+
+// Filter-mode kernel (2- and 4-bit codes), in filter.cu.
+cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
+                          cudaStream_t stream);
+size_t filter_scratch_bytes(uint64_t n, OutMode mode);
 
 }  // namespace pfac

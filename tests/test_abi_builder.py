@@ -140,12 +140,19 @@ def test_builder_jump_and_stride_shapes(lib):
     h = api.ac_compile(pats, host_only=True)
     info = api.ac_info(h)
     api.ac_destroy(h)
-    assert info["code_bits"] == 2 and info["jump_depth"] == 8
-    assert info["stride_depth"] == 4 and info["count_jump"] <= 32768
+    # ACGT: 2-bit codes, a root filter over 10 characters (2^20 bits), and a
+    # stride table of 4 more characters from the depth-10 states
+    assert info["code_bits"] == 2 and info["jump_depth"] == 10
+    assert info["stride_depth"] == 4
     h = api.ac_compile(pats, host_only=True, stride_bytes=1, jump_bytes=64)
     info = api.ac_info(h)
     api.ac_destroy(h)
-    assert info["stride_depth"] == 0 and info["jump_depth"] == 2
+    assert info["stride_depth"] == 0 and info["jump_depth"] == 4  # 512 filter bits
+    text, pats = workloads.zipf_byte(1 << 16, n_keywords=2000)
+    h = api.ac_compile(pats, host_only=True)
+    info = api.ac_info(h)
+    api.ac_destroy(h)
+    assert info["code_bits"] == 8 and info["jump_depth"] == 2  # 2^16 int16 jump entries
 
 
 @pytest.mark.parametrize("alphabet,shift,bits", [
