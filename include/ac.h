@@ -172,6 +172,35 @@ ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t 
 /* Select the kernel used by ac_match for this handle (default AC_KERNEL_TILED). */
 ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
 
+/*
+ * Compacted matching that allocates no device memory.  Same arguments, results
+ * and asynchrony as ac_match_compact; the difference is where its scratch
+ * lives.  ac_match_compact takes its scratch (a tile counter and one look-back
+ * word per half tile) from the stream-ordered pool with cudaMallocAsync on
+ * every call.  Some callers cannot allocate while they match: a serving process
+ * that hands all free device memory to another framework's caching allocator
+ * at start-up (later cudaMalloc / cudaMallocAsync calls then fail or take
+ * memory that allocator counts on), or a latency-critical loop whose rules
+ * forbid allocator calls after initialisation.  This entry point uses instead
+ * one file-scope device array of AC_STATIC_SCRATCH_BYTES that every GPU loading
+ * the library holds until the process exits.
+ *   - Texts longer than AC_STATIC_MAX_TEXT bytes are rejected with
+ *     AC_ERR_BUDGET before any work is enqueued.
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress, once per device); make that first call before any
+ *     stream capture.
+ *   - Every call clears the part of the array it uses (cudaMemsetAsync on
+ *     `stream`) and then launches.  All calls share the one array: calls whose
+ *     work overlaps on the GPU (different streams, or host threads without
+ *     ordering between them) race and give wrong results.  Serialise them.
+ *   - The paper has no counterpart: this is a deployment variant of the
+ *     compacted output.
+ */
+#define AC_STATIC_MAX_TEXT (64ull << 20)
+#define AC_STATIC_SCRATCH_BYTES (2u << 20)
+ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
+                                  uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream);
+
 /* Read and clear the calling device's kernel error word: AC_OK, or
  * AC_ERR_TIMEOUT when a bounded wait inside a kernel ran out.  Synchronises
  * the device. */

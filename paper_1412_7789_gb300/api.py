@@ -89,6 +89,7 @@ _SIGS = {
     "ac_match_compact": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_count": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_host": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
+    "ac_match_compact_static": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_set_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
     "ac_device_status": (ctypes.c_int, []),
     "ac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -199,6 +200,17 @@ def ac_match_compact(h: int, text, n: int, pos, ids, cap: int, count, stream=Non
     _check(lib().ac_match_compact(h, _dev_ptr(text), n, _dev_ptr(pos, 4) if cap else 0,
                                   _dev_ptr(ids, 4) if cap else 0, cap, _dev_ptr(count, 8),
                                   _stream_ptr(stream)), "ac_match_compact")
+
+
+# Largest text ac_match_compact_static accepts (AC_STATIC_MAX_TEXT in ac.h).
+AC_STATIC_MAX_TEXT = 64 << 20
+
+
+def ac_match_compact_static(h: int, text, n: int, pos, ids, cap: int, count, stream=None):
+    """ac_match_compact without device allocation (shared static scratch; see ac.h)."""
+    _check(lib().ac_match_compact_static(h, _dev_ptr(text), n, _dev_ptr(pos, 4) if cap else 0,
+                                         _dev_ptr(ids, 4) if cap else 0, cap, _dev_ptr(count, 8),
+                                         _stream_ptr(stream)), "ac_match_compact_static")
 
 
 def ac_count(h: int, text, n: int, count, stream=None):

@@ -116,6 +116,16 @@ ac_status cuda_status(cudaError_t e) {
 
 }  // namespace
 
+namespace pfac {
+// The device tables of a handle, for entry points outside this file.
+const DevTables *handle_tables(ac_handle h, int *device, bool *host_only) {
+    if (!h) return nullptr;
+    *device = h->device;
+    *host_only = h->host_only;
+    return &h->dev;
+}
+}  // namespace pfac
+
 extern "C" {
 
 void ac_default_options(ac_options *opt) {

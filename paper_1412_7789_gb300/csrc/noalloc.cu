@@ -1,0 +1,79 @@
+// ac_match_compact_static: the compacted matching call without any device
+// allocation.  Its scratch (the tile counter and the per-tile look-back words
+// of the ordered compaction) lives in one file-scope device array that every
+// call shares.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "ac.h"
+#include "pfac_internal.h"
+
+// Handle internals needed here (defined in api.cpp).
+namespace pfac {
+const DevTables *handle_tables(ac_handle h, int *device, bool *host_only);
+}
+
+namespace {
+
+// Scratch for texts of up to AC_STATIC_MAX_TEXT bytes, shared by all calls on a
+// device.  Every GPU that loads the library holds it until the process exits.
+__device__ __align__(256) unsigned char g_compact_scratch[AC_STATIC_SCRATCH_BYTES];
+
+std::mutex g_mu;
+void *g_scratch_ptr[64] = {nullptr};  // device address of g_compact_scratch, per device
+
+// The device address of the array on the current device, looked up once per
+// device (host code sees only a host-side stand-in for the symbol).
+cudaError_t scratch_address(int dev, void **out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_compact_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
+                                             uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream) {
+    int device = 0;
+    bool host_only = true;
+    const pfac::DevTables *t = pfac::handle_tables(h, &device, &host_only);
+    if (!t || host_only) return AC_ERR_INVALID_ARG;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return AC_ERR_CUDA;
+    if (cur != device || cur < 0 || cur >= 64) return AC_ERR_INVALID_ARG;
+    if (!d_count || (cap > 0 && (!d_pos || !d_ids))) return AC_ERR_INVALID_ARG;
+    if (n > AC_STATIC_MAX_TEXT) return AC_ERR_BUDGET;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st) == cudaSuccess ? AC_OK : AC_ERR_CUDA;
+    if (!d_text) return AC_ERR_INVALID_ARG;
+    pfac::Tuning tu;
+    const size_t bytes = t->filter ? pfac::filter_scratch_bytes(n, pfac::OUT_COMPACT)
+                                   : pfac::scratch_bytes(*t, n, pfac::OUT_COMPACT, tu);
+    if (bytes > AC_STATIC_SCRATCH_BYTES) return AC_ERR_BUDGET;
+    void *scratch = nullptr;
+    if (scratch_address(cur, &scratch) != cudaSuccess) return AC_ERR_CUDA;
+    // the counter and look-back words must start at zero; the array keeps the
+    // previous call's contents
+    if (cudaMemsetAsync(scratch, 0, bytes, st) != cudaSuccess) return AC_ERR_CUDA;
+    pfac::MatchRequest r;
+    r.text = d_text;
+    r.n = n;
+    r.pos = d_pos;
+    r.ids = d_ids;
+    r.cap = cap;
+    r.count = reinterpret_cast<unsigned long long *>(d_count);
+    r.scratch = scratch;
+    r.scratch_bytes = bytes;
+    const cudaError_t e = t->filter ? pfac::launch_filter(*t, r, pfac::OUT_COMPACT, tu, st)
+                                    : pfac::launch_tiled(*t, r, pfac::OUT_COMPACT, tu, st);
+    if (e == cudaSuccess) return AC_OK;
+    if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) return AC_ERR_INVALID_ARG;
+    return AC_ERR_CUDA;
+}
