@@ -31,6 +31,21 @@ sys.path.insert(0, ROOT)
 METRIC = "GB/s text scanned (1 GB300) & % HBM roofline; batch/serve p50/p99 vs plain PFAC"
 GIB = 1 << 30
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
+# ncu capture of the kernel as it stands, keyed by (workload, text bytes,
+# kernel): the 256 MiB capture summarised in
+# profiles/pfac_filter_pipe_acgt_256mib_full.md, scaled by 4 to the 1 GiB
+# launch.  Drop an entry whenever its kernel changes.
+KNOWN_TRAFFIC = {("sweep", GIB, "pfac_filter_pipe"): 5.416e9}
+
+
+def kernel_name(info: dict, out_kind: str, kernel: str) -> str:
+    if kernel == "simple":
+        return "pfac_simple"
+    if info["code_bits"] <= 4:
+        return "pfac_filter" if out_kind == "compact" else "pfac_filter_pipe"
+    return "pfac_match"
+
 
 def load_peaks():
     try:
@@ -291,10 +306,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     launch_ms = statistics.mean(per)
     achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
     value = world * n * args.steps / (t_ms * 1e-3) / 1e9
+    kname = kernel_name(info, out_kind, args.kernel)
+    traffic = args.traffic
+    if traffic is None:
+        traffic = KNOWN_TRAFFIC.get((args.workload, n, kname))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": args.traffic, "peak_kind": peak_kind,
-            "algorithmic_bytes_per_launch": algo_bytes,
-            "kernel": "pfac_tiled" if args.kernel != "simple" else "pfac_simple"}
+            "traffic": traffic, "peak_kind": peak_kind,
+            "algorithmic_bytes_per_launch": algo_bytes, "kernel": kname}
 
     extra = {"automaton": {k: info[k] for k in ("n_states", "n_classes", "index_width", "code_bits",
                                                   "jump_depth", "stride_depth", "max_len", "table_bytes")},
