@@ -351,6 +351,176 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         print(json.dumps(line), flush=True)
 
 
+
+# ----------------------------------------------------------------------------
+# input-size sweep and CPU/GPU crossover (the paper's section IV experiment)
+# ----------------------------------------------------------------------------
+def _median(xs):
+    return float(statistics.median(xs))
+
+
+class SweepTimer:
+    """Times one automaton on text prefixes: three GPU scopes against the
+    serial oracle on one host core."""
+
+    def __init__(self, pats, text_np, max_n):
+        import torch
+
+        import oracle
+        from paper_1412_7789_gb300 import api
+
+        self.torch, self.api = torch, api
+        self.text = text_np
+        self.a = api.Automaton(pats)
+        self.m = oracle.Machine(pats)
+        self.dev_text = torch.from_numpy(text_np[:max_n]).cuda()
+        self.dev_out = torch.empty(max(max_n, 1), dtype=torch.int32, device="cuda")
+        self.host_text = torch.from_numpy(text_np[:max_n]).pin_memory()
+        self.host_out = torch.empty(max(max_n, 1), dtype=torch.int32).pin_memory()
+        self.stream = torch.cuda.current_stream()
+
+    def gpu(self, n, reps):
+        torch, api = self.torch, self.api
+        t, o, h = self.dev_text[:n], self.dev_out[:n], self.a.handle
+        for _ in range(3):
+            api.ac_match(h, t, n, o, self.stream)
+        torch.cuda.synchronize()
+        # (i) kernel only: CUDA events around each call on its stream
+        ks = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            api.ac_match(h, t, n, o, self.stream)
+            e1.record(self.stream)
+            e1.synchronize()
+            ks.append(e0.elapsed_time(e1) * 1e-3)
+        # (ii) host call -> stream synchronised
+        cs = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            api.ac_match(h, t, n, o, self.stream)
+            self.stream.synchronize()
+            cs.append(time.perf_counter() - t0)
+        # (iii) (ii) plus the text copied in from pinned host memory and the ids copied out
+        hs = []
+        ht, ho = int(self.host_text.data_ptr()), int(self.host_out.data_ptr())
+        api.ac_match_host(h, ht, n, ho, self.stream)
+        for _ in range(max(3, reps // 4)):
+            t0 = time.perf_counter()
+            api.ac_match_host(h, ht, n, ho, self.stream)
+            hs.append(time.perf_counter() - t0)
+        return _median(ks), _median(cs), _median(hs)
+
+    def cpu(self, n, reps):
+        sample = self.text[:n]
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            self.m.pfac_ids(sample)
+            ts.append(time.perf_counter() - t0)
+        return _median(ts)
+
+    def point(self, n, cpu_reps=None):
+        reps = 100 if n <= (1 << 20) else 20
+        if cpu_reps is None:
+            cpu_reps = 5 if n <= (64 << 20) else (3 if n <= (256 << 20) else 1)
+        k, c, e = self.gpu(n, reps)
+        cs = self.cpu(n, cpu_reps)
+        return {"n": n, "gpu_kernel_s": k, "gpu_call_s": c, "gpu_e2e_s": e, "cpu_s": cs,
+                "gpu_kernel_gbs": n / k / 1e9, "gpu_e2e_gbs": n / e / 1e9, "cpu_gbs": n / cs / 1e9}
+
+    def close(self):
+        self.a.close()
+        self.m.close()
+
+
+def _crossing(points, key):
+    """Smallest n where the GPU scope is no slower than the CPU, log-interpolated
+    between the two sizes that bracket it (None if the GPU never wins; the
+    smallest size if it always does)."""
+    prev = None
+    for p in points:
+        d = p[key] - p["cpu_s"]
+        if d <= 0:
+            if prev is None:
+                return {"n": p["n"], "bracket": [None, p["n"]], "below_range": True}
+            pd = prev[key] - prev["cpu_s"]
+            f = pd / (pd - d) if pd != d else 0.0
+            import math
+
+            x = math.exp(math.log(prev["n"]) + (math.log(p["n"]) - math.log(prev["n"])) * f)
+            return {"n": x, "bracket": [prev["n"], p["n"]], "below_range": False}
+        prev = p
+    return None
+
+
+def _refine(timer, lo, hi, key, count=20):
+    """The paper's second, finer sweep between the bracketing sizes."""
+    import math
+
+    sizes = sorted({int(round(math.exp(math.log(lo) + (math.log(hi) - math.log(lo)) * j / (count - 1))))
+                    for j in range(count)})
+    pts = [timer.point(n) for n in sizes]
+    return pts, _crossing(pts, key)
+
+
+def run_sweep(args):
+    from paper_1412_7789_gb300 import build, workloads as W
+
+    build.build()
+    import torch
+
+    torch.cuda.set_device(0)
+    res = {"metric": "CPU/GPU crossover text size and GB/s over the input-size sweep", "unit": "bytes",
+           "cpu": "oracle, one host core (serial Aho-Corasick, paper section II)",
+           "gpu_scopes": {"gpu_kernel_s": "kernel only (CUDA events)",
+                          "gpu_call_s": "host call to stream synchronised (includes the launch)",
+                          "gpu_e2e_s": "call with the text copied in from pinned host memory and ids out"}}
+    try:
+        import multiprocessing
+
+        res["host_cores"] = multiprocessing.cpu_count()
+        res["host_cpu"] = subprocess.run(["lscpu"], capture_output=True, text=True).stdout.split("Model name:")[1].split("\n")[0].strip()
+    except Exception:
+        pass
+    max_n = args.sweep_max
+    text, pats = W.sweep_acgt(max_n)
+    timer = SweepTimer(pats, text, max_n)
+    coarse = []
+    for n in [4096 * 4 ** j for j in range(10) if 4096 * 4 ** j <= max_n]:
+        coarse.append(timer.point(n))
+        print("sweep n=%d %s" % (n, json.dumps(coarse[-1])), file=sys.stderr, flush=True)
+    res["sweep"] = coarse
+    res["crossover"] = {}
+    for key in ("gpu_kernel_s", "gpu_call_s", "gpu_e2e_s"):
+        c = _crossing(coarse, key)
+        if c is not None and c["below_range"]:
+            # extend below the smallest coarse size
+            pts = [timer.point(n) for n in (16, 64, 256, 1024, 4096)]
+            c = _crossing(pts, key)
+            if c is not None and not c["below_range"]:
+                _, c2 = _refine(timer, c["bracket"][0], c["bracket"][1], key)
+                c = c2 or c
+        elif c is not None:
+            _, c2 = _refine(timer, c["bracket"][0], c["bracket"][1], key)
+            c = c2 or c
+        res["crossover"][key] = c
+    timer.close()
+    # paper mode: the alphabet text with 5 and 10 permutation keywords, at the
+    # paper's sizes (section IV: 16,375..671,375 and 1,310..53,710 bytes)
+    paper = {}
+    sizes = sorted(set([16375 + 32750 * j for j in range(21)] + [1310 + 2620 * j for j in range(21)]))
+    ptext = W.paper_text(max(sizes))
+    for count in (5, 10):
+        pt = SweepTimer(W.paper_keywords(count, seed=0), ptext, max(sizes))
+        pts = [pt.point(n) for n in sizes]
+        paper[str(count)] = {"points": pts,
+                             "crossover": {key: _crossing(pts, key) for key in ("gpu_kernel_s", "gpu_call_s", "gpu_e2e_s")}}
+        pt.close()
+    res["paper_mode"] = paper
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,8 +536,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch from an ncu capture of the current kernel")
+    ap.add_argument("--sweep", action="store_true",
+                    help="input-size sweep and CPU/GPU crossover instead of the throughput line")
+    ap.add_argument("--sweep-max", type=int, default=GIB)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.sweep:
+        run_sweep(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
