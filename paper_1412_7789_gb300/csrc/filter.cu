@@ -279,10 +279,13 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Wa
     return found;
 }
 
+// One pass: classify, filter, finish the survivors, and write (dense) or count
+// the results.  For the compacted output the results stay staged and the
+// queue keeps the survivors (ascending position); returns their number.
 template <int B, typename GT, int MODE>
-__device__ __forceinline__ void filter_pass(const FilterParams &p, const WarpSmem &w, int64_t gpb, bool interior,
-                                            uint32_t tile, uint32_t h, int lane, unsigned long long &cnt,
-                                            bool &res_busy) {
+__device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const WarpSmem &w, int64_t gpb,
+                                                bool interior, uint32_t h, int lane, unsigned long long &cnt,
+                                                bool &res_busy) {
     const int64_t n = static_cast<int64_t>(p.tv.n);
     const uint32_t k = p.k;
     const uint32_t pbase = h * kPass;
@@ -439,56 +442,73 @@ __device__ __forceinline__ void filter_pass(const FilterParams &p, const WarpSme
                 }
             }
         }
-    } else if (MODE == OUT_COMPACT) {
-        // The matches of the pass are survivors with a result >= 0, and the
-        // queue lists survivors in ascending position: rank them by ballot.
-        uint32_t unit_total = 0;
-        if (found) {
-            for (uint32_t b = 0; b < total; b += 32) {
-                const uint32_t qi = b + lane;
-                const int v = qi < total ? w.res[(w.queue[qi] & 0x7FFFu) - pbase] : -1;
-                unit_total += __popc(__ballot_sync(kFull, v >= 0));
-            }
-        }
-        unsigned long long pre = 0;
-        const uint32_t unit = 2u * tile + h;
-        if (lane == 0) {
-            pre = lookback(p.status, unit, unit_total, p.err);
-            if (unit == 2u * p.tv.ntiles - 1u) *p.count = pre + unit_total;
-        }
-        pre = __shfl_sync(kFull, pre, 0);
-        if (found) {
-            unsigned long long o = pre;
-            for (uint32_t b = 0; b < total; b += 32) {
-                const uint32_t qi = b + lane;
-                uint32_t i = 0;
-                int v = -1;
-                if (qi < total) {
-                    i = w.queue[qi] & 0x7FFFu;
-                    v = w.res[i - pbase];
-                }
-                const uint32_t m = __ballot_sync(kFull, v >= 0);
-                if (v >= 0) {
-                    const unsigned long long at = o + __popc(m & ((1u << lane) - 1u));
-                    if (at < p.cap) {
-                        p.cpos[at] = static_cast<uint32_t>(gpb + i);
-                        p.cids[at] = static_cast<uint32_t>(v);
-                    }
-                }
-                o += __popc(m);
-            }
-        }
     }
     __syncwarp();
+    return total;
 }
 
-template <int B, typename GT, int MODE>
-__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter(const FilterParams p) {
+// ---------------------------------------------------------------------------
+// Compacted output.  The ascending (pos, id) list needs every match's rank, so
+// the unit of ordering is a CTA round: the CTA claims a chunk of nw
+// consecutive one-pass tiles (one per warp); each warp matches its tile,
+// keeping the survivors (the only positions that can match) queued in
+// ascending order with their results staged, and counts its matches; one warp
+// scans the counts and places the chunk with a warp-wide decoupled look-back;
+// then every warp writes its matches.  Chunks are claimed in increasing order
+// by running CTAs, so the look-back always ends, and with one chunk per CTA in
+// flight it stays short.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kOffChunk = 832;   // 2 x uint32: chunk held by each stage
+constexpr uint32_t kOffCounts = 840;  // kMaxWarps x uint32: matches per warp
+constexpr uint32_t kOffBase = 904;    // kMaxWarps x uint32: output offset per warp (n < 2^32)
+constexpr uint32_t kOffAbort = kOffBase + kMaxWarps * 4;
+static_assert(kOffAbort + 4 <= kOffCls, "compaction header overlaps the class map");
+
+// Survivors of the pass whose walk found a keyword.
+__device__ __forceinline__ uint32_t count_found(const WarpSmem &w, uint32_t total, int lane) {
+    uint32_t c = 0;
+    for (uint32_t b = 0; b < total; b += 32) {
+        const uint32_t qi = b + lane;
+        const int v = qi < total ? w.res[w.queue[qi] & 0x7FFFu] : -1;
+        c += __popc(__ballot_sync(kFull, v >= 0));
+    }
+    return c;
+}
+
+// Write them in ascending position from output offset o.
+__device__ __forceinline__ void write_found(const FilterParams &p, const WarpSmem &w, uint32_t total, int64_t gpb,
+                                            unsigned long long o, int lane) {
+    for (uint32_t b = 0; b < total; b += 32) {
+        const uint32_t qi = b + lane;
+        uint32_t i = 0;
+        int v = -1;
+        if (qi < total) {
+            i = w.queue[qi] & 0x7FFFu;
+            v = w.res[i];
+        }
+        const uint32_t m = __ballot_sync(kFull, v >= 0);
+        if (v >= 0) {
+            const unsigned long long at = o + __popc(m & ((1u << lane) - 1u));
+            if (at < p.cap) {
+                p.cpos[at] = static_cast<uint32_t>(gpb + i);
+                p.cids[at] = static_cast<uint32_t>(v);
+            }
+        }
+        o += __popc(m);
+    }
+}
+
+template <int B, typename GT>
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_compact(const FilterParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
     uint32_t *stile = reinterpret_cast<uint32_t *>(smem + kOffStageTile) + warp * kMaxStages;
+    volatile uint32_t *chunk = reinterpret_cast<uint32_t *>(smem + kOffChunk);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(smem + kOffCounts);
+    uint32_t *bases = reinterpret_cast<uint32_t *>(smem + kOffBase);
+    volatile uint32_t *abort_flag = reinterpret_cast<uint32_t *>(smem + kOffAbort);
     uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
     WarpSmem w;
     w.cls8 = smem + kOffCls;
@@ -498,16 +518,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter(const FilterParams p
     w.inv = reinterpret_cast<uint16_t *>(wreg + p.off_inv);
     w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
     w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
-    w.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
-    const uint32_t nst = p.nstages;
+    w.neg1 = nullptr;
+    const uint32_t nchunks = (p.tv.ntiles + nw - 1) / nw;
 
-    for (uint32_t i = threadIdx.x; i < kResWords; i += blockDim.x) reinterpret_cast<int32_t *>(smem + p.off_neg1)[i] = -1;
-    fence_proxy_async_smem();  // the constant buffer is read by bulk stores
     if (threadIdx.x == 0) {
         mbar_init(jbar, 1);
         uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
         for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
         fence_mbar_init();
+        *abort_flag = 0;
+        chunk[0] = atomicAdd(p.counter, 1u);
+        chunk[1] = atomicAdd(p.counter, 1u);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -515,64 +536,76 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter(const FilterParams p
         bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
         bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
     }
-    // Tiles are claimed from a global counter so that a warp meeting an
-    // expensive tile (long walks) stops taking work while the others go on.
-    // The compacted output claims every tile (ordered look-back needs tiles
-    // handed out in increasing order to running warps); the other outputs
-    // hand each warp its first tile statically (warp-major numbering, so
-    // neighbouring tiles land on different SMs) and claim the rest.
-    const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
-    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
-    auto next_tile = [&](uint32_t it) -> uint32_t {
-        if (MODE == OUT_COMPACT) return atomicAdd(p.counter, 1u);
-        if (it == 0) return gw < p.tv.ntiles ? static_cast<uint32_t>(gw) : 0xFFFFFFFFu;
-        const uint64_t t = GW + atomicAdd(p.counter, 1u);
-        return t < p.tv.ntiles ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+    auto tile_of = [&](uint32_t c) -> uint32_t {
+        const uint64_t t = static_cast<uint64_t>(c) * nw + warp;
+        return (c < nchunks && t < p.tv.ntiles) ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
     };
     if (lane == 0)
-        for (uint32_t s = 0; s < nst; ++s) issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, next_tile(s));
+        for (uint32_t s = 0; s < 2; ++s) issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, tile_of(chunk[s]));
 
-    unsigned long long cnt = 0;
+    unsigned long long unused = 0;
     bool res_busy = false;
     bool ok = mbar_wait(jbar, 0);
-    for (uint32_t it = 0;; ++it) {
-        const uint32_t s = it % nst;
-        ok = ok && mbar_wait(&bars[s], (it / nst) & 1u);
-        if (!__all_sync(kFull, ok)) {
+    for (uint32_t r = 0;; ++r) {
+        const uint32_t s = r & 1u;
+        const uint32_t c = chunk[s];
+        if (c >= nchunks) break;  // the same value for every warp of the CTA
+        ok = ok && mbar_wait(&bars[s], (r >> 1) & 1u);
+        ok = __all_sync(kFull, ok);
+        const uint32_t tile = stile[s];
+        uint32_t m = 0, total = 0;
+        int64_t gpb = 0;
+        if (ok && tile < p.tv.ntiles) {
+            w.st = wreg + s * p.tv.staged;
+            const uint64_t tlo = static_cast<uint64_t>(tile) * p.tv.tile;
+            gpb = static_cast<int64_t>(tlo) - p.tv.head;
+            const bool interior =
+                gpb >= 0 && gpb + static_cast<int64_t>(p.tv.staged) <= static_cast<int64_t>(p.tv.n);
+            if (!interior) {
+                load_fringe(p.tv, w.st, tlo, lane);
+                __syncwarp();
+            }
+            total = filter_pass<B, GT, OUT_COMPACT>(p, w, gpb, interior, 0, lane, unused, res_busy);
+            m = count_found(w, total, lane);
+        }
+        if (lane == 0) {
+            counts[warp] = m;
+            if (!ok) *abort_flag = 1;
+        }
+        __syncthreads();
+        if (*abort_flag) {
             // A copy never completed: latch the error, let this warp's copies in
-            // flight finish (bounded), and leave.
+            // flight finish (bounded), and leave (every warp of the CTA does).
             if (lane == 0) {
-                bulk_wait_all();
                 atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
                 mbar_wait(jbar, 0);
-                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u);
+                for (uint32_t j = r; j < r + 2; ++j) mbar_wait(&bars[j & 1u], (j >> 1) & 1u);
             }
             return;
         }
-        const uint32_t tile = stile[s];
-        if (tile >= p.tv.ntiles) break;
-        w.st = wreg + s * p.tv.staged;
-        const uint64_t tlo = static_cast<uint64_t>(tile) * kTile;
-        const int64_t gpb = static_cast<int64_t>(tlo) - p.tv.head;
-        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.tv.staged) <= static_cast<int64_t>(p.tv.n);
-        if (!interior) {
-            load_fringe(p.tv, w.st, tlo, lane);
-            __syncwarp();
+        if (warp == 0) {
+            const uint32_t mine = lane < nw ? counts[lane] : 0u;
+            uint32_t inc = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                if (lane >= d) inc += y;
+            }
+            const uint32_t ctotal = __shfl_sync(kFull, inc, 31);
+            const unsigned long long pre = lookback_warp(p.status, c, ctotal, p.err, lane);
+            if (lane < nw) bases[lane] = static_cast<uint32_t>(pre + (inc - mine));
+            if (lane == 0) {
+                if (c == nchunks - 1) *p.count = pre + ctotal;
+                chunk[s] = atomicAdd(p.counter, 1u);  // this stage's next chunk
+            }
         }
-#pragma unroll 1
-        for (uint32_t h = 0; h < kTile / kPass; ++h)
-            filter_pass<B, GT, MODE>(p, w, gpb, interior, tile, h, lane, cnt, res_busy);
+        __syncthreads();
+        if (tile < p.tv.ntiles && m) write_found(p, w, total, gpb, bases[warp], lane);
+        __syncwarp();
         if (lane == 0) {
             fence_proxy_async_smem();
-            issue_tile(p.tv, &bars[s], &stile[s], w.st, next_tile(it + nst));
+            issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, tile_of(chunk[s]));
         }
-    }
-
-    if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
-    if (MODE == OUT_COUNT) {
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
-        if (lane == 0 && cnt) atomicAdd(p.count, cnt);
     }
 }
 
@@ -1009,7 +1042,7 @@ cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uin
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     void (*kernel)(const FilterParams);
     if constexpr (MODE == OUT_COMPACT)
-        kernel = pfac_filter<B, GT, MODE>;
+        kernel = pfac_filter_compact<B, GT>;
     else
         kernel = pfac_filter_pipe<B, GT, MODE>;
     if (!configured[dev]) {
@@ -1038,8 +1071,10 @@ cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uin
 
 size_t filter_scratch_bytes(uint64_t n, OutMode mode) {
     if (mode != OUT_COMPACT) return 16;
-    const uint64_t tiles = (n + 15 + kTile - 1) / kTile;
-    return static_cast<size_t>(16 + 8 * (2 * tiles + 2));
+    // tile counter and one look-back word per chunk; sized per one-pass tile,
+    // which covers any number of warps per CTA
+    const uint64_t tiles = (n + 15 + kPass - 1) / kPass;
+    return static_cast<size_t>(16 + 8 * (tiles + 2));
 }
 
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
@@ -1057,10 +1092,13 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.tv.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(r.text) & 15u);
     p.tv.gbase = r.text - p.tv.head;
     p.tv.n = r.n;
-    p.tv.tile = kTile;
+    // warp tiles: two passes, or one for the compacted output (a warp keeps one
+    // pass of results staged until its CTA round is placed)
+    const uint32_t tlen = mode == OUT_COMPACT ? kPass : kTile;
+    p.tv.tile = tlen;
     uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
-    p.tv.staged = align16(kTile + H) > align16(kCodeSpan) ? align16(kTile + H) : align16(kCodeSpan);
-    const uint64_t tiles = (r.n + p.tv.head + kTile - 1) / kTile;
+    p.tv.staged = align16(tlen + H) > align16(tlen + 16) ? align16(tlen + H) : align16(tlen + 16);
+    const uint64_t tiles = (r.n + p.tv.head + tlen - 1) / tlen;
     if (tiles >= 0x7FFFFFFFull) return cudaErrorInvalidValue;
     p.tv.ntiles = static_cast<uint32_t>(tiles);
     // per-warp layout: stages, packed codes, unknown-byte bits, then for the
@@ -1074,7 +1112,7 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
     uint32_t smem = 0;
     bool fits = false;
-    for (int st = pipe ? 3 : tu.stages; st >= 2 && !fits; --st) {
+    for (int st = pipe ? 3 : 2; st >= 2 && !fits; --st) {
         p.nstages = static_cast<uint32_t>(st);
         p.off_packed = p.nstages * p.tv.staged;
         p.off_inv = p.off_packed + packed_bytes;

@@ -61,7 +61,8 @@ struct WarpParams {
     const uint8_t *gbase;   // text rounded down to 16 bytes
     uint64_t n;
     uint32_t head;          // text - gbase
-    uint32_t SLW;           // staged bytes per warp tile (kTW + halo)
+    uint32_t SLW;           // staged bytes per warp tile (tile + halo)
+    uint32_t tw;            // positions per warp tile (kTW, or kPass for the compacted output)
     uint32_t nstages, ntiles;
     const void *G;
     const int16_t *Jg;
@@ -101,7 +102,7 @@ __device__ __forceinline__ void issue_stage(const WarpParams &p, uint64_t *bar, 
         mbar_arrive(bar);
         return;
     }
-    const uint64_t tlo = static_cast<uint64_t>(tile) * kTW;
+    const uint64_t tlo = static_cast<uint64_t>(tile) * p.tw;
     const uint64_t a1 = (static_cast<uint64_t>(p.head) + 15ull) & ~15ull;
     const uint64_t a2 = (static_cast<uint64_t>(p.head) + p.n) & ~15ull;
     const uint64_t lo = tlo > a1 ? tlo : a1;
@@ -267,41 +268,6 @@ __device__ __forceinline__ bool fetch_code(const WarpParams &p, const WarpSmem &
     if (v == 0xFFu) return false;
     c = v;
     return true;
-}
-
-// Decoupled look-back over per-unit status words; returns the number of
-// matches in all earlier units.
-__device__ __forceinline__ unsigned long long lookback(unsigned long long *status, uint32_t unit,
-                                                       unsigned long long total) {
-    constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = (1ull << 62) - 1ull;
-    if (unit == 0) {
-        st_relaxed(&status[0], kPre | total);
-        return 0ull;
-    }
-    st_relaxed(&status[unit], kAgg | total);
-    unsigned long long excl = 0;
-    int64_t pred = static_cast<int64_t>(unit) - 1;
-    unsigned long long t0 = 0;
-    while (pred >= 0) {
-        const unsigned long long v = ld_relaxed(&status[pred]);
-        const unsigned long long f = v >> 62;
-        if (f == 0) {
-            const unsigned long long now = global_timer();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > kWaitNs) {
-                atomicOr(&g_dev_error, static_cast<unsigned>(kErrLookback));
-                break;
-            }
-            continue;
-        }
-        excl += v & kVal;
-        if (f == 2) break;
-        --pred;
-        t0 = 0;
-    }
-    st_relaxed(&status[unit], kPre | (excl + total));
-    return excl;
 }
 
 // Finish up to SLOTS * 32 queued survivors (entries base.. of the queue, `avail`
@@ -527,59 +493,8 @@ __device__ __forceinline__ void match_pass(const WarpParams &p, const WarpSmem &
                     if ((valid >> (4 * g + r)) & 1u) p.out[gp0 + r] = rr[r];
             }
         }
-    } else if (MODE == OUT_COMPACT) {
-        int rr[16];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const int4 r4 = reinterpret_cast<const int4 *>(w.res)[32 * g + lane];
-            rr[4 * g] = r4.x;
-            rr[4 * g + 1] = r4.y;
-            rr[4 * g + 2] = r4.z;
-            rr[4 * g + 3] = r4.w;
-        }
-        uint32_t mine = 0;  // 4 fields of 8 bits: matches per group (<= 4)
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            uint32_t cg = 0;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) cg += ((valid >> (4 * g + r)) & 1u) && rr[4 * g + r] >= 0 ? 1u : 0u;
-            mine |= cg << (8 * g);
-        }
-        uint32_t sc = mine;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_up_sync(kFull, sc, d);
-            if (lane >= d) sc += y;
-        }
-        const uint32_t tot = __shfl_sync(kFull, sc, 31);  // fields <= 128: no carries
-        const uint32_t excl = sc - mine;
-        const unsigned long long unit_total =
-            (tot & 0xFFu) + ((tot >> 8) & 0xFFu) + ((tot >> 16) & 0xFFu) + (tot >> 24);
-        unsigned long long pre = 0;
-        const uint32_t unit = 2u * tile + h;
-        if (lane == 0) {
-            pre = lookback(p.status, unit, unit_total);
-            if (unit == 2u * p.ntiles - 1u) *p.count = pre + unit_total;
-        }
-        pre = __shfl_sync(kFull, pre, 0);
-        unsigned long long base = pre;
-#pragma unroll
-        for (int g = 0; g < 4; ++g) {
-            const uint32_t i0 = ibase + 128u * g;
-            unsigned long long o = base + ((excl >> (8 * g)) & 0xFFu);
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                if (((valid >> (4 * g + r)) & 1u) && rr[4 * g + r] >= 0) {
-                    if (o < p.cap) {
-                        p.cpos[o] = static_cast<uint32_t>(gpb + i0 + r);
-                        p.cids[o] = static_cast<uint32_t>(rr[4 * g + r]);
-                    }
-                    ++o;
-                }
-            }
-            base += (tot >> (8 * g)) & 0xFFu;
-        }
     }
+    // compacted output: the staged results are ranked per CTA round (pfac_match_compact)
     __syncwarp();
 }
 
@@ -617,12 +532,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match(const WarpParams p) {
     const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
     // Tiles are claimed from a global counter, so a warp that meets an
-    // expensive tile (long walks) stops taking work while the others go on.
-    // The compacted output claims every tile (ordered look-back needs tiles
-    // handed out in increasing order to running warps); the other outputs
-    // hand each warp its first tile statically and claim the rest.
+    // expensive tile (long walks) stops taking work while the others go on;
+    // each warp's first tile is handed out statically.
     auto next_tile = [&](uint32_t it) -> uint32_t {
-        if (MODE == OUT_COMPACT) return atomicAdd(p.counter, 1u);
         if (it == 0) return gw < p.ntiles ? static_cast<uint32_t>(gw) : 0xFFFFFFFFu;
         const uint64_t t = GW + atomicAdd(p.counter, 1u);
         return t < p.ntiles ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
@@ -649,7 +561,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match(const WarpParams p) {
         const uint32_t tile = stile[s];
         if (tile >= p.ntiles) break;
         w.st = wreg + s * p.SLW;
-        const uint64_t tlo = static_cast<uint64_t>(tile) * kTW;
+        const uint64_t tlo = static_cast<uint64_t>(tile) * p.tw;
         const int64_t gpb = static_cast<int64_t>(tlo) - p.head;
         const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.SLW) <= static_cast<int64_t>(p.n);
         if (!interior) {
@@ -674,6 +586,188 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match(const WarpParams p) {
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
         if (lane == 0 && cnt) atomicAdd(p.count, cnt);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Compacted output.  The ascending (pos, id) list needs every match's rank, so
+// the unit of ordering is a CTA round: the CTA claims a chunk of nw
+// consecutive one-pass tiles (one per warp), each warp matches its tile into
+// shared memory and counts its matches, then one warp scans the counts and
+// places the chunk with a warp-wide decoupled look-back, and every warp writes
+// its matches.  Chunks are claimed in increasing order by running CTAs, so the
+// look-back always ends; with one chunk per CTA in flight it stays short.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kOffChunk = 832;   // 2 x uint32: chunk held by each stage
+constexpr uint32_t kOffCounts = 840;  // kMaxWarps x uint32: matches per warp
+constexpr uint32_t kOffBase = 904;    // kMaxWarps x uint32: output offset per warp (n < 2^32)
+constexpr uint32_t kOffAbort = kOffBase + kMaxWarps * 4;
+static_assert(kOffAbort + 4 <= kOffCls, "compaction header overlaps the class map");
+
+// Matches among the staged results of a pass (positions outside the text hold -1).
+__device__ __forceinline__ uint32_t count_staged(const int32_t *res, int lane) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int4 r4 = reinterpret_cast<const int4 *>(res)[32 * g + lane];
+        c += (r4.x >= 0) + (r4.y >= 0) + (r4.z >= 0) + (r4.w >= 0);
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_xor_sync(kFull, c, d);
+    return c;
+}
+
+// Write the staged matches of a pass, in ascending position, from output offset base.
+__device__ __forceinline__ void write_staged(const WarpParams &p, const int32_t *res, int64_t gpb,
+                                             unsigned long long base, int lane) {
+    int rr[16];
+    uint32_t mine = 0;  // 4 fields of 8 bits: matches per group of 4 (<= 4)
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int4 r4 = reinterpret_cast<const int4 *>(res)[32 * g + lane];
+        rr[4 * g] = r4.x;
+        rr[4 * g + 1] = r4.y;
+        rr[4 * g + 2] = r4.z;
+        rr[4 * g + 3] = r4.w;
+        const uint32_t cg = (r4.x >= 0) + (r4.y >= 0) + (r4.z >= 0) + (r4.w >= 0);
+        mine |= cg << (8 * g);
+    }
+    uint32_t sc = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, sc, d);
+        if (lane >= d) sc += y;
+    }
+    const uint32_t tot = __shfl_sync(kFull, sc, 31);  // fields <= 128: no carries
+    const uint32_t excl = sc - mine;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const uint32_t i0 = 4u * (32u * g + lane);
+        unsigned long long o = base + ((excl >> (8 * g)) & 0xFFu);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            if (rr[4 * g + r] >= 0) {
+                if (o < p.cap) {
+                    p.cpos[o] = static_cast<uint32_t>(gpb + i0 + r);
+                    p.cids[o] = static_cast<uint32_t>(rr[4 * g + r]);
+                }
+                ++o;
+            }
+        }
+        base += (tot >> (8 * g)) & 0xFFu;
+    }
+}
+
+template <int B, bool INV, typename GT>
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_match_compact(const WarpParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
+    uint32_t *stile = reinterpret_cast<uint32_t *>(smem + kOffStageTile) + warp * kMaxStages;
+    volatile uint32_t *chunk = reinterpret_cast<uint32_t *>(smem + kOffChunk);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(smem + kOffCounts);
+    uint32_t *bases = reinterpret_cast<uint32_t *>(smem + kOffBase);
+    volatile uint32_t *abort_flag = reinterpret_cast<uint32_t *>(smem + kOffAbort);
+    uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
+    WarpSmem w;
+    w.cls8 = smem + kOffCls;
+    w.jbase = smem + kOffJ;
+    w.st = wreg;
+    w.packed = reinterpret_cast<uint32_t *>(wreg + p.off_packed);
+    w.inv = reinterpret_cast<uint32_t *>(wreg + p.off_inv);
+    w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
+    w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
+    const uint32_t nchunks = (p.ntiles + nw - 1) / nw;
+
+    if (threadIdx.x == 0) {
+        mbar_init(jbar, 1);
+        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
+        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
+        fence_mbar_init();
+        *abort_flag = 0;
+        chunk[0] = atomicAdd(p.counter, 1u);
+        chunk[1] = atomicAdd(p.counter, 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(jbar, 256u + p.jbytes);
+        bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
+        if (p.jbytes) bulk_load(smem + kOffJ, p.Jg, p.jbytes, jbar);
+    }
+    auto tile_of = [&](uint32_t c) -> uint32_t {
+        const uint64_t t = static_cast<uint64_t>(c) * nw + warp;
+        return (c < nchunks && t < p.ntiles) ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+    };
+    if (lane == 0)
+        for (uint32_t s = 0; s < 2; ++s) issue_stage(p, &bars[s], &stile[s], wreg + s * p.SLW, tile_of(chunk[s]));
+
+    unsigned long long unused = 0;
+    bool ok = mbar_wait(jbar, 0);
+    for (uint32_t r = 0;; ++r) {
+        const uint32_t s = r & 1u;
+        const uint32_t c = chunk[s];
+        if (c >= nchunks) break;  // the same value for every warp of the CTA
+        ok = ok && mbar_wait(&bars[s], (r >> 1) & 1u);
+        ok = __all_sync(kFull, ok);
+        const uint32_t tile = stile[s];
+        uint32_t m = 0;
+        int64_t gpb = 0;
+        if (ok && tile < p.ntiles) {
+            w.st = wreg + s * p.SLW;
+            const uint64_t tlo = static_cast<uint64_t>(tile) * p.tw;
+            gpb = static_cast<int64_t>(tlo) - p.head;
+            const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.SLW) <= static_cast<int64_t>(p.n);
+            if (!interior) {
+                load_fringe(p, w.st, tlo, lane);
+                __syncwarp();
+            }
+            uint32_t flags = interior ? kInterior : 0u;
+            if (B < 8 || INV) {
+                if (convert_stage<B>(p, w, gpb, interior, lane)) flags |= kClean;
+                __syncwarp();
+            }
+            match_pass<B, INV, GT, OUT_COMPACT>(p, w, gpb, flags, tile, 0, lane, unused);
+            m = count_staged(w.res, lane);
+        }
+        if (lane == 0) {
+            counts[warp] = m;
+            if (!ok) *abort_flag = 1;
+        }
+        __syncthreads();
+        if (*abort_flag) {
+            // A copy never completed: latch the error, let this warp's copies in
+            // flight finish (bounded), and leave (every warp of the CTA does).
+            if (lane == 0) {
+                atomicOr(&g_dev_error, static_cast<unsigned>(kErrTimeout));
+                mbar_wait(jbar, 0);
+                for (uint32_t j = r; j < r + 2; ++j) mbar_wait(&bars[j & 1u], (j >> 1) & 1u);
+            }
+            return;
+        }
+        if (warp == 0) {
+            const uint32_t mine = lane < nw ? counts[lane] : 0u;
+            uint32_t inc = mine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                if (lane >= d) inc += y;
+            }
+            const uint32_t total = __shfl_sync(kFull, inc, 31);
+            const unsigned long long pre = lookback_warp(p.status, c, total, &g_dev_error, lane);
+            if (lane < nw) bases[lane] = static_cast<uint32_t>(pre + (inc - mine));
+            if (lane == 0) {
+                if (c == nchunks - 1) *p.count = pre + total;
+                chunk[s] = atomicAdd(p.counter, 1u);  // this stage's next chunk
+            }
+        }
+        __syncthreads();
+        if (tile < p.ntiles) write_staged(p, w.res, gpb, bases[warp], lane);
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            issue_stage(p, &bars[s], &stile[s], wreg + s * p.SLW, tile_of(chunk[s]));
+        }
     }
 }
 
@@ -717,19 +811,25 @@ struct Geometry {
     uint32_t SLW, nstages, ntiles, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue, smem;
 };
 
-bool make_geometry(const DevTables &t, uint64_t n, uint32_t head, const Tuning &tu, int max_smem, Geometry *g) {
+// Warp tile: two passes, or one for the compacted output (a warp keeps one
+// pass of results staged until its CTA round is placed).
+inline uint32_t tile_len(OutMode mode) { return mode == OUT_COMPACT ? kPass : kTW; }
+
+bool make_geometry(const DevTables &t, uint64_t n, uint32_t head, OutMode mode, const Tuning &tu, int max_smem,
+                   Geometry *g) {
     const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
+    const uint32_t tw = tile_len(mode);
     uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
     if (H < t.k + t.k2 + 8) H = t.k + t.k2 + 8;
     H = align16(H);
-    g->SLW = kTW + H;
-    const uint64_t tiles = (n + head + kTW - 1) / kTW;
+    g->SLW = tw + H;
+    const uint64_t tiles = (n + head + tw - 1) / tw;
     if (tiles >= 0x7FFFFFFFull) return false;
     g->ntiles = static_cast<uint32_t>(tiles);
     const bool inv = t.B < 8 || t.C < 256;
     const uint32_t packed_bytes = t.B < 8 ? align16(g->SLW * t.B / 8 + 16) : 0u;
     const uint32_t inv_bytes = inv ? align16(g->SLW / 8 + 16) : 0u;
-    for (int st = tu.stages; st >= 2; --st) {
+    for (int st = mode == OUT_COMPACT ? 2 : tu.stages; st >= 2; --st) {
         g->nstages = static_cast<uint32_t>(st);
         g->off_packed = g->nstages * g->SLW;
         g->off_inv = align16(g->off_packed + packed_bytes);
@@ -750,13 +850,17 @@ cudaError_t launch_one(const WarpParams &p, uint32_t grid, uint32_t block, uint3
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    void (*kernel)(const WarpParams);
+    if constexpr (MODE == OUT_COMPACT)
+        kernel = pfac_match_compact<B, INV, GT>;
+    else
+        kernel = pfac_match<B, INV, GT, MODE>;
     if (!configured[dev]) {
-        cudaError_t e =
-            cudaFuncSetAttribute(pfac_match<B, INV, GT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
-    pfac_match<B, INV, GT, MODE><<<grid, block, smem, stream>>>(p);
+    kernel<<<grid, block, smem, stream>>>(p);
     return cudaGetLastError();
 }
 
@@ -808,10 +912,11 @@ cudaError_t device_props(DeviceProps *out) {
 
 size_t scratch_bytes(const DevTables &t, uint64_t n, OutMode mode, const Tuning &tu) {
     (void)t;
-    (void)tu;
     if (mode != OUT_COMPACT) return 16;
-    const uint64_t tiles = (n + 15 + kTW - 1) / kTW;
-    return static_cast<size_t>(16 + 8 * (2 * tiles + 2));
+    const uint64_t nw = static_cast<uint64_t>(tu.block) / 32u;
+    const uint64_t tiles = (n + 15 + kPass - 1) / kPass;
+    const uint64_t chunks = (tiles + nw - 1) / nw;
+    return static_cast<size_t>(16 + 8 * (chunks + 2));  // tile counter, one look-back word per chunk
 }
 
 cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
@@ -827,7 +932,8 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     p.gbase = r.text - p.head;
     p.n = r.n;
     Geometry g;
-    if (!make_geometry(t, r.n, p.head, tu, dp.max_smem, &g)) return cudaErrorInvalidConfiguration;
+    if (!make_geometry(t, r.n, p.head, mode, tu, dp.max_smem, &g)) return cudaErrorInvalidConfiguration;
+    p.tw = tile_len(mode);
     p.SLW = g.SLW;
     p.nstages = g.nstages;
     p.ntiles = g.ntiles;
@@ -860,7 +966,7 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     p.cids = r.ids;
     p.cap = r.cap;
     p.count = r.count;
-    const size_t need_scratch = mode == OUT_COMPACT ? 16 + 8 * (2 * static_cast<size_t>(g.ntiles) + 2) : 16;
+    const size_t need_scratch = scratch_bytes(t, r.n, mode, tu);
     if (!r.scratch || r.scratch_bytes < need_scratch) return cudaErrorInvalidValue;
     p.counter = static_cast<unsigned int *>(r.scratch);
     if (mode == OUT_COMPACT)
