@@ -142,7 +142,8 @@ ac_status ac_export_tables(ac_handle h, int16_t *cls, void *goto_, uint32_t *dep
  * Dense matching.  d_out_ids[i] = id of the longest keyword starting at
  * d_text[i] (within the n bytes), or -1.  d_text: n bytes, d_out_ids: n int32,
  * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is
- * a no-op.
+ * a no-op.  Takes 16 bytes of scratch (the tile counter) per call from the
+ * library's stream-ordered pool.
  */
 ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_out_ids, void *stream);
 
@@ -151,7 +152,9 @@ ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_ou
  * their ids.  Writes min(total, cap) entries to d_pos / d_ids (uint32 each) and
  * the true total to *d_count (a device uint64).  The caller compares the total
  * with cap and calls again with more room when it is larger.  n must be below
- * 2^32.  Uses stream-ordered device scratch (cudaMallocAsync) per call.
+ * 2^32.  Takes its scratch (a tile counter and one look-back word per chunk of
+ * tiles) from the library's stream-ordered pool (cudaMallocFromPoolAsync) on
+ * `stream`; the pool keeps the memory it grows to until the process exits.
  */
 ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
                            uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream);
@@ -176,8 +179,8 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
  * Compacted matching that allocates no device memory.  Same arguments, results
  * and asynchrony as ac_match_compact; the difference is where its scratch
  * lives.  ac_match_compact takes its scratch (a tile counter and one look-back
- * word per half tile) from the stream-ordered pool with cudaMallocAsync on
- * every call.  Some callers cannot allocate while they match: a serving process
+ * word per chunk of tiles) from a stream-ordered pool (cudaMallocFromPoolAsync)
+ * on every call.  Some callers cannot allocate while they match: a serving process
  * that hands all free device memory to another framework's caching allocator
  * at start-up (later cudaMalloc / cudaMallocAsync calls then fail or take
  * memory that allocator counts on), or a latency-critical loop whose rules

@@ -1,6 +1,7 @@
 // The C ABI declared in include/ac.h: handle lifetime, device residency of the
 // compiled tables, argument checks and dispatch to the kernels.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -88,13 +89,46 @@ ac_status check_device(ac_automaton *h) {
     return AC_OK;
 }
 
+// The library's stream-ordered pool for per-call scratch on `dev`.  It keeps
+// the memory it has grown to (release threshold: unlimited), so a call does
+// not map fresh device memory after every synchronisation, as the default
+// pool (threshold 0) would.
+cudaError_t scratch_pool(int dev, cudaMemPool_t *out) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        pools[dev] = pool;
+    }
+    *out = pools[dev];
+    return cudaSuccess;
+}
+
 // A tiled launch with its zeroed scratch (tile counter, look-back words) in
 // stream-ordered memory, so calls on different streams never share it.
 cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode, cudaStream_t st) {
     const size_t bytes = h->dev.filter ? pfac::filter_scratch_bytes(r.n, mode)
                                        : pfac::scratch_bytes(h->dev, r.n, mode, h->tuning);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(h->device, &pool);
+    if (e != cudaSuccess) return e;
     void *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync(&scratch, bytes, st);
+    e = cudaMallocFromPoolAsync(&scratch, bytes, pool, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(scratch, 0, bytes, st);
     if (e == cudaSuccess) {

@@ -385,8 +385,8 @@ __device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const War
     } else if (total <= 64) {
         found = finish_survivors<B, GT, MODE, 2>(p, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
     } else {
-        for (uint32_t b = 0; b < total; b += 128)
-            found |= finish_survivors<B, GT, MODE, 4>(p, w, gpb, interior, clean, total - b, pbase, lane, cnt, b);
+        for (uint32_t b = 0; b < total; b += 256)
+            found |= finish_survivors<B, GT, MODE, 8>(p, w, gpb, interior, clean, total - b, pbase, lane, cnt, b);
     }
     found = __any_sync(kFull, found);
     __syncwarp();
@@ -974,8 +974,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                 }
                 __syncwarp();
             }
-            for (uint32_t b = 0; b < total; b += 128)
-                finish_survivors<B, GT, MODE, 4, true>(p, w, gpb, interior, clean, total - b, 0, lane, cnt, b,
+            for (uint32_t b = 0; b < total; b += 256)
+                finish_survivors<B, GT, MODE, 8, true>(p, w, gpb, interior, clean, total - b, 0, lane, cnt, b,
                                                        kCodeSpan);
             __syncwarp();
             continue;

@@ -464,8 +464,8 @@ __device__ __forceinline__ void match_pass(const WarpParams &p, const WarpSmem &
     if (total <= 64) {
         finish_survivors<B, INV, GT, MODE, 2>(p, w, gpb, interior, clean, total, h, lane, cnt);
     } else {
-        for (uint32_t base = 0; base < total; base += 128)
-            finish_survivors<B, INV, GT, MODE, 4>(p, w, gpb, interior, clean, total - base, h, lane, cnt,
+        for (uint32_t base = 0; base < total; base += 256)
+            finish_survivors<B, INV, GT, MODE, 8>(p, w, gpb, interior, clean, total - base, h, lane, cnt,
                                                   base);
     }
     __syncwarp();
