@@ -522,6 +522,212 @@ def run_sweep(args):
     print(json.dumps(res), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# batched workload: thousands of texts of uneven length, eight automata
+# ----------------------------------------------------------------------------
+def _event_ms(stream, fn, reps):
+    import torch
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = []
+    for _ in range(reps):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1))
+    return per
+
+
+def run_batch(args):
+    """Config: 4,096 texts, lengths log-uniform 1 KiB-4 MiB, half ACGT and half
+    Zipf(1.1) over 256 bytes, each matched against a uniformly chosen keyword
+    set of its own alphabet among eight (1k-50k keywords of length 8-64,
+    counts geometric), dense int32 ids per text.  One step = the whole batch.
+    Timed: the captured CUDA graph of the batch plan (planning kernel + one
+    persistent launch per automaton on forked streams), the same plan run
+    eagerly, the one-shot ac_match_batch, and the comparison the batch is for:
+    one ac_match launch per text on one stream (no graph), with the tiled
+    kernel and with the one-thread-per-position kernel."""
+    import torch
+
+    from paper_1412_7789_gb300 import api, build
+    from paper_1412_7789_gb300 import workloads as W
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    counts = (1000, 1750, 3000, 5500, 9500, 16500, 29000, 50000)
+    sets = W.batch_pattern_sets(seed=0, counts=counts)
+    texts, kinds = W.batch_texts(args.batch_texts, 1 << 10, 4 << 20, seed=0)
+    buf, offs, lens, which = W.batch_layout(texts, kinds, n_sets=8, seed=0)
+    gen_s = time.perf_counter() - t0
+    total = int(buf.size)
+    t0 = time.perf_counter()
+    autos = [api.Automaton(p) for p in sets]
+    build_s = time.perf_counter() - t0
+    handles = [a.handle for a in autos]
+    d_buf = torch.from_numpy(buf).to(dev)
+    items = api.batch_items(offs, lens, offs, which)
+    d_items = api.items_to_device(items, dev)
+    out = torch.empty(total, dtype=torch.int32, device=dev)
+
+    tuned = []
+    if args.autotune:
+        for j, a in enumerate(autos):
+            idx = np.nonzero(which == j)[0]
+            if idx.size == 0:
+                tuned.append(None)
+                continue
+            # the set's own texts, up to 64 MiB of them, as the tuning sample
+            take, acc = [], 0
+            for i in idx:
+                take.append(i)
+                acc += int(lens[i])
+                if acc >= 64 << 20:
+                    break
+            sample = torch.from_numpy(np.concatenate([texts[i] for i in take])).to(dev)
+            tuned.append(a.autotune(sample, reps=3))
+            del sample
+
+    plan = api.BatchPlan(handles, max_items=len(texts))
+    nitems = len(texts)
+
+    def graph_step():
+        plan.replay(stream)
+
+    def eager_step():
+        plan.run(d_buf, d_items, nitems, out, stream)
+
+    def oneshot_step():
+        api.ac_match_batch(handles, d_buf, d_items, nitems, out, stream)
+
+    views = [(d_buf[int(o):int(o) + int(n)], out[int(o):int(o) + int(n)], int(n), int(w))
+             for o, n, w in zip(offs, lens, which)]
+
+    def per_text_step():
+        for tv, ov, n, w in views:
+            api.ac_match(handles[w], tv, n, ov, stream)
+
+    plan.capture(d_buf, d_items, nitems, out)
+    # parity spot check against the oracle: a few texts of every set
+    import oracle
+
+    replays = max(3, args.warmup)
+    for _ in range(replays):
+        graph_step()
+    torch.cuda.synchronize(dev)
+    got = out.cpu().numpy()
+    checked = 0
+    for j in range(8):
+        idx = [i for i in np.nonzero(which == j)[0] if lens[i] <= (256 << 10)][:2]
+        for i in idx:
+            want = oracle.pfac_ids(sets[j], texts[i])
+            if not np.array_equal(got[offs[i]:offs[i] + lens[i]], want):
+                raise SystemExit("batch parity failure: text %d (set %d)" % (i, j))
+            checked += 1
+
+    sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", 0)))
+    sampler.start()
+    time.sleep(0.3)
+    for _ in range(args.warmup):
+        graph_step()
+    torch.cuda.synchronize(dev)
+    m0 = sampler.mark()
+    g_ms = _event_ms(stream, graph_step, args.steps)
+    m1 = sampler.mark()
+    e_ms = _event_ms(stream, eager_step, max(3, args.steps // 2))
+    o_ms = _event_ms(stream, oneshot_step, max(3, args.steps // 2))
+    per_text_step()
+    torch.cuda.synchronize(dev)
+    p_ms = _event_ms(stream, per_text_step, max(3, args.steps // 2))
+    for a in autos:
+        a.set_kernel("simple")
+    per_text_step()
+    torch.cuda.synchronize(dev)
+    s_ms = _event_ms(stream, per_text_step, 3)
+    for a in autos:
+        a.set_kernel("tiled")
+    time.sleep(0.25)
+    sampler.stop()
+    clocks = sampler.summary(m0, m1)
+
+    # end to end: pinned host texts in, ids out, around one graph replay
+    e2e = None
+    if not args.no_e2e:
+        hb = torch.from_numpy(buf).pin_memory()
+        ho = torch.empty(total, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            d_buf.copy_(hb, non_blocking=True)
+            plan.replay(stream)
+            ho.copy_(out, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e2e_s = (time.perf_counter() - t0) / reps
+        e2e = {"value": total / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": total,
+               "d2h_bytes_per_step": 4 * total, "ms_per_step": 1e3 * e2e_s}
+        del hb, ho
+
+    cpu = None
+    if not args.no_cpu:
+        # the oracle on the first texts of the batch, about cpu_seconds of work
+        t0 = time.perf_counter()
+        done_b = 0
+        for i in range(len(texts)):
+            oracle.pfac_ids(sets[which[i]], texts[i])
+            done_b += int(lens[i])
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": done_b / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d texts of the batch (%d B), serially, keyword sets compiled per text" % (
+                   i + 1, done_b)}
+
+    peak, peak_kind = load_peaks()
+    gm = statistics.median(g_ms)
+    line = {
+        "metric": "batched GB/s text scanned (1 GB300)", "value": total / (statistics.mean(g_ms) * 1e-3) / 1e9,
+        "unit": "GB/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(g_ms), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "batch: %d texts log-uniform 1 KiB-4 MiB (%d B), 50%% ACGT / 50%% Zipf-256, "
+                               "8 keyword sets %s of length 8-64, dense int32 ids" % (nitems, total, list(counts)),
+                   "l2": "inputs larger than L2 (%.1f GB per step)" % (5 * total / 1e9)},
+        "roofline": {"bound": "hbm", "achieved": 5 * total / (gm * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": 5 * total / (gm * 1e-3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": 5 * total, "kernel": "batch graph (all launches)"},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": args.steps * (1 + len(autos)),
+        "batch": {
+            "graph_ms_median": gm, "graph_gbs": total / (gm * 1e-3) / 1e9,
+            "plan_eager_ms_median": statistics.median(e_ms),
+            "match_batch_ms_median": statistics.median(o_ms),
+            "per_text_tiled_ms_median": statistics.median(p_ms),
+            "per_text_tiled_gbs": total / (statistics.median(p_ms) * 1e-3) / 1e9,
+            "per_text_simple_ms_median": statistics.median(s_ms),
+            "per_text_simple_gbs": total / (statistics.median(s_ms) * 1e-3) / 1e9,
+            "speedup_vs_per_text_tiled": statistics.median(p_ms) / gm,
+            "speedup_vs_per_text_simple": statistics.median(s_ms) / gm,
+            "texts_per_set": [int((which == j).sum()) for j in range(8)],
+            "bytes_per_set": [int(lens[which == j].sum()) for j in range(8)],
+            "autotuned": tuned, "parity_texts_checked": checked,
+            "host_build_s": build_s, "generate_s": gen_s,
+        },
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    for a in autos:
+        a.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,10 +746,17 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="input-size sweep and CPU/GPU crossover instead of the throughput line")
     ap.add_argument("--sweep-max", type=int, default=GIB)
+    ap.add_argument("--batch", action="store_true",
+                    help="batched workload (4,096 texts, eight automata) instead of the throughput line")
+    ap.add_argument("--batch-texts", type=int, default=4096)
+    ap.add_argument("--autotune", action="store_true", help="batch: autotune each automaton first")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.sweep:
         run_sweep(args)
+        return
+    if args.batch:
+        run_batch(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -204,9 +204,91 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
 ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
                                   uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream);
 
-/* Read and clear the calling device's kernel error word: AC_OK, or
- * AC_ERR_TIMEOUT when a bounded wait inside a kernel ran out.  Synchronises
- * the device. */
+/*
+ * ---- Batches: many texts, several automata --------------------------------
+ * The paper matches one text per run (section III); a batch is this library's
+ * way to keep the GPU busy with many short texts: every text is cut into the
+ * same work units (tiles) a single text is, and the units of all texts that
+ * use one automaton are matched by one persistent launch, so short texts do
+ * not each pay a launch and a tail.  Results are exactly those of ac_match on
+ * each text alone: walks stop at the end of their own text.
+ *
+ * One text of a batch: bytes d_texts[text_off, text_off + len), matched
+ * against hs[automaton], dense ids written to d_out[out_off, out_off + len).
+ * Texts may overlap or share bytes; their output ranges must not overlap.
+ * len = 0 is allowed (nothing is written).  `reserved` must be 0.
+ */
+typedef struct {
+    uint64_t text_off;
+    uint64_t len;
+    uint64_t out_off;
+    uint32_t automaton;
+    uint32_t reserved;
+} ac_batch_item;
+
+/*
+ * Dense matching of a batch.  hs: nh handles (host array; all compiled on the
+ * calling device).  d_items: nitems ac_batch_item in DEVICE memory (read by
+ * the kernels; not read on the host), d_texts / d_out the bases the offsets
+ * refer to.  Enqueues on `stream`: one planning kernel (groups the texts by
+ * automaton and numbers their work units), then one persistent launch per
+ * automaton.  An item whose automaton is >= nh is skipped and latches an
+ * error that ac_device_status() reports as AC_ERR_INVALID_ARG.  Scratch
+ * (nh * 16 + nitems * 32 bytes + 16 per automaton) comes from the library's
+ * stream-ordered pool.  Asynchronous; nitems = 0 is a no-op.
+ */
+ac_status ac_match_batch(const ac_handle *hs, uint32_t nh, const uint8_t *d_texts, const ac_batch_item *d_items,
+                         uint32_t nitems, int32_t *d_out, void *stream);
+
+/*
+ * A reusable batch plan: the handles, scratch for up to max_items texts, and
+ * (after ac_batch_capture) an instantiated CUDA graph of the whole batch.  The
+ * launches of the automata run on forked streams inside the plan, so those of
+ * different automata may overlap on the GPU.
+ *   ac_batch_create  copies the handle array; allocates the plan's scratch
+ *                    with cudaMalloc.  max_items >= 1.
+ *   ac_batch_run     enqueues the batch on `stream` (like ac_match_batch,
+ *                    with the plan's scratch).  nitems <= max_items.
+ *   ac_batch_capture records one ac_batch_run with these arguments into a
+ *                    CUDA graph (stream capture on an internal stream) and
+ *                    instantiates it, replacing any earlier graph.  Nothing
+ *                    runs.
+ *   ac_batch_replay  launches the captured graph on `stream`.  The pointers and
+ *                    nitems are those captured; the CONTENTS of d_items (and of
+ *                    the texts) may change between replays, so one graph serves
+ *                    any batch of up to nitems texts over the same buffers.
+ *                    AC_ERR_INVALID_ARG when nothing was captured.
+ *   ac_batch_destroy frees the plan (not the handles); no work using it may be
+ *                    in flight.
+ * A plan must not run on two streams at once (its scratch is shared).
+ */
+typedef struct ac_batch_plan *ac_batch;
+ac_status ac_batch_create(const ac_handle *hs, uint32_t nh, uint32_t max_items, ac_batch *out);
+ac_status ac_batch_run(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
+                       int32_t *d_out, void *stream);
+ac_status ac_batch_capture(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
+                           int32_t *d_out);
+ac_status ac_batch_replay(ac_batch b, void *stream);
+ac_status ac_batch_destroy(ac_batch b);
+
+/*
+ * Autotuning (no counterpart in the paper): time the dense kernel of handle h
+ * on the device text d_sample (n bytes, at least 1 MiB is sensible) with each
+ * candidate launch shape -- threads per CTA {256, 384, 512} x text stages per
+ * warp {2, 3, 4}, the shapes that fit shared memory -- and keep the fastest
+ * for every later call on h (single texts and batches).  Each candidate runs
+ * `reps` times (0 = 5) after one warm-up; the median is compared.  Writes the
+ * chosen shape to *block / *stages when they are not NULL.  Synchronises
+ * `stream`; uses scratch output memory of 4 * n bytes from the library pool.
+ * Results never depend on the shape, only the time does.
+ */
+ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t reps, void *stream,
+                      uint32_t *block, uint32_t *stages);
+
+/* Read and clear the calling device's kernel error word: AC_OK, AC_ERR_TIMEOUT
+ * when a bounded wait inside a kernel ran out, or AC_ERR_INVALID_ARG when a
+ * batch item named an automaton outside its handle array.  Synchronises the
+ * device. */
 ac_status ac_device_status(void);
 
 /* Static description of a status code. */

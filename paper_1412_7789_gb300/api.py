@@ -91,6 +91,14 @@ _SIGS = {
     "ac_match_host": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_compact_static": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_set_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ac_match_batch": (ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P]),
+    "ac_batch_create": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
+    "ac_batch_run": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P, _P]),
+    "ac_batch_capture": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P]),
+    "ac_batch_replay": (ctypes.c_int, [_P, _P]),
+    "ac_batch_destroy": (ctypes.c_int, [_P]),
+    "ac_autotune": (ctypes.c_int, [_H, _P, _U64, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_uint32),
+                                   ctypes.POINTER(ctypes.c_uint32)]),
     "ac_device_status": (ctypes.c_int, []),
     "ac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -230,6 +238,94 @@ def ac_device_status() -> int:
     return int(lib().ac_device_status())
 
 
+# ---- batches ---------------------------------------------------------------------
+# numpy mirror of ac_batch_item (32 bytes)
+BATCH_ITEM = np.dtype([("text_off", "<u8"), ("len", "<u8"), ("out_off", "<u8"), ("automaton", "<u4"),
+                       ("reserved", "<u4")])
+assert BATCH_ITEM.itemsize == 32
+
+
+def batch_items(text_off, lens, out_off, automaton) -> np.ndarray:
+    """A host array of ac_batch_item (copy it to the device for the calls)."""
+    k = len(lens)
+    it = np.zeros(k, dtype=BATCH_ITEM)
+    it["text_off"] = np.asarray(text_off, dtype=np.uint64)
+    it["len"] = np.asarray(lens, dtype=np.uint64)
+    it["out_off"] = np.asarray(out_off, dtype=np.uint64)
+    it["automaton"] = np.asarray(automaton, dtype=np.uint32)
+    return it
+
+
+def items_to_device(items: np.ndarray, device="cuda"):
+    """The item array as a uint8 CUDA tensor (the bytes the kernels read)."""
+    import torch
+
+    return torch.from_numpy(items.view(np.uint8).copy()).to(device)
+
+
+def _handles(hs):
+    arr = (ctypes.c_void_p * max(1, len(hs)))(*[int(h) for h in hs])
+    return arr
+
+
+def ac_match_batch(hs, texts, items, nitems: int, out, stream=None):
+    """hs: handles; texts: uint8 CUDA tensor; items: device bytes of nitems ac_batch_item; out: int32 tensor."""
+    arr = _handles(hs)
+    _check(lib().ac_match_batch(ctypes.cast(arr, ctypes.c_void_p), len(hs), _dev_ptr(texts), _dev_ptr(items), nitems,
+                                _dev_ptr(out, 4), _stream_ptr(stream)), "ac_match_batch")
+
+
+def ac_autotune(h: int, sample, n: int | None = None, reps: int = 0, stream=None) -> tuple[int, int]:
+    """Pick the fastest launch shape for h on a device sample; returns (block, stages)."""
+    b = ctypes.c_uint32()
+    s = ctypes.c_uint32()
+    n = sample.numel() if n is None else n
+    _check(lib().ac_autotune(h, _dev_ptr(sample), n, reps, _stream_ptr(stream), ctypes.byref(b), ctypes.byref(s)),
+           "ac_autotune")
+    return int(b.value), int(s.value)
+
+
+class BatchPlan:
+    """ac_batch_create / run / capture / replay / destroy."""
+
+    def __init__(self, handles, max_items: int):
+        self.handles = [int(h) for h in handles]
+        arr = _handles(self.handles)
+        p = ctypes.c_void_p()
+        _check(lib().ac_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.handles), max_items,
+                                     ctypes.byref(p)), "ac_batch_create")
+        self.plan = int(p.value)
+        self.max_items = max_items
+
+    def run(self, texts, items, nitems: int, out, stream=None):
+        _check(lib().ac_batch_run(self.plan, _dev_ptr(texts), _dev_ptr(items), nitems, _dev_ptr(out, 4),
+                                  _stream_ptr(stream)), "ac_batch_run")
+
+    def capture(self, texts, items, nitems: int, out):
+        _check(lib().ac_batch_capture(self.plan, _dev_ptr(texts), _dev_ptr(items), nitems, _dev_ptr(out, 4)),
+               "ac_batch_capture")
+
+    def replay(self, stream=None):
+        _check(lib().ac_batch_replay(self.plan, _stream_ptr(stream)), "ac_batch_replay")
+
+    def close(self):
+        if getattr(self, "plan", None):
+            lib().ac_batch_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 # ---- object wrapper ----------------------------------------------------------------
 class Automaton:
     """A compiled keyword set resident on the current CUDA device."""
@@ -295,6 +391,9 @@ class Automaton:
         cnt = torch.zeros(1, dtype=torch.int64, device=text.device)
         ac_match_compact(self.handle, text, n, pos, ids, cap, cnt, stream)
         return pos, ids, cnt
+
+    def autotune(self, sample, reps: int = 0, stream=None) -> tuple[int, int]:
+        return ac_autotune(self.handle, sample, reps=reps, stream=stream)
 
     def match_host(self, text, out=None, stream=None):
         """text: CPU uint8 tensor (pinned for overlap); returns a CPU int32 tensor."""

@@ -33,6 +33,19 @@ struct ac_automaton {
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
 };
 
+struct ac_batch_plan {
+    std::vector<ac_handle> hs;
+    int device = 0;
+    uint32_t max_items = 0;
+    void *scratch = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 void *dev_malloc(ac_automaton *h, size_t bytes) {
@@ -146,6 +159,67 @@ ac_status cuda_status(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return AC_ERR_OOM;
     if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) return AC_ERR_INVALID_ARG;
     return AC_ERR_CUDA;
+}
+
+// Bytes of a batch's scratch: per automaton a head and a tile counter
+// (16 bytes each), then the planned list (32 bytes per text).
+size_t batch_scratch_bytes(uint32_t nh, uint32_t nitems) {
+    return static_cast<size_t>(nh) * 32u + static_cast<size_t>(nitems) * sizeof(pfac::BatchItemDev);
+}
+
+ac_status check_handles(const ac_handle *hs, uint32_t nh) {
+    if (!hs || nh == 0 || nh > pfac::kMaxBatchAutomata) return AC_ERR_INVALID_ARG;
+    for (uint32_t a = 0; a < nh; ++a) {
+        const ac_status s = check_device(hs[a]);
+        if (s != AC_OK) return s;
+    }
+    return AC_OK;
+}
+
+// Forked streams of a batch plan: automaton a's launch runs on streams[a]
+// after `fork` and `stream` waits for done[a].
+struct Forks {
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+};
+
+// Enqueue a batch on `st`: clear the tile counters, plan on the device, then
+// one persistent dense launch per automaton (on forked streams when given).
+cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const uint8_t *texts,
+                          const ac_batch_item *items, uint32_t nitems, int32_t *out, cudaStream_t st,
+                          const Forks *forks) {
+    uint8_t *base = static_cast<uint8_t *>(scratch);
+    pfac::BatchHead *heads = reinterpret_cast<pfac::BatchHead *>(base);
+    uint8_t *counters = base + static_cast<size_t>(nh) * 16u;
+    pfac::BatchItemDev *lists = reinterpret_cast<pfac::BatchItemDev *>(base + static_cast<size_t>(nh) * 32u);
+    std::vector<uint32_t> tile_len(nh);
+    for (uint32_t a = 0; a < nh; ++a)
+        tile_len[a] = hs[a]->dev.filter ? pfac::filter_tile_positions() : pfac::tiled_tile_positions();
+    cudaError_t e = cudaMemsetAsync(counters, 0, static_cast<size_t>(nh) * 16u, st);
+    if (e == cudaSuccess) e = pfac::launch_batch_plan(items, nitems, nh, texts, tile_len.data(), heads, lists, st);
+    if (e == cudaSuccess && forks) e = cudaEventRecord(forks->fork, st);
+    for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
+        cudaStream_t sa = st;
+        if (forks) {
+            sa = forks->streams[a];
+            e = cudaStreamWaitEvent(sa, forks->fork, 0);
+            if (e != cudaSuccess) break;
+        }
+        pfac::MatchRequest r;
+        r.text = texts;
+        r.out = out;
+        r.batch = heads + a;
+        r.lists = lists;
+        r.scratch = counters + 16u * a;
+        r.scratch_bytes = 16;
+        ac_automaton *h = hs[a];
+        e = h->dev.filter ? pfac::launch_filter(h->dev, r, pfac::OUT_DENSE, h->tuning, sa)
+                          : pfac::launch_tiled(h->dev, r, pfac::OUT_DENSE, h->tuning, sa);
+        if (e == cudaSuccess && forks) e = cudaEventRecord(forks->done[a], sa);
+        if (e == cudaSuccess && forks) e = cudaStreamWaitEvent(st, forks->done[a], 0);
+    }
+    return e;
 }
 
 }  // namespace
@@ -403,11 +477,208 @@ ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t 
     return cuda_status(e);
 }
 
+ac_status ac_match_batch(const ac_handle *hs, uint32_t nh, const uint8_t *d_texts, const ac_batch_item *d_items,
+                         uint32_t nitems, int32_t *d_out, void *stream) {
+    ac_status s = check_handles(hs, nh);
+    if (s != AC_OK) return s;
+    if (nitems == 0) return AC_OK;
+    if (!d_texts || !d_items || !d_out) return AC_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(hs[0]->device, &pool);
+    if (e != cudaSuccess) return cuda_status(e);
+    void *scratch = nullptr;
+    e = cudaMallocFromPoolAsync(&scratch, batch_scratch_bytes(nh, nitems), pool, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = enqueue_batch(hs, nh, scratch, d_texts, d_items, nitems, d_out, st, nullptr);
+    const cudaError_t e2 = cudaFreeAsync(scratch, st);
+    return cuda_status(e != cudaSuccess ? e : e2);
+}
+
+ac_status ac_batch_destroy(ac_batch b) {
+    if (!b) return AC_OK;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaStream_t x : b->streams)
+        if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : b->done)
+        if (x) cudaEventDestroy(x);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->capture) cudaStreamDestroy(b->capture);
+    if (b->scratch) cudaFree(b->scratch);
+    delete b;
+    return AC_OK;
+}
+
+ac_status ac_batch_create(const ac_handle *hs, uint32_t nh, uint32_t max_items, ac_batch *out) {
+    if (!out) return AC_ERR_INVALID_ARG;
+    *out = nullptr;
+    ac_status s = check_handles(hs, nh);
+    if (s != AC_OK) return s;
+    if (max_items == 0) return AC_ERR_INVALID_ARG;
+    ac_batch b = new (std::nothrow) ac_batch_plan();
+    if (!b) return AC_ERR_OOM;
+    b->hs.assign(hs, hs + nh);
+    b->device = hs[0]->device;
+    b->max_items = max_items;
+    b->streams.assign(nh, nullptr);
+    b->done.assign(nh, nullptr);
+    cudaError_t e = cudaMalloc(&b->scratch, batch_scratch_bytes(nh, max_items));
+    if (e != cudaSuccess) b->scratch = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
+    for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
+        e = cudaStreamCreateWithFlags(&b->streams[a], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[a], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ac_batch_destroy(b);
+        return cuda_status(e);
+    }
+    *out = b;
+    return AC_OK;
+}
+
+namespace {
+ac_status batch_enqueue(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
+                        int32_t *d_out, cudaStream_t st) {
+    Forks f;
+    f.fork = b->fork;
+    f.streams = b->streams;
+    f.done = b->done;
+    return cuda_status(enqueue_batch(b->hs.data(), static_cast<uint32_t>(b->hs.size()), b->scratch, d_texts, d_items,
+                                     nitems, d_out, st, &f));
+}
+
+ac_status check_plan_args(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
+                          int32_t *d_out) {
+    if (!b || nitems > b->max_items) return AC_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AC_ERR_CUDA;
+    if (dev != b->device) return AC_ERR_INVALID_ARG;
+    if (nitems > 0 && (!d_texts || !d_items || !d_out)) return AC_ERR_INVALID_ARG;
+    return AC_OK;
+}
+}  // namespace
+
+ac_status ac_batch_run(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
+                       int32_t *d_out, void *stream) {
+    ac_status s = check_plan_args(b, d_texts, d_items, nitems, d_out);
+    if (s != AC_OK || nitems == 0) return s;
+    return batch_enqueue(b, d_texts, d_items, nitems, d_out, static_cast<cudaStream_t>(stream));
+}
+
+ac_status ac_batch_capture(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
+                           int32_t *d_out) {
+    ac_status s = check_plan_args(b, d_texts, d_items, nitems, d_out);
+    if (s != AC_OK) return s;
+    if (nitems == 0) return AC_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_status(e);
+    s = batch_enqueue(b, d_texts, d_items, nitems, d_out, b->capture);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->capture, &g);
+    if (s == AC_OK && e != cudaSuccess) s = cuda_status(e);
+    cudaGraphExec_t x = nullptr;
+    if (s == AC_OK) {
+        e = cudaGraphInstantiate(&x, g, 0);
+        if (e != cudaSuccess) s = cuda_status(e);
+    }
+    if (s != AC_OK) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->graph = g;
+    b->exec = x;
+    return AC_OK;
+}
+
+ac_status ac_batch_replay(ac_batch b, void *stream) {
+    if (!b || !b->exec) return AC_ERR_INVALID_ARG;
+    return cuda_status(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)));
+}
+
+ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t reps, void *stream,
+                      uint32_t *block, uint32_t *stages) {
+    ac_status s = check_device(h);
+    if (s != AC_OK) return s;
+    if (!d_sample || n == 0) return AC_ERR_INVALID_ARG;
+    if (reps == 0) reps = 5;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(h->device, &pool);
+    if (e != cudaSuccess) return cuda_status(e);
+    void *out = nullptr;
+    e = cudaMallocFromPoolAsync(&out, n * sizeof(int32_t), pool, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const pfac::Tuning keep = h->tuning;
+    pfac::Tuning best = keep;
+    float best_ms = -1.0f;
+    pfac::MatchRequest r;
+    r.text = d_sample;
+    r.n = n;
+    r.out = static_cast<int32_t *>(out);
+    static const int kBlocks[3] = {256, 384, 512};
+    for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
+        for (int sg = 2; sg <= 4 && e == cudaSuccess; ++sg) {
+            pfac::Tuning tu = keep;
+            tu.block = kBlocks[bi];
+            tu.stages = sg;
+            tu.grid = 0;
+            h->tuning = tu;
+            cudaError_t le = run_tiled(h, r, pfac::OUT_DENSE, st);  // warm-up
+            if (le == cudaErrorInvalidConfiguration) {              // does not fit shared memory
+                cudaGetLastError();
+                continue;
+            }
+            if (le != cudaSuccess) {
+                e = le;
+                break;
+            }
+            std::vector<float> ms;
+            for (uint32_t i = 0; i < reps && e == cudaSuccess; ++i) {
+                e = cudaEventRecord(t0, st);
+                if (e == cudaSuccess) e = run_tiled(h, r, pfac::OUT_DENSE, st);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                float v = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t0, t1);
+                ms.push_back(v);
+            }
+            if (e != cudaSuccess) break;
+            std::sort(ms.begin(), ms.end());
+            const float med = ms[ms.size() / 2];
+            if (best_ms < 0.0f || med < best_ms) {
+                best_ms = med;
+                best = tu;
+            }
+        }
+    }
+    h->tuning = e == cudaSuccess ? best : keep;
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    const cudaError_t e2 = cudaFreeAsync(out, st);
+    const cudaError_t e3 = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+    if (e != cudaSuccess) return cuda_status(e);
+    if (block) *block = static_cast<uint32_t>(h->tuning.block);
+    if (stages) *stages = static_cast<uint32_t>(h->tuning.stages);
+    return AC_OK;
+}
+
 ac_status ac_device_status(void) {
     unsigned int v = 0;
     cudaError_t e = pfac::read_device_error(&v);
     if (e != cudaSuccess) return AC_ERR_CUDA;
-    return v ? AC_ERR_TIMEOUT : AC_OK;
+    if (v & (pfac::kErrTimeout | pfac::kErrWalk | pfac::kErrLookback)) return AC_ERR_TIMEOUT;
+    return v ? AC_ERR_INVALID_ARG : AC_OK;
 }
 
 const char *ac_status_string(ac_status s) {

@@ -53,8 +53,11 @@ constexpr uint32_t kOffF = 1280;    // root filter bits
 constexpr unsigned kFull = 0xffffffffu;
 
 struct FilterParams {
-    TextView tv;
     const uint8_t *text;
+    uint64_t n;
+    uint32_t tile;    // positions per tile (multiple of 16)
+    uint32_t staged;  // bytes staged per tile (tile + halo, multiple of 16)
+    uint32_t ntiles;  // single text: its tiles
     uint32_t nstages;
     const void *G;
     const uint32_t *Fg;
@@ -65,7 +68,6 @@ struct FilterParams {
     int hash_shift;
     uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
     int32_t *out;
-    int vec_ok;
     uint32_t *cpos;
     uint32_t *cids;
     unsigned long long cap;
@@ -73,7 +75,11 @@ struct FilterParams {
     unsigned long long *status;
     unsigned int *counter;
     unsigned int *err;
-    uint32_t off_neg1, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue;
+    uint32_t off_neg1, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue, off_meta;
+    // batch: the automaton's head and the planned list (text and out are then
+    // the bases of all texts and outputs)
+    const BatchHead *batch;
+    const BatchItemDev *lists;
 };
 
 struct WarpSmem {
@@ -86,6 +92,27 @@ struct WarpSmem {
     uint16_t *queue;
     const int32_t *neg1;  // kResWords x -1, shared by the CTA's warps
 };
+
+// The text and tile of work unit u (entry `item` of the planned list in a batch).
+__device__ __forceinline__ TileText tile_text(const FilterParams &p, const Work &wk, uint32_t u, uint32_t item) {
+    if (!wk.list) return make_text(p.text, p.out, p.n, u);
+    return batch_text(wk, p.text, p.out, item, u);
+}
+
+// All lanes: point stage s at unit u (>= wk.units: the end of this warp's
+// work) and start its bulk copy.
+__device__ __forceinline__ void issue_unit(const FilterParams &p, const Work &wk, uint64_t *bar, uint32_t *stile,
+                                           uint32_t *sitem, uint8_t *st, uint32_t u, int lane) {
+    const uint32_t item = (wk.list && u < wk.units) ? find_item(wk, u, lane) : 0u;
+    if (lane == 0) {
+        *stile = u;
+        *sitem = item;
+        if (u >= wk.units)
+            mbar_arrive(bar);
+        else
+            issue_text_tile(tile_text(p, wk, u, item), p.tile, p.staged, bar, st);
+    }
+}
 
 // Classify the 4 bytes of w: their class codes (one per byte) and a word whose
 // non-zero bytes mark bytes in no keyword.
@@ -134,7 +161,7 @@ __device__ __forceinline__ uint32_t code_window(const uint32_t *packed, uint32_t
 // `coded` have their codes in the packed stream already; later ones are read
 // from the text in global memory (the stage may already hold the next tile).
 template <int B>
-__device__ __forceinline__ bool fetch_code(const FilterParams &p, const WarpSmem &w, int64_t gpb, uint32_t coded,
+__device__ __forceinline__ bool fetch_code(const TileText &tt, const WarpSmem &w, int64_t gpb, uint32_t coded,
                                            uint32_t q, uint32_t &c) {
     if (q < coded) {
         if ((w.inv[q >> 4] >> (q & 15u)) & 1u) return false;
@@ -142,8 +169,8 @@ __device__ __forceinline__ bool fetch_code(const FilterParams &p, const WarpSmem
         return true;
     }
     const int64_t gp = gpb + static_cast<int64_t>(q);
-    if (gp >= static_cast<int64_t>(p.tv.n)) return false;
-    const uint32_t v = w.cls8[__ldg(p.text + gp)];
+    if (gp >= static_cast<int64_t>(tt.n)) return false;
+    const uint32_t v = w.cls8[__ldg(tt.text + gp)];
     if (v == 0xFFu) return false;
     c = v;
     return true;
@@ -153,11 +180,11 @@ __device__ __forceinline__ bool fetch_code(const FilterParams &p, const WarpSmem
 // their results go to the pass's staging buffer (or are counted).  Returns
 // true when this lane found a keyword.
 template <int B, typename GT, int MODE, int SLOTS, bool DIRECT = false>
-__device__ __forceinline__ bool finish_survivors(const FilterParams &p, const WarpSmem &w, int64_t gpb,
-                                                 bool interior, bool clean, uint32_t avail, uint32_t pbase,
-                                                 int lane, unsigned long long &cnt, uint32_t base,
+__device__ __forceinline__ bool finish_survivors(const FilterParams &p, const TileText &tt, const WarpSmem &w,
+                                                 int64_t gpb, bool interior, bool clean, uint32_t avail,
+                                                 uint32_t pbase, int lane, unsigned long long &cnt, uint32_t base,
                                                  uint32_t coded = 0) {
-    const int64_t n = static_cast<int64_t>(p.tv.n);
+    const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k, k2 = p.k2;
     const GT *G = static_cast<const GT *>(p.G);
     uint32_t st[SLOTS], q[SLOTS], ii[SLOTS];
@@ -244,7 +271,7 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Wa
         for (int t = 0; t < SLOTS; ++t) {
             if ((walking >> t) & 1u) {
                 uint32_t c = 0;
-                const bool okc = fetch_code<B>(p, w, gpb, DIRECT ? coded : pbase + kPass + 16u, q[t], c);
+                const bool okc = fetch_code<B>(tt, w, gpb, DIRECT ? coded : pbase + kPass + 16u, q[t], c);
                 // an unknown byte or the text end reads the row's end column,
                 // which always holds the result of stopping there
                 e[t] = goto_ld(G, st[t], p.W, okc ? c : p.C);
@@ -271,7 +298,7 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Wa
             if (MODE == OUT_COUNT)
                 cnt += v[t] >= 0 ? 1ull : 0ull;
             else if (DIRECT)
-                p.out[gpb + ii[t]] = v[t];
+                tt.out[gpb + ii[t]] = v[t];
             else
                 w.res[ii[t] - pbase] = v[t];
         }
@@ -283,10 +310,10 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Wa
 // the results.  For the compacted output the results stay staged and the
 // queue keeps the survivors (ascending position); returns their number.
 template <int B, typename GT, int MODE>
-__device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const WarpSmem &w, int64_t gpb,
-                                                bool interior, uint32_t h, int lane, unsigned long long &cnt,
-                                                bool &res_busy) {
-    const int64_t n = static_cast<int64_t>(p.tv.n);
+__device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const TileText &tt, const WarpSmem &w,
+                                                int64_t gpb, bool interior, uint32_t h, int lane,
+                                                unsigned long long &cnt, bool &res_busy) {
+    const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k;
     const uint32_t pbase = h * kPass;
     const uint32_t i0 = pbase + 16u * static_cast<uint32_t>(lane);  // this lane's first position
@@ -381,22 +408,22 @@ __device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const War
     // 4. the survivors, spread over the lanes
     bool found = false;
     if (total <= 32) {
-        found = finish_survivors<B, GT, MODE, 1>(p, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
+        found = finish_survivors<B, GT, MODE, 1>(p, tt, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
     } else if (total <= 64) {
-        found = finish_survivors<B, GT, MODE, 2>(p, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
+        found = finish_survivors<B, GT, MODE, 2>(p, tt, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
     } else {
         for (uint32_t b = 0; b < total; b += 256)
-            found |= finish_survivors<B, GT, MODE, 8>(p, w, gpb, interior, clean, total - b, pbase, lane, cnt, b);
+            found |= finish_survivors<B, GT, MODE, 8>(p, tt, w, gpb, interior, clean, total - b, pbase, lane, cnt, b);
     }
     found = __any_sync(kFull, found);
     __syncwarp();
 
     // 5. output
     if (MODE == OUT_DENSE) {
-        if (!found && interior && p.vec_ok) {
+        if (!found && interior && tt.vec_ok) {
             // every result of the pass is -1: store the constant buffer
             if (lane == 0) {
-                bulk_store(p.out + gpb + pbase, w.neg1, kResWords * 4);
+                bulk_store(tt.out + gpb + pbase, w.neg1, kResWords * 4);
                 bulk_commit();
             }
         } else {
@@ -418,11 +445,11 @@ __device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const War
                 }
             }
             __syncwarp();
-            if (interior && p.vec_ok) {
+            if (interior && tt.vec_ok) {
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) {
-                    bulk_store(p.out + gpb + pbase, w.res, kResWords * 4);
+                    bulk_store(tt.out + gpb + pbase, w.res, kResWords * 4);
                     bulk_commit();
                 }
                 res_busy = true;
@@ -431,13 +458,13 @@ __device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const War
                 for (uint32_t g = 0; g < 4; ++g) {
                     const int4 r4 = reinterpret_cast<const int4 *>(w.res)[4u * lane + g];
                     const int64_t g0 = gpb + i0 + 4u * g;
-                    if (p.vec_ok && ((valid >> (4 * g)) & 0xFu) == 0xFu) {
-                        *reinterpret_cast<int4 *>(p.out + g0) = r4;
+                    if (tt.vec_ok && ((valid >> (4 * g)) & 0xFu) == 0xFu) {
+                        *reinterpret_cast<int4 *>(tt.out + g0) = r4;
                     } else {
                         const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
-                            if ((valid >> (4 * g + r)) & 1u) p.out[g0 + r] = rr[r];
+                            if ((valid >> (4 * g + r)) & 1u) tt.out[g0 + r] = rr[r];
                     }
                 }
             }
@@ -519,7 +546,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_compact(const Filter
     w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
     w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
     w.neg1 = nullptr;
-    const uint32_t nchunks = (p.tv.ntiles + nw - 1) / nw;
+    uint32_t *sitem = reinterpret_cast<uint32_t *>(wreg + p.off_meta);
+    const Work wk = load_work(nullptr, nullptr, p.ntiles);  // one text
+    const uint32_t nchunks = (wk.units + nw - 1) / nw;
 
     if (threadIdx.x == 0) {
         mbar_init(jbar, 1);
@@ -538,10 +567,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_compact(const Filter
     }
     auto tile_of = [&](uint32_t c) -> uint32_t {
         const uint64_t t = static_cast<uint64_t>(c) * nw + warp;
-        return (c < nchunks && t < p.tv.ntiles) ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+        return (c < nchunks && t < wk.units) ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
     };
-    if (lane == 0)
-        for (uint32_t s = 0; s < 2; ++s) issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, tile_of(chunk[s]));
+    for (uint32_t s = 0; s < 2; ++s)
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, tile_of(chunk[s]), lane);
 
     unsigned long long unused = 0;
     bool res_busy = false;
@@ -555,17 +584,18 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_compact(const Filter
         const uint32_t tile = stile[s];
         uint32_t m = 0, total = 0;
         int64_t gpb = 0;
-        if (ok && tile < p.tv.ntiles) {
-            w.st = wreg + s * p.tv.staged;
-            const uint64_t tlo = static_cast<uint64_t>(tile) * p.tv.tile;
-            gpb = static_cast<int64_t>(tlo) - p.tv.head;
-            const bool interior =
-                gpb >= 0 && gpb + static_cast<int64_t>(p.tv.staged) <= static_cast<int64_t>(p.tv.n);
+        TileText tt;
+        if (ok && tile < wk.units) {
+            tt = tile_text(p, wk, tile, sitem[s]);
+            w.st = wreg + s * p.staged;
+            const uint64_t tlo = static_cast<uint64_t>(tt.tile) * p.tile;
+            gpb = static_cast<int64_t>(tlo) - tt.head;
+            const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.staged) <= static_cast<int64_t>(tt.n);
             if (!interior) {
-                load_fringe(p.tv, w.st, tlo, lane);
+                load_text_fringe(tt, p.staged, w.st, tlo, lane);
                 __syncwarp();
             }
-            total = filter_pass<B, GT, OUT_COMPACT>(p, w, gpb, interior, 0, lane, unused, res_busy);
+            total = filter_pass<B, GT, OUT_COMPACT>(p, tt, w, gpb, interior, 0, lane, unused, res_busy);
             m = count_found(w, total, lane);
         }
         if (lane == 0) {
@@ -600,12 +630,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_compact(const Filter
             }
         }
         __syncthreads();
-        if (tile < p.tv.ntiles && m) write_found(p, w, total, gpb, bases[warp], lane);
+        if (tile < wk.units && m) write_found(p, w, total, gpb, bases[warp], lane);
         __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, tile_of(chunk[s]));
-        }
+        if (lane == 0) fence_proxy_async_smem();
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, tile_of(chunk[s]), lane);
     }
 }
 
@@ -623,7 +651,8 @@ enum : uint32_t { kPhJK = 0, kPhJ2 = 1, kPhWalk = 2, kPhDone = 3 };
 
 struct Flight {
     int64_t gpb;      // text index of the tile's position 0
-    uint32_t tile;    // 0xFFFFFFFF: empty
+    uint32_t tile;    // work unit; 0xFFFFFFFF: empty
+    uint32_t item;    // batch: its entry in the planned list
     uint32_t interior;
     uint32_t pos;     // this lane's survivor (tile position) or kNoPos
     uint32_t phase;
@@ -638,6 +667,7 @@ __device__ __forceinline__ Flight empty_flight() {
     Flight f;
     f.gpb = 0;
     f.tile = 0xFFFFFFFFu;
+    f.item = 0;
     f.interior = 0;
     f.pos = kNoPos;
     f.phase = kPhDone;
@@ -651,14 +681,14 @@ __device__ __forceinline__ Flight empty_flight() {
 
 // Walk the goto table from state s, reading the text from global memory.
 template <typename GT>
-__device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t *cls8, int64_t gpb, uint32_t s,
-                                           uint32_t q) {
+__device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t *cls8, const TileText &tt,
+                                           int64_t gpb, uint32_t s, uint32_t q) {
     const GT *G = static_cast<const GT *>(p.G);
     for (uint32_t step = 0; step <= p.maxlen + 1; ++step) {
         const int64_t gp = gpb + static_cast<int64_t>(q);
         uint32_t c = p.C;  // the end column: stop here
-        if (gp < static_cast<int64_t>(p.tv.n)) {
-            const uint32_t v = cls8[__ldg(p.text + gp)];
+        if (gp < static_cast<int64_t>(tt.n)) {
+            const uint32_t v = cls8[__ldg(tt.text + gp)];
             if (v != 0xFFu) c = v;
         }
         const int t = goto_ld(G, s, p.W, c);
@@ -692,7 +722,7 @@ __device__ __forceinline__ void flight_advance(const FilterParams &p, Flight &f)
 
 // Last stage: the stride-table result has arrived; finish the walk if needed.
 template <typename GT>
-__device__ __forceinline__ void flight_finish(const FilterParams &p, const uint8_t *cls8, Flight &f) {
+__device__ __forceinline__ void flight_finish(const FilterParams &p, const Work &wk, const uint8_t *cls8, Flight &f) {
     if (f.pos == kNoPos) return;
     if (f.phase == kPhJ2) {
         const int e = f.val;
@@ -706,7 +736,7 @@ __device__ __forceinline__ void flight_finish(const FilterParams &p, const uint8
         f.phase = kPhWalk;
     }
     if (f.phase == kPhWalk) {
-        f.val = walk_global<GT>(p, cls8, f.gpb, f.state, f.q);
+        f.val = walk_global<GT>(p, cls8, tile_text(p, wk, f.tile, f.item), f.gpb, f.state, f.q);
         f.phase = kPhDone;
     }
 }
@@ -714,8 +744,8 @@ __device__ __forceinline__ void flight_finish(const FilterParams &p, const uint8
 // Write (or count) a finished tile: one bulk store of -1 when no survivor
 // found a keyword, else -1 from the position owners and the survivors' ids.
 template <int MODE>
-__device__ __forceinline__ void flight_output(const FilterParams &p, const WarpSmem &w, const Flight &f, int lane,
-                                              unsigned long long &cnt) {
+__device__ __forceinline__ void flight_output(const FilterParams &p, const Work &wk, const WarpSmem &w, const Flight &f,
+                                              int lane, unsigned long long &cnt) {
     if (f.tile == 0xFFFFFFFFu) return;
     const bool mine = f.pos != kNoPos && f.val >= 0;
     if (MODE == OUT_COUNT) {
@@ -723,10 +753,11 @@ __device__ __forceinline__ void flight_output(const FilterParams &p, const WarpS
         return;
     }
     const bool found = __any_sync(kFull, mine);
-    const int64_t n = static_cast<int64_t>(p.tv.n);
-    if (!found && f.interior && p.vec_ok) {
+    const TileText tt = tile_text(p, wk, f.tile, f.item);
+    const int64_t n = static_cast<int64_t>(tt.n);
+    if (!found && f.interior && tt.vec_ok) {
         if (lane == 0) {
-            bulk_store(p.out + f.gpb, w.neg1, kTile * 4);
+            bulk_store(tt.out + f.gpb, w.neg1, kTile * 4);
             bulk_commit();
             bulk_wait_read_keep8();  // bound the groups in flight
         }
@@ -739,18 +770,18 @@ __device__ __forceinline__ void flight_output(const FilterParams &p, const WarpS
 #pragma unroll
             for (uint32_t g = 0; g < 4; ++g) {
                 const int64_t g0 = f.gpb + h * kPass + 16u * lane + 4u * g;
-                if (p.vec_ok && g0 >= 0 && g0 + 4 <= n) {
-                    *reinterpret_cast<int4 *>(p.out + g0) = none;
+                if (tt.vec_ok && g0 >= 0 && g0 + 4 <= n) {
+                    *reinterpret_cast<int4 *>(tt.out + g0) = none;
                 } else {
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        if (g0 + r >= 0 && g0 + r < n) p.out[g0 + r] = -1;
+                        if (g0 + r >= 0 && g0 + r < n) tt.out[g0 + r] = -1;
                 }
             }
         }
     }
     __syncwarp();  // the -1 stores of the owners come before the survivors' ids
-    if (mine) p.out[f.gpb + f.pos] = f.val;
+    if (mine) tt.out[f.gpb + f.pos] = f.val;
 }
 
 template <int B, typename GT, int MODE>
@@ -770,8 +801,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
     w.res = nullptr;
     w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
     w.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
+    uint32_t *sitem = reinterpret_cast<uint32_t *>(wreg + p.off_meta);
     const uint32_t nst = p.nstages;
-    const int64_t n = static_cast<int64_t>(p.tv.n);
+    const Work wk = load_work(p.batch, p.lists, p.ntiles);
     const uint32_t k = p.k, k2 = p.k2;
     const bool owner = lane < static_cast<int>(kOwnLanes);
 
@@ -795,12 +827,15 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
     const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
     auto next_tile = [&](uint32_t it) -> uint32_t {
-        if (it == 0) return gw < p.tv.ntiles ? static_cast<uint32_t>(gw) : 0xFFFFFFFFu;
-        const uint64_t t = GW + atomicAdd(p.counter, 1u);
-        return t < p.tv.ntiles ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+        uint32_t t = 0xFFFFFFFFu;
+        if (lane == 0) {
+            const uint64_t c = it == 0 ? gw : GW + atomicAdd(p.counter, 1u);
+            if (c < wk.units) t = static_cast<uint32_t>(c);
+        }
+        return __shfl_sync(kFull, t, 0);
     };
-    if (lane == 0)
-        for (uint32_t s = 0; s < nst; ++s) issue_tile(p.tv, &bars[s], &stile[s], wreg + s * p.tv.staged, next_tile(s));
+    for (uint32_t s = 0; s < nst; ++s)
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, next_tile(s), lane);
 
     unsigned long long cnt = 0;
     Flight f1 = empty_flight(), f2 = empty_flight();  // one and two tiles back
@@ -820,13 +855,16 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
             return;
         }
         const uint32_t tile = stile[s];
-        if (tile >= p.tv.ntiles) break;
-        uint8_t *st = wreg + s * p.tv.staged;
-        const uint64_t tlo = static_cast<uint64_t>(tile) * kTile;
-        const int64_t gpb = static_cast<int64_t>(tlo) - p.tv.head;
-        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.tv.staged) <= n;
+        if (tile >= wk.units) break;
+        const uint32_t item = sitem[s];
+        const TileText tt = tile_text(p, wk, tile, item);
+        const int64_t n = static_cast<int64_t>(tt.n);
+        uint8_t *st = wreg + s * p.staged;
+        const uint64_t tlo = static_cast<uint64_t>(tt.tile) * kTile;
+        const int64_t gpb = static_cast<int64_t>(tlo) - tt.head;
+        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.staged) <= n;
         if (!interior) {
-            load_fringe(p.tv, st, tlo, lane);
+            load_text_fringe(tt, p.staged, st, tlo, lane);
             __syncwarp();
         }
 
@@ -869,10 +907,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
         const bool clean = !__any_sync(kFull, (inv[0] | inv[1]) != 0);
         __syncwarp();
         // the stage is consumed: start fetching a later tile into it
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            issue_tile(p.tv, &bars[s], &stile[s], st, next_tile(it + nst));
-        }
+        if (lane == 0) fence_proxy_async_smem();
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], st, next_tile(it + nst), lane);
 
         // 2. root filter, one bit per start position (bits 0-15: first half)
         uint32_t sv = 0, slowm = 0;
@@ -947,10 +983,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
         if (total > 32) {
             // 4a. many survivors: finish the tiles in flight, then this one
             flight_advance<B>(p, f1);
-            flight_finish<GT>(p, w.cls8, f2);
-            flight_output<MODE>(p, w, f2, lane, cnt);
-            flight_finish<GT>(p, w.cls8, f1);
-            flight_output<MODE>(p, w, f1, lane, cnt);
+            flight_finish<GT>(p, wk, w.cls8, f2);
+            flight_output<MODE>(p, wk, w, f2, lane, cnt);
+            flight_finish<GT>(p, wk, w.cls8, f1);
+            flight_output<MODE>(p, wk, w, f1, lane, cnt);
             f1 = empty_flight();
             f2 = empty_flight();
             if (MODE == OUT_DENSE) {
@@ -962,12 +998,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
 #pragma unroll
                         for (uint32_t g = 0; g < 4; ++g) {
                             const int64_t g0 = gpb + h * kPass + 16u * lane + 4u * g;
-                            if (p.vec_ok && g0 >= 0 && g0 + 4 <= n) {
-                                *reinterpret_cast<int4 *>(p.out + g0) = none;
+                            if (tt.vec_ok && g0 >= 0 && g0 + 4 <= n) {
+                                *reinterpret_cast<int4 *>(tt.out + g0) = none;
                             } else {
 #pragma unroll
                                 for (int r = 0; r < 4; ++r)
-                                    if (g0 + r >= 0 && g0 + r < n) p.out[g0 + r] = -1;
+                                    if (g0 + r >= 0 && g0 + r < n) tt.out[g0 + r] = -1;
                             }
                         }
                     }
@@ -975,7 +1011,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                 __syncwarp();
             }
             for (uint32_t b = 0; b < total; b += 256)
-                finish_survivors<B, GT, MODE, 8, true>(p, w, gpb, interior, clean, total - b, 0, lane, cnt, b,
+                finish_survivors<B, GT, MODE, 8, true>(p, tt, w, gpb, interior, clean, total - b, 0, lane, cnt, b,
                                                        kCodeSpan);
             __syncwarp();
             continue;
@@ -984,6 +1020,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
         // 4b. at most one survivor per lane: issue its window-table load now
         Flight f0 = empty_flight();
         f0.tile = tile;
+        f0.item = item;
         f0.gpb = gpb;
         f0.interior = interior ? 1u : 0u;
         if (static_cast<uint32_t>(lane) < total) {
@@ -1011,17 +1048,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
         // 5. the tile one back: issue its stride-table loads
         flight_advance<B>(p, f1);
         // 6. the tile two back: finish and write it
-        flight_finish<GT>(p, w.cls8, f2);
-        flight_output<MODE>(p, w, f2, lane, cnt);
+        flight_finish<GT>(p, wk, w.cls8, f2);
+        flight_output<MODE>(p, wk, w, f2, lane, cnt);
         f2 = f1;
         f1 = f0;
     }
     // drain
     flight_advance<B>(p, f1);
-    flight_finish<GT>(p, w.cls8, f2);
-    flight_output<MODE>(p, w, f2, lane, cnt);
-    flight_finish<GT>(p, w.cls8, f1);
-    flight_output<MODE>(p, w, f1, lane, cnt);
+    flight_finish<GT>(p, wk, w.cls8, f2);
+    flight_output<MODE>(p, wk, w, f2, lane, cnt);
+    flight_finish<GT>(p, wk, w.cls8, f1);
+    flight_output<MODE>(p, wk, w, f1, lane, cnt);
 
     if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
     if (MODE == OUT_COUNT) {
@@ -1069,6 +1106,8 @@ cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uin
 
 }  // namespace
 
+uint32_t filter_tile_positions() { return kTile; }
+
 size_t filter_scratch_bytes(uint64_t n, OutMode mode) {
     if (mode != OUT_COMPACT) return 16;
     // tile counter and one look-back word per chunk; sized per one-pass tile,
@@ -1079,7 +1118,8 @@ size_t filter_scratch_bytes(uint64_t n, OutMode mode) {
 
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                           cudaStream_t stream) {
-    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || tu.stages < 2 || tu.stages > kMaxStages)
+    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
+        tu.stages > kMaxStages)
         return cudaErrorInvalidValue;
     if (t.B != 2 && t.B != 4) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, max_smem = 0;
@@ -1087,20 +1127,26 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
+    const bool batch = r.batch != nullptr;
+    if (batch && (mode != OUT_DENSE || !r.lists)) return cudaErrorInvalidValue;
     FilterParams p{};
     p.text = r.text;
-    p.tv.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(r.text) & 15u);
-    p.tv.gbase = r.text - p.tv.head;
-    p.tv.n = r.n;
+    p.n = r.n;
     // warp tiles: two passes, or one for the compacted output (a warp keeps one
     // pass of results staged until its CTA round is placed)
     const uint32_t tlen = mode == OUT_COMPACT ? kPass : kTile;
-    p.tv.tile = tlen;
+    p.tile = tlen;
     uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
-    p.tv.staged = align16(tlen + H) > align16(tlen + 16) ? align16(tlen + H) : align16(tlen + 16);
-    const uint64_t tiles = (r.n + p.tv.head + tlen - 1) / tlen;
-    if (tiles >= 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    p.tv.ntiles = static_cast<uint32_t>(tiles);
+    p.staged = align16(tlen + H) > align16(tlen + 16) ? align16(tlen + H) : align16(tlen + 16);
+    uint64_t tiles = 0;
+    if (!batch) {
+        const uint64_t head = reinterpret_cast<uintptr_t>(r.text) & 15u;
+        tiles = (r.n + head + tlen - 1) / tlen;
+        if (tiles >= 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    }
+    p.ntiles = static_cast<uint32_t>(tiles);
+    p.batch = r.batch;
+    p.lists = r.lists;
     // per-warp layout: stages, packed codes, unknown-byte bits, then for the
     // compacted output a result buffer and a per-pass queue, else a per-tile queue
     const bool pipe = mode != OUT_COMPACT;
@@ -1112,13 +1158,16 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
     uint32_t smem = 0;
     bool fits = false;
-    for (int st = pipe ? 3 : 2; st >= 2 && !fits; --st) {
+    // stages: 3 by default for the pipelined kernel; the compacted output keeps 2
+    const int want = !pipe ? 2 : (tu.stages ? tu.stages : 3);
+    for (int st = want; st >= 2 && !fits; --st) {
         p.nstages = static_cast<uint32_t>(st);
-        p.off_packed = p.nstages * p.tv.staged;
+        p.off_packed = p.nstages * p.staged;
         p.off_inv = p.off_packed + packed_bytes;
         p.off_res = p.off_inv + inv_bytes;
         p.off_queue = p.off_res + res_bytes;
-        p.warp_bytes = p.off_queue + queue_bytes;
+        p.off_meta = p.off_queue + queue_bytes;
+        p.warp_bytes = p.off_meta + 16u;
         p.off_neg1 = align16(kOffF + t.fbytes);
         p.off_warp = align16(p.off_neg1 + neg1_bytes);
         smem = p.off_warp + nw * p.warp_bytes;
@@ -1143,7 +1192,6 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.hbyte_lo = t.hash_byte[0];
     p.hbyte_hi = t.hash_byte[1];
     p.out = r.out;
-    p.vec_ok = ((reinterpret_cast<uintptr_t>(r.out) - 4u * p.tv.head) & 15u) == 0;
     p.cpos = r.pos;
     p.cids = r.ids;
     p.cap = r.cap;
@@ -1155,8 +1203,10 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     e = device_error_word(&p.err);
     if (e != cudaSuccess) return e;
     uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(sms);
-    const uint32_t need_ctas = (p.tv.ntiles + nw - 1) / nw;
-    if (grid > need_ctas) grid = need_ctas;
+    if (!batch) {  // a batch's units are counted on the device: every CTA starts
+        const uint32_t need_ctas = (p.ntiles + nw - 1) / nw;
+        if (grid > need_ctas) grid = need_ctas;
+    }
     if (grid == 0) return cudaSuccess;
     if (t.B == 2) {
         if (t.gbits == 16) return launch_modes<2, int16_t>(mode, p, grid, tu.block, smem, max_smem, stream);

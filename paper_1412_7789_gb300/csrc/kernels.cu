@@ -57,10 +57,10 @@ constexpr uint32_t kResBytes = kPass * 4;
 constexpr uint32_t kQueueBytes = kPass * 2;
 
 struct WarpParams {
-    const uint8_t *text;
-    const uint8_t *gbase;   // text rounded down to 16 bytes
+    const uint8_t *text;    // batch: base of all texts
     uint64_t n;
-    uint32_t head;          // text - gbase
+    const BatchHead *batch; // batch: this automaton's head and the planned list
+    const BatchItemDev *lists;
     uint32_t SLW;           // staged bytes per warp tile (tile + halo)
     uint32_t tw;            // positions per warp tile (kTW, or kPass for the compacted output)
     uint32_t nstages, ntiles;
@@ -72,15 +72,14 @@ struct WarpParams {
     int jslow;
     int hash_shift;          // >= 0: classify with the 3-bit hash
     uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
-    int32_t *out;
-    int vec_ok;
+    int32_t *out;           // batch: base of all outputs
     uint32_t *cpos;
     uint32_t *cids;
     unsigned long long cap;
     unsigned long long *count;
     unsigned long long *status;  // compact: one word per half tile
     unsigned int *counter;       // compact: next tile to claim
-    uint32_t off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue;
+    uint32_t off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue, off_meta;
 };
 
 struct WarpSmem {
@@ -93,46 +92,25 @@ struct WarpSmem {
     uint16_t *queue;
 };
 
-// Lane 0: start the bulk copy of warp tile `tile` into stage buffer `st`, or
-// mark the stage as the end of this warp's work.
-__device__ __forceinline__ void issue_stage(const WarpParams &p, uint64_t *bar, uint32_t *stile, uint8_t *st,
-                                            uint32_t tile) {
-    *stile = tile;
-    if (tile >= p.ntiles) {
-        mbar_arrive(bar);
-        return;
-    }
-    const uint64_t tlo = static_cast<uint64_t>(tile) * p.tw;
-    const uint64_t a1 = (static_cast<uint64_t>(p.head) + 15ull) & ~15ull;
-    const uint64_t a2 = (static_cast<uint64_t>(p.head) + p.n) & ~15ull;
-    const uint64_t lo = tlo > a1 ? tlo : a1;
-    const uint64_t hi = (tlo + p.SLW) < a2 ? (tlo + p.SLW) : a2;
-    if (a1 < a2 && lo < hi) {
-        const uint32_t bytes = static_cast<uint32_t>(hi - lo);
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_load(st + (lo - tlo), p.gbase + lo, bytes, bar);
-    } else {
-        mbar_arrive(bar);
-    }
+// The text and tile of work unit u (entry `item` of the planned list in a batch).
+__device__ __forceinline__ TileText tile_text(const WarpParams &p, const Work &wk, uint32_t u, uint32_t item) {
+    if (!wk.list) return make_text(p.text, p.out, p.n, u);
+    return batch_text(wk, p.text, p.out, item, u);
 }
 
-// The unaligned head and tail bytes of the text that the bulk copy leaves out
-// (at most 15 each): lanes 0-15 the head, 16-31 the tail.
-__device__ __forceinline__ void load_fringe(const WarpParams &p, uint8_t *st, uint64_t tlo, int lane) {
-    const uint64_t head = p.head, end = head + p.n;
-    const uint64_t a1 = (head + 15ull) & ~15ull, a2 = end & ~15ull;
-    uint64_t lo, hi;
-    if (lane < 16) {
-        lo = head;
-        hi = a1 < end ? a1 : end;
-    } else {
-        lo = a1 > a2 ? a1 : a2;
-        hi = end;
+// All lanes: point stage s at unit u (>= wk.units: the end of this warp's
+// work) and start its bulk copy.
+__device__ __forceinline__ void issue_unit(const WarpParams &p, const Work &wk, uint64_t *bar, uint32_t *stile,
+                                           uint32_t *sitem, uint8_t *st, uint32_t u, int lane) {
+    const uint32_t item = (wk.list && u < wk.units) ? find_item(wk, u, lane) : 0u;
+    if (lane == 0) {
+        *stile = u;
+        *sitem = item;
+        if (u >= wk.units)
+            mbar_arrive(bar);
+        else
+            issue_text_tile(tile_text(p, wk, u, item), p.tw, p.SLW, bar, st);
     }
-    if (lo < tlo) lo = tlo;
-    if (hi > tlo + p.SLW) hi = tlo + p.SLW;
-    const uint64_t idx = lo + static_cast<uint64_t>(lane & 15);
-    if (idx < hi) st[idx - tlo] = p.gbase[idx];
 }
 
 __device__ __forceinline__ uint32_t byte_of(uint32_t w, int b) {
@@ -150,9 +128,9 @@ __device__ __forceinline__ uint32_t classify4(const uint8_t *cls8, uint32_t w) {
 // bit for each position that cannot extend a walk (byte in no keyword, or
 // outside the text).  Returns true when no staged position has that bit.
 template <int B>
-__device__ __forceinline__ bool convert_stage(const WarpParams &p, const WarpSmem &w, int64_t gpb, bool interior,
-                                              int lane) {
-    const int64_t n = static_cast<int64_t>(p.n);
+__device__ __forceinline__ bool convert_stage(const WarpParams &p, const TileText &tt, const WarpSmem &w, int64_t gpb,
+                                              bool interior, int lane) {
+    const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t items = p.SLW / 8;
     uint8_t *inv8 = reinterpret_cast<uint8_t *>(w.inv);
     uint32_t any = 0;
@@ -243,13 +221,13 @@ __device__ __forceinline__ int jump_at(const uint8_t *jbase, uint32_t idx) {
 
 // Code of staged position q; false when q cannot extend a walk.
 template <int B, bool INV>
-__device__ __forceinline__ bool fetch_code(const WarpParams &p, const WarpSmem &w, int64_t gpb, uint32_t q,
-                                           uint32_t &c) {
+__device__ __forceinline__ bool fetch_code(const WarpParams &p, const TileText &tt, const WarpSmem &w, int64_t gpb,
+                                           uint32_t q, uint32_t &c) {
     if (q < p.SLW) {
         if (INV) {
             if ((w.inv[q >> 5] >> (q & 31u)) & 1u) return false;
         } else {
-            if (gpb + static_cast<int64_t>(q) >= static_cast<int64_t>(p.n)) return false;
+            if (gpb + static_cast<int64_t>(q) >= static_cast<int64_t>(tt.n)) return false;
         }
         if (B == 8)
             c = w.st[q];
@@ -258,8 +236,8 @@ __device__ __forceinline__ bool fetch_code(const WarpParams &p, const WarpSmem &
         return true;
     }
     const int64_t gp = gpb + static_cast<int64_t>(q);
-    if (gp >= static_cast<int64_t>(p.n)) return false;
-    const uint32_t b = __ldg(p.text + gp);
+    if (gp >= static_cast<int64_t>(tt.n)) return false;
+    const uint32_t b = __ldg(tt.text + gp);
     if (!INV) {
         c = b;
         return true;
@@ -273,10 +251,10 @@ __device__ __forceinline__ bool fetch_code(const WarpParams &p, const WarpSmem &
 // Finish up to SLOTS * 32 queued survivors (entries base.. of the queue, `avail`
 // of them): each lane takes SLOTS entries and advances their walks together.
 template <int B, bool INV, typename GT, int MODE, int SLOTS>
-__device__ __forceinline__ void finish_survivors(const WarpParams &p, const WarpSmem &w, int64_t gpb, bool interior,
-                                                 bool clean, uint32_t avail, uint32_t h, int lane,
-                                                 unsigned long long &cnt, uint32_t base = 0) {
-    const int64_t n = static_cast<int64_t>(p.n);
+__device__ __forceinline__ void finish_survivors(const WarpParams &p, const TileText &tt, const WarpSmem &w,
+                                                 int64_t gpb, bool interior, bool clean, uint32_t avail, uint32_t h,
+                                                 int lane, unsigned long long &cnt, uint32_t base = 0) {
+    const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k, k2 = p.k2;
     const uint32_t kmask = (1u << (B * k)) - 1u;
     const GT *G = static_cast<const GT *>(p.G);
@@ -340,7 +318,7 @@ __device__ __forceinline__ void finish_survivors(const WarpParams &p, const Warp
         for (int t = 0; t < SLOTS; ++t) {
             if ((walking >> t) & 1u) {
                 uint32_t c = 0;
-                const bool okc = fetch_code<B, INV>(p, w, gpb, q4[t], c);
+                const bool okc = fetch_code<B, INV>(p, tt, w, gpb, q4[t], c);
                 // an unknown byte or the text end reads the row's end column,
                 // which always holds the result of stopping there
                 e4[t] = goto_ld(G, st4[t], p.W, okc ? c : p.C);
@@ -374,9 +352,9 @@ __device__ __forceinline__ void finish_survivors(const WarpParams &p, const Warp
 enum : uint32_t { kInterior = 1u, kClean = 2u };
 
 template <int B, bool INV, typename GT, int MODE>
-__device__ __forceinline__ void match_pass(const WarpParams &p, const WarpSmem &w, int64_t gpb, uint32_t flags,
-                                           uint32_t tile, uint32_t h, int lane, unsigned long long &cnt) {
-    const int64_t n = static_cast<int64_t>(p.n);
+__device__ __forceinline__ void match_pass(const WarpParams &p, const TileText &tt, const WarpSmem &w, int64_t gpb,
+                                           uint32_t flags, uint32_t h, int lane, unsigned long long &cnt) {
+    const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k;
     const uint32_t kmask = (1u << (B * k)) - 1u;
     const bool interior = flags & kInterior;
@@ -462,21 +440,21 @@ __device__ __forceinline__ void match_pass(const WarpParams &p, const WarpSmem &
     //    their dependent loads overlap): stride table, then (rarely) the goto
     //    table one character at a time
     if (total <= 64) {
-        finish_survivors<B, INV, GT, MODE, 2>(p, w, gpb, interior, clean, total, h, lane, cnt);
+        finish_survivors<B, INV, GT, MODE, 2>(p, tt, w, gpb, interior, clean, total, h, lane, cnt);
     } else {
         for (uint32_t base = 0; base < total; base += 256)
-            finish_survivors<B, INV, GT, MODE, 8>(p, w, gpb, interior, clean, total - base, h, lane, cnt,
+            finish_survivors<B, INV, GT, MODE, 8>(p, tt, w, gpb, interior, clean, total - base, h, lane, cnt,
                                                   base);
     }
     __syncwarp();
 
     // 4. output
-    if (MODE == OUT_DENSE && interior && p.vec_ok) {
+    if (MODE == OUT_DENSE && interior && tt.vec_ok) {
         // the whole pass is inside the text: one bulk store of the staged ids
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) {
-            bulk_store(p.out + gpb + h * kPass, w.res, kResBytes);
+            bulk_store(tt.out + gpb + h * kPass, w.res, kResBytes);
             bulk_commit();
         }
     } else if (MODE == OUT_DENSE) {
@@ -484,13 +462,13 @@ __device__ __forceinline__ void match_pass(const WarpParams &p, const WarpSmem &
         for (int g = 0; g < 4; ++g) {
             const int4 r4 = reinterpret_cast<const int4 *>(w.res)[32 * g + lane];
             const int64_t gp0 = gpb + ibase + 128u * g;
-            if (p.vec_ok && ((valid >> (4 * g)) & 0xFu) == 0xFu) {
-                __stcs(reinterpret_cast<int4 *>(p.out + gp0), r4);
+            if (tt.vec_ok && ((valid >> (4 * g)) & 0xFu) == 0xFu) {
+                __stcs(reinterpret_cast<int4 *>(tt.out + gp0), r4);
             } else {
                 const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
-                    if ((valid >> (4 * g + r)) & 1u) p.out[gp0 + r] = rr[r];
+                    if ((valid >> (4 * g + r)) & 1u) tt.out[gp0 + r] = rr[r];
             }
         }
     }
@@ -514,7 +492,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match(const WarpParams p) {
     w.inv = reinterpret_cast<uint32_t *>(wreg + p.off_inv);
     w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
     w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
+    uint32_t *sitem = reinterpret_cast<uint32_t *>(wreg + p.off_meta);
     const uint32_t nst = p.nstages;
+    const Work wk = load_work(p.batch, p.lists, p.ntiles);
 
     if (threadIdx.x == 0) {
         mbar_init(jbar, 1);
@@ -534,13 +514,16 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match(const WarpParams p) {
     // Tiles are claimed from a global counter, so a warp that meets an
     // expensive tile (long walks) stops taking work while the others go on;
     // each warp's first tile is handed out statically.
-    auto next_tile = [&](uint32_t it) -> uint32_t {
-        if (it == 0) return gw < p.ntiles ? static_cast<uint32_t>(gw) : 0xFFFFFFFFu;
-        const uint64_t t = GW + atomicAdd(p.counter, 1u);
-        return t < p.ntiles ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+    auto next_tile = [&](uint32_t it) -> uint32_t {  // all lanes
+        uint32_t t = 0xFFFFFFFFu;
+        if (lane == 0) {
+            const uint64_t c = it == 0 ? gw : GW + atomicAdd(p.counter, 1u);
+            if (c < wk.units) t = static_cast<uint32_t>(c);
+        }
+        return __shfl_sync(kFull, t, 0);
     };
-    if (lane == 0)
-        for (uint32_t s = 0; s < nst; ++s) issue_stage(p, &bars[s], &stile[s], wreg + s * p.SLW, next_tile(s));
+    for (uint32_t s = 0; s < nst; ++s)
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.SLW, next_tile(s), lane);
 
     unsigned long long cnt = 0;
     bool ok = mbar_wait(jbar, 0);
@@ -559,26 +542,25 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match(const WarpParams p) {
             return;
         }
         const uint32_t tile = stile[s];
-        if (tile >= p.ntiles) break;
+        if (tile >= wk.units) break;
+        const TileText tt = tile_text(p, wk, tile, sitem[s]);
         w.st = wreg + s * p.SLW;
-        const uint64_t tlo = static_cast<uint64_t>(tile) * p.tw;
-        const int64_t gpb = static_cast<int64_t>(tlo) - p.head;
-        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.SLW) <= static_cast<int64_t>(p.n);
+        const uint64_t tlo = static_cast<uint64_t>(tt.tile) * p.tw;
+        const int64_t gpb = static_cast<int64_t>(tlo) - tt.head;
+        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.SLW) <= static_cast<int64_t>(tt.n);
         if (!interior) {
-            load_fringe(p, w.st, tlo, lane);
+            load_text_fringe(tt, p.SLW, w.st, tlo, lane);
             __syncwarp();
         }
         uint32_t flags = interior ? kInterior : 0u;
         if (B < 8 || INV) {
-            if (convert_stage<B>(p, w, gpb, interior, lane)) flags |= kClean;
+            if (convert_stage<B>(p, tt, w, gpb, interior, lane)) flags |= kClean;
             __syncwarp();
         }
 #pragma unroll 1
-        for (uint32_t h = 0; h < kTW / kPass; ++h) match_pass<B, INV, GT, MODE>(p, w, gpb, flags, tile, h, lane, cnt);
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            issue_stage(p, &bars[s], &stile[s], w.st, next_tile(it + nst));
-        }
+        for (uint32_t h = 0; h < kTW / kPass; ++h) match_pass<B, INV, GT, MODE>(p, tt, w, gpb, flags, h, lane, cnt);
+        if (lane == 0) fence_proxy_async_smem();
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], w.st, next_tile(it + nst), lane);
     }
 
     if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
@@ -678,7 +660,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match_compact(const WarpPar
     w.inv = reinterpret_cast<uint32_t *>(wreg + p.off_inv);
     w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
     w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
-    const uint32_t nchunks = (p.ntiles + nw - 1) / nw;
+    uint32_t *sitem = reinterpret_cast<uint32_t *>(wreg + p.off_meta);
+    const Work wk = load_work(nullptr, nullptr, p.ntiles);  // one text
+    const uint32_t nchunks = (wk.units + nw - 1) / nw;
 
     if (threadIdx.x == 0) {
         mbar_init(jbar, 1);
@@ -697,10 +681,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match_compact(const WarpPar
     }
     auto tile_of = [&](uint32_t c) -> uint32_t {
         const uint64_t t = static_cast<uint64_t>(c) * nw + warp;
-        return (c < nchunks && t < p.ntiles) ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
+        return (c < nchunks && t < wk.units) ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
     };
-    if (lane == 0)
-        for (uint32_t s = 0; s < 2; ++s) issue_stage(p, &bars[s], &stile[s], wreg + s * p.SLW, tile_of(chunk[s]));
+    for (uint32_t s = 0; s < 2; ++s)
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.SLW, tile_of(chunk[s]), lane);
 
     unsigned long long unused = 0;
     bool ok = mbar_wait(jbar, 0);
@@ -713,21 +697,22 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match_compact(const WarpPar
         const uint32_t tile = stile[s];
         uint32_t m = 0;
         int64_t gpb = 0;
-        if (ok && tile < p.ntiles) {
+        if (ok && tile < wk.units) {
+            const TileText tt = tile_text(p, wk, tile, sitem[s]);
             w.st = wreg + s * p.SLW;
-            const uint64_t tlo = static_cast<uint64_t>(tile) * p.tw;
-            gpb = static_cast<int64_t>(tlo) - p.head;
-            const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.SLW) <= static_cast<int64_t>(p.n);
+            const uint64_t tlo = static_cast<uint64_t>(tt.tile) * p.tw;
+            gpb = static_cast<int64_t>(tlo) - tt.head;
+            const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.SLW) <= static_cast<int64_t>(tt.n);
             if (!interior) {
-                load_fringe(p, w.st, tlo, lane);
+                load_text_fringe(tt, p.SLW, w.st, tlo, lane);
                 __syncwarp();
             }
             uint32_t flags = interior ? kInterior : 0u;
             if (B < 8 || INV) {
-                if (convert_stage<B>(p, w, gpb, interior, lane)) flags |= kClean;
+                if (convert_stage<B>(p, tt, w, gpb, interior, lane)) flags |= kClean;
                 __syncwarp();
             }
-            match_pass<B, INV, GT, OUT_COMPACT>(p, w, gpb, flags, tile, 0, lane, unused);
+            match_pass<B, INV, GT, OUT_COMPACT>(p, tt, w, gpb, flags, 0, lane, unused);
             m = count_staged(w.res, lane);
         }
         if (lane == 0) {
@@ -762,12 +747,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_match_compact(const WarpPar
             }
         }
         __syncthreads();
-        if (tile < p.ntiles) write_staged(p, w.res, gpb, bases[warp], lane);
+        if (tile < wk.units) write_staged(p, w.res, gpb, bases[warp], lane);
         __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            issue_stage(p, &bars[s], &stile[s], wreg + s * p.SLW, tile_of(chunk[s]));
-        }
+        if (lane == 0) fence_proxy_async_smem();
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.SLW, tile_of(chunk[s]), lane);
     }
 }
 
@@ -808,7 +791,7 @@ __global__ void __launch_bounds__(256) pfac_simple(const uint8_t *__restrict__ t
 inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
 
 struct Geometry {
-    uint32_t SLW, nstages, ntiles, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue, smem;
+    uint32_t SLW, nstages, ntiles, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue, off_meta, smem;
 };
 
 // Warp tile: two passes, or one for the compacted output (a warp keeps one
@@ -829,13 +812,14 @@ bool make_geometry(const DevTables &t, uint64_t n, uint32_t head, OutMode mode, 
     const bool inv = t.B < 8 || t.C < 256;
     const uint32_t packed_bytes = t.B < 8 ? align16(g->SLW * t.B / 8 + 16) : 0u;
     const uint32_t inv_bytes = inv ? align16(g->SLW / 8 + 16) : 0u;
-    for (int st = mode == OUT_COMPACT ? 2 : tu.stages; st >= 2; --st) {
+    for (int st = (mode == OUT_COMPACT || tu.stages == 0) ? 2 : tu.stages; st >= 2; --st) {
         g->nstages = static_cast<uint32_t>(st);
         g->off_packed = g->nstages * g->SLW;
         g->off_inv = align16(g->off_packed + packed_bytes);
         g->off_res = align16(g->off_inv + inv_bytes);
         g->off_queue = g->off_res + kResBytes;
-        g->warp_bytes = align16(g->off_queue + kQueueBytes);
+        g->off_meta = g->off_queue + kQueueBytes;
+        g->warp_bytes = align16(g->off_meta + 16u);
         g->off_warp = align16(kOffJ + t.jbytes);
         g->smem = g->off_warp + nw * g->warp_bytes;
         if (static_cast<int>(g->smem) <= max_smem) return true;
@@ -910,6 +894,8 @@ cudaError_t device_props(DeviceProps *out) {
 
 }  // namespace
 
+uint32_t tiled_tile_positions() { return kTW; }
+
 size_t scratch_bytes(const DevTables &t, uint64_t n, OutMode mode, const Tuning &tu) {
     (void)t;
     if (mode != OUT_COMPACT) return 16;
@@ -921,18 +907,22 @@ size_t scratch_bytes(const DevTables &t, uint64_t n, OutMode mode, const Tuning 
 
 cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                          cudaStream_t stream) {
-    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || tu.stages < 2 || tu.stages > kMaxStages)
+    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
+        tu.stages > kMaxStages)
         return cudaErrorInvalidValue;
     DeviceProps dp;
     cudaError_t e = device_props(&dp);
     if (e != cudaSuccess) return e;
+    const bool batch = r.batch != nullptr;
+    if (batch && (mode != OUT_DENSE || !r.lists)) return cudaErrorInvalidValue;
     WarpParams p{};
     p.text = r.text;
-    p.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(r.text) & 15u);
-    p.gbase = r.text - p.head;
     p.n = r.n;
+    p.batch = r.batch;
+    p.lists = r.lists;
+    const uint32_t head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(r.text) & 15u);
     Geometry g;
-    if (!make_geometry(t, r.n, p.head, mode, tu, dp.max_smem, &g)) return cudaErrorInvalidConfiguration;
+    if (!make_geometry(t, batch ? 0 : r.n, head, mode, tu, dp.max_smem, &g)) return cudaErrorInvalidConfiguration;
     p.tw = tile_len(mode);
     p.SLW = g.SLW;
     p.nstages = g.nstages;
@@ -943,6 +933,7 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     p.off_inv = g.off_inv;
     p.off_res = g.off_res;
     p.off_queue = g.off_queue;
+    p.off_meta = g.off_meta;
     p.G = t.G;
     p.Jg = t.J;
     p.J2 = t.J2;
@@ -961,7 +952,6 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     p.hbyte_lo = t.hash_byte[0];
     p.hbyte_hi = t.hash_byte[1];
     p.out = r.out;
-    p.vec_ok = ((reinterpret_cast<uintptr_t>(r.out) - 4u * p.head) & 15u) == 0;
     p.cpos = r.pos;
     p.cids = r.ids;
     p.cap = r.cap;
@@ -973,8 +963,10 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
         p.status = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(r.scratch) + 16);
     const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
     uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(dp.sms);
-    const uint32_t need = (g.ntiles + nw - 1) / nw;
-    if (grid > need) grid = need;
+    if (!batch) {  // a batch's units are counted on the device: every CTA starts
+        const uint32_t need = (g.ntiles + nw - 1) / nw;
+        if (grid > need) grid = need;
+    }
     if (grid == 0) return cudaSuccess;
     if (t.gbits == 16)
         return launch_gt<int16_t>(t, mode, p, grid, static_cast<uint32_t>(tu.block), g.smem, dp.max_smem, stream);

@@ -13,7 +13,6 @@
 
 namespace pfac {
 
-enum : unsigned { kErrTimeout = 1u, kErrWalk = 2u, kErrLookback = 4u };
 
 // Every bounded wait gives up after this many nanoseconds of %globaltimer.
 constexpr unsigned long long kWaitNs = 2000000000ull;
@@ -116,37 +115,101 @@ __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long 
 
 __device__ __forceinline__ int decode_dead(int e) { return -e - 2; }
 
-// Geometry of one text as the tiled kernels see it: text = gbase + head,
-// gbase 16-byte aligned; tile t stages bytes [t * tile, t * tile + staged) of
-// gbase (the part inside the text).
-struct TextView {
-    const uint8_t *gbase;
-    uint64_t n;
-    uint32_t head;
-    uint32_t tile;     // positions per tile (multiple of 16)
-    uint32_t staged;   // bytes staged per tile (multiple of 16)
-    uint32_t ntiles;
+// The text a work unit (one tile) belongs to.  The text is gbase + head with
+// gbase 16-byte aligned; tile t covers text positions [t * tile_len - head,
+// (t + 1) * tile_len - head) and stages bytes [t * tile_len, t * tile_len +
+// staged) of gbase, the part of them inside the text.
+struct TileText {
+    const uint8_t *text;   // first byte of the text
+    const uint8_t *gbase;  // text rounded down to 16 bytes
+    int32_t *out;          // its dense ids (out[i] for text position i)
+    uint64_t n;            // its length
+    uint32_t head;         // text - gbase
+    uint32_t tile;         // the unit's tile within the text
+    uint32_t vec_ok;       // out - 4 * head is 16-byte aligned (tiles store 16-byte groups)
 };
 
-// One thread: start the bulk copy of tile `t` into shared buffer `st`, or mark
-// the stage as the end of this warp's work (t >= ntiles).  Only the 16-byte
-// aligned part inside the text is copied; load_fringe fetches the rest.
-__device__ __forceinline__ void issue_tile(const TextView &v, uint64_t *bar, uint32_t *stile, uint8_t *st,
-                                           uint32_t t) {
-    *stile = t;
-    if (t >= v.ntiles) {
-        mbar_arrive(bar);
-        return;
+__device__ __forceinline__ TileText make_text(const uint8_t *text, int32_t *out, uint64_t n, uint32_t tile) {
+    TileText t;
+    t.text = text;
+    t.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text) & 15u);
+    t.gbase = text - t.head;
+    t.out = out;
+    t.n = n;
+    t.tile = tile;
+    t.vec_ok = ((reinterpret_cast<uintptr_t>(out) - 4u * t.head) & 15u) == 0 ? 1u : 0u;
+    return t;
+}
+
+// Where a launch's work units come from: the tiles of one text (list ==
+// nullptr), or the tiles of a batch's texts (the planned list of one
+// automaton, ascending in first_unit).
+struct Work {
+    uint32_t units;
+    uint32_t nlist;
+    const BatchItemDev *list;
+};
+
+__device__ __forceinline__ Work load_work(const BatchHead *head, const BatchItemDev *lists, uint32_t single_units) {
+    Work w;
+    if (!head) {
+        w.units = single_units;
+        w.nlist = 0;
+        w.list = nullptr;
+        return w;
     }
-    const uint64_t tlo = static_cast<uint64_t>(t) * v.tile;
-    const uint64_t a1 = (static_cast<uint64_t>(v.head) + 15ull) & ~15ull;
-    const uint64_t a2 = (static_cast<uint64_t>(v.head) + v.n) & ~15ull;
+    const uint4 h = __ldg(reinterpret_cast<const uint4 *>(head));
+    w.units = h.x;
+    w.nlist = h.y;
+    w.list = lists + h.z;
+    return w;
+}
+
+// The batch text of entry `item` of the planned list, for its unit u.
+__device__ __forceinline__ TileText batch_text(const Work &wk, const uint8_t *texts, int32_t *outs, uint32_t item,
+                                               uint32_t u) {
+    const uint4 *e = reinterpret_cast<const uint4 *>(wk.list + item);
+    const uint4 a = __ldg(e), b = __ldg(e + 1);
+    const uint64_t text_off = static_cast<uint64_t>(a.x) | (static_cast<uint64_t>(a.y) << 32);
+    const uint64_t len = static_cast<uint64_t>(a.z) | (static_cast<uint64_t>(a.w) << 32);
+    const uint64_t out_off = static_cast<uint64_t>(b.x) | (static_cast<uint64_t>(b.y) << 32);
+    return make_text(texts + text_off, outs + out_off, len, u - b.z);
+}
+
+// All lanes of a warp, u warp-uniform: the index of the last entry of the
+// planned list whose first_unit <= u, i.e. the text that unit u belongs to
+// (list[0].first_unit == 0; empty texts are not in the list).  32 entries are
+// sampled per round, so three rounds cover 32768 texts.
+__device__ __forceinline__ uint32_t find_item(const Work &wk, uint32_t u, int lane) {
+    uint32_t lo = 0, hi = wk.nlist;
+    while (hi - lo > 32u) {
+        const uint32_t step = (hi - lo + 31u) / 32u;
+        const uint32_t idx = lo + static_cast<uint32_t>(lane) * step;
+        const bool le = idx < hi && __ldg(&wk.list[idx].first_unit) <= u;
+        const unsigned b = __ballot_sync(0xffffffffu, le);  // bit 0 set: list[lo] <= u
+        lo += static_cast<uint32_t>(31 - __clz(b)) * step;
+        hi = (lo + step) < hi ? (lo + step) : hi;
+    }
+    const uint32_t idx = lo + static_cast<uint32_t>(lane);
+    const bool le = idx < hi && __ldg(&wk.list[idx].first_unit) <= u;
+    const unsigned b = __ballot_sync(0xffffffffu, le);
+    return lo + static_cast<uint32_t>(31 - __clz(b));
+}
+
+// One thread: start the bulk copy of tile t.tile into shared buffer st.  Only
+// the 16-byte aligned part inside the text is copied; load_text_fringe fetches
+// the rest.
+__device__ __forceinline__ void issue_text_tile(const TileText &t, uint32_t tile_len, uint32_t staged,
+                                                uint64_t *bar, uint8_t *st) {
+    const uint64_t tlo = static_cast<uint64_t>(t.tile) * tile_len;
+    const uint64_t a1 = (static_cast<uint64_t>(t.head) + 15ull) & ~15ull;
+    const uint64_t a2 = (static_cast<uint64_t>(t.head) + t.n) & ~15ull;
     const uint64_t lo = tlo > a1 ? tlo : a1;
-    const uint64_t hi = (tlo + v.staged) < a2 ? (tlo + v.staged) : a2;
+    const uint64_t hi = (tlo + staged) < a2 ? (tlo + staged) : a2;
     if (a1 < a2 && lo < hi) {
         const uint32_t bytes = static_cast<uint32_t>(hi - lo);
         mbar_arrive_expect_tx(bar, bytes);
-        bulk_load(st + (lo - tlo), v.gbase + lo, bytes, bar);
+        bulk_load(st + (lo - tlo), t.gbase + lo, bytes, bar);
     } else {
         mbar_arrive(bar);
     }
@@ -154,8 +217,9 @@ __device__ __forceinline__ void issue_tile(const TextView &v, uint64_t *bar, uin
 
 // A warp: the unaligned head and tail bytes of the text that the bulk copy
 // leaves out (at most 15 each): lanes 0-15 the head, 16-31 the tail.
-__device__ __forceinline__ void load_fringe(const TextView &v, uint8_t *st, uint64_t tlo, int lane) {
-    const uint64_t head = v.head, end = head + v.n;
+__device__ __forceinline__ void load_text_fringe(const TileText &t, uint32_t staged, uint8_t *st, uint64_t tlo,
+                                                 int lane) {
+    const uint64_t head = t.head, end = head + t.n;
     const uint64_t a1 = (head + 15ull) & ~15ull, a2 = end & ~15ull;
     uint64_t lo, hi;
     if (lane < 16) {
@@ -166,46 +230,9 @@ __device__ __forceinline__ void load_fringe(const TextView &v, uint8_t *st, uint
         hi = end;
     }
     if (lo < tlo) lo = tlo;
-    if (hi > tlo + v.staged) hi = tlo + v.staged;
+    if (hi > tlo + staged) hi = tlo + staged;
     const uint64_t idx = lo + static_cast<uint64_t>(lane & 15);
-    if (idx < hi) st[idx - tlo] = v.gbase[idx];
-}
-
-// Decoupled look-back over per-unit status words (flag in the top 2 bits:
-// 1 = this unit's count, 2 = inclusive prefix); returns the number of matches
-// in all earlier units.  A predecessor that never publishes ends the wait
-// after kWaitNs with the error latched in *err.
-__device__ __forceinline__ unsigned long long lookback(unsigned long long *status, uint32_t unit,
-                                                       unsigned long long total, unsigned int *err) {
-    constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = (1ull << 62) - 1ull;
-    if (unit == 0) {
-        st_relaxed(&status[0], kPre | total);
-        return 0ull;
-    }
-    st_relaxed(&status[unit], kAgg | total);
-    unsigned long long excl = 0;
-    int64_t pred = static_cast<int64_t>(unit) - 1;
-    unsigned long long t0 = 0;
-    while (pred >= 0) {
-        const unsigned long long v = ld_relaxed(&status[pred]);
-        const unsigned long long f = v >> 62;
-        if (f == 0) {
-            const unsigned long long now = global_timer();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > kWaitNs) {
-                atomicOr(err, static_cast<unsigned>(kErrLookback));
-                break;
-            }
-            continue;
-        }
-        excl += v & kVal;
-        if (f == 2) break;
-        --pred;
-        t0 = 0;
-    }
-    st_relaxed(&status[unit], kPre | (excl + total));
-    return excl;
+    if (idx < hi) st[idx - tlo] = t.gbase[idx];
 }
 
 template <typename GT>

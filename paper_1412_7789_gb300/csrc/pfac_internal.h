@@ -7,6 +7,8 @@
 
 #include <cuda_runtime_api.h>
 
+#include "ac.h"
+
 namespace pfac {
 
 // A dead goto entry encodes the result of a walk that stops at its row:
@@ -20,6 +22,9 @@ inline int32_t encode_dead(int32_t id) { return -(id + 2); }
 // plain walk (a result that does not fit 15 bits).
 constexpr int16_t kJumpSlow = -32768;
 constexpr uint32_t kJumpMaxStates = 32766;
+
+// Bits of the per-device kernel error word.
+enum : unsigned { kErrTimeout = 1u, kErrWalk = 2u, kErrLookback = 4u, kErrBatchItem = 8u };
 
 // Window bits of the root filter (2- and 4-bit codes): 2^20 bits = 128 KiB.
 constexpr uint32_t kFilterBits = 20;
@@ -96,10 +101,28 @@ struct DevTables {
 
 enum OutMode : int { OUT_DENSE = 0, OUT_COUNT = 1, OUT_COMPACT = 2 };
 
+// One text of a batch as the matching kernels read it: its bytes at
+// texts + text_off, its dense ids at outs + out_off, its tiles numbered from
+// first_unit among the texts of its automaton.  Written on the device by the
+// batch planning kernel; `item` is the text's index in the caller's list.
+struct alignas(16) BatchItemDev {
+    uint64_t text_off, len, out_off;
+    uint32_t first_unit, item;
+};
+static_assert(sizeof(BatchItemDev) == 32, "BatchItemDev is read as two 16-byte words");
+
+// Per automaton of a batch: its tiles (work units), its non-empty texts and
+// where they start in the planned list (ascending first_unit).
+struct BatchHead {
+    uint32_t units, count, offset, pad;
+};
+
 struct MatchRequest {
-    const uint8_t *text = nullptr;
-    uint64_t n = 0;
-    int32_t *out = nullptr;                  // dense
+    const uint8_t *text = nullptr;           // batch: base of all texts
+    uint64_t n = 0;                          // batch: unused
+    int32_t *out = nullptr;                  // dense (batch: base of all outputs)
+    const BatchHead *batch = nullptr;        // batch: this automaton's head (device)
+    const BatchItemDev *lists = nullptr;     // batch: the planned list (device)
     unsigned long long *count = nullptr;     // count / compact total
     uint32_t *pos = nullptr;                 // compact
     uint32_t *ids = nullptr;                 // compact
@@ -110,7 +133,8 @@ struct MatchRequest {
 
 struct Tuning {
     int block = 512;      // threads per CTA (multiple of 32, <= 512)
-    int stages = 2;       // text stages in flight per warp (2..4; fewer if shared memory is short)
+    int stages = 0;       // text stages in flight per warp (2..4, 0 = the kernel's default;
+                          // fewer when shared memory is short)
     int grid = 0;         // 0 = one CTA per SM
 };
 
@@ -128,9 +152,23 @@ cudaError_t read_device_error(unsigned int *value);
 // Device address of the current device's kernel error word.
 cudaError_t device_error_word(unsigned int **ptr);
 
+// Batch planning (batch.cu): from the caller's item list (device), one
+// BatchHead per automaton and the non-empty texts of each automaton in item
+// order with their first work unit.  tile_len: host array of nh entries, the
+// dense tile length of each automaton's kernel (filter_tile_positions or
+// tiled_tile_positions).  An item whose automaton is >= nh, or an automaton
+// with 2^32 or more units, latches kErrBatchItem.
+constexpr uint32_t kMaxBatchAutomata = 256;
+cudaError_t launch_batch_plan(const ac_batch_item *items, uint32_t nitems, uint32_t nh, const uint8_t *texts,
+                              const uint32_t *tile_len, BatchHead *heads, BatchItemDev *lists, cudaStream_t stream);
+
 // Filter-mode kernel (2- and 4-bit codes), in filter.cu.
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                           cudaStream_t stream);
 size_t filter_scratch_bytes(uint64_t n, OutMode mode);
+// Positions per work unit (tile) of the dense filter kernel and of the dense
+// 8-bit kernel: the tile lengths a batch is planned with.
+uint32_t filter_tile_positions();
+uint32_t tiled_tile_positions();
 
 }  // namespace pfac

@@ -229,3 +229,26 @@ def batch_texts(count: int, lmin: int, lmax: int, seed: int = 0):
         else:
             texts.append(zipf_text(int(lengths[i]), sub))
     return texts, kinds
+
+
+def batch_layout(texts, kinds, n_sets: int = 8, seed: int = 0):
+    """Pack ``texts`` back to back (no gaps, so most start unaligned) and give
+    each a keyword set of its own alphabet, uniformly: sets 0, 2, 4, ... are
+    ACGT and 1, 3, 5, ... Zipf-256 (``batch_pattern_sets``).  Returns
+    (buffer, offsets, lengths, set index per text); a dense output laid out
+    like the buffer uses the same offsets."""
+    g = rng(seed + 99)
+    lens = np.array([t.size for t in texts], dtype=np.int64)
+    offs = np.zeros(len(texts), dtype=np.int64)
+    if len(texts) > 1:
+        offs[1:] = np.cumsum(lens)[:-1]
+    buf = np.concatenate(texts) if len(texts) else np.zeros(0, dtype=np.uint8)
+    half = (n_sets + 1) // 2
+    pick = g.integers(0, 1 << 30, size=len(texts))
+    sets = np.empty(len(texts), dtype=np.int64)
+    for i, k in enumerate(kinds):
+        if k == 0:
+            sets[i] = 2 * (pick[i] % half)
+        else:
+            sets[i] = 2 * (pick[i] % (n_sets // 2)) + 1
+    return buf, offs, lens, sets
