@@ -43,9 +43,9 @@ KNOWN_TRAFFIC = {("sweep", GIB, "pfac_filter_pipe"): 5.408e9}
 def kernel_name(info: dict, out_kind: str, kernel: str) -> str:
     if kernel == "simple":
         return "pfac_simple"
-    if info["code_bits"] <= 4:
-        return "pfac_filter" if out_kind == "compact" else "pfac_filter_pipe"
-    return "pfac_match"
+    name = "pfac_filter_pipe" if info["code_bits"] <= 4 else "pfac_walk8"
+    # the compacted list: the matcher in slot mode, then scan and gather
+    return name + "+compact" if out_kind == "compact" else name
 
 
 def load_peaks():
@@ -221,6 +221,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         import torch.distributed as dist
 
     text_np, pats, desc, out_kind = make_workload(args.workload, args.n)
+    if args.out:
+        out_kind = args.out
+        desc += " [output: %s]" % out_kind
     n = text_np.size
     a = api.Automaton(pats)
     if args.kernel == "simple":
@@ -235,6 +238,13 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             api.ac_match(a.handle, text, n, out, stream)
 
         out_bytes_per_pos = 4.0
+    elif out_kind == "count":
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+
+        def step():
+            api.ac_count(a.handle, text, n, cnt, stream)
+
+        out_bytes_per_pos = 0.0
     else:
         cap = max(1, n // 256)
         pos = torch.empty(cap, dtype=torch.int32, device=dev)
@@ -253,6 +263,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if matches > cap:
             raise SystemExit("compact capacity too small: %d > %d" % (matches, cap))
         algo_bytes = n + 8 * matches
+    elif out_kind == "count":
+        matches = int(cnt.item())
+        algo_bytes = n
     else:
         matches = None
         algo_bytes = n * (1 + out_bytes_per_pos)
@@ -347,7 +360,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "l2": "inputs larger than L2 (%.1f GB text + output per step)" % (algo_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps, "extra": extra,
+            "gpu_launches": args.steps * (4 if out_kind == "compact" else 1), "extra": extra,
         }
         print(json.dumps(line), flush=True)
 
@@ -728,6 +741,126 @@ def run_batch(args):
         a.close()
 
 
+# ----------------------------------------------------------------------------
+# served workload: Poisson arrivals, 16 resident automata, continuous batching
+# ----------------------------------------------------------------------------
+def _serve_run(api, handles, reqs, arrivals, fifo, budget):
+    with api.Server(handles, hbm_budget=budget, fifo=fifo) as srv:
+        srv.replay(reqs, arrivals)
+        srv.drain()
+        done = srv.poll(len(reqs) + 16)
+    if len(done) != len(reqs) or not np.all(done["status"] == 0):
+        raise SystemExit("serve: %d of %d requests completed, statuses %s" % (
+            len(done), len(reqs), sorted(set(done["status"].tolist()))))
+    lat = done["t_done_us"] - done["t_submit_us"]
+    span_s = (done["t_done_us"].max() - done["t_submit_us"].min()) * 1e-6
+    return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+            "mean_us": float(lat.mean()), "span_s": span_s, "mean_wave": float(done["wave_size"].mean())}
+
+
+def run_serve(args):
+    """Config: Poisson arrivals at several rates of requests for the compacted
+    match of a text of log-uniform length 256 B - 64 MiB (mean 5.4 MB) taken
+    from a device-resident pool (1 GiB ACGT, 1 GiB Zipf(1.1) bytes), each
+    naming one of 16 resident automata (1k-50k keywords of length 4-100; 8
+    ACGT, 8 Zipf), admitted under a 40 GB HBM budget (automata + requests in
+    flight).  Per rate: p50/p99 latency (submission to observed completion)
+    and aggregate GB/s, for the continuous-batching server and for FIFO
+    one-launch-per-request through the same harness."""
+    import torch
+
+    from paper_1412_7789_gb300 import api, build
+    from paper_1412_7789_gb300 import workloads as W
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    sets = W.serve_pattern_sets(seed=0)
+    pool_bytes = args.serve_pool
+    pools = [W.acgt_text(pool_bytes, 11), W.zipf_text(pool_bytes, 12)]
+    d_pools = [torch.from_numpy(p).to(dev) for p in pools]
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    autos = [api.Automaton(p) for p in sets]
+    build_s = time.perf_counter() - t0
+    handles = [a.handle for a in autos]
+    table_bytes = sum(a.info()["table_bytes"] for a in autos)
+    budget = int(40e9) - table_bytes
+
+    n_max = max(args.serve_requests)
+    which, offs, lens = W.serve_requests(n_max, pool_bytes, seed=0)
+    caps = np.maximum(1, lens // 64)
+    cap_off = np.concatenate([[0], np.cumsum(caps)[:-1]])
+    out_pos = torch.empty(int(caps.sum()), dtype=torch.int32, device=dev)
+    out_ids = torch.empty(int(caps.sum()), dtype=torch.int32, device=dev)
+    counts = torch.zeros(n_max, dtype=torch.int64, device=dev)
+    reqs = np.zeros(n_max, dtype=api.SERVER_REQUEST)
+    reqs["automaton"] = which
+    alpha = (which >= 8).astype(np.int64)
+    base = np.array([d_pools[0].data_ptr(), d_pools[1].data_ptr()], dtype=np.uint64)
+    reqs["d_text"] = base[alpha] + offs.astype(np.uint64)
+    reqs["n"] = lens
+    reqs["d_pos"] = np.uint64(out_pos.data_ptr()) + 4 * cap_off.astype(np.uint64)
+    reqs["d_ids"] = np.uint64(out_ids.data_ptr()) + 4 * cap_off.astype(np.uint64)
+    reqs["cap"] = caps
+    reqs["d_count"] = np.uint64(counts.data_ptr()) + 8 * np.arange(n_max, dtype=np.uint64)
+
+    # warm-up (module loading, pool growth), then a parity spot check
+    _serve_run(api, handles, reqs[:64], W.poisson_arrivals(64, 1000.0, seed=99), False, budget)
+    torch.cuda.synchronize(dev)
+    import oracle
+
+    got_counts = counts.cpu().numpy()
+    checked = 0
+    for i in range(64):
+        if lens[i] > (256 << 10) or checked >= 8:
+            continue
+        text = pools[alpha[i]][offs[i]:offs[i] + lens[i]]
+        wp, wi = oracle.compact(oracle.pfac_ids(sets[which[i]], text))
+        m = min(wp.size, caps[i])
+        gp = out_pos[cap_off[i]:cap_off[i] + m].cpu().numpy().astype(np.uint32)
+        gi = out_ids[cap_off[i]:cap_off[i] + m].cpu().numpy().astype(np.uint32)
+        if got_counts[i] != wp.size or not (np.array_equal(gp, wp[:m]) and np.array_equal(gi, wi[:m])):
+            raise SystemExit("serve parity failure: request %d" % i)
+        checked += 1
+
+    sampler = ClockSampler(int(os.environ.get("BENCH_GPU_INDEX", 0)))
+    sampler.start()
+    time.sleep(0.3)
+    rows = []
+    m0 = sampler.mark()
+    for rate, n in zip(args.serve_rates, args.serve_requests):
+        arr = W.poisson_arrivals(n, rate, seed=int(rate))
+        total = int(lens[:n].sum())
+        cb = _serve_run(api, handles, reqs[:n], arr, False, budget)
+        ff = _serve_run(api, handles, reqs[:n], arr, True, budget)
+        rows.append({"rate_per_s": rate, "requests": n, "bytes": total,
+                     "offered_gbs": total / (arr[-1] * 1e-6) / 1e9,
+                     "gbs": total / cb["span_s"] / 1e9, "p50_us": cb["p50_us"], "p99_us": cb["p99_us"],
+                     "mean_wave": cb["mean_wave"],
+                     "fifo_gbs": total / ff["span_s"] / 1e9, "fifo_p50_us": ff["p50_us"],
+                     "fifo_p99_us": ff["p99_us"]})
+    m1 = sampler.mark()
+    time.sleep(0.25)
+    sampler.stop()
+    top = rows[-1]
+    line = {
+        "metric": "served GB/s and p50/p99 latency (1 GB300)", "value": top["gbs"], "unit": "GB/s", "n_gpus": 1,
+        "steps": len(rows), "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "serve: Poisson arrivals at %s req/s, texts log-uniform 256 B-64 MiB from a device "
+                               "pool (%d B ACGT + %d B Zipf), 16 resident automata (1k-50k keywords, length "
+                               "4-100, 8 ACGT + 8 Zipf), compacted (pos,id) per request, 40 GB budget" % (
+                                   list(args.serve_rates), pool_bytes, pool_bytes)},
+        "serve": rows, "clocks": sampler.summary(m0, m1),
+        "extra": {"automata_table_bytes": table_bytes, "request_budget_bytes": budget,
+                  "host_build_s": build_s, "generate_s": gen_s, "parity_requests_checked": checked},
+    }
+    print(json.dumps(line), flush=True)
+    for a in autos:
+        a.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -737,6 +870,8 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "zipf", "single"])
     ap.add_argument("--n", type=int, default=None, help="text bytes (default: the workload's size)")
     ap.add_argument("--kernel", default="tiled", choices=["tiled", "simple"])
+    ap.add_argument("--out", default=None, choices=["dense", "count", "compact"],
+                    help="output kind (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--compare-simple", action="store_true")
@@ -750,6 +885,11 @@ def main():
                     help="batched workload (4,096 texts, eight automata) instead of the throughput line")
     ap.add_argument("--batch-texts", type=int, default=4096)
     ap.add_argument("--autotune", action="store_true", help="batch: autotune each automaton first")
+    ap.add_argument("--serve", action="store_true",
+                    help="served workload (Poisson arrivals, 16 automata) instead of the throughput line")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000, 3000, 10000, 30000, 100000])
+    ap.add_argument("--serve-requests", type=int, nargs="+", default=[3000, 6000, 20000, 20000, 20000])
+    ap.add_argument("--serve-pool", type=int, default=GIB)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.sweep:
@@ -757,6 +897,11 @@ def main():
         return
     if args.batch:
         run_batch(args)
+        return
+    if args.serve:
+        if len(args.serve_requests) != len(args.serve_rates):
+            raise SystemExit("--serve-requests needs one count per rate")
+        run_serve(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

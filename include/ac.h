@@ -199,8 +199,8 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
  *   - The paper has no counterpart: this is a deployment variant of the
  *     compacted output.
  */
-#define AC_STATIC_MAX_TEXT (64ull << 20)
-#define AC_STATIC_SCRATCH_BYTES (2u << 20)
+#define AC_STATIC_MAX_TEXT (16ull << 20)
+#define AC_STATIC_SCRATCH_BYTES (5u << 20)
 ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
                                   uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream);
 
@@ -284,6 +284,90 @@ ac_status ac_batch_destroy(ac_batch b);
  */
 ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t reps, void *stream,
                       uint32_t *block, uint32_t *stages);
+
+/*
+ * ---- Serving: continuous batching of compacted-match requests ---------------
+ * No counterpart in the paper.  A server keeps nh compiled automata (the
+ * caller's handles, resident on the device) and a worker thread that turns the
+ * stream of requests into launch waves:
+ *   - a request names an automaton and a device text, and gets the compacted
+ *     (pos, id) list of that text as ac_match_compact would give it, in caller
+ *     buffers (d_pos, d_ids, cap, d_count with the same meaning);
+ *   - requests are admitted in arrival order while the bytes they hold on the
+ *     device (text + 8 * cap output + about 0.27 byte of scratch per text byte)
+ *     fit in the HBM budget; a request larger than the whole budget is refused
+ *     with AC_ERR_BUDGET at submission;
+ *   - every admitted request that is not yet on the GPU joins the next wave:
+ *     one persistent launch per automaton over the tiles of all its requests,
+ *     then one scan and one gather, so requests of any size share the launches;
+ *   - up to waves_in_flight waves run at once on their own streams: requests
+ *     that arrive while a wave is on the GPU go into the next one and overlap
+ *     it as SMs free up; a wave's requests complete when its last kernel ends.
+ * A request's results are the same whatever else shares its wave.
+ *
+ * Options (zero = default):
+ *   hbm_budget       device bytes of admitted requests (default 40 GiB)
+ *   max_wave         most requests per wave (default 4096)
+ *   waves_in_flight  waves on the GPU at once (default 2, at most 8)
+ *   fifo             1 = the comparison point: one request per wave, one wave
+ *                    at a time, matched by the single-text ac_match_compact path
+ */
+typedef struct ac_server_impl *ac_server;
+
+typedef struct {
+    uint64_t hbm_budget;
+    uint32_t max_wave;
+    uint32_t waves_in_flight;
+    uint32_t fifo;
+    uint32_t reserved;
+} ac_server_options;
+
+typedef struct {
+    uint32_t automaton;      /* index into the server's handles            */
+    uint32_t reserved;       /* 0                                          */
+    const uint8_t *d_text;   /* device text, n < 2^32 bytes                */
+    uint64_t n;
+    uint32_t *d_pos;         /* device, cap entries                        */
+    uint32_t *d_ids;         /* device, cap entries                        */
+    uint64_t cap;
+    uint64_t *d_count;       /* device uint64: the true number of matches  */
+} ac_server_request;
+
+typedef struct {
+    uint64_t ticket;         /* from ac_server_submit                      */
+    int32_t status;          /* AC_OK, or why the request failed           */
+    uint32_t wave_size;      /* requests in its wave                       */
+    double t_submit_us;      /* host clock, microseconds since the server  */
+    double t_launch_us;      /*   was created: submission, wave enqueued,  */
+    double t_done_us;        /*   wave observed complete                   */
+} ac_server_completion;
+
+/* Start a server on the calling device (all handles must live there).  The
+ * handle array is copied; the handles must outlive the server. */
+ac_status ac_server_create(const ac_handle *hs, uint32_t nh, const ac_server_options *opt, ac_server *out);
+
+/* Queue one request (thread-safe, returns at once).  The text and output
+ * buffers must stay valid until the request completes.  n = 0 completes with
+ * count 0.  AC_ERR_INVALID_ARG for a bad automaton or buffer, AC_ERR_BUDGET when
+ * the request alone exceeds the budget. */
+ac_status ac_server_submit(ac_server s, const ac_server_request *req, uint64_t *ticket);
+
+/* Submit reqs[i] when the host clock reaches the call's start + arrival_us[i]
+ * (non-decreasing), spinning between arrivals: a trace player for measuring
+ * latency under a given arrival process.  tickets may be NULL. */
+ac_status ac_server_replay(ac_server s, const ac_server_request *reqs, uint32_t n, const double *arrival_us,
+                           uint64_t *tickets);
+
+/* Move up to max completions (in completion order) to out; *n_out receives
+ * how many.  wait_us > 0: wait up to that long for at least one. */
+ac_status ac_server_poll(ac_server s, ac_server_completion *out, uint32_t max, uint32_t *n_out, uint32_t wait_us);
+
+/* Block until every request submitted so far has completed (their completion
+ * records stay queued for ac_server_poll). */
+ac_status ac_server_drain(ac_server s);
+
+/* Drain, stop the worker and free the server (not the handles). */
+ac_status ac_server_destroy(ac_server s);
 
 /* Read and clear the calling device's kernel error word: AC_OK, AC_ERR_TIMEOUT
  * when a bounded wait inside a kernel ran out, or AC_ERR_INVALID_ARG when a

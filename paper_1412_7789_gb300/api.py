@@ -99,6 +99,12 @@ _SIGS = {
     "ac_batch_destroy": (ctypes.c_int, [_P]),
     "ac_autotune": (ctypes.c_int, [_H, _P, _U64, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_uint32),
                                    ctypes.POINTER(ctypes.c_uint32)]),
+    "ac_server_create": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_void_p)]),
+    "ac_server_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "ac_server_replay": (ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P]),
+    "ac_server_poll": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]),
+    "ac_server_drain": (ctypes.c_int, [_P]),
+    "ac_server_destroy": (ctypes.c_int, [_P]),
     "ac_device_status": (ctypes.c_int, []),
     "ac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -211,7 +217,7 @@ def ac_match_compact(h: int, text, n: int, pos, ids, cap: int, count, stream=Non
 
 
 # Largest text ac_match_compact_static accepts (AC_STATIC_MAX_TEXT in ac.h).
-AC_STATIC_MAX_TEXT = 64 << 20
+AC_STATIC_MAX_TEXT = 16 << 20
 
 
 def ac_match_compact_static(h: int, text, n: int, pos, ids, cap: int, count, stream=None):
@@ -404,3 +410,85 @@ class Automaton:
             out = torch.empty(n, dtype=torch.int32, pin_memory=text.is_pinned())
         ac_match_host(self.handle, int(text.data_ptr()), n, int(out.data_ptr()), stream)
         return out
+
+
+# ---- serving ----------------------------------------------------------------------
+class ac_server_options(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_wave", ctypes.c_uint32),
+                ("waves_in_flight", ctypes.c_uint32), ("fifo", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+# numpy mirrors of ac_server_request (56 bytes) and ac_server_completion (40 bytes)
+SERVER_REQUEST = np.dtype([("automaton", "<u4"), ("reserved", "<u4"), ("d_text", "<u8"), ("n", "<u8"),
+                           ("d_pos", "<u8"), ("d_ids", "<u8"), ("cap", "<u8"), ("d_count", "<u8")])
+SERVER_COMPLETION = np.dtype([("ticket", "<u8"), ("status", "<i4"), ("wave_size", "<u4"),
+                              ("t_submit_us", "<f8"), ("t_launch_us", "<f8"), ("t_done_us", "<f8")])
+assert SERVER_REQUEST.itemsize == 56 and SERVER_COMPLETION.itemsize == 40
+
+
+class Server:
+    """ac_server_*: continuous batching of compacted-match requests."""
+
+    def __init__(self, handles, hbm_budget: int = 0, max_wave: int = 0, waves_in_flight: int = 0,
+                 fifo: bool = False):
+        self.handles = [int(h) for h in handles]
+        arr = _handles(self.handles)
+        opt = ac_server_options(hbm_budget, max_wave, waves_in_flight, 1 if fifo else 0, 0)
+        p = ctypes.c_void_p()
+        _check(lib().ac_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self.handles), ctypes.byref(opt),
+                                      ctypes.byref(p)), "ac_server_create")
+        self.srv = int(p.value)
+
+    @staticmethod
+    def request(automaton: int, text, n: int, pos, ids, cap: int, count) -> np.ndarray:
+        r = np.zeros(1, dtype=SERVER_REQUEST)
+        r["automaton"] = automaton
+        r["d_text"] = int(text.data_ptr()) if n else 0
+        r["n"] = n
+        r["d_pos"] = int(pos.data_ptr()) if cap else 0
+        r["d_ids"] = int(ids.data_ptr()) if cap else 0
+        r["cap"] = cap
+        r["d_count"] = int(count.data_ptr())
+        return r
+
+    def submit(self, req) -> int:
+        """Submit one request (a SERVER_REQUEST record or a length-1 array)."""
+        req = np.ascontiguousarray(np.array(req, dtype=SERVER_REQUEST).reshape(-1)[:1])
+        t = ctypes.c_uint64()
+        _check(lib().ac_server_submit(self.srv, req.ctypes.data, ctypes.byref(t)), "ac_server_submit")
+        return int(t.value)
+
+    def replay(self, reqs: np.ndarray, arrival_us: np.ndarray) -> np.ndarray:
+        """Submit reqs[i] at arrival_us[i] after the call starts; returns the tickets."""
+        reqs = np.ascontiguousarray(reqs, dtype=SERVER_REQUEST)
+        arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+        tickets = np.zeros(len(reqs), dtype=np.uint64)
+        _check(lib().ac_server_replay(self.srv, reqs.ctypes.data, len(reqs), arr.ctypes.data, tickets.ctypes.data),
+               "ac_server_replay")
+        return tickets
+
+    def poll(self, max_n: int = 4096, wait_us: int = 0) -> np.ndarray:
+        out = np.zeros(max_n, dtype=SERVER_COMPLETION)
+        k = ctypes.c_uint32()
+        _check(lib().ac_server_poll(self.srv, out.ctypes.data, max_n, ctypes.byref(k), wait_us), "ac_server_poll")
+        return out[:k.value]
+
+    def drain(self):
+        _check(lib().ac_server_drain(self.srv), "ac_server_drain")
+
+    def close(self):
+        if getattr(self, "srv", None):
+            lib().ac_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -102,11 +102,13 @@ ac_status check_device(ac_automaton *h) {
     return AC_OK;
 }
 
+}  // namespace
+
 // The library's stream-ordered pool for per-call scratch on `dev`.  It keeps
 // the memory it has grown to (release threshold: unlimited), so a call does
 // not map fresh device memory after every synchronisation, as the default
 // pool (threshold 0) would.
-cudaError_t scratch_pool(int dev, cudaMemPool_t *out) {
+cudaError_t pfac::scratch_pool(int dev, cudaMemPool_t *out) {
     static std::mutex mu;
     static cudaMemPool_t pools[64] = {};
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -132,11 +134,14 @@ cudaError_t scratch_pool(int dev, cudaMemPool_t *out) {
     return cudaSuccess;
 }
 
-// A tiled launch with its zeroed scratch (tile counter, look-back words) in
-// stream-ordered memory, so calls on different streams never share it.
+namespace {
+
+using pfac::scratch_pool;
+
+// A tiled launch (dense ids or count) with its zeroed scratch (the tile
+// counter) in stream-ordered memory, so calls on different streams never share it.
 cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode, cudaStream_t st) {
-    const size_t bytes = h->dev.filter ? pfac::filter_scratch_bytes(r.n, mode)
-                                       : pfac::scratch_bytes(h->dev, r.n, mode, h->tuning);
+    const size_t bytes = 16;
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);
     if (e != cudaSuccess) return e;
@@ -150,6 +155,23 @@ cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode,
         e = h->dev.filter ? pfac::launch_filter(h->dev, r, mode, h->tuning, st)
                           : pfac::launch_tiled(h->dev, r, mode, h->tuning, st);
     }
+    const cudaError_t e2 = cudaFreeAsync(scratch, st);
+    return e != cudaSuccess ? e : e2;
+}
+
+// The compacted match of one text with its scratch from the pool.
+cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const pfac::CompactOut &out,
+                        cudaStream_t st) {
+    const uint32_t units = pfac::compact_units(h->dev, text, n);
+    if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
+    const size_t bytes = pfac::compact_scratch_bytes(units);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(h->device, &pool);
+    if (e != cudaSuccess) return e;
+    void *scratch = nullptr;
+    e = cudaMallocFromPoolAsync(&scratch, bytes, pool, st);
+    if (e != cudaSuccess) return e;
+    e = pfac::enqueue_compact(h->dev, h->tuning, text, n, out, scratch, bytes, st);
     const cudaError_t e2 = cudaFreeAsync(scratch, st);
     return e != cudaSuccess ? e : e2;
 }
@@ -232,6 +254,8 @@ const DevTables *handle_tables(ac_handle h, int *device, bool *host_only) {
     *host_only = h->host_only;
     return &h->dev;
 }
+
+const Tuning *handle_tuning(ac_handle h) { return h ? &h->tuning : nullptr; }
 }  // namespace pfac
 
 extern "C" {
@@ -397,14 +421,8 @@ ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint3
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
     if (!d_text) return AC_ERR_INVALID_ARG;
-    pfac::MatchRequest r;
-    r.text = d_text;
-    r.n = n;
-    r.pos = d_pos;
-    r.ids = d_ids;
-    r.cap = cap;
-    r.count = reinterpret_cast<unsigned long long *>(d_count);
-    return cuda_status(run_tiled(h, r, pfac::OUT_COMPACT, st));
+    const pfac::CompactOut out{d_pos, d_ids, cap, reinterpret_cast<unsigned long long *>(d_count)};
+    return cuda_status(run_compact(h, d_text, n, out, st));
 }
 
 ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t *h_out_ids, void *stream) {

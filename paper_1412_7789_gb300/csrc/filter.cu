@@ -1,30 +1,32 @@
 // Failureless Aho-Corasick matching for small alphabets (keyword bytes mapped
 // to 2- or 4-bit codes), sm_103a.
 //
-// pfac_filter -- persistent CTAs (one per SM), every warp on its own tiles of
-// 992 positions (two passes of 496), no block-wide barrier after start-up:
+// pfac_filter_pipe -- persistent CTAs (one per SM), every warp on its own tiles
+// of 992 positions (two halves of 496), no block-wide barrier after start-up:
 //   * a tile plus a halo is fetched with one bulk async copy (cp.async.bulk,
 //     the TMA unit, no multicast) into one of the warp's shared-memory stages,
 //     completing on that stage's mbarrier, `stages` tiles ahead of use;
-//   * per pass, lane l classifies the 16 bytes at 16 l once (byte permutes on
-//     a 3-bit hash, or the byte table), packs their codes into one word (two
+//   * lane l classifies the 16 bytes at 16 l of each half once (byte permutes
+//     on a 3-bit hash, or the byte table), packs their codes into one word (two
 //     for 4-bit codes) and gets the next lane's word with one shuffle, so each
-//     of its 16 start positions has its window of codes in registers; lane 31
+//     of its start positions has its window of codes in registers; lane 31
 //     only supplies the look-ahead word;
 //   * one bit per position from the root filter (resident in shared memory for
 //     the whole kernel): clear means the walk from the root stops within the
 //     first k characters with no keyword, i.e. the result is -1 -- almost every
 //     position of a text whose keywords are longer than k;
-//   * the other positions ("survivors") go to a per-warp queue spread over all
-//     lanes: one load from the window table (depth-k state or result), one from
-//     the stride table (k2 more characters), and rarely the goto table one
-//     character at a time;
-//   * dense ids: a pass whose survivors found no keyword is written by one bulk
-//     async store from a constant buffer of -1; otherwise the survivors'
-//     results are merged into a -1 staging buffer and that is stored.  Counts
-//     take one atomic per warp; the compacted list ranks the survivors that
-//     found a keyword by ballot (the queue is in position order) and places
-//     each pass with a decoupled look-back.
+//   * the other positions ("survivors") are resolved by one load from the
+//     window table (depth-k state or result), one from the stride table (k2
+//     more characters), and rarely the goto table one character at a time.  A
+//     tile with at most one survivor per lane keeps them "in flight" across the
+//     next two tiles, so their dependent loads overlap other work; a tile with
+//     more finishes them at once, eight walks per lane;
+//   * output: dense ids (one bulk async store of a constant -1 buffer when no
+//     survivor found a keyword, else -1 stores and the survivors' ids), a count
+//     (one atomic per warp), or slots (per tile the number of matches and the
+//     first kSlotCap of them) from which compact.cu makes the compacted list.
+// Work units are the tiles of one text, or of all texts of one automaton in a
+// batch (the planned list), claimed from a global counter.
 #include <cuda_runtime.h>
 
 #include <climits>
@@ -43,7 +45,6 @@ constexpr uint32_t kOwnLanes = 31;            // lanes that own start positions 
 constexpr uint32_t kPass = 16 * kOwnLanes;    // 496 positions per pass
 constexpr uint32_t kTile = 2 * kPass;         // 992 positions per warp tile
 constexpr uint32_t kCodeSpan = kTile + 16;    // positions classified per tile
-constexpr uint32_t kResWords = kPass;         // staged results per pass
 // shared-memory header
 constexpr uint32_t kOffJBar = 0;
 constexpr uint32_t kOffStageBar = 64;
@@ -68,14 +69,11 @@ struct FilterParams {
     int hash_shift;
     uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
     int32_t *out;
-    uint32_t *cpos;
-    uint32_t *cids;
-    unsigned long long cap;
     unsigned long long *count;
-    unsigned long long *status;
+    SlotOut sl;
     unsigned int *counter;
     unsigned int *err;
-    uint32_t off_neg1, off_warp, warp_bytes, off_packed, off_inv, off_res, off_queue, off_meta;
+    uint32_t off_neg1, off_warp, warp_bytes, off_packed, off_inv, off_queue, off_meta;
     // batch: the automaton's head and the planned list (text and out are then
     // the bases of all texts and outputs)
     const BatchHead *batch;
@@ -88,9 +86,8 @@ struct WarpSmem {
     uint8_t *st;
     uint32_t *packed;  // codes of the tile's kCodeSpan positions, B bits each
     uint16_t *inv;     // 16 "cannot extend a walk" bits per 16 positions
-    int32_t *res;
     uint16_t *queue;
-    const int32_t *neg1;  // kResWords x -1, shared by the CTA's warps
+    const int32_t *neg1;  // kTile x -1, shared by the CTA's warps
 };
 
 // The text and tile of work unit u (entry `item` of the planned list in a batch).
@@ -183,7 +180,7 @@ template <int B, typename GT, int MODE, int SLOTS, bool DIRECT = false>
 __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const TileText &tt, const WarpSmem &w,
                                                  int64_t gpb, bool interior, bool clean, uint32_t avail,
                                                  uint32_t pbase, int lane, unsigned long long &cnt, uint32_t base,
-                                                 uint32_t coded = 0) {
+                                                 uint32_t coded = 0, uint32_t su = 0) {
     const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k, k2 = p.k2;
     const GT *G = static_cast<const GT *>(p.G);
@@ -295,346 +292,22 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
     for (int t = 0; t < SLOTS; ++t) {
         if ((act >> t) & 1u) {
             found |= v[t] >= 0;
-            if (MODE == OUT_COUNT)
+            if (MODE == OUT_COUNT) {
                 cnt += v[t] >= 0 ? 1ull : 0ull;
-            else if (DIRECT)
+            } else if (MODE == OUT_SLOTS) {
+                if (v[t] >= 0) {
+                    const uint32_t idx = atomicAdd(p.sl.counts + su, 1u);
+                    if (idx < kSlotCap)
+                        p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + idx] =
+                            (static_cast<unsigned long long>(static_cast<uint32_t>(v[t])) << 32) |
+                            static_cast<uint32_t>(gpb + ii[t]);
+                }
+            } else {
                 tt.out[gpb + ii[t]] = v[t];
-            else
-                w.res[ii[t] - pbase] = v[t];
+            }
         }
     }
     return found;
-}
-
-// One pass: classify, filter, finish the survivors, and write (dense) or count
-// the results.  For the compacted output the results stay staged and the
-// queue keeps the survivors (ascending position); returns their number.
-template <int B, typename GT, int MODE>
-__device__ __forceinline__ uint32_t filter_pass(const FilterParams &p, const TileText &tt, const WarpSmem &w,
-                                                int64_t gpb, bool interior, uint32_t h, int lane,
-                                                unsigned long long &cnt, bool &res_busy) {
-    const int64_t n = static_cast<int64_t>(tt.n);
-    const uint32_t k = p.k;
-    const uint32_t pbase = h * kPass;
-    const uint32_t i0 = pbase + 16u * static_cast<uint32_t>(lane);  // this lane's first position
-    const bool owner = lane < static_cast<int>(kOwnLanes);
-
-    // 1. classify this lane's 16 bytes once: packed codes and unknown-byte bits
-    const uint4 raw = *reinterpret_cast<const uint4 *>(w.st + i0);
-    uint32_t c0, c1, c2, c3, u0, u1, u2, u3;
-    classify_word(p, w.cls8, raw.x, c0, u0);
-    classify_word(p, w.cls8, raw.y, c1, u1);
-    classify_word(p, w.cls8, raw.z, c2, u2);
-    classify_word(p, w.cls8, raw.w, c3, u3);
-    uint32_t inv = 0;
-    if (u0 | u1 | u2 | u3)
-        inv = nonzero_bytes(u0) | (nonzero_bytes(u1) << 4) | (nonzero_bytes(u2) << 8) | (nonzero_bytes(u3) << 12);
-    if (!interior) {
-        const int64_t g0 = gpb + i0;
-        if (!(g0 >= 0 && g0 + 16 <= n)) {
-#pragma unroll
-            for (int b = 0; b < 16; ++b)
-                if (g0 + b < 0 || g0 + b >= n) inv |= 1u << b;
-        }
-    }
-    uint32_t plo, phi = 0;  // 16 codes: B = 2 one word, B = 4 two words
-    if (B == 2) {
-        plo = pack4<2>(c0) | (pack4<2>(c1) << 8) | (pack4<2>(c2) << 16) | (pack4<2>(c3) << 24);
-        w.packed[i0 >> 4] = plo;
-    } else {
-        plo = pack4<4>(c0) | (pack4<4>(c1) << 16);
-        phi = pack4<4>(c2) | (pack4<4>(c3) << 16);
-        w.packed[i0 >> 3] = plo;
-        w.packed[(i0 >> 3) + 1] = phi;
-    }
-    w.inv[i0 >> 4] = static_cast<uint16_t>(inv);
-    const bool clean = !__any_sync(kFull, inv != 0);
-    const uint32_t nlo = __shfl_down_sync(kFull, plo, 1);  // next lane's first codes
-    const uint32_t ninv = __shfl_down_sync(kFull, inv, 1);
-
-    // 2. root filter: one bit per start position
-    uint32_t sv = 0, slowm = 0, valid = owner ? 0xFFFFu : 0u;
-    if (owner) {
-        const uint32_t fmask = (1u << (B * k)) - 1u;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            uint32_t win;
-            if (B == 2)
-                win = __funnelshift_r(plo, nlo, 2 * r);
-            else
-                win = r < 8 ? __funnelshift_r(plo, phi, 4 * r) : __funnelshift_r(phi, nlo, 4 * (r - 8));
-            const uint32_t idx = win & fmask;
-            sv |= ((w.F[idx >> 5] >> (idx & 31u)) & 1u) << r;
-        }
-        if (!interior || !clean) {
-            const uint32_t iw = inv | (ninv << 16);
-            const uint32_t kbits = (1u << k) - 1u;
-#pragma unroll
-            for (int r = 0; r < 16; ++r) {
-                const int64_t gp = gpb + i0 + r;
-                if (gp < 0 || gp >= n) {
-                    valid &= ~(1u << r);
-                } else if (gp + static_cast<int64_t>(k) > n || ((iw >> r) & kbits)) {
-                    slowm |= 1u << r;
-                }
-            }
-            sv = (sv | slowm) & valid;
-        }
-    }
-
-    // 3. survivors into the warp's queue (position | slow flag), lane order
-    const uint32_t c = __popc(sv);
-    uint32_t inc = c;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, inc, d);
-        if (lane >= d) inc += y;
-    }
-    const uint32_t total = __shfl_sync(kFull, inc, 31);
-    {
-        uint32_t o = inc - c, m = sv;
-        while (m) {
-            const uint32_t r = __ffs(m) - 1;
-            m &= m - 1;
-            w.queue[o++] = static_cast<uint16_t>((i0 + r) | (((slowm >> r) & 1u) << 15));
-        }
-    }
-    if (MODE == OUT_DENSE && res_busy) {
-        if (lane == 0) bulk_wait_read();  // an earlier bulk store still reads the buffer
-        res_busy = false;
-    }
-    __syncwarp();
-
-    // 4. the survivors, spread over the lanes
-    bool found = false;
-    if (total <= 32) {
-        found = finish_survivors<B, GT, MODE, 1>(p, tt, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
-    } else if (total <= 64) {
-        found = finish_survivors<B, GT, MODE, 2>(p, tt, w, gpb, interior, clean, total, pbase, lane, cnt, 0);
-    } else {
-        for (uint32_t b = 0; b < total; b += 256)
-            found |= finish_survivors<B, GT, MODE, 8>(p, tt, w, gpb, interior, clean, total - b, pbase, lane, cnt, b);
-    }
-    found = __any_sync(kFull, found);
-    __syncwarp();
-
-    // 5. output
-    if (MODE == OUT_DENSE) {
-        if (!found && interior && tt.vec_ok) {
-            // every result of the pass is -1: store the constant buffer
-            if (lane == 0) {
-                bulk_store(tt.out + gpb + pbase, w.neg1, kResWords * 4);
-                bulk_commit();
-            }
-        } else {
-            // results of this lane's 16 positions: survivors' from the buffer, -1 elsewhere
-            if (owner) {
-#pragma unroll
-                for (uint32_t g = 0; g < 4; ++g) {
-                    int4 *slot = reinterpret_cast<int4 *>(w.res) + 4u * lane + g;
-                    const uint32_t m = (sv >> (4 * g)) & 0xFu;
-                    int4 r4 = make_int4(-1, -1, -1, -1);
-                    if (m) {
-                        const int4 sres = *slot;
-                        if (m & 1u) r4.x = sres.x;
-                        if (m & 2u) r4.y = sres.y;
-                        if (m & 4u) r4.z = sres.z;
-                        if (m & 8u) r4.w = sres.w;
-                    }
-                    *slot = r4;
-                }
-            }
-            __syncwarp();
-            if (interior && tt.vec_ok) {
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    bulk_store(tt.out + gpb + pbase, w.res, kResWords * 4);
-                    bulk_commit();
-                }
-                res_busy = true;
-            } else if (owner) {
-#pragma unroll
-                for (uint32_t g = 0; g < 4; ++g) {
-                    const int4 r4 = reinterpret_cast<const int4 *>(w.res)[4u * lane + g];
-                    const int64_t g0 = gpb + i0 + 4u * g;
-                    if (tt.vec_ok && ((valid >> (4 * g)) & 0xFu) == 0xFu) {
-                        *reinterpret_cast<int4 *>(tt.out + g0) = r4;
-                    } else {
-                        const int rr[4] = {r4.x, r4.y, r4.z, r4.w};
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-                            if ((valid >> (4 * g + r)) & 1u) tt.out[g0 + r] = rr[r];
-                    }
-                }
-            }
-        }
-    }
-    __syncwarp();
-    return total;
-}
-
-// ---------------------------------------------------------------------------
-// Compacted output.  The ascending (pos, id) list needs every match's rank, so
-// the unit of ordering is a CTA round: the CTA claims a chunk of nw
-// consecutive one-pass tiles (one per warp); each warp matches its tile,
-// keeping the survivors (the only positions that can match) queued in
-// ascending order with their results staged, and counts its matches; one warp
-// scans the counts and places the chunk with a warp-wide decoupled look-back;
-// then every warp writes its matches.  Chunks are claimed in increasing order
-// by running CTAs, so the look-back always ends, and with one chunk per CTA in
-// flight it stays short.
-// ---------------------------------------------------------------------------
-constexpr uint32_t kOffChunk = 832;   // 2 x uint32: chunk held by each stage
-constexpr uint32_t kOffCounts = 840;  // kMaxWarps x uint32: matches per warp
-constexpr uint32_t kOffBase = 904;    // kMaxWarps x uint32: output offset per warp (n < 2^32)
-constexpr uint32_t kOffAbort = kOffBase + kMaxWarps * 4;
-static_assert(kOffAbort + 4 <= kOffCls, "compaction header overlaps the class map");
-
-// Survivors of the pass whose walk found a keyword.
-__device__ __forceinline__ uint32_t count_found(const WarpSmem &w, uint32_t total, int lane) {
-    uint32_t c = 0;
-    for (uint32_t b = 0; b < total; b += 32) {
-        const uint32_t qi = b + lane;
-        const int v = qi < total ? w.res[w.queue[qi] & 0x7FFFu] : -1;
-        c += __popc(__ballot_sync(kFull, v >= 0));
-    }
-    return c;
-}
-
-// Write them in ascending position from output offset o.
-__device__ __forceinline__ void write_found(const FilterParams &p, const WarpSmem &w, uint32_t total, int64_t gpb,
-                                            unsigned long long o, int lane) {
-    for (uint32_t b = 0; b < total; b += 32) {
-        const uint32_t qi = b + lane;
-        uint32_t i = 0;
-        int v = -1;
-        if (qi < total) {
-            i = w.queue[qi] & 0x7FFFu;
-            v = w.res[i];
-        }
-        const uint32_t m = __ballot_sync(kFull, v >= 0);
-        if (v >= 0) {
-            const unsigned long long at = o + __popc(m & ((1u << lane) - 1u));
-            if (at < p.cap) {
-                p.cpos[at] = static_cast<uint32_t>(gpb + i);
-                p.cids[at] = static_cast<uint32_t>(v);
-            }
-        }
-        o += __popc(m);
-    }
-}
-
-template <int B, typename GT>
-__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_compact(const FilterParams p) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
-    uint32_t *stile = reinterpret_cast<uint32_t *>(smem + kOffStageTile) + warp * kMaxStages;
-    volatile uint32_t *chunk = reinterpret_cast<uint32_t *>(smem + kOffChunk);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(smem + kOffCounts);
-    uint32_t *bases = reinterpret_cast<uint32_t *>(smem + kOffBase);
-    volatile uint32_t *abort_flag = reinterpret_cast<uint32_t *>(smem + kOffAbort);
-    uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
-    WarpSmem w;
-    w.cls8 = smem + kOffCls;
-    w.F = reinterpret_cast<const uint32_t *>(smem + kOffF);
-    w.st = wreg;
-    w.packed = reinterpret_cast<uint32_t *>(wreg + p.off_packed);
-    w.inv = reinterpret_cast<uint16_t *>(wreg + p.off_inv);
-    w.res = reinterpret_cast<int32_t *>(wreg + p.off_res);
-    w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
-    w.neg1 = nullptr;
-    uint32_t *sitem = reinterpret_cast<uint32_t *>(wreg + p.off_meta);
-    const Work wk = load_work(nullptr, nullptr, p.ntiles);  // one text
-    const uint32_t nchunks = (wk.units + nw - 1) / nw;
-
-    if (threadIdx.x == 0) {
-        mbar_init(jbar, 1);
-        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
-        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
-        fence_mbar_init();
-        *abort_flag = 0;
-        chunk[0] = atomicAdd(p.counter, 1u);
-        chunk[1] = atomicAdd(p.counter, 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(jbar, 256u + p.fbytes);
-        bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
-        bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
-    }
-    auto tile_of = [&](uint32_t c) -> uint32_t {
-        const uint64_t t = static_cast<uint64_t>(c) * nw + warp;
-        return (c < nchunks && t < wk.units) ? static_cast<uint32_t>(t) : 0xFFFFFFFFu;
-    };
-    for (uint32_t s = 0; s < 2; ++s)
-        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, tile_of(chunk[s]), lane);
-
-    unsigned long long unused = 0;
-    bool res_busy = false;
-    bool ok = mbar_wait(jbar, 0);
-    for (uint32_t r = 0;; ++r) {
-        const uint32_t s = r & 1u;
-        const uint32_t c = chunk[s];
-        if (c >= nchunks) break;  // the same value for every warp of the CTA
-        ok = ok && mbar_wait(&bars[s], (r >> 1) & 1u);
-        ok = __all_sync(kFull, ok);
-        const uint32_t tile = stile[s];
-        uint32_t m = 0, total = 0;
-        int64_t gpb = 0;
-        TileText tt;
-        if (ok && tile < wk.units) {
-            tt = tile_text(p, wk, tile, sitem[s]);
-            w.st = wreg + s * p.staged;
-            const uint64_t tlo = static_cast<uint64_t>(tt.tile) * p.tile;
-            gpb = static_cast<int64_t>(tlo) - tt.head;
-            const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.staged) <= static_cast<int64_t>(tt.n);
-            if (!interior) {
-                load_text_fringe(tt, p.staged, w.st, tlo, lane);
-                __syncwarp();
-            }
-            total = filter_pass<B, GT, OUT_COMPACT>(p, tt, w, gpb, interior, 0, lane, unused, res_busy);
-            m = count_found(w, total, lane);
-        }
-        if (lane == 0) {
-            counts[warp] = m;
-            if (!ok) *abort_flag = 1;
-        }
-        __syncthreads();
-        if (*abort_flag) {
-            // A copy never completed: latch the error, let this warp's copies in
-            // flight finish (bounded), and leave (every warp of the CTA does).
-            if (lane == 0) {
-                atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
-                mbar_wait(jbar, 0);
-                for (uint32_t j = r; j < r + 2; ++j) mbar_wait(&bars[j & 1u], (j >> 1) & 1u);
-            }
-            return;
-        }
-        if (warp == 0) {
-            const uint32_t mine = lane < nw ? counts[lane] : 0u;
-            uint32_t inc = mine;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(kFull, inc, d);
-                if (lane >= d) inc += y;
-            }
-            const uint32_t ctotal = __shfl_sync(kFull, inc, 31);
-            const unsigned long long pre = lookback_warp(p.status, c, ctotal, p.err, lane);
-            if (lane < nw) bases[lane] = static_cast<uint32_t>(pre + (inc - mine));
-            if (lane == 0) {
-                if (c == nchunks - 1) *p.count = pre + ctotal;
-                chunk[s] = atomicAdd(p.counter, 1u);  // this stage's next chunk
-            }
-        }
-        __syncthreads();
-        if (tile < wk.units && m) write_found(p, w, total, gpb, bases[warp], lane);
-        __syncwarp();
-        if (lane == 0) fence_proxy_async_smem();
-        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, tile_of(chunk[s]), lane);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -752,6 +425,18 @@ __device__ __forceinline__ void flight_output(const FilterParams &p, const Work 
         cnt += mine ? 1ull : 0ull;
         return;
     }
+    if (MODE == OUT_SLOTS) {
+        // at most one survivor per lane: rank by lane (ascending position)
+        const unsigned m = __ballot_sync(kFull, mine);
+        const uint32_t su = p.sl.ubase + f.tile;
+        const uint32_t r = __popc(m & ((1u << lane) - 1u));
+        if (mine && r < kSlotCap)
+            p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + r] =
+                (static_cast<unsigned long long>(static_cast<uint32_t>(f.val)) << 32) |
+                static_cast<uint32_t>(f.gpb + f.pos);
+        if (lane == 0 && m) p.sl.counts[su] = __popc(m);  // the unit's only writer
+        return;
+    }
     const bool found = __any_sync(kFull, mine);
     const TileText tt = tile_text(p, wk, f.tile, f.item);
     const int64_t n = static_cast<int64_t>(tt.n);
@@ -784,7 +469,7 @@ __device__ __forceinline__ void flight_output(const FilterParams &p, const Work 
     if (mine) tt.out[f.gpb + f.pos] = f.val;
 }
 
-template <int B, typename GT, int MODE>
+template <int B, typename GT, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -798,12 +483,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
     w.st = wreg;
     w.packed = reinterpret_cast<uint32_t *>(wreg + p.off_packed);
     w.inv = reinterpret_cast<uint16_t *>(wreg + p.off_inv);
-    w.res = nullptr;
     w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
     w.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
     uint32_t *sitem = reinterpret_cast<uint32_t *>(wreg + p.off_meta);
     const uint32_t nst = p.nstages;
-    const Work wk = load_work(p.batch, p.lists, p.ntiles);
+    // one text: a null list the compiler sees, so the batch lookups fold away
+    const Work wk = BATCH ? load_work(p.batch, p.lists, p.ntiles) : load_work(nullptr, nullptr, p.ntiles);
     const uint32_t k = p.k, k2 = p.k2;
     const bool owner = lane < static_cast<int>(kOwnLanes);
 
@@ -1012,7 +697,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
             }
             for (uint32_t b = 0; b < total; b += 256)
                 finish_survivors<B, GT, MODE, 8, true>(p, tt, w, gpb, interior, clean, total - b, 0, lane, cnt, b,
-                                                       kCodeSpan);
+                                                       kCodeSpan, p.sl.ubase + tile);
             __syncwarp();
             continue;
         }
@@ -1070,18 +755,14 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
 
 inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
 
-template <int B, typename GT, int MODE>
+template <int B, typename GT, int MODE, bool BATCH>
 cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
                        cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    void (*kernel)(const FilterParams);
-    if constexpr (MODE == OUT_COMPACT)
-        kernel = pfac_filter_compact<B, GT>;
-    else
-        kernel = pfac_filter_pipe<B, GT, MODE>;
+    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH>;
     if (!configured[dev]) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
@@ -1096,11 +777,15 @@ cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uin
                          int max_smem, cudaStream_t stream) {
     switch (mode) {
         case OUT_DENSE:
-            return launch_one<B, GT, OUT_DENSE>(p, grid, block, smem, max_smem, stream);
+            return p.batch ? launch_one<B, GT, OUT_DENSE, true>(p, grid, block, smem, max_smem, stream)
+                           : launch_one<B, GT, OUT_DENSE, false>(p, grid, block, smem, max_smem, stream);
         case OUT_COUNT:
-            return launch_one<B, GT, OUT_COUNT>(p, grid, block, smem, max_smem, stream);
+            return launch_one<B, GT, OUT_COUNT, false>(p, grid, block, smem, max_smem, stream);
+        case OUT_SLOTS:
+            return p.batch ? launch_one<B, GT, OUT_SLOTS, true>(p, grid, block, smem, max_smem, stream)
+                           : launch_one<B, GT, OUT_SLOTS, false>(p, grid, block, smem, max_smem, stream);
         default:
-            return launch_one<B, GT, OUT_COMPACT>(p, grid, block, smem, max_smem, stream);
+            return cudaErrorInvalidValue;
     }
 }
 
@@ -1108,64 +793,51 @@ cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uin
 
 uint32_t filter_tile_positions() { return kTile; }
 
-size_t filter_scratch_bytes(uint64_t n, OutMode mode) {
-    if (mode != OUT_COMPACT) return 16;
-    // tile counter and one look-back word per chunk; sized per one-pass tile,
-    // which covers any number of warps per CTA
-    const uint64_t tiles = (n + 15 + kPass - 1) / kPass;
-    return static_cast<size_t>(16 + 8 * (tiles + 2));
-}
-
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                           cudaStream_t stream) {
     if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
         tu.stages > kMaxStages)
         return cudaErrorInvalidValue;
     if (t.B != 2 && t.B != 4) return cudaErrorInvalidValue;
+    if (mode != OUT_DENSE && mode != OUT_COUNT && mode != OUT_SLOTS) return cudaErrorInvalidValue;
+    const bool batch = r.batch != nullptr;
+    if (batch && (mode == OUT_COUNT || !r.lists)) return cudaErrorInvalidValue;
+    if (mode == OUT_SLOTS && (!r.slots.counts || !r.slots.slots)) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, max_smem = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
-    const bool batch = r.batch != nullptr;
-    if (batch && (mode != OUT_DENSE || !r.lists)) return cudaErrorInvalidValue;
     FilterParams p{};
     p.text = r.text;
     p.n = r.n;
-    // warp tiles: two passes, or one for the compacted output (a warp keeps one
-    // pass of results staged until its CTA round is placed)
-    const uint32_t tlen = mode == OUT_COMPACT ? kPass : kTile;
-    p.tile = tlen;
-    uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
-    p.staged = align16(tlen + H) > align16(tlen + 16) ? align16(tlen + H) : align16(tlen + 16);
+    p.tile = kTile;
+    const uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
+    p.staged = align16(kTile + H) > align16(kTile + 16) ? align16(kTile + H) : align16(kTile + 16);
     uint64_t tiles = 0;
     if (!batch) {
         const uint64_t head = reinterpret_cast<uintptr_t>(r.text) & 15u;
-        tiles = (r.n + head + tlen - 1) / tlen;
+        tiles = (r.n + head + kTile - 1) / kTile;
         if (tiles >= 0x7FFFFFFFull) return cudaErrorInvalidValue;
     }
     p.ntiles = static_cast<uint32_t>(tiles);
     p.batch = r.batch;
     p.lists = r.lists;
-    // per-warp layout: stages, packed codes, unknown-byte bits, then for the
-    // compacted output a result buffer and a per-pass queue, else a per-tile queue
-    const bool pipe = mode != OUT_COMPACT;
+    // per-warp layout: stages, packed codes, unknown-byte bits, survivor
+    // queue, stage descriptors; a CTA-wide -1 buffer for the bulk stores
     const uint32_t packed_bytes = align16(kCodeSpan * t.B / 8 + 16);
     const uint32_t inv_bytes = align16(kCodeSpan / 8 + 16);
-    const uint32_t res_bytes = pipe ? 0u : align16(kResWords * 4);
-    const uint32_t queue_bytes = align16((pipe ? kTile : kPass) * 2);
-    const uint32_t neg1_bytes = (pipe ? kTile : kResWords) * 4;
+    const uint32_t queue_bytes = align16(kTile * 2);
+    const uint32_t neg1_bytes = kTile * 4;
     const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
     uint32_t smem = 0;
     bool fits = false;
-    // stages: 3 by default for the pipelined kernel; the compacted output keeps 2
-    const int want = !pipe ? 2 : (tu.stages ? tu.stages : 3);
+    const int want = tu.stages ? tu.stages : 3;
     for (int st = want; st >= 2 && !fits; --st) {
         p.nstages = static_cast<uint32_t>(st);
         p.off_packed = p.nstages * p.staged;
         p.off_inv = p.off_packed + packed_bytes;
-        p.off_res = p.off_inv + inv_bytes;
-        p.off_queue = p.off_res + res_bytes;
+        p.off_queue = p.off_inv + inv_bytes;
         p.off_meta = p.off_queue + queue_bytes;
         p.warp_bytes = p.off_meta + 16u;
         p.off_neg1 = align16(kOffF + t.fbytes);
@@ -1192,14 +864,10 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.hbyte_lo = t.hash_byte[0];
     p.hbyte_hi = t.hash_byte[1];
     p.out = r.out;
-    p.cpos = r.pos;
-    p.cids = r.ids;
-    p.cap = r.cap;
     p.count = r.count;
-    const size_t need = filter_scratch_bytes(r.n, mode);
-    if (!r.scratch || r.scratch_bytes < need) return cudaErrorInvalidValue;
+    p.sl = r.slots;
+    if (!r.scratch || r.scratch_bytes < 16) return cudaErrorInvalidValue;
     p.counter = static_cast<unsigned int *>(r.scratch);
-    if (mode == OUT_COMPACT) p.status = reinterpret_cast<unsigned long long *>(static_cast<uint8_t *>(r.scratch) + 16);
     e = device_error_word(&p.err);
     if (e != cudaSuccess) return e;
     uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(sms);

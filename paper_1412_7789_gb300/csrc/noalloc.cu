@@ -1,7 +1,7 @@
 // ac_match_compact_static: the compacted matching call without any device
-// allocation.  Its scratch (the tile counter and the per-tile look-back words
-// of the ordered compaction) lives in one file-scope device array that every
-// call shares.
+// allocation.  Its scratch (tile counter, per-tile match counts, prefix sums and
+// match slots of the compaction) lives in one file-scope device array that
+// every call shares.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -9,10 +9,6 @@
 #include "ac.h"
 #include "pfac_internal.h"
 
-// Handle internals needed here (defined in api.cpp).
-namespace pfac {
-const DevTables *handle_tables(ac_handle h, int *device, bool *host_only);
-}
 
 namespace {
 
@@ -54,25 +50,15 @@ extern "C" ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text,
     if (n == 0) return cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st) == cudaSuccess ? AC_OK : AC_ERR_CUDA;
     if (!d_text) return AC_ERR_INVALID_ARG;
     pfac::Tuning tu;
-    const size_t bytes = t->filter ? pfac::filter_scratch_bytes(n, pfac::OUT_COMPACT)
-                                   : pfac::scratch_bytes(*t, n, pfac::OUT_COMPACT, tu);
+    const uint32_t units = pfac::compact_units(*t, d_text, n);
+    const size_t bytes = pfac::compact_scratch_bytes(units);
     if (bytes > AC_STATIC_SCRATCH_BYTES) return AC_ERR_BUDGET;
     void *scratch = nullptr;
     if (scratch_address(cur, &scratch) != cudaSuccess) return AC_ERR_CUDA;
-    // the counter and look-back words must start at zero; the array keeps the
-    // previous call's contents
-    if (cudaMemsetAsync(scratch, 0, bytes, st) != cudaSuccess) return AC_ERR_CUDA;
-    pfac::MatchRequest r;
-    r.text = d_text;
-    r.n = n;
-    r.pos = d_pos;
-    r.ids = d_ids;
-    r.cap = cap;
-    r.count = reinterpret_cast<unsigned long long *>(d_count);
-    r.scratch = scratch;
-    r.scratch_bytes = bytes;
-    const cudaError_t e = t->filter ? pfac::launch_filter(*t, r, pfac::OUT_COMPACT, tu, st)
-                                    : pfac::launch_tiled(*t, r, pfac::OUT_COMPACT, tu, st);
+    // enqueue_compact clears the counter and counts it uses: the array keeps
+    // the previous call's contents
+    pfac::CompactOut out{d_pos, d_ids, cap, reinterpret_cast<unsigned long long *>(d_count)};
+    const cudaError_t e = pfac::enqueue_compact(*t, tu, d_text, n, out, scratch, bytes, st);
     if (e == cudaSuccess) return AC_OK;
     if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) return AC_ERR_INVALID_ARG;
     return AC_ERR_CUDA;

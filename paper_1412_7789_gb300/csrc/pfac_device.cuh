@@ -58,6 +58,30 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
         : "memory");
 }
 
+// L2 eviction policies: streamed data (the text) leaves L2 first, the hot
+// rows of the goto table stay.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// bulk_load with an L2 eviction policy.
+__device__ __forceinline__ void bulk_load_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                               uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(policy)
+        : "memory");
+}
+
 // Shared -> global bulk copy (bulk-group completion); dst, src 16-byte
 // aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
@@ -196,9 +220,9 @@ __device__ __forceinline__ uint32_t find_item(const Work &wk, uint32_t u, int la
     return lo + static_cast<uint32_t>(31 - __clz(b));
 }
 
-// One thread: start the bulk copy of tile t.tile into shared buffer st.  Only
-// the 16-byte aligned part inside the text is copied; load_text_fringe fetches
-// the rest.
+// One thread: start the bulk copy of tile t.tile into shared buffer st (text
+// lines marked to leave L2 first: the text is read once).  Only the 16-byte
+// aligned part inside the text is copied; load_text_fringe fetches the rest.
 __device__ __forceinline__ void issue_text_tile(const TileText &t, uint32_t tile_len, uint32_t staged,
                                                 uint64_t *bar, uint8_t *st) {
     const uint64_t tlo = static_cast<uint64_t>(t.tile) * tile_len;
@@ -209,7 +233,7 @@ __device__ __forceinline__ void issue_text_tile(const TileText &t, uint32_t tile
     if (a1 < a2 && lo < hi) {
         const uint32_t bytes = static_cast<uint32_t>(hi - lo);
         mbar_arrive_expect_tx(bar, bytes);
-        bulk_load(st + (lo - tlo), t.gbase + lo, bytes, bar);
+        bulk_load_hint(st + (lo - tlo), t.gbase + lo, bytes, bar, policy_evict_first());
     } else {
         mbar_arrive(bar);
     }
@@ -238,6 +262,23 @@ __device__ __forceinline__ void load_text_fringe(const TileText &t, uint32_t sta
 template <typename GT>
 __device__ __forceinline__ int goto_ld(const GT *G, uint32_t s, uint32_t W, uint32_t c) {
     return static_cast<int>(__ldg(G + static_cast<uint64_t>(s) * W + c));
+}
+
+// goto_ld with an L2 eviction policy (read-only path).
+__device__ __forceinline__ int goto_ld_hint(const int32_t *G, uint32_t s, uint32_t W, uint32_t c, uint64_t pol) {
+    int v;
+    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;"
+                 : "=r"(v)
+                 : "l"(G + static_cast<uint64_t>(s) * W + c), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ int goto_ld_hint(const int16_t *G, uint32_t s, uint32_t W, uint32_t c, uint64_t pol) {
+    short v;
+    asm volatile("ld.global.nc.L2::cache_hint.s16 %0, [%1], %2;"
+                 : "=h"(v)
+                 : "l"(G + static_cast<uint64_t>(s) * W + c), "l"(pol));
+    return static_cast<int>(v);
 }
 
 // Decoupled look-back by a whole warp: the 32 closest predecessors are read at

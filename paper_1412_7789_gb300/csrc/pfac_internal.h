@@ -99,7 +99,28 @@ struct DevTables {
     uint32_t hash_byte[2] = {0, 0};
 };
 
-enum OutMode : int { OUT_DENSE = 0, OUT_COUNT = 1, OUT_COMPACT = 2 };
+// OUT_SLOTS: per work unit, the number of matches and the first kSlotCap of
+// them in any order (SlotOut); the compacted list is then made by the scan
+// and gather steps (compact.cu).  OUT_COMPACT names that whole sequence.
+enum OutMode : int { OUT_DENSE = 0, OUT_COUNT = 1, OUT_COMPACT = 2, OUT_SLOTS = 3 };
+
+// Matches a unit keeps in its slots; a unit with more is matched again by the
+// gather step.
+constexpr uint32_t kSlotCap = 32;
+
+struct SlotOut {
+    uint32_t *counts = nullptr;              // per unit, zeroed before the launch
+    unsigned long long *slots = nullptr;     // per unit kSlotCap entries: (id << 32) | position in its text
+    uint32_t ubase = 0;                      // counts / slots index of the launch's unit 0
+};
+
+// Where one text's compacted list goes (ac_match_compact's arguments).
+struct CompactOut {
+    uint32_t *pos;
+    uint32_t *ids;
+    unsigned long long cap;
+    unsigned long long *count;
+};
 
 // One text of a batch as the matching kernels read it: its bytes at
 // texts + text_off, its dense ids at outs + out_off, its tiles numbered from
@@ -123,13 +144,12 @@ struct MatchRequest {
     int32_t *out = nullptr;                  // dense (batch: base of all outputs)
     const BatchHead *batch = nullptr;        // batch: this automaton's head (device)
     const BatchItemDev *lists = nullptr;     // batch: the planned list (device)
-    unsigned long long *count = nullptr;     // count / compact total
-    uint32_t *pos = nullptr;                 // compact
-    uint32_t *ids = nullptr;                 // compact
-    uint64_t cap = 0;                        // compact
-    void *scratch = nullptr;                 // zeroed: tile counter (+ compact: per-unit status)
+    unsigned long long *count = nullptr;     // count
+    SlotOut slots;                           // OUT_SLOTS
+    void *scratch = nullptr;                 // zeroed: tile counter (16 bytes)
     size_t scratch_bytes = 0;
 };
+
 
 struct Tuning {
     int block = 512;      // threads per CTA (multiple of 32, <= 512)
@@ -138,13 +158,52 @@ struct Tuning {
     int grid = 0;         // 0 = one CTA per SM
 };
 
-// Zeroed device scratch a tiled launch needs: the tile counter, plus the
-// per-unit look-back words of the compacted output.
-size_t scratch_bytes(const DevTables &t, uint64_t n, OutMode mode, const Tuning &tu);
+// The scan and gather steps of the compacted output (compact.cu).
+//   units: launch units (host count), or, when units_dev is set, read there.
+//   partials: kScanCtas words of scratch.
+constexpr uint32_t kScanCtas = 256;
+cudaError_t launch_compact_scan(const uint32_t *counts, uint32_t units, const uint32_t *units_dev,
+                                unsigned long long *prefix, unsigned long long *partials, cudaStream_t stream);
+// Gather: for every unit of one automaton's launch (one text, or the planned
+// list of a batch with per-text outputs outs[item]), its matches in ascending
+// position at its place in its text's list; *count of each text from its last
+// unit.  tile = positions per unit.
+struct GatherRequest {
+    const uint8_t *text = nullptr;           // one text (or batch base)
+    uint64_t n = 0;
+    CompactOut out{};                        // one text
+    const BatchHead *batch = nullptr;        // batch
+    const BatchItemDev *lists = nullptr;
+    const CompactOut *outs = nullptr;        // batch: per caller item
+    uint32_t units = 0;                      // one text: its units
+    uint32_t tile = 0;
+    const uint32_t *counts = nullptr;
+    const unsigned long long *prefix = nullptr;
+    const unsigned long long *slots = nullptr;
+    uint32_t ubase = 0;
+};
+cudaError_t launch_compact_gather(const DevTables &t, const GatherRequest &g, cudaStream_t stream);
 
+// The whole compacted match of one text (slot-mode matching kernel, scan,
+// gather) on `stream`, with `scratch` of compact_scratch_bytes(units) bytes
+// (cleared here), units = compact_units(t, text, n).
+uint32_t compact_units(const DevTables &t, const uint8_t *text, uint64_t n);
+size_t compact_scratch_bytes(uint32_t units);
+cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
+                            const CompactOut &out, void *scratch, size_t scratch_bytes, cudaStream_t stream);
+
+// 8-bit-code kernel (kernels.cu).  Modes: dense, count, slots; 16 bytes of
+// zeroed scratch (tile counter).
 cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode,
                          const Tuning &tu, cudaStream_t stream);
 cudaError_t launch_simple(const DevTables &t, const MatchRequest &r, cudaStream_t stream);
+
+// The library's stream-ordered pool for per-call scratch on device `dev`.
+cudaError_t scratch_pool(int dev, cudaMemPool_t *out);
+
+// Handle internals for entry points outside api.cpp.
+const DevTables *handle_tables(ac_handle h, int *device, bool *host_only);
+const Tuning *handle_tuning(ac_handle h);
 
 // Read and clear the device error word of the current device.
 cudaError_t read_device_error(unsigned int *value);
@@ -162,10 +221,10 @@ constexpr uint32_t kMaxBatchAutomata = 256;
 cudaError_t launch_batch_plan(const ac_batch_item *items, uint32_t nitems, uint32_t nh, const uint8_t *texts,
                               const uint32_t *tile_len, BatchHead *heads, BatchItemDev *lists, cudaStream_t stream);
 
-// Filter-mode kernel (2- and 4-bit codes), in filter.cu.
+// Filter-mode kernel (2- and 4-bit codes), in filter.cu.  Modes: dense,
+// count, slots.  Every launch takes 16 bytes of zeroed scratch (tile counter).
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                           cudaStream_t stream);
-size_t filter_scratch_bytes(uint64_t n, OutMode mode);
 // Positions per work unit (tile) of the dense filter kernel and of the dense
 // 8-bit kernel: the tile lengths a batch is planned with.
 uint32_t filter_tile_positions();

@@ -252,3 +252,40 @@ def batch_layout(texts, kinds, n_sets: int = 8, seed: int = 0):
         else:
             sets[i] = 2 * (pick[i] % (n_sets // 2)) + 1
     return buf, offs, lens, sets
+
+
+def serve_pattern_sets(seed: int = 0, count: int = 16, kmin: int = 1000, kmax: int = 50_000,
+                       lmin: int = 4, lmax: int = 100):
+    """Keyword sets of the served workload: ``count`` sets with log-uniform
+    keyword counts in [kmin, kmax] and lengths uniform in [lmin, lmax]; the
+    first half random ACGT, the second half Zipf(1.1)-random bytes."""
+    g = rng(seed + 2000)
+    ks = np.exp(g.uniform(np.log(kmin), np.log(kmax), size=count)).astype(np.int64)
+    sets = []
+    for j in range(count):
+        sub = rng(seed + 3000 + j)
+        if j < count // 2:
+            sets.append(_random_acgt(sub, int(ks[j]), lmin, lmax))
+        else:
+            sets.append(_random_zipf(sub, int(ks[j]), lmin, lmax))
+    return sets
+
+
+def serve_requests(count: int, pool_bytes: int, seed: int = 0, n_sets: int = 16, lmin: int = 256,
+                   lmax: int = 64 << 20):
+    """Requests of the served workload: (set index, pool offset, length) with
+    lengths log-uniform in [lmin, lmax] and the set uniform; the offset is
+    uniform in a text pool of ``pool_bytes`` of the set's alphabet (sets
+    below n_sets // 2: ACGT, the rest Zipf)."""
+    g = rng(seed + 4000)
+    lens = np.exp(g.uniform(np.log(lmin), np.log(lmax), size=count)).astype(np.int64)
+    lens = np.minimum(lens, pool_bytes)
+    sets = g.integers(0, n_sets, size=count)
+    offs = (g.random(count) * (pool_bytes - lens + 1)).astype(np.int64)
+    return sets, offs, lens
+
+
+def poisson_arrivals(count: int, rate_per_s: float, seed: int = 0) -> np.ndarray:
+    """Arrival times in microseconds of a Poisson process of the given rate."""
+    g = rng(seed + 5000)
+    return np.cumsum(g.exponential(1e6 / rate_per_s, size=count))

@@ -58,8 +58,12 @@ def check_all_modes(h: int, text: np.ndarray, want: np.ndarray, t=None, modes=("
     if "compact" in modes:
         wpos, wid = oracle.compact(want)
         pos, ids, total = compact(h, t, max(1, wpos.size))
-        assert total == wpos.size
-        assert np.array_equal(pos, wpos) and np.array_equal(ids, wid)
+        assert total == wpos.size, (total, wpos.size)
+        if not (np.array_equal(pos, wpos) and np.array_equal(ids, wid)):
+            bad = np.nonzero((pos != wpos) | (ids != wid))[0]
+            raise AssertionError("compact mismatch at %d entries, first %s: got %s / %s want %s / %s" % (
+                bad.size, bad[:6].tolist(), pos[bad[:6]].tolist(), ids[bad[:6]].tolist(),
+                wpos[bad[:6]].tolist(), wid[bad[:6]].tolist()))
 
 
 def regions_check(pats, text: np.ndarray, got_dev, regions):

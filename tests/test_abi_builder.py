@@ -173,3 +173,44 @@ def test_class_hash_choice(lib, alphabet, shift, bits):
     assert info["class_hash_shift"] == shift and info["code_bits"] == bits
     if shift >= 0:
         assert len({(b >> shift) & 7 for b in alphabet}) == len(alphabet)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The Python mirrors of the C structs (ctypes and numpy) have the sizes
+    and field offsets a C compiler gives them from ac.h."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {
+        "ac_batch_item": api.BATCH_ITEM,
+        "ac_server_request": api.SERVER_REQUEST,
+        "ac_server_completion": api.SERVER_COMPLETION,
+        "ac_server_options": api.ac_server_options,
+        "ac_options": api.ac_options,
+        "ac_info_t": api.ac_info_t,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ac.h"', "int main(void) {"]
+    for name, m in mirrors.items():
+        fields = m.names if isinstance(m, np.dtype) else [f[0] for f in m._fields_]
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f in fields:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                   check=True).stdout.splitlines())
+    for name, m in mirrors.items():
+        if isinstance(m, np.dtype):
+            assert int(got[name]) == m.itemsize, name
+            for f in m.names:
+                assert int(got["%s.%s" % (name, f)]) == m.fields[f][1], (name, f)
+        else:
+            assert int(got[name]) == ctypes.sizeof(m), name
+            for f, _ in m._fields_:
+                assert int(got["%s.%s" % (name, f)]) == getattr(m, f).offset, (name, f)
