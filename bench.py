@@ -43,7 +43,10 @@ KNOWN_TRAFFIC = {("sweep", GIB, "pfac_filter_pipe"): 5.408e9}
 def kernel_name(info: dict, out_kind: str, kernel: str) -> str:
     if kernel == "simple":
         return "pfac_simple"
-    name = "pfac_filter_pipe" if info["code_bits"] <= 4 else "pfac_walk8"
+    if info["code_bits"] <= 4:
+        name = "pfac_filter_pipe"
+    else:
+        name = {"thread_jump": "pfac_jump8", "walk_slots": "pfac_walk8"}.get(kernel, "pfac_jump8g")
     # the compacted list: the matcher in slot mode, then scan and gather
     return name + "+compact" if out_kind == "compact" else name
 
@@ -207,6 +210,26 @@ def run_reference(args, rank: int, world: int):
 
 
 # ----------------------------------------------------------------------------
+# replicas: every rank matches its own copy of the workload on its own GPU
+# ----------------------------------------------------------------------------
+def slowest(x: float, dist=None, device=None) -> float:
+    """The largest value of x over the ranks (the job ends with its slowest
+    replica); x itself with one process."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_gbs(bytes_per_rank: float, steps: int, world: int, t_ms: float) -> float:
+    """Whole-job GB/s: every rank's bytes over the slowest rank's time."""
+    return world * bytes_per_rank * steps / (t_ms * 1e-3) / 1e9
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -226,8 +249,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         desc += " [output: %s]" % out_kind
     n = text_np.size
     a = api.Automaton(pats)
-    if args.kernel == "simple":
-        a.set_kernel("simple")
+    a.set_kernel(args.kernel)
     info = a.info()
     text = torch.from_numpy(text_np).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -293,11 +315,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     time.sleep(0.25)
     sampler.stop()
     per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    t_ms = evs[0].elapsed_time(evs[-1])
-    if dist is not None:
-        tt = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
+    t_ms = slowest(evs[0].elapsed_time(evs[-1]), dist, dev)
     clocks = sampler.summary(m0, m1)
 
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
@@ -311,15 +329,15 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         t0 = time.perf_counter()
         for _ in range(reps):
             api.ac_match_host(a.handle, int(ht.data_ptr()), n, int(ho.data_ptr()), stream)
-        e2e_s = (time.perf_counter() - t0) / reps
-        e2e = {"value": world * n / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": n,
+        e2e_s = slowest((time.perf_counter() - t0) / reps, dist, dev)
+        e2e = {"value": replica_gbs(n, 1, world, 1e3 * e2e_s), "unit": "GB/s", "h2d_bytes_per_step": n,
                "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * e2e_s}
         del ht, ho
 
     peak, peak_kind = load_peaks()
     launch_ms = statistics.mean(per)
     achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
-    value = world * n * args.steps / (t_ms * 1e-3) / 1e9
+    value = replica_gbs(n, args.steps, world, t_ms)
     kname = kernel_name(info, out_kind, args.kernel)
     traffic = args.traffic
     if traffic is None:
@@ -344,7 +362,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         extra["simple_kernel_gbs"] = n * 3 / (e0.elapsed_time(e1) * 1e-3) / 1e9
-        a.set_kernel("tiled")
+        a.set_kernel(args.kernel)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -869,7 +887,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sweep", choices=["sweep", "zipf", "single"])
     ap.add_argument("--n", type=int, default=None, help="text bytes (default: the workload's size)")
-    ap.add_argument("--kernel", default="tiled", choices=["tiled", "simple"])
+    ap.add_argument("--kernel", default="tiled", choices=["tiled", "simple", "walk_slots", "thread_jump", "thread_jump_l1"])
     ap.add_argument("--out", default=None, choices=["dense", "count", "compact"],
                     help="output kind (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -50,11 +50,22 @@ typedef enum {
     AC_ERR_NOT_FOUND = 9        /* unknown id (server requests)                   */
 } ac_status;
 
-/* Which matching kernel ac_match uses (ac_set_kernel). */
+/* Which matching kernel a handle uses (ac_set_kernel).  Results never depend
+ * on the choice; only the time does. */
 typedef enum {
-    AC_KERNEL_TILED = 0,  /* default: bulk-copied text tiles, shared-memory jump table */
-    AC_KERNEL_SIMPLE = 1  /* one thread per position walking the goto table in global
-                             memory (the design of the paper's GPU side); dense only */
+    AC_KERNEL_TILED = 0,       /* default, the library's choice per automaton: up to 16
+                                  keyword bytes, bulk-copied text tiles with the
+                                  shared-memory root filter; more, THREAD_JUMP_L1   */
+    AC_KERNEL_SIMPLE = 1,      /* one thread per position walking the goto table in
+                                  global memory (the design of the paper's GPU side);
+                                  ac_match and ac_match_host only                    */
+    AC_KERNEL_WALK_SLOTS = 2,  /* > 16 keyword bytes: warp tiles whose survivors are
+                                  walked in refilled per-lane slots (else as TILED)  */
+    AC_KERNEL_THREAD_JUMP = 3, /* > 16 keyword bytes: one thread per position with the
+                                  shared-memory jump table, 32 warps per SM (else as
+                                  TILED)                                              */
+    AC_KERNEL_THREAD_JUMP_L1 = 4 /* as THREAD_JUMP at 64 warps per SM, the jump table
+                                  and the text read through L1 (else as TILED)       */
 } ac_kernel;
 
 /*
@@ -242,9 +253,9 @@ ac_status ac_match_batch(const ac_handle *hs, uint32_t nh, const uint8_t *d_text
 
 /*
  * A reusable batch plan: the handles, scratch for up to max_items texts, and
- * (after ac_batch_capture) an instantiated CUDA graph of the whole batch.  The
- * launches of the automata run on forked streams inside the plan, so those of
- * different automata may overlap on the GPU.
+ * (after ac_batch_capture) an instantiated CUDA graph of the whole batch (the
+ * planning kernel and the automata's launches in sequence, each filling the
+ * GPU).
  *   ac_batch_create  copies the handle array; allocates the plan's scratch
  *                    with cudaMalloc.  max_items >= 1.
  *   ac_batch_run     enqueues the batch on `stream` (like ac_match_batch,

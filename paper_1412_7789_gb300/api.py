@@ -32,6 +32,11 @@ AC_ERR_NOT_FOUND = 9
 
 AC_KERNEL_TILED = 0
 AC_KERNEL_SIMPLE = 1
+AC_KERNEL_WALK_SLOTS = 2
+AC_KERNEL_THREAD_JUMP = 3
+AC_KERNEL_THREAD_JUMP_L1 = 4
+KERNELS = {"tiled": AC_KERNEL_TILED, "simple": AC_KERNEL_SIMPLE, "walk_slots": AC_KERNEL_WALK_SLOTS,
+           "thread_jump": AC_KERNEL_THREAD_JUMP, "thread_jump_l1": AC_KERNEL_THREAD_JUMP_L1}
 
 
 class AcError(RuntimeError):
@@ -365,7 +370,7 @@ class Automaton:
 
     def set_kernel(self, kernel: str | int):
         if isinstance(kernel, str):
-            kernel = {"tiled": AC_KERNEL_TILED, "simple": AC_KERNEL_SIMPLE}[kernel]
+            kernel = KERNELS[kernel]
         ac_set_kernel(self.handle, kernel)
 
     def match(self, text, out=None, stream=None):

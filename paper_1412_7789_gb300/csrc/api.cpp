@@ -38,9 +38,6 @@ struct ac_batch_plan {
     int device = 0;
     uint32_t max_items = 0;
     void *scratch = nullptr;
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> done;
-    cudaEvent_t fork = nullptr;
     cudaStream_t capture = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -164,14 +161,14 @@ cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const 
                         cudaStream_t st) {
     const uint32_t units = pfac::compact_units(h->dev, text, n);
     if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
-    const size_t bytes = pfac::compact_scratch_bytes(units);
+    const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, true);
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);
     if (e != cudaSuccess) return e;
     void *scratch = nullptr;
     e = cudaMallocFromPoolAsync(&scratch, bytes, pool, st);
     if (e != cudaSuccess) return e;
-    e = pfac::enqueue_compact(h->dev, h->tuning, text, n, out, scratch, bytes, st);
+    e = pfac::enqueue_compact(h->dev, h->tuning, text, n, out, scratch, bytes, true, st);
     const cudaError_t e2 = cudaFreeAsync(scratch, st);
     return e != cudaSuccess ? e : e2;
 }
@@ -198,19 +195,12 @@ ac_status check_handles(const ac_handle *hs, uint32_t nh) {
     return AC_OK;
 }
 
-// Forked streams of a batch plan: automaton a's launch runs on streams[a]
-// after `fork` and `stream` waits for done[a].
-struct Forks {
-    cudaEvent_t fork = nullptr;
-    std::vector<cudaStream_t> streams;
-    std::vector<cudaEvent_t> done;
-};
-
 // Enqueue a batch on `st`: clear the tile counters, plan on the device, then
-// one persistent dense launch per automaton (on forked streams when given).
+// one persistent dense launch per automaton, one after another (each fills
+// the GPU; launches of different automata running side by side measured
+// slower, as their CTAs compete for the same SMs).
 cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const uint8_t *texts,
-                          const ac_batch_item *items, uint32_t nitems, int32_t *out, cudaStream_t st,
-                          const Forks *forks) {
+                          const ac_batch_item *items, uint32_t nitems, int32_t *out, cudaStream_t st) {
     uint8_t *base = static_cast<uint8_t *>(scratch);
     pfac::BatchHead *heads = reinterpret_cast<pfac::BatchHead *>(base);
     uint8_t *counters = base + static_cast<size_t>(nh) * 16u;
@@ -220,14 +210,8 @@ cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const
         tile_len[a] = hs[a]->dev.filter ? pfac::filter_tile_positions() : pfac::tiled_tile_positions();
     cudaError_t e = cudaMemsetAsync(counters, 0, static_cast<size_t>(nh) * 16u, st);
     if (e == cudaSuccess) e = pfac::launch_batch_plan(items, nitems, nh, texts, tile_len.data(), heads, lists, st);
-    if (e == cudaSuccess && forks) e = cudaEventRecord(forks->fork, st);
     for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
         cudaStream_t sa = st;
-        if (forks) {
-            sa = forks->streams[a];
-            e = cudaStreamWaitEvent(sa, forks->fork, 0);
-            if (e != cudaSuccess) break;
-        }
         pfac::MatchRequest r;
         r.text = texts;
         r.out = out;
@@ -238,8 +222,6 @@ cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const
         ac_automaton *h = hs[a];
         e = h->dev.filter ? pfac::launch_filter(h->dev, r, pfac::OUT_DENSE, h->tuning, sa)
                           : pfac::launch_tiled(h->dev, r, pfac::OUT_DENSE, h->tuning, sa);
-        if (e == cudaSuccess && forks) e = cudaEventRecord(forks->done[a], sa);
-        if (e == cudaSuccess && forks) e = cudaStreamWaitEvent(st, forks->done[a], 0);
     }
     return e;
 }
@@ -378,8 +360,25 @@ ac_status ac_export_tables(ac_handle h, int16_t *cls, void *goto_, uint32_t *dep
 }
 
 ac_status ac_set_kernel(ac_handle h, ac_kernel kernel) {
-    if (!h || (kernel != AC_KERNEL_TILED && kernel != AC_KERNEL_SIMPLE)) return AC_ERR_INVALID_ARG;
-    h->kernel = kernel;
+    if (!h) return AC_ERR_INVALID_ARG;
+    switch (kernel) {
+        case AC_KERNEL_TILED:
+        case AC_KERNEL_SIMPLE:
+            h->tuning.variant = 0;
+            break;
+        case AC_KERNEL_WALK_SLOTS:
+            h->tuning.variant = 1;
+            break;
+        case AC_KERNEL_THREAD_JUMP:
+            h->tuning.variant = 2;
+            break;
+        case AC_KERNEL_THREAD_JUMP_L1:
+            h->tuning.variant = 3;
+            break;
+        default:
+            return AC_ERR_INVALID_ARG;
+    }
+    h->kernel = kernel == AC_KERNEL_SIMPLE ? AC_KERNEL_SIMPLE : AC_KERNEL_TILED;
     return AC_OK;
 }
 
@@ -508,7 +507,7 @@ ac_status ac_match_batch(const ac_handle *hs, uint32_t nh, const uint8_t *d_text
     void *scratch = nullptr;
     e = cudaMallocFromPoolAsync(&scratch, batch_scratch_bytes(nh, nitems), pool, st);
     if (e != cudaSuccess) return cuda_status(e);
-    e = enqueue_batch(hs, nh, scratch, d_texts, d_items, nitems, d_out, st, nullptr);
+    e = enqueue_batch(hs, nh, scratch, d_texts, d_items, nitems, d_out, st);
     const cudaError_t e2 = cudaFreeAsync(scratch, st);
     return cuda_status(e != cudaSuccess ? e : e2);
 }
@@ -517,11 +516,6 @@ ac_status ac_batch_destroy(ac_batch b) {
     if (!b) return AC_OK;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    for (cudaStream_t x : b->streams)
-        if (x) cudaStreamDestroy(x);
-    for (cudaEvent_t x : b->done)
-        if (x) cudaEventDestroy(x);
-    if (b->fork) cudaEventDestroy(b->fork);
     if (b->capture) cudaStreamDestroy(b->capture);
     if (b->scratch) cudaFree(b->scratch);
     delete b;
@@ -539,16 +533,9 @@ ac_status ac_batch_create(const ac_handle *hs, uint32_t nh, uint32_t max_items, 
     b->hs.assign(hs, hs + nh);
     b->device = hs[0]->device;
     b->max_items = max_items;
-    b->streams.assign(nh, nullptr);
-    b->done.assign(nh, nullptr);
     cudaError_t e = cudaMalloc(&b->scratch, batch_scratch_bytes(nh, max_items));
     if (e != cudaSuccess) b->scratch = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
-    for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
-        e = cudaStreamCreateWithFlags(&b->streams[a], cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done[a], cudaEventDisableTiming);
-    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         ac_batch_destroy(b);
@@ -561,12 +548,8 @@ ac_status ac_batch_create(const ac_handle *hs, uint32_t nh, uint32_t max_items, 
 namespace {
 ac_status batch_enqueue(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
                         int32_t *d_out, cudaStream_t st) {
-    Forks f;
-    f.fork = b->fork;
-    f.streams = b->streams;
-    f.done = b->done;
     return cuda_status(enqueue_batch(b->hs.data(), static_cast<uint32_t>(b->hs.size()), b->scratch, d_texts, d_items,
-                                     nitems, d_out, st, &f));
+                                     nitems, d_out, st));
 }
 
 ac_status check_plan_args(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,

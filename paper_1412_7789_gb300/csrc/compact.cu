@@ -179,10 +179,13 @@ __global__ void __launch_bounds__(kGatherThreads) compact_gather(const GatherPar
                 out.ids[o + rank] = static_cast<uint32_t>(e >> 32);
             }
         } else {
+            // more matches than slots: the unit's dense ids if kept, else match it again
+            const int32_t *dn = p.g.dense ? p.g.dense + su * kDenseStride : nullptr;
             for (uint32_t i0 = 0; i0 < T; i0 += 32) {
                 const int64_t gp = gpb + static_cast<int64_t>(i0) + lane;
                 int id = -1;
-                if (gp >= 0 && static_cast<uint64_t>(gp) < n) id = walk_from_root<GT>(p, text, n, gp);
+                if (gp >= 0 && static_cast<uint64_t>(gp) < n)
+                    id = dn ? __ldg(dn + i0 + lane) : walk_from_root<GT>(p, text, n, gp);
                 const unsigned m = __ballot_sync(0xffffffffu, id >= 0);
                 const uint32_t r = __popc(m & ((1u << lane) - 1u));
                 if (id >= 0 && o + r < out.cap) {
@@ -250,22 +253,31 @@ uint32_t compact_units(const DevTables &t, const uint8_t *text, uint64_t n) {
 }
 
 // Layout: tile counter (16) | counts (4 per unit) | prefix (8 per unit) |
-// slots (8 * kSlotCap per unit) | partial sums (8 * kScanCtas).
-size_t compact_scratch_bytes(uint32_t units) {
+// slots (8 * kSlotCap per unit) | partial sums (8 * kScanCtas) | dense
+// fallback (4 per position of every unit, optional; 16-byte aligned for the
+// kernels' 16-byte stores).
+size_t compact_dense_offset(uint32_t units) {
     const size_t U = units;
-    return 16 + round16(4 * U) + 8 * U + 8 * kSlotCap * U + 8 * static_cast<size_t>(kScanCtas);
+    return round16(16 + round16(4 * U) + 8 * U + 8 * kSlotCap * U + 8 * static_cast<size_t>(kScanCtas));
+}
+
+size_t compact_scratch_bytes(const DevTables &t, uint32_t units, bool dense) {
+    (void)t;
+    return compact_dense_offset(units) + (dense ? 4 * static_cast<size_t>(kDenseStride) * units : 0);
 }
 
 cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
-                            const CompactOut &out, void *scratch, size_t scratch_bytes, cudaStream_t stream) {
+                            const CompactOut &out, void *scratch, size_t scratch_bytes, bool dense,
+                            cudaStream_t stream) {
     const uint32_t U = compact_units(t, text, n);
     if (U == 0xFFFFFFFFu || n > 0xFFFFFFFFull) return cudaErrorInvalidValue;
-    if (!scratch || scratch_bytes < compact_scratch_bytes(U)) return cudaErrorInvalidValue;
+    if (!scratch || scratch_bytes < compact_scratch_bytes(t, U, dense)) return cudaErrorInvalidValue;
     uint8_t *b = static_cast<uint8_t *>(scratch);
     uint32_t *counts = reinterpret_cast<uint32_t *>(b + 16);
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(b + 16 + round16(4 * size_t(U)));
     unsigned long long *slots = prefix + U;
     unsigned long long *partials = slots + static_cast<size_t>(kSlotCap) * U;
+    int32_t *dn = dense ? reinterpret_cast<int32_t *>(b + compact_dense_offset(U)) : nullptr;
     cudaError_t e = cudaMemsetAsync(b, 0, 16 + 4 * size_t(U), stream);
     if (e != cudaSuccess) return e;
     MatchRequest r;
@@ -274,6 +286,7 @@ cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t 
     r.slots.counts = counts;
     r.slots.slots = slots;
     r.slots.ubase = 0;
+    r.slots.dense = dn;
     r.scratch = b;
     r.scratch_bytes = 16;
     e = t.filter ? launch_filter(t, r, OUT_SLOTS, tu, stream) : launch_tiled(t, r, OUT_SLOTS, tu, stream);
@@ -289,6 +302,7 @@ cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t 
     g.counts = counts;
     g.prefix = prefix;
     g.slots = slots;
+    g.dense = dn;
     return launch_compact_gather(t, g, stream);
 }
 

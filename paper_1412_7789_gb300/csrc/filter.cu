@@ -295,6 +295,7 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
             if (MODE == OUT_COUNT) {
                 cnt += v[t] >= 0 ? 1ull : 0ull;
             } else if (MODE == OUT_SLOTS) {
+                if (p.sl.dense) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + ii[t]] = v[t];
                 if (v[t] >= 0) {
                     const uint32_t idx = atomicAdd(p.sl.counts + su, 1u);
                     if (idx < kSlotCap)
@@ -692,6 +693,18 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                             }
                         }
                     }
+                }
+                __syncwarp();
+            }
+            if (MODE == OUT_SLOTS && p.sl.dense) {
+                // the tile may overflow its slots: keep its dense ids, -1 first
+                if (owner) {
+                    int32_t *dn = p.sl.dense + static_cast<uint64_t>(p.sl.ubase + tile) * kDenseStride;
+#pragma unroll
+                    for (uint32_t h = 0; h < 2; ++h)
+#pragma unroll
+                        for (uint32_t g = 0; g < 4; ++g)
+                            *reinterpret_cast<int4 *>(dn + h * kPass + 16u * lane + 4u * g) = make_int4(-1, -1, -1, -1);
                 }
                 __syncwarp();
             }

@@ -161,7 +161,9 @@ __device__ __forceinline__ void emit(const WarpParams &p, int32_t *op, uint32_t 
         __stcs(op, r);
     } else if (MODE == OUT_COUNT) {
         cnt += r >= 0 ? 1ull : 0ull;
-    } else if (r >= 0) {
+    } else {
+        if (op) __stcs(op, r);  // the tile's dense fallback
+        if (r < 0) return;
         const uint32_t idx = atomicAdd(p.sl.counts + su, 1u);
         if (idx < kSlotCap)
             p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + idx] =
@@ -301,7 +303,8 @@ constexpr int kLongMark = INT_MIN;
 // Move the lane's short walks into free long slots (as many as fit).
 template <int SS, int SL>
 __device__ __forceinline__ void spill(const WarpParams &p, const TileText &tt, int64_t gpb, uint32_t pbase,
-                                      uint32_t su, ShortWalks<SS> &s, LongWalks<SL> &l, int32_t *pb) {
+                                      uint32_t su, ShortWalks<SS> &s, LongWalks<SL> &l, int32_t *pb,
+                                      bool slots_mode, int32_t *tile_dense) {
 #pragma unroll
     for (int t = 0; t < SS; ++t) {
         if ((s.act >> t) & 1u) {
@@ -315,7 +318,8 @@ __device__ __forceinline__ void spill(const WarpParams &p, const TileText &tt, i
                     l.tp[u] = tt.text + gq;
                     l.rem[u] = left > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(left);
                     l.nb[u] = s.nb[t];
-                    l.op[u] = tt.out + gpos;
+                    // dense: the id's place; slots: the tile's dense fallback, if kept
+                    l.op[u] = !slots_mode ? tt.out + gpos : (tile_dense ? tile_dense + pbase + s.i[t] : nullptr);
                     l.pos[u] = static_cast<uint32_t>(gpos);
                     l.su[u] = su;
                     l.act |= 1u << u;
@@ -414,7 +418,10 @@ __device__ __forceinline__ void walk_pass(const WarpParams &p, const TileText &t
     for (;;) {
         head = refill<SS>(p, st, pbase, queue, head, qn, sw, lane);
         if (head >= qn) {
-            if (extra >= kExtraRounds) spill<SS, SL>(p, tt, gpb, pbase, su, sw, lw, pb);
+            if (extra >= kExtraRounds)
+                spill<SS, SL>(p, tt, gpb, pbase, su, sw, lw, pb, MODE == OUT_SLOTS,
+                              MODE == OUT_SLOTS && p.sl.dense ? p.sl.dense + static_cast<uint64_t>(su) * kDenseStride
+                                                              : nullptr);
             if (!__any_sync(kFull, sw.act != 0)) break;
             ++extra;
         }
@@ -457,6 +464,15 @@ __device__ __forceinline__ void walk_pass(const WarpParams &p, const TileText &t
         if (MODE == OUT_COUNT) {
             cnt += __popc(hit);
         } else {
+            if (p.sl.dense) {  // the tile may overflow its slots: keep its dense ids
+                int32_t *dn = p.sl.dense + static_cast<uint64_t>(su) * kDenseStride;
+#pragma unroll
+                for (int g = 0; g < 4; ++g)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (((valid >> (4 * g + r)) & 1u) && rr[4 * g + r] != kLongMark)
+                            __stcs(dn + ibase + 128u * g + r, rr[4 * g + r]);
+            }
             const uint32_t mine = __popc(hit);
             uint32_t sc = mine;
 #pragma unroll
@@ -682,6 +698,9 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
         tu.stages > kMaxStages)
         return cudaErrorInvalidValue;
     if (t.B != 8) return cudaErrorInvalidValue;  // small alphabets use the filter kernel
+    // default (variant 0): the full-occupancy one-thread-per-position kernel,
+    // the fastest of the three on the 256-value Zipf workloads
+    if (tu.variant != 1) return launch_jump8(t, r, mode, tu.variant != 2, stream);
     if (mode != OUT_DENSE && mode != OUT_COUNT && mode != OUT_SLOTS) return cudaErrorInvalidValue;
     const bool batch = r.batch != nullptr;
     if (batch && (mode == OUT_COUNT || !r.lists)) return cudaErrorInvalidValue;

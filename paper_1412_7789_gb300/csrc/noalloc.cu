@@ -51,14 +51,15 @@ extern "C" ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text,
     if (!d_text) return AC_ERR_INVALID_ARG;
     pfac::Tuning tu;
     const uint32_t units = pfac::compact_units(*t, d_text, n);
-    const size_t bytes = pfac::compact_scratch_bytes(units);
+    // no dense fallback here: a tile with many matches is matched again by the gather step
+    const size_t bytes = pfac::compact_scratch_bytes(*t, units, false);
     if (bytes > AC_STATIC_SCRATCH_BYTES) return AC_ERR_BUDGET;
     void *scratch = nullptr;
     if (scratch_address(cur, &scratch) != cudaSuccess) return AC_ERR_CUDA;
     // enqueue_compact clears the counter and counts it uses: the array keeps
     // the previous call's contents
     pfac::CompactOut out{d_pos, d_ids, cap, reinterpret_cast<unsigned long long *>(d_count)};
-    const cudaError_t e = pfac::enqueue_compact(*t, tu, d_text, n, out, scratch, bytes, st);
+    const cudaError_t e = pfac::enqueue_compact(*t, tu, d_text, n, out, scratch, bytes, false, st);
     if (e == cudaSuccess) return AC_OK;
     if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) return AC_ERR_INVALID_ARG;
     return AC_ERR_CUDA;

@@ -62,13 +62,13 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t b
 // rows of the goto table stay.
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 
 __device__ __forceinline__ uint64_t policy_evict_last() {
     uint64_t p;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
 
@@ -267,7 +267,7 @@ __device__ __forceinline__ int goto_ld(const GT *G, uint32_t s, uint32_t W, uint
 // goto_ld with an L2 eviction policy (read-only path).
 __device__ __forceinline__ int goto_ld_hint(const int32_t *G, uint32_t s, uint32_t W, uint32_t c, uint64_t pol) {
     int v;
-    asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;"
+    asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;"
                  : "=r"(v)
                  : "l"(G + static_cast<uint64_t>(s) * W + c), "l"(pol));
     return v;
@@ -275,7 +275,7 @@ __device__ __forceinline__ int goto_ld_hint(const int32_t *G, uint32_t s, uint32
 
 __device__ __forceinline__ int goto_ld_hint(const int16_t *G, uint32_t s, uint32_t W, uint32_t c, uint64_t pol) {
     short v;
-    asm volatile("ld.global.nc.L2::cache_hint.s16 %0, [%1], %2;"
+    asm("ld.global.nc.L2::cache_hint.s16 %0, [%1], %2;"
                  : "=h"(v)
                  : "l"(G + static_cast<uint64_t>(s) * W + c), "l"(pol));
     return static_cast<int>(v);

@@ -104,14 +104,22 @@ struct DevTables {
 // and gather steps (compact.cu).  OUT_COMPACT names that whole sequence.
 enum OutMode : int { OUT_DENSE = 0, OUT_COUNT = 1, OUT_COMPACT = 2, OUT_SLOTS = 3 };
 
-// Matches a unit keeps in its slots; a unit with more is matched again by the
-// gather step.
+// Matches a unit keeps in its slots; for a unit with more, the gather step
+// reads the unit's dense ids (SlotOut::dense), or matches it again.
 constexpr uint32_t kSlotCap = 32;
+
+// Entries per unit in SlotOut::dense (every kernel's tile is at most this long).
+constexpr uint32_t kDenseStride = 1024;
 
 struct SlotOut {
     uint32_t *counts = nullptr;              // per unit, zeroed before the launch
     unsigned long long *slots = nullptr;     // per unit kSlotCap entries: (id << 32) | position in its text
     uint32_t ubase = 0;                      // counts / slots index of the launch's unit 0
+    // Optional, per unit kDenseStride entries: the dense ids of the unit's
+    // positions (entry i: tile position i), written where a unit may hold more
+    // than kSlotCap matches, so the gather step reads them instead of matching
+    // the unit again.
+    int32_t *dense = nullptr;
 };
 
 // Where one text's compacted list goes (ac_match_compact's arguments).
@@ -156,6 +164,10 @@ struct Tuning {
     int stages = 0;       // text stages in flight per warp (2..4, 0 = the kernel's default;
                           // fewer when shared memory is short)
     int grid = 0;         // 0 = one CTA per SM
+    int variant = 0;      // 8-bit codes: 1 = warp tiles with walk slots (kernels.cu),
+                          // 2 = one thread per position with the jump table in shared
+                          // memory (jump8.cu), 0 or 3 = the same at full occupancy with
+                          // the table read through L1 (the default)
 };
 
 // The scan and gather steps of the compacted output (compact.cu).
@@ -180,17 +192,21 @@ struct GatherRequest {
     const uint32_t *counts = nullptr;
     const unsigned long long *prefix = nullptr;
     const unsigned long long *slots = nullptr;
+    const int32_t *dense = nullptr;          // optional, as SlotOut::dense
     uint32_t ubase = 0;
 };
 cudaError_t launch_compact_gather(const DevTables &t, const GatherRequest &g, cudaStream_t stream);
 
 // The whole compacted match of one text (slot-mode matching kernel, scan,
-// gather) on `stream`, with `scratch` of compact_scratch_bytes(units) bytes
-// (cleared here), units = compact_units(t, text, n).
+// gather) on `stream`, with `scratch` of compact_scratch_bytes(t, units, dense)
+// bytes (cleared here), units = compact_units(t, text, n).  dense: keep the
+// per-unit dense fallback (4 bytes per position) so that units with many
+// matches are copied, not matched again.
 uint32_t compact_units(const DevTables &t, const uint8_t *text, uint64_t n);
-size_t compact_scratch_bytes(uint32_t units);
+size_t compact_scratch_bytes(const DevTables &t, uint32_t units, bool dense);
 cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
-                            const CompactOut &out, void *scratch, size_t scratch_bytes, cudaStream_t stream);
+                            const CompactOut &out, void *scratch, size_t scratch_bytes, bool dense,
+                            cudaStream_t stream);
 
 // 8-bit-code kernel (kernels.cu).  Modes: dense, count, slots; 16 bytes of
 // zeroed scratch (tile counter).
@@ -229,5 +245,11 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
 // 8-bit kernel: the tile lengths a batch is planned with.
 uint32_t filter_tile_positions();
 uint32_t tiled_tile_positions();
+
+// One-thread-per-position 8-bit kernel (jump8.cu); same modes, scratch and
+// tile length as launch_tiled, which hands over to it for Tuning::variant 2.
+// global: the full-occupancy form that reads the jump table and the text
+// through L1 (Tuning::variant 3).
+cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode, bool global, cudaStream_t stream);
 
 }  // namespace pfac

@@ -103,9 +103,9 @@ uint64_t units_of(const pfac::DevTables &t, const uint8_t *text, uint64_t n) {
 }
 
 // Device bytes a request holds while admitted: its text, its output and the
-// scratch of its tiles (counts, prefix, slots).
+// scratch of its tiles (counts, prefix, slots, dense fallback).
 uint64_t request_bytes(const pfac::DevTables &t, const ac_server_request &r) {
-    const uint64_t per_unit = 4 + 8 + 8ull * pfac::kSlotCap;
+    const uint64_t per_unit = 4 + 8 + 8ull * pfac::kSlotCap + 4ull * pfac::kDenseStride;
     return r.n + 8ull * r.cap + units_of(t, r.d_text, r.n) * per_unit + 64;
 }
 
@@ -133,12 +133,13 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         const Request &q = w.reqs[0];
         if (q.r.n == 0) return cudaMemsetAsync(q.r.d_count, 0, sizeof(uint64_t), w.stream);
         const pfac::DevTables &t = *s->tabs[q.r.automaton];
-        const size_t bytes = pfac::compact_scratch_bytes(pfac::compact_units(t, q.r.d_text, q.r.n));
+        const size_t bytes = pfac::compact_scratch_bytes(t, pfac::compact_units(t, q.r.d_text, q.r.n), true);
         void *scratch = nullptr;
         e = cudaMallocFromPoolAsync(&scratch, bytes, pool, w.stream);
         if (e != cudaSuccess) return e;
         const pfac::CompactOut out{q.r.d_pos, q.r.d_ids, q.r.cap, reinterpret_cast<unsigned long long *>(q.r.d_count)};
-        e = pfac::enqueue_compact(t, s->tune[q.r.automaton], q.r.d_text, q.r.n, out, scratch, bytes, w.stream);
+        e = pfac::enqueue_compact(t, s->tune[q.r.automaton], q.r.d_text, q.r.n, out, scratch, bytes, true,
+                                  w.stream);
         const cudaError_t e2 = cudaFreeAsync(scratch, w.stream);
         return e != cudaSuccess ? e : e2;
     }
@@ -207,9 +208,11 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     std::memcpy(hp + round256(hb), list.data(), lb);
     std::memcpy(hp + round256(hb) + round256(lb), outs.data(), ob);
 
-    // device: plan | tile counters | counts | prefix | slots | partial sums
+    // device: plan | tile counters | counts | prefix | slots | partial sums |
+    // dense fallback
     const size_t cb = round256(16ull * nh), nb = round256(4 * U), pb = 8 * U, sb = 8ull * pfac::kSlotCap * U;
-    const size_t dev_bytes = plan_bytes + cb + nb + pb + sb + 8ull * pfac::kScanCtas;
+    const size_t db = round256(plan_bytes + cb + nb + pb + sb + 8ull * pfac::kScanCtas);  // dense fallback: aligned
+    const size_t dev_bytes = db + 4ull * pfac::kDenseStride * U;
     void *dev = nullptr;
     e = cudaMallocFromPoolAsync(&dev, dev_bytes, pool, w.stream);
     if (e != cudaSuccess) return e;
@@ -222,6 +225,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(counters + cb + nb);
     unsigned long long *slots = prefix + U;
     unsigned long long *partials = slots + static_cast<size_t>(pfac::kSlotCap) * U;
+    int32_t *dense = reinterpret_cast<int32_t *>(dp + db);
 
     e = cudaMemcpyAsync(dp, hp, plan_bytes, cudaMemcpyHostToDevice, w.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, cb + 4 * U, w.stream);
@@ -235,6 +239,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         m.slots.counts = counts;
         m.slots.slots = slots;
         m.slots.ubase = ubase[a];
+        m.slots.dense = dense;
         m.scratch = counters + 16u * a;
         m.scratch_bytes = 16;
         const pfac::DevTables &t = *s->tabs[a];
@@ -255,6 +260,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         g.prefix = prefix;
         g.slots = slots;
         g.ubase = ubase[a];
+        g.dense = dense;
         e = pfac::launch_compact_gather(*s->tabs[a], g, w.stream);
     }
     const cudaError_t e2 = cudaFreeAsync(dev, w.stream);

@@ -85,14 +85,18 @@ def random_case(g, alphabet: bytes, n: int, kw: int, lmax: int):
     return text, pats
 
 
+@pytest.mark.parametrize("kernel", ["tiled", "walk_slots", "thread_jump", "thread_jump_l1"])
 @pytest.mark.parametrize("alpha", sorted(ALPHABETS))
-def test_random_sizes(alpha):
+def test_random_sizes(alpha, kernel):
+    """Every kernel variant (the 8-bit ones differ; small alphabets always use
+    the filter kernel) on every code width and many sizes."""
     g = np.random.Generator(np.random.PCG64(sorted(ALPHABETS).index(alpha) + 1000))
     for n in SIZES:
         text, pats = random_case(g, ALPHABETS[alpha], max(n, 40), 50, 24)
         text = text[:n]
         want = oracle.pfac_ids(pats, text)
         with compile_(pats) as a:
+            a.set_kernel(kernel)
             _gpu.check_all_modes(a.handle, text, want)
 
 
@@ -113,7 +117,8 @@ def test_build_options_keep_results(opts):
             _gpu.check_all_modes(a.handle, t, want)
 
 
-def test_longest_walk_and_edges():
+@pytest.mark.parametrize("kernel", ["tiled", "walk_slots", "thread_jump", "thread_jump_l1"])
+def test_longest_walk_and_edges(kernel):
     """A run of one byte with keywords of that byte x1..x100: every start walks
     to the end of its run (the longest walks the method has)."""
     pats = [b"\x00" * L for L in range(1, 101)] + [b"\xff\x00", b"\x00\xff", b"\xff" * 3]
@@ -123,6 +128,7 @@ def test_longest_walk_and_edges():
         text[-1] = 0xFF
         want = oracle.pfac_ids(pats, text)
         with compile_(pats) as a:
+            a.set_kernel(kernel)
             _gpu.check_all_modes(a.handle, text, want)
 
 
@@ -135,7 +141,8 @@ def test_keyword_longer_than_text_and_duplicates():
         _gpu.check_all_modes(a.handle, text, want)
 
 
-def test_many_keywords_over_15_bits():
+@pytest.mark.parametrize("kernel", ["tiled", "walk_slots", "thread_jump", "thread_jump_l1"])
+def test_many_keywords_over_15_bits(kernel):
     """More than 32767 keywords: 32-bit goto entries, and jump-table results
     that do not fit 15 bits go to the plain walk."""
     g = np.random.Generator(np.random.PCG64(5))
@@ -146,6 +153,7 @@ def test_many_keywords_over_15_bits():
     want = oracle.pfac_ids(pats, text)
     with compile_(pats) as a:
         assert a.info()["index_width"] == 32
+        a.set_kernel(kernel)
         _gpu.check_all_modes(a.handle, text, want)
 
 
@@ -176,12 +184,14 @@ def test_sweep_keywords_full(n):
         _gpu.check_all_modes(a.handle, text, want)
 
 
-def test_zipf_compact_and_overflow():
+@pytest.mark.parametrize("kernel", ["tiled", "walk_slots", "thread_jump", "thread_jump_l1"])
+def test_zipf_compact_and_overflow(kernel):
     text, pats = workloads.zipf_byte(1 << 22, n_keywords=20_000)
     want = oracle.pfac_ids(pats, text)
     wpos, wid = oracle.compact(want)
     assert wpos.size > 100
     with compile_(pats) as a:
+        a.set_kernel(kernel)
         _gpu.check_all_modes(a.handle, text, want)
         t = _gpu.to_dev(text)
         cap = wpos.size // 3
@@ -221,3 +231,30 @@ def test_match_host_chunk_seams():
         want = oracle.pfac_ids(pats, small)
         got = a.match_host(torch.from_numpy(small.copy()))
         assert np.array_equal(got.numpy(), want)
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "walk_slots", "thread_jump", "thread_jump_l1"])
+@pytest.mark.parametrize("alpha", ["acgt", "bytes"])
+def test_dense_matches_compact(alpha, kernel):
+    """Nearly every position matches (one-byte keywords), so every tile holds
+    more matches than its slots and the compacted list comes from the tiles'
+    dense ids; the static-scratch call matches such tiles again instead."""
+    import torch
+
+    g = np.random.Generator(np.random.PCG64(77))
+    text, pats = random_case(g, ALPHABETS[alpha], 300_001, 60, 12)
+    pats += [bytes([b]) for b in ALPHABETS[alpha][::3]]
+    want = oracle.pfac_ids(pats, text)
+    assert (want >= 0).mean() > 0.2
+    with compile_(pats) as a:
+        a.set_kernel(kernel)
+        _gpu.check_all_modes(a.handle, text, want, modes=("compact", "count"))
+        wpos, wid = oracle.compact(want)
+        t = _gpu.to_dev(text)
+        pos = torch.full((wpos.size,), -7, dtype=torch.int32, device="cuda")
+        ids = torch.full((wpos.size,), -7, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        api.ac_match_compact_static(a.handle, t, text.size, pos, ids, wpos.size, cnt)
+        assert int(cnt.item()) == wpos.size
+        assert np.array_equal(pos.cpu().numpy().astype(np.uint32), wpos)
+        assert np.array_equal(ids.cpu().numpy().astype(np.uint32), wid)
