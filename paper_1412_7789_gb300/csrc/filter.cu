@@ -290,22 +290,30 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
     bool found = false;
 #pragma unroll
     for (int t = 0; t < SLOTS; ++t) {
-        if ((act >> t) & 1u) {
-            found |= v[t] >= 0;
-            if (MODE == OUT_COUNT) {
-                cnt += v[t] >= 0 ? 1ull : 0ull;
-            } else if (MODE == OUT_SLOTS) {
-                if (p.sl.dense) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + ii[t]] = v[t];
-                if (v[t] >= 0) {
-                    const uint32_t idx = atomicAdd(p.sl.counts + su, 1u);
-                    if (idx < kSlotCap)
-                        p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + idx] =
-                            (static_cast<unsigned long long>(static_cast<uint32_t>(v[t])) << 32) |
-                            static_cast<uint32_t>(gpb + ii[t]);
-                }
-            } else {
-                tt.out[gpb + ii[t]] = v[t];
+        const bool mine = (act >> t) & 1u;
+        if (MODE == OUT_SLOTS) {
+            // one atomic per warp and slot index, ranks by ballot (all lanes)
+            const bool hit = mine && v[t] >= 0;
+            const unsigned m = __ballot_sync(kFull, hit);
+            if (mine && p.sl.dense) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + ii[t]] = v[t];
+            if (m) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(p.sl.counts + su, static_cast<uint32_t>(__popc(m)));
+                base = __shfl_sync(kFull, base, 0) + __popc(m & ((1u << lane) - 1u));
+                if (hit && base < kSlotCap)
+                    p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + base] =
+                        (static_cast<unsigned long long>(static_cast<uint32_t>(v[t])) << 32) |
+                        static_cast<uint32_t>(gpb + ii[t]);
             }
+            found |= hit;
+            continue;
+        }
+        if (mine) {
+            found |= v[t] >= 0;
+            if (MODE == OUT_COUNT)
+                cnt += v[t] >= 0 ? 1ull : 0ull;
+            else
+                tt.out[gpb + ii[t]] = v[t];
         }
     }
     return found;
