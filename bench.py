@@ -248,7 +248,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         out_kind = args.out
         desc += " [output: %s]" % out_kind
     n = text_np.size
-    a = api.Automaton(pats)
+    a = api.Automaton(pats, chains=not args.no_chains)
     a.set_kernel(args.kernel)
     info = a.info()
     text = torch.from_numpy(text_np).to(dev)
@@ -891,6 +891,7 @@ def main():
     ap.add_argument("--out", default=None, choices=["dense", "count", "compact"],
                     help="output kind (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-chains", action="store_true", help="compile without chain records")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--compare-simple", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -83,6 +83,8 @@ typedef enum {
  *                  table (larger alphabets); 0 = 128 KiB.
  *   stride_bytes   device budget of the second-level stride table (0 = 16 MiB;
  *                  set 1 to disable it).
+ *   no_chains      1 = no chain records: every walk step reads a goto row (the
+ *                  records are a speed-up only; results do not change).
  *   dev_alloc / dev_free / alloc_ctx
  *                  optional device allocator for the handle's tables (e.g. a
  *                  PyTorch caching allocator); NULL = cudaMalloc / cudaFree.
@@ -96,6 +98,8 @@ typedef struct {
     void *(*dev_alloc)(size_t bytes, void *ctx);
     void (*dev_free)(void *ptr, void *ctx);
     void *alloc_ctx;
+    int32_t no_chains;      /* 1 = build no chain records (ac_export_chains)    */
+    int32_t reserved;       /* 0                                                 */
 } ac_options;
 
 /* Shape of a compiled automaton (ac_info). */
@@ -148,6 +152,21 @@ ac_status ac_info(ac_handle h, ac_info_t *info);
  *         depth d at ids [sum of counts below d, ...))
  */
 ac_status ac_export_tables(ac_handle h, int16_t *cls, void *goto_, uint32_t *depth);
+
+/*
+ * Chain records (for inspection and tests; host memory).  From state s_chain
+ * on (BFS order), every state has a record of four uint32: a run length L
+ * (0xFFFFFFFF: the state has two or more children and the walk takes its goto
+ * row; 0: a leaf, the walk stops), the offset of the run's L bytes in `bytes`,
+ * the state the run ends at, and the state's result (int32, -1 = none).  A
+ * walk at such a state whose next L text bytes equal the run's bytes goes on
+ * from the end state; otherwise it stops with the state's result (no state
+ * inside a run has its own keyword).  Call with NULL arrays to get the counts
+ * (*n_records, *n_bytes), then again with room for them.  s_chain = n_states
+ * means no records.
+ */
+ac_status ac_export_chains(ac_handle h, uint32_t *s_chain, uint32_t *records, uint8_t *bytes, uint64_t *n_records,
+                           uint64_t *n_bytes);
 
 /*
  * Dense matching.  d_out_ids[i] = id of the longest keyword starting at

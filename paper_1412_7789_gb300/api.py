@@ -55,6 +55,8 @@ class ac_options(ctypes.Structure):
         ("dev_alloc", ctypes.c_void_p),
         ("dev_free", ctypes.c_void_p),
         ("alloc_ctx", ctypes.c_void_p),
+        ("no_chains", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -96,6 +98,8 @@ _SIGS = {
     "ac_match_host": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_compact_static": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_set_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ac_export_chains": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint32), _P, _P, ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint64)]),
     "ac_match_batch": (ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P]),
     "ac_batch_create": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ctypes.c_void_p)]),
     "ac_batch_run": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P, _P]),
@@ -171,7 +175,7 @@ def _dev_ptr(t, dtype_bytes: int | None = None) -> int:
 
 # ---- C-named functions ----------------------------------------------------------
 def ac_compile(patterns, index_width: int = 0, class_compress: bool = True, host_only: bool = False,
-               jump_bytes: int = 0, stride_bytes: int = 0) -> int:
+               jump_bytes: int = 0, stride_bytes: int = 0, chains: bool = True) -> int:
     """Compile keywords (sequence of bytes-like) -> raw handle (int)."""
     pats = [bytes(p) for p in patterns]
     k = len(pats)
@@ -185,6 +189,7 @@ def ac_compile(patterns, index_width: int = 0, class_compress: bool = True, host
     opt.host_only = 1 if host_only else 0
     opt.jump_bytes = jump_bytes
     opt.stride_bytes = stride_bytes
+    opt.no_chains = 0 if chains else 1
     h = _H()
     _check(lib().ac_compile(arr, lens, k, ctypes.byref(opt), ctypes.byref(h)), "ac_compile")
     return int(h.value)
@@ -209,6 +214,20 @@ def ac_export_tables(h: int):
     depth = np.zeros(info["max_len"] + 1, dtype=np.uint32)
     _check(lib().ac_export_tables(h, cls.ctypes.data, G.ctypes.data, depth.ctypes.data), "ac_export_tables")
     return cls, G, depth
+
+
+def ac_export_chains(h: int):
+    """(s_chain, records uint32[n, 4], bytes uint8[m]) -- see ac.h."""
+    sc = ctypes.c_uint32()
+    nr = ctypes.c_uint64()
+    nb = ctypes.c_uint64()
+    _check(lib().ac_export_chains(h, ctypes.byref(sc), None, None, ctypes.byref(nr), ctypes.byref(nb)),
+           "ac_export_chains")
+    rec = np.zeros((nr.value, 4), dtype=np.uint32)
+    byt = np.zeros(nb.value, dtype=np.uint8)
+    _check(lib().ac_export_chains(h, ctypes.byref(sc), rec.ctypes.data, byt.ctypes.data, ctypes.byref(nr),
+                                  ctypes.byref(nb)), "ac_export_chains")
+    return int(sc.value), rec, byt
 
 
 def ac_match(h: int, text, n: int, out, stream=None):

@@ -267,6 +267,7 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     bo.class_compress = o.class_compress ? 1 : 0;
     if (o.jump_bytes) bo.jump_bytes = o.jump_bytes;
     if (o.stride_bytes) bo.stride_bytes = o.stride_bytes;
+    bo.chains = o.no_chains == 0;
     int st = pfac::build_tables(patterns, lens, k, bo, &h->host);
     if (st != AC_OK) {
         delete h;
@@ -311,6 +312,12 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
             s = upload(h, t.JK.data(), t.JK.size() * sizeof(int32_t), reinterpret_cast<const void **>(&d.JK));
         if (s == AC_OK && !t.J2.empty())
             s = upload(h, t.J2.data(), t.J2.size() * sizeof(int32_t), reinterpret_cast<const void **>(&d.J2));
+        if (s == AC_OK && !t.skip.empty()) {
+            s = upload(h, t.skip.data(), t.skip.size() * sizeof(uint32_t), reinterpret_cast<const void **>(&d.skip));
+            if (s == AC_OK)
+                s = upload(h, t.chain.data(), t.chain.size(), reinterpret_cast<const void **>(&d.chain));
+            d.s_chain = t.s_chain;
+        }
         if (s != AC_OK) {
             ac_destroy(h);
             return s;
@@ -343,7 +350,8 @@ ac_status ac_info(ac_handle h, ac_info_t *info) {
     info->min_len = t.minlen;
     info->max_len = t.maxlen;
     info->table_bytes = t.G.size() + t.J.size() * sizeof(int16_t) + t.J2.size() * sizeof(int32_t) +
-                        t.F.size() * sizeof(uint32_t) + t.JK.size() * sizeof(int32_t) + 768;
+                        t.F.size() * sizeof(uint32_t) + t.JK.size() * sizeof(int32_t) +
+                        t.skip.size() * sizeof(uint32_t) + t.chain.size() + 768;
     info->depth_base_jump = t.base_k;
     info->count_jump = t.count_k;
     info->class_hash_shift = t.hash_shift;
@@ -356,6 +364,18 @@ ac_status ac_export_tables(ac_handle h, int16_t *cls, void *goto_, uint32_t *dep
     if (cls) std::memcpy(cls, t.cls.data(), 256 * sizeof(int16_t));
     if (goto_) std::memcpy(goto_, t.G.data(), t.G.size());
     if (depth) std::memcpy(depth, t.depth_count.data(), t.depth_count.size() * sizeof(uint32_t));
+    return AC_OK;
+}
+
+ac_status ac_export_chains(ac_handle h, uint32_t *s_chain, uint32_t *records, uint8_t *bytes, uint64_t *n_records,
+                           uint64_t *n_bytes) {
+    if (!h || !s_chain || !n_records || !n_bytes) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    *s_chain = t.skip.empty() ? t.S : t.s_chain;
+    *n_records = t.skip.size() / 4;
+    *n_bytes = t.chain.size();
+    if (records && !t.skip.empty()) std::memcpy(records, t.skip.data(), t.skip.size() * sizeof(uint32_t));
+    if (bytes && !t.chain.empty()) std::memcpy(bytes, t.chain.data(), t.chain.size());
     return AC_OK;
 }
 

@@ -196,14 +196,21 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             else
                 reinterpret_cast<int32_t *>(h.G.data())[idx] = v;
         };
+        std::vector<uint32_t> kids(S, 0), child1(S, 0);  // children; the first child
+        std::vector<uint8_t> code1(S, 0);                 // its code
         for (uint32_t s = 0; s < S; ++s) {
             int32_t dead = encode_dead(pathbest[s]);
             uint64_t row = static_cast<uint64_t>(s) * h.W;
             for (uint32_t c = 0; c < h.W; ++c) put(row + c, dead);
             uint32_t old = order[s];
+            kids[s] = first[old + 1] - first[old];
             for (uint32_t a = first[old]; a < first[old + 1]; ++a) {
                 const Edge &e = edges[adj[a]];
                 put(row + e.code, static_cast<int32_t>(newid[e.child]));
+                if (a == first[old]) {
+                    child1[s] = newid[e.child];
+                    code1[s] = static_cast<uint8_t>(e.code);
+                }
             }
         }
         std::vector<Edge>().swap(edges);
@@ -305,6 +312,66 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                     walk_codes(h.base_k + r, w, h.k2, &e);
                     h.J2[static_cast<size_t>(r) * cols + w] = e;
                 }
+        }
+
+        // 8. chain records for the states from the first mostly-unbranched
+        //    depth on: a state with one child starts a run of forced
+        //    transitions through non-terminal one-child states; a walk that
+        //    matches the run's bytes jumps to its end, one that does not stops
+        //    with the state's result (no state inside the run has its own
+        //    keyword, so every stop inside it has that result).
+        uint32_t dc = h.maxlen + 1;
+        {
+            std::vector<uint64_t> single(h.maxlen + 1, 0);
+            for (uint32_t s2 = 0; s2 < S; ++s2)
+                if (kids[s2] <= 1) single[depth[s2]]++;
+            for (uint32_t d = 2; d <= h.maxlen; ++d)
+                if (h.depth_count[d] && single[d] * 100 >= 85ull * h.depth_count[d]) {
+                    dc = d;
+                    break;
+                }
+        }
+        h.s_chain = (opt.chains && dc <= h.maxlen) ? depth_base[dc] : S;
+        if (h.s_chain < S) {
+            std::vector<uint8_t> byte_of(256, 0);
+            for (int b = 0; b < 256; ++b)
+                if (h.cls[b] >= 0) byte_of[static_cast<uint32_t>(h.cls[b])] = static_cast<uint8_t>(b);
+            const uint32_t R = S - h.s_chain;
+            h.skip.assign(static_cast<size_t>(R) * 4, 0);
+            std::vector<uint8_t> done(R, 0);
+            for (uint32_t s2 = h.s_chain; s2 < S; ++s2) {
+                uint32_t *rec = &h.skip[static_cast<size_t>(s2 - h.s_chain) * 4];
+                rec[3] = static_cast<uint32_t>(pathbest[s2]);
+                if (kids[s2] >= 2) {
+                    rec[0] = kSkipBranch;
+                    continue;
+                }
+                if (kids[s2] == 0) {  // a leaf: the walk stops here
+                    rec[0] = 0;
+                    rec[2] = s2;
+                    continue;
+                }
+                if (done[s2 - h.s_chain]) continue;  // inside a run built from an earlier state
+                const uint32_t off = static_cast<uint32_t>(h.chain.size());
+                uint32_t v = s2, L = 0;
+                do {
+                    h.chain.push_back(byte_of[code1[v]]);
+                    v = child1[v];
+                    ++L;
+                } while (kids[v] == 1 && kw_at[order[v]] < 0);
+                // the run's states: s2 and the one-child states inside it
+                uint32_t u = s2;
+                for (uint32_t j = 0; j < L; ++j) {
+                    uint32_t *r = &h.skip[static_cast<size_t>(u - h.s_chain) * 4];
+                    r[0] = L - j;
+                    r[1] = off + j;
+                    r[2] = v;
+                    r[3] = static_cast<uint32_t>(pathbest[u]);
+                    done[u - h.s_chain] = 1;
+                    u = child1[u];
+                }
+            }
+            h.chain.resize(std::max<size_t>(16, (h.chain.size() + 15) & ~static_cast<size_t>(15)), 0);
         }
     } catch (const std::bad_alloc &) {
         return AC_ERR_OOM;

@@ -108,6 +108,9 @@ struct GatherParams {
     const uint8_t *cls8;
     uint32_t W, C, maxlen;
     unsigned int *err;
+    const uint4 *skip;      // chain records from state s_chain on
+    const uint8_t *chain;
+    uint32_t s_chain;       // 0xFFFFFFFF: none
 };
 
 // The id of the longest keyword starting at text position gp: the plain walk
@@ -116,8 +119,18 @@ template <typename GT>
 __device__ int walk_from_root(const GatherParams &p, const uint8_t *text, uint64_t n, uint64_t gp) {
     const GT *G = static_cast<const GT *>(p.G);
     uint32_t s = 0;
-    for (uint32_t step = 0; step <= p.maxlen + 1; ++step) {
-        const uint64_t q = gp + step;
+    uint64_t q = gp;
+    for (uint32_t step = 0; step <= p.maxlen + 1; ++step, ++q) {
+        if (s >= p.s_chain) {  // a run of forced transitions, a leaf, or a branch
+            const uint4 rc = __ldg(p.skip + (s - p.s_chain));
+            if (rc.x != kSkipBranch) {
+                const bool ok = rc.x > 0 && q + rc.x <= n && run_equal(text + q, p.chain + rc.y, rc.x);
+                if (!ok) return static_cast<int>(rc.w);
+                s = rc.z;
+                q += rc.x - 1;  // the loop adds one
+                continue;
+            }
+        }
         uint32_t c = p.C;
         if (q < n) {
             const uint32_t b = __ldg(text + q);
@@ -226,6 +239,9 @@ cudaError_t launch_compact_gather(const DevTables &t, const GatherRequest &g, cu
     p.W = t.W;
     p.C = t.C;
     p.maxlen = t.maxlen;
+    p.skip = t.skip;
+    p.chain = t.chain;
+    p.s_chain = t.skip ? t.s_chain : 0xFFFFFFFFu;
     e = device_error_word(&p.err);
     if (e != cudaSuccess) return e;
     const uint32_t per_cta = kGatherThreads / 32;

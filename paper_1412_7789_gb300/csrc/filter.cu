@@ -78,6 +78,10 @@ struct FilterParams {
     // the bases of all texts and outputs)
     const BatchHead *batch;
     const BatchItemDev *lists;
+    // chain records from state s_chain on (0xFFFFFFFF: none)
+    const uint4 *skip;
+    const uint8_t *chain;
+    uint32_t s_chain;
 };
 
 struct WarpSmem {
@@ -173,6 +177,28 @@ __device__ __forceinline__ bool fetch_code(const TileText &tt, const WarpSmem &w
     return true;
 }
 
+// A walk at state s (>= p.s_chain) whose next byte is at tile index q: its
+// chain record decides.  Returns 1 when the state's whole run of forced
+// transitions matched the text (s and q moved to the run's end), 0 when the
+// walk stops in the run or at a leaf (result in r), 2 when s branches (take its
+// goto row).  The text bytes come from global memory (L1/L2: the tile was
+// just read).
+__device__ __forceinline__ int chain_step(const FilterParams &p, const TileText &tt, int64_t gpb, uint32_t &s,
+                                          uint32_t &q, int &r) {
+    const uint4 rc = __ldg(p.skip + (s - p.s_chain));
+    if (rc.x == kSkipBranch) return 2;
+    const int64_t gq = gpb + static_cast<int64_t>(q);
+    const bool ok = rc.x > 0 && gq + static_cast<int64_t>(rc.x) <= static_cast<int64_t>(tt.n) &&
+                    run_equal(tt.text + gq, p.chain + rc.y, rc.x);
+    if (ok) {
+        s = rc.z;
+        q += rc.x;
+        return 1;
+    }
+    r = static_cast<int>(rc.w);
+    return 0;
+}
+
 // Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)):
 // their results go to the pass's staging buffer (or are counted).  Returns
 // true when this lane found a keyword.
@@ -264,19 +290,33 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
             break;
         }
         int e[SLOTS];
+        uint32_t loaded = 0;
 #pragma unroll
         for (int t = 0; t < SLOTS; ++t) {
             if ((walking >> t) & 1u) {
+                if (st[t] >= p.s_chain) {  // a run of forced transitions, a leaf, or a branch
+                    int rr = -1;
+                    // text bytes from global memory: the tile's stage already
+                    // takes the next bulk copy while its survivors are walked
+                    const int k3 = chain_step(p, tt, gpb, st[t], q[t], rr);
+                    if (k3 == 1) continue;
+                    if (k3 == 0) {
+                        v[t] = rr;
+                        walking &= ~(1u << t);
+                        continue;
+                    }
+                }
                 uint32_t c = 0;
                 const bool okc = fetch_code<B>(tt, w, gpb, DIRECT ? coded : pbase + kPass + 16u, q[t], c);
                 // an unknown byte or the text end reads the row's end column,
                 // which always holds the result of stopping there
                 e[t] = goto_ld(G, st[t], p.W, okc ? c : p.C);
+                loaded |= 1u << t;
             }
         }
 #pragma unroll
         for (int t = 0; t < SLOTS; ++t) {
-            if ((walking >> t) & 1u) {
+            if ((loaded >> t) & 1u) {
                 if (e[t] < 0) {
                     v[t] = decode_dead(e[t]);
                     walking &= ~(1u << t);
@@ -367,6 +407,12 @@ __device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t 
                                            int64_t gpb, uint32_t s, uint32_t q) {
     const GT *G = static_cast<const GT *>(p.G);
     for (uint32_t step = 0; step <= p.maxlen + 1; ++step) {
+        if (s >= p.s_chain) {  // a run of forced transitions, a leaf, or a branch
+            int rr = -1;
+            const int k3 = chain_step(p, tt, gpb, s, q, rr);
+            if (k3 == 1) continue;
+            if (k3 == 0) return rr;
+        }
         const int64_t gp = gpb + static_cast<int64_t>(q);
         uint32_t c = p.C;  // the end column: stop here
         if (gp < static_cast<int64_t>(tt.n)) {
@@ -879,6 +925,9 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.base_k = t.base_k;
     p.maxlen = t.maxlen;
     p.fbytes = t.fbytes;
+    p.skip = t.skip;
+    p.chain = t.chain;
+    p.s_chain = t.skip ? t.s_chain : 0xFFFFFFFFu;
     p.hash_shift = t.hash_shift;
     p.hcode_lo = t.hash_code[0];
     p.hcode_hi = t.hash_code[1];

@@ -58,6 +58,7 @@ struct JumpParams {
     uint32_t off_stage;     // first stage buffer
     uint32_t global;        // 1: pfac_jump8g (tables and text through L1)
     uint32_t sms;
+    uint32_t rows;          // pfac_jump8g: rows of a tile per claim (1 or 16)
 };
 
 __device__ __forceinline__ TileText tile_text(const JumpParams &p, const Work &wk, uint32_t u, uint32_t item) {
@@ -217,13 +218,13 @@ __device__ __forceinline__ void walk2g(const JumpParams &p, const TileText &tt, 
                 int v;
                 if (sizeof(GT) == 4) {
                     asm("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;"
-                                 : "=r"(v)
-                                 : "l"(G + (state[t] * p.W + c)), "l"(keep));
+                        : "=r"(v)
+                        : "l"(G + (state[t] * p.W + c)), "l"(keep));
                 } else {
                     short h;
                     asm("ld.global.nc.L2::cache_hint.s16 %0, [%1], %2;"
-                                 : "=h"(h)
-                                 : "l"(G + (state[t] * p.W + c)), "l"(keep));
+                        : "=h"(h)
+                        : "l"(G + (state[t] * p.W + c)), "l"(keep));
                     v = h;
                 }
                 e[t] = v;
@@ -370,11 +371,14 @@ __global__ void __launch_bounds__(kBlock, 1) pfac_jump8(const JumpParams p) {
 }
 
 // The same walks at full occupancy: no shared-memory tables or stages (the
-// jump table and the text are read through L1), 256-thread CTAs, 8 per SM.
+// jump table and the text are read through L1), 256-thread CTAs, 8 per SM
+// (32 registers a thread).  Chain records are not used here: their logic
+// costs the registers of that occupancy, which measured the larger win.
 constexpr int kBlockG = 256;
+constexpr int kCtasG = 8;
 
 template <bool INV, typename GT, int MODE, bool BATCH>
-__global__ void __launch_bounds__(kBlockG, 8) pfac_jump8g(const JumpParams p) {
+__global__ void __launch_bounds__(kBlockG, kCtasG) pfac_jump8g(const JumpParams p) {
     __shared__ uint8_t cls8[256];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const Work wk = BATCH ? load_work(p.batch, p.lists, p.ntiles) : load_work(nullptr, nullptr, p.ntiles);
@@ -385,20 +389,27 @@ __global__ void __launch_bounds__(kBlockG, 8) pfac_jump8g(const JumpParams p) {
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
     const uint64_t keep = policy_evict_last();
     unsigned long long cnt = 0;
+    // A claim is p.rows rows (16 = a whole tile; 1 for small texts, so that
+    // their few tiles spread over many warps).
+    const uint32_t rows = p.rows;
+    const uint64_t claims = static_cast<uint64_t>(wk.units) * (kHalf / 32) / rows;
     for (uint32_t it = 0;; ++it) {
-        uint32_t tile = 0xFFFFFFFFu;
+        uint32_t claim = 0xFFFFFFFFu;
         if (lane == 0) {
             const uint64_t c = it == 0 ? gw : GW + atomicAdd(p.counter, 1u);
-            if (c < wk.units) tile = static_cast<uint32_t>(c);
+            if (c < claims) claim = static_cast<uint32_t>(c);
         }
-        tile = __shfl_sync(kFull, tile, 0);
-        if (tile >= wk.units) break;
+        claim = __shfl_sync(kFull, claim, 0);
+        if (claim == 0xFFFFFFFFu) break;
+        const uint32_t row0 = claim * rows;
+        const uint32_t tile = row0 / (kHalf / 32);
         const uint32_t item = wk.list ? find_item(wk, tile, lane) : 0u;
         const TileText tt = tile_text(p, wk, tile, item);
         const int64_t gpb = static_cast<int64_t>(tt.tile) * kTile - tt.head;
         const int64_t n = static_cast<int64_t>(tt.n);
         const uint32_t su = p.sl.ubase + tile;
-        for (uint32_t j = 0; j < kHalf / 32; ++j) {
+        const uint32_t j0 = row0 % (kHalf / 32);
+        for (uint32_t j = j0; j < j0 + rows; ++j) {
             uint32_t i[2];
             bool in[2];
             i[0] = 32u * j + static_cast<uint32_t>(lane);
@@ -421,7 +432,7 @@ __global__ void __launch_bounds__(kBlockG, 8) pfac_jump8g(const JumpParams p) {
 template <bool INV, typename GT, int MODE, bool BATCH>
 cudaError_t launch_one(const JumpParams &p, uint32_t grid, uint32_t smem, int max_smem, cudaStream_t stream) {
     if (p.global) {
-        const uint32_t g = p.sms * (2048u / kBlockG);
+        const uint32_t g = p.sms * static_cast<uint32_t>(kCtasG);
         pfac_jump8g<INV, GT, MODE, BATCH><<<grid < g ? grid : g, kBlockG, 0, stream>>>(p);
         return cudaGetLastError();
     }
@@ -504,13 +515,17 @@ cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode
     if (static_cast<int>(smem) > max_smem) return cudaErrorInvalidConfiguration;
     if (global && static_cast<uint64_t>(t.S) * t.W >= (1ull << 31)) global = false;  // 32-bit row offsets
     p.global = global ? 1u : 0u;
+    // small texts: one row per claim, so their few tiles spread over many warps
+    p.rows = (!batch && static_cast<uint64_t>(p.ntiles) * (kHalf / 32) <= 4ull * sms * kCtasG * (kBlockG / 32u)) ? 1u
+                                                                                                  : kHalf / 32;
     p.sms = static_cast<uint32_t>(sms);
     uint32_t grid = static_cast<uint32_t>(sms);
-    if (global) grid = static_cast<uint32_t>(sms) * (2048u / kBlockG);
+    if (global) grid = static_cast<uint32_t>(sms) * static_cast<uint32_t>(kCtasG);
     if (!batch) {
         const uint32_t per = global ? kBlockG / 32u : static_cast<uint32_t>(kWarps);
-        const uint32_t need = (p.ntiles + per - 1) / per;
-        if (grid > need) grid = need;
+        const uint64_t work = global ? static_cast<uint64_t>(p.ntiles) * (kHalf / 32) / p.rows : p.ntiles;
+        const uint64_t need = (work + per - 1) / per;
+        if (grid > need) grid = static_cast<uint32_t>(need);
     }
     if (grid == 0) return cudaSuccess;
     const bool inv = t.C < 256;

@@ -259,6 +259,41 @@ __device__ __forceinline__ void load_text_fringe(const TileText &t, uint32_t sta
     if (idx < hi) st[idx - tlo] = t.gbase[idx];
 }
 
+// True when the L bytes at t equal the L bytes at c (any alignment): aligned
+// 4-byte words, 16 bytes per round with all of a round's loads issued before
+// any compare.  Only words holding at least one of the L bytes are read.
+__device__ __forceinline__ bool run_equal(const uint8_t *t, const uint8_t *c, uint32_t L) {
+    const uint32_t ta = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(t) & 3u);
+    const uint32_t ca = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(c) & 3u);
+    const uint32_t *tw = reinterpret_cast<const uint32_t *>(t - ta);
+    const uint32_t *cw = reinterpret_cast<const uint32_t *>(c - ca);
+    const uint32_t tn = (ta + L + 3u) >> 2, cn = (ca + L + 3u) >> 2;  // words holding the bytes
+    uint32_t tp = __ldg(tw), cp = __ldg(cw);
+    for (uint32_t j = 0; j < L; j += 16) {
+        const uint32_t w0 = (j >> 2) + 1;
+        uint32_t tx[4], cx[4];
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            tx[k] = w0 + k < tn ? __ldg(tw + w0 + k) : 0u;
+            cx[k] = w0 + k < cn ? __ldg(cw + w0 + k) : 0u;
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint32_t done = j + 4u * k;
+            if (done < L) {
+                const uint32_t a = __funnelshift_r(tp, tx[k], 8u * ta);
+                const uint32_t b = __funnelshift_r(cp, cx[k], 8u * ca);
+                const uint32_t left = L - done;
+                const uint32_t mask = left >= 4u ? 0xFFFFFFFFu : ((1u << (8u * left)) - 1u);
+                if ((a ^ b) & mask) return false;
+            }
+            tp = tx[k];
+            cp = cx[k];
+        }
+    }
+    return true;
+}
+
 template <typename GT>
 __device__ __forceinline__ int goto_ld(const GT *G, uint32_t s, uint32_t W, uint32_t c) {
     return static_cast<int>(__ldg(G + static_cast<uint64_t>(s) * W + c));

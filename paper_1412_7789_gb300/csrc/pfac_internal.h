@@ -21,6 +21,9 @@ inline int32_t encode_dead(int32_t id) { return -(id + 2); }
 // alive there (r < kJumpMaxStates), or kJumpSlow to send the start to the
 // plain walk (a result that does not fit 15 bits).
 constexpr int16_t kJumpSlow = -32768;
+
+// Chain record of a state with two or more children: take its goto row.
+constexpr uint32_t kSkipBranch = 0xFFFFFFFFu;
 constexpr uint32_t kJumpMaxStates = 32766;
 
 // Bits of the per-device kernel error word.
@@ -37,6 +40,7 @@ struct BuildOptions {
     int class_compress = 1;     // 1 = distinct keyword bytes, 0 = 256 columns
     uint32_t jump_bytes = 128u << 10;
     uint64_t stride_bytes = 16ull << 20;
+    bool chains = true;         // chain records for the deep states
 };
 
 // Host-side automaton: everything the kernels need, in the layout they use.
@@ -69,6 +73,12 @@ struct HostTables {
     std::vector<int16_t> J;          // 2^(B*k) (padded to 8 entries)
     std::vector<int32_t> J2;         // count_k << (B*k2)
     std::vector<uint32_t> depth_count;  // maxlen + 1
+    // Chain records, one per state from s_chain on (4 words: run length or
+    // kSkipBranch, offset of the run's bytes in `chain`, the run's end state,
+    // the state's result), and the runs' raw bytes.
+    uint32_t s_chain = 0;
+    std::vector<uint32_t> skip;
+    std::vector<uint8_t> chain;
     bool identity_classes() const { return C == 256; }
 };
 
@@ -89,6 +99,9 @@ struct DevTables {
     uint32_t fbytes = 0;             // bytes of F
     bool filter = false;
     const int32_t *J2 = nullptr;     // stride table
+    const uint4 *skip = nullptr;     // chain records (states from s_chain on), or none
+    const uint8_t *chain = nullptr;  // chain bytes
+    uint32_t s_chain = 0xFFFFFFFFu;  // first state with a chain record
     const int16_t *cls = nullptr;    // class map (256 entries)
     const uint8_t *cls8 = nullptr;   // byte class map (256 entries, 0xFF = unknown byte)
     uint32_t S = 0, C = 0, W = 0, gbits = 32, B = 8, k = 0, k2 = 0, base_k = 0, maxlen = 0;

@@ -214,3 +214,57 @@ def test_struct_layouts_match_the_header(tmp_path):
             assert int(got[name]) == ctypes.sizeof(m), name
             for f, _ in m._fields_:
                 assert int(got["%s.%s" % (name, f)]) == getattr(m, f).offset, (name, f)
+
+
+def _walk_with_chains(cls, G, s_chain, rec, byt, text, i):
+    """The walk from position i using the goto table above s_chain and the
+    chain records from s_chain on (the kernels' rule, written out plainly)."""
+    C = G.shape[1] - 1
+    n = text.size
+    s, q = 0, i
+    while True:
+        if s >= s_chain:
+            L, off, end, res = (int(x) for x in rec[s - s_chain])
+            res = res - (1 << 32) if res >= (1 << 31) else res
+            if L != 0xFFFFFFFF:
+                if L > 0 and q + L <= n and bytes(text[q:q + L]) == bytes(byt[off:off + L]):
+                    s, q = end, q + L
+                    continue
+                return res
+        c = int(cls[text[q]]) if q < n else C
+        if c < 0:
+            c = C
+        e = int(G[s, c])
+        if e < 0:
+            return -e - 2
+        s, q = e, q + 1
+
+
+@pytest.mark.parametrize("alpha", [b"ACGT", bytes(range(40, 80)), bytes(range(256))])
+def test_chain_records_reproduce_the_walk(lib, alpha):
+    """Walking with the chain records gives the oracle's ids (brute force over
+    every position of random texts with long, partly copied keywords)."""
+    g = np.random.Generator(np.random.PCG64(len(alpha)))
+    a = np.frombuffer(alpha, dtype=np.uint8)
+    for case in range(3):
+        text = a[g.integers(0, a.size, size=3000)]
+        pats = []
+        for _ in range(60):
+            L = int(g.integers(1, 40))
+            if g.random() < 0.6:
+                o = int(g.integers(0, text.size - L))
+                pats.append(bytes(text[o:o + L]))
+            else:
+                pats.append(bytes(a[g.integers(0, a.size, size=L)]))
+        h = api.ac_compile(pats, host_only=True)
+        try:
+            cls, G, depth = api.ac_export_tables(h)
+            s_chain, rec, byt = api.ac_export_chains(h)
+        finally:
+            api.ac_destroy(h)
+        assert s_chain < G.shape[0] and rec.shape[0] == G.shape[0] - s_chain
+        runs = rec[:, 0][rec[:, 0] != 0xFFFFFFFF]
+        assert runs.max() >= 2  # long runs exist, so the test exercises them
+        want = oracle.pfac_ids(pats, text)
+        got = np.array([_walk_with_chains(cls, G, s_chain, rec, byt, text, i) for i in range(text.size)])
+        assert np.array_equal(got, want), case
