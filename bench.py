@@ -34,10 +34,9 @@ GIB = 1 << 30
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the kernel as it stands, keyed by (workload, text bytes,
 # kernel): the 256 MiB capture summarised in
-# profiles/pfac_filter_pipe_acgt_256mib_full.md (DRAM bytes re-taken after the
-# last change of the kernel), scaled by 4 to the 1 GiB launch.  Drop an entry
-# whenever its kernel changes.
-KNOWN_TRAFFIC = {("sweep", GIB, "pfac_filter_pipe"): 5.408e9}
+# profiles/pfac_filter_pipe_acgt_256mib_full.md, scaled by 4 to the 1 GiB
+# launch.  Drop an entry whenever its kernel changes.
+KNOWN_TRAFFIC = {("sweep", GIB, "pfac_filter_pipe"): 5.313e9}
 
 
 def kernel_name(info: dict, out_kind: str, kernel: str) -> str:
@@ -709,17 +708,23 @@ def run_batch(args):
 
     cpu = None
     if not args.no_cpu:
-        # the oracle on the first texts of the batch, about cpu_seconds of work
-        t0 = time.perf_counter()
-        done_b = 0
-        for i in range(len(texts)):
-            oracle.pfac_ids(sets[which[i]], texts[i])
-            done_b += int(lens[i])
-            if time.perf_counter() - t0 > args.cpu_seconds:
-                break
-        dt = time.perf_counter() - t0
+        # the oracle on the first texts of the batch, about cpu_seconds of
+        # matching (its eight machines built first, outside the timing)
+        machines = [oracle.Machine(p) for p in sets]
+        try:
+            t0 = time.perf_counter()
+            done_b = 0
+            for i in range(len(texts)):
+                machines[which[i]].pfac_ids(texts[i])
+                done_b += int(lens[i])
+                if time.perf_counter() - t0 > args.cpu_seconds:
+                    break
+            dt = time.perf_counter() - t0
+        finally:
+            for m in machines:
+                m.close()
         cpu = {"value": done_b / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": "first %d texts of the batch (%d B), serially, keyword sets compiled per text" % (
+               "sample": "first %d texts of the batch (%d B), serially, one machine per keyword set" % (
                    i + 1, done_b)}
 
     peak, peak_kind = load_peaks()
