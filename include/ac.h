@@ -302,18 +302,21 @@ ac_status ac_batch_replay(ac_batch b, void *stream);
 ac_status ac_batch_destroy(ac_batch b);
 
 /*
- * Autotuning (no counterpart in the paper): time the dense kernel of handle h
- * on the device text d_sample (n bytes, at least 1 MiB is sensible) with each
- * candidate launch shape -- threads per CTA {256, 384, 512} x text stages per
- * warp {2, 3, 4}, the shapes that fit shared memory -- and keep the fastest
- * for every later call on h (single texts and batches).  Each candidate runs
- * `reps` times (0 = 5) after one warm-up; the median is compared.  Writes the
- * chosen shape to *block / *stages when they are not NULL.  Synchronises
- * `stream`; uses scratch output memory of 4 * n bytes from the library pool.
- * Results never depend on the shape, only the time does.
+ * Autotuning (no counterpart in the paper): time the dense matching of handle
+ * h on the device text d_sample (n bytes, at least 1 MiB is sensible) with
+ * each candidate -- for up to 16 keyword bytes, threads per CTA {256, 384,
+ * 512} x text stages per warp {2, 3, 4}, the shapes that fit shared memory;
+ * for more, the kernels AC_KERNEL_THREAD_JUMP_L1, AC_KERNEL_THREAD_JUMP and
+ * AC_KERNEL_WALK_SLOTS (the last with each shape) -- and keep the fastest for
+ * every later call on h (single texts, batches and servers created after).
+ * Each candidate runs `reps` times (0 = 5) after one warm-up; the median is
+ * compared.  Writes the choice to *block, *stages and *kernel (an ac_kernel)
+ * when they are not NULL.  Synchronises `stream`; takes 4 * n bytes of
+ * scratch from the library pool.  Do not match on h from another thread
+ * meanwhile.  Results never depend on the choice, only the time does.
  */
 ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t reps, void *stream,
-                      uint32_t *block, uint32_t *stages);
+                      uint32_t *block, uint32_t *stages, uint32_t *kernel);
 
 /*
  * ---- Serving: continuous batching of compacted-match requests ---------------

@@ -107,7 +107,7 @@ _SIGS = {
     "ac_batch_replay": (ctypes.c_int, [_P, _P]),
     "ac_batch_destroy": (ctypes.c_int, [_P]),
     "ac_autotune": (ctypes.c_int, [_H, _P, _U64, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_uint32),
-                                   ctypes.POINTER(ctypes.c_uint32)]),
+                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "ac_server_create": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_void_p)]),
     "ac_server_submit": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "ac_server_replay": (ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P]),
@@ -305,14 +305,17 @@ def ac_match_batch(hs, texts, items, nitems: int, out, stream=None):
                                 _dev_ptr(out, 4), _stream_ptr(stream)), "ac_match_batch")
 
 
-def ac_autotune(h: int, sample, n: int | None = None, reps: int = 0, stream=None) -> tuple[int, int]:
-    """Pick the fastest launch shape for h on a device sample; returns (block, stages)."""
+def ac_autotune(h: int, sample, n: int | None = None, reps: int = 0, stream=None) -> tuple[int, int, str]:
+    """Pick the fastest kernel and launch shape for h on a device sample;
+    returns (block, stages, kernel name)."""
     b = ctypes.c_uint32()
     s = ctypes.c_uint32()
+    k = ctypes.c_uint32()
     n = sample.numel() if n is None else n
-    _check(lib().ac_autotune(h, _dev_ptr(sample), n, reps, _stream_ptr(stream), ctypes.byref(b), ctypes.byref(s)),
-           "ac_autotune")
-    return int(b.value), int(s.value)
+    _check(lib().ac_autotune(h, _dev_ptr(sample), n, reps, _stream_ptr(stream), ctypes.byref(b), ctypes.byref(s),
+                             ctypes.byref(k)), "ac_autotune")
+    names = {v: name for name, v in KERNELS.items()}
+    return int(b.value), int(s.value), names.get(int(k.value), "tiled")
 
 
 class BatchPlan:
@@ -422,7 +425,7 @@ class Automaton:
         ac_match_compact(self.handle, text, n, pos, ids, cap, cnt, stream)
         return pos, ids, cnt
 
-    def autotune(self, sample, reps: int = 0, stream=None) -> tuple[int, int]:
+    def autotune(self, sample, reps: int = 0, stream=None) -> tuple[int, int, str]:
         return ac_autotune(self.handle, sample, reps=reps, stream=stream)
 
     def match_host(self, text, out=None, stream=None):

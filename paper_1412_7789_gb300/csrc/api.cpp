@@ -624,7 +624,7 @@ ac_status ac_batch_replay(ac_batch b, void *stream) {
 }
 
 ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t reps, void *stream,
-                      uint32_t *block, uint32_t *stages) {
+                      uint32_t *block, uint32_t *stages, uint32_t *kernel) {
     ac_status s = check_device(h);
     if (s != AC_OK) return s;
     if (!d_sample || n == 0) return AC_ERR_INVALID_ARG;
@@ -640,49 +640,69 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
     e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     const pfac::Tuning keep = h->tuning;
+    const ac_kernel keep_kernel = h->kernel;
+    h->kernel = AC_KERNEL_TILED;
     pfac::Tuning best = keep;
     float best_ms = -1.0f;
     pfac::MatchRequest r;
     r.text = d_sample;
     r.n = n;
     r.out = static_cast<int32_t *>(out);
+    // candidates: threads per CTA x stages for the tiled kernels; for 8-bit
+    // codes also the two one-thread-per-position kernels (one shape each)
+    std::vector<pfac::Tuning> cands;
     static const int kBlocks[3] = {256, 384, 512};
-    for (int bi = 0; bi < 3 && e == cudaSuccess; ++bi) {
-        for (int sg = 2; sg <= 4 && e == cudaSuccess; ++sg) {
+    const std::vector<int> variants = h->dev.filter ? std::vector<int>{0} : std::vector<int>{3, 2, 1};
+    for (int v : variants) {
+        if (v == 2 || v == 3) {
             pfac::Tuning tu = keep;
-            tu.block = kBlocks[bi];
-            tu.stages = sg;
+            tu.variant = v;
             tu.grid = 0;
-            h->tuning = tu;
-            cudaError_t le = run_tiled(h, r, pfac::OUT_DENSE, st);  // warm-up
-            if (le == cudaErrorInvalidConfiguration) {              // does not fit shared memory
-                cudaGetLastError();
-                continue;
+            cands.push_back(tu);
+            continue;
+        }
+        for (int bi = 0; bi < 3; ++bi)
+            for (int sg = 2; sg <= 4; ++sg) {
+                pfac::Tuning tu = keep;
+                tu.variant = v;
+                tu.block = kBlocks[bi];
+                tu.stages = sg;
+                tu.grid = 0;
+                cands.push_back(tu);
             }
-            if (le != cudaSuccess) {
-                e = le;
-                break;
-            }
-            std::vector<float> ms;
-            for (uint32_t i = 0; i < reps && e == cudaSuccess; ++i) {
-                e = cudaEventRecord(t0, st);
-                if (e == cudaSuccess) e = run_tiled(h, r, pfac::OUT_DENSE, st);
-                if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-                float v = 0.0f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t0, t1);
-                ms.push_back(v);
-            }
-            if (e != cudaSuccess) break;
-            std::sort(ms.begin(), ms.end());
-            const float med = ms[ms.size() / 2];
-            if (best_ms < 0.0f || med < best_ms) {
-                best_ms = med;
-                best = tu;
-            }
+    }
+    for (const pfac::Tuning &tu : cands) {
+        if (e != cudaSuccess) break;
+        h->tuning = tu;
+        cudaError_t le = run_tiled(h, r, pfac::OUT_DENSE, st);  // warm-up
+        if (le == cudaErrorInvalidConfiguration) {              // does not fit shared memory
+            cudaGetLastError();
+            continue;
+        }
+        if (le != cudaSuccess) {
+            e = le;
+            break;
+        }
+        std::vector<float> ms;
+        for (uint32_t i = 0; i < reps && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(t0, st);
+            if (e == cudaSuccess) e = run_tiled(h, r, pfac::OUT_DENSE, st);
+            if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+            float v = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t0, t1);
+            ms.push_back(v);
+        }
+        if (e != cudaSuccess) break;
+        std::sort(ms.begin(), ms.end());
+        const float med = ms[ms.size() / 2];
+        if (best_ms < 0.0f || med < best_ms) {
+            best_ms = med;
+            best = tu;
         }
     }
     h->tuning = e == cudaSuccess ? best : keep;
+    h->kernel = keep_kernel == AC_KERNEL_SIMPLE ? AC_KERNEL_TILED : keep_kernel;
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
     const cudaError_t e2 = cudaFreeAsync(out, st);
@@ -691,6 +711,11 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
     if (e != cudaSuccess) return cuda_status(e);
     if (block) *block = static_cast<uint32_t>(h->tuning.block);
     if (stages) *stages = static_cast<uint32_t>(h->tuning.stages);
+    if (kernel) {
+        static const uint32_t kByVariant[4] = {AC_KERNEL_TILED, AC_KERNEL_WALK_SLOTS, AC_KERNEL_THREAD_JUMP,
+                                               AC_KERNEL_THREAD_JUMP_L1};
+        *kernel = h->dev.filter ? AC_KERNEL_TILED : kByVariant[h->tuning.variant & 3];
+    }
     return AC_OK;
 }
 

@@ -229,8 +229,9 @@ def test_autotune_keeps_results(automata):
     for j in (0, 2):
         text = _text_for(j, 3 << 20, 40 + j, sets)
         t = _gpu.to_dev(text)
-        block, stages = hs[j].autotune(t, reps=2)
-        assert block in (256, 384, 512) and stages in (2, 3, 4)
+        block, stages, kernel = hs[j].autotune(t, reps=2)
+        assert block in (256, 384, 512) and stages in (0, 2, 3, 4)
+        assert kernel in (("tiled",) if j == 0 else ("thread_jump_l1", "thread_jump", "walk_slots"))
         want = oracle.pfac_ids(sets[j], text[: 1 << 20])
         got = _gpu.dense(hs[j].handle, t[: 1 << 20]).cpu().numpy()
         assert np.array_equal(got, want)
