@@ -561,15 +561,15 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
         bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
         bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
     }
-    // Tiles: the first one per warp statically (warp-major numbering, so
-    // neighbouring tiles land on different SMs), the rest claimed from a global
+    // Tiles: the first one per warp statically, the rest claimed from a global
     // counter so that a warp held up by an expensive tile stops taking work.
     const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
-    auto next_tile = [&](uint32_t it) -> uint32_t {
+    UnitClaims claims = claims_start(gw, GW);
+    auto next_tile = [&](uint32_t) -> uint32_t {
         uint32_t t = 0xFFFFFFFFu;
         if (lane == 0) {
-            const uint64_t c = it == 0 ? gw : GW + atomicAdd(p.counter, 1u);
+            const uint64_t c = claims_next(claims, p.counter, wk.units);
             if (c < wk.units) t = static_cast<uint32_t>(c);
         }
         return __shfl_sync(kFull, t, 0);

@@ -310,10 +310,11 @@ __global__ void __launch_bounds__(kBlock, 1) pfac_jump8(const JumpParams p) {
     }
     const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
     const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
-    auto next_tile = [&](uint32_t it) -> uint32_t {  // all lanes
+    UnitClaims claims = claims_start(gw, GW);
+    auto next_tile = [&](uint32_t) -> uint32_t {  // all lanes
         uint32_t t = 0xFFFFFFFFu;
         if (lane == 0) {
-            const uint64_t c = it == 0 ? gw : GW + atomicAdd(p.counter, 1u);
+            const uint64_t c = claims_next(claims, p.counter, wk.units);
             if (c < wk.units) t = static_cast<uint32_t>(c);
         }
         return __shfl_sync(kFull, t, 0);

@@ -220,6 +220,57 @@ __device__ __forceinline__ uint32_t find_item(const Work &wk, uint32_t u, int la
     return lo + static_cast<uint32_t>(31 - __clz(b));
 }
 
+// Lane 0 of a warp: the warp's work units in the order it takes them.  The
+// first is static (warp-major numbering, so neighbouring units land on
+// different SMs); the rest come from a global counter in blocks of
+// consecutive units whose size shrinks with the work left: a quarter of one
+// warp's share of it, at most kClaimMax and at least 1.  Early claims are
+// large, so the counter sees few atomics; the last units still go out one at
+// a time, so a warp held up by an expensive unit leaves the rest to others.
+constexpr uint32_t kClaimMax = 32;
+
+struct UnitClaims {
+    uint64_t first;  // the static unit (~0: taken)
+    uint32_t skip;   // units before the counter's first: warps in the grid
+    uint32_t next;   // the current block's next unit (counter numbering)
+    uint32_t left;   // its units not yet taken
+    uint32_t seen;   // the counter after this warp's last claim
+};
+
+__device__ __forceinline__ UnitClaims claims_start(uint64_t first, uint64_t grid_warps) {
+    UnitClaims c;
+    c.first = first;
+    c.skip = static_cast<uint32_t>(grid_warps);
+    c.next = 0;
+    c.left = 0;
+    c.seen = 0;
+    return c;
+}
+
+// Lane 0: the next unit, or ~0 once the units are used up (then ~0 for good).
+// units < 2^31.
+__device__ __forceinline__ uint64_t claims_next(UnitClaims &c, unsigned int *counter, uint64_t units) {
+    if (c.first != ~0ull) {
+        const uint64_t u = c.first;
+        c.first = ~0ull;
+        return u;
+    }
+    if (c.left == 0) {
+        if (units <= c.skip) return ~0ull;
+        const uint32_t dyn = static_cast<uint32_t>(units) - c.skip;  // units the counter hands out
+        if (c.seen >= dyn) return ~0ull;
+        uint32_t blk = (dyn - c.seen) / (4u * c.skip);
+        blk = blk < 1u ? 1u : (blk > kClaimMax ? kClaimMax : blk);
+        const uint32_t at = atomicAdd(counter, blk);
+        c.seen = at + blk < at ? 0xFFFFFFFFu : at + blk;
+        if (at >= dyn) return ~0ull;
+        c.next = at;
+        c.left = dyn - at < blk ? dyn - at : blk;
+    }
+    --c.left;
+    return static_cast<uint64_t>(c.skip) + c.next++;
+}
+
 // One thread: start the bulk copy of tile t.tile into shared buffer st (text
 // lines marked to leave L2 first: the text is read once).  Only the 16-byte
 // aligned part inside the text is copied; load_text_fringe fetches the rest.
