@@ -251,13 +251,19 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             h.base_k = depth_base[kf];
             h.count_k = h.depth_count[kf];
             const uint32_t nwin = 1u << (h.B * kf);
+            // The bit of window w is bit 31 - (w & 31) of word w >> 5 (the
+            // kernel rotates it to bit 31); windows of fewer than 5 bits are
+            // repeated over the 32 bits of word 0, as the kernel indexes by
+            // the low 5 bits of the code stream.
             h.F.assign(std::max<uint32_t>(nwin / 32u, 4u), 0u);
             h.JK.assign(nwin, 0);
             for (uint32_t w = 0; w < nwin; ++w) {
                 int32_t e = 0;
                 const bool alive = walk_codes(0, w, kf, &e);
                 h.JK[w] = e;
-                if (alive || e < -1) h.F[w >> 5] |= 1u << (w & 31u);
+                if (alive || e < -1)
+                    for (uint32_t v = w; v < std::max<uint32_t>(nwin, 32u); v += nwin)
+                        h.F[v >> 5] |= 1u << (31u - (v & 31u));
             }
         } else {
             // 6b. root jump table (8-bit codes).  Entry for a window of k codes:

@@ -66,6 +66,7 @@ struct FilterParams {
     const int32_t *J2;
     const uint8_t *cls8g;
     uint32_t C, W, k, k2, base_k, maxlen, fbytes;
+    uint32_t famask;  // byte offsets of the root filter's words reached by a window
     int hash_shift;
     uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
     int32_t *out;
@@ -656,7 +657,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
         nlo[0] = __shfl_down_sync(kFull, plo[0], 1);
         nlo[1] = __shfl_down_sync(kFull, plo[1], 1);
         if (owner) {
-            const uint32_t fmask = (1u << (B * k)) - 1u;
+            // The bit of window value v is bit 31 - (v & 31) of filter word
+            // v >> 5: rotating the word left by v's low five bits brings it to
+            // bit 31, and a funnel shift appends it to acc (first position
+            // ends highest, hence the bit reversal).
+            const uint8_t *fb = reinterpret_cast<const uint8_t *>(w.F);
+            uint32_t acc = 0;
 #pragma unroll
             for (uint32_t h = 0; h < 2; ++h) {
 #pragma unroll
@@ -667,10 +673,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                     else
                         win = r < 8 ? __funnelshift_r(plo[h], phi[h], 4 * r)
                                     : __funnelshift_r(phi[h], nlo[h], 4 * (r - 8));
-                    const uint32_t idx = win & fmask;
-                    sv |= ((w.F[idx >> 5] >> (idx & 31u)) & 1u) << (16 * h + r);
+                    const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & p.famask));
+                    acc = __funnelshift_l(__funnelshift_l(word, word, win), acc, 1);
                 }
             }
+            sv = __brev(acc);
         }
         if (!interior || !clean) {
             const uint32_t kbits = (1u << k) - 1u;
@@ -925,6 +932,12 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.base_k = t.base_k;
     p.maxlen = t.maxlen;
     p.fbytes = t.fbytes;
+    {
+        const uint32_t wb = t.B * t.k;  // window bits; windows below 32 are replicated to 32
+        const uint32_t nb = (wb >= 5 ? (1u << wb) : 32u) / 8u;
+        if (nb > t.fbytes) return cudaErrorInvalidValue;
+        p.famask = (nb - 1u) & ~3u;
+    }
     p.skip = t.skip;
     p.chain = t.chain;
     p.s_chain = t.skip ? t.s_chain : 0xFFFFFFFFu;
