@@ -581,9 +581,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
     unsigned long long cnt = 0;
     Flight f1 = empty_flight(), f2 = empty_flight();  // one and two tiles back
     bool ok = mbar_wait(jbar, 0);
-    for (uint32_t it = 0;; ++it) {
-        const uint32_t s = it % nst;
-        ok = ok && mbar_wait(&bars[s], (it / nst) & 1u);
+    // stage s of iteration it is it % nst, its phase parity (it / nst) & 1
+    for (uint32_t it = 0, s = 0, par = 0;; ++it, s = s + 1 == nst ? 0u : s + 1, par ^= s == 0 ? 1u : 0u) {
+        ok = ok && mbar_wait(&bars[s], par);
         if (!__all_sync(kFull, ok)) {
             // A copy never completed: latch the error, let this warp's copies in
             // flight finish (bounded), and leave.
