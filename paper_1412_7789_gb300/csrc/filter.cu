@@ -79,6 +79,12 @@ struct FilterParams {
     // the bases of all texts and outputs)
     const BatchHead *batch;
     const BatchItemDev *lists;
+    // one text: its 16-byte aligned base, the tile starts whose staged bytes
+    // lie wholly in its aligned part [a1, a2), and whether its output takes
+    // 16-byte stores
+    const uint8_t *gbase;
+    uint64_t a1, a2;
+    uint32_t vec_ok;
     // chain records from state s_chain on (0xFFFFFFFF: none)
     const uint4 *skip;
     const uint8_t *chain;
@@ -109,10 +115,16 @@ __device__ __forceinline__ void issue_unit(const FilterParams &p, const Work &wk
     if (lane == 0) {
         *stile = u;
         *sitem = item;
-        if (u >= wk.units)
+        const uint64_t tlo = static_cast<uint64_t>(u) * p.tile;
+        if (u >= wk.units) {
             mbar_arrive(bar);
-        else
+        } else if (!wk.list && tlo >= p.a1 && tlo + p.staged <= p.a2) {
+            // one text, a tile inside its aligned part: the whole stage
+            mbar_arrive_expect_tx(bar, p.staged);
+            bulk_load_hint(st, p.gbase + tlo, p.staged, bar, policy_evict_first());
+        } else {
             issue_text_tile(tile_text(p, wk, u, item), p.tile, p.staged, bar, st);
+        }
     }
 }
 
@@ -494,6 +506,14 @@ __device__ __forceinline__ void flight_output(const FilterParams &p, const Work 
         return;
     }
     const bool found = __any_sync(kFull, mine);
+    if (!found && f.interior && !wk.list && p.vec_ok) {  // one text: no lookup of its output
+        if (lane == 0) {
+            bulk_store(p.out + f.gpb, w.neg1, kTile * 4);
+            bulk_commit();
+            bulk_wait_read_keep8();  // bound the groups in flight
+        }
+        return;
+    }
     const TileText tt = tile_text(p, wk, f.tile, f.item);
     const int64_t n = static_cast<int64_t>(tt.n);
     if (!found && f.interior && tt.vec_ok) {
@@ -895,6 +915,13 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
         if (tiles >= 0x7FFFFFFFull) return cudaErrorInvalidValue;
     }
     p.ntiles = static_cast<uint32_t>(tiles);
+    if (!batch) {
+        const uint64_t head = reinterpret_cast<uintptr_t>(r.text) & 15u;
+        p.gbase = r.text - head;
+        p.a1 = (head + 15u) & ~15ull;
+        p.a2 = (head + r.n) & ~15ull;
+        p.vec_ok = ((reinterpret_cast<uintptr_t>(r.out) - 4u * head) & 15u) == 0 ? 1u : 0u;
+    }
     p.batch = r.batch;
     p.lists = r.lists;
     // per-warp layout: stages, packed codes, unknown-byte bits, survivor
