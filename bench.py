@@ -46,8 +46,9 @@ def kernel_name(info: dict, out_kind: str, kernel: str) -> str:
         name = "pfac_filter_pipe"
     else:
         name = {"thread_jump": "pfac_jump8", "walk_slots": "pfac_walk8"}.get(kernel, "pfac_jump8g")
-    # the compacted list: the matcher in slot mode, then scan and gather
-    return name + "+compact" if out_kind == "compact" else name
+    # the compacted list: the matcher in slot mode, then scan and gather; the
+    # full output: the matcher in slot mode, occurrence counts, scan, expansion
+    return name + {"compact": "+compact", "full": "+full"}.get(out_kind, "")
 
 
 def load_peaks():
@@ -149,23 +150,27 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands, one core, bounded sample
 # ----------------------------------------------------------------------------
-def cpu_baseline(text: np.ndarray, pats, budget_s: float = 12.0):
+def cpu_baseline(text: np.ndarray, pats, budget_s: float = 12.0, full: bool = False):
     import oracle
 
     with oracle.Machine(pats) as m:
+        # the full output: the serial pass listing every occurrence
+        run = m.full_occurrences if full else m.pfac_ids
         probe = min(text.size, 1 << 18)
         t0 = time.perf_counter()
-        m.pfac_ids(text[:probe])
+        run(text[:probe])
         dt = max(time.perf_counter() - t0, 1e-6)
         size = int(min(text.size, max(probe, probe * budget_s / dt)))
         t0 = time.perf_counter()
-        m.pfac_ids(text[:size])
+        run(text[:size])
         dt = time.perf_counter() - t0
         wprobe = min(size, 1 << 22)
         steps, longest = m.walk_steps(text[:wprobe])
     return {"value": size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "first %d B of the same text, one serial pass (goto/failure/output, then per-start "
-                      "longest conversion) on one host core" % size,
+            "sample": ("first %d B of the same text, one serial pass (goto/failure/output, every occurrence "
+                       "listed) on one host core" % size) if full else
+                      ("first %d B of the same text, one serial pass (goto/failure/output, then per-start "
+                       "longest conversion) on one host core" % size),
             "seconds": dt, "walk_steps_per_position": steps / max(wprobe, 1), "longest_walk": longest}
 
 
@@ -247,7 +252,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         out_kind = args.out
         desc += " [output: %s]" % out_kind
     n = text_np.size
-    a = api.Automaton(pats, chains=not args.no_chains)
+    t_build = time.perf_counter()
+    a = api.Automaton(pats, chains=not args.no_chains)  # host build + upload, outside the timed region
+    build_s = time.perf_counter() - t_build
     a.set_kernel(args.kernel)
     info = a.info()
     text = torch.from_numpy(text_np).to(dev)
@@ -271,18 +278,19 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         pos = torch.empty(cap, dtype=torch.int32, device=dev)
         ids = torch.empty(cap, dtype=torch.int32, device=dev)
         cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        call = api.ac_match_full if out_kind == "full" else api.ac_match_compact
 
         def step():
-            api.ac_match_compact(a.handle, text, n, pos, ids, cap, cnt, stream)
+            call(a.handle, text, n, pos, ids, cap, cnt, stream)
 
         out_bytes_per_pos = None
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
-    if out_kind == "compact":
+    if out_kind in ("compact", "full"):
         matches = int(cnt.item())
         if matches > cap:
-            raise SystemExit("compact capacity too small: %d > %d" % (matches, cap))
+            raise SystemExit("%s capacity too small: %d > %d" % (out_kind, matches, cap))
         algo_bytes = n + 8 * matches
     elif out_kind == "count":
         matches = int(cnt.item())
@@ -347,7 +355,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     extra = {"automaton": {k: info[k] for k in ("n_states", "n_classes", "index_width", "code_bits",
                                                   "jump_depth", "stride_depth", "max_len", "table_bytes")},
-             "launch_ms_median": statistics.median(per), "launch_ms_min": min(per)}
+             "launch_ms_median": statistics.median(per), "launch_ms_min": min(per),
+             "automaton_build_s": build_s}
     if matches is not None:
         extra["matches"] = matches
     if args.compare_simple and out_kind == "dense" and args.kernel != "simple":
@@ -365,7 +374,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(text_np, pats, args.cpu_seconds)
+        cpu = cpu_baseline(text_np, pats, args.cpu_seconds, full=out_kind == "full")
         extra["lookups_per_s"] = cpu["walk_steps_per_position"] * n * args.steps / (t_ms * 1e-3)
 
     if rank == 0:
@@ -377,7 +386,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                        "l2": "inputs larger than L2 (%.1f GB text + output per step)" % (algo_bytes / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps * (4 if out_kind == "compact" else 1), "extra": extra,
+            "gpu_launches": args.steps * {"compact": 4, "full": 5}.get(out_kind, 1), "extra": extra,
         }
         print(json.dumps(line), flush=True)
 
@@ -549,6 +558,63 @@ def run_sweep(args):
                              "crossover": {key: _crossing(pts, key) for key in ("gpu_kernel_s", "gpu_call_s", "gpu_e2e_s")}}
         pt.close()
     res["paper_mode"] = paper
+    print(json.dumps(res), flush=True)
+
+
+def _crossovers(timer, sizes, refine: bool):
+    """Coarse points and, per GPU scope, the crossover (refined between the
+    bracketing sizes with the paper's 20-point second sweep)."""
+    pts = [timer.point(n) for n in sizes]
+    cross = {}
+    for key in ("gpu_kernel_s", "gpu_call_s", "gpu_e2e_s"):
+        c = _crossing(pts, key)
+        if refine and c is not None and not c["below_range"]:
+            _, c2 = _refine(timer, c["bracket"][0], c["bracket"][1], key)
+            c = c2 or c
+        cross[key] = c
+    return pts, cross
+
+
+def run_sweep_keywords(args):
+    """The crossover against the keyword count (the paper's Fig. 8: ten
+    keywords against five move it): on the paper-mode workload (the alphabet
+    text, permutations of the 26 letters) and on the ACGT sweep workload
+    (keywords of 16-64 characters, half copied from the first 4 KiB)."""
+    from paper_1412_7789_gb300 import build, workloads as W
+
+    build.build()
+    import torch
+
+    torch.cuda.set_device(0)
+    counts = [int(c) for c in args.sweep_keyword_counts]
+    res = {"metric": "CPU/GPU crossover text size against the keyword count", "unit": "bytes",
+           "cpu": "oracle, one host core (serial Aho-Corasick, paper section II)", "counts": counts}
+    try:
+        import multiprocessing
+
+        res["host_cores"] = multiprocessing.cpu_count()
+    except Exception:
+        pass
+    psizes = sorted(set([16375 + 32750 * j for j in range(21)] + [1310 + 2620 * j for j in range(21)]))
+    ptext = W.paper_text(max(psizes))
+    asizes = [1024 * 2 ** j for j in range(13)]  # 1 KiB .. 4 MiB
+    atext, _ = W.sweep_acgt(max(asizes), seed=0, n_keywords=10)
+    out = {"paper_mode": {}, "acgt": {}}
+    for count in counts:
+        pt = SweepTimer(W.paper_keywords(count, seed=0), ptext, max(psizes))
+        pts, cross = _crossovers(pt, psizes, refine=False)
+        out["paper_mode"][str(count)] = {"crossover": cross, "states": pt.a.info()["n_states"],
+                                         "points": pts}
+        pt.close()
+        _, pats = W.sweep_acgt(max(asizes), seed=0, n_keywords=count)
+        at = SweepTimer(pats, atext, max(asizes))
+        pts, cross = _crossovers(at, asizes, refine=True)
+        out["acgt"][str(count)] = {"crossover": cross, "states": at.a.info()["n_states"], "points": pts}
+        at.close()
+        print("keywords %d: paper %s acgt %s" % (
+            count, {k: (v or {}).get("n") for k, v in out["paper_mode"][str(count)]["crossover"].items()},
+            {k: (v or {}).get("n") for k, v in cross.items()}), file=sys.stderr, flush=True)
+    res.update(out)
     print(json.dumps(res), flush=True)
 
 
@@ -893,7 +959,7 @@ def main():
     ap.add_argument("--workload", default="sweep", choices=["sweep", "zipf", "single"])
     ap.add_argument("--n", type=int, default=None, help="text bytes (default: the workload's size)")
     ap.add_argument("--kernel", default="tiled", choices=["tiled", "simple", "walk_slots", "thread_jump", "thread_jump_l1"])
-    ap.add_argument("--out", default=None, choices=["dense", "count", "compact"],
+    ap.add_argument("--out", default=None, choices=["dense", "count", "compact", "full"],
                     help="output kind (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-chains", action="store_true", help="compile without chain records")
@@ -905,6 +971,9 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="input-size sweep and CPU/GPU crossover instead of the throughput line")
     ap.add_argument("--sweep-max", type=int, default=GIB)
+    ap.add_argument("--sweep-keywords", action="store_true",
+                    help="the CPU/GPU crossover against the keyword count (paper Fig. 8)")
+    ap.add_argument("--sweep-keyword-counts", type=int, nargs="+", default=[5, 10, 100, 1000, 10000])
     ap.add_argument("--batch", action="store_true",
                     help="batched workload (4,096 texts, eight automata) instead of the throughput line")
     ap.add_argument("--batch-texts", type=int, default=4096)
@@ -918,6 +987,9 @@ def main():
     args.warmup = max(3, args.warmup)
     if args.sweep:
         run_sweep(args)
+        return
+    if args.sweep_keywords:
+        run_sweep_keywords(args)
         return
     if args.batch:
         run_batch(args)

@@ -169,6 +169,19 @@ ac_status ac_export_chains(ac_handle h, uint32_t *s_chain, uint32_t *records, ui
                            uint64_t *n_bytes);
 
 /*
+ * Full-output records (for inspection and tests; host memory).  For the
+ * lowest id r of each distinct keyword string (the id a walk reports), four
+ * uint32 at records[4 r ..]: up = the lowest id of the longest keyword that is
+ * a proper prefix of r's string (0xFFFFFFFF: none), len = |r|, dup_off, and
+ * clen = the number of keyword ids that are prefixes of r's string (r's own
+ * string and its equal keywords included).  dups[dup_off .. dup_off + clen -
+ * clen(up)) are the ids equal to r's string, ascending.  The records of the
+ * other ids are zero.  records: 4 * n_keywords entries, dups: n_keywords
+ * (either may be NULL); *max_chain receives the largest clen.
+ */
+ac_status ac_export_full(ac_handle h, uint32_t *records, uint32_t *dups, uint32_t *max_chain);
+
+/*
  * Dense matching.  d_out_ids[i] = id of the longest keyword starting at
  * d_text[i] (within the n bytes), or -1.  d_text: n bytes, d_out_ids: n int32,
  * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is
@@ -182,12 +195,30 @@ ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_ou
  * their ids.  Writes min(total, cap) entries to d_pos / d_ids (uint32 each) and
  * the true total to *d_count (a device uint64).  The caller compares the total
  * with cap and calls again with more room when it is larger.  n must be below
- * 2^32.  Takes its scratch (a tile counter and one look-back word per chunk of
- * tiles) from the library's stream-ordered pool (cudaMallocFromPoolAsync) on
- * `stream`; the pool keeps the memory it grows to until the process exits.
+ * 2^32.  Takes its scratch (per tile a match count, a prefix sum, 32 match
+ * slots and a dense fallback of 4 bytes per position) from the library's
+ * stream-ordered pool (cudaMallocFromPoolAsync) on `stream`; the pool keeps the
+ * memory it grows to until the process exits.
  */
 ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
                            uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream);
+
+/*
+ * Full Aho-Corasick output (the serial machine's output function, paper
+ * section II, which reports at every text position each keyword that ends
+ * there, the sub-patterns the failureless walk's longest match leaves out):
+ * every occurrence of every keyword, as its end position (the index of its
+ * last byte) and its id.  Entries are ordered by start position (end - len +
+ * 1), then by end, then by id; equal keywords each get their own entry.
+ * Writes min(total, cap) entries to d_end / d_ids (uint32 each) and the true
+ * total to *d_count (a device uint64); the caller compares the total with cap
+ * and calls again with more room when it is larger.  n must be below 2^32.
+ * Scratch as ac_match_compact, plus 12 bytes per tile, from the same pool.
+ * Returns AC_ERR_OVERFLOW when a tile's occurrences could exceed 2^32 (a
+ * keyword with more than 4 million keywords among its prefixes).
+ */
+ac_status ac_match_full(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_end, uint32_t *d_ids,
+                        uint64_t cap, uint64_t *d_count, void *stream);
 
 /* Number of matched start positions (positions whose dense id is >= 0) into
  * the device uint64 *d_count (overwritten). */

@@ -94,6 +94,8 @@ _SIGS = {
     "ac_export_tables": (ctypes.c_int, [_H, _P, _P, _P]),
     "ac_match": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_compact": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
+    "ac_match_full": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
+    "ac_export_full": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32)]),
     "ac_count": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_host": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_compact_static": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
@@ -230,6 +232,15 @@ def ac_export_chains(h: int):
     return int(sc.value), rec, byt
 
 
+def ac_export_full(h: int, n_keywords: int):
+    """(records uint32[n_keywords, 4], dups uint32[n_keywords], max_chain) -- see ac.h."""
+    rec = np.zeros((n_keywords, 4), dtype=np.uint32)
+    dups = np.zeros(n_keywords, dtype=np.uint32)
+    mc = ctypes.c_uint32()
+    _check(lib().ac_export_full(h, rec.ctypes.data, dups.ctypes.data, ctypes.byref(mc)), "ac_export_full")
+    return rec, dups, int(mc.value)
+
+
 def ac_match(h: int, text, n: int, out, stream=None):
     _check(lib().ac_match(h, _dev_ptr(text), n, _dev_ptr(out, 4), _stream_ptr(stream)), "ac_match")
 
@@ -238,6 +249,12 @@ def ac_match_compact(h: int, text, n: int, pos, ids, cap: int, count, stream=Non
     _check(lib().ac_match_compact(h, _dev_ptr(text), n, _dev_ptr(pos, 4) if cap else 0,
                                   _dev_ptr(ids, 4) if cap else 0, cap, _dev_ptr(count, 8),
                                   _stream_ptr(stream)), "ac_match_compact")
+
+
+def ac_match_full(h: int, text, n: int, end, ids, cap: int, count, stream=None):
+    _check(lib().ac_match_full(h, _dev_ptr(text), n, _dev_ptr(end, 4) if cap else 0,
+                               _dev_ptr(ids, 4) if cap else 0, cap, _dev_ptr(count, 8),
+                               _stream_ptr(stream)), "ac_match_full")
 
 
 # Largest text ac_match_compact_static accepts (AC_STATIC_MAX_TEXT in ac.h).
@@ -424,6 +441,23 @@ class Automaton:
         cnt = torch.zeros(1, dtype=torch.int64, device=text.device)
         ac_match_compact(self.handle, text, n, pos, ids, cap, cnt, stream)
         return pos, ids, cnt
+
+    def match_full(self, text, cap: int | None = None, stream=None):
+        """(end, ids, count): every keyword occurrence (sub-patterns included),
+        ordered by start, end, id; end/ids hold min(count, cap) entries."""
+        import torch
+
+        n = text.numel()
+        if cap is None:
+            cap = max(1, n // 64)
+        end = torch.empty(max(cap, 1), dtype=torch.int32, device=text.device)
+        ids = torch.empty(max(cap, 1), dtype=torch.int32, device=text.device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=text.device)
+        ac_match_full(self.handle, text, n, end, ids, cap, cnt, stream)
+        return end, ids, cnt
+
+    def export_full(self):
+        return ac_export_full(self.handle, self.info()["n_keywords"])
 
     def autotune(self, sample, reps: int = 0, stream=None) -> tuple[int, int, str]:
         return ac_autotune(self.handle, sample, reps=reps, stream=stream)

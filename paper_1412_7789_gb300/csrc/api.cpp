@@ -173,6 +173,23 @@ cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const 
     return e != cudaSuccess ? e : e2;
 }
 
+// The full output of one text with its scratch from the pool.
+cudaError_t run_full(ac_automaton *h, const uint8_t *text, uint64_t n, const pfac::CompactOut &out,
+                     cudaStream_t st) {
+    const uint32_t units = pfac::compact_units(h->dev, text, n);
+    if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
+    const size_t bytes = pfac::full_scratch_bytes(h->dev, units);
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(h->device, &pool);
+    if (e != cudaSuccess) return e;
+    void *scratch = nullptr;
+    e = cudaMallocFromPoolAsync(&scratch, bytes, pool, st);
+    if (e != cudaSuccess) return e;
+    e = pfac::enqueue_full(h->dev, h->tuning, text, n, out, scratch, bytes, st);
+    const cudaError_t e2 = cudaFreeAsync(scratch, st);
+    return e != cudaSuccess ? e : e2;
+}
+
 ac_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return AC_OK;
     if (e == cudaErrorMemoryAllocation) return AC_ERR_OOM;
@@ -293,6 +310,8 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     d.filter = t.filter;
     d.fbytes = static_cast<uint32_t>(t.F.size() * sizeof(uint32_t));
     d.hash_shift = t.hash_shift;
+    d.full_max_clen = t.full_max_clen;
+    d.nkw = t.nkw;
     std::memcpy(d.hash_code, t.hash_code, 8);
     std::memcpy(d.hash_byte, t.hash_byte, 8);
     if (!h->host_only) {
@@ -318,6 +337,12 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
                 s = upload(h, t.chain.data(), t.chain.size(), reinterpret_cast<const void **>(&d.chain));
             d.s_chain = t.s_chain;
         }
+        if (s == AC_OK)
+            s = upload(h, t.full_rec.data(), t.full_rec.size() * sizeof(uint32_t),
+                       reinterpret_cast<const void **>(&d.full_rec));
+        if (s == AC_OK)
+            s = upload(h, t.full_dups.data(), t.full_dups.size() * sizeof(uint32_t),
+                       reinterpret_cast<const void **>(&d.full_dups));
         if (s != AC_OK) {
             ac_destroy(h);
             return s;
@@ -351,7 +376,8 @@ ac_status ac_info(ac_handle h, ac_info_t *info) {
     info->max_len = t.maxlen;
     info->table_bytes = t.G.size() + t.J.size() * sizeof(int16_t) + t.J2.size() * sizeof(int32_t) +
                         t.F.size() * sizeof(uint32_t) + t.JK.size() * sizeof(int32_t) +
-                        t.skip.size() * sizeof(uint32_t) + t.chain.size() + 768;
+                        t.skip.size() * sizeof(uint32_t) + t.chain.size() + 768 +
+                        (t.full_rec.size() + t.full_dups.size()) * sizeof(uint32_t);
     info->depth_base_jump = t.base_k;
     info->count_jump = t.count_k;
     info->class_hash_shift = t.hash_shift;
@@ -376,6 +402,15 @@ ac_status ac_export_chains(ac_handle h, uint32_t *s_chain, uint32_t *records, ui
     *n_bytes = t.chain.size();
     if (records && !t.skip.empty()) std::memcpy(records, t.skip.data(), t.skip.size() * sizeof(uint32_t));
     if (bytes && !t.chain.empty()) std::memcpy(bytes, t.chain.data(), t.chain.size());
+    return AC_OK;
+}
+
+ac_status ac_export_full(ac_handle h, uint32_t *records, uint32_t *dups, uint32_t *max_chain) {
+    if (!h) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    if (records) std::memcpy(records, t.full_rec.data(), t.full_rec.size() * sizeof(uint32_t));
+    if (dups) std::memcpy(dups, t.full_dups.data(), t.full_dups.size() * sizeof(uint32_t));
+    if (max_chain) *max_chain = t.full_max_clen;
     return AC_OK;
 }
 
@@ -442,6 +477,22 @@ ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint3
     if (!d_text) return AC_ERR_INVALID_ARG;
     const pfac::CompactOut out{d_pos, d_ids, cap, reinterpret_cast<unsigned long long *>(d_count)};
     return cuda_status(run_compact(h, d_text, n, out, st));
+}
+
+ac_status ac_match_full(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_end, uint32_t *d_ids,
+                        uint64_t cap, uint64_t *d_count, void *stream) {
+    ac_status s = check_device(h);
+    if (s != AC_OK) return s;
+    if (!d_count || (cap > 0 && (!d_end || !d_ids))) return AC_ERR_INVALID_ARG;
+    if (n > 0xFFFFFFFFull) return AC_ERR_INVALID_ARG;
+    // a unit's occurrence count (at most kDenseStride results, each with up to
+    // full_max_clen occurrences) must fit 32 bits
+    if (static_cast<uint64_t>(h->dev.full_max_clen) * pfac::kDenseStride > 0xFFFFFFFFull) return AC_ERR_OVERFLOW;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) return cuda_status(cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st));
+    if (!d_text) return AC_ERR_INVALID_ARG;
+    const pfac::CompactOut out{d_end, d_ids, cap, reinterpret_cast<unsigned long long *>(d_count)};
+    return cuda_status(run_full(h, d_text, n, out, st));
 }
 
 ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t *h_out_ids, void *stream) {

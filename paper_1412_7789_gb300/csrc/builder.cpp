@@ -18,7 +18,10 @@
 //      the window table (depth-k state reached, or the encoded result); for
 //      8-bit codes the root jump table (result, or depth-k state, per window);
 //   7. the stride table: the depth-(k+k2) state or the result, for k2 more
-//      codes from every depth-k state.
+//      codes from every depth-k state;
+//   8. chain records for the deep, mostly unbranched states;
+//   9. the full-output records: for each keyword, the keywords that are
+//      prefixes of it (its sub-patterns on any walk that reaches it).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -119,6 +122,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         std::unordered_map<uint64_t, uint32_t> child;
         child.reserve(static_cast<size_t>(std::min<uint64_t>(total, 1ull << 26)) + 16);
         std::vector<int32_t> kw_at{-1};   // lowest keyword id ending at each provisional state
+        std::vector<uint32_t> kw_state(nkw);  // each keyword's provisional state
         std::vector<Edge> edges;
         edges.reserve(static_cast<size_t>(std::min<uint64_t>(total, 1ull << 26)));
         for (uint32_t id = 0; id < nkw; ++id) {
@@ -138,6 +142,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                 }
             }
             if (kw_at[s] < 0) kw_at[s] = static_cast<int32_t>(id);  // ids arrive in increasing order
+            kw_state[id] = s;
         }
         child.clear();
         child.rehash(0);
@@ -378,6 +383,41 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                 }
             }
             h.chain.resize(std::max<size_t>(16, (h.chain.size() + 15) & ~static_cast<size_t>(15)), 0);
+        }
+
+        // 9. full output (every keyword occurrence on a walk's path, the
+        //    sub-patterns included): for the lowest id r of each keyword
+        //    string, a record {up, len, dup_off, clen}.  up: the lowest id of
+        //    the longest keyword that is a proper prefix of r's string
+        //    (kNoKeyword: none); len = |r|; dups[dup_off ..) the ids of r's
+        //    string, ascending; clen: the ids of r's string and of every
+        //    keyword that is a proper prefix of it.  States in BFS order come
+        //    after their prefixes, so up's clen is known when r's is set.
+        {
+            std::vector<uint64_t> by_state(nkw);  // (state << 32) | id
+            for (uint32_t id = 0; id < nkw; ++id)
+                by_state[id] = (static_cast<uint64_t>(newid[kw_state[id]]) << 32) | id;
+            std::sort(by_state.begin(), by_state.end());
+            h.full_rec.assign(4ull * nkw, 0);
+            h.full_dups.resize(nkw);
+            h.full_max_clen = 0;
+            for (uint32_t i = 0; i < nkw;) {
+                const uint32_t st = static_cast<uint32_t>(by_state[i] >> 32);
+                uint32_t j = i;
+                while (j < nkw && (by_state[j] >> 32) == st) {
+                    h.full_dups[j] = static_cast<uint32_t>(by_state[j]);
+                    ++j;
+                }
+                const uint32_t r = static_cast<uint32_t>(by_state[i]);  // lowest id of the string
+                const int32_t up = pathbest[parent[st]];
+                uint32_t *rec = &h.full_rec[4ull * r];
+                rec[0] = up >= 0 ? static_cast<uint32_t>(up) : kNoKeyword;
+                rec[1] = depth[st];
+                rec[2] = i;
+                rec[3] = (j - i) + (up >= 0 ? h.full_rec[4ull * static_cast<uint32_t>(up) + 3] : 0u);
+                h.full_max_clen = std::max(h.full_max_clen, rec[3]);
+                i = j;
+            }
         }
     } catch (const std::bad_alloc &) {
         return AC_ERR_OOM;

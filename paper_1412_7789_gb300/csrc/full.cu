@@ -1,0 +1,225 @@
+// Full Aho-Corasick output: every occurrence of every keyword, the
+// sub-patterns included (paper section II: the serial machine's output
+// function reports at each text position all keywords ending there; the
+// failureless walk keeps only the longest keyword per start).
+//
+// A keyword occurs at start i exactly when it is a prefix of the longest
+// keyword r that the failureless walk from i reports, so the full list is the
+// walk's compacted results with each result r expanded into the keywords that
+// are prefixes of r (the builder's full-output records: r's string, its equal
+// keywords, and the chain of proper-prefix keywords).  After the slot-mode
+// matching kernel (per tile its match count and first 32 matches, plus its
+// dense ids when it has more):
+//   full_count   one warp per tile: the tile's occurrences, the sum of the
+//                chain lengths of its results;
+//   scan         the exclusive prefix of those counts over the tiles
+//                (compact_reduce / compact_prefix of compact.cu);
+//   full_gather  one warp per tile: its results in ascending position, each
+//                written out as its occurrences (end = start + len - 1, id),
+//                shortest first, equal strings in ascending id.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pfac_device.cuh"
+
+namespace pfac {
+
+namespace {
+
+constexpr int kFullThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct FullParams {
+    uint64_t n;
+    uint32_t units, tile, head, max_clen, nkw;
+    unsigned int *err;
+    const uint32_t *counts;
+    const unsigned long long *slots;
+    const int32_t *dense;
+    uint32_t *fcounts;
+    const unsigned long long *fprefix;
+    const uint4 *rec;
+    const uint32_t *dups;
+    CompactOut out;
+};
+
+// Chain length of result id (an id outside the keyword set, which no matching
+// kernel writes, latches kErrWalk and counts as none).
+__device__ __forceinline__ uint32_t chain_len(const FullParams &p, uint32_t id) {
+    if (id >= p.nkw) {
+        atomicOr(p.err, static_cast<unsigned>(kErrWalk));
+        return 0;
+    }
+    return __ldg(reinterpret_cast<const uint32_t *>(p.rec) + 4ull * id + 3u);
+}
+
+// The dense id of tile position i of unit u (-1 outside the text).
+__device__ __forceinline__ int dense_id(const FullParams &p, uint32_t u, int64_t gpb, uint32_t i) {
+    const int64_t gp = gpb + static_cast<int64_t>(i);
+    if (gp < 0 || static_cast<uint64_t>(gp) >= p.n) return -1;
+    return __ldg(p.dense + static_cast<uint64_t>(u) * kDenseStride + i);
+}
+
+__global__ void __launch_bounds__(kFullThreads) full_count(const FullParams p) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t u = gw; u < p.units; u += nwarps) {
+        const uint32_t c = __ldg(p.counts + u);
+        uint32_t sum = 0;
+        if (c <= kSlotCap) {
+            if (static_cast<uint32_t>(lane) < c)
+                sum = chain_len(p, static_cast<uint32_t>(__ldg(p.slots + static_cast<uint64_t>(u) * kSlotCap + lane) >> 32));
+        } else {
+            const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
+            for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
+                const int id = dense_id(p, u, gpb, i0 + lane);
+                if (id >= 0) sum += chain_len(p, static_cast<uint32_t>(id));
+            }
+        }
+        sum = __reduce_add_sync(kFull, sum);
+        if (lane == 0) p.fcounts[u] = sum;
+    }
+}
+
+// One lane: the occurrences of result r at start `pos`, from list index `at`:
+// the chain from r down to its shortest prefix keyword fills the range from
+// its end backwards, each string's equal keywords in ascending id.
+__device__ __forceinline__ void put_chain(const FullParams &p, unsigned long long at, uint32_t pos, uint32_t r) {
+    if (r >= p.nkw) return;  // latched by chain_len
+    uint4 rx = __ldg(p.rec + r);
+    for (uint32_t guard = 0; guard < p.max_clen; ++guard) {  // a chain has at most max_clen strings
+        uint4 ru = make_uint4(kNoKeyword, 0u, 0u, 0u);
+        if (rx.x != kNoKeyword && rx.x < p.nkw) ru = __ldg(p.rec + rx.x);
+        const uint32_t end = pos + rx.y - 1u;
+        for (uint32_t j = ru.w; j < rx.w; ++j) {
+            const unsigned long long o = at + j;
+            if (o < p.out.cap) {
+                p.out.pos[o] = end;
+                p.out.ids[o] = __ldg(p.dups + rx.z + (j - ru.w));
+            }
+        }
+        if (rx.x == kNoKeyword) break;
+        rx = ru;
+    }
+}
+
+__global__ void __launch_bounds__(kFullThreads) full_gather(const FullParams p) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t u = gw; u < p.units; u += nwarps) {
+        const uint32_t c = __ldg(p.counts + u);
+        unsigned long long o = __ldg(p.fprefix + u);
+        if (c <= kSlotCap) {
+            // the slots in any order: a result's place is the chain lengths of
+            // the results at smaller positions
+            const unsigned long long e =
+                static_cast<uint32_t>(lane) < c ? __ldg(p.slots + static_cast<uint64_t>(u) * kSlotCap + lane) : ~0ull;
+            const uint32_t pos = static_cast<uint32_t>(e), id = static_cast<uint32_t>(e >> 32);
+            const uint32_t cl = static_cast<uint32_t>(lane) < c ? chain_len(p, id) : 0u;
+            unsigned long long off = 0;
+#pragma unroll 8
+            for (int d = 0; d < 32; ++d) {
+                const uint32_t op = __shfl_sync(kFull, pos, d), oc = __shfl_sync(kFull, cl, d);
+                off += op < pos ? oc : 0u;
+            }
+            if (static_cast<uint32_t>(lane) < c) put_chain(p, o + off, pos, id);
+        } else {
+            const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
+            for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
+                const int id = dense_id(p, u, gpb, i0 + lane);
+                const uint32_t cl = id >= 0 ? chain_len(p, static_cast<uint32_t>(id)) : 0u;
+                uint32_t inc = cl;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                    if (lane >= d) inc += y;
+                }
+                if (id >= 0)
+                    put_chain(p, o + (inc - cl), static_cast<uint32_t>(gpb + i0 + lane), static_cast<uint32_t>(id));
+                o += __shfl_sync(kFull, inc, 31);
+            }
+        }
+        if (lane == 0 && u + 1 == p.units) *p.out.count = __ldg(p.fprefix + u) + __ldg(p.fcounts + u);
+    }
+}
+
+inline size_t round16(size_t v) { return (v + 15u) & ~static_cast<size_t>(15u); }
+
+}  // namespace
+
+// Layout: the compacted output's scratch with its dense fallback | occurrence
+// counts (4 per unit) | their prefix (8 per unit) | partial sums (8 * kScanCtas).
+size_t full_scratch_bytes(const DevTables &t, uint32_t units) {
+    const size_t U = units;
+    return round16(compact_scratch_bytes(t, units, true)) + round16(4 * U) + 8 * U + 8 * static_cast<size_t>(kScanCtas);
+}
+
+cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
+                         const CompactOut &out, void *scratch, size_t scratch_bytes, cudaStream_t stream) {
+    const uint32_t U = compact_units(t, text, n);
+    if (U == 0xFFFFFFFFu || n == 0 || n > 0xFFFFFFFFull || !t.full_rec || !t.full_dups)
+        return cudaErrorInvalidValue;
+    if (!scratch || scratch_bytes < full_scratch_bytes(t, U)) return cudaErrorInvalidValue;
+    uint8_t *b = static_cast<uint8_t *>(scratch);
+    // the compacted output's layout (compact.cu): tile counter | counts | prefix | slots | partials | dense
+    uint32_t *counts = reinterpret_cast<uint32_t *>(b + 16);
+    unsigned long long *slots =
+        reinterpret_cast<unsigned long long *>(b + 16 + round16(4 * size_t(U))) + static_cast<size_t>(U);
+    int32_t *dn = reinterpret_cast<int32_t *>(b + compact_dense_offset(U));
+    uint8_t *f = b + round16(compact_scratch_bytes(t, U, true));
+    uint32_t *fcounts = reinterpret_cast<uint32_t *>(f);
+    unsigned long long *fprefix = reinterpret_cast<unsigned long long *>(f + round16(4 * size_t(U)));
+    unsigned long long *fpartials = fprefix + U;
+
+    cudaError_t e = cudaMemsetAsync(b, 0, 16 + 4 * size_t(U), stream);
+    if (e != cudaSuccess) return e;
+    MatchRequest r;
+    r.text = text;
+    r.n = n;
+    r.slots.counts = counts;
+    r.slots.slots = slots;
+    r.slots.ubase = 0;
+    r.slots.dense = dn;
+    r.scratch = b;
+    r.scratch_bytes = 16;
+    e = t.filter ? launch_filter(t, r, OUT_SLOTS, tu, stream) : launch_tiled(t, r, OUT_SLOTS, tu, stream);
+    if (e != cudaSuccess) return e;
+
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    FullParams p{};
+    p.n = n;
+    p.units = U;
+    p.tile = t.filter ? filter_tile_positions() : tiled_tile_positions();
+    p.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text) & 15u);
+    p.max_clen = t.full_max_clen;
+    p.nkw = t.nkw;
+    p.counts = counts;
+    p.slots = slots;
+    p.dense = dn;
+    p.fcounts = fcounts;
+    p.fprefix = fprefix;
+    p.rec = t.full_rec;
+    p.dups = t.full_dups;
+    p.out = out;
+    e = device_error_word(&p.err);
+    if (e != cudaSuccess) return e;
+    const uint32_t per_cta = kFullThreads / 32;
+    uint32_t grid = static_cast<uint32_t>(sms) * 8u;  // grid-stride over units
+    const uint32_t need = (U + per_cta - 1) / per_cta;
+    if (grid > need) grid = need;
+    full_count<<<grid, kFullThreads, 0, stream>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_compact_scan(fcounts, U, nullptr, fprefix, fpartials, stream);
+    if (e != cudaSuccess) return e;
+    full_gather<<<grid, kFullThreads, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace pfac

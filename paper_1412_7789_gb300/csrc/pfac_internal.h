@@ -24,6 +24,9 @@ constexpr int16_t kJumpSlow = -32768;
 
 // Chain record of a state with two or more children: take its goto row.
 constexpr uint32_t kSkipBranch = 0xFFFFFFFFu;
+
+// Full-output record field `up` of a keyword with no keyword as a proper prefix.
+constexpr uint32_t kNoKeyword = 0xFFFFFFFFu;
 constexpr uint32_t kJumpMaxStates = 32766;
 
 // Bits of the per-device kernel error word.
@@ -79,6 +82,12 @@ struct HostTables {
     uint32_t s_chain = 0;
     std::vector<uint32_t> skip;
     std::vector<uint8_t> chain;
+    // Full output: 4 words per keyword id {up, len, dup_off, clen} (set for
+    // the lowest id of each keyword string, the id a walk reports), the ids
+    // grouped by string, and the largest clen.
+    std::vector<uint32_t> full_rec;
+    std::vector<uint32_t> full_dups;
+    uint32_t full_max_clen = 0;
     bool identity_classes() const { return C == 256; }
 };
 
@@ -102,6 +111,10 @@ struct DevTables {
     const uint4 *skip = nullptr;     // chain records (states from s_chain on), or none
     const uint8_t *chain = nullptr;  // chain bytes
     uint32_t s_chain = 0xFFFFFFFFu;  // first state with a chain record
+    const uint4 *full_rec = nullptr;    // full-output records (one per keyword id)
+    const uint32_t *full_dups = nullptr;
+    uint32_t full_max_clen = 0;
+    uint32_t nkw = 0;
     const int16_t *cls = nullptr;    // class map (256 entries)
     const uint8_t *cls8 = nullptr;   // byte class map (256 entries, 0xFF = unknown byte)
     uint32_t S = 0, C = 0, W = 0, gbits = 32, B = 8, k = 0, k2 = 0, base_k = 0, maxlen = 0;
@@ -220,6 +233,16 @@ size_t compact_scratch_bytes(const DevTables &t, uint32_t units, bool dense);
 cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
                             const CompactOut &out, void *scratch, size_t scratch_bytes, bool dense,
                             cudaStream_t stream);
+// Byte offset of the dense fallback in that scratch (16-byte aligned).
+size_t compact_dense_offset(uint32_t units);
+
+// Full output of one text (full.cu): every keyword occurrence as (end, id)
+// into out.pos / out.ids, ordered by start, end, id; the slot-mode matching
+// kernel, per-unit occurrence counts, their scan, and the expansion.  Scratch:
+// full_scratch_bytes(t, units) bytes, units = compact_units(t, text, n).
+size_t full_scratch_bytes(const DevTables &t, uint32_t units);
+cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
+                         const CompactOut &out, void *scratch, size_t scratch_bytes, cudaStream_t stream);
 
 // 8-bit-code kernel (kernels.cu).  Modes: dense, count, slots; 16 bytes of
 // zeroed scratch (tile counter).

@@ -114,11 +114,13 @@ def paper_keywords(count: int = 5, seed: int = 0) -> list[bytes]:
     permutations of the 26 letters that are not rotations of a..z."""
     g = rng(seed)
     out = [bytes(ALPHABET)]
+    seen = set(out)
     while len(out) < count:
         p = bytes(ALPHABET[g.permutation(26)])
-        if _is_rotation_of_alphabet(p) or p in out:
+        if _is_rotation_of_alphabet(p) or p in seen:
             continue
         out.append(p)
+        seen.add(p)
     return out
 
 

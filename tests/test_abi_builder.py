@@ -268,3 +268,99 @@ def test_chain_records_reproduce_the_walk(lib, alpha):
         want = oracle.pfac_ids(pats, text)
         got = np.array([_walk_with_chains(cls, G, s_chain, rec, byt, text, i) for i in range(text.size)])
         assert np.array_equal(got, want), case
+
+
+def _nested_keywords(g, alpha: bytes, k: int, maxlen: int):
+    """Keywords with many prefix relations and equal strings: prefixes of a few
+    stems, random short words and repeats."""
+    a = np.frombuffer(alpha, dtype=np.uint8)
+    stems = [bytes(a[g.integers(0, a.size, size=maxlen)]) for _ in range(4)]
+    pats = []
+    for _ in range(k):
+        u = g.random()
+        if u < 0.5:
+            s = stems[int(g.integers(0, len(stems)))]
+            pats.append(s[:int(g.integers(1, maxlen + 1))])
+        elif u < 0.8:
+            pats.append(bytes(a[g.integers(0, a.size, size=int(g.integers(1, 5)))]))
+        else:
+            pats.append(pats[int(g.integers(0, len(pats)))] if pats else b"x")
+    return pats
+
+
+def full_chain_brute(pats, r: int):
+    """Ids of every keyword that is a prefix of keyword r (equal strings
+    included), ordered by length, then id -- from the definition."""
+    p = pats[r]
+    return sorted((len(q), i) for i, q in enumerate(pats) if p[:len(q)] == q)
+
+
+@pytest.mark.parametrize("alpha", [b"ACGT", b"abcdefghijkl", bytes(range(256))])
+def test_full_records_match_definition(lib, alpha):
+    """The builder's full-output records: for the lowest id of each keyword
+    string, its proper-prefix link, length, equal keywords and chain length,
+    checked against brute force over the keyword list."""
+    g = np.random.Generator(np.random.PCG64(7 + len(alpha)))
+    for case in range(4):
+        pats = _nested_keywords(g, alpha, 120, 12)
+        h = api.ac_compile(pats, host_only=True)
+        try:
+            rec, dups, max_chain = api.ac_export_full(h, len(pats))
+        finally:
+            api.ac_destroy(h)
+        lowest = {}
+        for i, p in enumerate(pats):
+            lowest.setdefault(p, i)
+        clens = []
+        for p, r in lowest.items():
+            chain = full_chain_brute(pats, r)
+            up_cands = [q for q in lowest if len(q) < len(p) and p[:len(q)] == q]
+            up = lowest[max(up_cands, key=len)] if up_cands else 0xFFFFFFFF
+            equal = sorted(i for i, q in enumerate(pats) if q == p)
+            assert rec[r, 0] == up and rec[r, 1] == len(p) and rec[r, 3] == len(chain), (case, p)
+            assert dups[rec[r, 2]:rec[r, 2] + len(equal)].tolist() == equal, (case, p)
+            # following the links reproduces the whole chain, shortest first
+            got, x = [], r
+            while x != 0xFFFFFFFF:
+                below = rec[rec[x, 0], 3] if rec[x, 0] != 0xFFFFFFFF else 0
+                got = [(int(rec[x, 1]), int(i)) for i in dups[rec[x, 2]:rec[x, 2] + rec[x, 3] - below]] + got
+                x = rec[x, 0]
+            assert got == chain, (case, p)
+            clens.append(len(chain))
+        for i, p in enumerate(pats):
+            if lowest[p] != i:
+                assert not rec[i].any()
+        assert max_chain == max(clens)
+
+
+def test_full_expansion_equals_serial_machine(lib):
+    """Each per-start longest result expanded through the records gives exactly
+    the serial machine's occurrences (section II's output function), in the
+    order start, end, id."""
+    g = np.random.Generator(np.random.PCG64(31))
+    for alpha in (b"ACGT", b"abcdef"):
+        a = np.frombuffer(alpha, dtype=np.uint8)
+        for case in range(3):
+            pats = _nested_keywords(g, alpha, 80, 10)
+            text = a[g.integers(0, a.size, size=4000)]
+            for _ in range(30):  # plant the long stems
+                p = pats[int(g.integers(0, len(pats)))]
+                o = int(g.integers(0, text.size - len(p)))
+                text[o:o + len(p)] = np.frombuffer(p, dtype=np.uint8)
+            h = api.ac_compile(pats, host_only=True)
+            try:
+                rec, dups, _ = api.ac_export_full(h, len(pats))
+            finally:
+                api.ac_destroy(h)
+            ids = oracle.pfac_ids(pats, text)
+            got = []
+            for i in np.nonzero(ids >= 0)[0]:
+                x, chain = int(ids[i]), []
+                while x != 0xFFFFFFFF:
+                    below = rec[rec[x, 0], 3] if rec[x, 0] != 0xFFFFFFFF else 0
+                    chain = [(int(i) + int(rec[x, 1]) - 1, int(d)) for d in dups[rec[x, 2]:rec[x, 2] + rec[x, 3] - below]] + chain
+                    x = int(rec[x, 0])
+                got += chain
+            ends, fids = oracle.full_occurrences(pats, text)
+            want = sorted(((int(e) - len(pats[d]) + 1, int(e), int(d)) for e, d in zip(ends, fids)))
+            assert got == [(e, d) for _, e, d in want], (alpha, case)
