@@ -7,11 +7,13 @@
 //   compact_prefix   the exclusive prefix of counts at every unit (each CTA
 //                    adds the partial sums before its range to a block scan of
 //                    its own range);
-//   compact_gather   one warp per unit: the unit's matches in ascending
-//                    position at the unit's place in its text's list, and the
-//                    text's total from its last unit.  A unit with more than
-//                    kSlotCap matches (a dense run of matches) is matched again
-//                    here, one plain walk per position, in position order.
+//   compact_gather   one warp per unit with matches (grid stride; 32 units'
+//                    counts read per warp round, the empty ones skipped): the unit's matches in
+//                    ascending position at the unit's place in its text's
+//                    list; then every text's total.  A unit with more than
+//                    kSlotCap matches (a dense run of matches) is read from the
+//                    dense ids the matching kernel kept for it, or, without
+//                    them, matched again here, one plain walk per position.
 // No step waits on another CTA, so no step can stall on a CTA that is not
 // resident; each runs at the speed of its memory traffic (4 + 8 bytes per unit
 // for the scan, 8 bytes per match for the gather).
@@ -149,6 +151,63 @@ __device__ int walk_from_root(const GatherParams &p, const uint8_t *text, uint64
     return -1;
 }
 
+// One warp: unit u's matches in ascending position at the unit's place in its
+// text's list.
+template <typename GT>
+__device__ __forceinline__ void gather_unit(const GatherParams &p, const Work &wk, uint32_t T, uint32_t u, int lane) {
+    const uint8_t *text = p.g.text;
+    uint64_t n = p.g.n;
+    uint32_t first = 0;
+    CompactOut out = p.g.out;
+    if (wk.list) {
+        const uint32_t item = find_item(wk, u, lane);
+        const BatchItemDev it = wk.list[item];
+        text = p.g.text + it.text_off;
+        n = it.len;
+        first = it.first_unit;
+        out = p.g.outs[it.item];
+    }
+    const uint32_t head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text) & 15u);
+    const uint32_t lu = u - first;  // the unit's tile within its text
+    const int64_t gpb = static_cast<int64_t>(lu) * T - head;
+    const uint64_t su = static_cast<uint64_t>(p.g.ubase) + u;
+    const unsigned long long base = __ldg(p.g.prefix + p.g.ubase + first);
+    const unsigned long long at = __ldg(p.g.prefix + su);
+    const uint32_t c = __ldg(p.g.counts + su);
+    unsigned long long o = at - base;
+    if (c <= kSlotCap) {
+        const unsigned long long e =
+            static_cast<uint32_t>(lane) < c ? __ldg(p.g.slots + su * kSlotCap + lane) : ~0ull;
+        const uint32_t mine = static_cast<uint32_t>(e);
+        uint32_t rank = 0;
+#pragma unroll 8
+        for (int d = 0; d < 32; ++d) {
+            const uint32_t other = __shfl_sync(0xffffffffu, mine, d);
+            rank += (static_cast<uint32_t>(d) < c && other < mine) ? 1u : 0u;
+        }
+        if (static_cast<uint32_t>(lane) < c && o + rank < out.cap) {
+            out.pos[o + rank] = mine;
+            out.ids[o + rank] = static_cast<uint32_t>(e >> 32);
+        }
+    } else {
+        // more matches than slots: the unit's dense ids if kept, else match it again
+        const int32_t *dn = p.g.dense ? p.g.dense + su * kDenseStride : nullptr;
+        for (uint32_t i0 = 0; i0 < T; i0 += 32) {
+            const int64_t gp = gpb + static_cast<int64_t>(i0) + lane;
+            int id = -1;
+            if (gp >= 0 && static_cast<uint64_t>(gp) < n)
+                id = dn ? __ldg(dn + i0 + lane) : walk_from_root<GT>(p, text, n, gp);
+            const unsigned m = __ballot_sync(0xffffffffu, id >= 0);
+            const uint32_t r = __popc(m & ((1u << lane) - 1u));
+            if (id >= 0 && o + r < out.cap) {
+                out.pos[o + r] = static_cast<uint32_t>(gp);
+                out.ids[o + r] = static_cast<uint32_t>(id);
+            }
+            o += __popc(m);
+        }
+    }
+}
+
 template <typename GT>
 __global__ void __launch_bounds__(kGatherThreads) compact_gather(const GatherParams p) {
     const int lane = threadIdx.x & 31;
@@ -156,60 +215,30 @@ __global__ void __launch_bounds__(kGatherThreads) compact_gather(const GatherPar
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const Work wk = load_work(p.g.batch, p.g.lists, p.g.units);
     const uint32_t T = p.g.tile;
-    for (uint32_t u = gw; u < wk.units; u += nwarps) {
-        const uint8_t *text = p.g.text;
-        uint64_t n = p.g.n;
-        uint32_t first = 0;
-        CompactOut out = p.g.out;
-        if (wk.list) {
-            const uint32_t item = find_item(wk, u, lane);
-            const BatchItemDev it = wk.list[item];
-            text = p.g.text + it.text_off;
-            n = it.len;
-            first = it.first_unit;
-            out = p.g.outs[it.item];
+    // Units gw, gw + nwarps, ... (grid stride), 32 of them per round with one
+    // count load per lane: only units with matches are visited (most have
+    // none), and every warp keeps its share of the units.
+    for (uint64_t u0 = gw; u0 < wk.units; u0 += 32ull * nwarps) {
+        const uint64_t uu = u0 + static_cast<uint64_t>(lane) * nwarps;
+        const uint32_t cu = uu < wk.units ? __ldg(p.g.counts + p.g.ubase + uu) : 0u;
+        for (uint32_t todo = __ballot_sync(0xffffffffu, cu != 0); todo; todo &= todo - 1)
+            gather_unit<GT>(p, wk, T, static_cast<uint32_t>(u0 + static_cast<uint64_t>(__ffs(todo) - 1) * nwarps), lane);
+    }
+    // each text's total: its last unit's prefix and count, less its first's prefix
+    if (!wk.list) {
+        if (gw == 0 && lane == 0 && wk.units > 0) {
+            const uint64_t last = static_cast<uint64_t>(p.g.ubase) + wk.units - 1;
+            *p.g.out.count = __ldg(p.g.prefix + last) + __ldg(p.g.counts + last) - __ldg(p.g.prefix + p.g.ubase);
         }
-        const uint32_t head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text) & 15u);
-        const uint32_t lu = u - first;  // the unit's tile within its text
-        const int64_t gpb = static_cast<int64_t>(lu) * T - head;
-        const uint64_t su = static_cast<uint64_t>(p.g.ubase) + u;
-        const unsigned long long base = __ldg(p.g.prefix + p.g.ubase + first);
-        const unsigned long long at = __ldg(p.g.prefix + su);
-        const uint32_t c = __ldg(p.g.counts + su);
-        unsigned long long o = at - base;
-        if (c <= kSlotCap) {
-            const unsigned long long e =
-                static_cast<uint32_t>(lane) < c ? __ldg(p.g.slots + su * kSlotCap + lane) : ~0ull;
-            const uint32_t mine = static_cast<uint32_t>(e);
-            uint32_t rank = 0;
-#pragma unroll 8
-            for (int d = 0; d < 32; ++d) {
-                const uint32_t other = __shfl_sync(0xffffffffu, mine, d);
-                rank += (static_cast<uint32_t>(d) < c && other < mine) ? 1u : 0u;
-            }
-            if (static_cast<uint32_t>(lane) < c && o + rank < out.cap) {
-                out.pos[o + rank] = mine;
-                out.ids[o + rank] = static_cast<uint32_t>(e >> 32);
-            }
-        } else {
-            // more matches than slots: the unit's dense ids if kept, else match it again
-            const int32_t *dn = p.g.dense ? p.g.dense + su * kDenseStride : nullptr;
-            for (uint32_t i0 = 0; i0 < T; i0 += 32) {
-                const int64_t gp = gpb + static_cast<int64_t>(i0) + lane;
-                int id = -1;
-                if (gp >= 0 && static_cast<uint64_t>(gp) < n)
-                    id = dn ? __ldg(dn + i0 + lane) : walk_from_root<GT>(p, text, n, gp);
-                const unsigned m = __ballot_sync(0xffffffffu, id >= 0);
-                const uint32_t r = __popc(m & ((1u << lane) - 1u));
-                if (id >= 0 && o + r < out.cap) {
-                    out.pos[o + r] = static_cast<uint32_t>(gp);
-                    out.ids[o + r] = static_cast<uint32_t>(id);
-                }
-                o += __popc(m);
-            }
-        }
-        const uint64_t text_units = (n + head + T - 1) / T;
-        if (lane == 0 && lu + 1 == text_units) *out.count = at + c - base;
+        return;
+    }
+    for (uint32_t i = gw * 32u + static_cast<uint32_t>(lane); i < wk.nlist; i += nwarps * 32u) {
+        const BatchItemDev it = wk.list[i];
+        const uint32_t head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(p.g.text + it.text_off) & 15u);
+        const uint64_t text_units = (it.len + head + T - 1) / T;
+        const uint64_t first = static_cast<uint64_t>(p.g.ubase) + it.first_unit;
+        const uint64_t last = first + text_units - 1;
+        *p.g.outs[it.item].count = __ldg(p.g.prefix + last) + __ldg(p.g.counts + last) - __ldg(p.g.prefix + first);
     }
 }
 

@@ -65,21 +65,31 @@ __global__ void __launch_bounds__(kFullThreads) full_count(const FullParams p) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t u = gw; u < p.units; u += nwarps) {
-        const uint32_t c = __ldg(p.counts + u);
-        uint32_t sum = 0;
-        if (c <= kSlotCap) {
-            if (static_cast<uint32_t>(lane) < c)
-                sum = chain_len(p, static_cast<uint32_t>(__ldg(p.slots + static_cast<uint64_t>(u) * kSlotCap + lane) >> 32));
-        } else {
-            const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
-            for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
-                const int id = dense_id(p, u, gpb, i0 + lane);
-                if (id >= 0) sum += chain_len(p, static_cast<uint32_t>(id));
+    // units gw, gw + nwarps, ... (grid stride), 32 per round: the empty ones
+    // get 0 from their lane, the others are summed by the whole warp
+    for (uint64_t u0 = gw; u0 < p.units; u0 += 32ull * nwarps) {
+        const uint64_t uu = u0 + static_cast<uint64_t>(lane) * nwarps;
+        const uint32_t cu = uu < p.units ? __ldg(p.counts + uu) : 0u;
+        if (uu < p.units && cu == 0) p.fcounts[uu] = 0;
+        for (uint32_t todo = __ballot_sync(kFull, cu != 0); todo; todo &= todo - 1) {
+            const uint32_t b = static_cast<uint32_t>(__ffs(todo) - 1);
+            const uint32_t u = static_cast<uint32_t>(u0 + static_cast<uint64_t>(b) * nwarps);
+            const uint32_t c = __shfl_sync(kFull, cu, static_cast<int>(b));
+            uint32_t sum = 0;
+            if (c <= kSlotCap) {
+                if (static_cast<uint32_t>(lane) < c)
+                    sum = chain_len(p, static_cast<uint32_t>(
+                                           __ldg(p.slots + static_cast<uint64_t>(u) * kSlotCap + lane) >> 32));
+            } else {
+                const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
+                for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
+                    const int id = dense_id(p, u, gpb, i0 + lane);
+                    if (id >= 0) sum += chain_len(p, static_cast<uint32_t>(id));
+                }
             }
+            sum = __reduce_add_sync(kFull, sum);
+            if (lane == 0) p.fcounts[u] = sum;
         }
-        sum = __reduce_add_sync(kFull, sum);
-        if (lane == 0) p.fcounts[u] = sum;
     }
 }
 
@@ -109,41 +119,51 @@ __global__ void __launch_bounds__(kFullThreads) full_gather(const FullParams p) 
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t u = gw; u < p.units; u += nwarps) {
-        const uint32_t c = __ldg(p.counts + u);
-        unsigned long long o = __ldg(p.fprefix + u);
-        if (c <= kSlotCap) {
-            // the slots in any order: a result's place is the chain lengths of
-            // the results at smaller positions
-            const unsigned long long e =
-                static_cast<uint32_t>(lane) < c ? __ldg(p.slots + static_cast<uint64_t>(u) * kSlotCap + lane) : ~0ull;
-            const uint32_t pos = static_cast<uint32_t>(e), id = static_cast<uint32_t>(e >> 32);
-            const uint32_t cl = static_cast<uint32_t>(lane) < c ? chain_len(p, id) : 0u;
-            unsigned long long off = 0;
+    // units gw, gw + nwarps, ... (grid stride), 32 per round, only those with
+    // results visited
+    for (uint64_t u0 = gw; u0 < p.units; u0 += 32ull * nwarps) {
+        const uint64_t uu = u0 + static_cast<uint64_t>(lane) * nwarps;
+        const uint32_t cu = uu < p.units ? __ldg(p.counts + uu) : 0u;
+        for (uint32_t todo = __ballot_sync(kFull, cu != 0); todo; todo &= todo - 1) {
+            const uint32_t b = static_cast<uint32_t>(__ffs(todo) - 1);
+            const uint32_t u = static_cast<uint32_t>(u0 + static_cast<uint64_t>(b) * nwarps);
+            const uint32_t c = __shfl_sync(kFull, cu, static_cast<int>(b));
+            unsigned long long o = __ldg(p.fprefix + u);
+            if (c <= kSlotCap) {
+                // the slots in any order: a result's place is the chain lengths
+                // of the results at smaller positions
+                const unsigned long long e = static_cast<uint32_t>(lane) < c
+                                                 ? __ldg(p.slots + static_cast<uint64_t>(u) * kSlotCap + lane)
+                                                 : ~0ull;
+                const uint32_t pos = static_cast<uint32_t>(e), id = static_cast<uint32_t>(e >> 32);
+                const uint32_t cl = static_cast<uint32_t>(lane) < c ? chain_len(p, id) : 0u;
+                unsigned long long off = 0;
 #pragma unroll 8
-            for (int d = 0; d < 32; ++d) {
-                const uint32_t op = __shfl_sync(kFull, pos, d), oc = __shfl_sync(kFull, cl, d);
-                off += op < pos ? oc : 0u;
-            }
-            if (static_cast<uint32_t>(lane) < c) put_chain(p, o + off, pos, id);
-        } else {
-            const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
-            for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
-                const int id = dense_id(p, u, gpb, i0 + lane);
-                const uint32_t cl = id >= 0 ? chain_len(p, static_cast<uint32_t>(id)) : 0u;
-                uint32_t inc = cl;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_up_sync(kFull, inc, d);
-                    if (lane >= d) inc += y;
+                for (int d = 0; d < 32; ++d) {
+                    const uint32_t op = __shfl_sync(kFull, pos, d), oc = __shfl_sync(kFull, cl, d);
+                    off += op < pos ? oc : 0u;
                 }
-                if (id >= 0)
-                    put_chain(p, o + (inc - cl), static_cast<uint32_t>(gpb + i0 + lane), static_cast<uint32_t>(id));
-                o += __shfl_sync(kFull, inc, 31);
+                if (static_cast<uint32_t>(lane) < c) put_chain(p, o + off, pos, id);
+            } else {
+                const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
+                for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
+                    const int id = dense_id(p, u, gpb, i0 + lane);
+                    const uint32_t cl = id >= 0 ? chain_len(p, static_cast<uint32_t>(id)) : 0u;
+                    uint32_t inc = cl;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                        if (lane >= d) inc += y;
+                    }
+                    if (id >= 0)
+                        put_chain(p, o + (inc - cl), static_cast<uint32_t>(gpb + i0 + lane),
+                                  static_cast<uint32_t>(id));
+                    o += __shfl_sync(kFull, inc, 31);
+                }
             }
         }
-        if (lane == 0 && u + 1 == p.units) *p.out.count = __ldg(p.fprefix + u) + __ldg(p.fcounts + u);
     }
+    if (gw == 0 && lane == 0) *p.out.count = __ldg(p.fprefix + p.units - 1) + __ldg(p.fcounts + p.units - 1);
 }
 
 inline size_t round16(size_t v) { return (v + 15u) & ~static_cast<size_t>(15u); }
