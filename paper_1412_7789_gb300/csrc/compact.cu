@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kScanThreads = 512;
 constexpr int kGatherThreads = 256;
+constexpr uint32_t kRows = 8;  // rows of 32 dense ids loaded together
 
 // Block-wide sum; every thread gets the total.
 __device__ __forceinline__ unsigned long long block_sum(unsigned long long v) {
@@ -190,20 +191,28 @@ __device__ __forceinline__ void gather_unit(const GatherParams &p, const Work &w
             out.ids[o + rank] = static_cast<uint32_t>(e >> 32);
         }
     } else {
-        // more matches than slots: the unit's dense ids if kept, else match it again
+        // more matches than slots: the unit's dense ids if kept (eight rows of
+        // 32 loaded at a time, so their loads overlap), else match it again
         const int32_t *dn = p.g.dense ? p.g.dense + su * kDenseStride : nullptr;
-        for (uint32_t i0 = 0; i0 < T; i0 += 32) {
-            const int64_t gp = gpb + static_cast<int64_t>(i0) + lane;
-            int id = -1;
-            if (gp >= 0 && static_cast<uint64_t>(gp) < n)
-                id = dn ? __ldg(dn + i0 + lane) : walk_from_root<GT>(p, text, n, gp);
-            const unsigned m = __ballot_sync(0xffffffffu, id >= 0);
-            const uint32_t r = __popc(m & ((1u << lane) - 1u));
-            if (id >= 0 && o + r < out.cap) {
-                out.pos[o + r] = static_cast<uint32_t>(gp);
-                out.ids[o + r] = static_cast<uint32_t>(id);
+        for (uint32_t i0 = 0; i0 < T; i0 += 32 * kRows) {
+            int id[kRows];
+#pragma unroll
+            for (uint32_t j = 0; j < kRows; ++j) {
+                const int64_t gp = gpb + static_cast<int64_t>(i0 + 32 * j) + lane;
+                id[j] = -1;
+                if (i0 + 32 * j < T && gp >= 0 && static_cast<uint64_t>(gp) < n)
+                    id[j] = dn ? __ldg(dn + i0 + 32 * j + lane) : walk_from_root<GT>(p, text, n, gp);
             }
-            o += __popc(m);
+#pragma unroll
+            for (uint32_t j = 0; j < kRows; ++j) {
+                const unsigned m = __ballot_sync(0xffffffffu, id[j] >= 0);
+                const uint32_t r = __popc(m & ((1u << lane) - 1u));
+                if (id[j] >= 0 && o + r < out.cap) {
+                    out.pos[o + r] = static_cast<uint32_t>(gpb + static_cast<int64_t>(i0 + 32 * j) + lane);
+                    out.ids[o + r] = static_cast<uint32_t>(id[j]);
+                }
+                o += __popc(m);
+            }
         }
     }
 }

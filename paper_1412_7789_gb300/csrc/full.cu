@@ -28,6 +28,7 @@ namespace pfac {
 namespace {
 
 constexpr int kFullThreads = 256;
+constexpr uint32_t kRows = 8;  // rows of 32 dense ids loaded together
 constexpr unsigned kFull = 0xffffffffu;
 
 struct FullParams {
@@ -81,10 +82,16 @@ __global__ void __launch_bounds__(kFullThreads) full_count(const FullParams p) {
                     sum = chain_len(p, static_cast<uint32_t>(
                                            __ldg(p.slots + static_cast<uint64_t>(u) * kSlotCap + lane) >> 32));
             } else {
+                // eight rows of 32 dense ids at a time, so their loads overlap
                 const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
-                for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
-                    const int id = dense_id(p, u, gpb, i0 + lane);
-                    if (id >= 0) sum += chain_len(p, static_cast<uint32_t>(id));
+                for (uint32_t i0 = 0; i0 < p.tile; i0 += 32 * kRows) {
+                    int id[kRows];
+#pragma unroll
+                    for (uint32_t j = 0; j < kRows; ++j)
+                        id[j] = i0 + 32 * j < p.tile ? dense_id(p, u, gpb, i0 + 32 * j + lane) : -1;
+#pragma unroll
+                    for (uint32_t j = 0; j < kRows; ++j)
+                        if (id[j] >= 0) sum += chain_len(p, static_cast<uint32_t>(id[j]));
                 }
             }
             sum = __reduce_add_sync(kFull, sum);
@@ -145,20 +152,31 @@ __global__ void __launch_bounds__(kFullThreads) full_gather(const FullParams p) 
                 }
                 if (static_cast<uint32_t>(lane) < c) put_chain(p, o + off, pos, id);
             } else {
+                // eight rows of 32 at a time: their id and chain-length loads
+                // overlap, then each row is scanned and written
                 const int64_t gpb = static_cast<int64_t>(u) * p.tile - p.head;
-                for (uint32_t i0 = 0; i0 < p.tile; i0 += 32) {
-                    const int id = dense_id(p, u, gpb, i0 + lane);
-                    const uint32_t cl = id >= 0 ? chain_len(p, static_cast<uint32_t>(id)) : 0u;
-                    uint32_t inc = cl;
+                for (uint32_t i0 = 0; i0 < p.tile; i0 += 32 * kRows) {
+                    int id[kRows];
+                    uint32_t cl[kRows];
 #pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t y = __shfl_up_sync(kFull, inc, d);
-                        if (lane >= d) inc += y;
+                    for (uint32_t j = 0; j < kRows; ++j)
+                        id[j] = i0 + 32 * j < p.tile ? dense_id(p, u, gpb, i0 + 32 * j + lane) : -1;
+#pragma unroll
+                    for (uint32_t j = 0; j < kRows; ++j)
+                        cl[j] = id[j] >= 0 ? chain_len(p, static_cast<uint32_t>(id[j])) : 0u;
+#pragma unroll
+                    for (uint32_t j = 0; j < kRows; ++j) {
+                        uint32_t inc = cl[j];
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const uint32_t y = __shfl_up_sync(kFull, inc, d);
+                            if (lane >= d) inc += y;
+                        }
+                        if (id[j] >= 0)
+                            put_chain(p, o + (inc - cl[j]), static_cast<uint32_t>(gpb + i0 + 32 * j + lane),
+                                      static_cast<uint32_t>(id[j]));
+                        o += __shfl_sync(kFull, inc, 31);
                     }
-                    if (id >= 0)
-                        put_chain(p, o + (inc - cl), static_cast<uint32_t>(gpb + i0 + lane),
-                                  static_cast<uint32_t>(id));
-                    o += __shfl_sync(kFull, inc, 31);
                 }
             }
         }

@@ -227,7 +227,7 @@ __device__ __forceinline__ uint32_t find_item(const Work &wk, uint32_t u, int la
 // warp's share of it, at most kClaimMax and at least 1.  Early claims are
 // large, so the counter sees few atomics; the last units still go out one at
 // a time, so a warp held up by an expensive unit leaves the rest to others.
-constexpr uint32_t kClaimMax = 32;
+constexpr uint32_t kClaimMax = 8;
 
 struct UnitClaims {
     uint64_t first;  // the static unit (~0: taken)
