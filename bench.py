@@ -174,6 +174,54 @@ def cpu_baseline(text: np.ndarray, pats, budget_s: float = 12.0, full: bool = Fa
             "seconds": dt, "walk_steps_per_position": steps / max(wprobe, 1), "longest_walk": longest}
 
 
+# the same oracle on every host core (context: the paper notes that a parallel
+# CPU matcher would move the crossover): each process takes one contiguous
+# stretch of a sample plus a halo of max_len - 1 bytes, so no start position's
+# walk is cut; processes are spawned (never forked after CUDA is up)
+_PAR = {}
+
+
+def _par_init(pats, shm_name, size):
+    from multiprocessing import shared_memory
+
+    import oracle
+
+    _PAR["m"] = oracle.Machine(pats)
+    _PAR["shm"] = shared_memory.SharedMemory(name=shm_name)
+    _PAR["text"] = np.ndarray((size,), dtype=np.uint8, buffer=_PAR["shm"].buf)
+
+
+def _par_scan(rng):
+    a, b, halo = rng
+    ids = _PAR["m"].pfac_ids(_PAR["text"][a:min(b + halo, _PAR["text"].size)])
+    return int(np.count_nonzero(ids[:b - a] >= 0))
+
+
+def cpu_parallel(text: np.ndarray, pats, single_gbs: float, budget_s: float = 6.0, cores: int = 0):
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    cores = cores or (os.cpu_count() or 1)
+    halo = max(len(p) for p in pats) - 1
+    size = int(min(text.size, max(1 << 20, single_gbs * 1e9 * budget_s * cores)))
+    shm = shared_memory.SharedMemory(create=True, size=size)
+    try:
+        np.ndarray((size,), dtype=np.uint8, buffer=shm.buf)[:] = text[:size]
+        step = (size + cores - 1) // cores
+        ranges = [(a, min(a + step, size), halo) for a in range(0, size, step)]
+        with mp.get_context("spawn").Pool(cores, initializer=_par_init, initargs=(pats, shm.name, size)) as pool:
+            pool.map(_par_scan, [(0, 1, 0)] * (4 * cores))  # every worker has built its machine
+            t0 = time.perf_counter()
+            matches = sum(pool.map(_par_scan, ranges, chunksize=1))
+            dt = time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
+    return {"value": size / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle, all host cores",
+            "sample": "first %d B of the same text in %d contiguous stretches (plus a %d-byte halo each), one "
+                      "process per core" % (size, len(ranges), halo), "seconds": dt, "matches": matches}
+
+
 # ----------------------------------------------------------------------------
 # the reference arm: the oracle, timed on the host cores
 # ----------------------------------------------------------------------------
@@ -376,6 +424,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(text_np, pats, args.cpu_seconds, full=out_kind == "full")
         extra["lookups_per_s"] = cpu["walk_steps_per_position"] * n * args.steps / (t_ms * 1e-3)
+        if out_kind != "full" and not args.no_cpu_parallel:
+            extra["cpu_all_cores"] = cpu_parallel(text_np, pats, cpu["value"], args.cpu_seconds / 2)
 
     if rank == 0:
         line = {
@@ -964,6 +1014,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-chains", action="store_true", help="compile without chain records")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cpu-parallel", action="store_true", help="skip the all-cores oracle context figure")
     ap.add_argument("--compare-simple", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--traffic", type=float, default=None,

@@ -186,7 +186,8 @@ ac_status ac_export_full(ac_handle h, uint32_t *records, uint32_t *dups, uint32_
  * d_text[i] (within the n bytes), or -1.  d_text: n bytes, d_out_ids: n int32,
  * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is
  * a no-op.  Takes 16 bytes of scratch (the tile counter) per call from the
- * library's stream-ordered pool.
+ * library's stream-ordered pool, except for a text short enough that each of
+ * its tiles is some warp's first (no counter, no allocation).
  */
 ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_out_ids, void *stream);
 
@@ -239,9 +240,10 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
 /*
  * Compacted matching that allocates no device memory.  Same arguments, results
  * and asynchrony as ac_match_compact; the difference is where its scratch
- * lives.  ac_match_compact takes its scratch (a tile counter and one look-back
- * word per chunk of tiles) from a stream-ordered pool (cudaMallocFromPoolAsync)
- * on every call.  Some callers cannot allocate while they match: a serving process
+ * lives.  ac_match_compact takes its scratch (a tile counter, per-tile counts,
+ * prefix sums and match slots, and a dense fallback) from a stream-ordered pool
+ * (cudaMallocFromPoolAsync) on every call; this one keeps no dense fallback and
+ * matches a tile with more than 32 matches again in its gather step.  Some callers cannot allocate while they match: a serving process
  * that hands all free device memory to another framework's caching allocator
  * at start-up (later cudaMalloc / cudaMallocAsync calls then fail or take
  * memory that allocator counts on), or a latency-critical loop whose rules

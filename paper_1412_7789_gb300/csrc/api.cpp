@@ -137,7 +137,18 @@ using pfac::scratch_pool;
 
 // A tiled launch (dense ids or count) with its zeroed scratch (the tile
 // counter) in stream-ordered memory, so calls on different streams never share it.
+// A text short enough that every tile is some warp's first needs no counter:
+// the launchers accept no scratch then, which saves the allocation and the
+// clearing of small calls.
 cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode, cudaStream_t st) {
+    if (!r.batch && r.n <= (16u << 20)) {
+        pfac::MatchRequest r0 = r;
+        r0.scratch = nullptr;
+        r0.scratch_bytes = 0;
+        const cudaError_t e0 = h->dev.filter ? pfac::launch_filter(h->dev, r0, mode, h->tuning, st)
+                                             : pfac::launch_tiled(h->dev, r0, mode, h->tuning, st);
+        if (e0 == cudaSuccess) return e0;  // else: a counter is needed (or a real error, reported below)
+    }
     const size_t bytes = 16;
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);

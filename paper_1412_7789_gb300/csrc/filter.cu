@@ -976,8 +976,8 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;
-    if (!r.scratch || r.scratch_bytes < 16) return cudaErrorInvalidValue;
-    p.counter = static_cast<unsigned int *>(r.scratch);
+    // the tile counter; none is needed when every tile is some warp's first
+    p.counter = r.scratch && r.scratch_bytes >= 16 ? static_cast<unsigned int *>(r.scratch) : nullptr;
     e = device_error_word(&p.err);
     if (e != cudaSuccess) return e;
     uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(sms);
@@ -985,6 +985,8 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
         const uint32_t need_ctas = (p.ntiles + nw - 1) / nw;
         if (grid > need_ctas) grid = need_ctas;
     }
+    if (!p.counter && (batch || static_cast<uint64_t>(p.ntiles) > static_cast<uint64_t>(grid) * nw))
+        return cudaErrorInvalidValue;
     if (grid == 0) return cudaSuccess;
     if (t.B == 2) {
         if (t.gbits == 16) return launch_modes<2, int16_t>(mode, p, grid, tu.block, smem, max_smem, stream);

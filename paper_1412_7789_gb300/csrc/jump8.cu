@@ -397,7 +397,8 @@ __global__ void __launch_bounds__(kBlockG, kCtasG) pfac_jump8g(const JumpParams 
     for (uint32_t it = 0;; ++it) {
         uint32_t claim = 0xFFFFFFFFu;
         if (lane == 0) {
-            const uint64_t c = it == 0 ? gw : GW + atomicAdd(p.counter, 1u);
+            // no claims beyond the warps' first: the counter is not touched
+            const uint64_t c = it == 0 ? gw : (GW >= claims || !p.counter ? claims : GW + atomicAdd(p.counter, 1u));
             if (c < claims) claim = static_cast<uint32_t>(c);
         }
         claim = __shfl_sync(kFull, claim, 0);
@@ -507,8 +508,8 @@ cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;
-    if (!r.scratch || r.scratch_bytes < 16) return cudaErrorInvalidValue;
-    p.counter = static_cast<unsigned int *>(r.scratch);
+    // the claim counter; none is needed when every claim is some warp's first
+    p.counter = r.scratch && r.scratch_bytes >= 16 ? static_cast<unsigned int *>(r.scratch) : nullptr;
     e = device_error_word(&p.err);
     if (e != cudaSuccess) return e;
     p.off_stage = (kOffJ + t.jbytes + 127u) & ~127u;
@@ -522,11 +523,14 @@ cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode
     p.sms = static_cast<uint32_t>(sms);
     uint32_t grid = static_cast<uint32_t>(sms);
     if (global) grid = static_cast<uint32_t>(sms) * static_cast<uint32_t>(kCtasG);
-    if (!batch) {
+    {
         const uint32_t per = global ? kBlockG / 32u : static_cast<uint32_t>(kWarps);
         const uint64_t work = global ? static_cast<uint64_t>(p.ntiles) * (kHalf / 32) / p.rows : p.ntiles;
-        const uint64_t need = (work + per - 1) / per;
-        if (grid > need) grid = static_cast<uint32_t>(need);
+        if (!batch) {
+            const uint64_t need = (work + per - 1) / per;
+            if (grid > need) grid = static_cast<uint32_t>(need);
+        }
+        if (!p.counter && (batch || work > static_cast<uint64_t>(grid) * per)) return cudaErrorInvalidValue;
     }
     if (grid == 0) return cudaSuccess;
     const bool inv = t.C < 256;

@@ -749,13 +749,15 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;
-    if (!r.scratch || r.scratch_bytes < 16) return cudaErrorInvalidValue;
-    p.counter = static_cast<unsigned int *>(r.scratch);
+    // the tile counter; none is needed when every tile is some warp's first
+    p.counter = r.scratch && r.scratch_bytes >= 16 ? static_cast<unsigned int *>(r.scratch) : nullptr;
     uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(dp.sms);
     if (!batch) {  // a batch's units are counted on the device: every CTA starts
         const uint32_t need = (p.ntiles + nw - 1) / nw;
         if (grid > need) grid = need;
     }
+    if (!p.counter && (batch || static_cast<uint64_t>(p.ntiles) > static_cast<uint64_t>(grid) * nw))
+        return cudaErrorInvalidValue;
     if (grid == 0) return cudaSuccess;
     const uint32_t block = static_cast<uint32_t>(tu.block);
     const bool inv = t.C < 256;

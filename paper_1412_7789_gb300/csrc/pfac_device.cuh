@@ -256,7 +256,7 @@ __device__ __forceinline__ uint64_t claims_next(UnitClaims &c, unsigned int *cou
         return u;
     }
     if (c.left == 0) {
-        if (units <= c.skip) return ~0ull;
+        if (units <= c.skip || !counter) return ~0ull;  // no counter: the launcher saw units <= skip
         const uint32_t dyn = static_cast<uint32_t>(units) - c.skip;  // units the counter hands out
         if (c.seen >= dyn) return ~0ull;
         uint32_t blk = (dyn - c.seen) / (4u * c.skip);

@@ -258,3 +258,33 @@ def test_dense_matches_compact(alpha, kernel):
         assert int(cnt.item()) == wpos.size
         assert np.array_equal(pos.cpu().numpy().astype(np.uint32), wpos)
         assert np.array_equal(ids.cpu().numpy().astype(np.uint32), wid)
+
+
+@pytest.mark.parametrize("alpha,kernel", [(b"ACGT", "tiled"), (b"abcdefghijklmnopqrstuvwxyz", "tiled"),
+                                          (b"abcdefghijklmnopqrstuvwxyz", "thread_jump"),
+                                          (b"abcdefghijklmnopqrstuvwxyz", "walk_slots")])
+def test_counter_free_boundary(alpha, kernel):
+    """Dense ids and counts of texts just below and above the largest text
+    whose tiles (or rows) all go to the warps' first claims -- launched
+    without a tile counter -- and of two calls in a row on the same handle."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    g = np.random.Generator(np.random.PCG64(len(alpha) + len(kernel)))
+    a = np.frombuffer(alpha, dtype=np.uint8)
+    base = a[g.integers(0, a.size, size=1 << 22)]
+    pats = [bytes(base[o:o + int(L)]) for o, L in zip(g.integers(0, 1 << 20, size=300), g.integers(3, 20, size=300))]
+    if alpha == b"ACGT":
+        edge = sms * 16 * 992  # filter kernel: 16 warps per CTA, 992 positions per tile
+    elif kernel == "tiled":
+        edge = sms * 4 * 1024  # full-occupancy 8-bit kernel: 64-position rows, 8 warps x 8 CTAs per SM
+    elif kernel == "thread_jump":
+        edge = sms * 32 * 1024  # one CTA of 32 warps per SM, 1024-position tiles
+    else:
+        edge = sms * 16 * 1024
+    with compile_(pats) as h:
+        h.set_kernel(kernel)
+        for n in (edge - 4096, edge - 1, edge, edge + 1, edge + 4096):
+            text = base[:n]
+            want = oracle.pfac_ids(pats, text)
+            _gpu.check_all_modes(h.handle, text, want, modes=("dense", "count"))
