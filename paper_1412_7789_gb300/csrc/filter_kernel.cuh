@@ -1,0 +1,1101 @@
+// Failureless Aho-Corasick matching for small alphabets (keyword bytes mapped
+// to 2- or 4-bit codes), sm_103a.
+//
+// pfac_filter_pipe -- persistent CTAs (one per SM), every warp on its own tiles
+// of 992 positions (two halves of 496), no block-wide barrier after start-up:
+//   * a tile plus a halo is fetched with one bulk async copy (cp.async.bulk,
+//     the TMA unit, no multicast) into one of the warp's shared-memory stages,
+//     completing on that stage's mbarrier, `stages` tiles ahead of use;
+//   * lane l classifies the 16 bytes at 16 l of each half once (byte permutes
+//     on a 3-bit hash, or the byte table), packs their codes into one word (two
+//     for 4-bit codes) and gets the next lane's word with one shuffle, so each
+//     of its start positions has its window of codes in registers; lane 31
+//     only supplies the look-ahead word;
+//   * one bit per position from the root filter (resident in shared memory for
+//     the whole kernel): clear means the walk from the root stops within the
+//     first k characters with no keyword, i.e. the result is -1 -- almost every
+//     position of a text whose keywords are longer than k;
+//   * the other positions ("survivors") are resolved by one load from the
+//     window table (depth-k state or result), one from the stride table (k2
+//     more characters), and rarely the goto table one character at a time.  A
+//     tile with at most one survivor per lane keeps them "in flight" across the
+//     next two tiles, so their dependent loads overlap other work; a tile with
+//     more finishes them at once, eight walks per lane;
+//   * output: dense ids (one bulk async store of a constant -1 buffer when no
+//     survivor found a keyword, else -1 stores and the survivors' ids), a count
+//     (one atomic per warp), or slots (per tile the number of matches and the
+//     first kSlotCap of them) from which compact.cu makes the compacted list.
+// Work units are the tiles of one text, or of all texts of one automaton in a
+// batch (the planned list), claimed from a global counter.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+
+#include "pfac_device.cuh"
+
+namespace pfac {
+
+// The kernel and its launch templates; filter.cu launches the plain forms,
+// filter_help.cu the forms whose heavy tiles are shared within the CTA.
+namespace filt {
+
+constexpr int kMaxBlock = 512;
+constexpr int kMaxWarps = kMaxBlock / 32;
+constexpr int kMaxStages = 4;
+constexpr uint32_t kOwnLanes = 31;            // lanes that own start positions in a pass
+constexpr uint32_t kPass = 16 * kOwnLanes;    // 496 positions per pass
+constexpr uint32_t kTile = 2 * kPass;         // 992 positions per warp tile
+constexpr uint32_t kCodeSpan = kTile + 16;    // positions classified per tile
+// shared-memory header
+constexpr uint32_t kOffJBar = 0;
+constexpr uint32_t kOffStageBar = 64;
+constexpr uint32_t kOffStageTile = kOffStageBar + kMaxWarps * kMaxStages * 8;
+constexpr uint32_t kOffRetired = 1008;  // warps of the CTA done with their own tiles
+constexpr uint32_t kOffOffers = 1012;   // heavy tiles offered and not yet finished
+static_assert(kOffStageTile + kMaxWarps * kMaxStages * 4 <= kOffRetired && kOffOffers + 4 <= 1024,
+              "CTA counters overlap the stage descriptors or the class map");
+constexpr uint32_t kOffCls = 1024;  // 256 x uint8
+constexpr uint32_t kOffF = 1280;    // root filter bits
+constexpr unsigned kFull = 0xffffffffu;
+// Texts of at most this many tiles per warp of the grid take the forms that
+// share heavy tiles within the CTA.
+constexpr uint32_t kHelpTilesPerWarp = 16;
+
+struct FilterParams {
+    const uint8_t *text;
+    uint64_t n;
+    uint32_t tile;    // positions per tile (multiple of 16)
+    uint32_t staged;  // bytes staged per tile (tile + halo, multiple of 16)
+    uint32_t ntiles;  // single text: its tiles
+    uint32_t nstages;
+    const void *G;
+    const uint32_t *Fg;
+    const int32_t *JK;
+    const int32_t *J2;
+    const uint8_t *cls8g;
+    uint32_t C, W, k, k2, base_k, maxlen, fbytes;
+    uint32_t famask;  // byte offsets of the root filter's words reached by a window
+    int hash_shift;
+    uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
+    int32_t *out;
+    unsigned long long *count;
+    SlotOut sl;
+    unsigned int *counter;
+    unsigned int *err;
+    uint32_t off_neg1, off_warp, warp_bytes, off_packed, off_inv, off_queue, off_meta, off_help;
+    // batch: the automaton's head and the planned list (text and out are then
+    // the bases of all texts and outputs)
+    const BatchHead *batch;
+    const BatchItemDev *lists;
+    // one text: its 16-byte aligned base, the tile starts whose staged bytes
+    // lie wholly in its aligned part [a1, a2), and whether its output takes
+    // 16-byte stores
+    const uint8_t *gbase;
+    uint64_t a1, a2;
+    uint32_t vec_ok;
+    // chain records from state s_chain on (0xFFFFFFFF: none)
+    const uint4 *skip;
+    const uint8_t *chain;
+    uint32_t s_chain;
+};
+
+struct WarpSmem {
+    const uint8_t *cls8;
+    const uint32_t *F;
+    uint8_t *st;
+    uint32_t *packed;  // codes of the tile's kCodeSpan positions, B bits each
+    uint16_t *inv;     // 16 "cannot extend a walk" bits per 16 positions
+    uint16_t *queue;
+    const int32_t *neg1;  // kTile x -1, shared by the CTA's warps
+};
+
+// A warp's tile with more survivors than one round of walks, offered to the
+// CTA's other warps once they have no tiles of their own: chunks of 256 queued
+// survivors, claimed by an atomic on `ticket` ((publication << 32) | next
+// chunk).  The fields are written before the ticket is reset for a new
+// publication, and a claim is valid only for the publication it names and a
+// chunk below nchunks, so a stale claim never touches a new tile.  The owner
+// reuses its queue and codes only after `done` reaches nchunks.
+struct HelpSlot {
+    unsigned long long ticket;
+    uint32_t pub;      // publication the fields belong to (0: none yet)
+    uint32_t nchunks;
+    uint32_t done;     // chunks finished, this publication
+    uint32_t tile, item, total;
+    long long gpb;
+    uint32_t flags;    // bit 0: interior, bit 1: clean
+    uint32_t su;       // slot-mode unit
+};
+
+// The text and tile of work unit u (entry `item` of the planned list in a batch).
+__device__ __forceinline__ TileText tile_text(const FilterParams &p, const Work &wk, uint32_t u, uint32_t item) {
+    if (!wk.list) return make_text(p.text, p.out, p.n, u);
+    return batch_text(wk, p.text, p.out, item, u);
+}
+
+// All lanes: point stage s at unit u (>= wk.units: the end of this warp's
+// work) and start its bulk copy.
+__device__ __forceinline__ void issue_unit(const FilterParams &p, const Work &wk, uint64_t *bar, uint32_t *stile,
+                                           uint32_t *sitem, uint8_t *st, uint32_t u, int lane) {
+    const uint32_t item = (wk.list && u < wk.units) ? find_item(wk, u, lane) : 0u;
+    if (lane == 0) {
+        *stile = u;
+        *sitem = item;
+        const uint64_t tlo = static_cast<uint64_t>(u) * p.tile;
+        if (u >= wk.units) {
+            mbar_arrive(bar);
+        } else if (!wk.list && tlo >= p.a1 && tlo + p.staged <= p.a2) {
+            // one text, a tile inside its aligned part: the whole stage
+            mbar_arrive_expect_tx(bar, p.staged);
+            bulk_load_hint(st, p.gbase + tlo, p.staged, bar, policy_evict_first());
+        } else {
+            issue_text_tile(tile_text(p, wk, u, item), p.tile, p.staged, bar, st);
+        }
+    }
+}
+
+// Classify the 4 bytes of w: their class codes (one per byte) and a word whose
+// non-zero bytes mark bytes in no keyword.
+__device__ __forceinline__ void classify_word(const FilterParams &p, const uint8_t *cls8, uint32_t w,
+                                              uint32_t &codes, uint32_t &unknown) {
+    if (p.hash_shift >= 0) {
+        // h = (byte >> s) & 7 selects, with byte permutes, the code of the one
+        // keyword byte with that hash and the byte itself; a mismatch is a byte
+        // in no keyword
+        const uint32_t sh = static_cast<uint32_t>(p.hash_shift);
+        const uint32_t hv = (w >> sh) & 0x07070707u;
+        const uint32_t sel = __byte_perm(hv | (hv >> 4), 0u, 0x4420u);
+        codes = __byte_perm(p.hcode_lo, p.hcode_hi, sel);
+        unknown = w ^ __byte_perm(p.hbyte_lo, p.hbyte_hi, sel);
+    } else {
+        const uint32_t t0 = cls8[__byte_perm(w, 0u, 0x4440u)], t1 = cls8[__byte_perm(w, 0u, 0x4441u)];
+        const uint32_t t2 = cls8[__byte_perm(w, 0u, 0x4442u)], t3 = cls8[__byte_perm(w, 0u, 0x4443u)];
+        codes = __byte_perm(__byte_perm(t0, t1, 0x0040u), __byte_perm(t2, t3, 0x0040u), 0x5410u);
+        unknown = codes & 0x80808080u;  // class value 0xFF marks a byte in no keyword
+    }
+}
+
+// One flag per non-zero byte of x (bit i for byte i).
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
+    const uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;  // bit 7 of each byte: that byte != 0
+    return ((t & 0x80808080u) * 0x00204081u) >> 28;
+}
+
+// Pack the low B bits of the 4 byte codes of `codes` (4 B bits, first byte lowest).
+template <int B>
+__device__ __forceinline__ uint32_t pack4(uint32_t codes) {
+    if (B == 2) return ((codes & 0x03030303u) * 0x01041040u) >> 24;
+    uint32_t x = codes & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    return (x | (x >> 8)) & 0xFFFFu;
+}
+
+// Codes of positions i.. (16 for B = 2, 8 for B = 4) from the packed stream.
+template <int B>
+__device__ __forceinline__ uint32_t code_window(const uint32_t *packed, uint32_t i) {
+    const uint32_t bo = B * i, w = bo >> 5;
+    return __funnelshift_r(packed[w], packed[w + 1], bo & 31u);
+}
+
+// Code of tile position q; false when q cannot extend a walk.  Positions below
+// `coded` have their codes in the packed stream already; later ones are read
+// from the text in global memory (the stage may already hold the next tile).
+template <int B>
+__device__ __forceinline__ bool fetch_code(const TileText &tt, const WarpSmem &w, int64_t gpb, uint32_t coded,
+                                           uint32_t q, uint32_t &c) {
+    if (q < coded) {
+        if ((w.inv[q >> 4] >> (q & 15u)) & 1u) return false;
+        c = (w.packed[(B * q) >> 5] >> ((B * q) & 31u)) & ((1u << B) - 1u);
+        return true;
+    }
+    const int64_t gp = gpb + static_cast<int64_t>(q);
+    if (gp >= static_cast<int64_t>(tt.n)) return false;
+    const uint32_t v = w.cls8[__ldg(tt.text + gp)];
+    if (v == 0xFFu) return false;
+    c = v;
+    return true;
+}
+
+// A walk at state s (>= p.s_chain) whose next byte is at tile index q: its
+// chain record decides.  Returns 1 when the state's whole run of forced
+// transitions matched the text (s and q moved to the run's end), 0 when the
+// walk stops in the run or at a leaf (result in r), 2 when s branches (take its
+// goto row).  The text bytes come from global memory (L1/L2: the tile was
+// just read).
+__device__ __forceinline__ int chain_step(const FilterParams &p, const TileText &tt, int64_t gpb, uint32_t &s,
+                                          uint32_t &q, int &r) {
+    const uint4 rc = __ldg(p.skip + (s - p.s_chain));
+    if (rc.x == kSkipBranch) return 2;
+    const int64_t gq = gpb + static_cast<int64_t>(q);
+    const bool ok = rc.x > 0 && gq + static_cast<int64_t>(rc.x) <= static_cast<int64_t>(tt.n) &&
+                    run_equal(tt.text + gq, p.chain + rc.y, rc.x);
+    if (ok) {
+        s = rc.z;
+        q += rc.x;
+        return 1;
+    }
+    r = static_cast<int>(rc.w);
+    return 0;
+}
+
+// Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)):
+// their results go to the pass's staging buffer (or are counted).  Returns
+// true when this lane found a keyword.
+template <int B, typename GT, int MODE, int SLOTS, bool DIRECT = false>
+__device__ __forceinline__ bool finish_survivors(const FilterParams &p, const TileText &tt, const WarpSmem &w,
+                                                 int64_t gpb, bool interior, bool clean, uint32_t avail,
+                                                 uint32_t pbase, int lane, unsigned long long &cnt, uint32_t base,
+                                                 uint32_t coded = 0, uint32_t su = 0) {
+    const int64_t n = static_cast<int64_t>(tt.n);
+    const uint32_t k = p.k, k2 = p.k2;
+    const GT *G = static_cast<const GT *>(p.G);
+    uint32_t st[SLOTS], q[SLOTS], ii[SLOTS];
+    int v[SLOTS];
+    uint32_t act = 0, pend = 0, walking = 0;
+    uint32_t x[SLOTS];
+    // window table: depth-k state or result
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        const uint32_t qi = lane + 32u * t;
+        v[t] = INT_MIN;
+        st[t] = 0;
+        q[t] = 0;
+        ii[t] = 0;
+        x[t] = 0;
+        if (qi < avail) {
+            act |= 1u << t;
+            const uint32_t e16 = w.queue[base + qi];
+            const uint32_t i = e16 & 0x7FFFu;
+            ii[t] = i;
+            q[t] = i;
+            if (!(e16 >> 15)) {
+                x[t] = code_window<B>(w.packed, i);
+                v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
+                pend |= 1u << t;
+            }
+        }
+    }
+    // stride table for the walks still alive at depth k
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if ((pend >> t) & 1u) {
+            const int e = v[t];
+            if (e < 0) {
+                v[t] = decode_dead(e);
+                pend &= ~(1u << t);
+            } else {
+                st[t] = static_cast<uint32_t>(e);
+                q[t] = ii[t] + k;
+                v[t] = INT_MIN;
+                bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(ii[t] + k + k2) <= n);
+                if (ok2 && !clean) {
+                    const uint32_t j = ii[t] + k;
+                    const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
+                    ok2 = (wi & ((1u << k2) - 1u)) == 0;
+                }
+                if (ok2) {
+                    const uint32_t w2 = (x[t] >> (B * k)) & ((1u << (B * k2)) - 1u);
+                    v[t] = __ldg(p.J2 + ((static_cast<uint64_t>(st[t] - p.base_k) << (B * k2)) | w2));
+                } else {
+                    pend &= ~(1u << t);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if ((act >> t) & 1u) {
+            if ((pend >> t) & 1u) {
+                if (v[t] < 0) {
+                    v[t] = decode_dead(v[t]);
+                } else {
+                    st[t] = static_cast<uint32_t>(v[t]);
+                    q[t] += k2;
+                    v[t] = INT_MIN;
+                    walking |= 1u << t;
+                }
+            } else if (v[t] == INT_MIN) {
+                walking |= 1u << t;
+            }
+        }
+    }
+    // the goto table, one character at a time
+    for (uint32_t step = 0; walking; ++step) {
+        if (step > p.maxlen + 1) {  // impossible for a well-formed table
+            atomicOr(p.err, static_cast<unsigned>(kErrWalk));
+#pragma unroll
+            for (int t = 0; t < SLOTS; ++t)
+                if ((walking >> t) & 1u) v[t] = -1;
+            break;
+        }
+        int e[SLOTS];
+        uint32_t loaded = 0;
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            if ((walking >> t) & 1u) {
+                if (st[t] >= p.s_chain) {  // a run of forced transitions, a leaf, or a branch
+                    int rr = -1;
+                    // text bytes from global memory: the tile's stage already
+                    // takes the next bulk copy while its survivors are walked
+                    const int k3 = chain_step(p, tt, gpb, st[t], q[t], rr);
+                    if (k3 == 1) continue;
+                    if (k3 == 0) {
+                        v[t] = rr;
+                        walking &= ~(1u << t);
+                        continue;
+                    }
+                }
+                uint32_t c = 0;
+                const bool okc = fetch_code<B>(tt, w, gpb, DIRECT ? coded : pbase + kPass + 16u, q[t], c);
+                // an unknown byte or the text end reads the row's end column,
+                // which always holds the result of stopping there
+                e[t] = goto_ld(G, st[t], p.W, okc ? c : p.C);
+                loaded |= 1u << t;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            if ((loaded >> t) & 1u) {
+                if (e[t] < 0) {
+                    v[t] = decode_dead(e[t]);
+                    walking &= ~(1u << t);
+                } else {
+                    st[t] = static_cast<uint32_t>(e[t]);
+                    q[t] += 1;
+                }
+            }
+        }
+    }
+    bool found = false;
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        const bool mine = (act >> t) & 1u;
+        if (MODE == OUT_SLOTS) {
+            // one atomic per warp and slot index, ranks by ballot (all lanes)
+            const bool hit = mine && v[t] >= 0;
+            const unsigned m = __ballot_sync(kFull, hit);
+            if (mine && p.sl.dense) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + ii[t]] = v[t];
+            if (m) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(p.sl.counts + su, static_cast<uint32_t>(__popc(m)));
+                base = __shfl_sync(kFull, base, 0) + __popc(m & ((1u << lane) - 1u));
+                if (hit && base < kSlotCap)
+                    p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + base] =
+                        (static_cast<unsigned long long>(static_cast<uint32_t>(v[t])) << 32) |
+                        static_cast<uint32_t>(gpb + ii[t]);
+            }
+            found |= hit;
+            continue;
+        }
+        if (mine) {
+            found |= v[t] >= 0;
+            if (MODE == OUT_COUNT)
+                cnt += v[t] >= 0 ? 1ull : 0ull;
+            else
+                tt.out[gpb + ii[t]] = v[t];
+        }
+    }
+    return found;
+}
+
+// One warp: claim a chunk of the tile offered in slot hs.  True (with the
+// chunk) when the claim names the slot's current publication and a chunk it
+// has; any other claim is void and changes nothing.
+__device__ __forceinline__ bool claim_chunk(HelpSlot *hs, int lane, uint32_t &chunk) {
+    uint32_t ok = 0, c = 0;
+    // a plain look first: no atomic on a slot with nothing left to claim
+    bool open = false;
+    if (lane == 0) {
+        const unsigned long long t = *reinterpret_cast<volatile unsigned long long *>(&hs->ticket);
+        const uint32_t pub = *reinterpret_cast<volatile uint32_t *>(&hs->pub);
+        const uint32_t nch = *reinterpret_cast<volatile uint32_t *>(&hs->nchunks);
+        open = static_cast<uint32_t>(t >> 32) != 0u && static_cast<uint32_t>(t >> 32) == pub &&
+               static_cast<uint32_t>(t) < nch;
+    }
+    if (lane == 0 && open) {
+        const unsigned long long t = atomicAdd(&hs->ticket, 1ull);
+        __threadfence_block();
+        const uint32_t gen = static_cast<uint32_t>(t >> 32);
+        c = static_cast<uint32_t>(t);
+        const uint32_t pub = *reinterpret_cast<volatile uint32_t *>(&hs->pub);
+        const uint32_t nch = *reinterpret_cast<volatile uint32_t *>(&hs->nchunks);
+        ok = (gen != 0u && gen == pub && c < nch) ? 1u : 0u;
+    }
+    chunk = __shfl_sync(kFull, c, 0);
+    return __shfl_sync(kFull, ok, 0) != 0u;
+}
+
+// One warp: finish chunk c of the tile offered by warp s (its queue and codes
+// stay in place until every chunk is done), then report it done.
+template <int B, typename GT, int MODE>
+__device__ __forceinline__ void help_chunk(const FilterParams &p, const Work &wk, uint8_t *smem, HelpSlot *hs,
+                                           uint32_t s, uint32_t c, int lane, unsigned long long &cnt) {
+    uint32_t tile = 0, item = 0, total = 0, flags = 0, su = 0, glo = 0, ghi = 0;
+    if (lane == 0) {
+        tile = hs->tile;
+        item = hs->item;
+        total = hs->total;
+        flags = hs->flags;
+        su = hs->su;
+        const unsigned long long g = static_cast<unsigned long long>(hs->gpb);
+        glo = static_cast<uint32_t>(g);
+        ghi = static_cast<uint32_t>(g >> 32);
+    }
+    tile = __shfl_sync(kFull, tile, 0);
+    item = __shfl_sync(kFull, item, 0);
+    total = __shfl_sync(kFull, total, 0);
+    flags = __shfl_sync(kFull, flags, 0);
+    su = __shfl_sync(kFull, su, 0);
+    glo = __shfl_sync(kFull, glo, 0);
+    ghi = __shfl_sync(kFull, ghi, 0);
+    const int64_t gpb = static_cast<int64_t>((static_cast<uint64_t>(ghi) << 32) | glo);
+    uint8_t *ws = smem + p.off_warp + static_cast<size_t>(s) * p.warp_bytes;
+    WarpSmem v;
+    v.cls8 = smem + kOffCls;
+    v.F = reinterpret_cast<const uint32_t *>(smem + kOffF);
+    v.st = ws;
+    v.packed = reinterpret_cast<uint32_t *>(ws + p.off_packed);
+    v.inv = reinterpret_cast<uint16_t *>(ws + p.off_inv);
+    v.queue = reinterpret_cast<uint16_t *>(ws + p.off_queue);
+    v.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
+    const TileText tt = tile_text(p, wk, tile, item);
+    finish_survivors<B, GT, MODE, 8, true>(p, tt, v, gpb, (flags & 1u) != 0, (flags & 2u) != 0, total - 256u * c, 0,
+                                           lane, cnt, 256u * c, kCodeSpan, su);
+    __threadfence_block();
+    __syncwarp();
+    if (lane == 0) atomicAdd(&hs->done, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined variant (dense ids and counts).  A tile's survivors (at most one
+// per lane) stay in flight while the warp works on the next tiles: the window
+// table load is issued when the tile is filtered, the stride table load one
+// tile later, and the tile is finished and written two tiles later, so the
+// two dependent L2 round trips overlap the classification and filtering of
+// the next tiles.  A tile with more survivors than lanes (long walks) drains
+// the pipeline and is finished at once.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNoPos = 0xFFFFu;
+enum : uint32_t { kPhJK = 0, kPhJ2 = 1, kPhWalk = 2, kPhDone = 3 };
+
+struct Flight {
+    int64_t gpb;      // text index of the tile's position 0
+    uint32_t tile;    // work unit; 0xFFFFFFFF: empty
+    uint32_t item;    // batch: its entry in the planned list
+    uint32_t interior;
+    uint32_t pos;     // this lane's survivor (tile position) or kNoPos
+    uint32_t phase;
+    uint32_t state;   // goto state of the walk
+    uint32_t q;       // tile position of the walk's next character
+    uint32_t w2;      // stride-table codes
+    uint32_t ok2;     // the stride window is usable
+    int val;          // load in flight, or the result when done
+};
+
+__device__ __forceinline__ Flight empty_flight() {
+    Flight f;
+    f.gpb = 0;
+    f.tile = 0xFFFFFFFFu;
+    f.item = 0;
+    f.interior = 0;
+    f.pos = kNoPos;
+    f.phase = kPhDone;
+    f.state = 0;
+    f.q = 0;
+    f.w2 = 0;
+    f.ok2 = 0;
+    f.val = -1;
+    return f;
+}
+
+// Walk the goto table from state s, reading the text from global memory.
+template <typename GT>
+__device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t *cls8, const TileText &tt,
+                                           int64_t gpb, uint32_t s, uint32_t q) {
+    const GT *G = static_cast<const GT *>(p.G);
+    for (uint32_t step = 0; step <= p.maxlen + 1; ++step) {
+        if (s >= p.s_chain) {  // a run of forced transitions, a leaf, or a branch
+            int rr = -1;
+            const int k3 = chain_step(p, tt, gpb, s, q, rr);
+            if (k3 == 1) continue;
+            if (k3 == 0) return rr;
+        }
+        const int64_t gp = gpb + static_cast<int64_t>(q);
+        uint32_t c = p.C;  // the end column: stop here
+        if (gp < static_cast<int64_t>(tt.n)) {
+            const uint32_t v = cls8[__ldg(tt.text + gp)];
+            if (v != 0xFFu) c = v;
+        }
+        const int t = goto_ld(G, s, p.W, c);
+        if (t < 0) return decode_dead(t);
+        s = static_cast<uint32_t>(t);
+        ++q;
+    }
+    atomicOr(p.err, static_cast<unsigned>(kErrWalk));
+    return -1;
+}
+
+// Second stage: the window-table result has arrived; issue the stride load.
+template <int B>
+__device__ __forceinline__ void flight_advance(const FilterParams &p, Flight &f) {
+    if (f.pos == kNoPos || f.phase != kPhJK) return;
+    const int e = f.val;
+    if (e < 0) {
+        f.val = decode_dead(e);
+        f.phase = kPhDone;
+        return;
+    }
+    f.state = static_cast<uint32_t>(e);
+    f.q = f.pos + p.k;
+    if (f.ok2) {
+        f.val = __ldg(p.J2 + ((static_cast<uint64_t>(f.state - p.base_k) << (B * p.k2)) | f.w2));
+        f.phase = kPhJ2;
+    } else {
+        f.phase = kPhWalk;
+    }
+}
+
+// Last stage: the stride-table result has arrived; finish the walk if needed.
+template <typename GT>
+__device__ __forceinline__ void flight_finish(const FilterParams &p, const Work &wk, const uint8_t *cls8, Flight &f) {
+    if (f.pos == kNoPos) return;
+    if (f.phase == kPhJ2) {
+        const int e = f.val;
+        if (e < 0) {
+            f.val = decode_dead(e);
+            f.phase = kPhDone;
+            return;
+        }
+        f.state = static_cast<uint32_t>(e);
+        f.q += p.k2;
+        f.phase = kPhWalk;
+    }
+    if (f.phase == kPhWalk) {
+        f.val = walk_global<GT>(p, cls8, tile_text(p, wk, f.tile, f.item), f.gpb, f.state, f.q);
+        f.phase = kPhDone;
+    }
+}
+
+// Write (or count) a finished tile: one bulk store of -1 when no survivor
+// found a keyword, else -1 from the position owners and the survivors' ids.
+template <int MODE>
+__device__ __forceinline__ void flight_output(const FilterParams &p, const Work &wk, const WarpSmem &w, const Flight &f,
+                                              int lane, unsigned long long &cnt) {
+    if (f.tile == 0xFFFFFFFFu) return;
+    const bool mine = f.pos != kNoPos && f.val >= 0;
+    if (MODE == OUT_COUNT) {
+        cnt += mine ? 1ull : 0ull;
+        return;
+    }
+    if (MODE == OUT_SLOTS) {
+        // at most one survivor per lane: rank by lane (ascending position)
+        const unsigned m = __ballot_sync(kFull, mine);
+        const uint32_t su = p.sl.ubase + f.tile;
+        const uint32_t r = __popc(m & ((1u << lane) - 1u));
+        if (mine && r < kSlotCap)
+            p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + r] =
+                (static_cast<unsigned long long>(static_cast<uint32_t>(f.val)) << 32) |
+                static_cast<uint32_t>(f.gpb + f.pos);
+        if (lane == 0 && m) p.sl.counts[su] = __popc(m);  // the unit's only writer
+        return;
+    }
+    const bool found = __any_sync(kFull, mine);
+    if (!found && f.interior && !wk.list && p.vec_ok) {  // one text: no lookup of its output
+        if (lane == 0) {
+            bulk_store(p.out + f.gpb, w.neg1, kTile * 4);
+            bulk_commit();
+            bulk_wait_read_keep8();  // bound the groups in flight
+        }
+        return;
+    }
+    const TileText tt = tile_text(p, wk, f.tile, f.item);
+    const int64_t n = static_cast<int64_t>(tt.n);
+    if (!found && f.interior && tt.vec_ok) {
+        if (lane == 0) {
+            bulk_store(tt.out + f.gpb, w.neg1, kTile * 4);
+            bulk_commit();
+            bulk_wait_read_keep8();  // bound the groups in flight
+        }
+        return;
+    }
+    if (lane < static_cast<int>(kOwnLanes)) {
+        const int4 none = make_int4(-1, -1, -1, -1);
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+#pragma unroll
+            for (uint32_t g = 0; g < 4; ++g) {
+                const int64_t g0 = f.gpb + h * kPass + 16u * lane + 4u * g;
+                if (tt.vec_ok && g0 >= 0 && g0 + 4 <= n) {
+                    *reinterpret_cast<int4 *>(tt.out + g0) = none;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (g0 + r >= 0 && g0 + r < n) tt.out[g0 + r] = -1;
+                }
+            }
+        }
+    }
+    __syncwarp();  // the -1 stores of the owners come before the survivors' ids
+    if (mine) tt.out[f.gpb + f.pos] = f.val;
+}
+
+// HELP: share heavy tiles within the CTA (the forms for one text that is short
+// next to the grid; see the heavy path below).
+template <int B, typename GT, int MODE, bool BATCH, bool HELP>
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
+    uint32_t *stile = reinterpret_cast<uint32_t *>(smem + kOffStageTile) + warp * kMaxStages;
+    uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
+    WarpSmem w;
+    w.cls8 = smem + kOffCls;
+    w.F = reinterpret_cast<const uint32_t *>(smem + kOffF);
+    w.st = wreg;
+    w.packed = reinterpret_cast<uint32_t *>(wreg + p.off_packed);
+    w.inv = reinterpret_cast<uint16_t *>(wreg + p.off_inv);
+    w.queue = reinterpret_cast<uint16_t *>(wreg + p.off_queue);
+    w.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
+    uint32_t *sitem = reinterpret_cast<uint32_t *>(wreg + p.off_meta);
+    HelpSlot *my_help = reinterpret_cast<HelpSlot *>(wreg + p.off_help);
+    uint32_t *retired = reinterpret_cast<uint32_t *>(smem + kOffRetired);
+    uint32_t *offers = reinterpret_cast<uint32_t *>(smem + kOffOffers);
+    const uint32_t nst = p.nstages;
+    // one text: a null list the compiler sees, so the batch lookups fold away
+    const Work wk = BATCH ? load_work(p.batch, p.lists, p.ntiles) : load_work(nullptr, nullptr, p.ntiles);
+    const uint32_t k = p.k, k2 = p.k2;
+    const bool owner = lane < static_cast<int>(kOwnLanes);
+
+    for (uint32_t i = threadIdx.x; i < kTile; i += blockDim.x) reinterpret_cast<int32_t *>(smem + p.off_neg1)[i] = -1;
+    fence_proxy_async_smem();  // the constant buffer is read by bulk stores
+    if (lane == 0) {
+        my_help->ticket = 0;
+        my_help->pub = 0;
+        my_help->nchunks = 0;
+        my_help->done = 0;
+    }
+    if (threadIdx.x == 0) {
+        *retired = 0;
+        *offers = 0;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(jbar, 1);
+        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
+        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(jbar, 256u + p.fbytes);
+        bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
+        bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
+    }
+    // Tiles: the first one per warp statically, the rest claimed from a global
+    // counter so that a warp held up by an expensive tile stops taking work.
+    const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
+    const uint64_t GW = static_cast<uint64_t>(gridDim.x) * nw;
+    UnitClaims claims = claims_start(gw, GW);
+    auto next_tile = [&](uint32_t) -> uint32_t {
+        uint32_t t = 0xFFFFFFFFu;
+        if (lane == 0) {
+            const uint64_t c = claims_next(claims, p.counter, wk.units);
+            if (c < wk.units) t = static_cast<uint32_t>(c);
+        }
+        return __shfl_sync(kFull, t, 0);
+    };
+    for (uint32_t s = 0; s < nst; ++s)
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, next_tile(s), lane);
+
+    unsigned long long cnt = 0;
+    Flight f1 = empty_flight(), f2 = empty_flight();  // one and two tiles back
+    bool ok = mbar_wait(jbar, 0);
+    // stage s of iteration it is it % nst, its phase parity (it / nst) & 1
+    for (uint32_t it = 0, s = 0, par = 0;; ++it, s = s + 1 == nst ? 0u : s + 1, par ^= s == 0 ? 1u : 0u) {
+        ok = ok && mbar_wait(&bars[s], par);
+        if (!__all_sync(kFull, ok)) {
+            // A copy never completed: latch the error, let this warp's copies in
+            // flight finish (bounded), and leave.
+            if (lane == 0) {
+                bulk_wait_all();
+                atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
+                atomicAdd(retired, 1u);
+                mbar_wait(jbar, 0);
+                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u);
+            }
+            return;
+        }
+        const uint32_t tile = stile[s];
+        if (tile >= wk.units) break;
+        const uint32_t item = sitem[s];
+        const TileText tt = tile_text(p, wk, tile, item);
+        const int64_t n = static_cast<int64_t>(tt.n);
+        uint8_t *st = wreg + s * p.staged;
+        const uint64_t tlo = static_cast<uint64_t>(tt.tile) * kTile;
+        const int64_t gpb = static_cast<int64_t>(tlo) - tt.head;
+        const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.staged) <= n;
+        if (!interior) {
+            load_text_fringe(tt, p.staged, st, tlo, lane);
+            __syncwarp();
+        }
+
+        // 1. classify the tile's bytes (both halves), once per byte
+        uint32_t plo[2], phi[2], inv[2];
+#pragma unroll
+        for (uint32_t h = 0; h < 2; ++h) {
+            const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
+            const uint4 raw = *reinterpret_cast<const uint4 *>(st + i0);
+            uint32_t c0, c1, c2, c3, u0, u1, u2, u3;
+            classify_word(p, w.cls8, raw.x, c0, u0);
+            classify_word(p, w.cls8, raw.y, c1, u1);
+            classify_word(p, w.cls8, raw.z, c2, u2);
+            classify_word(p, w.cls8, raw.w, c3, u3);
+            uint32_t iv = 0;
+            if (u0 | u1 | u2 | u3)
+                iv = nonzero_bytes(u0) | (nonzero_bytes(u1) << 4) | (nonzero_bytes(u2) << 8) |
+                     (nonzero_bytes(u3) << 12);
+            if (!interior) {
+                const int64_t g0 = gpb + i0;
+                if (!(g0 >= 0 && g0 + 16 <= n)) {
+#pragma unroll
+                    for (int b = 0; b < 16; ++b)
+                        if (g0 + b < 0 || g0 + b >= n) iv |= 1u << b;
+                }
+            }
+            inv[h] = iv;
+            if (B == 2) {
+                plo[h] = pack4<2>(c0) | (pack4<2>(c1) << 8) | (pack4<2>(c2) << 16) | (pack4<2>(c3) << 24);
+                phi[h] = 0;
+                w.packed[i0 >> 4] = plo[h];
+            } else {
+                plo[h] = pack4<4>(c0) | (pack4<4>(c1) << 16);
+                phi[h] = pack4<4>(c2) | (pack4<4>(c3) << 16);
+                w.packed[i0 >> 3] = plo[h];
+                w.packed[(i0 >> 3) + 1] = phi[h];
+            }
+            w.inv[i0 >> 4] = static_cast<uint16_t>(iv);
+        }
+        const bool clean = !__any_sync(kFull, (inv[0] | inv[1]) != 0);
+        __syncwarp();
+        // the stage is consumed: start fetching a later tile into it
+        if (lane == 0) fence_proxy_async_smem();
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], st, next_tile(it + nst), lane);
+
+        // 2. root filter, one bit per start position (bits 0-15: first half)
+        uint32_t sv = 0, slowm = 0;
+        uint32_t nlo[2];  // the next lane's first codes (lane 31 supplies the look-ahead)
+        nlo[0] = __shfl_down_sync(kFull, plo[0], 1);
+        nlo[1] = __shfl_down_sync(kFull, plo[1], 1);
+        if (owner) {
+            // The bit of window value v is bit 31 - (v & 31) of filter word
+            // v >> 5: rotating the word left by v's low five bits brings it to
+            // bit 31, and a funnel shift appends it to acc (first position
+            // ends highest, hence the bit reversal).
+            const uint8_t *fb = reinterpret_cast<const uint8_t *>(w.F);
+            uint32_t acc = 0;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    uint32_t win;
+                    if (B == 2)
+                        win = __funnelshift_r(plo[h], nlo[h], 2 * r);
+                    else
+                        win = r < 8 ? __funnelshift_r(plo[h], phi[h], 4 * r)
+                                    : __funnelshift_r(phi[h], nlo[h], 4 * (r - 8));
+                    const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & p.famask));
+                    acc = __funnelshift_l(__funnelshift_l(word, word, win), acc, 1);
+                }
+            }
+            sv = __brev(acc);
+        }
+        if (!interior || !clean) {
+            const uint32_t kbits = (1u << k) - 1u;
+            uint32_t valid = 0;
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+                const uint32_t ninv = __shfl_down_sync(kFull, inv[h], 1);
+                const uint32_t iw = inv[h] | (ninv << 16);
+                const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int64_t gp = gpb + i0 + r;
+                    if (owner && gp >= 0 && gp < n) {
+                        valid |= 1u << (16 * h + r);
+                        if (gp + static_cast<int64_t>(k) > n || ((iw >> r) & kbits)) slowm |= 1u << (16 * h + r);
+                    }
+                }
+            }
+            sv = (sv | slowm) & valid;
+        }
+
+        // 3. survivors into the warp's queue in ascending position
+        const uint32_t c = __popc(sv & 0xFFFFu) | (__popc(sv >> 16) << 16);
+        uint32_t inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, inc, d);
+            if (lane >= d) inc += y;
+        }
+        const uint32_t tot2 = __shfl_sync(kFull, inc, 31);
+        const uint32_t total = (tot2 & 0xFFFFu) + (tot2 >> 16);
+        {
+            const uint32_t excl = inc - c;
+            uint32_t o0 = excl & 0xFFFFu, o1 = (tot2 & 0xFFFFu) + (excl >> 16);
+            uint32_t m = sv;
+            while (m) {
+                const uint32_t b = __ffs(m) - 1;
+                m &= m - 1;
+                const uint32_t h = b >> 4;
+                const uint32_t i = h * kPass + 16u * static_cast<uint32_t>(lane) + (b & 15u);
+                const uint16_t e = static_cast<uint16_t>(i | (((slowm >> b) & 1u) << 15));
+                if (h == 0)
+                    w.queue[o0++] = e;
+                else
+                    w.queue[o1++] = e;
+            }
+        }
+        __syncwarp();
+
+        if (total > 32) {
+            // 4a. many survivors: finish the tiles in flight, then this one
+            flight_advance<B>(p, f1);
+            flight_finish<GT>(p, wk, w.cls8, f2);
+            flight_output<MODE>(p, wk, w, f2, lane, cnt);
+            flight_finish<GT>(p, wk, w.cls8, f1);
+            flight_output<MODE>(p, wk, w, f1, lane, cnt);
+            f1 = empty_flight();
+            f2 = empty_flight();
+            if (MODE == OUT_DENSE) {
+                // -1 from the position owners first, then every survivor's id
+                if (owner) {
+                    const int4 none = make_int4(-1, -1, -1, -1);
+#pragma unroll
+                    for (uint32_t h = 0; h < 2; ++h) {
+#pragma unroll
+                        for (uint32_t g = 0; g < 4; ++g) {
+                            const int64_t g0 = gpb + h * kPass + 16u * lane + 4u * g;
+                            if (tt.vec_ok && g0 >= 0 && g0 + 4 <= n) {
+                                *reinterpret_cast<int4 *>(tt.out + g0) = none;
+                            } else {
+#pragma unroll
+                                for (int r = 0; r < 4; ++r)
+                                    if (g0 + r >= 0 && g0 + r < n) tt.out[g0 + r] = -1;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            if (MODE == OUT_SLOTS && p.sl.dense) {
+                // the tile may overflow its slots: keep its dense ids, -1 first
+                if (owner) {
+                    int32_t *dn = p.sl.dense + static_cast<uint64_t>(p.sl.ubase + tile) * kDenseStride;
+#pragma unroll
+                    for (uint32_t h = 0; h < 2; ++h)
+#pragma unroll
+                        for (uint32_t g = 0; g < 4; ++g)
+                            *reinterpret_cast<int4 *>(dn + h * kPass + 16u * lane + 4u * g) = make_int4(-1, -1, -1, -1);
+                }
+                __syncwarp();
+            }
+            const uint32_t nchunks = (total + 255u) / 256u;
+            // more than one round (HELP forms): offer the rounds to the CTA's
+            // warps that run out of tiles (now or while this warp works), take
+            // rounds too, then wait until the helpers are done with this warp's
+            // queue and codes
+            const bool offer = HELP && nchunks > 1;
+            if (offer) {
+                __threadfence_block();  // the -1 prefill before the offer
+                __syncwarp();
+                if (lane == 0) {
+                    const uint32_t pub = my_help->pub + 1u;
+                    my_help->tile = tile;
+                    my_help->item = item;
+                    my_help->total = total;
+                    my_help->gpb = gpb;
+                    my_help->flags = (interior ? 1u : 0u) | (clean ? 2u : 0u);
+                    my_help->su = p.sl.ubase + tile;
+                    my_help->nchunks = nchunks;
+                    my_help->done = 0;
+                    my_help->pub = pub;
+                    __threadfence_block();
+                    atomicExch(&my_help->ticket, static_cast<unsigned long long>(pub) << 32);
+                    atomicAdd(offers, 1u);
+                }
+                __syncwarp();
+            }
+            for (uint32_t next = 0;;) {
+                uint32_t c = next++;
+                if (offer ? !claim_chunk(my_help, lane, c) : c >= nchunks) break;
+                finish_survivors<B, GT, MODE, 8, true>(p, tt, w, gpb, interior, clean, total - 256u * c, 0, lane,
+                                                       cnt, 256u * c, kCodeSpan, p.sl.ubase + tile);
+                __syncwarp();
+                if (offer && lane == 0) atomicAdd(&my_help->done, 1u);
+            }
+            if (offer && lane == 0) {
+                const unsigned long long t0 = global_timer();
+                while (*reinterpret_cast<volatile uint32_t *>(&my_help->done) < nchunks) {
+                    if (global_timer() - t0 > kWaitNs) {
+                        atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+                atomicSub(offers, 1u);
+            }
+            __syncwarp();
+            continue;
+        }
+
+        // 4b. at most one survivor per lane: issue its window-table load now
+        Flight f0 = empty_flight();
+        f0.tile = tile;
+        f0.item = item;
+        f0.gpb = gpb;
+        f0.interior = interior ? 1u : 0u;
+        if (static_cast<uint32_t>(lane) < total) {
+            const uint32_t e16 = w.queue[lane];
+            const uint32_t i = e16 & 0x7FFFu;
+            f0.pos = i;
+            if (e16 >> 15) {
+                f0.phase = kPhWalk;  // walk from the root
+                f0.state = 0;
+                f0.q = i;
+            } else {
+                const uint32_t x = code_window<B>(w.packed, i);
+                f0.val = __ldg(p.JK + (x & ((1u << (B * k)) - 1u)));
+                f0.phase = kPhJK;
+                f0.w2 = (x >> (B * k)) & ((1u << (B * k2)) - 1u);
+                bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(i + k + k2) <= n);
+                if (ok2 && !clean) {
+                    const uint32_t j = i + k;
+                    const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
+                    ok2 = (wi & ((1u << k2) - 1u)) == 0;
+                }
+                f0.ok2 = ok2 ? 1u : 0u;
+            }
+        }
+        // 5. the tile one back: issue its stride-table loads
+        flight_advance<B>(p, f1);
+        // 6. the tile two back: finish and write it
+        flight_finish<GT>(p, wk, w.cls8, f2);
+        flight_output<MODE>(p, wk, w, f2, lane, cnt);
+        f2 = f1;
+        f1 = f0;
+    }
+    // drain
+    flight_advance<B>(p, f1);
+    flight_finish<GT>(p, wk, w.cls8, f2);
+    flight_output<MODE>(p, wk, w, f2, lane, cnt);
+    flight_finish<GT>(p, wk, w.cls8, f1);
+    flight_output<MODE>(p, wk, w, f1, lane, cnt);
+
+    // no tiles left: help with the CTA's heavy tiles until every warp is done
+    // with its own (no tile is offered after that, and every offer is then
+    // finished: its owner waits for its chunks before going on)
+    if (HELP && lane == 0) {
+        __threadfence_block();
+        atomicAdd(retired, 1u);
+    }
+    if (HELP) {
+        unsigned long long t0 = 0;
+        if (lane == 0) t0 = global_timer();
+        for (;;) {
+            bool any = false;
+            uint32_t open = 0;
+            if (lane == 0) open = *reinterpret_cast<volatile uint32_t *>(offers);
+            open = __shfl_sync(kFull, open, 0);
+            for (int s = 0; open != 0 && s < nw; ++s) {
+                if (s == warp) continue;
+                HelpSlot *hs = reinterpret_cast<HelpSlot *>(smem + p.off_warp + static_cast<size_t>(s) * p.warp_bytes +
+                                                            p.off_help);
+                uint32_t c = 0;
+                while (claim_chunk(hs, lane, c)) {
+                    any = true;
+                    help_chunk<B, GT, MODE>(p, wk, smem, hs, static_cast<uint32_t>(s), c, lane, cnt);
+                }
+            }
+            if (any) continue;
+            uint32_t stop = 0;
+            if (lane == 0) {
+                if (*reinterpret_cast<volatile uint32_t *>(retired) >= static_cast<uint32_t>(nw)) {
+                    stop = 1;
+                } else if (global_timer() - t0 > kWaitNs) {
+                    atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
+                    stop = 1;
+                } else {
+                    __nanosleep(256);
+                }
+            }
+            if (__shfl_sync(kFull, stop, 0)) break;
+        }
+    }
+
+    if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
+    if (MODE == OUT_COUNT) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
+        if (lane == 0 && cnt) atomicAdd(p.count, cnt);
+    }
+}
+
+inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
+
+template <int B, typename GT, int MODE, bool BATCH, bool HELP>
+cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
+                       cudaStream_t stream) {
+    static bool configured[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH, HELP>;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    kernel<<<grid, block, smem, stream>>>(p);
+    return cudaGetLastError();
+}
+
+template <int B, typename GT, bool HELP>
+cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem,
+                         int max_smem, cudaStream_t stream) {
+    if constexpr (HELP) {  // one text only
+        switch (mode) {
+            case OUT_DENSE:
+                return launch_one<B, GT, OUT_DENSE, false, true>(p, grid, block, smem, max_smem, stream);
+            case OUT_COUNT:
+                return launch_one<B, GT, OUT_COUNT, false, true>(p, grid, block, smem, max_smem, stream);
+            case OUT_SLOTS:
+                return launch_one<B, GT, OUT_SLOTS, false, true>(p, grid, block, smem, max_smem, stream);
+            default:
+                return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (mode) {
+            case OUT_DENSE:
+                return p.batch ? launch_one<B, GT, OUT_DENSE, true, false>(p, grid, block, smem, max_smem, stream)
+                               : launch_one<B, GT, OUT_DENSE, false, false>(p, grid, block, smem, max_smem, stream);
+            case OUT_COUNT:
+                return launch_one<B, GT, OUT_COUNT, false, false>(p, grid, block, smem, max_smem, stream);
+            case OUT_SLOTS:
+                return p.batch ? launch_one<B, GT, OUT_SLOTS, true, false>(p, grid, block, smem, max_smem, stream)
+                               : launch_one<B, GT, OUT_SLOTS, false, false>(p, grid, block, smem, max_smem, stream);
+            default:
+                return cudaErrorInvalidValue;
+        }
+    }
+}
+
+}  // namespace filt
+
+// Launch of the forms that share heavy tiles (one text only), filter_help.cu.
+cudaError_t launch_filter_help(OutMode mode, const filt::FilterParams &p, uint32_t B, uint32_t gbits, uint32_t grid,
+                               uint32_t block, uint32_t smem, int max_smem, cudaStream_t stream);
+
+}  // namespace pfac
