@@ -36,7 +36,7 @@ GIB = 1 << 30
 # kernel): the 256 MiB capture summarised in
 # profiles/pfac_filter_pipe_acgt_256mib_full.md, scaled by 4 to the 1 GiB
 # launch.  Drop an entry whenever its kernel changes.
-KNOWN_TRAFFIC = {("sweep", GIB, "pfac_filter_pipe"): 5.432e9}
+KNOWN_TRAFFIC: dict = {}
 
 
 def kernel_name(info: dict, out_kind: str, kernel: str) -> str:
