@@ -20,7 +20,9 @@
 //     more characters), and rarely the goto table one character at a time.  A
 //     tile with at most one survivor per lane keeps them "in flight" across the
 //     next two tiles, so their dependent loads overlap other work; a tile with
-//     more finishes them at once, eight walks per lane;
+//     more finishes them at once, eight walks per lane per round of 256 (in the
+//     HELP forms, used for short texts, the rounds of such a tile are shared
+//     with the CTA's warps that have run out of tiles);
 //   * output: dense ids (one bulk async store of a constant -1 buffer when no
 //     survivor found a keyword, else -1 stores and the survivors' ids), a count
 //     (one atomic per warp), or slots (per tile the number of matches and the
