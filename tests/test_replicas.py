@@ -51,3 +51,27 @@ def test_single_process_is_its_own_slowest():
 
     assert bench.slowest(3.5) == 3.5
     assert bench.replica_gbs(1e9, 2, 1, 1000.0) == pytest.approx(2.0)
+
+
+def test_cpu_all_cores_context_matches_single_pass():
+    """The all-cores oracle figure of bench.py: contiguous stretches with
+    max-length halos in spawned processes give the same match count as one
+    serial pass over the same sample."""
+    import numpy as np
+
+    import bench
+    import oracle
+    from paper_1412_7789_gb300 import workloads
+
+    text, pats = workloads.sweep_acgt(1 << 21, seed=3, n_keywords=300)
+    # plant keywords across the stretch boundaries of a two-process split
+    g = np.random.default_rng(4)
+    text = text.copy()
+    for o in list(g.integers(0, text.size - 64, size=200)) + [text.size // 2 - 10, text.size // 2 - 1]:
+        p = pats[int(g.integers(0, len(pats)))]
+        text[o:o + len(p)] = np.frombuffer(p, dtype=np.uint8)
+    r = bench.cpu_parallel(text, pats, single_gbs=4e-3, budget_s=1.0, cores=2)
+    size = int(r["sample"].split()[1])
+    assert size == text.size
+    want = int(np.count_nonzero(oracle.pfac_ids(pats, text[:size]) >= 0))
+    assert r["matches"] == want and r["cores"] == 2
