@@ -8,7 +8,10 @@
  * its own walk through the keyword trie (section I, Fig. 3: all characters in
  * parallel) and stops at the first missing transition, so it reports, per
  * start position, only the longest keyword beginning there -- sub-pattern
- * outputs of the full machine are not reported (section II).
+ * outputs of the full machine are not reported (section II).  ac_match_full
+ * adds them back: every keyword that is a prefix of a start's longest keyword
+ * occurs there too, so the full machine's occurrences follow from the
+ * failureless results.
  *
  * Conventions shared by every call:
  *   - Keyword ids are 0-based in the order given to ac_compile.  -1 = no match.
