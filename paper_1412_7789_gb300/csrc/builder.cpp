@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <unordered_map>
 
 #include "ac.h"
@@ -45,6 +46,32 @@ inline uint32_t code_bits_for(uint32_t C) { return C <= 4 ? 2u : (C <= 16 ? 4u :
 template <typename T>
 inline int32_t g_at(const HostTables &h, uint64_t idx) {
     return static_cast<int32_t>(reinterpret_cast<const T *>(h.G.data())[idx]);
+}
+
+// body(lo, hi) over [0, n) in contiguous ranges on up to the machine's
+// hardware threads (at least min_per_thread items each).  Callers write
+// disjoint parts of their outputs, so results never depend on the split; a
+// range whose thread cannot be started runs on the calling thread.
+template <typename F>
+void parallel_ranges(uint64_t n, uint64_t min_per_thread, F body) {
+    uint64_t t = std::thread::hardware_concurrency();
+    t = std::min<uint64_t>(std::max<uint64_t>(t, 1), 32);
+    t = std::min<uint64_t>(t, std::max<uint64_t>(1, n / std::max<uint64_t>(min_per_thread, 1)));
+    if (t <= 1) {
+        body(uint64_t{0}, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(t);
+    for (uint64_t i = 0; i < t; ++i) {
+        const uint64_t lo = n * i / t, hi = n * (i + 1) / t;
+        try {
+            th.emplace_back(body, lo, hi);
+        } catch (...) {
+            body(lo, hi);
+        }
+    }
+    for (std::thread &x : th) x.join();
 }
 
 inline int32_t goto_entry(const HostTables &h, uint32_t s, uint32_t c) {
@@ -194,7 +221,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         if (opt.index_width == 16 && !fits16) return AC_ERR_INVALID_ARG;
         h.gbits = (opt.index_width == 32 || !fits16) ? 32u : 16u;
         const uint64_t cells = static_cast<uint64_t>(S) * h.W;
-        h.G.assign(cells * (h.gbits / 8), 0);
+        h.G.resize_unfilled(cells * (h.gbits / 8));  // every row is filled below
         auto put = [&](uint64_t idx, int32_t v) {
             if (h.gbits == 16)
                 reinterpret_cast<int16_t *>(h.G.data())[idx] = static_cast<int16_t>(v);
@@ -203,21 +230,27 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         };
         std::vector<uint32_t> kids(S, 0), child1(S, 0);  // children; the first child
         std::vector<uint8_t> code1(S, 0);                 // its code
-        for (uint32_t s = 0; s < S; ++s) {
-            int32_t dead = encode_dead(pathbest[s]);
-            uint64_t row = static_cast<uint64_t>(s) * h.W;
-            for (uint32_t c = 0; c < h.W; ++c) put(row + c, dead);
-            uint32_t old = order[s];
-            kids[s] = first[old + 1] - first[old];
-            for (uint32_t a = first[old]; a < first[old + 1]; ++a) {
-                const Edge &e = edges[adj[a]];
-                put(row + e.code, static_cast<int32_t>(newid[e.child]));
-                if (a == first[old]) {
-                    child1[s] = newid[e.child];
-                    code1[s] = static_cast<uint8_t>(e.code);
+        // rows in parallel (each range writes its own rows and entries)
+        parallel_ranges(S, 4096, [&](uint64_t s0, uint64_t s1) {
+            for (uint64_t s = s0; s < s1; ++s) {
+                const int32_t dead = encode_dead(pathbest[s]);
+                const uint64_t row = s * h.W;
+                if (h.gbits == 16)
+                    std::fill_n(reinterpret_cast<int16_t *>(h.G.data()) + row, h.W, static_cast<int16_t>(dead));
+                else
+                    std::fill_n(reinterpret_cast<int32_t *>(h.G.data()) + row, h.W, dead);
+                const uint32_t old = order[s];
+                kids[s] = first[old + 1] - first[old];
+                for (uint32_t a = first[old]; a < first[old + 1]; ++a) {
+                    const Edge &e = edges[adj[a]];
+                    put(row + e.code, static_cast<int32_t>(newid[e.child]));
+                    if (a == first[old]) {
+                        child1[s] = newid[e.child];
+                        code1[s] = static_cast<uint8_t>(e.code);
+                    }
                 }
             }
-        }
+        });
         std::vector<Edge>().swap(edges);
 
         h.B = code_bits_for(h.C);

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include <cuda_runtime_api.h>
@@ -46,6 +47,21 @@ struct BuildOptions {
     bool chains = true;         // chain records for the deep states
 };
 
+// A byte buffer sized without a fill: its owner writes every byte (the
+// builder fills the goto table's rows in parallel, so a zero fill first would
+// be one more serial pass over up to a gigabyte).
+struct RawBytes {
+    std::unique_ptr<uint8_t[]> p;
+    size_t n = 0;
+    uint8_t *data() { return p.get(); }
+    const uint8_t *data() const { return p.get(); }
+    size_t size() const { return n; }
+    void resize_unfilled(size_t m) {  // throws std::bad_alloc
+        p.reset(new uint8_t[m]);
+        n = m;
+    }
+};
+
 // Host-side automaton: everything the kernels need, in the layout they use.
 struct HostTables {
     uint32_t nkw = 0;        // keywords
@@ -69,7 +85,7 @@ struct HostTables {
     int hash_shift = -1;
     uint8_t hash_code[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint8_t hash_byte[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    std::vector<uint8_t> G;          // S * W entries of gbits
+    RawBytes G;                      // S * W entries of gbits
     bool filter = false;             // B <= 4: root filter + window table instead of J
     std::vector<uint32_t> F;         // filter bits, 2^(B*k) (at least 4 words)
     std::vector<int32_t> JK;         // window table, 2^(B*k) entries
