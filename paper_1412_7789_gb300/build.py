@@ -30,7 +30,7 @@ def _nvcc() -> str:
 
 
 def _compile_cmd(src: str, obj: str) -> list[str]:
-    common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC, "-Xcompiler", "-fPIC"]
+    common = ["-O3", "-std=c++17", "-I", INCLUDE, "-I", CSRC, "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread"]
     if src.endswith(".cu"):
         return [_nvcc(), *ARCH, "-lineinfo", *common, "-c", src, "-o", obj]
     return [_nvcc(), *common, "-x", "c++", "-c", src, "-o", obj]
@@ -69,7 +69,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 print(err)
     if force or jobs or _stale(LIB_PATH, objs):
         tmp = LIB_PATH + ".tmp%d" % os.getpid()
-        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"])
+        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lpthread"])
         os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
