@@ -364,3 +364,26 @@ def test_full_expansion_equals_serial_machine(lib):
             ends, fids = oracle.full_occurrences(pats, text)
             want = sorted(((int(e) - len(pats[d]) + 1, int(e), int(d)) for e, d in zip(ends, fids)))
             assert got == [(e, d) for _, e, d in want], (alpha, case)
+
+
+def test_parallel_build_is_deterministic(lib):
+    """The goto table's rows are filled on several host threads: two builds of
+    the same large keyword set export byte-identical tables, and every entry
+    is either a larger child state or an encoded result."""
+    text, pats = workloads.zipf_byte(1 << 20, seed=5, n_keywords=3000)
+    tabs = []
+    for _ in range(2):
+        h = api.ac_compile(pats, host_only=True)
+        try:
+            tabs.append(api.ac_export_tables(h))
+            info = api.ac_info(h)
+        finally:
+            api.ac_destroy(h)
+    (c0, g0, d0), (c1, g1, d1) = tabs
+    assert np.array_equal(c0, c1) and np.array_equal(d0, d1) and np.array_equal(g0, g1)
+    G = g0.reshape(info["n_states"], info["row_width"]).astype(np.int64)
+    rows = np.arange(info["n_states"])[:, None]
+    live = G > 0
+    assert np.all(G[live] > np.broadcast_to(rows, G.shape)[live])  # BFS order: children after parents
+    assert np.all(G[~live] <= -1)  # encoded results -(id + 2), id >= -1
+    assert np.all(-G[~live] - 2 < len(pats))
