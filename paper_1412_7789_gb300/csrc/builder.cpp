@@ -26,7 +26,6 @@
 #include <cstring>
 #include <new>
 #include <thread>
-#include <unordered_map>
 
 #include "ac.h"
 #include "pfac_internal.h"
@@ -47,6 +46,63 @@ template <typename T>
 inline int32_t g_at(const HostTables &h, uint64_t idx) {
     return static_cast<int32_t>(reinterpret_cast<const T *>(h.G.data())[idx]);
 }
+
+// The children of the trie under construction: open addressing over keys
+// (state << 8) | code with linear probing, Knuth's multiplicative hash, and a
+// doubling of the table once it is half full.
+class ChildTable {
+public:
+    explicit ChildTable(uint64_t expect) {
+        uint32_t bits = 6;
+        while ((1ull << bits) < 2 * expect) ++bits;
+        rebuild(bits);
+    }
+    // The child stored under key; if none, t is stored and *inserted set.
+    uint32_t find_or_insert(uint64_t key, uint32_t t, bool *inserted) {
+        if ((used_ + 1) * 2 > keys_.size()) rebuild(bits_ + 1);
+        const uint64_t mask = keys_.size() - 1;
+        for (uint64_t i = slot(key);; i = (i + 1) & mask) {
+            if (keys_[i] == kEmpty) {
+                keys_[i] = key;
+                vals_[i] = t;
+                ++used_;
+                *inserted = true;
+                return t;
+            }
+            if (keys_[i] == key) {
+                *inserted = false;
+                return vals_[i];
+            }
+        }
+    }
+
+private:
+    static constexpr uint64_t kEmpty = ~0ull;  // keys are below 2^39
+    uint64_t slot(uint64_t key) const { return (key * 0x9E3779B97F4A7C15ull) >> (64 - bits_); }
+    void rebuild(uint32_t bits) {
+        std::vector<uint64_t> ok;
+        std::vector<uint32_t> ov;
+        ok.swap(keys_);
+        ov.swap(vals_);
+        bits_ = bits;
+        keys_.assign(1ull << bits, kEmpty);
+        vals_.assign(1ull << bits, 0u);
+        used_ = 0;
+        const uint64_t mask = keys_.size() - 1;
+        for (uint64_t j = 0; j < ok.size(); ++j) {
+            if (ok[j] == kEmpty) continue;
+            uint64_t i = slot(ok[j]);
+            while (keys_[i] != kEmpty) i = (i + 1) & mask;
+            keys_[i] = ok[j];
+            vals_[i] = ov[j];
+            ++used_;
+        }
+    }
+    std::vector<uint64_t> keys_;
+    std::vector<uint32_t> vals_;
+    uint64_t used_ = 0;
+    uint32_t bits_ = 0;
+};
 
 // body(lo, hi) over [0, n) in contiguous ranges on up to the machine's
 // hardware threads (at least min_per_thread items each).  Callers write
@@ -146,8 +202,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         }
 
         // 2. trie insertion (provisional ids in creation order)
-        std::unordered_map<uint64_t, uint32_t> child;
-        child.reserve(static_cast<size_t>(std::min<uint64_t>(total, 1ull << 26)) + 16);
+        ChildTable child(std::min<uint64_t>(total, 1ull << 26) + 16);
         std::vector<int32_t> kw_at{-1};   // lowest keyword id ending at each provisional state
         std::vector<uint32_t> kw_state(nkw);  // each keyword's provisional state
         std::vector<Edge> edges;
@@ -156,23 +211,19 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             uint32_t s = 0;
             for (uint32_t j = 0; j < lens[id]; ++j) {
                 uint32_t c = static_cast<uint32_t>(h.cls[patterns[id][j]]);
-                uint64_t key = (static_cast<uint64_t>(s) << 8) | c;
-                auto it = child.find(key);
-                if (it == child.end()) {
-                    uint32_t t = static_cast<uint32_t>(kw_at.size());
+                const uint64_t key = (static_cast<uint64_t>(s) << 8) | c;
+                bool inserted = false;
+                const uint32_t t = child.find_or_insert(key, static_cast<uint32_t>(kw_at.size()), &inserted);
+                if (inserted) {
                     kw_at.push_back(-1);
-                    child.emplace(key, t);
                     edges.push_back({s, c, t});
-                    s = t;
-                } else {
-                    s = it->second;
                 }
+                s = t;
             }
             if (kw_at[s] < 0) kw_at[s] = static_cast<int32_t>(id);  // ids arrive in increasing order
             kw_state[id] = s;
         }
-        child.clear();
-        child.rehash(0);
+        child = ChildTable(0);  // release the table
         const uint32_t S = static_cast<uint32_t>(kw_at.size());
         h.S = S;
 
