@@ -185,6 +185,22 @@ ac_status ac_export_chains(ac_handle h, uint32_t *s_chain, uint32_t *records, ui
 ac_status ac_export_full(ac_handle h, uint32_t *records, uint32_t *dups, uint32_t *max_chain);
 
 /*
+ * Root filter and window table of an automaton whose keyword bytes take 2- or
+ * 4-bit codes (for inspection and tests; host memory).  A window value v holds
+ * the codes of k consecutive text bytes, B bits each, the first byte lowest.
+ *   F   uint32[*f_words]: the filter bit of v is bit 31 - (v & 31) of word
+ *       v >> 5 (set when the walk from the root is still alive after the k
+ *       bytes, or found a keyword in them); windows of fewer than 5 bits are
+ *       repeated over the 32 bits of word 0.
+ *   JK  int32[*jk_entries] = 2^(B k): the state reached after the k bytes, or
+ *       -(result + 2) when the walk stopped inside them (result -1: none).
+ * *B = 0 and zero sizes for an automaton without a filter (8-bit codes).
+ * Call with NULL arrays to get the sizes, then again with room for them.
+ */
+ac_status ac_export_filter(ac_handle h, uint32_t *F, int32_t *JK, uint32_t *B, uint32_t *k, uint64_t *f_words,
+                           uint64_t *jk_entries);
+
+/*
  * Dense matching.  d_out_ids[i] = id of the longest keyword starting at
  * d_text[i] (within the n bytes), or -1.  d_text: n bytes, d_out_ids: n int32,
  * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is

@@ -96,6 +96,8 @@ _SIGS = {
     "ac_match_compact": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_match_full": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_export_full": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32)]),
+    "ac_export_filter": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "ac_count": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_host": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_compact_static": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
@@ -239,6 +241,19 @@ def ac_export_full(h: int, n_keywords: int):
     mc = ctypes.c_uint32()
     _check(lib().ac_export_full(h, rec.ctypes.data, dups.ctypes.data, ctypes.byref(mc)), "ac_export_full")
     return rec, dups, int(mc.value)
+
+
+def ac_export_filter(h: int):
+    """(B, k, F uint32[...], JK int32[...]) of a 2-/4-bit-code automaton, or (0, 0, empty, empty)."""
+    B, k = ctypes.c_uint32(), ctypes.c_uint32()
+    nf, nj = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().ac_export_filter(h, None, None, ctypes.byref(B), ctypes.byref(k), ctypes.byref(nf), ctypes.byref(nj)),
+           "ac_export_filter")
+    F = np.zeros(nf.value, dtype=np.uint32)
+    JK = np.zeros(nj.value, dtype=np.int32)
+    _check(lib().ac_export_filter(h, F.ctypes.data, JK.ctypes.data, ctypes.byref(B), ctypes.byref(k), ctypes.byref(nf),
+                                  ctypes.byref(nj)), "ac_export_filter")
+    return int(B.value), int(k.value), F, JK
 
 
 def ac_match(h: int, text, n: int, out, stream=None):

@@ -425,6 +425,19 @@ ac_status ac_export_full(ac_handle h, uint32_t *records, uint32_t *dups, uint32_
     return AC_OK;
 }
 
+ac_status ac_export_filter(ac_handle h, uint32_t *F, int32_t *JK, uint32_t *B, uint32_t *k, uint64_t *f_words,
+                           uint64_t *jk_entries) {
+    if (!h || !B || !k || !f_words || !jk_entries) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    *B = t.filter ? t.B : 0u;
+    *k = t.filter ? t.k : 0u;
+    *f_words = t.filter ? t.F.size() : 0u;
+    *jk_entries = t.filter ? t.JK.size() : 0u;
+    if (t.filter && F) std::memcpy(F, t.F.data(), t.F.size() * sizeof(uint32_t));
+    if (t.filter && JK) std::memcpy(JK, t.JK.data(), t.JK.size() * sizeof(int32_t));
+    return AC_OK;
+}
+
 ac_status ac_set_kernel(ac_handle h, ac_kernel kernel) {
     if (!h) return AC_ERR_INVALID_ARG;
     switch (kernel) {

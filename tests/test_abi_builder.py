@@ -387,3 +387,48 @@ def test_parallel_build_is_deterministic(lib):
     assert np.all(G[live] > np.broadcast_to(rows, G.shape)[live])  # BFS order: children after parents
     assert np.all(G[~live] <= -1)  # encoded results -(id + 2), id >= -1
     assert np.all(-G[~live] - 2 < len(pats))
+
+
+@pytest.mark.parametrize("alpha,lmin,lmax", [(b"ACGT", 4, 40), (b"abcdefghijkl", 2, 12), (b"ACGT", 1, 2),
+                                             (b"ACG", 3, 9)])
+def test_root_filter_and_window_table(lib, alpha, lmin, lmax):
+    """Every window of k codes: the window table holds the state the goto
+    table's walk reaches (or its encoded result), and the filter bit read the
+    way the kernel reads it -- the word at byte offset (w >> 3) & mask rotated
+    left by w's low five bits, bit 31 -- is set exactly when that walk is
+    alive or found a keyword, whatever codes follow the window in w."""
+    g = np.random.Generator(np.random.PCG64(len(alpha) * 100 + lmax))
+    a = np.frombuffer(alpha, dtype=np.uint8)
+    pats = [bytes(a[g.integers(0, a.size, size=int(g.integers(lmin, lmax + 1)))]) for _ in range(300)]
+    h = api.ac_compile(pats, host_only=True)
+    try:
+        B, k, F, JK = api.ac_export_filter(h)
+        cls, G, depth = api.ac_export_tables(h)
+        info = api.ac_info(h)
+    finally:
+        api.ac_destroy(h)
+    assert B in (2, 4) and k >= 1 and JK.size == 1 << (B * k)
+    C, W = info["n_classes"], info["row_width"]
+    G = G.reshape(info["n_states"], W).astype(np.int64)
+    v = np.arange(1 << (B * k), dtype=np.int64)
+    s = np.zeros(v.size, dtype=np.int64)
+    res = np.full(v.size, -2, dtype=np.int64)  # -2: still alive
+    for i in range(k):
+        c = (v >> (B * i)) & ((1 << B) - 1)
+        e = G[s, np.where(c < C, c, C)]  # codes no keyword byte takes read the end column
+        live = res == -2
+        stop = live & (e < 0)
+        res[stop] = -e[stop] - 2
+        s = np.where(live & (e > 0), e, s)
+    alive = res == -2
+    assert np.array_equal(JK, np.where(alive, s, -(res + 2)))
+    want = alive | (res >= 0)
+    wb = B * k
+    famask = (((1 << wb) if wb >= 5 else 32) // 8 - 1) & ~3
+    for garbage in (0, 1, 0x5A5A5A5A, 0xFFFFFFFF):
+        win = (v | (garbage << wb)) & 0xFFFFFFFF
+        words = F[((win >> 3) & famask) >> 2].astype(np.int64)
+        r = win & 31
+        rot = ((words << r) | (words >> ((32 - r) & 31))) & 0xFFFFFFFF
+        rot = np.where(r == 0, words, rot)
+        assert np.array_equal((rot >> 31) & 1, want.astype(np.int64)), (alpha, garbage)
