@@ -201,6 +201,17 @@ ac_status ac_export_filter(ac_handle h, uint32_t *F, int32_t *JK, uint32_t *B, u
                            uint64_t *jk_entries);
 
 /*
+ * Stride table (for inspection and tests; host memory): for the r-th state at
+ * depth k (state base_k + r, BFS order) and a window v of k2 more codes (B bits
+ * each, first lowest; B as for ac_export_filter), J2[(r << (B k2)) | v] is the
+ * state reached after those codes, or -(result + 2) when the walk stopped in
+ * them.  *k2 = 0 and *entries = 0 when the automaton has no stride table.
+ * Call with J2 = NULL to get the sizes.
+ */
+ac_status ac_export_stride(ac_handle h, int32_t *J2, uint32_t *k2, uint32_t *base_k, uint32_t *count_k,
+                           uint64_t *entries);
+
+/*
  * Dense matching.  d_out_ids[i] = id of the longest keyword starting at
  * d_text[i] (within the n bytes), or -1.  d_text: n bytes, d_out_ids: n int32,
  * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is

@@ -96,6 +96,8 @@ _SIGS = {
     "ac_match_compact": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_match_full": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_export_full": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32)]),
+    "ac_export_stride": (ctypes.c_int, [_H, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                        ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
     "ac_export_filter": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "ac_count": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
@@ -254,6 +256,18 @@ def ac_export_filter(h: int):
     _check(lib().ac_export_filter(h, F.ctypes.data, JK.ctypes.data, ctypes.byref(B), ctypes.byref(k), ctypes.byref(nf),
                                   ctypes.byref(nj)), "ac_export_filter")
     return int(B.value), int(k.value), F, JK
+
+
+def ac_export_stride(h: int):
+    """(k2, base_k, count_k, J2 int32[...]) -- see ac.h."""
+    k2, bk, ck = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    ne = ctypes.c_uint64()
+    _check(lib().ac_export_stride(h, None, ctypes.byref(k2), ctypes.byref(bk), ctypes.byref(ck), ctypes.byref(ne)),
+           "ac_export_stride")
+    J2 = np.zeros(ne.value, dtype=np.int32)
+    _check(lib().ac_export_stride(h, J2.ctypes.data, ctypes.byref(k2), ctypes.byref(bk), ctypes.byref(ck),
+                                  ctypes.byref(ne)), "ac_export_stride")
+    return int(k2.value), int(bk.value), int(ck.value), J2
 
 
 def ac_match(h: int, text, n: int, out, stream=None):

@@ -438,6 +438,18 @@ ac_status ac_export_filter(ac_handle h, uint32_t *F, int32_t *JK, uint32_t *B, u
     return AC_OK;
 }
 
+ac_status ac_export_stride(ac_handle h, int32_t *J2, uint32_t *k2, uint32_t *base_k, uint32_t *count_k,
+                           uint64_t *entries) {
+    if (!h || !k2 || !base_k || !count_k || !entries) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    *k2 = t.J2.empty() ? 0u : t.k2;
+    *base_k = t.base_k;
+    *count_k = t.count_k;
+    *entries = t.J2.size();
+    if (J2 && !t.J2.empty()) std::memcpy(J2, t.J2.data(), t.J2.size() * sizeof(int32_t));
+    return AC_OK;
+}
+
 ac_status ac_set_kernel(ac_handle h, ac_kernel kernel) {
     if (!h) return AC_ERR_INVALID_ARG;
     switch (kernel) {

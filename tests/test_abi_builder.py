@@ -432,3 +432,36 @@ def test_root_filter_and_window_table(lib, alpha, lmin, lmax):
         rot = ((words << r) | (words >> ((32 - r) & 31))) & 0xFFFFFFFF
         rot = np.where(r == 0, words, rot)
         assert np.array_equal((rot >> 31) & 1, want.astype(np.int64)), (alpha, garbage)
+
+
+@pytest.mark.parametrize("alpha,lmin,lmax", [(b"ACGT", 12, 40), (b"abcdefghijkl", 6, 20)])
+def test_stride_table(lib, alpha, lmin, lmax):
+    """Every stride-table entry equals the goto table's walk of its k2 codes
+    from its depth-k state."""
+    g = np.random.Generator(np.random.PCG64(len(alpha) * 7 + lmin))
+    a = np.frombuffer(alpha, dtype=np.uint8)
+    pats = [bytes(a[g.integers(0, a.size, size=int(g.integers(lmin, lmax + 1)))]) for _ in range(400)]
+    h = api.ac_compile(pats, host_only=True)
+    try:
+        B, k, F, JK = api.ac_export_filter(h)
+        k2, base_k, count_k, J2 = api.ac_export_stride(h)
+        cls, G, depth = api.ac_export_tables(h)
+        info = api.ac_info(h)
+    finally:
+        api.ac_destroy(h)
+    assert k2 >= 2 and J2.size == count_k << (B * k2)
+    assert base_k == int(depth[:k].sum()) and count_k == int(depth[k])
+    C, W = info["n_classes"], info["row_width"]
+    G = G.reshape(info["n_states"], W).astype(np.int64)
+    idx = np.arange(J2.size, dtype=np.int64)
+    v = idx & ((1 << (B * k2)) - 1)
+    s = base_k + (idx >> (B * k2))
+    res = np.full(idx.size, -2, dtype=np.int64)
+    for i in range(k2):
+        c = (v >> (B * i)) & ((1 << B) - 1)
+        e = G[s, np.where(c < C, c, C)]
+        live = res == -2
+        stop = live & (e < 0)
+        res[stop] = -e[stop] - 2
+        s = np.where(live & (e > 0), e, s)
+    assert np.array_equal(J2, np.where(res == -2, s, -(res + 2)))
