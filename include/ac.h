@@ -212,6 +212,17 @@ ac_status ac_export_stride(ac_handle h, int32_t *J2, uint32_t *k2, uint32_t *bas
                            uint64_t *entries);
 
 /*
+ * Root jump table of an automaton with 8-bit codes (for inspection and tests;
+ * host memory): for a window v of k codes (8 bits each, the first byte lowest),
+ * J[v] is the walk's result (>= -1) when it stopped inside the window,
+ * -(2 + r) when it reached the r-th state at depth k (state base_k + r), or
+ * -32768 when a result does not fit 15 bits (the kernels then walk the goto
+ * table from the root).  *k = 0 and *entries = 0 without a jump table.  Call
+ * with J = NULL to get the sizes.
+ */
+ac_status ac_export_jump(ac_handle h, int16_t *J, uint32_t *k, uint32_t *base_k, uint64_t *entries);
+
+/*
  * Dense matching.  d_out_ids[i] = id of the longest keyword starting at
  * d_text[i] (within the n bytes), or -1.  d_text: n bytes, d_out_ids: n int32,
  * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is

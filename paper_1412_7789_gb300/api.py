@@ -98,6 +98,8 @@ _SIGS = {
     "ac_export_full": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32)]),
     "ac_export_stride": (ctypes.c_int, [_H, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
+    "ac_export_jump": (ctypes.c_int, [_H, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                      ctypes.POINTER(ctypes.c_uint64)]),
     "ac_export_filter": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "ac_count": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
@@ -268,6 +270,17 @@ def ac_export_stride(h: int):
     _check(lib().ac_export_stride(h, J2.ctypes.data, ctypes.byref(k2), ctypes.byref(bk), ctypes.byref(ck),
                                   ctypes.byref(ne)), "ac_export_stride")
     return int(k2.value), int(bk.value), int(ck.value), J2
+
+
+def ac_export_jump(h: int):
+    """(k, base_k, J int16[...]) of an 8-bit-code automaton -- see ac.h."""
+    k, bk = ctypes.c_uint32(), ctypes.c_uint32()
+    ne = ctypes.c_uint64()
+    _check(lib().ac_export_jump(h, None, ctypes.byref(k), ctypes.byref(bk), ctypes.byref(ne)), "ac_export_jump")
+    J = np.zeros(ne.value, dtype=np.int16)
+    _check(lib().ac_export_jump(h, J.ctypes.data, ctypes.byref(k), ctypes.byref(bk), ctypes.byref(ne)),
+           "ac_export_jump")
+    return int(k.value), int(bk.value), J
 
 
 def ac_match(h: int, text, n: int, out, stream=None):

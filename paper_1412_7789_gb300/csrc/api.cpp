@@ -450,6 +450,17 @@ ac_status ac_export_stride(ac_handle h, int32_t *J2, uint32_t *k2, uint32_t *bas
     return AC_OK;
 }
 
+ac_status ac_export_jump(ac_handle h, int16_t *J, uint32_t *k, uint32_t *base_k, uint64_t *entries) {
+    if (!h || !k || !base_k || !entries) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    const bool has = !t.filter && t.k > 0 && !t.J.empty();
+    *k = has ? t.k : 0u;
+    *base_k = t.base_k;
+    *entries = has ? (1ull << (t.B * t.k)) : 0u;  // J is padded to at least 8 entries
+    if (has && J) std::memcpy(J, t.J.data(), static_cast<size_t>(*entries) * sizeof(int16_t));
+    return AC_OK;
+}
+
 ac_status ac_set_kernel(ac_handle h, ac_kernel kernel) {
     if (!h) return AC_ERR_INVALID_ARG;
     switch (kernel) {

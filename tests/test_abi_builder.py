@@ -465,3 +465,35 @@ def test_stride_table(lib, alpha, lmin, lmax):
         res[stop] = -e[stop] - 2
         s = np.where(live & (e > 0), e, s)
     assert np.array_equal(J2, np.where(res == -2, s, -(res + 2)))
+
+
+@pytest.mark.parametrize("kw", [{}, {"class_compress": False}])
+def test_root_jump_table(lib, kw):
+    """Every entry of the 8-bit root jump table equals the goto table's walk of
+    its two bytes: the result where the walk stopped, or the index of the
+    depth-2 state it reached."""
+    text, pats = workloads.zipf_byte(1 << 18, seed=9, n_keywords=2000)
+    h = api.ac_compile(pats, host_only=True, **kw)
+    try:
+        k, base_k, J = api.ac_export_jump(h)
+        cls, G, depth = api.ac_export_tables(h)
+        info = api.ac_info(h)
+    finally:
+        api.ac_destroy(h)
+    assert info["code_bits"] == 8 and k == 2 and J.size == 1 << 16
+    C, W = info["n_classes"], info["row_width"]
+    G = G.reshape(info["n_states"], W).astype(np.int64)
+    v = np.arange(J.size, dtype=np.int64)
+    s = np.zeros(v.size, dtype=np.int64)
+    res = np.full(v.size, -2, dtype=np.int64)
+    for i in range(k):
+        c = (v >> (8 * i)) & 0xFF  # class codes (identity when 256 columns)
+        e = G[s, np.where(c < C, c, C)]
+        live = res == -2
+        stop = live & (e < 0)
+        res[stop] = -e[stop] - 2
+        s = np.where(live & (e > 0), e, s)
+    want = np.where(res == -2, -(2 + (s - base_k)), res)
+    slow = J == -32768
+    assert np.array_equal(J[~slow].astype(np.int64), want[~slow])
+    assert np.all(want[slow] > 32767) and np.all((res[slow] > 32767))
