@@ -497,3 +497,59 @@ def test_root_jump_table(lib, kw):
     slow = J == -32768
     assert np.array_equal(J[~slow].astype(np.int64), want[~slow])
     assert np.all(want[slow] > 32767) and np.all((res[slow] > 32767))
+
+
+def test_c_program_uses_the_library(lib, tmp_path):
+    """A plain C program (no Python) compiles against ac.h, links the shared
+    library and builds a host-only automaton: he/she/his/hers gives 10 states,
+    5 classes (h, e, s, i, r) in 4-bit codes, and the exported goto table takes
+    the walk "she" to a state whose end column reports keyword 1."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include "ac.h"
+int main(void) {
+    const char *kw[4] = {"he", "she", "his", "hers"};
+    const uint8_t *p[4];
+    uint32_t len[4];
+    for (int i = 0; i < 4; ++i) { p[i] = (const uint8_t *)kw[i]; len[i] = (uint32_t)strlen(kw[i]); }
+    ac_options o;
+    ac_default_options(&o);
+    o.host_only = 1;
+    ac_handle h = NULL;
+    if (ac_compile(p, len, 4, &o, &h) != AC_OK) return 2;
+    ac_info_t info;
+    if (ac_info(h, &info) != AC_OK) return 3;
+    int16_t cls[256];
+    size_t cells = (size_t)info.n_states * info.row_width;
+    int32_t *g = malloc(cells * sizeof(int32_t));
+    if (info.index_width != 16 && info.index_width != 32) return 4;
+    void *raw = malloc(cells * (info.index_width / 8));
+    uint32_t *depth = malloc((info.max_len + 1) * sizeof(uint32_t));
+    if (ac_export_tables(h, cls, raw, depth) != AC_OK) return 5;
+    for (size_t i = 0; i < cells; ++i)
+        g[i] = info.index_width == 16 ? ((int16_t *)raw)[i] : ((int32_t *)raw)[i];
+    int32_t s = 0;
+    const char *w = "she";
+    for (int i = 0; i < 3; ++i) s = g[(size_t)s * info.row_width + cls[(uint8_t)w[i]]];
+    int32_t end = g[(size_t)s * info.row_width + info.n_classes];  /* end column: stop here */
+    printf("%u %u %u %d\n", info.n_states, info.n_classes, info.code_bits, -end - 2);
+    ac_destroy(h);
+    free(g); free(raw); free(depth);
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(api.library_path())
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lpfac",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out == ["10", "5", "4", "1"], out
