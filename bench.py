@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GB/s text scanned (1 GB300) & % HBM roofline; batch/serve p50/p99 vs plain PFAC"
 GIB = 1 << 30
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the kernel as it stands, keyed by (workload, text bytes,
@@ -399,6 +400,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         traffic = KNOWN_TRAFFIC.get((args.workload, n, kname))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
+            # context: the nominal HBM3e figure (7.9 TB/s) beside the measured copy peak
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
             "algorithmic_bytes_per_launch": algo_bytes, "kernel": kname}
 
     extra = {"automaton": {k: info[k] for k in ("n_states", "n_classes", "index_width", "code_bits",
