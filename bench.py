@@ -34,9 +34,9 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the kernel as it stands, keyed by (workload, text bytes,
-# kernel): the 256 MiB capture summarised in
-# profiles/pfac_filter_pipe_acgt_256mib_full.md, scaled by 4 to the 1 GiB
-# launch.  Drop an entry whenever its kernel changes.
+# kernel): a capture of a 256 MiB launch of the same workload, scaled by 4 to
+# the 1 GiB launch (the traffic grows with the positions).  Drop an entry
+# whenever its kernel changes.
 KNOWN_TRAFFIC: dict = {}
 
 
@@ -386,8 +386,20 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         for _ in range(reps):
             api.ac_match_host(a.handle, int(ht.data_ptr()), n, int(ho.data_ptr()), stream)
         e2e_s = slowest((time.perf_counter() - t0) / reps, dist, dev)
+        # the legs alone, for the bound a perfect overlap would reach: the text
+        # in (pinned host -> device), the kernel, the ids out (device -> pinned host)
+        legs = {}
+        for name, fn in (("h2d", lambda: text.copy_(ht, non_blocking=True)),
+                         ("d2h", lambda: ho.copy_(out, non_blocking=True))):
+            fn()
+            ms = statistics.median(_event_ms(stream, fn, 3))
+            legs[name + "_ms"] = ms
+            legs[name + "_gbs"] = (n if name == "h2d" else 4 * n) / (ms * 1e-3) / 1e9
+        legs["kernel_ms"] = statistics.mean(per)
+        legs["overlap_bound_ms"] = max(legs["h2d_ms"], legs["d2h_ms"], legs["kernel_ms"])
         e2e = {"value": replica_gbs(n, 1, world, 1e3 * e2e_s), "unit": "GB/s", "h2d_bytes_per_step": n,
-               "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * e2e_s}
+               "d2h_bytes_per_step": 4 * n, "ms_per_step": 1e3 * e2e_s, "legs": legs,
+               "api": "ac_match_host (pinned host text in, ids out, 64 MiB chunks on three streams)"}
         del ht, ho
 
     peak, peak_kind = load_peaks()

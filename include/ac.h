@@ -279,27 +279,49 @@ ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t 
 ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
 
 /*
+ * Bounded waits (no counterpart in the paper).  Every wait inside this
+ * handle's kernels -- a bulk copy landing on its mbarrier, an owner warp
+ * waiting for the warps of its CTA to finish the rounds of a heavy tile it
+ * shared, warps without work waiting for the rest of their CTA -- gives up
+ * after limit_ns nanoseconds of %globaltimer (0 = the default, 2 s), latches
+ * AC_ERR_TIMEOUT in the device error word (ac_device_status) and lets the
+ * kernel finish; no wait spins without a limit.
+ * stall_help = 1 is a test aid for the shared-tile wait: an owner warp waits
+ * for one more finished round than its tile has, a count nothing ever
+ * reaches, so that wait runs out after limit_ns while every round is done
+ * (results stay exact).  It applies to single texts short enough to share
+ * heavy tiles (ac_match, ac_count, ac_match_compact on small-alphabet
+ * automata).  Do not change a handle's limit while work using it is being
+ * enqueued from another thread.
+ */
+ac_status ac_set_wait_limit(ac_handle h, uint64_t limit_ns, int32_t stall_help);
+
+/*
  * Compacted matching that allocates no device memory.  Same arguments, results
  * and asynchrony as ac_match_compact; the difference is where its scratch
  * lives.  ac_match_compact takes its scratch (a tile counter, per-tile counts,
  * prefix sums and match slots, and a dense fallback) from a stream-ordered pool
  * (cudaMallocFromPoolAsync) on every call; this one keeps no dense fallback and
- * matches a tile with more than 32 matches again in its gather step.  Some callers cannot allocate while they match: a serving process
- * that hands all free device memory to another framework's caching allocator
- * at start-up (later cudaMalloc / cudaMallocAsync calls then fail or take
- * memory that allocator counts on), or a latency-critical loop whose rules
- * forbid allocator calls after initialisation.  This entry point uses instead
- * one file-scope device array of AC_STATIC_SCRATCH_BYTES that every GPU loading
- * the library holds until the process exits.
+ * matches a tile with more than 32 matches again in its gather step.  Some
+ * callers cannot allocate while they match: a serving process that hands all
+ * free device memory to another framework's caching allocator at start-up
+ * (later cudaMalloc / cudaMallocAsync calls then fail or take memory that
+ * allocator counts on), or a latency-critical loop whose rules forbid
+ * allocator calls after initialisation.  This entry point uses instead one
+ * file-scope device array of AC_STATIC_SCRATCH_BYTES (5 MiB) per device.
+ *   - The array is committed on a device, and its device address looked up
+ *     (cudaGetSymbolAddress, once per device), when the first handle is
+ *     compiled there (ac_compile), and held until the process exits.  So
+ *     compile before another allocator reserves the device's free memory, and
+ *     before any stream capture.  A call never allocates.
  *   - Texts longer than AC_STATIC_MAX_TEXT bytes are rejected with
  *     AC_ERR_BUDGET before any work is enqueued.
- *   - The first call on a device looks the array's device address up
- *     (cudaGetSymbolAddress, once per device); make that first call before any
- *     stream capture.
  *   - Every call clears the part of the array it uses (cudaMemsetAsync on
  *     `stream`) and then launches.  All calls share the one array: calls whose
  *     work overlaps on the GPU (different streams, or host threads without
  *     ordering between them) race and give wrong results.  Serialise them.
+ *   - It runs the kernel and launch shape chosen for the handle (ac_set_kernel,
+ *     ac_autotune), like ac_match_compact.
  *   - The paper has no counterpart: this is a deployment variant of the
  *     compacted output.
  */
@@ -475,6 +497,13 @@ ac_status ac_server_drain(ac_server s);
 
 /* Drain, stop the worker and free the server (not the handles). */
 ac_status ac_server_destroy(ac_server s);
+
+/* Diagnostics (no counterpart in the paper): bytes of the library's
+ * stream-ordered scratch pool on the calling device that are allocated now
+ * (*used_now) and at most since the last reset (*used_high); reset_high = 1
+ * then resets that high-water mark to the current use.  Lets a caller check
+ * that a call took no pool memory (ac_match_compact_static never does). */
+ac_status ac_scratch_pool_usage(uint64_t *used_now, uint64_t *used_high, int32_t reset_high);
 
 /* Read and clear the calling device's kernel error word: AC_OK, AC_ERR_TIMEOUT
  * when a bounded wait inside a kernel ran out, or AC_ERR_INVALID_ARG when a

@@ -106,6 +106,7 @@ _SIGS = {
     "ac_match_host": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
     "ac_match_compact_static": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_set_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
+    "ac_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int32]),
     "ac_export_chains": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint32), _P, _P, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "ac_match_batch": (ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P]),
@@ -122,6 +123,8 @@ _SIGS = {
     "ac_server_poll": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]),
     "ac_server_drain": (ctypes.c_int, [_P]),
     "ac_server_destroy": (ctypes.c_int, [_P]),
+    "ac_scratch_pool_usage": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                             ctypes.c_int32]),
     "ac_device_status": (ctypes.c_int, []),
     "ac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -323,8 +326,20 @@ def ac_set_kernel(h: int, kernel: int):
     _check(lib().ac_set_kernel(h, kernel), "ac_set_kernel")
 
 
+def ac_set_wait_limit(h: int, limit_ns: int = 0, stall_help: bool = False):
+    _check(lib().ac_set_wait_limit(h, limit_ns, 1 if stall_help else 0), "ac_set_wait_limit")
+
+
 def ac_device_status() -> int:
     return int(lib().ac_device_status())
+
+
+def ac_scratch_pool_usage(reset_high: bool = False) -> tuple[int, int]:
+    """(bytes of the library's scratch pool in use now, high-water mark since the last reset)."""
+    now, high = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().ac_scratch_pool_usage(ctypes.byref(now), ctypes.byref(high), 1 if reset_high else 0),
+           "ac_scratch_pool_usage")
+    return int(now.value), int(high.value)
 
 
 # ---- batches ---------------------------------------------------------------------

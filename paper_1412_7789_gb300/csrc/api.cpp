@@ -354,6 +354,13 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
         if (s == AC_OK)
             s = upload(h, t.full_dups.data(), t.full_dups.size() * sizeof(uint32_t),
                        reinterpret_cast<const void **>(&d.full_dups));
+        // commit the static scratch of ac_match_compact_static on this device
+        // now, while device memory can still be had, rather than at its first call
+        void *stat = nullptr;
+        if (s == AC_OK && pfac::static_scratch_address(h->device, &stat) != cudaSuccess) {
+            cudaGetLastError();
+            s = AC_ERR_CUDA;
+        }
         if (s != AC_OK) {
             ac_destroy(h);
             return s;
@@ -481,6 +488,13 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel) {
             return AC_ERR_INVALID_ARG;
     }
     h->kernel = kernel == AC_KERNEL_SIMPLE ? AC_KERNEL_SIMPLE : AC_KERNEL_TILED;
+    return AC_OK;
+}
+
+ac_status ac_set_wait_limit(ac_handle h, uint64_t limit_ns, int32_t stall_help) {
+    if (!h) return AC_ERR_INVALID_ARG;
+    h->tuning.wait_ns = limit_ns;
+    h->tuning.stall_help = stall_help ? 1 : 0;
     return AC_OK;
 }
 
@@ -817,11 +831,30 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
     return AC_OK;
 }
 
+ac_status ac_scratch_pool_usage(uint64_t *used_now, uint64_t *used_high, int32_t reset_high) {
+    if (!used_now || !used_high) return AC_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AC_ERR_CUDA;
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = scratch_pool(dev, &pool);
+    uint64_t now = 0, high = 0;
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &now);
+    if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high);
+    if (e == cudaSuccess && reset_high) {
+        uint64_t zero = 0;  // resets the high-water mark to the current use
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero);
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    *used_now = now;
+    *used_high = high;
+    return AC_OK;
+}
+
 ac_status ac_device_status(void) {
     unsigned int v = 0;
     cudaError_t e = pfac::read_device_error(&v);
     if (e != cudaSuccess) return AC_ERR_CUDA;
-    if (v & (pfac::kErrTimeout | pfac::kErrWalk | pfac::kErrLookback)) return AC_ERR_TIMEOUT;
+    if (v & (pfac::kErrTimeout | pfac::kErrWalk)) return AC_ERR_TIMEOUT;
     return v ? AC_ERR_INVALID_ARG : AC_OK;
 }
 

@@ -306,15 +306,6 @@ uint32_t compact_units(const DevTables &t, const uint8_t *text, uint64_t n) {
     return u >= 0x7FFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(u);
 }
 
-// Layout: tile counter (16) | counts (4 per unit) | prefix (8 per unit) |
-// slots (8 * kSlotCap per unit) | partial sums (8 * kScanCtas) | dense
-// fallback (4 per position of every unit, optional; 16-byte aligned for the
-// kernels' 16-byte stores).
-size_t compact_dense_offset(uint32_t units) {
-    const size_t U = units;
-    return round16(16 + round16(4 * U) + 8 * U + 8 * kSlotCap * U + 8 * static_cast<size_t>(kScanCtas));
-}
-
 size_t compact_scratch_bytes(const DevTables &t, uint32_t units, bool dense) {
     (void)t;
     return compact_dense_offset(units) + (dense ? 4 * static_cast<size_t>(kDenseStride) * units : 0);

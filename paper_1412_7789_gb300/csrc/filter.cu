@@ -91,6 +91,8 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.skip = t.skip;
     p.chain = t.chain;
     p.s_chain = t.skip ? t.s_chain : 0xFFFFFFFFu;
+    p.wait_ns = tu.wait_ns ? tu.wait_ns : kWaitNs;
+    p.stall_help = tu.stall_help ? 1u : 0u;
     p.hash_shift = t.hash_shift;
     p.hcode_lo = t.hash_code[0];
     p.hcode_hi = t.hash_code[1];

@@ -102,6 +102,10 @@ struct FilterParams {
     const uint4 *skip;
     const uint8_t *chain;
     uint32_t s_chain;
+    // bounded waits give up after wait_ns; stall_help: an owner waits for one
+    // more finished chunk than its offered tile has (a test of that wait)
+    unsigned long long wait_ns;
+    uint32_t stall_help;
 };
 
 struct WarpSmem {
@@ -714,10 +718,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
 
     unsigned long long cnt = 0;
     Flight f1 = empty_flight(), f2 = empty_flight();  // one and two tiles back
-    bool ok = mbar_wait(jbar, 0);
+    bool ok = mbar_wait(jbar, 0, p.wait_ns);
     // stage s of iteration it is it % nst, its phase parity (it / nst) & 1
     for (uint32_t it = 0, s = 0, par = 0;; ++it, s = s + 1 == nst ? 0u : s + 1, par ^= s == 0 ? 1u : 0u) {
-        ok = ok && mbar_wait(&bars[s], par);
+        ok = ok && mbar_wait(&bars[s], par, p.wait_ns);
         if (!__all_sync(kFull, ok)) {
             // A copy never completed: latch the error, let this warp's copies in
             // flight finish (bounded), and leave.
@@ -725,8 +729,8 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                 bulk_wait_all();
                 atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
                 atomicAdd(retired, 1u);
-                mbar_wait(jbar, 0);
-                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u);
+                mbar_wait(jbar, 0, p.wait_ns);
+                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u, p.wait_ns);
             }
             return;
         }
@@ -940,8 +944,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
             }
             if (offer && lane == 0) {
                 const unsigned long long t0 = global_timer();
-                while (*reinterpret_cast<volatile uint32_t *>(&my_help->done) < nchunks) {
-                    if (global_timer() - t0 > kWaitNs) {
+                const uint32_t need = nchunks + (p.stall_help ? 1u : 0u);
+                while (*reinterpret_cast<volatile uint32_t *>(&my_help->done) < need) {
+                    if (global_timer() - t0 > p.wait_ns) {
                         atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
                         break;
                     }
@@ -1026,7 +1031,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
             if (lane == 0) {
                 if (*reinterpret_cast<volatile uint32_t *>(retired) >= static_cast<uint32_t>(nw)) {
                     stop = 1;
-                } else if (global_timer() - t0 > kWaitNs) {
+                } else if (global_timer() - t0 > p.wait_ns) {
                     atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
                     stop = 1;
                 } else {

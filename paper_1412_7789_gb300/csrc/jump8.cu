@@ -59,6 +59,7 @@ struct JumpParams {
     uint32_t global;        // 1: pfac_jump8g (tables and text through L1)
     uint32_t sms;
     uint32_t rows;          // pfac_jump8g: rows of a tile per claim (1 or 16)
+    unsigned long long wait_ns;  // bounded waits give up after this
 };
 
 __device__ __forceinline__ TileText tile_text(const JumpParams &p, const Work &wk, uint32_t u, uint32_t item) {
@@ -324,15 +325,16 @@ __global__ void __launch_bounds__(kBlock, 1) pfac_jump8(const JumpParams p) {
 
     const uint64_t keep = policy_evict_last();
     unsigned long long cnt = 0;
-    bool ok = mbar_wait(jbar, 0);
+    bool ok = mbar_wait(jbar, 0, p.wait_ns);
     for (uint32_t it = 0;; ++it) {
         const uint32_t s = it % kStages;
-        ok = ok && mbar_wait(&bars[s], (it / kStages) & 1u);
+        ok = ok && mbar_wait(&bars[s], (it / kStages) & 1u, p.wait_ns);
         if (!__all_sync(kFull, ok)) {
             if (lane == 0) {
                 atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
-                mbar_wait(jbar, 0);
-                for (uint32_t j = it; j < it + kStages; ++j) mbar_wait(&bars[j % kStages], (j / kStages) & 1u);
+                mbar_wait(jbar, 0, p.wait_ns);
+                for (uint32_t j = it; j < it + kStages; ++j)
+                    mbar_wait(&bars[j % kStages], (j / kStages) & 1u, p.wait_ns);
             }
             return;
         }
@@ -473,7 +475,8 @@ cudaError_t launch_modes(OutMode mode, const JumpParams &p, uint32_t grid, uint3
 
 uint32_t jump8_tile_positions() { return kTile; }
 
-cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode, bool global, cudaStream_t stream) {
+cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode, bool global,
+                         unsigned long long wait_ns, cudaStream_t stream) {
     if (t.B != 8 || t.k > 2) return cudaErrorInvalidValue;
     if (mode != OUT_DENSE && mode != OUT_COUNT && mode != OUT_SLOTS) return cudaErrorInvalidValue;
     const bool batch = r.batch != nullptr;
@@ -505,6 +508,7 @@ cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode
     p.base_k = t.base_k;
     p.maxlen = t.maxlen;
     p.jbytes = t.jbytes;
+    p.wait_ns = wait_ns ? wait_ns : kWaitNs;
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;

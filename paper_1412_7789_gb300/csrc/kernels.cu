@@ -80,6 +80,7 @@ struct WarpParams {
     SlotOut sl;
     unsigned int *counter;  // next tile to claim
     uint32_t off_warp, warp_bytes, off_queue, off_pass, off_meta;
+    unsigned long long wait_ns;  // bounded waits give up after this
 };
 
 // The text and tile of work unit u (entry `item` of the planned list in a batch).
@@ -550,17 +551,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_walk8(const WarpParams p) {
     LongWalks<SL> lw;
     lw.act = 0;
     unsigned long long cnt = 0;
-    bool ok = mbar_wait(jbar, 0);
+    bool ok = mbar_wait(jbar, 0, p.wait_ns);
     // stage s of iteration it is it % nst, its phase parity (it / nst) & 1
     for (uint32_t it = 0, s = 0, par = 0;; ++it, s = s + 1 == nst ? 0u : s + 1, par ^= s == 0 ? 1u : 0u) {
-        ok = ok && mbar_wait(&bars[s], par);
+        ok = ok && mbar_wait(&bars[s], par, p.wait_ns);
         if (!__all_sync(kFull, ok)) {
             // A copy never completed: latch the error, let this warp's copies in
             // flight finish (bounded), and leave.
             if (lane == 0) {
                 atomicOr(&g_dev_error, static_cast<unsigned>(kErrTimeout));
-                mbar_wait(jbar, 0);
-                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u);
+                mbar_wait(jbar, 0, p.wait_ns);
+                for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u, p.wait_ns);
             }
             return;
         }
@@ -701,7 +702,7 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     if (t.B != 8) return cudaErrorInvalidValue;  // small alphabets use the filter kernel
     // default (variant 0): the full-occupancy one-thread-per-position kernel,
     // the fastest of the three on the 256-value Zipf workloads
-    if (tu.variant != 1) return launch_jump8(t, r, mode, tu.variant != 2, stream);
+    if (tu.variant != 1) return launch_jump8(t, r, mode, tu.variant != 2, tu.wait_ns, stream);
     if (mode != OUT_DENSE && mode != OUT_COUNT && mode != OUT_SLOTS) return cudaErrorInvalidValue;
     const bool batch = r.batch != nullptr;
     if (batch && (mode == OUT_COUNT || !r.lists)) return cudaErrorInvalidValue;
@@ -746,6 +747,7 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     p.base_k = t.base_k;
     p.maxlen = t.maxlen;
     p.jbytes = t.jbytes;
+    p.wait_ns = tu.wait_ns ? tu.wait_ns : kWaitNs;
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;

@@ -14,7 +14,8 @@
 namespace pfac {
 
 
-// Every bounded wait gives up after this many nanoseconds of %globaltimer.
+// Every bounded wait gives up after this many nanoseconds of %globaltimer
+// unless the launch names another limit (ac_set_wait_limit).
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
@@ -115,26 +116,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for a phase with a time limit; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for a phase with a time limit (ns of %globaltimer); false when the
+// limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_timer();
     for (;;) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_timer() - t0 > kWaitNs) return false;
+        if (global_timer() - t0 > limit) return false;
     }
-}
-
-// ---- relaxed GPU-scope 64-bit flag words (decoupled look-back) ---------------
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ int decode_dead(int e) { return -e - 2; }
@@ -365,55 +356,6 @@ __device__ __forceinline__ int goto_ld_hint(const int16_t *G, uint32_t s, uint32
                  : "=h"(v)
                  : "l"(G + static_cast<uint64_t>(s) * W + c), "l"(pol));
     return static_cast<int>(v);
-}
-
-// Decoupled look-back by a whole warp: the 32 closest predecessors are read at
-// once, so a long run of units that have published only their own count costs
-// one step per 32 units.  Status words: flag in the top 2 bits (1 = the unit's
-// count, 2 = inclusive prefix), value in the rest; a unit before the first
-// counts as prefix 0.  Every lane returns the number of matches in all earlier
-// units.  A window whose units do not publish within kWaitNs latches
-// kErrLookback in *err and is counted as empty.
-__device__ __forceinline__ unsigned long long lookback_warp(unsigned long long *status, uint32_t unit,
-                                                            unsigned long long total, unsigned int *err,
-                                                            int lane) {
-    constexpr unsigned long long kAgg = 1ull << 62, kPre = 2ull << 62, kVal = (1ull << 62) - 1ull;
-    if (unit == 0) {
-        if (lane == 0) st_relaxed(&status[0], kPre | total);
-        return 0ull;
-    }
-    if (lane == 0) st_relaxed(&status[unit], kAgg | total);
-    unsigned long long excl = 0;
-    int64_t top = static_cast<int64_t>(unit) - 1;  // closest predecessor of the window
-    unsigned long long t0 = 0;
-    for (;;) {
-        const int64_t idx = top - lane;
-        const unsigned long long v = idx >= 0 ? ld_relaxed(&status[idx]) : kPre;
-        const unsigned f = static_cast<unsigned>(v >> 62);
-        const unsigned pre = __ballot_sync(0xffffffffu, f == 2u);
-        const unsigned stop = pre ? static_cast<unsigned>(__ffs(pre) - 1) : 32u;  // closest prefix
-        const unsigned need = stop < 31u ? ((2u << stop) - 1u) : 0xffffffffu;   // lanes 0..stop
-        const unsigned notyet = __ballot_sync(0xffffffffu, f == 0u) & need;
-        if (notyet) {
-            const unsigned long long now = global_timer();
-            if (t0 == 0) {
-                t0 = now;
-            } else if (now - t0 > kWaitNs) {
-                if (lane == 0) atomicOr(err, static_cast<unsigned>(kErrLookback));
-                break;
-            }
-            continue;
-        }
-        t0 = 0;
-        unsigned long long add = (static_cast<unsigned>(lane) <= stop) ? (v & kVal) : 0ull;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) add += __shfl_xor_sync(0xffffffffu, add, d);
-        excl += add;
-        if (stop < 32u) break;
-        top -= 32;
-    }
-    if (lane == 0) st_relaxed(&status[unit], kPre | (excl + total));
-    return excl;
 }
 
 }  // namespace pfac

@@ -31,7 +31,7 @@ constexpr uint32_t kNoKeyword = 0xFFFFFFFFu;
 constexpr uint32_t kJumpMaxStates = 32766;
 
 // Bits of the per-device kernel error word.
-enum : unsigned { kErrTimeout = 1u, kErrWalk = 2u, kErrLookback = 4u, kErrBatchItem = 8u };
+enum : unsigned { kErrTimeout = 1u, kErrWalk = 2u, kErrBatchItem = 8u };
 
 // Window bits of the root filter (2- and 4-bit codes): 2^20 bits = 128 KiB.
 constexpr uint32_t kFilterBits = 20;
@@ -210,6 +210,8 @@ struct Tuning {
                           // 2 = one thread per position with the jump table in shared
                           // memory (jump8.cu), 0 or 3 = the same at full occupancy with
                           // the table read through L1 (the default)
+    unsigned long long wait_ns = 0;  // bounded waits give up after this (0 = kWaitNs)
+    int stall_help = 0;   // test aid: owners wait for one chunk more than their heavy tile has
 };
 
 // The scan and gather steps of the compacted output (compact.cu).
@@ -250,7 +252,18 @@ cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t 
                             const CompactOut &out, void *scratch, size_t scratch_bytes, bool dense,
                             cudaStream_t stream);
 // Byte offset of the dense fallback in that scratch (16-byte aligned).
-size_t compact_dense_offset(uint32_t units);
+// Layout: tile counter (16) | counts (4 per unit) | prefix (8 per unit) |
+// slots (8 * kSlotCap per unit) | partial sums (8 * kScanCtas) | dense
+// fallback (4 per position of every unit, optional).
+constexpr size_t round16c(size_t v) { return (v + 15u) & ~static_cast<size_t>(15u); }
+constexpr size_t compact_dense_offset(uint64_t units) {
+    return round16c(16 + round16c(4 * units) + 8 * units + 8 * static_cast<size_t>(kSlotCap) * units +
+                    8 * static_cast<size_t>(kScanCtas));
+}
+// Fewest positions per work unit of any matching kernel (the filter kernel's
+// tile); a text of n bytes at any alignment has at most
+// (n + 15 + kMinTile - 1) / kMinTile units.
+constexpr uint32_t kMinTile = 992;
 
 // Full output of one text (full.cu): every keyword occurrence as (end, id)
 // into out.pos / out.ids, ordered by start, end, id; the slot-mode matching
@@ -268,6 +281,11 @@ cudaError_t launch_simple(const DevTables &t, const MatchRequest &r, cudaStream_
 
 // The library's stream-ordered pool for per-call scratch on device `dev`.
 cudaError_t scratch_pool(int dev, cudaMemPool_t *out);
+
+// Device address of the static scratch of ac_match_compact_static on device
+// `dev` (the current device); the first call on a device loads the module that
+// holds the array, which commits its memory (noalloc.cu).
+cudaError_t static_scratch_address(int dev, void **out);
 
 // Handle internals for entry points outside api.cpp.
 const DevTables *handle_tables(ac_handle h, int *device, bool *host_only);
@@ -302,6 +320,7 @@ uint32_t tiled_tile_positions();
 // tile length as launch_tiled, which hands over to it for Tuning::variant 2.
 // global: the full-occupancy form that reads the jump table and the text
 // through L1 (Tuning::variant 3).
-cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode, bool global, cudaStream_t stream);
+cudaError_t launch_jump8(const DevTables &t, const MatchRequest &r, OutMode mode, bool global,
+                         unsigned long long wait_ns, cudaStream_t stream);
 
 }  // namespace pfac

@@ -64,34 +64,3 @@ def check_all_modes(h: int, text: np.ndarray, want: np.ndarray, t=None, modes=("
             raise AssertionError("compact mismatch at %d entries, first %s: got %s / %s want %s / %s" % (
                 bad.size, bad[:6].tolist(), pos[bad[:6]].tolist(), ids[bad[:6]].tolist(),
                 wpos[bad[:6]].tolist(), wid[bad[:6]].tolist()))
-
-
-def regions_check(pats, text: np.ndarray, got_dev, regions):
-    """Sampled parity for texts too large for a full oracle pass: the result
-    at i depends only on text[i : i + max_len], so each region [a, b) is
-    matched by the oracle on text[a : b + max_len]."""
-    maxlen = max(len(p) for p in pats)
-    n = text.size
-    with oracle.Machine(pats) as m:
-        for a, b in regions:
-            a = max(0, a)
-            b = min(n, b)
-            if a >= b:
-                continue
-            want = m.pfac_ids(text[a:min(n, b + maxlen)])[: b - a]
-            got = got_dev[a:b].cpu().numpy()
-            if not np.array_equal(got, want):
-                bad = np.nonzero(got != want)[0]
-                raise AssertionError("region [%d,%d) mismatch at %s" % (a, b, (bad[:8] + a).tolist()))
-
-
-def standard_regions(n: int, tile: int = 8192, seed: int = 0, count: int = 48, width: int = 600):
-    """Regions around tile seams, at both text ends and at random offsets."""
-    g = np.random.Generator(np.random.PCG64(seed))
-    regs = [(0, width), (n - width, n)]
-    ntiles = max(1, n // tile)
-    for t in g.integers(1, ntiles + 1, size=count // 2):
-        regs.append((int(t) * tile - width // 2, int(t) * tile + width // 2))
-    for o in g.integers(0, max(1, n - width), size=count // 2):
-        regs.append((int(o), int(o) + width))
-    return regs

@@ -1,0 +1,137 @@
+"""Parity at full size, every position: the CUDA path through the C ABI against
+the CPU oracle run over the whole text on every host core (tests/_par.py: the
+id at start i depends only on text[i : i + max_len], so stretches with a
+max_len - 1 halo reproduce one serial pass exactly).
+
+* the benchmark's workload in its launch configuration: 1 GiB of ACGT text,
+  the 10,000-keyword sweep set, dense ids (plus count and compacted list);
+* every other size of the input-size sweep (4 KiB .. 256 MiB, prefixes of the
+  same text);
+* texts on both sides of the launcher's switch between the kernel forms that
+  share heavy tiles within the CTA and the plain forms;
+* the byte-alphabet workload at 256 MiB (Zipf(1.1) bytes, its own 20,000
+  keywords): compacted list, count and dense ids, every 8-bit kernel;
+* the host-buffer call across its 64 MiB chunk seams.
+"""
+import numpy as np
+import pytest
+
+from paper_1412_7789_gb300 import api, workloads
+from tests import _par
+
+pytestmark = pytest.mark.gpu
+
+TILE = 992            # positions per tile of the small-alphabet kernel
+HELP_TILES_PER_WARP = 16
+WARPS_PER_CTA = 16    # default launch: 512 threads
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1412_7789_gb300 import build
+
+    build.build()
+    api.lib()
+    yield
+    assert api.ac_device_status() == api.AC_OK
+
+
+@pytest.fixture(scope="module")
+def sweep():
+    import torch
+
+    text, pats = workloads.sweep_acgt(1 << 30)
+    wpos, wids = _par.oracle_compact(pats, text)
+    t = torch.from_numpy(text).cuda()
+    a = api.Automaton(pats)
+    yield text, pats, wpos, wids, t, a
+    a.close()
+    del t
+    torch.cuda.empty_cache()
+
+
+def _all_outputs(a, t, n, wpos, wids, what):
+    """Dense ids, count and compacted list of text t[:n] against the oracle's list."""
+    import torch
+
+    out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    api.ac_match(a.handle, t, n, out)
+    _par.check_dense(out[:n], wpos, wids, what)
+    del out
+    cnt = torch.full((1,), 12345, dtype=torch.int64, device="cuda")
+    api.ac_count(a.handle, t, n, cnt)
+    assert int(cnt.item()) == wpos.size, (what, int(cnt.item()), wpos.size)
+    cap = max(1, wpos.size)
+    pos = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    ids = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    api.ac_match_compact(a.handle, t, n, pos, ids, cap, cnt)
+    _par.check_compact(pos, ids, int(cnt.item()), wpos, wids, what)
+
+
+def test_sweep_1gib_every_position(sweep):
+    """The benchmark's step (ac_match on the 1 GiB text, default launch)."""
+    text, pats, wpos, wids, t, a = sweep
+    assert wpos.size > 1000
+    _all_outputs(a, t, text.size, wpos, wids, "1 GiB")
+
+
+def test_sweep_sizes_every_position(sweep):
+    text, pats, wpos, wids, t, a = sweep
+    for n in workloads.SWEEP_SIZES[:-1]:
+        p, i = _par.window_compact(wpos, wids, pats, text, 0, n)
+        _all_outputs(a, t[:n], n, p, i, "%d B" % n)
+
+
+def test_shared_and_plain_forms_boundary(sweep):
+    """Texts of exactly the largest tile count that takes the forms sharing
+    heavy tiles within the CTA (16 tiles per warp of the grid), one tile
+    fewer and one more (plain forms), each with a ragged last tile; the heavy
+    tiles of the sweep set's first 4 KiB run in both forms."""
+    import torch
+
+    text, pats, wpos, wids, t, a = sweep
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    edge = HELP_TILES_PER_WARP * sms * WARPS_PER_CTA
+    for tiles in (edge - 1, edge, edge + 1):
+        n = tiles * TILE - 37
+        p, i = _par.window_compact(wpos, wids, pats, text, 0, n)
+        _all_outputs(a, t[:n], n, p, i, "%d tiles" % tiles)
+
+
+@pytest.fixture(scope="module")
+def zipf():
+    import torch
+
+    text, pats = workloads.zipf_byte(256 << 20)
+    wpos, wids = _par.oracle_compact(pats, text)
+    t = torch.from_numpy(text).cuda()
+    yield text, pats, wpos, wids, t
+    del t
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kernel", ["tiled", "walk_slots", "thread_jump", "thread_jump_l1"])
+def test_zipf_256mib_every_match(zipf, kernel):
+    text, pats, wpos, wids, t = zipf
+    assert wpos.size > 10000
+    with api.Automaton(pats) as a:
+        a.set_kernel(kernel)
+        _all_outputs(a, t, text.size, wpos, wids, "zipf 256 MiB " + kernel)
+
+
+def test_match_host_every_position():
+    """ac_match_host: 64 MiB chunks with a max_len halo each, pinned host
+    buffers, a text ending 12,345 bytes into its second chunk."""
+    import torch
+
+    n = (64 << 20) + 12_345
+    text, pats = workloads.sweep_acgt(n, seed=4)
+    wpos, wids = _par.oracle_compact(pats, text)
+    with api.Automaton(pats) as a:
+        ht = torch.from_numpy(text).pin_memory()
+        got = a.match_host(ht)
+        _par.check_dense(got, wpos, wids, "host")
+        small = text[:5000]
+        p, i = _par.window_compact(wpos, wids, pats, text, 0, small.size)
+        got = a.match_host(torch.from_numpy(small.copy()))
+        _par.check_dense(got, p, i, "host small")

@@ -202,37 +202,6 @@ def test_zipf_compact_and_overflow(kernel):
         assert total == wpos.size and pos.size == 0
 
 
-def test_sweep_full_size_sampled():
-    """The benchmark's workload and launch configuration (1 GiB ACGT text,
-    10,000 keywords), checked on sampled regions (tile seams, both ends)."""
-    import torch
-
-    text, pats = workloads.sweep_acgt(1 << 30)
-    t = _gpu.to_dev(text)
-    with compile_(pats) as a:
-        out = a.match(t)
-        torch.cuda.synchronize()
-        _gpu.regions_check(pats, text, out, _gpu.standard_regions(text.size))
-        assert int(a.count(t).item()) == int((out >= 0).sum().item())
-    del out, t
-
-
-def test_match_host_chunk_seams():
-    import torch
-
-    n = (64 << 20) + 12_345
-    text, pats = workloads.sweep_acgt(n, seed=4)
-    with compile_(pats) as a:
-        ht = torch.from_numpy(text).pin_memory()
-        got = a.match_host(ht)
-        regs = _gpu.standard_regions(n, seed=2, count=16) + [((64 << 20) - 700, (64 << 20) + 700)]
-        _gpu.regions_check(pats, text, got, regs)
-        small = text[:5000]
-        want = oracle.pfac_ids(pats, small)
-        got = a.match_host(torch.from_numpy(small.copy()))
-        assert np.array_equal(got.numpy(), want)
-
-
 @pytest.mark.parametrize("kernel", ["tiled", "walk_slots", "thread_jump", "thread_jump_l1"])
 @pytest.mark.parametrize("alpha", ["acgt", "bytes"])
 def test_dense_matches_compact(alpha, kernel):

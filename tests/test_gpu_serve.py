@@ -1,14 +1,14 @@
 """The serving loop (ac_server_*) through the C ABI: every request's compacted
-list must be the same alone (ac_match_compact on its text, itself checked
-against the CPU oracle) and inside a mix of requests of other sizes and
-automata batched into shared waves, under any admission budget, wave size or
-arrival pattern."""
+list must equal the CPU oracle's for its text, alone (ac_match_compact on its
+text) and inside a mix of requests of other sizes and automata batched into
+shared waves, under any admission budget, wave size or arrival pattern.  The
+oracle's list of a request is cut from the list of its whole pool (tests/_par.py:
+exact, with the window's last max_len - 1 starts recomputed)."""
 import numpy as np
 import pytest
 
-import oracle
 from paper_1412_7789_gb300 import api, workloads
-from tests import _gpu
+from tests import _gpu, _par
 
 pytestmark = pytest.mark.gpu
 
@@ -50,18 +50,17 @@ def setup():
         n = 0 if i % 37 == 5 else int(np.exp(g.uniform(0, np.log(1.5 * (1 << 20)))))
         off = int(g.integers(0, pools[a].size - n + 1))
         reqs.append((a, off, n))
-    # expected: the single-text compacted path (checked against the oracle on the small ones)
+    # expected: the oracle's list of every request; the single-text compacted
+    # path (the request alone) must give it too
+    lists = [_par.oracle_compact(sets[a], pools[a]) for a in range(3)]
     want = []
     for a, off, n in reqs:
-        text = d_pools[a][off:off + n]
+        wp, wi = _par.window_compact(*lists[a], sets[a], pools[a], off, n)
+        want.append((wp.astype(np.uint32), wi.astype(np.uint32), wp.size))
         if n == 0:
-            want.append((np.zeros(0, np.uint32), np.zeros(0, np.uint32), 0))
             continue
-        pos, ids, total = _gpu.compact(autos[a].handle, text, max(1, n))  # room for every match
-        want.append((pos, ids, total))
-        if n <= (64 << 10):
-            wp, wi = oracle.compact(oracle.pfac_ids(sets[a], pools[a][off:off + n]))
-            assert total == wp.size and np.array_equal(pos, wp) and np.array_equal(ids, wi)
+        pos, ids, total = _gpu.compact(autos[a].handle, d_pools[a][off:off + n], max(1, n))  # room for every match
+        assert total == wp.size and np.array_equal(pos, wp) and np.array_equal(ids, wi), (a, off, n)
     yield sets, pools, d_pools, autos, reqs, want
     for x in autos:
         x.close()

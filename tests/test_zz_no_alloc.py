@@ -61,6 +61,58 @@ def test_static_scratch_matches_allocating_call(kind):
     assert api.ac_device_status() == api.AC_OK
 
 
+def test_static_scratch_at_the_size_limit_misaligned():
+    """A text of exactly AC_STATIC_MAX_TEXT bytes starting 15 bytes past a
+    16-byte boundary (the most work units a text of that length can have)."""
+    import torch
+
+    from paper_1412_7789_gb300 import build
+
+    build.build()
+    n = api.AC_STATIC_MAX_TEXT
+    text, pats = workloads.sweep_acgt(n + 15, seed=5)
+    base = torch.from_numpy(text.copy()).cuda()
+    t = base[15:15 + n]
+    assert t.data_ptr() % 16 == 15
+    with api.Automaton(pats) as a:
+        want_pos, want_ids, want_total = _compact(api.ac_match_compact, a.handle, t, n, n // 64 + 1)
+        pos, ids, total = _compact(api.ac_match_compact_static, a.handle, t, n, n // 64 + 1)
+        assert total == want_total > 0
+        assert np.array_equal(pos, want_pos) and np.array_equal(ids, want_ids)
+    assert api.ac_device_status() == api.AC_OK
+
+
+def test_static_scratch_call_allocates_nothing():
+    """After a first call (which loads the kernels' code), further calls change
+    neither the device's free memory nor the library's scratch pool use."""
+    import torch
+
+    from paper_1412_7789_gb300 import build
+
+    build.build()
+    text, pats = workloads.zipf_byte(1 << 20, seed=6, n_keywords=2000)
+    t = torch.from_numpy(text.copy()).cuda()
+    n = text.size
+    cap = n // 8 + 1
+    pos = torch.empty(cap, dtype=torch.int32, device="cuda")
+    ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with api.Automaton(pats) as a:
+        api.ac_match_compact_static(a.handle, t, n, pos, ids, cap, cnt)
+        torch.cuda.synchronize()
+        first = int(cnt.item())
+        free0, _ = torch.cuda.mem_get_info()
+        used0, _ = api.ac_scratch_pool_usage(reset_high=True)
+        for _ in range(3):
+            api.ac_match_compact_static(a.handle, t, n, pos, ids, cap, cnt)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        used1, high1 = api.ac_scratch_pool_usage()
+        assert int(cnt.item()) == first
+        assert free1 == free0, (free0, free1)
+        assert used1 == used0 and high1 == used0, (used0, used1, high1)
+
+
 def test_static_scratch_rejects_long_text():
     import torch
 
