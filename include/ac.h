@@ -56,9 +56,10 @@ typedef enum {
 /* Which matching kernel a handle uses (ac_set_kernel).  Results never depend
  * on the choice; only the time does. */
 typedef enum {
-    AC_KERNEL_TILED = 0,       /* default, the library's choice per automaton: up to 16
-                                  keyword bytes, bulk-copied text tiles with the
-                                  shared-memory root filter; more, THREAD_JUMP_L1   */
+    AC_KERNEL_TILED = 0,       /* default: bulk-copied warp tiles of text with the
+                                  shared-memory root filter (a hashed filter over
+                                  windows of up to 4 codes for more than 16 keyword
+                                  bytes) and the survivors' walks pipelined        */
     AC_KERNEL_SIMPLE = 1,      /* one thread per position walking the goto table in
                                   global memory (the design of the paper's GPU side);
                                   ac_match and ac_match_host only                    */
@@ -81,9 +82,9 @@ typedef enum {
  *   host_only      1 = build the host tables only; the handle can be inspected
  *                  (ac_info, ac_export_tables) but match calls refuse it.
  *                  Needs no GPU.
- *   jump_bytes     shared-memory budget of the first-level table: the root filter
- *                  (alphabets of at most 16 keyword bytes) or the root jump
- *                  table (larger alphabets); 0 = 128 KiB.
+ *   jump_bytes     shared-memory budget of the first-level tables: the root
+ *                  filter (both forms) and the root jump table of larger
+ *                  alphabets; 0 = 128 KiB.
  *   stride_bytes   device budget of the second-level stride table (0 = 16 MiB;
  *                  set 1 to disable it).
  *   no_chains      1 = no chain records: every walk step reads a goto row (the
@@ -199,6 +200,27 @@ ac_status ac_export_full(ac_handle h, uint32_t *records, uint32_t *dups, uint32_
  */
 ac_status ac_export_filter(ac_handle h, uint32_t *F, int32_t *JK, uint32_t *B, uint32_t *k, uint64_t *f_words,
                            uint64_t *jk_entries);
+
+/*
+ * Hashed root filter and state hash of an automaton whose keyword bytes take
+ * 8-bit codes (for inspection and tests; host memory).  A window w holds the
+ * codes of kh = min(4, shortest keyword) consecutive text bytes, 8 bits each,
+ * the first byte lowest (a byte's code is its class, or the byte itself with
+ * 256 columns).  A walk that does not reach depth kh stops before any keyword
+ * ends, so its result is -1.
+ *   F   uint32[2^fbits / 32]: with f = (w * 0x9E3779B1 mod 2^32) >> (32 - fbits),
+ *       bit 31 - (f & 31) of word f >> 5 is set for the window of every state
+ *       at depth kh (a clear bit: result -1; other windows may share a bit).
+ *   HK  uint32[4 * 2^hk_bits]: buckets of two {window, state} entries (state 0:
+ *       empty).  The depth-kh state with window w is in the first bucket with
+ *       room at or after bucket (w * 0x85EBCA77 mod 2^32) >> (32 - hk_bits)
+ *       (cyclically), at most *probes buckets from it; a window found in none
+ *       of those buckets, or before a bucket with an empty entry, has no state.
+ * *kh = 0 and zero sizes for an automaton without them (2- or 4-bit codes).
+ * Call with NULL arrays to get the sizes.
+ */
+ac_status ac_export_hash(ac_handle h, uint32_t *F, uint32_t *HK, uint32_t *kh, uint32_t *fbits, uint32_t *hk_bits,
+                         uint32_t *probes);
 
 /*
  * Stride table (for inspection and tests; host memory): for the r-th state at

@@ -100,6 +100,7 @@ _SIGS = {
                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64)]),
     "ac_export_jump": (ctypes.c_int, [_H, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                       ctypes.POINTER(ctypes.c_uint64)]),
+    "ac_export_hash": (ctypes.c_int, [_H, _P, _P] + [ctypes.POINTER(ctypes.c_uint32)] * 4),
     "ac_export_filter": (ctypes.c_int, [_H, _P, _P, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "ac_count": (ctypes.c_int, [_H, _P, _U64, _P, _P]),
@@ -273,6 +274,17 @@ def ac_export_stride(h: int):
     _check(lib().ac_export_stride(h, J2.ctypes.data, ctypes.byref(k2), ctypes.byref(bk), ctypes.byref(ck),
                                   ctypes.byref(ne)), "ac_export_stride")
     return int(k2.value), int(bk.value), int(ck.value), J2
+
+
+def ac_export_hash(h: int):
+    """(kh, fbits, hk_bits, probes, F uint32[...], HK uint32[n_buckets, 4]) of an 8-bit-code automaton -- see ac.h."""
+    v = [ctypes.c_uint32() for _ in range(4)]
+    _check(lib().ac_export_hash(h, None, None, *[ctypes.byref(x) for x in v]), "ac_export_hash")
+    kh, fbits, hk_bits, probes = (int(x.value) for x in v)
+    F = np.zeros((1 << fbits) // 32 if kh else 0, dtype=np.uint32)
+    HK = np.zeros(((1 << hk_bits) if kh else 0, 4), dtype=np.uint32)
+    _check(lib().ac_export_hash(h, F.ctypes.data, HK.ctypes.data, *[ctypes.byref(x) for x in v]), "ac_export_hash")
+    return kh, fbits, hk_bits, probes, F, HK
 
 
 def ac_export_jump(h: int):

@@ -145,8 +145,7 @@ cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode,
         pfac::MatchRequest r0 = r;
         r0.scratch = nullptr;
         r0.scratch_bytes = 0;
-        const cudaError_t e0 = h->dev.filter ? pfac::launch_filter(h->dev, r0, mode, h->tuning, st)
-                                             : pfac::launch_tiled(h->dev, r0, mode, h->tuning, st);
+        const cudaError_t e0 = pfac::launch_match(h->dev, r0, mode, h->tuning, st);
         if (e0 == cudaSuccess) return e0;  // else: a counter is needed (or a real error, reported below)
     }
     const size_t bytes = 16;
@@ -160,8 +159,7 @@ cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode,
     if (e == cudaSuccess) {
         r.scratch = scratch;
         r.scratch_bytes = bytes;
-        e = h->dev.filter ? pfac::launch_filter(h->dev, r, mode, h->tuning, st)
-                          : pfac::launch_tiled(h->dev, r, mode, h->tuning, st);
+        e = pfac::launch_match(h->dev, r, mode, h->tuning, st);
     }
     const cudaError_t e2 = cudaFreeAsync(scratch, st);
     return e != cudaSuccess ? e : e2;
@@ -170,7 +168,7 @@ cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode,
 // The compacted match of one text with its scratch from the pool.
 cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const pfac::CompactOut &out,
                         cudaStream_t st) {
-    const uint32_t units = pfac::compact_units(h->dev, text, n);
+    const uint32_t units = pfac::compact_units(h->dev, h->tuning, text, n);
     if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
     const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, true);
     cudaMemPool_t pool = nullptr;
@@ -187,7 +185,7 @@ cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const 
 // The full output of one text with its scratch from the pool.
 cudaError_t run_full(ac_automaton *h, const uint8_t *text, uint64_t n, const pfac::CompactOut &out,
                      cudaStream_t st) {
-    const uint32_t units = pfac::compact_units(h->dev, text, n);
+    const uint32_t units = pfac::compact_units(h->dev, h->tuning, text, n);
     if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
     const size_t bytes = pfac::full_scratch_bytes(h->dev, units);
     cudaMemPool_t pool = nullptr;
@@ -235,7 +233,7 @@ cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const
     pfac::BatchItemDev *lists = reinterpret_cast<pfac::BatchItemDev *>(base + static_cast<size_t>(nh) * 32u);
     std::vector<uint32_t> tile_len(nh);
     for (uint32_t a = 0; a < nh; ++a)
-        tile_len[a] = hs[a]->dev.filter ? pfac::filter_tile_positions() : pfac::tiled_tile_positions();
+        tile_len[a] = pfac::unit_positions(hs[a]->dev, hs[a]->tuning);
     cudaError_t e = cudaMemsetAsync(counters, 0, static_cast<size_t>(nh) * 16u, st);
     if (e == cudaSuccess) e = pfac::launch_batch_plan(items, nitems, nh, texts, tile_len.data(), heads, lists, st);
     for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
@@ -248,8 +246,7 @@ cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const
         r.scratch = counters + 16u * a;
         r.scratch_bytes = 16;
         ac_automaton *h = hs[a];
-        e = h->dev.filter ? pfac::launch_filter(h->dev, r, pfac::OUT_DENSE, h->tuning, sa)
-                          : pfac::launch_tiled(h->dev, r, pfac::OUT_DENSE, h->tuning, sa);
+        e = pfac::launch_match(h->dev, r, pfac::OUT_DENSE, h->tuning, sa);
     }
     return e;
 }
@@ -319,6 +316,11 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     d.jbytes = static_cast<uint32_t>(t.J.size() * sizeof(int16_t));
     d.jslow = t.jslow;
     d.filter = t.filter;
+    d.hashed = t.hashed;
+    d.kh = t.kh;
+    d.fbits = t.fbits;
+    d.hk_bits = t.hk_bits;
+    d.hk_probes = t.hk_probes;
     d.fbytes = static_cast<uint32_t>(t.F.size() * sizeof(uint32_t));
     d.hash_shift = t.hash_shift;
     d.full_max_clen = t.full_max_clen;
@@ -340,6 +342,8 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
             s = upload(h, t.F.data(), t.F.size() * sizeof(uint32_t), reinterpret_cast<const void **>(&d.F));
         if (s == AC_OK && !t.JK.empty())
             s = upload(h, t.JK.data(), t.JK.size() * sizeof(int32_t), reinterpret_cast<const void **>(&d.JK));
+        if (s == AC_OK && !t.HK.empty())
+            s = upload(h, t.HK.data(), t.HK.size() * sizeof(uint32_t), reinterpret_cast<const void **>(&d.HK));
         if (s == AC_OK && !t.J2.empty())
             s = upload(h, t.J2.data(), t.J2.size() * sizeof(int32_t), reinterpret_cast<const void **>(&d.J2));
         if (s == AC_OK && !t.skip.empty()) {
@@ -445,6 +449,19 @@ ac_status ac_export_filter(ac_handle h, uint32_t *F, int32_t *JK, uint32_t *B, u
     return AC_OK;
 }
 
+ac_status ac_export_hash(ac_handle h, uint32_t *F, uint32_t *HK, uint32_t *kh, uint32_t *fbits, uint32_t *hk_bits,
+                         uint32_t *probes) {
+    if (!h || !kh || !fbits || !hk_bits || !probes) return AC_ERR_INVALID_ARG;
+    const pfac::HostTables &t = h->host;
+    *kh = t.hashed ? t.kh : 0u;
+    *fbits = t.hashed ? t.fbits : 0u;
+    *hk_bits = t.hashed ? t.hk_bits : 0u;
+    *probes = t.hashed ? t.hk_probes : 0u;
+    if (t.hashed && F) std::memcpy(F, t.F.data(), t.F.size() * sizeof(uint32_t));
+    if (t.hashed && HK) std::memcpy(HK, t.HK.data(), t.HK.size() * sizeof(uint32_t));
+    return AC_OK;
+}
+
 ac_status ac_export_stride(ac_handle h, int32_t *J2, uint32_t *k2, uint32_t *base_k, uint32_t *count_k,
                            uint64_t *entries) {
     if (!h || !k2 || !base_k || !count_k || !entries) return AC_ERR_INVALID_ARG;
@@ -460,7 +477,7 @@ ac_status ac_export_stride(ac_handle h, int32_t *J2, uint32_t *k2, uint32_t *bas
 ac_status ac_export_jump(ac_handle h, int16_t *J, uint32_t *k, uint32_t *base_k, uint64_t *entries) {
     if (!h || !k || !base_k || !entries) return AC_ERR_INVALID_ARG;
     const pfac::HostTables &t = h->host;
-    const bool has = !t.filter && t.k > 0 && !t.J.empty();
+    const bool has = t.B == 8 && t.k > 0 && !t.J.empty();
     *k = has ? t.k : 0u;
     *base_k = t.base_k;
     *entries = has ? (1ull << (t.B * t.k)) : 0u;  // J is padded to at least 8 entries
@@ -760,11 +777,14 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
     r.text = d_sample;
     r.n = n;
     r.out = static_cast<int32_t *>(out);
-    // candidates: threads per CTA x stages for the tiled kernels; for 8-bit
-    // codes also the two one-thread-per-position kernels (one shape each)
+    // candidates: threads per CTA x stages for the filter kernel and the warp
+    // walk; the two one-thread-per-position kernels with one shape each
     std::vector<pfac::Tuning> cands;
     static const int kBlocks[3] = {256, 384, 512};
-    const std::vector<int> variants = h->dev.filter ? std::vector<int>{0} : std::vector<int>{3, 2, 1};
+    // small alphabets: the filter kernel only; 8-bit codes: the filter kernel
+    // with the hashed filter (when built) and the three 8-bit kernels
+    std::vector<int> variants{0};
+    if (!h->dev.filter) variants = h->dev.hashed ? std::vector<int>{0, 3, 2, 1} : std::vector<int>{3, 2, 1};
     for (int v : variants) {
         if (v == 2 || v == 3) {
             pfac::Tuning tu = keep;
@@ -826,7 +846,7 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
     if (kernel) {
         static const uint32_t kByVariant[4] = {AC_KERNEL_TILED, AC_KERNEL_WALK_SLOTS, AC_KERNEL_THREAD_JUMP,
                                                AC_KERNEL_THREAD_JUMP_L1};
-        *kernel = h->dev.filter ? AC_KERNEL_TILED : kByVariant[h->tuning.variant & 3];
+        *kernel = pfac::uses_filter(h->dev, h->tuning) ? AC_KERNEL_TILED : kByVariant[h->tuning.variant & 3];
     }
     return AC_OK;
 }

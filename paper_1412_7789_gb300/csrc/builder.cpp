@@ -16,7 +16,9 @@
 //      for small alphabets (2- or 4-bit codes) a filter bit per window of k
 //      codes (clear: the walk stops inside the window with no keyword) plus
 //      the window table (depth-k state reached, or the encoded result); for
-//      8-bit codes the root jump table (result, or depth-k state, per window);
+//      8-bit codes the root jump table (result, or depth-k state, per window),
+//      and a hashed filter over windows of kh codes with a hash of the
+//      depth-kh states by their window;
 //   7. the stride table: the depth-(k+k2) state or the result, for k2 more
 //      codes from every depth-k state;
 //   8. chain records for the deep, mostly unbranched states;
@@ -244,6 +246,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         std::vector<uint32_t> newid(S, 0);
         std::vector<uint32_t> depth(S, 0);     // by new id
         std::vector<uint32_t> parent(S, 0);    // by new id
+        std::vector<uint32_t> incode(S, 0);    // by new id: the code of the edge into the state
         order.push_back(0);
         for (size_t qi = 0; qi < order.size(); ++qi) {
             uint32_t old = order[qi];
@@ -253,6 +256,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                 newid[e.child] = nid;
                 depth[nid] = depth[qi] + 1;
                 parent[nid] = static_cast<uint32_t>(qi);
+                incode[nid] = e.code;
                 order.push_back(e.child);
             }
         }
@@ -381,6 +385,51 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                         if (v > 32767) h.jslow = true;
                     }
                 }
+            }
+        }
+        if (h.B == 8) {
+            // 6c. hashed root filter and state hash (8-bit codes).  Windows of
+            //     kh = min(4, shortest keyword) codes: a walk that does not
+            //     reach depth kh stops before any keyword ends, so its result is
+            //     -1.  The filter bit of the window of every depth-kh state is
+            //     set (a clear bit: result -1); HK holds each depth-kh state
+            //     under its window, two {window, state} entries per bucket,
+            //     linear probing.
+            const uint32_t kh = std::min<uint32_t>(kHashWindow, h.minlen);
+            uint32_t fb = 0;
+            while (fb < kFilterBits && (2ull << fb) <= 8ull * opt.jump_bytes) ++fb;
+            if (fb >= 5) {
+                const uint32_t b0 = depth_base[kh], cnt = h.depth_count[kh];
+                std::vector<uint32_t> key(static_cast<size_t>(b0) + cnt, 0);  // codes of the path, first lowest
+                for (uint32_t s = 1; s < b0 + cnt; ++s)
+                    key[s] = key[parent[s]] | (incode[s] << (8u * (depth[s] - 1u)));
+                uint32_t hb = 6;
+                while ((1ull << hb) < 2ull * cnt) ++hb;
+                if (hb > 31) return AC_ERR_TOO_MANY_STATES;
+                h.hashed = true;
+                h.kh = kh;
+                h.fbits = fb;
+                h.hk_bits = hb;
+                h.F.assign((1u << fb) / 32u, 0u);
+                h.HK.assign((1ull << hb) * 4ull, 0u);
+                const uint32_t bmask = (1u << hb) - 1u;
+                uint32_t probes = 1;
+                for (uint32_t s = b0; s < b0 + cnt; ++s) {
+                    const uint32_t w = key[s];
+                    const uint32_t f = (w * kFilterHashMul) >> (32u - fb);
+                    h.F[f >> 5] |= 1u << (31u - (f & 31u));
+                    uint32_t b = (w * kStateHashMul) >> (32u - hb);
+                    for (uint32_t p = 1;; ++p, b = (b + 1u) & bmask) {
+                        uint32_t *e = &h.HK[4ull * b];
+                        const int slot = e[1] == 0u ? 0 : (e[3] == 0u ? 2 : -1);
+                        if (slot < 0) continue;
+                        e[slot] = w;
+                        e[slot + 1] = s;
+                        probes = std::max(probes, p);
+                        break;
+                    }
+                }
+                h.hk_probes = probes;
             }
         }
         const uint32_t kj = h.k;

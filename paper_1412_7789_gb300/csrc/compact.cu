@@ -299,8 +299,8 @@ namespace {
 inline size_t round16(size_t v) { return (v + 15u) & ~static_cast<size_t>(15u); }
 }  // namespace
 
-uint32_t compact_units(const DevTables &t, const uint8_t *text, uint64_t n) {
-    const uint64_t T = t.filter ? filter_tile_positions() : tiled_tile_positions();
+uint32_t compact_units(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n) {
+    const uint64_t T = unit_positions(t, tu);
     const uint64_t head = reinterpret_cast<uintptr_t>(text) & 15u;
     const uint64_t u = (n + head + T - 1) / T;
     return u >= 0x7FFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(u);
@@ -314,7 +314,7 @@ size_t compact_scratch_bytes(const DevTables &t, uint32_t units, bool dense) {
 cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
                             const CompactOut &out, void *scratch, size_t scratch_bytes, bool dense,
                             cudaStream_t stream) {
-    const uint32_t U = compact_units(t, text, n);
+    const uint32_t U = compact_units(t, tu, text, n);
     if (U == 0xFFFFFFFFu || n > 0xFFFFFFFFull) return cudaErrorInvalidValue;
     if (!scratch || scratch_bytes < compact_scratch_bytes(t, U, dense)) return cudaErrorInvalidValue;
     uint8_t *b = static_cast<uint8_t *>(scratch);
@@ -334,7 +334,7 @@ cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t 
     r.slots.dense = dn;
     r.scratch = b;
     r.scratch_bytes = 16;
-    e = t.filter ? launch_filter(t, r, OUT_SLOTS, tu, stream) : launch_tiled(t, r, OUT_SLOTS, tu, stream);
+    e = launch_match(t, r, OUT_SLOTS, tu, stream);
     if (e != cudaSuccess) return e;
     e = launch_compact_scan(counts, U, nullptr, prefix, partials, stream);
     if (e != cudaSuccess) return e;
@@ -343,7 +343,7 @@ cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t 
     g.n = n;
     g.out = out;
     g.units = U;
-    g.tile = t.filter ? filter_tile_positions() : tiled_tile_positions();
+    g.tile = unit_positions(t, tu);
     g.counts = counts;
     g.prefix = prefix;
     g.slots = slots;

@@ -1,6 +1,6 @@
-// Failureless Aho-Corasick matching for small alphabets (keyword bytes mapped
-// to 2- or 4-bit codes), sm_103a: the launcher.  The kernel is in
-// filter_kernel.cuh.
+// Failureless Aho-Corasick matching with a root filter, sm_103a: the launcher
+// (2- and 4-bit codes with the exact filter, 8-bit codes with the hashed
+// filter and state hash).  The kernel is in filter_kernel.cuh.
 #include "filter_kernel.cuh"
 
 namespace pfac {
@@ -14,7 +14,8 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
         tu.stages > kMaxStages)
         return cudaErrorInvalidValue;
-    if (t.B != 2 && t.B != 4) return cudaErrorInvalidValue;
+    const bool hashed = t.B == 8 && t.hashed && t.HK != nullptr;
+    if (!((t.B == 2 || t.B == 4) && t.filter) && !hashed) return cudaErrorInvalidValue;
     if (mode != OUT_DENSE && mode != OUT_COUNT && mode != OUT_SLOTS) return cudaErrorInvalidValue;
     const bool batch = r.batch != nullptr;
     if (batch && (mode == OUT_COUNT || !r.lists)) return cudaErrorInvalidValue;
@@ -77,17 +78,27 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.cls8g = t.cls8;
     p.C = t.C;
     p.W = t.W;
-    p.k = t.k;
-    p.k2 = t.k2;
+    p.k = hashed ? t.kh : t.k;
+    p.k2 = hashed ? 0u : t.k2;
     p.base_k = t.base_k;
     p.maxlen = t.maxlen;
     p.fbytes = t.fbytes;
     {
-        const uint32_t wb = t.B * t.k;  // window bits; windows below 32 are replicated to 32
+        // filter index bits: the window's (windows below 32 bits are
+        // replicated to 32), or the hash's
+        const uint32_t wb = hashed ? t.fbits : t.B * t.k;
         const uint32_t nb = (wb >= 5 ? (1u << wb) : 32u) / 8u;
-        if (nb > t.fbytes) return cudaErrorInvalidValue;
+        if (nb > t.fbytes || (hashed && (t.fbits < 5 || t.fbits > 31 || t.kh < 1 || t.kh > kHashWindow)))
+            return cudaErrorInvalidValue;
         p.famask = (nb - 1u) & ~3u;
     }
+    p.identity = t.C >= 256 ? 1u : 0u;
+    p.wmask = hashed ? (t.kh >= 4 ? 0xFFFFFFFFu : (1u << (8u * t.kh)) - 1u) : 0u;
+    p.fshift = hashed ? 32u - t.fbits : 0u;
+    p.HK = hashed ? t.HK : nullptr;
+    p.hk_shift = hashed ? 32u - t.hk_bits : 0u;
+    p.hk_mask = hashed ? (1u << t.hk_bits) - 1u : 0u;
+    p.hk_probes = hashed ? t.hk_probes : 0u;
     p.skip = t.skip;
     p.chain = t.chain;
     p.s_chain = t.skip ? t.s_chain : 0xFFFFFFFFu;
@@ -115,9 +126,11 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     if (grid == 0) return cudaSuccess;
     // a text short next to the grid: its heavy tiles (many survivors, long
     // walks) would be one warp's work each while most warps have run out of
-    // tiles, so those forms share them within the CTA
-    if (!batch && static_cast<uint64_t>(p.ntiles) <= static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw)
+    // tiles, so those forms share them within the CTA (small alphabets)
+    if (!batch && t.B <= 4 &&
+        static_cast<uint64_t>(p.ntiles) <= static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw)
         return launch_filter_help(mode, p, t.B, t.gbits, grid, tu.block, smem, max_smem, stream);
+    if (t.B == 8) return launch_filter8(mode, p, t.gbits, grid, tu.block, smem, max_smem, stream);
     if (t.B == 2) {
         if (t.gbits == 16) return launch_modes<2, int16_t, false>(mode, p, grid, tu.block, smem, max_smem, stream);
         return launch_modes<2, int32_t, false>(mode, p, grid, tu.block, smem, max_smem, stream);

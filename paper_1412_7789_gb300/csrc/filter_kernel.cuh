@@ -1,5 +1,8 @@
-// Failureless Aho-Corasick matching for small alphabets (keyword bytes mapped
-// to 2- or 4-bit codes), sm_103a.
+// Failureless Aho-Corasick matching with a root filter, sm_103a: keyword
+// bytes mapped to 2- or 4-bit codes (small alphabets: the filter is exact over
+// windows of k codes), or 8-bit codes (any alphabet: the filter is hashed over
+// windows of kh = min(4, shortest keyword) codes, and survivors find their
+// depth-kh state in a hash of those states).
 //
 // pfac_filter_pipe -- persistent CTAs (one per SM), every warp on its own tiles
 // of 992 positions (two halves of 496), no block-wide barrier after start-up:
@@ -16,8 +19,10 @@
 //     first k characters with no keyword, i.e. the result is -1 -- almost every
 //     position of a text whose keywords are longer than k;
 //   * the other positions ("survivors") are resolved by one load from the
-//     window table (depth-k state or result), one from the stride table (k2
-//     more characters), and rarely the goto table one character at a time.  A
+//     window table (depth-k state or result; with 8-bit codes one bucket of
+//     the state hash), one from the stride table (k2 more characters), and
+//     the goto table one character at a time (chain records for the long
+//     unbranched runs of deep states).  A
 //     tile with at most one survivor per lane keeps them "in flight" across the
 //     next two tiles, so their dependent loads overlap other work; a tile with
 //     more finishes them at once, eight walks per lane per round of 256 (in the
@@ -65,6 +70,11 @@ constexpr unsigned kFull = 0xffffffffu;
 // Texts of at most this many tiles per warp of the grid take the forms that
 // share heavy tiles within the CTA.
 constexpr uint32_t kHelpTilesPerWarp = 16;
+// Walks per lane in one round of a tile with many survivors: 8 (rounds of
+// 256); with 8-bit codes, whose tiles hold about a hundred survivors each and
+// whose window lookups hold a 16-byte bucket per walk, 4 (rounds of 128).
+template <int B>
+__host__ __device__ constexpr int heavy_slots() { return B == 8 ? 4 : 8; }
 
 struct FilterParams {
     const uint8_t *text;
@@ -106,6 +116,15 @@ struct FilterParams {
     // more finished chunk than its offered tile has (a test of that wait)
     unsigned long long wait_ns;
     uint32_t stall_help;
+    // 8-bit codes: the codes are the bytes (256 columns), or classes from the
+    // byte table; the filter index is the top bits of (window & wmask) *
+    // kFilterHashMul (32 - fshift of them), the state hash's bucket the top
+    // hk_bits of (window & wmask) * kStateHashMul, probed over hk_probes buckets
+    uint32_t identity;
+    uint32_t wmask;
+    uint32_t fshift;
+    const uint4 *HK;
+    uint32_t hk_shift, hk_mask, hk_probes;
 };
 
 struct WarpSmem {
@@ -132,7 +151,7 @@ struct HelpSlot {
     uint32_t done;     // chunks finished, this publication
     uint32_t tile, item, total;
     long long gpb;
-    uint32_t flags;    // bit 0: interior, bit 1: clean
+    uint32_t flags;    // bit 0: interior, bit 1: clean, bit 2: results to the dense fallback too
     uint32_t su;       // slot-mode unit
 };
 
@@ -184,6 +203,56 @@ __device__ __forceinline__ void classify_word(const FilterParams &p, const uint8
     }
 }
 
+// 8-bit codes: the codes of the 4 bytes of w (the bytes themselves with 256
+// columns, else their classes from the byte table, 0xFF for a byte in no
+// keyword) and a word whose non-zero bytes mark bytes in no keyword.
+__device__ __forceinline__ void classify_word8(const FilterParams &p, const uint8_t *cls8, uint32_t w,
+                                               uint32_t &codes, uint32_t &unknown) {
+    if (p.identity) {
+        codes = w;
+        unknown = 0;
+        return;
+    }
+    const uint32_t t0 = cls8[__byte_perm(w, 0u, 0x4440u)], t1 = cls8[__byte_perm(w, 0u, 0x4441u)];
+    const uint32_t t2 = cls8[__byte_perm(w, 0u, 0x4442u)], t3 = cls8[__byte_perm(w, 0u, 0x4443u)];
+    codes = __byte_perm(__byte_perm(t0, t1, 0x0040u), __byte_perm(t2, t3, 0x0040u), 0x5410u);
+    const uint32_t x = ~codes;  // a zero byte: code 0xFF
+    unknown = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
+}
+
+// 8-bit codes: the depth-kh state whose window is w (already masked to kh
+// codes), given the first bucket b0 of its probe sequence (loaded by the
+// caller, so that several lookups overlap); -1 when no state has that window
+// (the encoded result -1: the walk stops before depth kh, where no keyword
+// ends).  Entries of a bucket fill in order, so a bucket with an empty entry
+// ends the probe sequence.
+__device__ __forceinline__ uint32_t hk_bucket(const FilterParams &p, uint32_t w) {
+    return (w * kStateHashMul) >> p.hk_shift;
+}
+
+__device__ __forceinline__ int hk_resolve(const FilterParams &p, uint32_t w, uint4 e) {
+    uint32_t b = hk_bucket(p, w);
+    for (uint32_t i = 0;;) {
+        if (e.y != 0u && e.x == w) return static_cast<int>(e.y);
+        if (e.w != 0u && e.z == w) return static_cast<int>(e.w);
+        if (e.y == 0u || e.w == 0u || ++i >= p.hk_probes) return -1;
+        b = (b + 1u) & p.hk_mask;
+        e = __ldg(p.HK + b);
+    }
+}
+
+// The window-table entry of window x (codes from the first position on): the
+// depth-k state, or the encoded result where the walk stops inside the window.
+template <int B>
+__device__ __forceinline__ int window_entry(const FilterParams &p, uint32_t x) {
+    if constexpr (B == 8) {
+        const uint32_t w = x & p.wmask;
+        return hk_resolve(p, w, __ldg(p.HK + hk_bucket(p, w)));
+    } else {
+        return __ldg(p.JK + (x & ((1u << (B * p.k)) - 1u)));
+    }
+}
+
 // One flag per non-zero byte of x (bit i for byte i).
 __device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
     const uint32_t t = ((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x;  // bit 7 of each byte: that byte != 0
@@ -199,7 +268,8 @@ __device__ __forceinline__ uint32_t pack4(uint32_t codes) {
     return (x | (x >> 8)) & 0xFFFFu;
 }
 
-// Codes of positions i.. (16 for B = 2, 8 for B = 4) from the packed stream.
+// Codes of positions i.. (16 for B = 2, 8 for B = 4, 4 for B = 8) from the
+// packed stream.
 template <int B>
 __device__ __forceinline__ uint32_t code_window(const uint32_t *packed, uint32_t i) {
     const uint32_t bo = B * i, w = bo >> 5;
@@ -209,9 +279,11 @@ __device__ __forceinline__ uint32_t code_window(const uint32_t *packed, uint32_t
 // Code of tile position q; false when q cannot extend a walk.  Positions below
 // `coded` have their codes in the packed stream already; later ones are read
 // from the text in global memory (the stage may already hold the next tile).
+// identity: 256 columns, the code is the byte (the byte table's 0xFF would
+// read as "in no keyword").
 template <int B>
 __device__ __forceinline__ bool fetch_code(const TileText &tt, const WarpSmem &w, int64_t gpb, uint32_t coded,
-                                           uint32_t q, uint32_t &c) {
+                                           uint32_t q, uint32_t &c, bool identity) {
     if (q < coded) {
         if ((w.inv[q >> 4] >> (q & 15u)) & 1u) return false;
         c = (w.packed[(B * q) >> 5] >> ((B * q) & 31u)) & ((1u << B) - 1u);
@@ -219,7 +291,12 @@ __device__ __forceinline__ bool fetch_code(const TileText &tt, const WarpSmem &w
     }
     const int64_t gp = gpb + static_cast<int64_t>(q);
     if (gp >= static_cast<int64_t>(tt.n)) return false;
-    const uint32_t v = w.cls8[__ldg(tt.text + gp)];
+    const uint32_t b = __ldg(tt.text + gp);
+    if (B == 8 && identity) {
+        c = b;
+        return true;
+    }
+    const uint32_t v = w.cls8[b];
     if (v == 0xFFu) return false;
     c = v;
     return true;
@@ -247,14 +324,17 @@ __device__ __forceinline__ int chain_step(const FilterParams &p, const TileText 
     return 0;
 }
 
-// Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)):
-// their results go to the pass's staging buffer (or are counted).  Returns
-// true when this lane found a keyword.
-template <int B, typename GT, int MODE, int SLOTS, bool DIRECT = false>
+// Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)) of a
+// tile whose dense ids were set to -1 first: the ids found go to the dense
+// output (MODE == OUT_DENSE; with FALLBACK to the unit's dense fallback
+// instead), are counted, or go to the unit's slots (dense_all: every result
+// also to the unit's dense fallback, set to -1 first).  Returns true when this
+// lane found a keyword.
+template <int B, typename GT, int MODE, int SLOTS, bool DIRECT = false, bool FALLBACK = false>
 __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const TileText &tt, const WarpSmem &w,
                                                  int64_t gpb, bool interior, bool clean, uint32_t avail,
                                                  uint32_t pbase, int lane, unsigned long long &cnt, uint32_t base,
-                                                 uint32_t coded = 0, uint32_t su = 0) {
+                                                 uint32_t coded = 0, uint32_t su = 0, bool dense_all = false) {
     const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k, k2 = p.k2;
     const GT *G = static_cast<const GT *>(p.G);
@@ -262,7 +342,8 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
     int v[SLOTS];
     uint32_t act = 0, pend = 0, walking = 0;
     uint32_t x[SLOTS];
-    // window table: depth-k state or result
+    uint4 hb[B == 8 ? SLOTS : 1];  // 8-bit codes: the first bucket of each window's state-hash probe
+    // window table (state hash): depth-k state or result; all loads first
 #pragma unroll
     for (int t = 0; t < SLOTS; ++t) {
         const uint32_t qi = lane + 32u * t;
@@ -279,12 +360,20 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
             q[t] = i;
             if (!(e16 >> 15)) {
                 x[t] = code_window<B>(w.packed, i);
-                v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
+                if constexpr (B == 8)
+                    hb[t] = __ldg(p.HK + hk_bucket(p, x[t] & p.wmask));
+                else
+                    v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
                 pend |= 1u << t;
             }
         }
     }
-    // stride table for the walks still alive at depth k
+    if constexpr (B == 8) {
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t)
+            if ((pend >> t) & 1u) v[t] = hk_resolve(p, x[t] & p.wmask, hb[t]);
+    }
+    // stride table for the walks still alive at depth k (none with 8-bit codes)
 #pragma unroll
     for (int t = 0; t < SLOTS; ++t) {
         if ((pend >> t) & 1u) {
@@ -296,18 +385,19 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
                 st[t] = static_cast<uint32_t>(e);
                 q[t] = ii[t] + k;
                 v[t] = INT_MIN;
-                bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(ii[t] + k + k2) <= n);
+                bool ok2 = B != 8 && k2 > 0 && (interior || gpb + static_cast<int64_t>(ii[t] + k + k2) <= n);
                 if (ok2 && !clean) {
                     const uint32_t j = ii[t] + k;
                     const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
                     ok2 = (wi & ((1u << k2) - 1u)) == 0;
                 }
-                if (ok2) {
-                    const uint32_t w2 = (x[t] >> (B * k)) & ((1u << (B * k2)) - 1u);
-                    v[t] = __ldg(p.J2 + ((static_cast<uint64_t>(st[t] - p.base_k) << (B * k2)) | w2));
-                } else {
-                    pend &= ~(1u << t);
+                if constexpr (B != 8) {
+                    if (ok2) {
+                        const uint32_t w2 = (x[t] >> (B * k)) & ((1u << (B * k2)) - 1u);
+                        v[t] = __ldg(p.J2 + ((static_cast<uint64_t>(st[t] - p.base_k) << (B * k2)) | w2));
+                    }
                 }
+                if (!ok2) pend &= ~(1u << t);
             }
         }
     }
@@ -355,7 +445,8 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
                     }
                 }
                 uint32_t c = 0;
-                const bool okc = fetch_code<B>(tt, w, gpb, DIRECT ? coded : pbase + kPass + 16u, q[t], c);
+                const bool okc =
+                    fetch_code<B>(tt, w, gpb, DIRECT ? coded : pbase + kPass + 16u, q[t], c, p.identity != 0);
                 // an unknown byte or the text end reads the row's end column,
                 // which always holds the result of stopping there
                 e[t] = goto_ld(G, st[t], p.W, okc ? c : p.C);
@@ -383,7 +474,7 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
             // one atomic per warp and slot index, ranks by ballot (all lanes)
             const bool hit = mine && v[t] >= 0;
             const unsigned m = __ballot_sync(kFull, hit);
-            if (mine && p.sl.dense) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + ii[t]] = v[t];
+            if (hit && dense_all) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + ii[t]] = v[t];
             if (m) {
                 uint32_t base = 0;
                 if (lane == 0) base = atomicAdd(p.sl.counts + su, static_cast<uint32_t>(__popc(m)));
@@ -400,11 +491,28 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
             found |= v[t] >= 0;
             if (MODE == OUT_COUNT)
                 cnt += v[t] >= 0 ? 1ull : 0ull;
-            else
+            else if (v[t] >= 0 && FALLBACK)
+                p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + ii[t]] = v[t];
+            else if (v[t] >= 0)  // the -1 of every other position is written already
                 tt.out[gpb + ii[t]] = v[t];
         }
     }
     return found;
+}
+
+// One warp, a tile whose matches overflowed its slots: the survivors walked
+// again, 64 at a time (rare, so with few registers), the ids found written to
+// the unit's dense fallback (set to -1 by the caller).
+template <int B, typename GT>
+__device__ __forceinline__ void refill_fallback(const FilterParams &p, const TileText &tt, const WarpSmem &w,
+                                                int64_t gpb, bool interior, bool clean, uint32_t total, int lane,
+                                                uint32_t su) {
+    unsigned long long none = 0;
+    for (uint32_t c = 0; 64u * c < total; ++c) {
+        finish_survivors<B, GT, OUT_DENSE, 2, true, true>(p, tt, w, gpb, interior, clean, total - 64u * c, 0, lane,
+                                                          none, 64u * c, kCodeSpan, su);
+        __syncwarp();
+    }
 }
 
 // One warp: claim a chunk of the tile offered in slot hs.  True (with the
@@ -468,8 +576,10 @@ __device__ __forceinline__ void help_chunk(const FilterParams &p, const Work &wk
     v.queue = reinterpret_cast<uint16_t *>(ws + p.off_queue);
     v.neg1 = reinterpret_cast<const int32_t *>(smem + p.off_neg1);
     const TileText tt = tile_text(p, wk, tile, item);
-    finish_survivors<B, GT, MODE, 8, true>(p, tt, v, gpb, (flags & 1u) != 0, (flags & 2u) != 0, total - 256u * c, 0,
-                                           lane, cnt, 256u * c, kCodeSpan, su);
+    constexpr uint32_t kRound = 32u * heavy_slots<B>();
+    finish_survivors<B, GT, MODE, heavy_slots<B>(), true>(p, tt, v, gpb, (flags & 1u) != 0, (flags & 2u) != 0,
+                                                          total - kRound * c, 0, lane, cnt, kRound * c, kCodeSpan, su,
+                                                          (flags & 4u) != 0);
     __threadfence_block();
     __syncwarp();
     if (lane == 0) atomicAdd(&hs->done, 1u);
@@ -532,8 +642,9 @@ __device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t 
         const int64_t gp = gpb + static_cast<int64_t>(q);
         uint32_t c = p.C;  // the end column: stop here
         if (gp < static_cast<int64_t>(tt.n)) {
-            const uint32_t v = cls8[__ldg(tt.text + gp)];
-            if (v != 0xFFu) c = v;
+            const uint32_t b = __ldg(tt.text + gp);
+            const uint32_t v = p.identity ? b : cls8[b];  // 256 columns: the byte itself
+            if (p.identity || v != 0xFFu) c = v;
         }
         const int t = goto_ld(G, s, p.W, c);
         if (t < 0) return decode_dead(t);
@@ -651,7 +762,7 @@ __device__ __forceinline__ void flight_output(const FilterParams &p, const Work 
 // HELP: share heavy tiles within the CTA (the forms for one text that is short
 // next to the grid; see the heavy path below).
 template <int B, typename GT, int MODE, bool BATCH, bool HELP>
-__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterParams p) {
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_constant__ FilterParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
@@ -750,15 +861,23 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
 
         // 1. classify the tile's bytes (both halves), once per byte
         uint32_t plo[2], phi[2], inv[2];
+        uint32_t p8[2][4];  // 8-bit codes: the lane's 16 codes of each half
 #pragma unroll
         for (uint32_t h = 0; h < 2; ++h) {
             const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
             const uint4 raw = *reinterpret_cast<const uint4 *>(st + i0);
             uint32_t c0, c1, c2, c3, u0, u1, u2, u3;
-            classify_word(p, w.cls8, raw.x, c0, u0);
-            classify_word(p, w.cls8, raw.y, c1, u1);
-            classify_word(p, w.cls8, raw.z, c2, u2);
-            classify_word(p, w.cls8, raw.w, c3, u3);
+            if constexpr (B == 8) {
+                classify_word8(p, w.cls8, raw.x, c0, u0);
+                classify_word8(p, w.cls8, raw.y, c1, u1);
+                classify_word8(p, w.cls8, raw.z, c2, u2);
+                classify_word8(p, w.cls8, raw.w, c3, u3);
+            } else {
+                classify_word(p, w.cls8, raw.x, c0, u0);
+                classify_word(p, w.cls8, raw.y, c1, u1);
+                classify_word(p, w.cls8, raw.z, c2, u2);
+                classify_word(p, w.cls8, raw.w, c3, u3);
+            }
             uint32_t iv = 0;
             if (u0 | u1 | u2 | u3)
                 iv = nonzero_bytes(u0) | (nonzero_bytes(u1) << 4) | (nonzero_bytes(u2) << 8) |
@@ -772,15 +891,23 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                 }
             }
             inv[h] = iv;
-            if (B == 2) {
+            if constexpr (B == 2) {
                 plo[h] = pack4<2>(c0) | (pack4<2>(c1) << 8) | (pack4<2>(c2) << 16) | (pack4<2>(c3) << 24);
                 phi[h] = 0;
                 w.packed[i0 >> 4] = plo[h];
-            } else {
+            } else if constexpr (B == 4) {
                 plo[h] = pack4<4>(c0) | (pack4<4>(c1) << 16);
                 phi[h] = pack4<4>(c2) | (pack4<4>(c3) << 16);
                 w.packed[i0 >> 3] = plo[h];
                 w.packed[(i0 >> 3) + 1] = phi[h];
+            } else {
+                p8[h][0] = c0;
+                p8[h][1] = c1;
+                p8[h][2] = c2;
+                p8[h][3] = c3;
+                plo[h] = c0;
+                phi[h] = 0;
+                *reinterpret_cast<uint4 *>(w.packed + (i0 >> 2)) = make_uint4(c0, c1, c2, c3);
             }
             w.inv[i0 >> 4] = static_cast<uint16_t>(iv);
         }
@@ -807,11 +934,16 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     uint32_t win;
-                    if (B == 2)
+                    if constexpr (B == 2) {
                         win = __funnelshift_r(plo[h], nlo[h], 2 * r);
-                    else
+                    } else if constexpr (B == 4) {
                         win = r < 8 ? __funnelshift_r(plo[h], phi[h], 4 * r)
                                     : __funnelshift_r(phi[h], nlo[h], 4 * (r - 8));
+                    } else {
+                        // 8-bit codes: the filter bit's index is a hash of the window
+                        const uint32_t lo = p8[h][r >> 2], hi = (r >> 2) < 3 ? p8[h][(r >> 2) + 1] : nlo[h];
+                        win = ((__funnelshift_r(lo, hi, 8 * (r & 3)) & p.wmask) * kFilterHashMul) >> p.fshift;
+                    }
                     const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & p.famask));
                     acc = __funnelshift_l(__funnelshift_l(word, word, win), acc, 1);
                 }
@@ -831,7 +963,12 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                     const int64_t gp = gpb + i0 + r;
                     if (owner && gp >= 0 && gp < n) {
                         valid |= 1u << (16 * h + r);
-                        if (gp + static_cast<int64_t>(k) > n || ((iw >> r) & kbits)) slowm |= 1u << (16 * h + r);
+                        // a window past the text end; with small alphabets also one
+                        // holding a byte in no keyword (a shorter keyword may end
+                        // before it; with 8-bit codes such a window has no state
+                        // in the hash, and no keyword ends before depth k)
+                        if (gp + static_cast<int64_t>(k) > n || (B != 8 && ((iw >> r) & kbits)))
+                            slowm |= 1u << (16 * h + r);
                     }
                 }
             }
@@ -896,19 +1033,26 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                 }
                 __syncwarp();
             }
-            if (MODE == OUT_SLOTS && p.sl.dense) {
-                // the tile may overflow its slots: keep its dense ids, -1 first
+            // slots: a tile whose survivors are most of its positions will
+            // likely hold more matches than its slots, so its dense ids are
+            // kept as they are found (-1 first); the others keep them only if
+            // their matches do overflow (a second pass below)
+            const bool dense_all = MODE == OUT_SLOTS && p.sl.dense && total > kTile / 2;
+            int32_t *const fdn =
+                MODE == OUT_SLOTS && p.sl.dense ? p.sl.dense + static_cast<uint64_t>(p.sl.ubase + tile) * kDenseStride
+                                                : nullptr;
+            if (dense_all) {
                 if (owner) {
-                    int32_t *dn = p.sl.dense + static_cast<uint64_t>(p.sl.ubase + tile) * kDenseStride;
 #pragma unroll
                     for (uint32_t h = 0; h < 2; ++h)
 #pragma unroll
                         for (uint32_t g = 0; g < 4; ++g)
-                            *reinterpret_cast<int4 *>(dn + h * kPass + 16u * lane + 4u * g) = make_int4(-1, -1, -1, -1);
+                            *reinterpret_cast<int4 *>(fdn + h * kPass + 16u * lane + 4u * g) = make_int4(-1, -1, -1, -1);
                 }
                 __syncwarp();
             }
-            const uint32_t nchunks = (total + 255u) / 256u;
+            constexpr uint32_t kRound = 32u * heavy_slots<B>();
+            const uint32_t nchunks = (total + kRound - 1u) / kRound;
             // more than one round (HELP forms): offer the rounds to the CTA's
             // warps that run out of tiles (now or while this warp works), take
             // rounds too, then wait until the helpers are done with this warp's
@@ -923,7 +1067,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                     my_help->item = item;
                     my_help->total = total;
                     my_help->gpb = gpb;
-                    my_help->flags = (interior ? 1u : 0u) | (clean ? 2u : 0u);
+                    my_help->flags = (interior ? 1u : 0u) | (clean ? 2u : 0u) | (dense_all ? 4u : 0u);
                     my_help->su = p.sl.ubase + tile;
                     my_help->nchunks = nchunks;
                     my_help->done = 0;
@@ -937,8 +1081,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
             for (uint32_t next = 0;;) {
                 uint32_t c = next++;
                 if (offer ? !claim_chunk(my_help, lane, c) : c >= nchunks) break;
-                finish_survivors<B, GT, MODE, 8, true>(p, tt, w, gpb, interior, clean, total - 256u * c, 0, lane,
-                                                       cnt, 256u * c, kCodeSpan, p.sl.ubase + tile);
+                finish_survivors<B, GT, MODE, heavy_slots<B>(), true>(p, tt, w, gpb, interior, clean,
+                                                                      total - kRound * c, 0, lane, cnt, kRound * c,
+                                                                      kCodeSpan, p.sl.ubase + tile, dense_all);
                 __syncwarp();
                 if (offer && lane == 0) atomicAdd(&my_help->done, 1u);
             }
@@ -955,6 +1100,25 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                 atomicSub(offers, 1u);
             }
             __syncwarp();
+            if (MODE == OUT_SLOTS && fdn && !dense_all) {
+                // every round is done: when the tile's matches overflow its
+                // slots after all, keep its dense ids (-1, then a second pass
+                // over the survivors writing the ids found)
+                uint32_t found_all = 0;
+                if (lane == 0) found_all = atomicAdd(p.sl.counts + p.sl.ubase + tile, 0u);
+                if (__shfl_sync(kFull, found_all, 0) > kSlotCap) {
+                    if (owner) {
+#pragma unroll
+                        for (uint32_t h = 0; h < 2; ++h)
+#pragma unroll
+                            for (uint32_t g = 0; g < 4; ++g)
+                                *reinterpret_cast<int4 *>(fdn + h * kPass + 16u * lane + 4u * g) =
+                                    make_int4(-1, -1, -1, -1);
+                    }
+                    __syncwarp();
+                    refill_fallback<B, GT>(p, tt, w, gpb, interior, clean, total, lane, p.sl.ubase + tile);
+                }
+            }
             continue;
         }
 
@@ -974,14 +1138,17 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const FilterPar
                 f0.q = i;
             } else {
                 const uint32_t x = code_window<B>(w.packed, i);
-                f0.val = __ldg(p.JK + (x & ((1u << (B * k)) - 1u)));
+                f0.val = window_entry<B>(p, x);
                 f0.phase = kPhJK;
-                f0.w2 = (x >> (B * k)) & ((1u << (B * k2)) - 1u);
-                bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(i + k + k2) <= n);
-                if (ok2 && !clean) {
-                    const uint32_t j = i + k;
-                    const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
-                    ok2 = (wi & ((1u << k2) - 1u)) == 0;
+                bool ok2 = false;
+                if constexpr (B != 8) {  // no stride table with 8-bit codes
+                    f0.w2 = (x >> (B * k)) & ((1u << (B * k2)) - 1u);
+                    ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(i + k + k2) <= n);
+                    if (ok2 && !clean) {
+                        const uint32_t j = i + k;
+                        const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
+                        ok2 = (wi & ((1u << k2) - 1u)) == 0;
+                    }
                 }
                 f0.ok2 = ok2 ? 1u : 0u;
             }
@@ -1104,5 +1271,8 @@ cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uin
 // Launch of the forms that share heavy tiles (one text only), filter_help.cu.
 cudaError_t launch_filter_help(OutMode mode, const filt::FilterParams &p, uint32_t B, uint32_t gbits, uint32_t grid,
                                uint32_t block, uint32_t smem, int max_smem, cudaStream_t stream);
+// Launch of the 8-bit-code forms (hashed filter), filter8.cu.
+cudaError_t launch_filter8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t grid, uint32_t block,
+                           uint32_t smem, int max_smem, cudaStream_t stream);
 
 }  // namespace pfac

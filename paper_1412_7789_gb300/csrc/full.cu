@@ -197,7 +197,7 @@ size_t full_scratch_bytes(const DevTables &t, uint32_t units) {
 
 cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
                          const CompactOut &out, void *scratch, size_t scratch_bytes, cudaStream_t stream) {
-    const uint32_t U = compact_units(t, text, n);
+    const uint32_t U = compact_units(t, tu, text, n);
     if (U == 0xFFFFFFFFu || n == 0 || n > 0xFFFFFFFFull || !t.full_rec || !t.full_dups)
         return cudaErrorInvalidValue;
     if (!scratch || scratch_bytes < full_scratch_bytes(t, U)) return cudaErrorInvalidValue;
@@ -223,7 +223,7 @@ cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *te
     r.slots.dense = dn;
     r.scratch = b;
     r.scratch_bytes = 16;
-    e = t.filter ? launch_filter(t, r, OUT_SLOTS, tu, stream) : launch_tiled(t, r, OUT_SLOTS, tu, stream);
+    e = launch_match(t, r, OUT_SLOTS, tu, stream);
     if (e != cudaSuccess) return e;
 
     int dev = 0, sms = 0;
@@ -233,7 +233,7 @@ cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *te
     FullParams p{};
     p.n = n;
     p.units = U;
-    p.tile = t.filter ? filter_tile_positions() : tiled_tile_positions();
+    p.tile = unit_positions(t, tu);
     p.head = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(text) & 15u);
     p.max_clen = t.full_max_clen;
     p.nkw = t.nkw;

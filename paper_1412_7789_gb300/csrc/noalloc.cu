@@ -59,7 +59,7 @@ extern "C" ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text,
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n == 0) return cudaMemsetAsync(d_count, 0, sizeof(uint64_t), st) == cudaSuccess ? AC_OK : AC_ERR_CUDA;
     if (!d_text) return AC_ERR_INVALID_ARG;
-    const uint32_t units = pfac::compact_units(*t, d_text, n);
+    const uint32_t units = pfac::compact_units(*t, *pfac::handle_tuning(h), d_text, n);
     // no dense fallback here: a tile with many matches is matched again by the gather step
     const size_t bytes = pfac::compact_scratch_bytes(*t, units, false);
     if (bytes > AC_STATIC_SCRATCH_BYTES) return AC_ERR_BUDGET;

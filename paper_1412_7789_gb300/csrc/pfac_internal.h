@@ -36,6 +36,13 @@ enum : unsigned { kErrTimeout = 1u, kErrWalk = 2u, kErrBatchItem = 8u };
 // Window bits of the root filter (2- and 4-bit codes): 2^20 bits = 128 KiB.
 constexpr uint32_t kFilterBits = 20;
 
+// 8-bit codes: the hashed root filter and the hash of the depth-kh states
+// index a window w of kh codes (first code lowest) by the top bits of
+// w * kFilterHashMul and w * kStateHashMul (mod 2^32).
+constexpr uint32_t kFilterHashMul = 0x9E3779B1u;
+constexpr uint32_t kStateHashMul = 0x85EBCA77u;
+constexpr uint32_t kHashWindow = 4;  // codes per hashed window (at most)
+
 // Longest halo staged in shared memory; walks that run past it read global memory.
 constexpr uint32_t kHaloCap = 256;
 
@@ -98,6 +105,16 @@ struct HostTables {
     uint32_t s_chain = 0;
     std::vector<uint32_t> skip;
     std::vector<uint8_t> chain;
+    // 8-bit codes: a hashed root filter over windows of kh = min(4, shortest
+    // keyword) codes, in F (2^fbits bits, the same bit layout as the small
+    // alphabets' filter): the bit of the window of every depth-kh state is
+    // set, so a clear bit means the walk stops before depth kh, where no
+    // keyword ends (result -1).  HK: the depth-kh states by their window, in
+    // 2^hk_bits buckets of two {window, state} entries (state 0: empty),
+    // linear probing over at most hk_probes buckets.
+    bool hashed = false;
+    uint32_t kh = 0, fbits = 0, hk_bits = 0, hk_probes = 0;
+    std::vector<uint32_t> HK;
     // Full output: 4 words per keyword id {up, len, dup_off, clen} (set for
     // the lowest id of each keyword string, the id a walk reports), the ids
     // grouped by string, and the largest clen.
@@ -122,7 +139,10 @@ struct DevTables {
     const uint32_t *F = nullptr;     // root filter bits (device copy, for the bulk load)
     const int32_t *JK = nullptr;     // window table (filter mode)
     uint32_t fbytes = 0;             // bytes of F
-    bool filter = false;
+    bool filter = false;             // 2- and 4-bit codes: root filter + window table
+    bool hashed = false;             // 8-bit codes: hashed root filter + state hash
+    const uint4 *HK = nullptr;       // state hash buckets (hashed)
+    uint32_t kh = 0, fbits = 0, hk_bits = 0, hk_probes = 0;
     const int32_t *J2 = nullptr;     // stride table
     const uint4 *skip = nullptr;     // chain records (states from s_chain on), or none
     const uint8_t *chain = nullptr;  // chain bytes
@@ -246,7 +266,7 @@ cudaError_t launch_compact_gather(const DevTables &t, const GatherRequest &g, cu
 // bytes (cleared here), units = compact_units(t, text, n).  dense: keep the
 // per-unit dense fallback (4 bytes per position) so that units with many
 // matches are copied, not matched again.
-uint32_t compact_units(const DevTables &t, const uint8_t *text, uint64_t n);
+uint32_t compact_units(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n);
 size_t compact_scratch_bytes(const DevTables &t, uint32_t units, bool dense);
 cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
                             const CompactOut &out, void *scratch, size_t scratch_bytes, bool dense,
@@ -307,14 +327,28 @@ constexpr uint32_t kMaxBatchAutomata = 256;
 cudaError_t launch_batch_plan(const ac_batch_item *items, uint32_t nitems, uint32_t nh, const uint8_t *texts,
                               const uint32_t *tile_len, BatchHead *heads, BatchItemDev *lists, cudaStream_t stream);
 
-// Filter-mode kernel (2- and 4-bit codes), in filter.cu.  Modes: dense,
-// count, slots.  Every launch takes 16 bytes of zeroed scratch (tile counter).
+// Filter-mode kernel (2- and 4-bit codes; 8-bit codes with the hashed
+// filter), in filter.cu.  Modes: dense, count, slots.  Every launch takes 16
+// bytes of zeroed scratch (tile counter).
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                           cudaStream_t stream);
 // Positions per work unit (tile) of the dense filter kernel and of the dense
-// 8-bit kernel: the tile lengths a batch is planned with.
+// 8-bit kernels: the tile lengths a batch is planned with.
 uint32_t filter_tile_positions();
 uint32_t tiled_tile_positions();
+
+// The filter kernel serves an automaton: always for 2- and 4-bit codes; for
+// 8-bit codes (hashed filter) unless another kernel was chosen (Tuning::variant).
+inline bool uses_filter(const DevTables &t, const Tuning &tu) { return t.filter || (t.hashed && tu.variant == 0); }
+// Positions per work unit of the kernel that serves the automaton.
+inline uint32_t unit_positions(const DevTables &t, const Tuning &tu) {
+    return uses_filter(t, tu) ? filter_tile_positions() : tiled_tile_positions();
+}
+// A matching launch on the kernel that serves the automaton.
+inline cudaError_t launch_match(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
+                                cudaStream_t stream) {
+    return uses_filter(t, tu) ? launch_filter(t, r, mode, tu, stream) : launch_tiled(t, r, mode, tu, stream);
+}
 
 // One-thread-per-position 8-bit kernel (jump8.cu); same modes, scratch and
 // tile length as launch_tiled, which hands over to it for Tuning::variant 2.

@@ -91,22 +91,20 @@ struct ac_server_impl {
 
 namespace {
 
-uint32_t tile_of(const pfac::DevTables &t) {
-    return t.filter ? pfac::filter_tile_positions() : pfac::tiled_tile_positions();
-}
+uint32_t tile_of(const pfac::DevTables &t, const pfac::Tuning &tu) { return pfac::unit_positions(t, tu); }
 
-uint64_t units_of(const pfac::DevTables &t, const uint8_t *text, uint64_t n) {
+uint64_t units_of(const pfac::DevTables &t, const pfac::Tuning &tu, const uint8_t *text, uint64_t n) {
     if (n == 0) return 0;
-    const uint64_t T = tile_of(t);
+    const uint64_t T = tile_of(t, tu);
     const uint64_t head = reinterpret_cast<uintptr_t>(text) & 15u;
     return (n + head + T - 1) / T;
 }
 
 // Device bytes a request holds while admitted: its text, its output and the
 // scratch of its tiles (counts, prefix, slots, dense fallback).
-uint64_t request_bytes(const pfac::DevTables &t, const ac_server_request &r) {
+uint64_t request_bytes(const pfac::DevTables &t, const pfac::Tuning &tu, const ac_server_request &r) {
     const uint64_t per_unit = 4 + 8 + 8ull * pfac::kSlotCap + 4ull * pfac::kDenseStride;
-    return r.n + 8ull * r.cap + units_of(t, r.d_text, r.n) * per_unit + 64;
+    return r.n + 8ull * r.cap + units_of(t, tu, r.d_text, r.n) * per_unit + 64;
 }
 
 cudaError_t ensure_host(WaveSlot &w, size_t bytes) {
@@ -133,7 +131,8 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         const Request &q = w.reqs[0];
         if (q.r.n == 0) return cudaMemsetAsync(q.r.d_count, 0, sizeof(uint64_t), w.stream);
         const pfac::DevTables &t = *s->tabs[q.r.automaton];
-        const size_t bytes = pfac::compact_scratch_bytes(t, pfac::compact_units(t, q.r.d_text, q.r.n), true);
+        const size_t bytes =
+            pfac::compact_scratch_bytes(t, pfac::compact_units(t, s->tune[q.r.automaton], q.r.d_text, q.r.n), true);
         void *scratch = nullptr;
         e = cudaMallocFromPoolAsync(&scratch, bytes, pool, w.stream);
         if (e != cudaSuccess) return e;
@@ -184,7 +183,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
             d.out_off = 0;
             d.first_unit = static_cast<uint32_t>(units);
             d.item = order[j];
-            units += units_of(t, r.d_text, r.n);
+            units += units_of(t, s->tune[a], r.d_text, r.n);
             ++j;
         }
         heads[a].count = j - heads[a].offset;
@@ -243,8 +242,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         m.scratch = counters + 16u * a;
         m.scratch_bytes = 16;
         const pfac::DevTables &t = *s->tabs[a];
-        e = t.filter ? pfac::launch_filter(t, m, pfac::OUT_SLOTS, s->tune[a], w.stream)
-                     : pfac::launch_tiled(t, m, pfac::OUT_SLOTS, s->tune[a], w.stream);
+        e = pfac::launch_match(t, m, pfac::OUT_SLOTS, s->tune[a], w.stream);
     }
     if (e == cudaSuccess)
         e = pfac::launch_compact_scan(counts, static_cast<uint32_t>(U), nullptr, prefix, partials, w.stream);
@@ -255,7 +253,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         g.batch = d_heads + a;
         g.lists = d_list;
         g.outs = d_outs;
-        g.tile = tile_of(*s->tabs[a]);
+        g.tile = tile_of(*s->tabs[a], s->tune[a]);
         g.counts = counts;
         g.prefix = prefix;
         g.slots = slots;
@@ -441,7 +439,7 @@ ac_status ac_server_submit(ac_server s, const ac_server_request *req, uint64_t *
     if (r.cap > 0 && (!r.d_pos || !r.d_ids)) return AC_ERR_INVALID_ARG;
     Request q;
     q.r = r;
-    q.bytes = request_bytes(*s->tabs[r.automaton], r);
+    q.bytes = request_bytes(*s->tabs[r.automaton], s->tune[r.automaton], r);
     if (q.bytes > s->budget) return AC_ERR_BUDGET;
     {
         std::lock_guard<std::mutex> lk(s->mu);

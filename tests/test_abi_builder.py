@@ -499,6 +499,91 @@ def test_root_jump_table(lib, kw):
     assert np.all(want[slow] > 32767) and np.all((res[slow] > 32767))
 
 
+def _hk_find(HK, hk_bits, probes, w):
+    """Lookup in the state hash as ac.h documents it: from bucket
+    (w * 0x85EBCA77 mod 2^32) >> (32 - hk_bits), at most `probes` buckets,
+    stopping at a bucket with an empty entry; 0 = no state."""
+    b = ((w * 0x85EBCA77) & 0xFFFFFFFF) >> (32 - hk_bits)
+    for _ in range(probes):
+        e = HK[b]
+        for j in (0, 2):
+            if e[j + 1] != 0 and e[j] == w:
+                return int(e[j + 1])
+        if e[1] == 0 or e[3] == 0:
+            return 0
+        b = (b + 1) % HK.shape[0]
+    return 0
+
+
+@pytest.mark.parametrize("case", ["zipf", "zipf_256cols", "short_keywords", "long_only"])
+def test_hashed_filter_and_state_hash(lib, case):
+    """8-bit codes: for every state at depth kh (= min(4, shortest keyword)),
+    the walk of its kh codes through the goto table reaches it, its window's
+    filter bit is set and the state hash finds it; windows whose walk does not
+    reach depth kh (random ones, and every depth-kh window with one code
+    changed) are not found."""
+    g = np.random.default_rng(3)
+    kw = {}
+    if case.startswith("zipf"):
+        _, pats = workloads.zipf_byte(1 << 18, seed=9, n_keywords=3000)
+        if case == "zipf_256cols":
+            kw = {"class_compress": False}
+    elif case == "short_keywords":
+        pats = [bytes(g.integers(0, 256, size=int(g.integers(2, 9)), dtype=np.uint8)) for _ in range(700)]
+    else:
+        pats = [bytes(g.integers(30, 90, size=int(g.integers(6, 40)), dtype=np.uint8)) for _ in range(500)]
+    h = api.ac_compile(pats, host_only=True, **kw)
+    try:
+        kh, fbits, hk_bits, probes, F, HK = api.ac_export_hash(h)
+        cls, G, depth = api.ac_export_tables(h)
+        info = api.ac_info(h)
+    finally:
+        api.ac_destroy(h)
+    assert info["code_bits"] == 8
+    assert kh == min(4, min(len(p) for p in pats)) and fbits == 20 and probes >= 1
+    C = info["n_classes"]
+    G = G.reshape(info["n_states"], info["row_width"]).astype(np.int64)
+    base = int(depth[:kh].sum())
+    states = np.arange(base, base + int(depth[kh]))
+
+    def walk(wins):
+        s = np.zeros(wins.size, dtype=np.int64)
+        alive = np.ones(wins.size, dtype=bool)
+        for i in range(kh):
+            c = (wins >> np.int64(8 * i)) & 0xFF
+            e = G[s, np.where(c < C, c, C)]
+            alive &= e > 0
+            s = np.where(alive, e, 0)
+        return np.where(alive, s, 0)
+
+    # the window of every depth-kh state: the codes along its path, from the
+    # goto table (BFS order: a state's parent is the row holding it)
+    par = np.zeros(G.shape[0], dtype=np.int64)
+    code = np.zeros(G.shape[0], dtype=np.int64)
+    rows, cols = np.nonzero(G[:, :C] > 0)
+    par[G[rows, cols]] = rows
+    code[G[rows, cols]] = cols
+    wins = np.zeros(states.size, dtype=np.int64)
+    for j in range(kh):
+        anc = states.copy()
+        for _ in range(kh - 1 - j):
+            anc = par[anc]
+        wins |= code[anc] << np.int64(8 * j)
+    assert np.array_equal(walk(wins), states)
+    f = ((wins * 0x9E3779B1) & 0xFFFFFFFF) >> (32 - fbits)
+    assert np.all((F[f >> 5] >> (31 - (f & 31))) & 1)
+    assert all(_hk_find(HK, hk_bits, probes, int(w)) == int(s) for w, s in zip(wins, states))
+    # windows whose walk stops before depth kh are not in the hash
+    rnd = g.integers(0, 1 << (8 * kh), size=4000, dtype=np.int64)
+    mutated = wins ^ (np.int64(1) << np.int64(8 * g.integers(0, kh, size=wins.size)))
+    for cand in (rnd, mutated):
+        reach = walk(cand)
+        for w, s in zip(cand[:3000], reach[:3000]):
+            assert _hk_find(HK, hk_bits, probes, int(w)) == int(s)
+    # the filter keeps few windows: at most one bit per depth-kh state
+    assert int(np.unpackbits(F.view(np.uint8)).sum()) <= states.size
+
+
 def test_c_program_uses_the_library(lib, tmp_path):
     """A plain C program (no Python) compiles against ac.h, links the shared
     library and builds a host-only automaton: he/she/his/hers gives 10 states,
