@@ -43,8 +43,8 @@ KNOWN_TRAFFIC: dict = {}
 def kernel_name(info: dict, out_kind: str, kernel: str) -> str:
     if kernel == "simple":
         return "pfac_simple"
-    if info["code_bits"] <= 4:
-        name = "pfac_filter_pipe"
+    if info["code_bits"] <= 4 or kernel == "tiled":
+        name = "pfac_filter_pipe"  # 8-bit codes: its hashed-filter form
     else:
         name = {"thread_jump": "pfac_jump8", "walk_slots": "pfac_walk8"}.get(kernel, "pfac_jump8g")
     # the compacted list: the matcher in slot mode, then scan and gather; the
@@ -939,7 +939,7 @@ def run_serve(args):
     build_s = time.perf_counter() - t0
     handles = [a.handle for a in autos]
     table_bytes = sum(a.info()["table_bytes"] for a in autos)
-    budget = int(40e9) - table_bytes
+    budget = int(40e9)  # the server counts the resident automata in it
 
     n_max = max(args.serve_requests)
     which, offs, lens = W.serve_requests(n_max, pool_bytes, seed=0)
@@ -1007,7 +1007,7 @@ def run_serve(args):
                                "4-100, 8 ACGT + 8 Zipf), compacted (pos,id) per request, 40 GB budget" % (
                                    list(args.serve_rates), pool_bytes, pool_bytes)},
         "serve": rows, "clocks": sampler.summary(m0, m1),
-        "extra": {"automata_table_bytes": table_bytes, "request_budget_bytes": budget,
+        "extra": {"automata_table_bytes": table_bytes, "request_budget_bytes": budget - table_bytes,
                   "host_build_s": build_s, "generate_s": gen_s, "parity_requests_checked": checked},
     }
     print(json.dumps(line), flush=True)

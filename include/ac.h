@@ -50,7 +50,8 @@ typedef enum {
     AC_ERR_OVERFLOW = 6,        /* compacted output: more matches than capacity   */
     AC_ERR_BUDGET = 7,          /* request larger than the configured budget      */
     AC_ERR_TIMEOUT = 8,         /* a bounded device-side wait ran out             */
-    AC_ERR_NOT_FOUND = 9        /* unknown id (server requests)                   */
+    AC_ERR_NOT_FOUND = 9,       /* unknown id (server requests)                   */
+    AC_ERR_CANCELLED = 10       /* a server request cancelled before its launch   */
 } ac_status;
 
 /* Which matching kernel a handle uses (ac_set_kernel).  Results never depend
@@ -211,11 +212,15 @@ ac_status ac_export_filter(ac_handle h, uint32_t *F, int32_t *JK, uint32_t *B, u
  *   F   uint32[2^fbits / 32]: with f = (w * 0x9E3779B1 mod 2^32) >> (32 - fbits),
  *       bit 31 - (f & 31) of word f >> 5 is set for the window of every state
  *       at depth kh (a clear bit: result -1; other windows may share a bit).
- *   HK  uint32[4 * 2^hk_bits]: buckets of two {window, state} entries (state 0:
- *       empty).  The depth-kh state with window w is in the first bucket with
- *       room at or after bucket (w * 0x85EBCA77 mod 2^32) >> (32 - hk_bits)
- *       (cyclically), at most *probes buckets from it; a window found in none
- *       of those buckets, or before a bucket with an empty entry, has no state.
+ *   HK  uint32[4 * 2^hk_bits]: entries {window, state, child, info} (state 0:
+ *       empty).  The depth-kh state with window w is in the first empty entry
+ *       at or after entry (w * 0x85EBCA77 mod 2^32) >> (32 - hk_bits)
+ *       (cyclically), at most *probes entries from it; a window met by no
+ *       entry before an empty one, or within *probes entries, has no state.
+ *       child: the state's only child, 0 when it has none, 0xFFFFFFFF when it
+ *       has several (or its result does not fit 24 bits); info: the child's
+ *       code << 24 | (the state's result + 1), the result being the longest
+ *       keyword ending on the path to the state (-1: none).
  * *kh = 0 and zero sizes for an automaton without them (2- or 4-bit codes).
  * Call with NULL arrays to get the sizes.
  */
@@ -441,13 +446,21 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
  * No counterpart in the paper.  A server keeps nh compiled automata (the
  * caller's handles, resident on the device) and a worker thread that turns the
  * stream of requests into launch waves:
- *   - a request names an automaton and a device text, and gets the compacted
+ *   - a request names an automaton and a text -- in device memory (the primary
+ *     path: a device-resident pool), or in pinned host memory (the secondary
+ *     path: the wave copies it to the device first) -- and gets the compacted
  *     (pos, id) list of that text as ac_match_compact would give it, in caller
- *     buffers (d_pos, d_ids, cap, d_count with the same meaning);
- *   - requests are admitted in arrival order while the bytes they hold on the
- *     device (text + 8 * cap output + about 0.27 byte of scratch per text byte)
- *     fit in the HBM budget; a request larger than the whole budget is refused
- *     with AC_ERR_BUDGET at submission;
+ *     device buffers (d_pos, d_ids, cap, d_count with the same meaning);
+ *   - the HBM budget covers the resident automata (their tables, counted once
+ *     per handle at ac_server_create) and the requests in flight; requests are
+ *     admitted in arrival order while the bytes they hold on the device fit in
+ *     what the automata leave: the text (or its device copy), 8 * cap of output
+ *     and the scratch of its tiles of about 1 KiB (a match count, a prefix, 32
+ *     match slots and a dense fallback of 4 bytes per position, which a tile
+ *     writes only when its matches overflow the slots): about 4.4 bytes per
+ *     text byte.  A request larger than the whole budget is refused with
+ *     AC_ERR_BUDGET at submission, and a server whose automata alone exceed
+ *     the budget at creation;
  *   - every admitted request that is not yet on the GPU joins the next wave:
  *     one persistent launch per automaton over the tiles of all its requests,
  *     then one scan and one gather, so requests of any size share the launches;
@@ -457,11 +470,19 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
  * A request's results are the same whatever else shares its wave.
  *
  * Options (zero = default):
- *   hbm_budget       device bytes of admitted requests (default 40 GiB)
+ *   hbm_budget       device bytes of the resident automata and the admitted
+ *                    requests (default 40 GiB)
  *   max_wave         most requests per wave (default 4096)
  *   waves_in_flight  waves on the GPU at once (default 2, at most 8)
  *   fifo             1 = the comparison point: one request per wave, one wave
  *                    at a time, matched by the single-text ac_match_compact path
+ *   dev_alloc / dev_free / alloc_ctx
+ *                    optional allocator of each wave's device scratch (plan,
+ *                    host-text copies, tile scratch), e.g. a framework's caching
+ *                    allocator; NULL = the library's stream-ordered pool.  A
+ *                    wave's scratch is freed once the wave has completed; when
+ *                    dev_alloc returns NULL the wave's requests complete with
+ *                    AC_ERR_OOM.  Called from the server's worker thread.
  */
 typedef struct ac_server_impl *ac_server;
 
@@ -470,13 +491,20 @@ typedef struct {
     uint32_t max_wave;
     uint32_t waves_in_flight;
     uint32_t fifo;
-    uint32_t reserved;
+    uint32_t reserved;       /* 0 */
+    void *(*dev_alloc)(size_t bytes, void *ctx);
+    void (*dev_free)(void *ptr, void *ctx);
+    void *alloc_ctx;
 } ac_server_options;
+
+/* ac_server_request.flags: the text is in pinned host memory. */
+#define AC_REQ_HOST_TEXT 1u
 
 typedef struct {
     uint32_t automaton;      /* index into the server's handles            */
-    uint32_t reserved;       /* 0                                          */
-    const uint8_t *d_text;   /* device text, n < 2^32 bytes                */
+    uint32_t flags;          /* 0, or AC_REQ_HOST_TEXT                     */
+    const uint8_t *d_text;   /* the text (device, or pinned host with
+                                AC_REQ_HOST_TEXT), n < 2^32 bytes           */
     uint64_t n;
     uint32_t *d_pos;         /* device, cap entries                        */
     uint32_t *d_ids;         /* device, cap entries                        */
@@ -516,6 +544,12 @@ ac_status ac_server_poll(ac_server s, ac_server_completion *out, uint32_t max, u
 /* Block until every request submitted so far has completed (their completion
  * records stay queued for ac_server_poll). */
 ac_status ac_server_drain(ac_server s);
+
+/* Cancel a request that has not been admitted into a wave yet: it completes
+ * at once with status AC_ERR_CANCELLED (its outputs are not written) and gives
+ * back nothing it did not hold.  AC_ERR_NOT_FOUND when the ticket is unknown or
+ * its request is already in a wave or done. */
+ac_status ac_server_cancel(ac_server s, uint64_t ticket);
 
 /* Drain, stop the worker and free the server (not the handles). */
 ac_status ac_server_destroy(ac_server s);

@@ -29,6 +29,8 @@ AC_ERR_OVERFLOW = 6
 AC_ERR_BUDGET = 7
 AC_ERR_TIMEOUT = 8
 AC_ERR_NOT_FOUND = 9
+AC_ERR_CANCELLED = 10
+AC_REQ_HOST_TEXT = 1
 
 AC_KERNEL_TILED = 0
 AC_KERNEL_SIMPLE = 1
@@ -123,6 +125,7 @@ _SIGS = {
     "ac_server_replay": (ctypes.c_int, [_P, _P, ctypes.c_uint32, _P, _P]),
     "ac_server_poll": (ctypes.c_int, [_P, _P, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]),
     "ac_server_drain": (ctypes.c_int, [_P]),
+    "ac_server_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "ac_server_destroy": (ctypes.c_int, [_P]),
     "ac_scratch_pool_usage": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                              ctypes.c_int32]),
@@ -545,11 +548,16 @@ class Automaton:
 # ---- serving ----------------------------------------------------------------------
 class ac_server_options(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_wave", ctypes.c_uint32),
-                ("waves_in_flight", ctypes.c_uint32), ("fifo", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("waves_in_flight", ctypes.c_uint32), ("fifo", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
 
+
+# C types of the server's optional scratch allocator (ac_server_options)
+DEV_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEV_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 # numpy mirrors of ac_server_request (56 bytes) and ac_server_completion (40 bytes)
-SERVER_REQUEST = np.dtype([("automaton", "<u4"), ("reserved", "<u4"), ("d_text", "<u8"), ("n", "<u8"),
+SERVER_REQUEST = np.dtype([("automaton", "<u4"), ("flags", "<u4"), ("d_text", "<u8"), ("n", "<u8"),
                            ("d_pos", "<u8"), ("d_ids", "<u8"), ("cap", "<u8"), ("d_count", "<u8")])
 SERVER_COMPLETION = np.dtype([("ticket", "<u8"), ("status", "<i4"), ("wave_size", "<u4"),
                               ("t_submit_us", "<f8"), ("t_launch_us", "<f8"), ("t_done_us", "<f8")])
@@ -560,10 +568,19 @@ class Server:
     """ac_server_*: continuous batching of compacted-match requests."""
 
     def __init__(self, handles, hbm_budget: int = 0, max_wave: int = 0, waves_in_flight: int = 0,
-                 fifo: bool = False):
+                 fifo: bool = False, dev_alloc=None, dev_free=None):
+        """dev_alloc(bytes) -> device address (0 = failure) and dev_free(address):
+        optional Python allocator of the waves' device scratch (called from
+        the server's worker thread)."""
         self.handles = [int(h) for h in handles]
         arr = _handles(self.handles)
         opt = ac_server_options(hbm_budget, max_wave, waves_in_flight, 1 if fifo else 0, 0)
+        self._hooks = None
+        if dev_alloc is not None:
+            self._hooks = (DEV_ALLOC(lambda n, ctx: dev_alloc(int(n)) or None),
+                           DEV_FREE(lambda p, ctx: dev_free(int(p or 0))))
+            opt.dev_alloc = ctypes.cast(self._hooks[0], ctypes.c_void_p)
+            opt.dev_free = ctypes.cast(self._hooks[1], ctypes.c_void_p)
         p = ctypes.c_void_p()
         _check(lib().ac_server_create(ctypes.cast(arr, ctypes.c_void_p), len(self.handles), ctypes.byref(opt),
                                       ctypes.byref(p)), "ac_server_create")
@@ -571,8 +588,10 @@ class Server:
 
     @staticmethod
     def request(automaton: int, text, n: int, pos, ids, cap: int, count) -> np.ndarray:
+        """A request record; a CPU (pinned) text tensor makes it a host-text request."""
         r = np.zeros(1, dtype=SERVER_REQUEST)
         r["automaton"] = automaton
+        r["flags"] = 0 if (n == 0 or text.is_cuda) else AC_REQ_HOST_TEXT
         r["d_text"] = int(text.data_ptr()) if n else 0
         r["n"] = n
         r["d_pos"] = int(pos.data_ptr()) if cap else 0
@@ -605,6 +624,10 @@ class Server:
 
     def drain(self):
         _check(lib().ac_server_drain(self.srv), "ac_server_drain")
+
+    def cancel(self, ticket: int):
+        """Cancel a request not yet in a wave (raises AcError(AC_ERR_NOT_FOUND) otherwise)."""
+        _check(lib().ac_server_cancel(self.srv, ticket), "ac_server_cancel")
 
     def close(self):
         if getattr(self, "srv", None):

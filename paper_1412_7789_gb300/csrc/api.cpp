@@ -890,6 +890,7 @@ const char *ac_status_string(ac_status s) {
         case AC_ERR_BUDGET: return "request exceeds the memory budget";
         case AC_ERR_TIMEOUT: return "a bounded device wait ran out";
         case AC_ERR_NOT_FOUND: return "unknown id";
+        case AC_ERR_CANCELLED: return "cancelled";
     }
     return "unknown status";
 }

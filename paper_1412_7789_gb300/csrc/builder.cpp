@@ -393,8 +393,10 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             //     reach depth kh stops before any keyword ends, so its result is
             //     -1.  The filter bit of the window of every depth-kh state is
             //     set (a clear bit: result -1); HK holds each depth-kh state
-            //     under its window, two {window, state} entries per bucket,
-            //     linear probing.
+            //     under its window, one 16-byte entry {window, state, child,
+            //     (child code << 24) | (result + 1)} per slot, linear probing:
+            //     child is the state's one child, 0 for a leaf, or kHkBranch
+            //     when it has several children (or a result of 2^24 - 1 or more).
             const uint32_t kh = std::min<uint32_t>(kHashWindow, h.minlen);
             uint32_t fb = 0;
             while (fb < kFilterBits && (2ull << fb) <= 8ull * opt.jump_bytes) ++fb;
@@ -404,27 +406,34 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                 for (uint32_t s = 1; s < b0 + cnt; ++s)
                     key[s] = key[parent[s]] | (incode[s] << (8u * (depth[s] - 1u)));
                 uint32_t hb = 6;
-                while ((1ull << hb) < 2ull * cnt) ++hb;
-                if (hb > 31) return AC_ERR_TOO_MANY_STATES;
+                while ((1ull << hb) < 4ull * cnt) ++hb;
+                if (hb > 30) return AC_ERR_TOO_MANY_STATES;
                 h.hashed = true;
                 h.kh = kh;
                 h.fbits = fb;
                 h.hk_bits = hb;
                 h.F.assign((1u << fb) / 32u, 0u);
                 h.HK.assign((1ull << hb) * 4ull, 0u);
-                const uint32_t bmask = (1u << hb) - 1u;
+                const uint32_t emask = (1u << hb) - 1u;
                 uint32_t probes = 1;
                 for (uint32_t s = b0; s < b0 + cnt; ++s) {
                     const uint32_t w = key[s];
                     const uint32_t f = (w * kFilterHashMul) >> (32u - fb);
                     h.F[f >> 5] |= 1u << (31u - (f & 31u));
+                    const uint32_t r1 = static_cast<uint32_t>(pathbest[s] + 1);
+                    uint32_t child = kHkBranch, info = r1;
+                    if (r1 < (1u << 24) && kids[s] <= 1) {
+                        child = kids[s] == 0 ? 0u : child1[s];
+                        info |= kids[s] == 0 ? 0u : (static_cast<uint32_t>(code1[s]) << 24);
+                    }
                     uint32_t b = (w * kStateHashMul) >> (32u - hb);
-                    for (uint32_t p = 1;; ++p, b = (b + 1u) & bmask) {
+                    for (uint32_t p = 1;; ++p, b = (b + 1u) & emask) {
                         uint32_t *e = &h.HK[4ull * b];
-                        const int slot = e[1] == 0u ? 0 : (e[3] == 0u ? 2 : -1);
-                        if (slot < 0) continue;
-                        e[slot] = w;
-                        e[slot + 1] = s;
+                        if (e[1] != 0u) continue;
+                        e[0] = w;
+                        e[1] = s;
+                        e[2] = child;
+                        e[3] = info;
                         probes = std::max(probes, p);
                         break;
                     }

@@ -220,37 +220,55 @@ __device__ __forceinline__ void classify_word8(const FilterParams &p, const uint
     unknown = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x) & 0x80808080u;
 }
 
-// 8-bit codes: the depth-kh state whose window is w (already masked to kh
-// codes), given the first bucket b0 of its probe sequence (loaded by the
-// caller, so that several lookups overlap); -1 when no state has that window
-// (the encoded result -1: the walk stops before depth kh, where no keyword
-// ends).  Entries of a bucket fill in order, so a bucket with an empty entry
-// ends the probe sequence.
-__device__ __forceinline__ uint32_t hk_bucket(const FilterParams &p, uint32_t w) {
+// 8-bit codes: the state hash.  Entry slot of window w (masked to kh codes),
+// and the entry of w given the entry e at that slot (loaded by the caller, so
+// that several lookups overlap): linear probing up to an empty entry (state
+// 0) or hk_probes entries; an entry with state 0 when no depth-kh state has
+// window w (a walk that does not reach depth kh finds no keyword).
+__device__ __forceinline__ uint32_t hk_slot(const FilterParams &p, uint32_t w) {
     return (w * kStateHashMul) >> p.hk_shift;
 }
 
-__device__ __forceinline__ int hk_resolve(const FilterParams &p, uint32_t w, uint4 e) {
-    uint32_t b = hk_bucket(p, w);
-    for (uint32_t i = 0;;) {
-        if (e.y != 0u && e.x == w) return static_cast<int>(e.y);
-        if (e.w != 0u && e.z == w) return static_cast<int>(e.w);
-        if (e.y == 0u || e.w == 0u || ++i >= p.hk_probes) return -1;
+__device__ __forceinline__ uint4 hk_find(const FilterParams &p, uint32_t w, uint4 e) {
+    uint32_t b = hk_slot(p, w);
+    for (uint32_t i = 1; e.y != 0u && e.x != w; ++i) {
+        if (i >= p.hk_probes) return make_uint4(0u, 0u, 0u, 0u);
         b = (b + 1u) & p.hk_mask;
         e = __ldg(p.HK + b);
     }
+    return e;
 }
 
-// The window-table entry of window x (codes from the first position on): the
-// depth-k state, or the encoded result where the walk stops inside the window.
+// A survivor at tile position i from its state-hash entry e and the code c of
+// the character after its window (c_ok: one is there, in a keyword byte):
+// true with its result r, or false with its walk to go on from state s at
+// tile position q.  A depth-kh state with one child: the walk stops there
+// (result: the state's) unless c is the child's code; a leaf: it stops; with
+// several children: its goto row decides.
+__device__ __forceinline__ bool hk_outcome(const FilterParams &p, const uint4 e, uint32_t i, uint32_t c, bool c_ok,
+                                           int &r, uint32_t &s, uint32_t &q) {
+    if (e.y == 0u) {
+        r = -1;
+        return true;
+    }
+    if (e.z == kHkBranch) {
+        s = e.y;
+        q = i + p.k;
+        return false;
+    }
+    r = static_cast<int>(e.w & 0xFFFFFFu) - 1;
+    if (e.z == 0u || !c_ok || c != (e.w >> 24)) return true;
+    s = e.z;
+    q = i + p.k + 1;
+    return false;
+}
+
+// The window-table entry of window x (codes from the first position on), 2-
+// and 4-bit codes: the depth-k state, or the encoded result where the walk
+// stops inside the window.
 template <int B>
 __device__ __forceinline__ int window_entry(const FilterParams &p, uint32_t x) {
-    if constexpr (B == 8) {
-        const uint32_t w = x & p.wmask;
-        return hk_resolve(p, w, __ldg(p.HK + hk_bucket(p, w)));
-    } else {
-        return __ldg(p.JK + (x & ((1u << (B * p.k)) - 1u)));
-    }
+    return __ldg(p.JK + (x & ((1u << (B * p.k)) - 1u)));
 }
 
 // One flag per non-zero byte of x (bit i for byte i).
@@ -324,6 +342,103 @@ __device__ __forceinline__ int chain_step(const FilterParams &p, const TileText 
     return 0;
 }
 
+// The walk from state s at tile position q, text bytes from global memory;
+// out of line, for the few walks of 8-bit codes that the state hash leaves
+// open (a copy per call site would crowd the instruction cache).
+template <typename GT>
+__device__ __noinline__ int walk_far(const FilterParams &p, const uint8_t *cls8, const TileText &tt, int64_t gpb,
+                                     uint32_t s, uint32_t q);
+
+// A found id (or, for slots, a match) of a survivor at tile position i:
+// dense output (with FALLBACK: the unit's dense fallback), count, or the
+// unit's slots (dense_all: into the dense fallback as well).  The tile's -1
+// are written already.  All lanes (slots: ballot).
+template <int MODE, bool FALLBACK>
+__device__ __forceinline__ void put_result(const FilterParams &p, const TileText &tt, int64_t gpb, uint32_t su,
+                                           bool mine, uint32_t i, int v, int lane, unsigned long long &cnt,
+                                           bool dense_all) {
+    if (MODE == OUT_SLOTS) {
+        // one atomic per warp and slot index, ranks by ballot
+        const bool hit = mine && v >= 0;
+        const unsigned m = __ballot_sync(kFull, hit);
+        if (hit && dense_all) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + i] = v;
+        if (m) {
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(p.sl.counts + su, static_cast<uint32_t>(__popc(m)));
+            base = __shfl_sync(kFull, base, 0) + __popc(m & ((1u << lane) - 1u));
+            if (hit && base < kSlotCap)
+                p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + base] =
+                    (static_cast<unsigned long long>(static_cast<uint32_t>(v)) << 32) | static_cast<uint32_t>(gpb + i);
+        }
+        return;
+    }
+    if (!mine || v < 0) return;
+    if (MODE == OUT_COUNT)
+        cnt += 1ull;
+    else if (FALLBACK)
+        p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + i] = v;
+    else
+        tt.out[gpb + i] = v;
+}
+
+// 8-bit codes: finish up to SLOTS * 32 queued survivors (as finish_survivors):
+// every window's state-hash entry is loaded first; the entry settles most
+// survivors (no state: -1; a leaf, or a one-child state whose child's code is
+// not next: the state's result); the others, and the windows past the text
+// end, walk on through walk_far.
+template <typename GT, int MODE, int SLOTS, bool FALLBACK>
+__device__ __forceinline__ bool finish_survivors8(const FilterParams &p, const TileText &tt, const WarpSmem &w,
+                                                  int64_t gpb, uint32_t avail, int lane, unsigned long long &cnt,
+                                                  uint32_t base, uint32_t su, bool dense_all) {
+    uint32_t ii[SLOTS], x[SLOTS], st[SLOTS], q[SLOTS];
+    uint4 e[SLOTS];
+    int v[SLOTS];
+    uint32_t act = 0, far = 0;
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        const uint32_t qi = lane + 32u * t;
+        ii[t] = 0;
+        x[t] = 0;
+        st[t] = 0;
+        q[t] = 0;
+        v[t] = -1;
+        e[t] = make_uint4(0u, 0u, 0u, 0u);
+        if (qi < avail) {
+            act |= 1u << t;
+            const uint32_t e16 = w.queue[base + qi];
+            ii[t] = e16 & 0x7FFFu;
+            if (e16 >> 15) {  // the window runs past the text end: walk from the root
+                far |= 1u << t;
+                q[t] = ii[t];
+            } else {
+                x[t] = code_window<8>(w.packed, ii[t]) & p.wmask;
+                e[t] = __ldg(p.HK + hk_slot(p, x[t]));
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        if (((act & ~far) >> t) & 1u) {
+            const uint4 f = hk_find(p, x[t], e[t]);
+            const uint32_t j = ii[t] + p.k;  // the character after the window (j < kCodeSpan)
+            const bool c_ok = !((w.inv[j >> 4] >> (j & 15u)) & 1u);
+            const uint32_t c = (w.packed[j >> 2] >> (8u * (j & 3u))) & 0xFFu;
+            if (!hk_outcome(p, f, ii[t], c, c_ok, v[t], st[t], q[t])) far |= 1u << t;
+        }
+    }
+#pragma unroll 1
+    for (int t = 0; t < SLOTS; ++t)
+        if ((far >> t) & 1u) v[t] = walk_far<GT>(p, w.cls8, tt, gpb, st[t], q[t]);
+    bool found = false;
+#pragma unroll
+    for (int t = 0; t < SLOTS; ++t) {
+        const bool mine = (act >> t) & 1u;
+        put_result<MODE, FALLBACK>(p, tt, gpb, su, mine, ii[t], v[t], lane, cnt, dense_all);
+        found |= mine && v[t] >= 0;
+    }
+    return found;
+}
+
 // Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)) of a
 // tile whose dense ids were set to -1 first: the ids found go to the dense
 // output (MODE == OUT_DENSE; with FALLBACK to the unit's dense fallback
@@ -335,6 +450,9 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
                                                  int64_t gpb, bool interior, bool clean, uint32_t avail,
                                                  uint32_t pbase, int lane, unsigned long long &cnt, uint32_t base,
                                                  uint32_t coded = 0, uint32_t su = 0, bool dense_all = false) {
+    if constexpr (B == 8) {
+        return finish_survivors8<GT, MODE, SLOTS, FALLBACK>(p, tt, w, gpb, avail, lane, cnt, base, su, dense_all);
+    } else {
     const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k, k2 = p.k2;
     const GT *G = static_cast<const GT *>(p.G);
@@ -342,8 +460,7 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
     int v[SLOTS];
     uint32_t act = 0, pend = 0, walking = 0;
     uint32_t x[SLOTS];
-    uint4 hb[B == 8 ? SLOTS : 1];  // 8-bit codes: the first bucket of each window's state-hash probe
-    // window table (state hash): depth-k state or result; all loads first
+    // window table: depth-k state or result; all loads first
 #pragma unroll
     for (int t = 0; t < SLOTS; ++t) {
         const uint32_t qi = lane + 32u * t;
@@ -360,20 +477,12 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
             q[t] = i;
             if (!(e16 >> 15)) {
                 x[t] = code_window<B>(w.packed, i);
-                if constexpr (B == 8)
-                    hb[t] = __ldg(p.HK + hk_bucket(p, x[t] & p.wmask));
-                else
-                    v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
+                v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
                 pend |= 1u << t;
             }
         }
     }
-    if constexpr (B == 8) {
-#pragma unroll
-        for (int t = 0; t < SLOTS; ++t)
-            if ((pend >> t) & 1u) v[t] = hk_resolve(p, x[t] & p.wmask, hb[t]);
-    }
-    // stride table for the walks still alive at depth k (none with 8-bit codes)
+    // stride table for the walks still alive at depth k
 #pragma unroll
     for (int t = 0; t < SLOTS; ++t) {
         if ((pend >> t) & 1u) {
@@ -385,19 +494,18 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
                 st[t] = static_cast<uint32_t>(e);
                 q[t] = ii[t] + k;
                 v[t] = INT_MIN;
-                bool ok2 = B != 8 && k2 > 0 && (interior || gpb + static_cast<int64_t>(ii[t] + k + k2) <= n);
+                bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(ii[t] + k + k2) <= n);
                 if (ok2 && !clean) {
                     const uint32_t j = ii[t] + k;
                     const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
                     ok2 = (wi & ((1u << k2) - 1u)) == 0;
                 }
-                if constexpr (B != 8) {
-                    if (ok2) {
-                        const uint32_t w2 = (x[t] >> (B * k)) & ((1u << (B * k2)) - 1u);
-                        v[t] = __ldg(p.J2 + ((static_cast<uint64_t>(st[t] - p.base_k) << (B * k2)) | w2));
-                    }
+                if (ok2) {
+                    const uint32_t w2 = (x[t] >> (B * k)) & ((1u << (B * k2)) - 1u);
+                    v[t] = __ldg(p.J2 + ((static_cast<uint64_t>(st[t] - p.base_k) << (B * k2)) | w2));
+                } else {
+                    pend &= ~(1u << t);
                 }
-                if (!ok2) pend &= ~(1u << t);
             }
         }
     }
@@ -498,6 +606,7 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
         }
     }
     return found;
+    }
 }
 
 // One warp, a tile whose matches overflowed its slots: the survivors walked
@@ -655,6 +764,12 @@ __device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t 
     return -1;
 }
 
+template <typename GT>
+__device__ __noinline__ int walk_far(const FilterParams &p, const uint8_t *cls8, const TileText &tt, int64_t gpb,
+                                     uint32_t s, uint32_t q) {
+    return walk_global<GT>(p, cls8, tt, gpb, s, q);
+}
+
 // Second stage: the window-table result has arrived; issue the stride load.
 template <int B>
 __device__ __forceinline__ void flight_advance(const FilterParams &p, Flight &f) {
@@ -675,8 +790,9 @@ __device__ __forceinline__ void flight_advance(const FilterParams &p, Flight &f)
     }
 }
 
-// Last stage: the stride-table result has arrived; finish the walk if needed.
-template <typename GT>
+// Last stage: the stride-table result has arrived; finish the walk if needed
+// (8-bit codes: out of line).
+template <int B, typename GT>
 __device__ __forceinline__ void flight_finish(const FilterParams &p, const Work &wk, const uint8_t *cls8, Flight &f) {
     if (f.pos == kNoPos) return;
     if (f.phase == kPhJ2) {
@@ -691,7 +807,10 @@ __device__ __forceinline__ void flight_finish(const FilterParams &p, const Work 
         f.phase = kPhWalk;
     }
     if (f.phase == kPhWalk) {
-        f.val = walk_global<GT>(p, cls8, tile_text(p, wk, f.tile, f.item), f.gpb, f.state, f.q);
+        if constexpr (B == 8)
+            f.val = walk_far<GT>(p, cls8, tile_text(p, wk, f.tile, f.item), f.gpb, f.state, f.q);
+        else
+            f.val = walk_global<GT>(p, cls8, tile_text(p, wk, f.tile, f.item), f.gpb, f.state, f.q);
         f.phase = kPhDone;
     }
 }
@@ -1006,9 +1125,9 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
         if (total > 32) {
             // 4a. many survivors: finish the tiles in flight, then this one
             flight_advance<B>(p, f1);
-            flight_finish<GT>(p, wk, w.cls8, f2);
+            flight_finish<B, GT>(p, wk, w.cls8, f2);
             flight_output<MODE>(p, wk, w, f2, lane, cnt);
-            flight_finish<GT>(p, wk, w.cls8, f1);
+            flight_finish<B, GT>(p, wk, w.cls8, f1);
             flight_output<MODE>(p, wk, w, f1, lane, cnt);
             f1 = empty_flight();
             f2 = empty_flight();
@@ -1138,34 +1257,50 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
                 f0.q = i;
             } else {
                 const uint32_t x = code_window<B>(w.packed, i);
-                f0.val = window_entry<B>(p, x);
-                f0.phase = kPhJK;
-                bool ok2 = false;
-                if constexpr (B != 8) {  // no stride table with 8-bit codes
+                if constexpr (B == 8) {
+                    // the state hash settles the survivor, or names where its walk goes on
+                    const uint32_t wx = x & p.wmask;
+                    const uint4 fe = hk_find(p, wx, __ldg(p.HK + hk_slot(p, wx)));
+                    const uint32_t j = i + k;
+                    const bool c_ok = !((w.inv[j >> 4] >> (j & 15u)) & 1u);
+                    const uint32_t c = (w.packed[j >> 2] >> (8u * (j & 3u))) & 0xFFu;
+                    int r = -1;
+                    uint32_t s2 = 0, q2 = 0;
+                    if (hk_outcome(p, fe, i, c, c_ok, r, s2, q2)) {
+                        f0.val = r;
+                        f0.phase = kPhDone;
+                    } else {
+                        f0.state = s2;
+                        f0.q = q2;
+                        f0.phase = kPhWalk;
+                    }
+                } else {
+                    f0.val = window_entry<B>(p, x);
+                    f0.phase = kPhJK;
                     f0.w2 = (x >> (B * k)) & ((1u << (B * k2)) - 1u);
-                    ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(i + k + k2) <= n);
+                    bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(i + k + k2) <= n);
                     if (ok2 && !clean) {
                         const uint32_t j = i + k;
                         const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
                         ok2 = (wi & ((1u << k2) - 1u)) == 0;
                     }
+                    f0.ok2 = ok2 ? 1u : 0u;
                 }
-                f0.ok2 = ok2 ? 1u : 0u;
             }
         }
         // 5. the tile one back: issue its stride-table loads
         flight_advance<B>(p, f1);
         // 6. the tile two back: finish and write it
-        flight_finish<GT>(p, wk, w.cls8, f2);
+        flight_finish<B, GT>(p, wk, w.cls8, f2);
         flight_output<MODE>(p, wk, w, f2, lane, cnt);
         f2 = f1;
         f1 = f0;
     }
     // drain
     flight_advance<B>(p, f1);
-    flight_finish<GT>(p, wk, w.cls8, f2);
+    flight_finish<B, GT>(p, wk, w.cls8, f2);
     flight_output<MODE>(p, wk, w, f2, lane, cnt);
-    flight_finish<GT>(p, wk, w.cls8, f1);
+    flight_finish<B, GT>(p, wk, w.cls8, f1);
     flight_output<MODE>(p, wk, w, f1, lane, cnt);
 
     // no tiles left: help with the CTA's heavy tiles until every warp is done

@@ -42,6 +42,8 @@ constexpr uint32_t kFilterBits = 20;
 constexpr uint32_t kFilterHashMul = 0x9E3779B1u;
 constexpr uint32_t kStateHashMul = 0x85EBCA77u;
 constexpr uint32_t kHashWindow = 4;  // codes per hashed window (at most)
+// State-hash entry field `child` of a depth-kh state with several children.
+constexpr uint32_t kHkBranch = 0xFFFFFFFFu;
 
 // Longest halo staged in shared memory; walks that run past it read global memory.
 constexpr uint32_t kHaloCap = 256;
@@ -110,8 +112,10 @@ struct HostTables {
     // alphabets' filter): the bit of the window of every depth-kh state is
     // set, so a clear bit means the walk stops before depth kh, where no
     // keyword ends (result -1).  HK: the depth-kh states by their window, in
-    // 2^hk_bits buckets of two {window, state} entries (state 0: empty),
-    // linear probing over at most hk_probes buckets.
+    // 2^hk_bits entries of four words {window, state (0: empty), child,
+    // (child code << 24) | (result + 1)}, linear probing over at most
+    // hk_probes entries; child: the state's one child, 0 for a leaf, or
+    // kHkBranch (several children: take the goto row).
     bool hashed = false;
     uint32_t kh = 0, fbits = 0, hk_bits = 0, hk_probes = 0;
     std::vector<uint32_t> HK;

@@ -43,7 +43,8 @@ struct Request {
 };
 
 // A wave slot: its stream, completion event, pinned staging for the plan
-// (grown on demand) and the requests of the wave it runs.
+// (grown on demand), the requests of the wave it runs, and the wave's device
+// scratch when it came from the caller's allocator (freed at completion).
 struct WaveSlot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -51,6 +52,7 @@ struct WaveSlot {
     size_t host_bytes = 0;
     bool busy = false;
     std::vector<Request> reqs;
+    void *user_scratch = nullptr;
 };
 
 constexpr uint32_t kMaxWaves = 8;
@@ -64,7 +66,11 @@ struct ac_server_impl {
     std::vector<const pfac::DevTables *> tabs;
     std::vector<pfac::Tuning> tune;
     int device = 0;
-    uint64_t budget = 0;
+    uint64_t budget = 0;         // for requests: the option's budget less the automata's tables
+    uint64_t table_bytes = 0;    // the resident automata (each handle once)
+    void *(*dev_alloc)(size_t, void *) = nullptr;
+    void (*dev_free)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
     uint32_t max_wave = 0;
     uint32_t nslots = 0;
     bool fifo = false;
@@ -93,19 +99,51 @@ namespace {
 
 uint32_t tile_of(const pfac::DevTables &t, const pfac::Tuning &tu) { return pfac::unit_positions(t, tu); }
 
-uint64_t units_of(const pfac::DevTables &t, const pfac::Tuning &tu, const uint8_t *text, uint64_t n) {
-    if (n == 0) return 0;
-    const uint64_t T = tile_of(t, tu);
-    const uint64_t head = reinterpret_cast<uintptr_t>(text) & 15u;
-    return (n + head + T - 1) / T;
+bool host_text(const ac_server_request &r) { return (r.flags & AC_REQ_HOST_TEXT) != 0; }
+
+// The text's offset from a 16-byte boundary on the device: a host text is
+// copied to a 16-byte aligned place.
+uint64_t text_head(const ac_server_request &r) {
+    return host_text(r) ? 0u : (reinterpret_cast<uintptr_t>(r.d_text) & 15u);
 }
 
-// Device bytes a request holds while admitted: its text, its output and the
-// scratch of its tiles (counts, prefix, slots, dense fallback).
+uint64_t units_of(const pfac::DevTables &t, const pfac::Tuning &tu, const ac_server_request &r) {
+    if (r.n == 0) return 0;
+    const uint64_t T = tile_of(t, tu);
+    return (r.n + text_head(r) + T - 1) / T;
+}
+
+// Device bytes a request holds while admitted: its text (a host text's device
+// copy), its output and the scratch of its tiles (counts, prefix, slots,
+// dense fallback).
 uint64_t request_bytes(const pfac::DevTables &t, const pfac::Tuning &tu, const ac_server_request &r) {
     const uint64_t per_unit = 4 + 8 + 8ull * pfac::kSlotCap + 4ull * pfac::kDenseStride;
-    return r.n + 8ull * r.cap + units_of(t, tu, r.d_text, r.n) * per_unit + 64;
+    return r.n + 8ull * r.cap + units_of(t, tu, r) * per_unit + 64;
 }
+
+// Device scratch of a wave: from the caller's allocator (freed when the wave
+// completes) or the library pool (freed in stream order after the wave).
+cudaError_t wave_alloc(ac_server_impl *s, WaveSlot &w, size_t bytes, void **out) {
+    *out = nullptr;
+    if (s->dev_alloc) {
+        void *p = s->dev_alloc(bytes, s->alloc_ctx);
+        if (!p) return cudaErrorMemoryAllocation;
+        w.user_scratch = p;
+        *out = p;
+        return cudaSuccess;
+    }
+    cudaMemPool_t pool = nullptr;
+    cudaError_t e = pfac::scratch_pool(s->device, &pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(out, bytes, pool, w.stream);
+}
+
+cudaError_t wave_release(ac_server_impl *s, WaveSlot &w, void *p) {
+    if (!p || s->dev_alloc) return cudaSuccess;  // caller's memory: freed at completion
+    return cudaFreeAsync(p, w.stream);
+}
+
+inline size_t round16(size_t v) { return (v + 15u) & ~static_cast<size_t>(15u); }
 
 cudaError_t ensure_host(WaveSlot &w, size_t bytes) {
     if (w.host_bytes >= bytes) return cudaSuccess;
@@ -123,31 +161,40 @@ cudaError_t ensure_host(WaveSlot &w, size_t bytes) {
 cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     const uint32_t nh = static_cast<uint32_t>(s->hs.size());
     const uint32_t R = static_cast<uint32_t>(w.reqs.size());
-    cudaMemPool_t pool = nullptr;
-    cudaError_t e = pfac::scratch_pool(s->device, &pool);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
 
     if (s->fifo) {  // the comparison point: the single-text compacted path
         const Request &q = w.reqs[0];
         if (q.r.n == 0) return cudaMemsetAsync(q.r.d_count, 0, sizeof(uint64_t), w.stream);
         const pfac::DevTables &t = *s->tabs[q.r.automaton];
-        const size_t bytes =
-            pfac::compact_scratch_bytes(t, pfac::compact_units(t, s->tune[q.r.automaton], q.r.d_text, q.r.n), true);
+        const pfac::Tuning &tu = s->tune[q.r.automaton];
+        // a host text: its copy at the front of the scratch (16-byte aligned)
+        const size_t tb = host_text(q.r) ? round16(q.r.n) : 0;
+        const uint32_t units = static_cast<uint32_t>(units_of(t, tu, q.r));
+        const size_t bytes = tb + pfac::compact_scratch_bytes(t, units, true);
         void *scratch = nullptr;
-        e = cudaMallocFromPoolAsync(&scratch, bytes, pool, w.stream);
+        e = wave_alloc(s, w, bytes, &scratch);
         if (e != cudaSuccess) return e;
+        const uint8_t *text = q.r.d_text;
+        if (tb) {
+            e = cudaMemcpyAsync(scratch, q.r.d_text, q.r.n, cudaMemcpyHostToDevice, w.stream);
+            text = static_cast<const uint8_t *>(scratch);
+        }
         const pfac::CompactOut out{q.r.d_pos, q.r.d_ids, q.r.cap, reinterpret_cast<unsigned long long *>(q.r.d_count)};
-        e = pfac::enqueue_compact(t, s->tune[q.r.automaton], q.r.d_text, q.r.n, out, scratch, bytes, true,
-                                  w.stream);
-        const cudaError_t e2 = cudaFreeAsync(scratch, w.stream);
+        if (e == cudaSuccess)
+            e = pfac::enqueue_compact(t, tu, text, q.r.n, out, static_cast<uint8_t *>(scratch) + tb, bytes - tb, true,
+                                      w.stream);
+        const cudaError_t e2 = wave_release(s, w, scratch);
         return e != cudaSuccess ? e : e2;
     }
 
     // plan on the host: per automaton its texts in arrival order, their first
-    // tile, and the automaton's first tile in the wave's numbering
+    // tile, and the automaton's first tile in the wave's numbering; host texts
+    // get a 16-byte aligned place in the wave's scratch for their copies
     std::vector<uint32_t> order;
     order.reserve(R);
-    const uint8_t *base = nullptr;
+    std::vector<size_t> stage_off(R, 0);
+    size_t staged = 0;
     for (uint32_t i = 0; i < R; ++i) {
         const ac_server_request &r = w.reqs[i].r;
         if (r.n == 0) {
@@ -156,7 +203,10 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
             continue;
         }
         order.push_back(i);
-        if (!base || r.d_text < base) base = r.d_text;
+        if (host_text(r)) {
+            stage_off[i] = staged;
+            staged += round16(r.n);
+        }
     }
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t a, uint32_t b) { return w.reqs[a].r.automaton < w.reqs[b].r.automaton; });
@@ -177,13 +227,11 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         while (j < L && w.reqs[order[j]].r.automaton == a) {
             const ac_server_request &r = w.reqs[order[j]].r;
             pfac::BatchItemDev &d = list[j];
-            d.text_off = static_cast<uint64_t>(reinterpret_cast<uintptr_t>(r.d_text) -
-                                               reinterpret_cast<uintptr_t>(base));
             d.len = r.n;
             d.out_off = 0;
             d.first_unit = static_cast<uint32_t>(units);
             d.item = order[j];
-            units += units_of(t, s->tune[a], r.d_text, r.n);
+            units += units_of(t, s->tune[a], r);
             ++j;
         }
         heads[a].count = j - heads[a].offset;
@@ -196,26 +244,40 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         outs[i] = pfac::CompactOut{r.d_pos, r.d_ids, r.cap, reinterpret_cast<unsigned long long *>(r.d_count)};
     }
 
-    // staging: heads | list | outs, copied in one piece
+    // device: plan (heads | list | outs) | tile counters | counts | prefix |
+    // slots | partial sums | dense fallback | host-text copies
     const size_t hb = sizeof(pfac::BatchHead) * nh, lb = sizeof(pfac::BatchItemDev) * L,
                  ob = sizeof(pfac::CompactOut) * R;
     const size_t plan_bytes = round256(hb) + round256(lb) + round256(ob);
-    e = ensure_host(w, plan_bytes);
+    const size_t cb = round256(16ull * nh), nb = round256(4 * U), pb = 8 * U, sb = 8ull * pfac::kSlotCap * U;
+    const size_t db = round256(plan_bytes + cb + nb + pb + sb + 8ull * pfac::kScanCtas);  // dense fallback: aligned
+    const size_t stb = round256(db + 4ull * pfac::kDenseStride * U);
+    void *dev = nullptr;
+    e = wave_alloc(s, w, stb + staged, &dev);
     if (e != cudaSuccess) return e;
+    uint8_t *dp = static_cast<uint8_t *>(dev);
+
+    // the texts as the kernels see them: offsets from the lowest text address
+    std::vector<const uint8_t *> ptr(L);
+    const uint8_t *base = nullptr;
+    for (uint32_t k = 0; k < L; ++k) {
+        const ac_server_request &r = w.reqs[order[k]].r;
+        ptr[k] = host_text(r) ? dp + stb + stage_off[order[k]] : r.d_text;
+        if (!base || ptr[k] < base) base = ptr[k];
+    }
+    for (uint32_t k = 0; k < L; ++k)
+        list[k].text_off = static_cast<uint64_t>(reinterpret_cast<uintptr_t>(ptr[k]) - reinterpret_cast<uintptr_t>(base));
+
+    e = ensure_host(w, plan_bytes);
+    if (e != cudaSuccess) {
+        wave_release(s, w, dev);
+        return e;
+    }
     uint8_t *hp = static_cast<uint8_t *>(w.host);
     std::memcpy(hp, heads.data(), hb);
     std::memcpy(hp + round256(hb), list.data(), lb);
     std::memcpy(hp + round256(hb) + round256(lb), outs.data(), ob);
 
-    // device: plan | tile counters | counts | prefix | slots | partial sums |
-    // dense fallback
-    const size_t cb = round256(16ull * nh), nb = round256(4 * U), pb = 8 * U, sb = 8ull * pfac::kSlotCap * U;
-    const size_t db = round256(plan_bytes + cb + nb + pb + sb + 8ull * pfac::kScanCtas);  // dense fallback: aligned
-    const size_t dev_bytes = db + 4ull * pfac::kDenseStride * U;
-    void *dev = nullptr;
-    e = cudaMallocFromPoolAsync(&dev, dev_bytes, pool, w.stream);
-    if (e != cudaSuccess) return e;
-    uint8_t *dp = static_cast<uint8_t *>(dev);
     const pfac::BatchHead *d_heads = reinterpret_cast<const pfac::BatchHead *>(dp);
     const pfac::BatchItemDev *d_list = reinterpret_cast<const pfac::BatchItemDev *>(dp + round256(hb));
     const pfac::CompactOut *d_outs = reinterpret_cast<const pfac::CompactOut *>(dp + round256(hb) + round256(lb));
@@ -227,6 +289,11 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     int32_t *dense = reinterpret_cast<int32_t *>(dp + db);
 
     e = cudaMemcpyAsync(dp, hp, plan_bytes, cudaMemcpyHostToDevice, w.stream);
+    for (uint32_t k = 0; k < L && e == cudaSuccess; ++k) {  // host texts: one copy each
+        const ac_server_request &r = w.reqs[order[k]].r;
+        if (host_text(r)) e = cudaMemcpyAsync(const_cast<uint8_t *>(ptr[k]), r.d_text, r.n, cudaMemcpyHostToDevice,
+                                              w.stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, cb + 4 * U, w.stream);
     for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
         if (heads[a].units == 0) continue;
@@ -241,8 +308,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         m.slots.dense = dense;
         m.scratch = counters + 16u * a;
         m.scratch_bytes = 16;
-        const pfac::DevTables &t = *s->tabs[a];
-        e = pfac::launch_match(t, m, pfac::OUT_SLOTS, s->tune[a], w.stream);
+        e = pfac::launch_match(*s->tabs[a], m, pfac::OUT_SLOTS, s->tune[a], w.stream);
     }
     if (e == cudaSuccess)
         e = pfac::launch_compact_scan(counts, static_cast<uint32_t>(U), nullptr, prefix, partials, w.stream);
@@ -261,7 +327,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         g.dense = dense;
         e = pfac::launch_compact_gather(*s->tabs[a], g, w.stream);
     }
-    const cudaError_t e2 = cudaFreeAsync(dev, w.stream);
+    const cudaError_t e2 = wave_release(s, w, dev);
     return e != cudaSuccess ? e : e2;
 }
 
@@ -273,6 +339,10 @@ ac_status to_status(cudaError_t e) {
 }
 
 void complete_wave(ac_server_impl *s, WaveSlot &w, ac_status st, std::vector<ac_server_completion> &out) {
+    if (w.user_scratch) {  // the wave's work is done: its scratch goes back to the caller's allocator
+        s->dev_free(w.user_scratch, s->alloc_ctx);
+        w.user_scratch = nullptr;
+    }
     const double t = s->now_us();
     for (const Request &q : w.reqs) {
         ac_server_completion c;
@@ -339,6 +409,7 @@ void worker_main(ac_server_impl *s) {
             busy = true;
             if (e != cudaSuccess) {
                 cudaGetLastError();
+                cudaStreamSynchronize(w->stream);  // what was enqueued ends before its scratch is freed
                 done.clear();
                 complete_wave(s, *w, to_status(e), done);
                 lk.lock();
@@ -397,6 +468,13 @@ ac_status ac_server_create(const ac_handle *hs, uint32_t nh, const ac_server_opt
     ac_server s = new (std::nothrow) ac_server_impl();
     if (!s) return AC_ERR_OOM;
     s->device = cur;
+    if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr) || o.reserved != 0) {
+        delete s;
+        return AC_ERR_INVALID_ARG;
+    }
+    s->dev_alloc = o.dev_alloc;
+    s->dev_free = o.dev_free;
+    s->alloc_ctx = o.alloc_ctx;
     for (uint32_t a = 0; a < nh; ++a) {
         int dev = -1;
         bool host_only = true;
@@ -405,11 +483,23 @@ ac_status ac_server_create(const ac_handle *hs, uint32_t nh, const ac_server_opt
             delete s;
             return AC_ERR_INVALID_ARG;
         }
+        bool seen = false;  // a handle named twice is resident once
+        for (uint32_t b = 0; b < a; ++b) seen = seen || hs[b] == hs[a];
+        if (!seen) {
+            ac_info_t info;
+            ac_info(hs[a], &info);
+            s->table_bytes += info.table_bytes;
+        }
         s->hs.push_back(hs[a]);
         s->tabs.push_back(t);
         s->tune.push_back(*pfac::handle_tuning(hs[a]));
     }
-    s->budget = o.hbm_budget ? o.hbm_budget : (40ull << 30);
+    const uint64_t budget = o.hbm_budget ? o.hbm_budget : (40ull << 30);
+    if (s->table_bytes >= budget) {
+        delete s;
+        return AC_ERR_BUDGET;
+    }
+    s->budget = budget - s->table_bytes;
     s->max_wave = o.max_wave ? o.max_wave : 4096u;
     s->fifo = o.fifo != 0;
     uint32_t nw = o.waves_in_flight ? o.waves_in_flight : 2u;
@@ -434,7 +524,8 @@ ac_status ac_server_create(const ac_handle *hs, uint32_t nh, const ac_server_opt
 ac_status ac_server_submit(ac_server s, const ac_server_request *req, uint64_t *ticket) {
     if (!s || !req) return AC_ERR_INVALID_ARG;
     const ac_server_request &r = *req;
-    if (r.automaton >= s->hs.size() || !r.d_count || r.n > 0xFFFFFFFFull) return AC_ERR_INVALID_ARG;
+    if (r.automaton >= s->hs.size() || !r.d_count || r.n > 0xFFFFFFFFull || (r.flags & ~AC_REQ_HOST_TEXT))
+        return AC_ERR_INVALID_ARG;
     if (r.n > 0 && !r.d_text) return AC_ERR_INVALID_ARG;
     if (r.cap > 0 && (!r.d_pos || !r.d_ids)) return AC_ERR_INVALID_ARG;
     Request q;
@@ -487,6 +578,26 @@ ac_status ac_server_drain(ac_server s) {
     std::unique_lock<std::mutex> lk(s->mu);
     s->cv_done.wait(lk, [&] { return s->finished >= s->submitted; });
     return AC_OK;
+}
+
+ac_status ac_server_cancel(ac_server s, uint64_t ticket) {
+    if (!s) return AC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+        if (it->ticket != ticket) continue;
+        ac_server_completion c;
+        c.ticket = ticket;
+        c.status = AC_ERR_CANCELLED;
+        c.wave_size = 0;
+        c.t_submit_us = it->t_submit;
+        c.t_launch_us = c.t_done_us = s->now_us();
+        s->pending.erase(it);
+        s->completed.push_back(c);
+        ++s->finished;
+        s->cv_done.notify_all();
+        return AC_OK;
+    }
+    return AC_ERR_NOT_FOUND;
 }
 
 }  // extern "C"

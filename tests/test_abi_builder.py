@@ -500,28 +500,28 @@ def test_root_jump_table(lib, kw):
 
 
 def _hk_find(HK, hk_bits, probes, w):
-    """Lookup in the state hash as ac.h documents it: from bucket
-    (w * 0x85EBCA77 mod 2^32) >> (32 - hk_bits), at most `probes` buckets,
-    stopping at a bucket with an empty entry; 0 = no state."""
+    """Lookup in the state hash as ac.h documents it: from entry
+    (w * 0x85EBCA77 mod 2^32) >> (32 - hk_bits), at most `probes` entries,
+    stopping at an empty one; returns the entry's index, or -1."""
     b = ((w * 0x85EBCA77) & 0xFFFFFFFF) >> (32 - hk_bits)
     for _ in range(probes):
         e = HK[b]
-        for j in (0, 2):
-            if e[j + 1] != 0 and e[j] == w:
-                return int(e[j + 1])
-        if e[1] == 0 or e[3] == 0:
-            return 0
+        if e[1] == 0:
+            return -1
+        if e[0] == w:
+            return b
         b = (b + 1) % HK.shape[0]
-    return 0
+    return -1
 
 
 @pytest.mark.parametrize("case", ["zipf", "zipf_256cols", "short_keywords", "long_only"])
 def test_hashed_filter_and_state_hash(lib, case):
     """8-bit codes: for every state at depth kh (= min(4, shortest keyword)),
     the walk of its kh codes through the goto table reaches it, its window's
-    filter bit is set and the state hash finds it; windows whose walk does not
-    reach depth kh (random ones, and every depth-kh window with one code
-    changed) are not found."""
+    filter bit is set and the state hash finds it, with the state's child
+    (none, the only one with its code, or several) and result as its goto row
+    has them; windows whose walk does not reach depth kh (random ones, and
+    every depth-kh window with one code changed) are not found."""
     g = np.random.default_rng(3)
     kw = {}
     if case.startswith("zipf"):
@@ -572,14 +572,29 @@ def test_hashed_filter_and_state_hash(lib, case):
     assert np.array_equal(walk(wins), states)
     f = ((wins * 0x9E3779B1) & 0xFFFFFFFF) >> (32 - fbits)
     assert np.all((F[f >> 5] >> (31 - (f & 31))) & 1)
-    assert all(_hk_find(HK, hk_bits, probes, int(w)) == int(s) for w, s in zip(wins, states))
+    live = G[:, :C] > 0
+    for w, s in zip(wins, states):
+        b = _hk_find(HK, hk_bits, probes, int(w))
+        assert b >= 0 and HK[b, 1] == s
+        kids = np.nonzero(live[s])[0]
+        res = -int(G[s, C]) - 2  # the end column holds the result of stopping at s
+        child, info = int(HK[b, 2]), int(HK[b, 3])
+        if kids.size >= 2:
+            assert child == 0xFFFFFFFF
+        else:
+            assert (info & 0xFFFFFF) == res + 1
+            if kids.size == 0:
+                assert child == 0
+            else:
+                assert child == int(G[s, kids[0]]) and (info >> 24) == int(kids[0])
     # windows whose walk stops before depth kh are not in the hash
     rnd = g.integers(0, 1 << (8 * kh), size=4000, dtype=np.int64)
     mutated = wins ^ (np.int64(1) << np.int64(8 * g.integers(0, kh, size=wins.size)))
     for cand in (rnd, mutated):
         reach = walk(cand)
         for w, s in zip(cand[:3000], reach[:3000]):
-            assert _hk_find(HK, hk_bits, probes, int(w)) == int(s)
+            b = _hk_find(HK, hk_bits, probes, int(w))
+            assert (b < 0 and s == 0) or (b >= 0 and HK[b, 1] == s)
     # the filter keeps few windows: at most one bit per depth-kh state
     assert int(np.unpackbits(F.view(np.uint8)).sum()) <= states.size
 

@@ -78,10 +78,13 @@ def _buffers(reqs, cap_div=1):
     return out
 
 
-def _request_array(d_pools, reqs, bufs):
+def _request_array(d_pools, reqs, bufs, h_pools=None):
+    """Request records; with h_pools (pinned host copies of the pools) every
+    third request names its text in host memory (the secondary path)."""
     arr = np.zeros(len(reqs), dtype=api.SERVER_REQUEST)
     for i, ((a, off, n), (pos, ids, cnt, cap)) in enumerate(zip(reqs, bufs)):
-        arr[i] = api.Server.request(a, d_pools[a][off:off + n], n, pos, ids, cap, cnt)[0]
+        src = h_pools[a] if (h_pools is not None and i % 3 == 1) else d_pools[a]
+        arr[i] = api.Server.request(a, src[off:off + n], n, pos, ids, cap, cnt)[0]
     return arr
 
 
@@ -97,17 +100,35 @@ def _check_results(reqs, bufs, want):
         assert np.array_equal(ids[:m].cpu().numpy().astype(np.uint32), wi[:m]), (i, a, n)
 
 
+@pytest.fixture(scope="module")
+def h_pools(setup):
+    import torch
+
+    sets, pools, d_pools, autos, reqs, want = setup
+    return [torch.from_numpy(p.copy()).pin_memory() for p in pools]
+
+
+def _tables(autos):
+    return sum(a.info()["table_bytes"] for a in autos)
+
+
 @pytest.mark.parametrize("opts", [
     dict(),                                   # defaults: everything in as few waves as possible
     dict(max_wave=7, waves_in_flight=3),      # many small waves overlapping
-    dict(hbm_budget=24 << 20, max_wave=64),   # admission held back by the budget
+    dict(hbm_budget=24 << 20, max_wave=64),   # admission held back by the budget (beyond the automata)
     dict(fifo=True),                          # one request per launch, in order
+    dict(host=True),                          # every third text from pinned host memory
+    dict(host=True, fifo=True),
 ])
-def test_alone_equals_mixed(setup, opts):
+def test_alone_equals_mixed(setup, h_pools, opts):
     sets, pools, d_pools, autos, reqs, want = setup
     bufs = _buffers(reqs)
+    opts = dict(opts)
+    host = opts.pop("host", False)
+    if "hbm_budget" in opts:
+        opts["hbm_budget"] += _tables(autos)
     with api.Server([a.handle for a in autos], **opts) as srv:
-        tickets = [srv.submit(r) for r in _request_array(d_pools, reqs, bufs)]
+        tickets = [srv.submit(r) for r in _request_array(d_pools, reqs, bufs, h_pools if host else None)]
         srv.drain()
         done = srv.poll(len(reqs) + 10)
     assert len(done) == len(reqs)
@@ -140,7 +161,11 @@ def test_submit_rejects(setup):
     sets, pools, d_pools, autos, reqs, want = setup
     pos = torch.zeros(4, dtype=torch.int32, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
-    with api.Server([a.handle for a in autos], hbm_budget=1 << 20) as srv:
+    # the automata alone exceed the budget: no server
+    with pytest.raises(api.AcError) as e:
+        api.Server([a.handle for a in autos], hbm_budget=_tables(autos))
+    assert e.value.status == api.AC_ERR_BUDGET
+    with api.Server([a.handle for a in autos], hbm_budget=_tables(autos) + (1 << 20)) as srv:
         big = api.Server.request(0, d_pools[0], 4 << 20, pos, pos, 4, cnt)
         with pytest.raises(api.AcError) as e:
             srv.submit(big)
@@ -149,3 +174,94 @@ def test_submit_rejects(setup):
         with pytest.raises(api.AcError) as e:
             srv.submit(bad)
         assert e.value.status == api.AC_ERR_INVALID_ARG
+
+
+def test_scratch_allocation_failure_is_reported(setup):
+    """Host-side fault injection: the waves' scratch comes from a caller
+    allocator that fails its first calls; those waves' requests complete with
+    AC_ERR_OOM, later waves succeed with exact results, and every block handed
+    out is given back."""
+    import threading
+
+    import torch
+
+    sets, pools, d_pools, autos, reqs, want = setup
+    sub = [r for r in reqs if r[2] > 0][:40]
+    sub_want = [want[reqs.index(r)] for r in sub]
+    lock = threading.Lock()
+    state = {"calls": 0, "live": {}}
+
+    def alloc(nbytes):
+        with lock:
+            state["calls"] += 1
+            if state["calls"] <= 3:
+                return 0  # injected failure
+            t = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            state["live"][t.data_ptr()] = t
+            return t.data_ptr()
+
+    def free(ptr):
+        with lock:
+            state["live"].pop(ptr)
+
+    bufs = _buffers(sub)
+    arr = _request_array(d_pools, sub, bufs)
+    with api.Server([a.handle for a in autos], max_wave=4, waves_in_flight=1, dev_alloc=alloc,
+                    dev_free=free) as srv:
+        tickets = [srv.submit(r) for r in arr]
+        srv.drain()
+        done = srv.poll(len(sub) + 10)
+    assert len(done) == len(sub)
+    by_ticket = {int(d["ticket"]): int(d["status"]) for d in done}
+    failed = [i for i, t in enumerate(tickets) if by_ticket[t] != api.AC_OK]
+    assert failed and all(by_ticket[tickets[i]] == api.AC_ERR_OOM for i in failed)
+    assert len(failed) < len(sub)
+    assert not state["live"]
+    ok = [i for i in range(len(sub)) if i not in failed]
+    _check_results([sub[i] for i in ok], [bufs[i] for i in ok], [sub_want[i] for i in ok])
+
+    # the same server settings again with a working allocator: all exact
+    state["calls"] = 100
+    bufs = _buffers(sub)
+    with api.Server([a.handle for a in autos], max_wave=4, dev_alloc=alloc, dev_free=free) as srv:
+        for r in _request_array(d_pools, sub, bufs):
+            srv.submit(r)
+        srv.drain()
+        done = srv.poll(len(sub) + 10)
+    assert np.all(done["status"] == api.AC_OK) and not state["live"]
+    _check_results(sub, bufs, sub_want)
+
+
+def test_cancel_pending_request(setup):
+    """A request that waits for budget can be cancelled: it completes with
+    AC_ERR_CANCELLED and leaves its outputs alone; the others complete exactly;
+    a request already done cannot be cancelled."""
+    sets, pools, d_pools, autos, reqs, want = setup
+    sub = sorted([r for r in reqs if r[2] > (256 << 10)], key=lambda r: -r[2])[:6]
+    sub_want = [want[reqs.index(r)] for r in sub]
+    bufs = _buffers(sub)
+    arr = _request_array(d_pools, sub, bufs)
+    import torch
+
+    # room for about one request at a time (one holds its text, 8 bytes of
+    # output room and about 4.4 bytes of scratch per text byte): the later
+    # ones wait in the queue
+    per = max(int(r["n"]) for r in arr) * 16
+    with api.Server([a.handle for a in autos], hbm_budget=_tables(autos) + per, waves_in_flight=1) as srv:
+        tickets = [srv.submit(r) for r in arr]
+        srv.cancel(tickets[-1])
+        with pytest.raises(api.AcError) as e:
+            srv.cancel(tickets[-1])
+        assert e.value.status == api.AC_ERR_NOT_FOUND
+        srv.drain()
+        done = srv.poll(len(sub) + 10)
+        with pytest.raises(api.AcError) as e:
+            srv.cancel(tickets[0])
+        assert e.value.status == api.AC_ERR_NOT_FOUND
+    st = {int(d["ticket"]): int(d["status"]) for d in done}
+    assert st[tickets[-1]] == api.AC_ERR_CANCELLED
+    assert all(st[t] == api.AC_OK for t in tickets[:-1])
+    _check_results(sub[:-1], bufs[:-1], sub_want[:-1])
+    pos, ids, cnt, cap = bufs[-1]
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == 12345 and int(pos[0].item()) == -7
