@@ -361,10 +361,17 @@ ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text, uint64_t n
  * ---- Batches: many texts, several automata --------------------------------
  * The paper matches one text per run (section III); a batch is this library's
  * way to keep the GPU busy with many short texts: every text is cut into the
- * same work units (tiles) a single text is, and the units of all texts that
- * use one automaton are matched by one persistent launch, so short texts do
- * not each pay a launch and a tail.  Results are exactly those of ac_match on
- * each text alone: walks stop at the end of their own text.
+ * same work units (tiles) a single text is, and the units of all texts and all
+ * automata are matched by one persistent launch (each CTA takes the automata
+ * in turn, loading each one's root filter into shared memory, and its warps
+ * take that automaton's units), so short texts do not each pay a launch and a
+ * tail, and no launch boundary drains the GPU between automata.  That launch
+ * serves up to 32 automata with root filters (every automaton has one unless
+ * built with jump_bytes below 4); it runs the filter kernel for each, whatever
+ * kernel ac_set_kernel or ac_autotune chose for its single texts.  Otherwise
+ * the batch takes one persistent launch per automaton.  Results are exactly
+ * those of ac_match on each text alone: walks stop at the end of their own
+ * text.
  *
  * One text of a batch: bytes d_texts[text_off, text_off + len), matched
  * against hs[automaton], dense ids written to d_out[out_off, out_off + len).
@@ -384,8 +391,8 @@ typedef struct {
  * calling device).  d_items: nitems ac_batch_item in DEVICE memory (read by
  * the kernels; not read on the host), d_texts / d_out the bases the offsets
  * refer to.  Enqueues on `stream`: one planning kernel (groups the texts by
- * automaton and numbers their work units), then one persistent launch per
- * automaton.  An item whose automaton is >= nh is skipped and latches an
+ * automaton and numbers their work units), then the matching launch (see
+ * above).  An item whose automaton is >= nh is skipped and latches an
  * error that ac_device_status() reports as AC_ERR_INVALID_ARG.  Scratch
  * (nh * 16 + nitems * 32 bytes + 16 per automaton) comes from the library's
  * stream-ordered pool.  Asynchronous; nitems = 0 is a no-op.
@@ -396,8 +403,7 @@ ac_status ac_match_batch(const ac_handle *hs, uint32_t nh, const uint8_t *d_text
 /*
  * A reusable batch plan: the handles, scratch for up to max_items texts, and
  * (after ac_batch_capture) an instantiated CUDA graph of the whole batch (the
- * planning kernel and the automata's launches in sequence, each filling the
- * GPU).
+ * planning kernel and the matching launch).
  *   ac_batch_create  copies the handle array; allocates the plan's scratch
  *                    with cudaMalloc.  max_items >= 1.
  *   ac_batch_run     enqueues the batch on `stream` (like ac_match_batch,
@@ -462,8 +468,10 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
  *     AC_ERR_BUDGET at submission, and a server whose automata alone exceed
  *     the budget at creation;
  *   - every admitted request that is not yet on the GPU joins the next wave:
- *     one persistent launch per automaton over the tiles of all its requests,
- *     then one scan and one gather, so requests of any size share the launches;
+ *     one persistent matching launch over the tiles of all its requests and
+ *     automata (as a batch: up to 32 automata with root filters; else one
+ *     launch per automaton), then one scan and a gather per automaton, so
+ *     requests of any size share the launches;
  *   - up to waves_in_flight waves run at once on their own streams: requests
  *     that arrive while a wave is on the GPU go into the next one and overlap
  *     it as SMs free up; a wave's requests complete when its last kernel ends.

@@ -222,20 +222,38 @@ ac_status check_handles(const ac_handle *hs, uint32_t nh) {
 }
 
 // Enqueue a batch on `st`: clear the tile counters, plan on the device, then
-// one persistent dense launch per automaton, one after another (each fills
-// the GPU; launches of different automata running side by side measured
-// slower, as their CTAs compete for the same SMs).
+// match: when the filter kernel serves every automaton, one persistent launch
+// for all of them (each CTA takes the automata in turn, so they overlap and no
+// launch boundary drains the GPU between them); otherwise one persistent
+// launch per automaton, one after another.
 cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const uint8_t *texts,
                           const ac_batch_item *items, uint32_t nitems, int32_t *out, cudaStream_t st) {
     uint8_t *base = static_cast<uint8_t *>(scratch);
     pfac::BatchHead *heads = reinterpret_cast<pfac::BatchHead *>(base);
     uint8_t *counters = base + static_cast<size_t>(nh) * 16u;
     pfac::BatchItemDev *lists = reinterpret_cast<pfac::BatchItemDev *>(base + static_cast<size_t>(nh) * 32u);
+    std::vector<const pfac::DevTables *> ts(nh);
+    for (uint32_t a = 0; a < nh; ++a) ts[a] = &hs[a]->dev;
+    const bool multi = pfac::filter_multi_serves(ts.data(), nh);
     std::vector<uint32_t> tile_len(nh);
     for (uint32_t a = 0; a < nh; ++a)
-        tile_len[a] = pfac::unit_positions(hs[a]->dev, hs[a]->tuning);
+        tile_len[a] = multi ? pfac::filter_tile_positions() : pfac::unit_positions(hs[a]->dev, hs[a]->tuning);
     cudaError_t e = cudaMemsetAsync(counters, 0, static_cast<size_t>(nh) * 16u, st);
     if (e == cudaSuccess) e = pfac::launch_batch_plan(items, nitems, nh, texts, tile_len.data(), heads, lists, st);
+    if (multi) {
+        std::vector<pfac::MatchRequest> rs(nh);
+        for (uint32_t a = 0; a < nh; ++a) {
+            rs[a].text = texts;
+            rs[a].out = out;
+            rs[a].batch = heads + a;
+            rs[a].lists = lists;
+            rs[a].scratch = counters + 16u * a;
+            rs[a].scratch_bytes = 16;
+        }
+        if (e == cudaSuccess)
+            e = pfac::launch_filter_multi(ts.data(), rs.data(), nh, pfac::OUT_DENSE, hs[0]->tuning.wait_ns, st);
+        return e;
+    }
     for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
         cudaStream_t sa = st;
         pfac::MatchRequest r;

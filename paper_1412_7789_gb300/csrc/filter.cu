@@ -1,6 +1,9 @@
-// Failureless Aho-Corasick matching with a root filter, sm_103a: the launcher
+// Failureless Aho-Corasick matching with a root filter, sm_103a: the launchers
 // (2- and 4-bit codes with the exact filter, 8-bit codes with the hashed
-// filter and state hash).  The kernel is in filter_kernel.cuh.
+// filter and state hash; one text, one automaton's batch texts, or a whole
+// batch of automata in one launch).  The kernel is in filter_kernel.cuh.
+#include <mutex>
+
 #include "filter_kernel.cuh"
 
 namespace pfac {
@@ -9,68 +12,44 @@ using namespace filt;
 
 uint32_t filter_tile_positions() { return kTile; }
 
-cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
-                          cudaStream_t stream) {
-    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
-        tu.stages > kMaxStages)
-        return cudaErrorInvalidValue;
-    const bool hashed = t.B == 8 && t.hashed && t.HK != nullptr;
-    if (!((t.B == 2 || t.B == 4) && t.filter) && !hashed) return cudaErrorInvalidValue;
+namespace {
+
+bool served(const DevTables &t) { return ((t.B == 2 || t.B == 4) && t.filter) || (t.B == 8 && t.hashed && t.HK); }
+
+// Bytes staged per tile: the tile and a halo of up to kHaloCap bytes (at
+// least 16, the windows' look-ahead).
+uint32_t staged_bytes(const DevTables &t) {
+    const uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
+    return align16(kTile + H) > align16(kTile + 16) ? align16(kTile + H) : align16(kTile + 16);
+}
+
+// The launch parameters of automaton t and request r, all but the shared-
+// memory layout.
+cudaError_t fill_params(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu, FilterParams &p) {
+    if (!served(t)) return cudaErrorInvalidValue;
+    const bool hashed = t.B == 8;
     if (mode != OUT_DENSE && mode != OUT_COUNT && mode != OUT_SLOTS) return cudaErrorInvalidValue;
     const bool batch = r.batch != nullptr;
     if (batch && (mode == OUT_COUNT || !r.lists)) return cudaErrorInvalidValue;
     if (mode == OUT_SLOTS && (!r.slots.counts || !r.slots.slots)) return cudaErrorInvalidValue;
-    int dev = 0, sms = 0, max_smem = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    FilterParams p{};
+    p = FilterParams{};
     p.text = r.text;
     p.n = r.n;
     p.tile = kTile;
-    const uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
-    p.staged = align16(kTile + H) > align16(kTile + 16) ? align16(kTile + H) : align16(kTile + 16);
+    p.staged = staged_bytes(t);
     uint64_t tiles = 0;
     if (!batch) {
         const uint64_t head = reinterpret_cast<uintptr_t>(r.text) & 15u;
         tiles = (r.n + head + kTile - 1) / kTile;
         if (tiles >= 0x7FFFFFFFull) return cudaErrorInvalidValue;
-    }
-    p.ntiles = static_cast<uint32_t>(tiles);
-    if (!batch) {
-        const uint64_t head = reinterpret_cast<uintptr_t>(r.text) & 15u;
         p.gbase = r.text - head;
         p.a1 = (head + 15u) & ~15ull;
         p.a2 = (head + r.n) & ~15ull;
         p.vec_ok = ((reinterpret_cast<uintptr_t>(r.out) - 4u * head) & 15u) == 0 ? 1u : 0u;
     }
+    p.ntiles = static_cast<uint32_t>(tiles);
     p.batch = r.batch;
     p.lists = r.lists;
-    // per-warp layout: stages, packed codes, unknown-byte bits, survivor
-    // queue, stage descriptors; a CTA-wide -1 buffer for the bulk stores
-    const uint32_t packed_bytes = align16(kCodeSpan * t.B / 8 + 16);
-    const uint32_t inv_bytes = align16(kCodeSpan / 8 + 16);
-    const uint32_t queue_bytes = align16(kTile * 2);
-    const uint32_t neg1_bytes = kTile * 4;
-    const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
-    uint32_t smem = 0;
-    bool fits = false;
-    const int want = tu.stages ? tu.stages : 3;
-    for (int st = want; st >= 2 && !fits; --st) {
-        p.nstages = static_cast<uint32_t>(st);
-        p.off_packed = p.nstages * p.staged;
-        p.off_inv = p.off_packed + packed_bytes;
-        p.off_queue = p.off_inv + inv_bytes;
-        p.off_meta = p.off_queue + queue_bytes;
-        p.off_help = p.off_meta + 16u;
-        p.warp_bytes = p.off_help + align16(static_cast<uint32_t>(sizeof(HelpSlot)));
-        p.off_neg1 = align16(kOffF + t.fbytes);
-        p.off_warp = align16(p.off_neg1 + neg1_bytes);
-        smem = p.off_warp + nw * p.warp_bytes;
-        fits = static_cast<int>(smem) <= max_smem;
-    }
-    if (!fits) return cudaErrorInvalidConfiguration;
     p.G = t.G;
     p.Fg = t.F;
     p.JK = t.JK;
@@ -99,11 +78,12 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.hk_shift = hashed ? 32u - t.hk_bits : 0u;
     p.hk_mask = hashed ? (1u << t.hk_bits) - 1u : 0u;
     p.hk_probes = hashed ? t.hk_probes : 0u;
+    p.wait_ns = tu.wait_ns ? tu.wait_ns : kWaitNs;
+    p.stall_help = tu.stall_help ? 1u : 0u;
+    p.kind = filter_kind(t.B, t.gbits);
     p.skip = t.skip;
     p.chain = t.chain;
     p.s_chain = t.skip ? t.s_chain : 0xFFFFFFFFu;
-    p.wait_ns = tu.wait_ns ? tu.wait_ns : kWaitNs;
-    p.stall_help = tu.stall_help ? 1u : 0u;
     p.hash_shift = t.hash_shift;
     p.hcode_lo = t.hash_code[0];
     p.hcode_hi = t.hash_code[1];
@@ -114,9 +94,77 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     p.sl = r.slots;
     // the tile counter; none is needed when every tile is some warp's first
     p.counter = r.scratch && r.scratch_bytes >= 16 ? static_cast<unsigned int *>(r.scratch) : nullptr;
-    e = device_error_word(&p.err);
+    return device_error_word(&p.err);
+}
+
+// The shared-memory layout of a launch of nw warps whose automata stage up to
+// `staged` bytes per tile, take up to B bits per code and have filters of up
+// to fbytes: per warp the stages, packed codes, unknown-byte bits, survivor
+// queue, stage descriptors and help slot; a CTA-wide -1 buffer for the bulk
+// stores.  The most stages (want, down to 2) that fit max_smem; false if none.
+bool layout(FilterParams &p, uint32_t staged, uint32_t B, uint32_t fbytes, uint32_t nw, int want, int max_smem,
+            uint32_t *smem) {
+    const uint32_t packed_bytes = align16(kCodeSpan * B / 8 + 16);
+    const uint32_t inv_bytes = align16(kCodeSpan / 8 + 16);
+    const uint32_t queue_bytes = align16(kTile * 2);
+    const uint32_t neg1_bytes = kTile * 4;
+    for (int st = want; st >= 2; --st) {
+        p.nstages = static_cast<uint32_t>(st);
+        p.off_packed = p.nstages * staged;
+        p.off_inv = p.off_packed + packed_bytes;
+        p.off_queue = p.off_inv + inv_bytes;
+        p.off_meta = p.off_queue + queue_bytes;
+        p.off_help = p.off_meta + 16u;
+        p.warp_bytes = p.off_help + align16(static_cast<uint32_t>(sizeof(HelpSlot)));
+        p.off_neg1 = align16(kOffF + fbytes);
+        p.off_warp = align16(p.off_neg1 + neg1_bytes);
+        *smem = p.off_warp + nw * p.warp_bytes;
+        if (static_cast<int>(*smem) <= max_smem) return true;
+    }
+    return false;
+}
+
+struct DeviceShape {
+    int sms = 0;
+    int max_smem = 0;
+};
+
+cudaError_t device_shape(DeviceShape *out) {
+    static DeviceShape cache[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(sms);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (cache[dev].sms == 0) {
+        DeviceShape d;
+        e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return e;
+        cache[dev] = d;
+    }
+    *out = cache[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
+                          cudaStream_t stream) {
+    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
+        tu.stages > kMaxStages)
+        return cudaErrorInvalidValue;
+    DeviceShape ds;
+    cudaError_t e = device_shape(&ds);
+    if (e != cudaSuccess) return e;
+    FilterParams p;
+    e = fill_params(t, r, mode, tu, p);
+    if (e != cudaSuccess) return e;
+    const bool batch = r.batch != nullptr;
+    const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
+    uint32_t smem = 0;
+    if (!layout(p, p.staged, t.B, t.fbytes, nw, tu.stages ? tu.stages : 3, ds.max_smem, &smem))
+        return cudaErrorInvalidConfiguration;
+    uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(ds.sms);
     if (!batch) {  // a batch's units are counted on the device: every CTA starts
         const uint32_t need_ctas = (p.ntiles + nw - 1) / nw;
         if (grid > need_ctas) grid = need_ctas;
@@ -129,14 +177,67 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     // tiles, so those forms share them within the CTA (small alphabets)
     if (!batch && t.B <= 4 &&
         static_cast<uint64_t>(p.ntiles) <= static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw)
-        return launch_filter_help(mode, p, t.B, t.gbits, grid, tu.block, smem, max_smem, stream);
-    if (t.B == 8) return launch_filter8(mode, p, t.gbits, grid, tu.block, smem, max_smem, stream);
+        return launch_filter_help(mode, p, t.B, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
+    if (t.B == 8) return launch_filter8(mode, p, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
     if (t.B == 2) {
-        if (t.gbits == 16) return launch_modes<2, int16_t, false>(mode, p, grid, tu.block, smem, max_smem, stream);
-        return launch_modes<2, int32_t, false>(mode, p, grid, tu.block, smem, max_smem, stream);
+        if (t.gbits == 16) return launch_modes<2, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+        return launch_modes<2, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
     }
-    if (t.gbits == 16) return launch_modes<4, int16_t, false>(mode, p, grid, tu.block, smem, max_smem, stream);
-    return launch_modes<4, int32_t, false>(mode, p, grid, tu.block, smem, max_smem, stream);
+    if (t.gbits == 16) return launch_modes<4, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+    return launch_modes<4, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+}
+
+bool filter_multi_serves(const DevTables *const *ts, uint32_t nh) {
+    if (nh == 0 || nh > kMultiMax) return false;
+    for (uint32_t a = 0; a < nh; ++a)
+        if (!served(*ts[a])) return false;
+    return true;
+}
+
+cudaError_t launch_filter_multi(const DevTables *const *ts, const MatchRequest *rs, uint32_t nh, OutMode mode,
+                                unsigned long long wait_ns, cudaStream_t stream) {
+    if (!filter_multi_serves(ts, nh) || (mode != OUT_DENSE && mode != OUT_SLOTS)) return cudaErrorInvalidValue;
+    DeviceShape ds;
+    cudaError_t e = device_shape(&ds);
+    if (e != cudaSuccess) return e;
+    // 11 KiB of parameters: kept off the stack, filled and launched under a lock
+    static MultiParams mp;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    mp.nh = nh;
+    uint32_t staged = 0, B = 0, fbytes = 0;
+    Tuning tu;
+    tu.wait_ns = wait_ns;
+    for (uint32_t a = 0; a < nh; ++a) {
+        if (!rs[a].batch || !rs[a].lists || !rs[a].scratch || rs[a].scratch_bytes < 16) return cudaErrorInvalidValue;
+        e = fill_params(*ts[a], rs[a], mode, tu, mp.a[a]);
+        if (e != cudaSuccess) return e;
+        staged = staged > mp.a[a].staged ? staged : mp.a[a].staged;
+        B = B > ts[a]->B ? B : ts[a]->B;
+        fbytes = fbytes > ts[a]->fbytes ? fbytes : ts[a]->fbytes;
+    }
+    // one layout for all: the largest stages, codes and filter; the active
+    // automaton's parameters after it
+    FilterParams shape{};
+    uint32_t smem = 0;
+    const uint32_t pbytes = align16(static_cast<uint32_t>(sizeof(FilterParams)));
+    if (!layout(shape, staged, B, fbytes, kMultiBlock / 32, 3, ds.max_smem - static_cast<int>(pbytes), &smem))
+        return cudaErrorInvalidConfiguration;
+    mp.params_off = smem;
+    smem += pbytes;
+    for (uint32_t a = 0; a < nh; ++a) {
+        FilterParams &p = mp.a[a];
+        p.nstages = shape.nstages;
+        p.off_packed = shape.off_packed;
+        p.off_inv = shape.off_inv;
+        p.off_queue = shape.off_queue;
+        p.off_meta = shape.off_meta;
+        p.off_help = shape.off_help;
+        p.warp_bytes = shape.warp_bytes;
+        p.off_neg1 = shape.off_neg1;
+        p.off_warp = shape.off_warp;
+    }
+    return launch_filter_multi_modes(mode, mp, static_cast<uint32_t>(ds.sms), smem, ds.max_smem, stream);
 }
 
 }  // namespace pfac

@@ -116,6 +116,7 @@ struct FilterParams {
     // more finished chunk than its offered tile has (a test of that wait)
     unsigned long long wait_ns;
     uint32_t stall_help;
+    uint32_t kind;  // (B << 8) | goto-entry bits, for the multi-automaton launch
     // 8-bit codes: the codes are the bytes (256 columns), or classes from the
     // byte table; the filter index is the top bits of (window & wmask) *
     // kFilterHashMul (32 - fshift of them), the state hash's bucket the top
@@ -349,96 +350,6 @@ template <typename GT>
 __device__ __noinline__ int walk_far(const FilterParams &p, const uint8_t *cls8, const TileText &tt, int64_t gpb,
                                      uint32_t s, uint32_t q);
 
-// A found id (or, for slots, a match) of a survivor at tile position i:
-// dense output (with FALLBACK: the unit's dense fallback), count, or the
-// unit's slots (dense_all: into the dense fallback as well).  The tile's -1
-// are written already.  All lanes (slots: ballot).
-template <int MODE, bool FALLBACK>
-__device__ __forceinline__ void put_result(const FilterParams &p, const TileText &tt, int64_t gpb, uint32_t su,
-                                           bool mine, uint32_t i, int v, int lane, unsigned long long &cnt,
-                                           bool dense_all) {
-    if (MODE == OUT_SLOTS) {
-        // one atomic per warp and slot index, ranks by ballot
-        const bool hit = mine && v >= 0;
-        const unsigned m = __ballot_sync(kFull, hit);
-        if (hit && dense_all) p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + i] = v;
-        if (m) {
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(p.sl.counts + su, static_cast<uint32_t>(__popc(m)));
-            base = __shfl_sync(kFull, base, 0) + __popc(m & ((1u << lane) - 1u));
-            if (hit && base < kSlotCap)
-                p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + base] =
-                    (static_cast<unsigned long long>(static_cast<uint32_t>(v)) << 32) | static_cast<uint32_t>(gpb + i);
-        }
-        return;
-    }
-    if (!mine || v < 0) return;
-    if (MODE == OUT_COUNT)
-        cnt += 1ull;
-    else if (FALLBACK)
-        p.sl.dense[static_cast<uint64_t>(su) * kDenseStride + i] = v;
-    else
-        tt.out[gpb + i] = v;
-}
-
-// 8-bit codes: finish up to SLOTS * 32 queued survivors (as finish_survivors):
-// every window's state-hash entry is loaded first; the entry settles most
-// survivors (no state: -1; a leaf, or a one-child state whose child's code is
-// not next: the state's result); the others, and the windows past the text
-// end, walk on through walk_far.
-template <typename GT, int MODE, int SLOTS, bool FALLBACK>
-__device__ __forceinline__ bool finish_survivors8(const FilterParams &p, const TileText &tt, const WarpSmem &w,
-                                                  int64_t gpb, uint32_t avail, int lane, unsigned long long &cnt,
-                                                  uint32_t base, uint32_t su, bool dense_all) {
-    uint32_t ii[SLOTS], x[SLOTS], st[SLOTS], q[SLOTS];
-    uint4 e[SLOTS];
-    int v[SLOTS];
-    uint32_t act = 0, far = 0;
-#pragma unroll
-    for (int t = 0; t < SLOTS; ++t) {
-        const uint32_t qi = lane + 32u * t;
-        ii[t] = 0;
-        x[t] = 0;
-        st[t] = 0;
-        q[t] = 0;
-        v[t] = -1;
-        e[t] = make_uint4(0u, 0u, 0u, 0u);
-        if (qi < avail) {
-            act |= 1u << t;
-            const uint32_t e16 = w.queue[base + qi];
-            ii[t] = e16 & 0x7FFFu;
-            if (e16 >> 15) {  // the window runs past the text end: walk from the root
-                far |= 1u << t;
-                q[t] = ii[t];
-            } else {
-                x[t] = code_window<8>(w.packed, ii[t]) & p.wmask;
-                e[t] = __ldg(p.HK + hk_slot(p, x[t]));
-            }
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < SLOTS; ++t) {
-        if (((act & ~far) >> t) & 1u) {
-            const uint4 f = hk_find(p, x[t], e[t]);
-            const uint32_t j = ii[t] + p.k;  // the character after the window (j < kCodeSpan)
-            const bool c_ok = !((w.inv[j >> 4] >> (j & 15u)) & 1u);
-            const uint32_t c = (w.packed[j >> 2] >> (8u * (j & 3u))) & 0xFFu;
-            if (!hk_outcome(p, f, ii[t], c, c_ok, v[t], st[t], q[t])) far |= 1u << t;
-        }
-    }
-#pragma unroll 1
-    for (int t = 0; t < SLOTS; ++t)
-        if ((far >> t) & 1u) v[t] = walk_far<GT>(p, w.cls8, tt, gpb, st[t], q[t]);
-    bool found = false;
-#pragma unroll
-    for (int t = 0; t < SLOTS; ++t) {
-        const bool mine = (act >> t) & 1u;
-        put_result<MODE, FALLBACK>(p, tt, gpb, su, mine, ii[t], v[t], lane, cnt, dense_all);
-        found |= mine && v[t] >= 0;
-    }
-    return found;
-}
-
 // Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)) of a
 // tile whose dense ids were set to -1 first: the ids found go to the dense
 // output (MODE == OUT_DENSE; with FALLBACK to the unit's dense fallback
@@ -450,9 +361,6 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
                                                  int64_t gpb, bool interior, bool clean, uint32_t avail,
                                                  uint32_t pbase, int lane, unsigned long long &cnt, uint32_t base,
                                                  uint32_t coded = 0, uint32_t su = 0, bool dense_all = false) {
-    if constexpr (B == 8) {
-        return finish_survivors8<GT, MODE, SLOTS, FALLBACK>(p, tt, w, gpb, avail, lane, cnt, base, su, dense_all);
-    } else {
     const int64_t n = static_cast<int64_t>(tt.n);
     const uint32_t k = p.k, k2 = p.k2;
     const GT *G = static_cast<const GT *>(p.G);
@@ -460,7 +368,9 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
     int v[SLOTS];
     uint32_t act = 0, pend = 0, walking = 0;
     uint32_t x[SLOTS];
-    // window table: depth-k state or result; all loads first
+    uint4 he[B == 8 ? SLOTS : 1];  // 8-bit codes: each window's first state-hash entry
+    // window table (8-bit codes: state hash): depth-k state or result; all
+    // loads first
 #pragma unroll
     for (int t = 0; t < SLOTS; ++t) {
         const uint32_t qi = lane + 32u * t;
@@ -477,10 +387,35 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
             q[t] = i;
             if (!(e16 >> 15)) {
                 x[t] = code_window<B>(w.packed, i);
-                v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
+                if constexpr (B == 8) {
+                    x[t] &= p.wmask;
+                    he[t] = __ldg(p.HK + hk_slot(p, x[t]));
+                } else {
+                    v[t] = __ldg(p.JK + (x[t] & ((1u << (B * k)) - 1u)));
+                }
                 pend |= 1u << t;
             }
         }
+    }
+    if constexpr (B == 8) {
+        // the entry settles most survivors; the others walk on from the state
+        // or its child (no stride table)
+#pragma unroll
+        for (int t = 0; t < SLOTS; ++t) {
+            if ((pend >> t) & 1u) {
+                const uint4 f = hk_find(p, x[t], he[t]);
+                const uint32_t j = ii[t] + k;  // the character after the window (j < kCodeSpan)
+                const bool c_ok = !((w.inv[j >> 4] >> (j & 15u)) & 1u);
+                const uint32_t c = (w.packed[j >> 2] >> (8u * (j & 3u))) & 0xFFu;
+                int r = -1;
+                if (!hk_outcome(p, f, ii[t], c, c_ok, r, st[t], q[t])) {
+                    v[t] = INT_MIN;  // walking
+                } else {
+                    v[t] = r;
+                }
+            }
+        }
+        pend = 0;
     }
     // stride table for the walks still alive at depth k
 #pragma unroll
@@ -606,14 +541,13 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
         }
     }
     return found;
-    }
 }
 
 // One warp, a tile whose matches overflowed its slots: the survivors walked
 // again, 64 at a time (rare, so with few registers), the ids found written to
 // the unit's dense fallback (set to -1 by the caller).
 template <int B, typename GT>
-__device__ __forceinline__ void refill_fallback(const FilterParams &p, const TileText &tt, const WarpSmem &w,
+__device__ __noinline__ void refill_fallback(const FilterParams &p, const TileText &tt, const WarpSmem &w,
                                                 int64_t gpb, bool interior, bool clean, uint32_t total, int lane,
                                                 uint32_t su) {
     unsigned long long none = 0;
@@ -878,11 +812,56 @@ __device__ __forceinline__ void flight_output(const FilterParams &p, const Work 
     if (mine) tt.out[f.gpb + f.pos] = f.val;
 }
 
+// The CTA's start: the constant -1 buffer, the help slots and CTA counters,
+// and the mbarriers (p: the launch's shared-memory layout).  Ends with a
+// CTA barrier.
+__device__ __forceinline__ void filter_setup(const FilterParams &p, uint8_t *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint8_t *wreg = smem + p.off_warp + static_cast<size_t>(warp) * p.warp_bytes;
+    HelpSlot *my_help = reinterpret_cast<HelpSlot *>(wreg + p.off_help);
+    for (uint32_t i = threadIdx.x; i < kTile; i += blockDim.x) reinterpret_cast<int32_t *>(smem + p.off_neg1)[i] = -1;
+    fence_proxy_async_smem();  // the constant buffer is read by bulk stores
+    if (lane == 0) {
+        my_help->ticket = 0;
+        my_help->pub = 0;
+        my_help->nchunks = 0;
+        my_help->done = 0;
+    }
+    if (threadIdx.x == 0) {
+        *reinterpret_cast<uint32_t *>(smem + kOffRetired) = 0;
+        *reinterpret_cast<uint32_t *>(smem + kOffOffers) = 0;
+        mbar_init(reinterpret_cast<uint64_t *>(smem + kOffJBar), 1);
+        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
+        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// One thread: fetch an automaton's byte table and root filter into shared
+// memory, completing on the table mbarrier.  The CTA must be done reading
+// the previous ones (a CTA barrier before).
+__device__ __forceinline__ void filter_load_tables(const FilterParams &p, uint8_t *smem) {
+    uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
+    fence_proxy_async_smem();  // earlier generic reads of these bytes before the async writes
+    mbar_arrive_expect_tx(jbar, 256u + p.fbytes);
+    bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
+    bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
+}
+
+// One warp: every work unit of the launch's automaton that this warp takes,
+// through the pipeline below.  Stage barriers are used in a running order:
+// iteration it uses stage it % nstages with phase parity (it / nstages) & 1;
+// the warp starts at iteration it0 and returns in *it_next where the next
+// automaton's units start.  jpar: the phase parity of the table barrier that
+// the automaton's tables complete.  False when a bounded wait ran out (the
+// error is latched; the warp's copies in flight have landed or been waited
+// for, within the limit).
 // HELP: share heavy tiles within the CTA (the forms for one text that is short
 // next to the grid; see the heavy path below).
 template <int B, typename GT, int MODE, bool BATCH, bool HELP>
-__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_constant__ FilterParams p) {
-    extern __shared__ __align__(128) uint8_t smem[];
+__device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *smem, uint32_t it0, uint32_t jpar,
+                                             unsigned long long &cnt, uint32_t *it_next) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint64_t *jbar = reinterpret_cast<uint64_t *>(smem + kOffJBar);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kOffStageBar) + warp * kMaxStages;
@@ -906,30 +885,6 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
     const uint32_t k = p.k, k2 = p.k2;
     const bool owner = lane < static_cast<int>(kOwnLanes);
 
-    for (uint32_t i = threadIdx.x; i < kTile; i += blockDim.x) reinterpret_cast<int32_t *>(smem + p.off_neg1)[i] = -1;
-    fence_proxy_async_smem();  // the constant buffer is read by bulk stores
-    if (lane == 0) {
-        my_help->ticket = 0;
-        my_help->pub = 0;
-        my_help->nchunks = 0;
-        my_help->done = 0;
-    }
-    if (threadIdx.x == 0) {
-        *retired = 0;
-        *offers = 0;
-    }
-    if (threadIdx.x == 0) {
-        mbar_init(jbar, 1);
-        uint64_t *all = reinterpret_cast<uint64_t *>(smem + kOffStageBar);
-        for (int i = 0; i < nw * kMaxStages; ++i) mbar_init(&all[i], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(jbar, 256u + p.fbytes);
-        bulk_load(smem + kOffCls, p.cls8g, 256u, jbar);
-        bulk_load(smem + kOffF, p.Fg, p.fbytes, jbar);
-    }
     // Tiles: the first one per warp statically, the rest claimed from a global
     // counter so that a warp held up by an expensive tile stops taking work.
     const uint64_t gw = static_cast<uint64_t>(warp) * gridDim.x + blockIdx.x;
@@ -943,14 +898,16 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
         }
         return __shfl_sync(kFull, t, 0);
     };
-    for (uint32_t s = 0; s < nst; ++s)
-        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, next_tile(s), lane);
+    for (uint32_t j = it0; j < it0 + nst; ++j) {
+        const uint32_t s = j % nst;
+        issue_unit(p, wk, &bars[s], &stile[s], &sitem[s], wreg + s * p.staged, next_tile(j), lane);
+    }
 
-    unsigned long long cnt = 0;
     Flight f1 = empty_flight(), f2 = empty_flight();  // one and two tiles back
-    bool ok = mbar_wait(jbar, 0, p.wait_ns);
+    bool ok = mbar_wait(jbar, jpar, p.wait_ns);
     // stage s of iteration it is it % nst, its phase parity (it / nst) & 1
-    for (uint32_t it = 0, s = 0, par = 0;; ++it, s = s + 1 == nst ? 0u : s + 1, par ^= s == 0 ? 1u : 0u) {
+    uint32_t it = it0;
+    for (uint32_t s = it0 % nst, par = (it0 / nst) & 1u;; ++it, s = s + 1 == nst ? 0u : s + 1, par ^= s == 0 ? 1u : 0u) {
         ok = ok && mbar_wait(&bars[s], par, p.wait_ns);
         if (!__all_sync(kFull, ok)) {
             // A copy never completed: latch the error, let this warp's copies in
@@ -959,10 +916,10 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
                 bulk_wait_all();
                 atomicOr(p.err, static_cast<unsigned>(kErrTimeout));
                 atomicAdd(retired, 1u);
-                mbar_wait(jbar, 0, p.wait_ns);
+                mbar_wait(jbar, jpar, p.wait_ns);
                 for (uint32_t j = it; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u, p.wait_ns);
             }
-            return;
+            return false;
         }
         const uint32_t tile = stile[s];
         if (tile >= wk.units) break;
@@ -1302,6 +1259,11 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
     flight_output<MODE>(p, wk, w, f2, lane, cnt);
     flight_finish<B, GT>(p, wk, w.cls8, f1);
     flight_output<MODE>(p, wk, w, f1, lane, cnt);
+    // the stages issued past this warp's last unit hold end marks (an arrival
+    // without a copy): complete their phases, so the next automaton's units
+    // start on fresh ones
+    for (uint32_t j = it + 1; j < it + nst; ++j) mbar_wait(&bars[j % nst], (j / nst) & 1u, p.wait_ns);
+    *it_next = it + nst;
 
     // no tiles left: help with the CTA's heavy tiles until every warp is done
     // with its own (no tile is offered after that, and every offer is then
@@ -1344,12 +1306,81 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
         }
     }
 
+    return true;
+}
+
+template <int B, typename GT, int MODE, bool BATCH, bool HELP>
+__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_constant__ FilterParams p) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    filter_setup(p, smem);
+    if (threadIdx.x == 0) filter_load_tables(p, smem);
+    unsigned long long cnt = 0;
+    uint32_t it = 0;
+    if (!filter_units<B, GT, MODE, BATCH, HELP>(p, smem, 0, 0, cnt, &it)) return;
     if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
     if (MODE == OUT_COUNT) {
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
         if (lane == 0 && cnt) atomicAdd(p.count, cnt);
     }
+}
+
+// Batches: every automaton of the batch (at most kMultiMax) in one persistent
+// launch.  Each CTA takes the automata in order: it fetches an automaton's
+// tables into shared memory, its warps take that automaton's units through
+// filter_units (the units of all its texts, from its own counter), and once
+// all of the CTA's warps are done with it the CTA moves to the next.  CTAs
+// move on independently, so the automata overlap on the GPU and no launch
+// boundary drains the grid between them.  Every automaton of the launch
+// shares one shared-memory layout (offsets from a[0]); the automaton being
+// matched has its parameters copied to shared memory at params_off.
+constexpr uint32_t kMultiMax = 32;
+// Threads per CTA of the multi-automaton kernel: 12 warps, which leaves room
+// for the automaton loop's registers around the largest form without spills.
+constexpr int kMultiBlock = 384;
+
+struct MultiParams {
+    FilterParams a[kMultiMax];
+    uint32_t nh;
+    uint32_t params_off;
+};
+static_assert(sizeof(FilterParams) % 4 == 0, "parameters are copied as words");
+
+// FilterParams::kind of a form: (B << 8) | goto-entry bits.
+__host__ __device__ constexpr uint32_t filter_kind(uint32_t B, uint32_t gbits) { return (B << 8) | gbits; }
+
+template <int MODE>
+__global__ void __launch_bounds__(kMultiBlock, 1) pfac_filter_multi(const __grid_constant__ MultiParams mp) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    const int lane = threadIdx.x & 31;
+    filter_setup(mp.a[0], smem);
+    FilterParams &p = *reinterpret_cast<FilterParams *>(smem + mp.params_off);
+    uint32_t it = 0, loads = 0;
+    int bad = 0;
+    for (uint32_t a = 0; a < mp.nh; ++a) {
+        if (__ldg(&mp.a[a].batch->units) == 0) continue;  // the same for every thread
+        // the CTA is done with the previous automaton (and leaves together
+        // when a warp's bounded wait ran out)
+        if (__syncthreads_or(bad)) break;
+        for (uint32_t i = threadIdx.x; i < sizeof(FilterParams) / 4; i += blockDim.x)
+            reinterpret_cast<uint32_t *>(&p)[i] = reinterpret_cast<const uint32_t *>(&mp.a[a])[i];
+        __syncthreads();
+        if (threadIdx.x == 0) filter_load_tables(p, smem);
+        unsigned long long cnt = 0;
+        bool ok = true;
+        switch (p.kind) {
+            case filter_kind(2, 16): ok = filter_units<2, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(2, 32): ok = filter_units<2, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(4, 16): ok = filter_units<4, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(4, 32): ok = filter_units<4, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(8, 16): ok = filter_units<8, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+            default: ok = filter_units<8, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+        }
+        ++loads;
+        bad |= ok ? 0 : 1;
+    }
+    if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
 }
 
 inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
@@ -1409,5 +1440,35 @@ cudaError_t launch_filter_help(OutMode mode, const filt::FilterParams &p, uint32
 // Launch of the 8-bit-code forms (hashed filter), filter8.cu.
 cudaError_t launch_filter8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t grid, uint32_t block,
                            uint32_t smem, int max_smem, cudaStream_t stream);
+
+namespace filt {
+template <int MODE>
+cudaError_t launch_multi(const MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem, cudaStream_t stream) {
+    static bool configured[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(pfac_filter_multi<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             max_smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    pfac_filter_multi<MODE><<<grid, kMultiBlock, smem, stream>>>(mp);
+    return cudaGetLastError();
+}
+}  // namespace filt
+
+// Launches of the multi-automaton kernel, filter_multi_dense.cu and
+// filter_multi_slots.cu.
+cudaError_t launch_filter_multi_dense(const filt::MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem,
+                                      cudaStream_t stream);
+cudaError_t launch_filter_multi_slots(const filt::MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem,
+                                      cudaStream_t stream);
+inline cudaError_t launch_filter_multi_modes(OutMode mode, const filt::MultiParams &mp, uint32_t grid, uint32_t smem,
+                                             int max_smem, cudaStream_t stream) {
+    return mode == OUT_DENSE ? launch_filter_multi_dense(mp, grid, smem, max_smem, stream)
+                             : launch_filter_multi_slots(mp, grid, smem, max_smem, stream);
+}
 
 }  // namespace pfac

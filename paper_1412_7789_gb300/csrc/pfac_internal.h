@@ -348,6 +348,16 @@ inline bool uses_filter(const DevTables &t, const Tuning &tu) { return t.filter 
 inline uint32_t unit_positions(const DevTables &t, const Tuning &tu) {
     return uses_filter(t, tu) ? filter_tile_positions() : tiled_tile_positions();
 }
+// A batch of nh automata in one persistent launch of the filter kernel
+// (filter.cu): whether it serves them all (every automaton has a root filter
+// and nh is small enough for the launch's parameters), and the launch.  rs[a]:
+// automaton a's request (batch head, planned list, its tile counter as
+// scratch, dense output or slots).  Every automaton runs the filter kernel,
+// whatever kernel its tuning names for single texts.
+bool filter_multi_serves(const DevTables *const *ts, uint32_t nh);
+cudaError_t launch_filter_multi(const DevTables *const *ts, const MatchRequest *rs, uint32_t nh, OutMode mode,
+                                unsigned long long wait_ns, cudaStream_t stream);
+
 // A matching launch on the kernel that serves the automaton.
 inline cudaError_t launch_match(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                                 cudaStream_t stream) {

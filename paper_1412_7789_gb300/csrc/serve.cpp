@@ -66,6 +66,7 @@ struct ac_server_impl {
     std::vector<const pfac::DevTables *> tabs;
     std::vector<pfac::Tuning> tune;
     int device = 0;
+    bool multi = false;          // waves match all automata in one launch (filter kernel for all)
     uint64_t budget = 0;         // for requests: the option's budget less the automata's tables
     uint64_t table_bytes = 0;    // the resident automata (each handle once)
     void *(*dev_alloc)(size_t, void *) = nullptr;
@@ -97,7 +98,10 @@ struct ac_server_impl {
 
 namespace {
 
-uint32_t tile_of(const pfac::DevTables &t, const pfac::Tuning &tu) { return pfac::unit_positions(t, tu); }
+// Positions per work unit of automaton a in the server's waves.
+uint32_t tile_of(const ac_server_impl *s, uint32_t a) {
+    return s->multi ? pfac::filter_tile_positions() : pfac::unit_positions(*s->tabs[a], s->tune[a]);
+}
 
 bool host_text(const ac_server_request &r) { return (r.flags & AC_REQ_HOST_TEXT) != 0; }
 
@@ -107,18 +111,18 @@ uint64_t text_head(const ac_server_request &r) {
     return host_text(r) ? 0u : (reinterpret_cast<uintptr_t>(r.d_text) & 15u);
 }
 
-uint64_t units_of(const pfac::DevTables &t, const pfac::Tuning &tu, const ac_server_request &r) {
+uint64_t units_of(const ac_server_impl *s, const ac_server_request &r) {
     if (r.n == 0) return 0;
-    const uint64_t T = tile_of(t, tu);
+    const uint64_t T = tile_of(s, r.automaton);
     return (r.n + text_head(r) + T - 1) / T;
 }
 
 // Device bytes a request holds while admitted: its text (a host text's device
 // copy), its output and the scratch of its tiles (counts, prefix, slots,
 // dense fallback).
-uint64_t request_bytes(const pfac::DevTables &t, const pfac::Tuning &tu, const ac_server_request &r) {
+uint64_t request_bytes(const ac_server_impl *s, const ac_server_request &r) {
     const uint64_t per_unit = 4 + 8 + 8ull * pfac::kSlotCap + 4ull * pfac::kDenseStride;
-    return r.n + 8ull * r.cap + units_of(t, tu, r) * per_unit + 64;
+    return r.n + 8ull * r.cap + units_of(s, r) * per_unit + 64;
 }
 
 // Device scratch of a wave: from the caller's allocator (freed when the wave
@@ -170,7 +174,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         const pfac::Tuning &tu = s->tune[q.r.automaton];
         // a host text: its copy at the front of the scratch (16-byte aligned)
         const size_t tb = host_text(q.r) ? round16(q.r.n) : 0;
-        const uint32_t units = static_cast<uint32_t>(units_of(t, tu, q.r));
+        const uint32_t units = pfac::compact_units(t, tu, tb ? nullptr : q.r.d_text, q.r.n);
         const size_t bytes = tb + pfac::compact_scratch_bytes(t, units, true);
         void *scratch = nullptr;
         e = wave_alloc(s, w, bytes, &scratch);
@@ -223,7 +227,6 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         heads[a].pad = 0;
         ubase[a] = static_cast<uint32_t>(U);
         uint64_t units = 0;
-        const pfac::DevTables &t = *s->tabs[a];
         while (j < L && w.reqs[order[j]].r.automaton == a) {
             const ac_server_request &r = w.reqs[order[j]].r;
             pfac::BatchItemDev &d = list[j];
@@ -231,7 +234,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
             d.out_off = 0;
             d.first_unit = static_cast<uint32_t>(units);
             d.item = order[j];
-            units += units_of(t, s->tune[a], r);
+            units += units_of(s, r);
             ++j;
         }
         heads[a].count = j - heads[a].offset;
@@ -295,7 +298,23 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
                                               w.stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, cb + 4 * U, w.stream);
-    for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
+    if (s->multi && e == cudaSuccess) {  // every automaton of the wave in one launch
+        std::vector<pfac::MatchRequest> rs(nh);
+        for (uint32_t a = 0; a < nh; ++a) {
+            pfac::MatchRequest &m = rs[a];
+            m.text = base;
+            m.batch = d_heads + a;
+            m.lists = d_list;
+            m.slots.counts = counts;
+            m.slots.slots = slots;
+            m.slots.ubase = ubase[a];
+            m.slots.dense = dense;
+            m.scratch = counters + 16u * a;
+            m.scratch_bytes = 16;
+        }
+        e = pfac::launch_filter_multi(s->tabs.data(), rs.data(), nh, pfac::OUT_SLOTS, s->tune[0].wait_ns, w.stream);
+    }
+    for (uint32_t a = 0; a < nh && e == cudaSuccess && !s->multi; ++a) {
         if (heads[a].units == 0) continue;
         pfac::MatchRequest m;
         m.text = base;
@@ -319,7 +338,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         g.batch = d_heads + a;
         g.lists = d_list;
         g.outs = d_outs;
-        g.tile = tile_of(*s->tabs[a], s->tune[a]);
+        g.tile = tile_of(s, a);
         g.counts = counts;
         g.prefix = prefix;
         g.slots = slots;
@@ -502,6 +521,7 @@ ac_status ac_server_create(const ac_handle *hs, uint32_t nh, const ac_server_opt
     s->budget = budget - s->table_bytes;
     s->max_wave = o.max_wave ? o.max_wave : 4096u;
     s->fifo = o.fifo != 0;
+    s->multi = !s->fifo && pfac::filter_multi_serves(s->tabs.data(), nh);
     uint32_t nw = o.waves_in_flight ? o.waves_in_flight : 2u;
     if (nw > kMaxWaves) nw = kMaxWaves;
     if (s->fifo) nw = 1;
@@ -530,7 +550,7 @@ ac_status ac_server_submit(ac_server s, const ac_server_request *req, uint64_t *
     if (r.cap > 0 && (!r.d_pos || !r.d_ids)) return AC_ERR_INVALID_ARG;
     Request q;
     q.r = r;
-    q.bytes = request_bytes(*s->tabs[r.automaton], s->tune[r.automaton], r);
+    q.bytes = request_bytes(s, r);
     if (q.bytes > s->budget) return AC_ERR_BUDGET;
     {
         std::lock_guard<std::mutex> lk(s->mu);
