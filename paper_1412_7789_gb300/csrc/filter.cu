@@ -92,6 +92,11 @@ cudaError_t fill_params(const DevTables &t, const MatchRequest &r, OutMode mode,
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;
+    if (hashed && !batch && r.list && r.list_count && r.list_cap && p.ntiles < (1u << 22)) {
+        p.list = r.list;
+        p.list_count = r.list_count;
+        p.list_cap = r.list_cap;
+    }
     // the tile counter; none is needed when every tile is some warp's first
     p.counter = r.scratch && r.scratch_bytes >= 16 ? static_cast<unsigned int *>(r.scratch) : nullptr;
     return device_error_word(&p.err);
@@ -178,7 +183,11 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     if (!batch && t.B <= 4 &&
         static_cast<uint64_t>(p.ntiles) <= static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw)
         return launch_filter_help(mode, p, t.B, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
-    if (t.B == 8) return launch_filter8(mode, p, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
+    if (t.B == 8) {
+        e = launch_filter8(mode, p, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
+        if (e == cudaSuccess && p.list) e = launch_survivors8(mode, p, t.gbits, static_cast<uint32_t>(ds.sms), stream);
+        return e;
+    }
     if (t.B == 2) {
         if (t.gbits == 16) return launch_modes<2, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
         return launch_modes<2, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);

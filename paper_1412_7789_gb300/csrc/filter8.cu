@@ -9,8 +9,14 @@ namespace pfac {
 cudaError_t launch_filter8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t grid, uint32_t block,
                            uint32_t smem, int max_smem, cudaStream_t stream) {
     using filt::launch_modes;
-    if (gbits == 16) return launch_modes<8, int16_t, false>(mode, p, grid, block, smem, max_smem, stream);
-    return launch_modes<8, int32_t, false>(mode, p, grid, block, smem, max_smem, stream);
+    return gbits == 16 ? launch_modes<8, int16_t, false>(mode, p, grid, block, smem, max_smem, stream)
+                       : launch_modes<8, int32_t, false>(mode, p, grid, block, smem, max_smem, stream);
+}
+
+cudaError_t launch_survivors8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t sms,
+                              cudaStream_t stream) {
+    return gbits == 16 ? filt::launch_survivors8<int16_t>(mode, p, sms, stream)
+                       : filt::launch_survivors8<int32_t>(mode, p, sms, stream);
 }
 
 }  // namespace pfac

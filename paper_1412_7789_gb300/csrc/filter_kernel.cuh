@@ -117,6 +117,11 @@ struct FilterParams {
     unsigned long long wait_ns;
     uint32_t stall_help;
     uint32_t kind;  // (B << 8) | goto-entry bits, for the multi-automaton launch
+    // one text, 8-bit codes: the survivor list of the two-phase form (null:
+    // one phase)
+    uint2 *list;
+    unsigned int *list_count;
+    uint32_t list_cap;
     // 8-bit codes: the codes are the bytes (256 columns), or classes from the
     // byte table; the filter index is the top bits of (window & wmask) *
     // kFilterHashMul (32 - fshift of them), the state hash's bucket the top
@@ -1060,7 +1065,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
             if (lane >= d) inc += y;
         }
         const uint32_t tot2 = __shfl_sync(kFull, inc, 31);
-        const uint32_t total = (tot2 & 0xFFFFu) + (tot2 >> 16);
+        uint32_t total = (tot2 & 0xFFFFu) + (tot2 >> 16);
         {
             const uint32_t excl = inc - c;
             uint32_t o0 = excl & 0xFFFFu, o1 = (tot2 & 0xFFFFu) + (excl >> 16);
@@ -1078,6 +1083,28 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
             }
         }
         __syncwarp();
+
+        if constexpr (B == 8 && !BATCH) {
+            // two-phase form: the tile's survivors go to the list (their
+            // windows with them) and the tile counts as one without survivors
+            // here; a window past the text end, or no room, keeps them here
+            if (p.list && total > 0 && !__any_sync(kFull, (slowm & sv) != 0u)) {
+                uint32_t lbase = 0;
+                if (lane == 0) lbase = atomicAdd(p.list_count, total);
+                lbase = __shfl_sync(kFull, lbase, 0);
+                if (static_cast<uint64_t>(lbase) + total <= p.list_cap) {
+                    for (uint32_t j = static_cast<uint32_t>(lane); j < total; j += 32u) {
+                        const uint32_t i = w.queue[j] & 0x7FFFu;
+                        p.list[lbase + j] = make_uint2((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask);
+                    }
+                    total = 0;
+                } else {
+                    // the entries reserved below the capacity: marked empty
+                    for (uint32_t j = static_cast<uint32_t>(lane); j < total && lbase + j < p.list_cap; j += 32u)
+                        p.list[lbase + j] = make_uint2(0xFFFFFFFFu, 0u);
+                }
+            }
+        }
 
         if (total > 32) {
             // 4a. many survivors: finish the tiles in flight, then this one
@@ -1326,6 +1353,91 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
     }
 }
 
+// The second phase of the two-phase form (one text, 8-bit codes): one thread
+// per listed survivor, two at a time so that their loads overlap, at full
+// occupancy (six CTAs of 256 threads per SM).  Each survivor's state-hash
+// entry and the code after its window are loaded together; the entry settles
+// most survivors, the others walk on (chain records, goto rows, text from
+// global memory).  Ids found go to the dense output (its -1 are written by
+// the first phase), the count, or the unit's slots (no dense fallback: the
+// gather step matches a unit with more matches than slots again).
+constexpr int kSurvBlock = 256;
+constexpr int kSurvCtas = 6;
+
+template <typename GT, int MODE>
+__global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const __grid_constant__ FilterParams p) {
+    __shared__ uint8_t cls8[256];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) cls8[i] = __ldg(p.cls8g + i);
+    __syncthreads();
+    const uint32_t listed = *reinterpret_cast<volatile const unsigned int *>(p.list_count);
+    const uint32_t m = listed < p.list_cap ? listed : p.list_cap;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    const int64_t head = static_cast<int64_t>(reinterpret_cast<uintptr_t>(p.text) & 15u);
+    const int64_t n = static_cast<int64_t>(p.n);
+    unsigned long long cnt = 0;
+    for (uint32_t b0 = blockIdx.x * blockDim.x + threadIdx.x; b0 < m; b0 += 2u * stride) {
+        uint2 e[2];
+        uint4 he[2];
+        uint32_t c[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
+            e[t] = idx < m ? __ldg(p.list + idx) : make_uint2(0xFFFFFFFFu, 0u);
+            he[t] = make_uint4(0u, 0u, 0u, 0u);
+            c[t] = 0x100u;  // no character after the window (or one in no keyword)
+            if (e[t].x != 0xFFFFFFFFu) {
+                he[t] = __ldg(p.HK + hk_slot(p, e[t].y));
+                const int64_t j = static_cast<int64_t>(e[t].x >> 10) * kTile - head + (e[t].x & 1023u) + p.k;
+                if (j < n) {
+                    const uint32_t bt = __ldg(p.text + j);
+                    c[t] = p.identity ? bt : (cls8[bt] == 0xFFu ? 0x100u : cls8[bt]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            if (e[t].x == 0xFFFFFFFFu) continue;
+            const uint32_t unit = e[t].x >> 10, i = e[t].x & 1023u;
+            const int64_t gpb = static_cast<int64_t>(unit) * kTile - head;
+            int r = -1;
+            uint32_t s = 0, q = 0;
+            if (!hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c[t] & 0xFFu, c[t] < 0x100u, r, s, q))
+                r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, s, q);
+            if (r < 0) continue;
+            if (MODE == OUT_DENSE) {
+                p.out[gpb + i] = r;
+            } else if (MODE == OUT_COUNT) {
+                ++cnt;
+            } else {
+                const uint32_t su = p.sl.ubase + unit;
+                const uint32_t k = atomicAdd(p.sl.counts + su, 1u);
+                if (k < kSlotCap)
+                    p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + k] =
+                        (static_cast<unsigned long long>(static_cast<uint32_t>(r)) << 32) |
+                        static_cast<uint32_t>(gpb + i);
+            }
+        }
+    }
+    if (MODE == OUT_COUNT) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
+        if (lane == 0 && cnt) atomicAdd(p.count, cnt);
+    }
+}
+
+template <typename GT>
+cudaError_t launch_survivors8(OutMode mode, const FilterParams &p, uint32_t sms, cudaStream_t stream) {
+    const uint32_t grid = sms * static_cast<uint32_t>(kSurvCtas);
+    switch (mode) {
+        case OUT_DENSE: pfac_survivors8<GT, OUT_DENSE><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_COUNT: pfac_survivors8<GT, OUT_COUNT><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_SLOTS: pfac_survivors8<GT, OUT_SLOTS><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // Batches: every automaton of the batch (at most kMultiMax) in one persistent
 // launch.  Each CTA takes the automata in order: it fetches an automaton's
 // tables into shared memory, its warps take that automaton's units through
@@ -1437,9 +1549,12 @@ cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uin
 // Launch of the forms that share heavy tiles (one text only), filter_help.cu.
 cudaError_t launch_filter_help(OutMode mode, const filt::FilterParams &p, uint32_t B, uint32_t gbits, uint32_t grid,
                                uint32_t block, uint32_t smem, int max_smem, cudaStream_t stream);
-// Launch of the 8-bit-code forms (hashed filter), filter8.cu.
+// Launch of the 8-bit-code forms (hashed filter) and of the second phase of
+// their two-phase form, filter8.cu.
 cudaError_t launch_filter8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t grid, uint32_t block,
                            uint32_t smem, int max_smem, cudaStream_t stream);
+cudaError_t launch_survivors8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t sms,
+                              cudaStream_t stream);
 
 namespace filt {
 template <int MODE>

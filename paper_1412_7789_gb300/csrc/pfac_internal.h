@@ -222,7 +222,27 @@ struct MatchRequest {
     SlotOut slots;                           // OUT_SLOTS
     void *scratch = nullptr;                 // zeroed: tile counter (16 bytes)
     size_t scratch_bytes = 0;
+    // One text, 8-bit codes (hashed filter): the survivor list of the
+    // two-phase form (see survivor_list_entries); nullptr = every tile's
+    // survivors are resolved by the warp that filtered it.
+    uint2 *list = nullptr;
+    unsigned int *list_count = nullptr;      // zeroed
+    uint32_t list_cap = 0;
 };
+
+// The two-phase form of the filter kernel for one text with 8-bit codes: the
+// first launch stages, filters and writes the -1 of every tile, and appends
+// each survivor's window to a list -- {(tile << 10) | tile position, window}
+// -- instead of resolving it; a second launch, one thread per survivor at
+// full occupancy, resolves them (state hash, then the walks) and writes the
+// ids found.  A tile whose survivors do not fit the list, or that holds a
+// window past the text end, is resolved by its warp as in the one-phase form.
+// Entries of list space for a text of n bytes (0: the one-phase form: short
+// texts, and texts of more tiles than the entries can name).
+inline uint32_t survivor_list_entries(const DevTables &t, uint64_t n) {
+    if (!t.hashed || n < (4ull << 20) || n / 992 >= (1ull << 22)) return 0;
+    return static_cast<uint32_t>(n / 8);  // 12.5 % of the positions
+}
 
 
 struct Tuning {

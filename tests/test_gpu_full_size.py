@@ -135,3 +135,29 @@ def test_match_host_every_position():
         p, i = _par.window_compact(wpos, wids, pats, text, 0, small.size)
         got = a.match_host(torch.from_numpy(small.copy()))
         _par.check_dense(got, p, i, "host small")
+
+
+@pytest.mark.parametrize("kind", ["short_keywords", "zipf_sparse"])
+def test_two_phase_byte_form_and_list_overflow(kind):
+    """8-bit codes on texts long enough for the two-phase form: a keyword set
+    whose windows nearly all survive the filter (keywords of 1-3 bytes) fills
+    the survivor list, so most tiles fall back to their warps; a sparse set
+    lists nearly every tile.  Dense ids, count and compacted list, every
+    position, against the oracle."""
+    g = np.random.default_rng(17)
+    text = workloads.zipf_text(6 << 20, 21)
+    if kind == "short_keywords":
+        pats = [bytes(g.integers(0, 64, size=int(g.integers(1, 4)), dtype=np.uint8)) for _ in range(3000)]
+    else:
+        pats = workloads.keywords_zipf(text[:1 << 20], 5000, 4, 60, 0.3, seed=22)
+    wpos, wids = _par.oracle_compact(pats, text)
+    t = _gpu_tensor(text)
+    with api.Automaton(pats) as a:
+        assert a.info()["code_bits"] == 8
+        _all_outputs(a, t, text.size, wpos, wids, kind)
+
+
+def _gpu_tensor(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
