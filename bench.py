@@ -442,6 +442,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         if out_kind != "full" and not args.no_cpu_parallel:
             extra["cpu_all_cores"] = cpu_parallel(text_np, pats, cpu["value"], args.cpu_seconds / 2)
 
+    if rank == 0 and world == 1 and args.workload == "sweep" and out_kind == "dense" and not args.no_extras:
+        # the rest of the metric, after the headline's timed region
+        del text, out
+        torch.cuda.empty_cache()
+        extra.update(extra_figures(args))
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -455,6 +461,76 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         }
         print(json.dumps(line), flush=True)
 
+
+
+def zipf_summary(steps: int, warmup: int) -> dict:
+    """The byte-alphabet workload (1 GiB Zipf(1.1) bytes, 20,000 keywords of
+    length 4-100) with compacted output, timed like the headline line."""
+    import torch
+
+    from paper_1412_7789_gb300 import api
+    from paper_1412_7789_gb300 import workloads as W
+
+    text_np, pats = W.zipf_byte(GIB)
+    n = text_np.size
+    stream = torch.cuda.current_stream()
+    with api.Automaton(pats) as a:
+        text = torch.from_numpy(text_np).cuda()
+        cap = n // 256
+        pos = torch.empty(cap, dtype=torch.int32, device="cuda")
+        ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+        def step():
+            api.ac_match_compact(a.handle, text, n, pos, ids, cap, cnt, stream)
+
+        for _ in range(max(3, warmup)):
+            step()
+        torch.cuda.synchronize()
+        per = _event_ms(stream, step, steps)
+        matches = int(cnt.item())
+        del text, pos, ids
+    ms = statistics.mean(per)
+    peak, peak_kind = load_peaks()
+    achieved = (n + 8 * matches) / (ms * 1e-3) / 1e9
+    return {"workload": "1 GiB Zipf(1.1) bytes, 20,000 keywords length 4-100, compacted (pos,id) output",
+            "value": n / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms, "steps": steps, "matches": matches,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "algorithmic_bytes_per_step": n + 8 * matches},
+            "kernels": "pfac_filter_pipe (hashed filter, survivors listed) + pfac_survivors8 + scan + gather"}
+
+
+def extra_figures(args) -> dict:
+    """The metric's other parts beside the headline: the byte-alphabet
+    workload (compacted), the batch of 4,096 texts and eight automata against
+    one launch per text, and the served workload at one arrival rate against
+    FIFO one-launch-per-request (p50/p99)."""
+    import argparse
+
+    out = {}
+    try:
+        out["zipf"] = zipf_summary(args.extra_steps, args.warmup)
+    except Exception as e:  # reported, not fatal to the headline line
+        out["zipf"] = {"error": repr(e)}
+    ns = argparse.Namespace(**vars(args))
+    ns.steps, ns.warmup, ns.autotune, ns.no_e2e, ns.no_cpu = args.extra_steps, args.warmup, False, True, True
+    try:
+        b = batch_line(ns)
+        keep = ("graph_ms_median", "graph_gbs", "per_text_tiled_ms_median", "per_text_tiled_gbs",
+                "speedup_vs_per_text_tiled", "text_done_ms_p50", "text_done_ms_p99", "per_text_done_ms_p50",
+                "per_text_done_ms_p99", "parity_texts_checked")
+        out["batch"] = {"workload": b["config"]["workload"], "value": b["value"], "unit": "GB/s",
+                        "roofline_frac": b["roofline"]["frac"], **{k: b["batch"][k] for k in keep}}
+    except Exception as e:
+        out["batch"] = {"error": repr(e)}
+    ns.serve_rates, ns.serve_requests, ns.serve_pool = [10000.0], [3000], 256 << 20
+    try:
+        s = serve_line(ns)
+        out["serve"] = {"workload": s["config"]["workload"], **s["serve"][0],
+                        "parity_requests_checked": s["extra"]["parity_requests_checked"]}
+    except Exception as e:
+        out["serve"] = {"error": repr(e)}
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -700,16 +776,39 @@ def _event_ms(stream, fn, reps):
     return per
 
 
+def _completion_ms(stream, launches):
+    """Run launches[i]() in order on `stream`, each followed by an event: the
+    time from the start to each one's completion (ms), and the total."""
+    import torch
+
+    start = torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in launches]
+    start.record(stream)
+    for f, e in zip(launches, evs):
+        f()
+        e.record(stream)
+    evs[-1].synchronize()
+    done = [start.elapsed_time(e) for e in evs]
+    return done, done[-1]
+
+
 def run_batch(args):
+    print(json.dumps(batch_line(args)), flush=True)
+
+
+def batch_line(args) -> dict:
     """Config: 4,096 texts, lengths log-uniform 1 KiB-4 MiB, half ACGT and half
     Zipf(1.1) over 256 bytes, each matched against a uniformly chosen keyword
     set of its own alphabet among eight (1k-50k keywords of length 8-64,
     counts geometric), dense int32 ids per text.  One step = the whole batch.
     Timed: the captured CUDA graph of the batch plan (planning kernel + one
-    persistent launch per automaton on forked streams), the same plan run
+    persistent matching launch for all eight automata), the same plan run
     eagerly, the one-shot ac_match_batch, and the comparison the batch is for:
-    one ac_match launch per text on one stream (no graph), with the tiled
-    kernel and with the one-thread-per-position kernel."""
+    one ac_match launch per text on one stream (no graph), with the default
+    kernel and with the one-thread-per-position kernel; per text, the time
+    from the step's start to its ids being complete (p50/p99): in the batch
+    every text completes with the graph, one launch per text completes them
+    one after another."""
     import torch
 
     from paper_1412_7789_gb300 import api, build
@@ -803,6 +902,8 @@ def run_batch(args):
     per_text_step()
     torch.cuda.synchronize(dev)
     p_ms = _event_ms(stream, per_text_step, max(3, args.steps // 2))
+    done_ms, _ = _completion_ms(stream, [(lambda tv=tv, ov=ov, n=n, w=w: api.ac_match(handles[w], tv, n, ov, stream))
+                                         for tv, ov, n, w in views])
     for a in autos:
         a.set_kernel("simple")
     per_text_step()
@@ -872,9 +973,12 @@ def run_batch(args):
                      "frac": 5 * total / (gm * 1e-3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": 5 * total, "kernel": "batch graph (all launches)"},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": args.steps * (1 + len(autos)),
+        "gpu_launches": args.steps * 2,  # the planning kernel and the one matching launch
         "batch": {
             "graph_ms_median": gm, "graph_gbs": total / (gm * 1e-3) / 1e9,
+            "text_done_ms_p50": gm, "text_done_ms_p99": gm,
+            "per_text_done_ms_p50": float(np.percentile(done_ms, 50)),
+            "per_text_done_ms_p99": float(np.percentile(done_ms, 99)),
             "plan_eager_ms_median": statistics.median(e_ms),
             "match_batch_ms_median": statistics.median(o_ms),
             "per_text_tiled_ms_median": statistics.median(p_ms),
@@ -889,10 +993,10 @@ def run_batch(args):
             "host_build_s": build_s, "generate_s": gen_s,
         },
     }
-    print(json.dumps(line), flush=True)
     plan.close()
     for a in autos:
         a.close()
+    return line
 
 
 # ----------------------------------------------------------------------------
@@ -913,6 +1017,10 @@ def _serve_run(api, handles, reqs, arrivals, fifo, budget):
 
 
 def run_serve(args):
+    print(json.dumps(serve_line(args)), flush=True)
+
+
+def serve_line(args) -> dict:
     """Config: Poisson arrivals at several rates of requests for the compacted
     match of a text of log-uniform length 256 B - 64 MiB (mean 5.4 MB) taken
     from a device-resident pool (1 GiB ACGT, 1 GiB Zipf(1.1) bytes), each
@@ -1010,9 +1118,9 @@ def run_serve(args):
         "extra": {"automata_table_bytes": table_bytes, "request_budget_bytes": budget - table_bytes,
                   "host_build_s": build_s, "generate_s": gen_s, "parity_requests_checked": checked},
     }
-    print(json.dumps(line), flush=True)
     for a in autos:
         a.close()
+    return line
 
 
 def main():
@@ -1027,6 +1135,9 @@ def main():
     ap.add_argument("--out", default=None, choices=["dense", "count", "compact", "full"],
                     help="output kind (default: the workload's)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default run: skip the byte-alphabet, batch and serve figures under extra")
+    ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of each extra figure")
     ap.add_argument("--no-chains", action="store_true", help="compile without chain records")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cpu-parallel", action="store_true", help="skip the all-cores oracle context figure")

@@ -141,32 +141,29 @@ using pfac::scratch_pool;
 // the launchers accept no scratch then, which saves the allocation and the
 // clearing of small calls.
 cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode, cudaStream_t st) {
-    // 8-bit codes, long text: the two-phase form's survivor list after the counter
-    const uint32_t le =
-        !r.batch && pfac::uses_filter(h->dev, h->tuning) ? pfac::survivor_list_entries(h->dev, r.n) : 0u;
-    if (!r.batch && r.n <= (16u << 20) && le == 0) {
+    // 8-bit codes, long text: the phased form's lists after the counter
+    pfac::SurvivorLists sl;
+    if (!r.batch && pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, r.n);
+    const bool le = sl.list_cap != 0;
+    if (!r.batch && r.n <= (16u << 20) && !le) {
         pfac::MatchRequest r0 = r;
         r0.scratch = nullptr;
         r0.scratch_bytes = 0;
         const cudaError_t e0 = pfac::launch_match(h->dev, r0, mode, h->tuning, st);
         if (e0 == cudaSuccess) return e0;  // else: a counter is needed (or a real error, reported below)
     }
-    const size_t bytes = le ? 32 + 8ull * le : 16;
+    const size_t bytes = 16 + sl.bytes();
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);
     if (e != cudaSuccess) return e;
     void *scratch = nullptr;
     e = cudaMallocFromPoolAsync(&scratch, bytes, pool, st);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(scratch, 0, le ? 32 : 16, st);
+    e = cudaMemsetAsync(scratch, 0, le ? 48 : 16, st);
     if (e == cudaSuccess) {
         r.scratch = scratch;
         r.scratch_bytes = 16;
-        if (le) {
-            r.list_count = reinterpret_cast<unsigned int *>(static_cast<uint8_t *>(scratch) + 16);
-            r.list = reinterpret_cast<uint2 *>(static_cast<uint8_t *>(scratch) + 32);
-            r.list_cap = le;
-        }
+        if (le) pfac::set_lists(r, static_cast<uint8_t *>(scratch) + 16, sl);
         e = pfac::launch_match(h->dev, r, mode, h->tuning, st);
     }
     const cudaError_t e2 = cudaFreeAsync(scratch, st);
@@ -178,9 +175,10 @@ cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const 
                         cudaStream_t st) {
     const uint32_t units = pfac::compact_units(h->dev, h->tuning, text, n);
     if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
-    // 8-bit codes, long text: room for the two-phase form's survivor list too
-    const uint32_t le = pfac::uses_filter(h->dev, h->tuning) ? pfac::survivor_list_entries(h->dev, n) : 0u;
-    const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, true) + (le ? 32 + 8ull * le : 0);
+    // 8-bit codes, long text: room for the phased form's lists too
+    pfac::SurvivorLists sl;
+    if (pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, n);
+    const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, true) + sl.bytes();
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);
     if (e != cudaSuccess) return e;

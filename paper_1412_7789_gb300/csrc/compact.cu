@@ -326,17 +326,15 @@ cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t 
     cudaError_t e = cudaMemsetAsync(b, 0, 16 + 4 * size_t(U), stream);
     if (e != cudaSuccess) return e;
     MatchRequest r;
-    // room after the scratch for the two-phase form's survivor list: then its
-    // units keep no dense fallback (the gather matches an overflowing unit
-    // again)
+    // room after the scratch for the phased form's lists: then its units
+    // keep no dense fallback (the gather matches an overflowing unit again)
     const size_t lo = compact_scratch_bytes(t, U, dense);
-    const uint32_t le = uses_filter(t, tu) ? survivor_list_entries(t, n) : 0u;
-    if (le && scratch_bytes >= lo + 32 + 8ull * le) {
-        e = cudaMemsetAsync(b + lo, 0, 16, stream);
+    SurvivorLists sl;
+    if (uses_filter(t, tu)) sl = survivor_lists(t, n);
+    if (sl.list_cap && scratch_bytes >= lo + sl.bytes()) {
+        e = cudaMemsetAsync(b + lo, 0, 32, stream);
         if (e != cudaSuccess) return e;
-        r.list_count = reinterpret_cast<unsigned int *>(b + lo);
-        r.list = reinterpret_cast<uint2 *>(b + lo + 32);
-        r.list_cap = le;
+        set_lists(r, b + lo, sl);
         dn = nullptr;
     }
     r.text = text;

@@ -96,6 +96,8 @@ cudaError_t fill_params(const DevTables &t, const MatchRequest &r, OutMode mode,
         p.list = r.list;
         p.list_count = r.list_count;
         p.list_cap = r.list_cap;
+        p.walks = r.walks;
+        p.walk_cap = r.walks ? r.walk_cap : 0u;
     }
     // the tile counter; none is needed when every tile is some warp's first
     p.counter = r.scratch && r.scratch_bytes >= 16 ? static_cast<unsigned int *>(r.scratch) : nullptr;

@@ -70,6 +70,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // Texts of at most this many tiles per warp of the grid take the forms that
 // share heavy tiles within the CTA.
 constexpr uint32_t kHelpTilesPerWarp = 16;
+// Entries of the phased form's lists a warp reserves at a time.
+constexpr uint32_t kListChunk = 1024;
+constexpr uint32_t kWalkChunk = 256;
+
 // Walks per lane in one round of a tile with many survivors: 8 (rounds of
 // 256); with 8-bit codes, whose tiles hold about a hundred survivors each and
 // whose window lookups hold a 16-byte bucket per walk, 4 (rounds of 128).
@@ -117,11 +121,13 @@ struct FilterParams {
     unsigned long long wait_ns;
     uint32_t stall_help;
     uint32_t kind;  // (B << 8) | goto-entry bits, for the multi-automaton launch
-    // one text, 8-bit codes: the survivor list of the two-phase form (null:
-    // one phase)
+    // one text, 8-bit codes: the lists of the phased form (null: one phase);
+    // list_count[0] survivors, list_count[1] walks
     uint2 *list;
     unsigned int *list_count;
     uint32_t list_cap;
+    uint4 *walks;
+    uint32_t walk_cap;
     // 8-bit codes: the codes are the bytes (256 columns), or classes from the
     // byte table; the filter index is the top bits of (window & wmask) *
     // kFilterHashMul (32 - fshift of them), the state hash's bucket the top
@@ -909,6 +915,10 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     }
 
     Flight f1 = empty_flight(), f2 = empty_flight();  // one and two tiles back
+    // phased form: the part [lnext, lend) of the survivor list this warp
+    // reserved and has not filled yet (lfull: no more room)
+    uint32_t lnext = 0, lend = 0;
+    bool lfull = false;
     bool ok = mbar_wait(jbar, jpar, p.wait_ns);
     // stage s of iteration it is it % nst, its phase parity (it / nst) & 1
     uint32_t it = it0;
@@ -1088,20 +1098,32 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
             // two-phase form: the tile's survivors go to the list (their
             // windows with them) and the tile counts as one without survivors
             // here; a window past the text end, or no room, keeps them here
-            if (p.list && total > 0 && !__any_sync(kFull, (slowm & sv) != 0u)) {
-                uint32_t lbase = 0;
-                if (lane == 0) lbase = atomicAdd(p.list_count, total);
-                lbase = __shfl_sync(kFull, lbase, 0);
-                if (static_cast<uint64_t>(lbase) + total <= p.list_cap) {
+            if (p.list && !lfull && total > 0 && !__any_sync(kFull, (slowm & sv) != 0u)) {
+                if (lend - lnext < total) {
+                    // a new chunk of list space (the rest of the old one: empty)
+                    for (uint32_t j = lnext + static_cast<uint32_t>(lane); j < lend; j += 32u)
+                        p.list[j] = make_uint2(0xFFFFFFFFu, 0u);
+                    const uint32_t want = total > kListChunk ? total : kListChunk;
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(p.list_count, want);
+                    base = __shfl_sync(kFull, base, 0);
+                    lnext = base;
+                    lend = base + want;
+                    if (static_cast<uint64_t>(base) + want > p.list_cap) {
+                        // no room: what was reserved below the capacity is empty
+                        for (uint32_t j = base + static_cast<uint32_t>(lane); j < p.list_cap && j < lend; j += 32u)
+                            p.list[j] = make_uint2(0xFFFFFFFFu, 0u);
+                        lnext = lend = 0;
+                        lfull = true;
+                    }
+                }
+                if (!lfull) {
                     for (uint32_t j = static_cast<uint32_t>(lane); j < total; j += 32u) {
                         const uint32_t i = w.queue[j] & 0x7FFFu;
-                        p.list[lbase + j] = make_uint2((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask);
+                        p.list[lnext + j] = make_uint2((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask);
                     }
+                    lnext += total;
                     total = 0;
-                } else {
-                    // the entries reserved below the capacity: marked empty
-                    for (uint32_t j = static_cast<uint32_t>(lane); j < total && lbase + j < p.list_cap; j += 32u)
-                        p.list[lbase + j] = make_uint2(0xFFFFFFFFu, 0u);
                 }
             }
         }
@@ -1286,6 +1308,10 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     flight_output<MODE>(p, wk, w, f2, lane, cnt);
     flight_finish<B, GT>(p, wk, w.cls8, f1);
     flight_output<MODE>(p, wk, w, f1, lane, cnt);
+    // phased form: the unfilled rest of this warp's list chunk is empty
+    if (B == 8 && p.list)
+        for (uint32_t j = lnext + static_cast<uint32_t>(lane); j < lend; j += 32u)
+            p.list[j] = make_uint2(0xFFFFFFFFu, 0u);
     // the stages issued past this warp's last unit hold end marks (an arrival
     // without a copy): complete their phases, so the next automaton's units
     // start on fresh ones
@@ -1354,15 +1380,15 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
 }
 
 // The second phase of the two-phase form (one text, 8-bit codes): one thread
-// per listed survivor, two at a time so that their loads overlap, at full
-// occupancy (six CTAs of 256 threads per SM).  Each survivor's state-hash
+// per listed survivor, two at a time so that their loads overlap, at high
+// occupancy (five CTAs of 256 threads per SM).  Each survivor's state-hash
 // entry and the code after its window are loaded together; the entry settles
 // most survivors, the others walk on (chain records, goto rows, text from
 // global memory).  Ids found go to the dense output (its -1 are written by
 // the first phase), the count, or the unit's slots (no dense fallback: the
 // gather step matches a unit with more matches than slots again).
 constexpr int kSurvBlock = 256;
-constexpr int kSurvCtas = 6;
+constexpr int kSurvCtas = 5;
 
 template <typename GT, int MODE>
 __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const __grid_constant__ FilterParams p) {
@@ -1376,7 +1402,13 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const _
     const int64_t head = static_cast<int64_t>(reinterpret_cast<uintptr_t>(p.text) & 15u);
     const int64_t n = static_cast<int64_t>(p.n);
     unsigned long long cnt = 0;
-    for (uint32_t b0 = blockIdx.x * blockDim.x + threadIdx.x; b0 < m; b0 += 2u * stride) {
+    // the part [wnext, wend) of the walk list this warp reserved (wfull: no room)
+    uint32_t wnext = 0, wend = 0;
+    bool wfull = p.walk_cap == 0;
+    // all lanes of a warp take part in every round (the walk list is filled
+    // warp-wide): the loop runs on the warp's first index
+    for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < m; wb += 2u * stride) {
+        const uint32_t b0 = wb + static_cast<uint32_t>(lane);
         uint2 e[2];
         uint4 he[2];
         uint32_t c[2];
@@ -1397,14 +1429,40 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const _
         }
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-            if (e[t].x == 0xFFFFFFFFu) continue;
+            const bool on = e[t].x != 0xFFFFFFFFu;
             const uint32_t unit = e[t].x >> 10, i = e[t].x & 1023u;
             const int64_t gpb = static_cast<int64_t>(unit) * kTile - head;
             int r = -1;
             uint32_t s = 0, q = 0;
-            if (!hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c[t] & 0xFFu, c[t] < 0x100u, r, s, q))
-                r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, s, q);
-            if (r < 0) continue;
+            const bool walk = on && !hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c[t] & 0xFFu, c[t] < 0x100u, r, s, q);
+            // walks that go on: to the walk list (warp-wide), else walked here
+            const unsigned wm = __ballot_sync(kFull, walk);
+            bool listed_walk = false;
+            if (wm && !wfull) {
+                const uint32_t need = __popc(wm);
+                if (wend - wnext < need) {
+                    for (uint32_t j = wnext + static_cast<uint32_t>(lane); j < wend; j += 32u)
+                        p.walks[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(p.list_count + 1, kWalkChunk);
+                    base = __shfl_sync(kFull, base, 0);
+                    wnext = base;
+                    wend = base + kWalkChunk;
+                    if (static_cast<uint64_t>(base) + kWalkChunk > p.walk_cap) {
+                        for (uint32_t j = base + static_cast<uint32_t>(lane); j < p.walk_cap && j < wend; j += 32u)
+                            p.walks[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                        wnext = wend = 0;
+                        wfull = true;
+                    }
+                }
+                if (!wfull) {
+                    if (walk) p.walks[wnext + __popc(wm & ((1u << lane) - 1u))] = make_uint4(e[t].x, s, q, 0u);
+                    wnext += need;
+                    listed_walk = true;
+                }
+            }
+            if (walk && !listed_walk) r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, s, q);
+            if (!on || r < 0) continue;
             if (MODE == OUT_DENSE) {
                 p.out[gpb + i] = r;
             } else if (MODE == OUT_COUNT) {
@@ -1417,6 +1475,46 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const _
                         (static_cast<unsigned long long>(static_cast<uint32_t>(r)) << 32) |
                         static_cast<uint32_t>(gpb + i);
             }
+        }
+    }
+    for (uint32_t j = wnext + static_cast<uint32_t>(lane); j < wend; j += 32u)
+        p.walks[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    if (MODE == OUT_COUNT) {
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
+        if (lane == 0 && cnt) atomicAdd(p.count, cnt);
+    }
+}
+
+// The third step of the phased form: one thread per listed walk (state, next
+// byte) at high occupancy; the ids found go out as in the second step.
+template <typename GT, int MODE>
+__global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_walks8(const __grid_constant__ FilterParams p) {
+    __shared__ uint8_t cls8[256];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) cls8[i] = __ldg(p.cls8g + i);
+    __syncthreads();
+    const uint32_t listed = *reinterpret_cast<volatile const unsigned int *>(p.list_count + 1);
+    const uint32_t m = listed < p.walk_cap ? listed : p.walk_cap;
+    const int64_t head = static_cast<int64_t>(reinterpret_cast<uintptr_t>(p.text) & 15u);
+    unsigned long long cnt = 0;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const uint4 e = __ldg(p.walks + j);
+        if (e.x == 0xFFFFFFFFu) continue;
+        const uint32_t unit = e.x >> 10, i = e.x & 1023u;
+        const int64_t gpb = static_cast<int64_t>(unit) * kTile - head;
+        const int r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, e.y, e.z);
+        if (r < 0) continue;
+        if (MODE == OUT_DENSE) {
+            p.out[gpb + i] = r;
+        } else if (MODE == OUT_COUNT) {
+            ++cnt;
+        } else {
+            const uint32_t su = p.sl.ubase + unit;
+            const uint32_t k = atomicAdd(p.sl.counts + su, 1u);
+            if (k < kSlotCap)
+                p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + k] =
+                    (static_cast<unsigned long long>(static_cast<uint32_t>(r)) << 32) | static_cast<uint32_t>(gpb + i);
         }
     }
     if (MODE == OUT_COUNT) {
@@ -1434,6 +1532,13 @@ cudaError_t launch_survivors8(OutMode mode, const FilterParams &p, uint32_t sms,
         case OUT_COUNT: pfac_survivors8<GT, OUT_COUNT><<<grid, kSurvBlock, 0, stream>>>(p); break;
         case OUT_SLOTS: pfac_survivors8<GT, OUT_SLOTS><<<grid, kSurvBlock, 0, stream>>>(p); break;
         default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !p.walks) return e;
+    switch (mode) {
+        case OUT_DENSE: pfac_walks8<GT, OUT_DENSE><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_COUNT: pfac_walks8<GT, OUT_COUNT><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        default: pfac_walks8<GT, OUT_SLOTS><<<grid, kSurvBlock, 0, stream>>>(p); break;
     }
     return cudaGetLastError();
 }

@@ -222,26 +222,50 @@ struct MatchRequest {
     SlotOut slots;                           // OUT_SLOTS
     void *scratch = nullptr;                 // zeroed: tile counter (16 bytes)
     size_t scratch_bytes = 0;
-    // One text, 8-bit codes (hashed filter): the survivor list of the
-    // two-phase form (see survivor_list_entries); nullptr = every tile's
-    // survivors are resolved by the warp that filtered it.
+    // One text, 8-bit codes (hashed filter): the lists of the phased form
+    // (survivor_lists); list = nullptr: every tile's survivors are resolved
+    // by the warp that filtered it.
     uint2 *list = nullptr;
-    unsigned int *list_count = nullptr;      // zeroed
+    unsigned int *list_count = nullptr;      // zeroed, two words: survivors, walks
     uint32_t list_cap = 0;
+    uint4 *walks = nullptr;
+    uint32_t walk_cap = 0;
 };
 
-// The two-phase form of the filter kernel for one text with 8-bit codes: the
-// first launch stages, filters and writes the -1 of every tile, and appends
-// each survivor's window to a list -- {(tile << 10) | tile position, window}
-// -- instead of resolving it; a second launch, one thread per survivor at
-// full occupancy, resolves them (state hash, then the walks) and writes the
-// ids found.  A tile whose survivors do not fit the list, or that holds a
-// window past the text end, is resolved by its warp as in the one-phase form.
-// Entries of list space for a text of n bytes (0: the one-phase form: short
-// texts, and texts of more tiles than the entries can name).
-inline uint32_t survivor_list_entries(const DevTables &t, uint64_t n) {
-    if (!t.hashed || n < (4ull << 20) || n / 992 >= (1ull << 22)) return 0;
-    return static_cast<uint32_t>(n / 8);  // 12.5 % of the positions
+// The phased form of the filter kernel for one text with 8-bit codes:
+//   1. the filter kernel stages, filters and writes the -1 of every tile, and
+//      appends each survivor to a list -- {(tile << 10) | tile position,
+//      window} -- instead of resolving it;
+//   2. one thread per survivor at full occupancy loads its state-hash entry,
+//      settles most survivors and writes the ids found; a survivor whose walk
+//      goes on is appended to a second list -- {(tile << 10) | position,
+//      state, tile index of the walk's next byte, 0};
+//   3. one thread per walk, at full occupancy, finishes the walks.
+// Warps reserve list space in chunks (entries they leave unused are marked
+// empty: x = 0xFFFFFFFF).  A tile whose survivors do not fit, or that holds a
+// window past the text end, is resolved by its warp as in the one-phase form,
+// and a walk that does not fit by its thread in step 2.
+struct SurvivorLists {
+    uint32_t list_cap = 0, walk_cap = 0;
+    size_t bytes() const { return list_cap ? 32 + 8ull * list_cap + 16ull * walk_cap : 0; }
+};
+// The lists of a text of n bytes (none: the one-phase form, for short texts
+// and for texts of more tiles than the entries can name).  Scratch layout:
+// two counters (32 bytes, zeroed) | list_cap uint2 | walk_cap uint4.
+inline SurvivorLists survivor_lists(const DevTables &t, uint64_t n) {
+    SurvivorLists s;
+    if (!t.hashed || n < (4ull << 20) || n / 992 >= (1ull << 22)) return s;
+    s.list_cap = static_cast<uint32_t>(n / 8);   // 12.5 % of the positions
+    s.walk_cap = static_cast<uint32_t>(n / 32);  // 3.1 %
+    return s;
+}
+inline void set_lists(MatchRequest &r, void *scratch, const SurvivorLists &s) {
+    uint8_t *b = static_cast<uint8_t *>(scratch);
+    r.list_count = reinterpret_cast<unsigned int *>(b);
+    r.list = reinterpret_cast<uint2 *>(b + 32);
+    r.list_cap = s.list_cap;
+    r.walks = reinterpret_cast<uint4 *>(b + 32 + 8ull * s.list_cap);
+    r.walk_cap = s.walk_cap;
 }
 
 
