@@ -181,10 +181,9 @@ __device__ __forceinline__ void gather_unit(const GatherParams &p, const Work &w
             static_cast<uint32_t>(lane) < c ? __ldg(p.g.slots + su * kSlotCap + lane) : ~0ull;
         const uint32_t mine = static_cast<uint32_t>(e);
         uint32_t rank = 0;
-#pragma unroll 8
-        for (int d = 0; d < 32; ++d) {
-            const uint32_t other = __shfl_sync(0xffffffffu, mine, d);
-            rank += (static_cast<uint32_t>(d) < c && other < mine) ? 1u : 0u;
+        for (uint32_t d = 0; d < c; ++d) {  // c is the same for the whole warp
+            const uint32_t other = __shfl_sync(0xffffffffu, mine, static_cast<int>(d));
+            rank += other < mine ? 1u : 0u;
         }
         if (static_cast<uint32_t>(lane) < c && o + rank < out.cap) {
             out.pos[o + rank] = mine;

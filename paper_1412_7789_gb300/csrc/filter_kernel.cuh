@@ -123,7 +123,7 @@ struct FilterParams {
     uint32_t kind;  // (B << 8) | goto-entry bits, for the multi-automaton launch
     // one text, 8-bit codes: the lists of the phased form (null: one phase);
     // list_count[0] survivors, list_count[1] walks
-    uint2 *list;
+    uint4 *list;
     unsigned int *list_count;
     uint32_t list_cap;
     uint4 *walks;
@@ -1102,7 +1102,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                 if (lend - lnext < total) {
                     // a new chunk of list space (the rest of the old one: empty)
                     for (uint32_t j = lnext + static_cast<uint32_t>(lane); j < lend; j += 32u)
-                        p.list[j] = make_uint2(0xFFFFFFFFu, 0u);
+                        p.list[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
                     const uint32_t want = total > kListChunk ? total : kListChunk;
                     uint32_t base = 0;
                     if (lane == 0) base = atomicAdd(p.list_count, want);
@@ -1112,7 +1112,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                     if (static_cast<uint64_t>(base) + want > p.list_cap) {
                         // no room: what was reserved below the capacity is empty
                         for (uint32_t j = base + static_cast<uint32_t>(lane); j < p.list_cap && j < lend; j += 32u)
-                            p.list[j] = make_uint2(0xFFFFFFFFu, 0u);
+                            p.list[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
                         lnext = lend = 0;
                         lfull = true;
                     }
@@ -1120,7 +1120,13 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                 if (!lfull) {
                     for (uint32_t j = static_cast<uint32_t>(lane); j < total; j += 32u) {
                         const uint32_t i = w.queue[j] & 0x7FFFu;
-                        p.list[lnext + j] = make_uint2((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask);
+                        // the code after the window (0x100: the text ends, or a
+                        // byte in no keyword); i + k < kCodeSpan
+                        const uint32_t ja = i + k;
+                        const uint32_t ca = ((w.inv[ja >> 4] >> (ja & 15u)) & 1u)
+                                                ? 0x100u
+                                                : (w.packed[ja >> 2] >> (8u * (ja & 3u))) & 0xFFu;
+                        p.list[lnext + j] = make_uint4((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask, ca, 0u);
                     }
                     lnext += total;
                     total = 0;
@@ -1311,7 +1317,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     // phased form: the unfilled rest of this warp's list chunk is empty
     if (B == 8 && p.list)
         for (uint32_t j = lnext + static_cast<uint32_t>(lane); j < lend; j += 32u)
-            p.list[j] = make_uint2(0xFFFFFFFFu, 0u);
+            p.list[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     // the stages issued past this warp's last unit hold end marks (an arrival
     // without a copy): complete their phases, so the next automaton's units
     // start on fresh ones
@@ -1409,23 +1415,16 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const _
     // warp-wide): the loop runs on the warp's first index
     for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < m; wb += 2u * stride) {
         const uint32_t b0 = wb + static_cast<uint32_t>(lane);
-        uint2 e[2];
+        uint4 e[2];
         uint4 he[2];
         uint32_t c[2];
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
             const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
-            e[t] = idx < m ? __ldg(p.list + idx) : make_uint2(0xFFFFFFFFu, 0u);
+            e[t] = idx < m ? __ldg(p.list + idx) : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
             he[t] = make_uint4(0u, 0u, 0u, 0u);
-            c[t] = 0x100u;  // no character after the window (or one in no keyword)
-            if (e[t].x != 0xFFFFFFFFu) {
-                he[t] = __ldg(p.HK + hk_slot(p, e[t].y));
-                const int64_t j = static_cast<int64_t>(e[t].x >> 10) * kTile - head + (e[t].x & 1023u) + p.k;
-                if (j < n) {
-                    const uint32_t bt = __ldg(p.text + j);
-                    c[t] = p.identity ? bt : (cls8[bt] == 0xFFu ? 0x100u : cls8[bt]);
-                }
-            }
+            c[t] = e[t].z;  // the code after the window (0x100: none, or a byte in no keyword)
+            if (e[t].x != 0xFFFFFFFFu) he[t] = __ldg(p.HK + hk_slot(p, e[t].y));
         }
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
@@ -1435,6 +1434,7 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const _
             int r = -1;
             uint32_t s = 0, q = 0;
             const bool walk = on && !hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c[t] & 0xFFu, c[t] < 0x100u, r, s, q);
+            if (walk) r = -1;  // its id comes from the walk (here, or in the third step)
             // walks that go on: to the walk list (warp-wide), else walked here
             const unsigned wm = __ballot_sync(kFull, walk);
             bool listed_walk = false;

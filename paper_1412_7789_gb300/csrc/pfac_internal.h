@@ -225,7 +225,7 @@ struct MatchRequest {
     // One text, 8-bit codes (hashed filter): the lists of the phased form
     // (survivor_lists); list = nullptr: every tile's survivors are resolved
     // by the warp that filtered it.
-    uint2 *list = nullptr;
+    uint4 *list = nullptr;
     unsigned int *list_count = nullptr;      // zeroed, two words: survivors, walks
     uint32_t list_cap = 0;
     uint4 *walks = nullptr;
@@ -235,7 +235,8 @@ struct MatchRequest {
 // The phased form of the filter kernel for one text with 8-bit codes:
 //   1. the filter kernel stages, filters and writes the -1 of every tile, and
 //      appends each survivor to a list -- {(tile << 10) | tile position,
-//      window} -- instead of resolving it;
+//      window, code of the character after it (0x100: none), 0} -- instead of
+//      resolving it;
 //   2. one thread per survivor at full occupancy loads its state-hash entry,
 //      settles most survivors and writes the ids found; a survivor whose walk
 //      goes on is appended to a second list -- {(tile << 10) | position,
@@ -247,11 +248,11 @@ struct MatchRequest {
 // and a walk that does not fit by its thread in step 2.
 struct SurvivorLists {
     uint32_t list_cap = 0, walk_cap = 0;
-    size_t bytes() const { return list_cap ? 32 + 8ull * list_cap + 16ull * walk_cap : 0; }
+    size_t bytes() const { return list_cap ? 32 + 16ull * list_cap + 16ull * walk_cap : 0; }
 };
 // The lists of a text of n bytes (none: the one-phase form, for short texts
 // and for texts of more tiles than the entries can name).  Scratch layout:
-// two counters (32 bytes, zeroed) | list_cap uint2 | walk_cap uint4.
+// two counters (32 bytes, zeroed) | list_cap uint4 | walk_cap uint4.
 inline SurvivorLists survivor_lists(const DevTables &t, uint64_t n) {
     SurvivorLists s;
     if (!t.hashed || n < (4ull << 20) || n / 992 >= (1ull << 22)) return s;
@@ -262,9 +263,9 @@ inline SurvivorLists survivor_lists(const DevTables &t, uint64_t n) {
 inline void set_lists(MatchRequest &r, void *scratch, const SurvivorLists &s) {
     uint8_t *b = static_cast<uint8_t *>(scratch);
     r.list_count = reinterpret_cast<unsigned int *>(b);
-    r.list = reinterpret_cast<uint2 *>(b + 32);
+    r.list = reinterpret_cast<uint4 *>(b + 32);
     r.list_cap = s.list_cap;
-    r.walks = reinterpret_cast<uint4 *>(b + 32 + 8ull * s.list_cap);
+    r.walks = reinterpret_cast<uint4 *>(b + 32 + 16ull * s.list_cap);
     r.walk_cap = s.walk_cap;
 }
 
