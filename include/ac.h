@@ -306,6 +306,53 @@ ac_status ac_match_host(ac_handle h, const uint8_t *h_text, uint64_t n, int32_t 
 ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
 
 /*
+ * Launch shape of the root filter kernel (AC_KERNEL_TILED; no counterpart in
+ * the paper).  Results never depend on it, only the time does.
+ *   block         threads per CTA: a multiple of 32, 32 .. 512 (default 512).
+ *   stages        text tiles in flight per warp: 2 .. 4, 0 = 3 (fewer when
+ *                 shared memory is short).
+ *   halo          bytes bulk-copied after each tile of 992 text bytes: 0 or
+ *                 16 = the look-ahead the filter's windows read (default), up
+ *                 to 256 (capped at the longest keyword); the extra bytes are
+ *                 not read from shared memory but reach L2 ahead of the walks
+ *                 that run past the tile.
+ *   per_thread    chars per thread of the one-thread-per-survivor step that
+ *                 texts of 4 MiB or more with 8-bit codes take after the
+ *                 filter: 2 (default; 0 means 2) or 4 survivors a thread at a
+ *                 time, at 48 or 32 warps per SM.
+ *   filter_bytes  shared-table depth: bytes of the root filter held in shared
+ *                 memory per CTA.  ac_get_tuning reports the current size.
+ *                 ac_set_tuning with a non-zero value rebuilds the root tables
+ *                 for the largest filter within it, from the goto table alone:
+ *                 2- and 4-bit codes, windows of k codes with 2^(B k) / 8
+ *                 <= filter_bytes (and the window and stride tables for that
+ *                 k); 8-bit codes, a hashed filter of 2^fbits bits, fbits
+ *                 >= 5 and 2^fbits / 8 <= filter_bytes; at most 128 KiB
+ *                 either way (filter_bytes below 16, or below 4 for 8-bit
+ *                 codes, fits none).  0
+ *                 keeps the tables.  Tables replaced stay allocated until
+ *                 ac_destroy, so launches captured before still read valid
+ *                 tables.  AC_ERR_INVALID_ARG for an automaton without a
+ *                 root filter, or a size below the smallest filter.
+ *   reserved      0.
+ * ac_set_tuning validates every field before changing any; do not call it
+ * while work on h is being enqueued from another thread.  Batch plans and
+ * servers read the tuning of their handles at each launch (a captured batch
+ * graph keeps the shape it was captured with).
+ */
+typedef struct {
+    uint32_t block;
+    uint32_t stages;
+    uint32_t halo;
+    uint32_t per_thread;
+    uint32_t filter_bytes;
+    uint32_t reserved;
+} ac_tuning;
+
+ac_status ac_get_tuning(ac_handle h, ac_tuning *out);
+ac_status ac_set_tuning(ac_handle h, const ac_tuning *t);
+
+/*
  * Bounded waits (no counterpart in the paper).  Every wait inside this
  * handle's kernels -- a bulk copy landing on its mbarrier, an owner warp
  * waiting for the warps of its CTA to finish the rounds of a heavy tile it
@@ -432,17 +479,24 @@ ac_status ac_batch_destroy(ac_batch b);
 
 /*
  * Autotuning (no counterpart in the paper): time the dense matching of handle
- * h on the device text d_sample (n bytes, at least 1 MiB is sensible) with
- * each candidate -- for up to 16 keyword bytes, threads per CTA {256, 384,
- * 512} x text stages per warp {2, 3, 4}, the shapes that fit shared memory;
- * for more, the kernels AC_KERNEL_THREAD_JUMP_L1, AC_KERNEL_THREAD_JUMP and
- * AC_KERNEL_WALK_SLOTS (the last with each shape) -- and keep the fastest for
- * every later call on h (single texts, batches and servers created after).
- * Each candidate runs `reps` times (0 = 5) after one warm-up; the median is
- * compared.  Writes the choice to *block, *stages and *kernel (an ac_kernel)
- * when they are not NULL.  Synchronises `stream`; takes 4 * n bytes of
- * scratch from the library pool.  Do not match on h from another thread
- * meanwhile.  Results never depend on the choice, only the time does.
+ * h on the device text d_sample (n bytes, at least 1 MiB is sensible; 4 MiB or
+ * more for the one-thread-per-survivor step of 8-bit codes) with each
+ * candidate and keep the fastest for every later call on h (single texts,
+ * batches and servers).  The candidates, for an automaton with a root filter
+ * (ac_tuning): the shared-table depth -- the filter as built and two smaller
+ * ones (windows of one and two codes fewer, or a hashed filter of a quarter
+ * and a sixteenth of the bits) -- x threads per CTA {256, 384, 512} x text
+ * stages {2, 3, 4} (the shapes that fit shared memory); then, at the best of
+ * those, the halo (16 bytes or the longest keyword, up to 256) and, for 8-bit
+ * codes, chars per thread {2, 4}; with 8-bit codes also the kernels
+ * AC_KERNEL_THREAD_JUMP_L1, AC_KERNEL_THREAD_JUMP and AC_KERNEL_WALK_SLOTS (the
+ * last with each shape).  Each candidate runs `reps` times (0 = 5) after one
+ * warm-up; the median is compared.  Writes the choice to *block, *stages and
+ * *kernel (an ac_kernel) when they are not NULL; ac_get_tuning reports the
+ * rest.  The root tables of depths not chosen are freed.  Synchronises
+ * `stream`; takes 4 * n bytes of scratch from the library pool.  Do not match
+ * on h from another thread meanwhile.  Results never depend on the choice,
+ * only the time does.
  */
 ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t reps, void *stream,
                       uint32_t *block, uint32_t *stages, uint32_t *kernel);

@@ -81,6 +81,11 @@ class ac_info_t(ctypes.Structure):
     ]
 
 
+class ac_tuning(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint32) for name in ("block", "stages", "halo", "per_thread", "filter_bytes",
+                                                     "reserved")]
+
+
 _lock = threading.Lock()
 _LIB: ctypes.CDLL | None = None
 
@@ -110,6 +115,8 @@ _SIGS = {
     "ac_match_compact_static": (ctypes.c_int, [_H, _P, _U64, _P, _P, _U64, _P, _P]),
     "ac_set_kernel": (ctypes.c_int, [_H, ctypes.c_int]),
     "ac_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_uint64, ctypes.c_int32]),
+    "ac_get_tuning": (ctypes.c_int, [_H, ctypes.POINTER(ac_tuning)]),
+    "ac_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(ac_tuning)]),
     "ac_export_chains": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_uint32), _P, _P, ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "ac_match_batch": (ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, ctypes.c_uint32, _P, _P]),
@@ -394,6 +401,26 @@ def ac_match_batch(hs, texts, items, nitems: int, out, stream=None):
                                 _dev_ptr(out, 4), _stream_ptr(stream)), "ac_match_batch")
 
 
+def ac_get_tuning(h: int) -> dict:
+    """The filter kernel's launch shape for h (ac_tuning fields but reserved)."""
+    t = ac_tuning()
+    _check(lib().ac_get_tuning(h, ctypes.byref(t)), "ac_get_tuning")
+    return {name: int(getattr(t, name)) for name, _ in ac_tuning._fields_ if name != "reserved"}
+
+
+def ac_set_tuning(h: int, **fields) -> None:
+    """Change fields of h's tuning (the others keep their values; filter_bytes
+    defaults to 0, keep the root tables)."""
+    cur = ac_get_tuning(h)
+    cur["filter_bytes"] = 0
+    unknown = set(fields) - set(cur)
+    if unknown:
+        raise TypeError("unknown tuning fields: %s" % sorted(unknown))
+    cur.update(fields)
+    t = ac_tuning(**cur)
+    _check(lib().ac_set_tuning(h, ctypes.byref(t)), "ac_set_tuning")
+
+
 def ac_autotune(h: int, sample, n: int | None = None, reps: int = 0, stream=None) -> tuple[int, int, str]:
     """Pick the fastest kernel and launch shape for h on a device sample;
     returns (block, stages, kernel name)."""
@@ -533,6 +560,12 @@ class Automaton:
 
     def autotune(self, sample, reps: int = 0, stream=None) -> tuple[int, int, str]:
         return ac_autotune(self.handle, sample, reps=reps, stream=stream)
+
+    def tuning(self) -> dict:
+        return ac_get_tuning(self.handle)
+
+    def set_tuning(self, **fields):
+        ac_set_tuning(self.handle, **fields)
 
     def match_host(self, text, out=None, stream=None):
         """text: CPU uint8 tensor (pinned for overlap); returns a CPU int32 tensor."""

@@ -23,6 +23,19 @@ struct ac_automaton {
     void (*dev_free)(void *, void *) = nullptr;
     void *alloc_ctx = nullptr;
     std::vector<void *> owned;  // device allocations of the tables
+    uint64_t stride_bytes = 0;  // the build's stride-table budget
+    // Root filter tables by shared-table depth (key: the window k, or the
+    // hashed filter's bits), once a depth other than the built one is asked
+    // for: the built tables first.  Replaced tables stay allocated (launches
+    // captured before may read them) until ac_destroy, or until the autotuner
+    // drops the depths it did not choose.
+    struct RootSet {
+        uint32_t key = 0;
+        pfac::RootTables t;
+        const uint32_t *F = nullptr;
+        const int32_t *JK = nullptr, *J2 = nullptr;
+    };
+    std::vector<RootSet> roots;
 
     // staging for ac_match_host (allocated on first use)
     std::mutex host_mu;
@@ -71,6 +84,115 @@ ac_status upload(ac_automaton *h, const void *src, size_t bytes, const void **ds
     if (bytes && cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return AC_ERR_CUDA;
     *dst = p;
     return AC_OK;
+}
+
+void release_owned(ac_automaton *h, const void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < h->owned.size(); ++i)
+        if (h->owned[i] == p) {
+            dev_release(h, h->owned[i]);
+            h->owned.erase(h->owned.begin() + static_cast<std::ptrdiff_t>(i));
+            return;
+        }
+}
+
+// ---- shared-table depth: the root filter tables rebuilt at another size ----
+
+bool has_root(const pfac::HostTables &t) { return t.filter || t.hashed; }
+uint32_t root_key(const pfac::HostTables &t) { return t.filter ? t.k : t.fbits; }
+
+// The depth of the largest root filter within `bytes` (0: none fits).
+uint32_t root_key_for(const pfac::HostTables &t, uint32_t bytes) {
+    if (t.filter) return bytes >= 16 ? pfac::filter_window(t.B, t.maxlen, bytes) : 0u;
+    uint32_t fb = 0;
+    while (fb < pfac::kFilterBits && (2ull << fb) <= 8ull * bytes) ++fb;
+    return fb >= 5 ? fb : 0u;
+}
+
+// Make depth `key` the handle's (host and device tables), building and
+// uploading its tables the first time.
+ac_status use_root(ac_automaton *h, uint32_t key) {
+    pfac::HostTables &t = h->host;
+    pfac::DevTables &d = h->dev;
+    if (!has_root(t)) return AC_ERR_INVALID_ARG;
+    if (key == root_key(t)) return AC_OK;
+    if (h->roots.empty()) {  // the built tables, as they are
+        ac_automaton::RootSet b;
+        b.key = root_key(t);
+        b.t.k = t.k;
+        b.t.k2 = t.k2;
+        b.t.base_k = t.base_k;
+        b.t.count_k = t.count_k;
+        b.t.fbits = t.fbits;
+        b.t.F = t.F;
+        if (t.filter) {
+            b.t.JK = t.JK;
+            b.t.J2 = t.J2;
+        }
+        b.F = d.F;
+        b.JK = d.JK;
+        b.J2 = d.J2;
+        h->roots.push_back(std::move(b));
+    }
+    size_t at = h->roots.size();
+    for (size_t i = 0; i < h->roots.size(); ++i)
+        if (h->roots[i].key == key) at = i;
+    if (at == h->roots.size()) {
+        ac_automaton::RootSet rs;
+        rs.key = key;
+        try {
+            if (t.filter)
+                pfac::window_tables(t, key, h->stride_bytes, &rs.t);
+            else
+                pfac::hashed_filter(t, key, &rs.t);
+        } catch (const std::bad_alloc &) {
+            return AC_ERR_OOM;
+        }
+        if (!h->host_only) {
+            ac_status s = upload(h, rs.t.F.data(), rs.t.F.size() * sizeof(uint32_t),
+                                 reinterpret_cast<const void **>(&rs.F));
+            if (s == AC_OK && t.filter)
+                s = upload(h, rs.t.JK.data(), rs.t.JK.size() * sizeof(int32_t), reinterpret_cast<const void **>(&rs.JK));
+            if (s == AC_OK && t.filter && !rs.t.J2.empty())
+                s = upload(h, rs.t.J2.data(), rs.t.J2.size() * sizeof(int32_t), reinterpret_cast<const void **>(&rs.J2));
+            if (s != AC_OK) {
+                release_owned(h, rs.F);
+                release_owned(h, rs.JK);
+                release_owned(h, rs.J2);
+                return s;
+            }
+        }
+        h->roots.push_back(std::move(rs));
+    }
+    const ac_automaton::RootSet &rs = h->roots[at];
+    t.F = rs.t.F;
+    d.F = rs.F;
+    d.fbytes = static_cast<uint32_t>(rs.t.F.size() * sizeof(uint32_t));
+    if (t.filter) {
+        t.k = d.k = rs.t.k;
+        t.k2 = d.k2 = rs.t.k2;
+        t.base_k = d.base_k = rs.t.base_k;
+        t.count_k = rs.t.count_k;
+        t.JK = rs.t.JK;
+        t.J2 = rs.t.J2;
+        d.JK = rs.JK;
+        d.J2 = rs.J2;
+    } else {
+        t.fbits = d.fbits = rs.t.fbits;
+    }
+    return AC_OK;
+}
+
+// Free the root tables of every depth but the built one and the current one.
+void drop_roots(ac_automaton *h) {
+    const uint32_t cur = root_key(h->host);
+    for (size_t i = h->roots.size(); i-- > 1;) {
+        if (h->roots[i].key == cur) continue;
+        release_owned(h, h->roots[i].F);
+        release_owned(h, h->roots[i].JK);
+        release_owned(h, h->roots[i].J2);
+        h->roots.erase(h->roots.begin() + static_cast<std::ptrdiff_t>(i));
+    }
 }
 
 void release_host_path(ac_automaton *h) {
@@ -319,6 +441,7 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     if (o.jump_bytes) bo.jump_bytes = o.jump_bytes;
     if (o.stride_bytes) bo.stride_bytes = o.stride_bytes;
     bo.chains = o.no_chains == 0;
+    h->stride_bytes = bo.stride_bytes;
     int st = pfac::build_tables(patterns, lens, k, bo, &h->host);
     if (st != AC_OK) {
         delete h;
@@ -531,6 +654,37 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel) {
             return AC_ERR_INVALID_ARG;
     }
     h->kernel = kernel == AC_KERNEL_SIMPLE ? AC_KERNEL_SIMPLE : AC_KERNEL_TILED;
+    return AC_OK;
+}
+
+ac_status ac_get_tuning(ac_handle h, ac_tuning *out) {
+    if (!h || !out) return AC_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->block = static_cast<uint32_t>(h->tuning.block);
+    out->stages = static_cast<uint32_t>(h->tuning.stages);
+    out->halo = h->tuning.halo > 16 ? static_cast<uint32_t>(h->tuning.halo) : 16u;
+    out->per_thread = h->tuning.per_thread == 4 ? 4u : 2u;
+    out->filter_bytes = has_root(h->host) ? static_cast<uint32_t>(h->host.F.size() * sizeof(uint32_t)) : 0u;
+    return AC_OK;
+}
+
+ac_status ac_set_tuning(ac_handle h, const ac_tuning *tu) {
+    if (!h || !tu) return AC_ERR_INVALID_ARG;
+    if (tu->block < 32 || tu->block > 512 || (tu->block & 31u) || (tu->stages != 0 && (tu->stages < 2 || tu->stages > 4)) ||
+        tu->halo > pfac::kHaloCap || (tu->per_thread != 0 && tu->per_thread != 2 && tu->per_thread != 4) ||
+        tu->reserved != 0)
+        return AC_ERR_INVALID_ARG;
+    if (tu->filter_bytes != 0) {
+        if (!has_root(h->host)) return AC_ERR_INVALID_ARG;
+        const uint32_t key = root_key_for(h->host, tu->filter_bytes);
+        if (key == 0) return AC_ERR_INVALID_ARG;
+        const ac_status s = use_root(h, key);
+        if (s != AC_OK) return s;
+    }
+    h->tuning.block = static_cast<int>(tu->block);
+    h->tuning.stages = static_cast<int>(tu->stages);
+    h->tuning.halo = static_cast<int>(tu->halo);
+    h->tuning.per_thread = static_cast<int>(tu->per_thread);
     return AC_OK;
 }
 
@@ -796,50 +950,30 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
     const pfac::Tuning keep = h->tuning;
     const ac_kernel keep_kernel = h->kernel;
+    const bool root = has_root(h->host);
+    const uint32_t keep_key = root ? root_key(h->host) : 0u;
     h->kernel = AC_KERNEL_TILED;
     pfac::Tuning best = keep;
+    uint32_t best_key = keep_key;
     float best_ms = -1.0f;
     pfac::MatchRequest r;
     r.text = d_sample;
     r.n = n;
     r.out = static_cast<int32_t *>(out);
-    // candidates: threads per CTA x stages for the filter kernel and the warp
-    // walk; the two one-thread-per-position kernels with one shape each
-    std::vector<pfac::Tuning> cands;
-    static const int kBlocks[3] = {256, 384, 512};
-    // small alphabets: the filter kernel only; 8-bit codes: the filter kernel
-    // with the hashed filter (when built) and the three 8-bit kernels
-    std::vector<int> variants{0};
-    if (!h->dev.filter) variants = h->dev.hashed ? std::vector<int>{0, 3, 2, 1} : std::vector<int>{3, 2, 1};
-    for (int v : variants) {
-        if (v == 2 || v == 3) {
-            pfac::Tuning tu = keep;
-            tu.variant = v;
-            tu.grid = 0;
-            cands.push_back(tu);
-            continue;
-        }
-        for (int bi = 0; bi < 3; ++bi)
-            for (int sg = 2; sg <= 4; ++sg) {
-                pfac::Tuning tu = keep;
-                tu.variant = v;
-                tu.block = kBlocks[bi];
-                tu.stages = sg;
-                tu.grid = 0;
-                cands.push_back(tu);
-            }
-    }
-    for (const pfac::Tuning &tu : cands) {
-        if (e != cudaSuccess) break;
+    ac_status fail = AC_OK;
+    // time one candidate (at the current depth); one that does not fit shared
+    // memory is skipped
+    auto time_one = [&](const pfac::Tuning &tu) {
+        if (e != cudaSuccess) return;
         h->tuning = tu;
         cudaError_t le = run_tiled(h, r, pfac::OUT_DENSE, st);  // warm-up
-        if (le == cudaErrorInvalidConfiguration) {              // does not fit shared memory
+        if (le == cudaErrorInvalidConfiguration) {
             cudaGetLastError();
-            continue;
+            return;
         }
         if (le != cudaSuccess) {
             e = le;
-            break;
+            return;
         }
         std::vector<float> ms;
         for (uint32_t i = 0; i < reps && e == cudaSuccess; ++i) {
@@ -851,15 +985,75 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
             if (e == cudaSuccess) e = cudaEventElapsedTime(&v, t0, t1);
             ms.push_back(v);
         }
-        if (e != cudaSuccess) break;
+        if (e != cudaSuccess) return;
         std::sort(ms.begin(), ms.end());
         const float med = ms[ms.size() / 2];
         if (best_ms < 0.0f || med < best_ms) {
             best_ms = med;
             best = tu;
+            best_key = root && tu.variant == 0 ? root_key(h->host) : keep_key;
+        }
+    };
+    // shared-table depths: as built (or set), and two smaller
+    std::vector<uint32_t> depths{keep_key};
+    if (root) {
+        const uint32_t step = h->host.filter ? 1u : 2u, lo = h->host.filter ? 1u : 5u;
+        for (uint32_t i = 1; i <= 2; ++i)
+            if (keep_key >= lo + i * step) depths.push_back(keep_key - i * step);
+    }
+    static const int kBlocks[3] = {256, 384, 512};
+    // small alphabets: the filter kernel only; 8-bit codes: the filter kernel
+    // with the hashed filter (when built) and the three 8-bit kernels
+    std::vector<int> variants{0};
+    if (!h->dev.filter) variants = h->dev.hashed ? std::vector<int>{0, 3, 2, 1} : std::vector<int>{3, 2, 1};
+    for (int v : variants) {
+        pfac::Tuning tu = keep;
+        tu.variant = v;
+        tu.grid = 0;
+        tu.halo = 0;
+        tu.per_thread = 0;
+        if (v == 2 || v == 3) {
+            time_one(tu);
+            continue;
+        }
+        const bool filtered = v == 0 && root;
+        for (size_t di = 0; di < (filtered ? depths.size() : 1u) && e == cudaSuccess && fail == AC_OK; ++di) {
+            if (filtered) fail = use_root(h, depths[di]);
+            for (int bi = 0; bi < 3 && fail == AC_OK; ++bi)
+                for (int sg = 2; sg <= 4; ++sg) {
+                    tu.block = kBlocks[bi];
+                    tu.stages = sg;
+                    time_one(tu);
+                }
         }
     }
-    h->tuning = e == cudaSuccess ? best : keep;
+    // at the best shape: the halo, and chars per thread of the survivor step
+    if (e == cudaSuccess && fail == AC_OK && best.variant == 0 && root) {
+        fail = use_root(h, best_key);
+        const pfac::Tuning base = best;
+        const int hmax = static_cast<int>(std::min<uint32_t>(pfac::kHaloCap, (h->host.maxlen + 15u) & ~15u));
+        std::vector<int> halos{0};
+        if (hmax > 16) halos.push_back(hmax);
+        std::vector<int> pts{0};
+        if (h->host.hashed && n >= (4u << 20)) pts.push_back(4);
+        for (int hv : halos)
+            for (int pt : pts) {
+                if (hv == 0 && pt == 0) continue;  // timed above
+                if (fail != AC_OK) break;
+                pfac::Tuning tu = base;
+                tu.halo = hv;
+                tu.per_thread = pt;
+                time_one(tu);
+            }
+    }
+    if (e == cudaSuccess && fail == AC_OK) {
+        if (root) fail = use_root(h, best_key);
+        h->tuning = best;
+    } else {
+        if (root) use_root(h, keep_key);
+        h->tuning = keep;
+    }
+    if (root) drop_roots(h);
     h->kernel = keep_kernel == AC_KERNEL_SIMPLE ? AC_KERNEL_TILED : keep_kernel;
     if (t0) cudaEventDestroy(t0);
     if (t1) cudaEventDestroy(t1);
@@ -867,6 +1061,7 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
     const cudaError_t e3 = cudaStreamSynchronize(st);
     if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
     if (e != cudaSuccess) return cuda_status(e);
+    if (fail != AC_OK) return fail;
     if (block) *block = static_cast<uint32_t>(h->tuning.block);
     if (stages) *stages = static_cast<uint32_t>(h->tuning.stages);
     if (kernel) {

@@ -137,7 +137,103 @@ inline int32_t goto_entry(const HostTables &h, uint32_t s, uint32_t c) {
     return h.gbits == 16 ? g_at<int16_t>(h, idx) : g_at<int32_t>(h, idx);
 }
 
+// Walk `len` codes of window w (first code in the low bits) from state s:
+// true with the state reached, or false with the encoded result where the
+// walk stopped.  A code >= C (a byte in no keyword) reads the end column,
+// which holds every state's encoded result.
+bool walk_window(const HostTables &h, uint32_t s, uint32_t w, uint32_t len, int32_t *out) {
+    const uint32_t cmask = (1u << h.B) - 1u;
+    for (uint32_t i = 0; i < len; ++i) {
+        const uint32_t c = (w >> (h.B * i)) & cmask;
+        const int32_t t = goto_entry(h, s, c < h.C ? c : h.C);
+        if (t < 0) {
+            *out = t;
+            return false;
+        }
+        s = static_cast<uint32_t>(t);
+    }
+    *out = static_cast<int32_t>(s);
+    return true;
+}
+
+uint32_t first_state_at(const HostTables &h, uint32_t d) {
+    uint32_t b = 0;
+    for (uint32_t i = 0; i < d && i < h.depth_count.size(); ++i) b += h.depth_count[i];
+    return b;
+}
+
+// Step 7: the stride table from the depth-k states: the deepest k2 >= 2 whose
+// table fits stride_bytes (k + k2 codes in the kernel's window), each entry
+// the walk of its k2 codes from its state.
+void stride_rows(const HostTables &h, RootTables *rt, uint64_t stride_bytes) {
+    rt->k2 = 0;
+    rt->J2.clear();
+    if (rt->k == 0 || stride_bytes <= 1 || rt->k >= h.maxlen) return;
+    const uint32_t wl = window_limit(h.B);
+    if (rt->k >= wl) return;
+    const uint32_t top = std::min(h.maxlen - rt->k, wl - rt->k);
+    for (uint32_t cand = top; cand >= 2; --cand) {
+        if (h.B * cand >= 32) continue;
+        const uint64_t bytes = (static_cast<uint64_t>(rt->count_k) << (h.B * cand)) * 4ull;
+        if (bytes <= stride_bytes) {
+            rt->k2 = cand;
+            break;
+        }
+    }
+    if (rt->k2 == 0) return;
+    const uint32_t cols = 1u << (h.B * rt->k2);
+    rt->J2.assign(static_cast<size_t>(rt->count_k) * cols, 0);
+    for (uint32_t r = 0; r < rt->count_k; ++r)
+        for (uint32_t w = 0; w < cols; ++w) {
+            int32_t e = 0;
+            walk_window(h, rt->base_k + r, w, rt->k2, &e);
+            rt->J2[static_cast<size_t>(r) * cols + w] = e;
+        }
+}
+
 }  // namespace
+
+uint32_t filter_window(uint32_t B, uint32_t maxlen, uint32_t bytes) {
+    uint32_t fbits = 0;  // largest filter (in bits) that fits the budget
+    while (fbits < kFilterBits && (2ull << fbits) <= 8ull * bytes) ++fbits;
+    return std::max<uint32_t>(1u, std::min<uint32_t>(maxlen, fbits / B));
+}
+
+void window_tables(const HostTables &h, uint32_t k, uint64_t stride_bytes, RootTables *rt) {
+    // Step 6a: for every window of k codes, one filter bit that is clear when
+    // the walk from the root stops inside the window with no keyword found
+    // (the start's result is -1), and the window table: the depth-k state
+    // reached, or the encoded result where the walk stopped.
+    rt->k = k;
+    rt->base_k = first_state_at(h, k);
+    rt->count_k = k < h.depth_count.size() ? h.depth_count[k] : 0u;
+    rt->fbits = 0;
+    const uint32_t nwin = 1u << (h.B * k);
+    // The bit of window w is bit 31 - (w & 31) of word w >> 5 (the kernel
+    // rotates it to bit 31); windows of fewer than 5 bits are repeated over
+    // the 32 bits of word 0, as the kernel indexes by the low 5 bits of the
+    // code stream.
+    rt->F.assign(std::max<uint32_t>(nwin / 32u, 4u), 0u);
+    rt->JK.assign(nwin, 0);
+    for (uint32_t w = 0; w < nwin; ++w) {
+        int32_t e = 0;
+        const bool alive = walk_window(h, 0, w, k, &e);
+        rt->JK[w] = e;
+        if (alive || e < -1)
+            for (uint32_t v = w; v < std::max<uint32_t>(nwin, 32u); v += nwin) rt->F[v >> 5] |= 1u << (31u - (v & 31u));
+    }
+    stride_rows(h, rt, stride_bytes);
+}
+
+void hashed_filter(const HostTables &h, uint32_t fbits, RootTables *rt) {
+    rt->fbits = fbits;
+    rt->F.assign((1u << fbits) / 32u, 0u);
+    for (size_t b = 0; b + 3 < h.HK.size(); b += 4) {
+        if (h.HK[b + 1] == 0u) continue;  // an empty entry
+        const uint32_t f = (h.HK[b] * kFilterHashMul) >> (32u - fbits);
+        rt->F[f >> 5] |= 1u << (31u - (f & 31u));
+    }
+}
 
 int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t nkw,
                  const BuildOptions &opt, HostTables *out) {
@@ -336,28 +432,17 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             //     the window with no keyword found (the start's result is -1), and
             //     the window table: the depth-kf state reached, or the encoded
             //     result where the walk stopped.
+            //     (window_tables; step 7 with it)
             h.filter = true;
-            uint32_t fbits = 0;  // largest window that fits the shared-memory budget
-            while (fbits < kFilterBits && (2ull << fbits) <= 8ull * opt.jump_bytes) ++fbits;
-            const uint32_t kf = std::max<uint32_t>(1u, std::min<uint32_t>(h.maxlen, fbits / h.B));
-            h.k = kf;
-            h.base_k = depth_base[kf];
-            h.count_k = h.depth_count[kf];
-            const uint32_t nwin = 1u << (h.B * kf);
-            // The bit of window w is bit 31 - (w & 31) of word w >> 5 (the
-            // kernel rotates it to bit 31); windows of fewer than 5 bits are
-            // repeated over the 32 bits of word 0, as the kernel indexes by
-            // the low 5 bits of the code stream.
-            h.F.assign(std::max<uint32_t>(nwin / 32u, 4u), 0u);
-            h.JK.assign(nwin, 0);
-            for (uint32_t w = 0; w < nwin; ++w) {
-                int32_t e = 0;
-                const bool alive = walk_codes(0, w, kf, &e);
-                h.JK[w] = e;
-                if (alive || e < -1)
-                    for (uint32_t v = w; v < std::max<uint32_t>(nwin, 32u); v += nwin)
-                        h.F[v >> 5] |= 1u << (31u - (v & 31u));
-            }
+            RootTables rt;
+            window_tables(h, filter_window(h.B, h.maxlen, opt.jump_bytes), opt.stride_bytes, &rt);
+            h.k = rt.k;
+            h.base_k = rt.base_k;
+            h.count_k = rt.count_k;
+            h.k2 = rt.k2;
+            h.F = std::move(rt.F);
+            h.JK = std::move(rt.JK);
+            h.J2 = std::move(rt.J2);
         } else {
             // 6b. root jump table (8-bit codes).  Entry for a window of k codes:
             //     the walk's result (>= -1) when it stops inside the window, else
@@ -443,28 +528,16 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
         }
         const uint32_t kj = h.k;
 
-        // 7. stride table from the depth-k states
-        h.k2 = 0;
-        if (kj > 0 && opt.stride_bytes > 1) {
-            uint32_t top = std::min(h.maxlen - kj, wl - kj);
-            for (uint32_t cand = top; cand >= 2; --cand) {
-                if (h.B * cand >= 32) continue;
-                uint64_t bytes = (static_cast<uint64_t>(h.count_k) << (h.B * cand)) * 4ull;
-                if (bytes <= opt.stride_bytes) {
-                    h.k2 = cand;
-                    break;
-                }
-            }
-        }
-        if (h.k2 > 0) {
-            const uint32_t cols = 1u << (h.B * h.k2);
-            h.J2.assign(static_cast<size_t>(h.count_k) * cols, 0);
-            for (uint32_t r = 0; r < h.count_k; ++r)
-                for (uint32_t w = 0; w < cols; ++w) {
-                    int32_t e = 0;
-                    walk_codes(h.base_k + r, w, h.k2, &e);
-                    h.J2[static_cast<size_t>(r) * cols + w] = e;
-                }
+        // 7. stride table from the depth-k states (with 2- and 4-bit codes
+        //    window_tables made it)
+        if (h.B == 8) {
+            RootTables rt;
+            rt.k = kj;
+            rt.base_k = h.base_k;
+            rt.count_k = h.count_k;
+            stride_rows(h, &rt, opt.stride_bytes);
+            h.k2 = rt.k2;
+            h.J2 = std::move(rt.J2);
         }
 
         // 8. chain records for the states from the first mostly-unbranched

@@ -16,11 +16,16 @@ namespace {
 
 bool served(const DevTables &t) { return ((t.B == 2 || t.B == 4) && t.filter) || (t.B == 8 && t.hashed && t.HK); }
 
-// Bytes staged per tile: the tile and a halo of up to kHaloCap bytes (at
-// least 16, the windows' look-ahead).
-uint32_t staged_bytes(const DevTables &t) {
-    const uint32_t H = t.maxlen < kHaloCap ? t.maxlen : kHaloCap;
-    return align16(kTile + H) > align16(kTile + 16) ? align16(kTile + H) : align16(kTile + 16);
+// Bytes staged per tile: the tile and the 16 bytes after it (the windows'
+// look-ahead; kCodeSpan positions are classified), or a wider halo (tuning:
+// up to kHaloCap bytes, at most the longest keyword).  The filter reads no
+// further; a walk past the classified span reads its bytes through L1/L2,
+// where a wider halo has brought them.
+uint32_t staged_bytes(const DevTables &t, const Tuning &tu) {
+    uint32_t h = tu.halo > 16 ? static_cast<uint32_t>(tu.halo) : 16u;
+    if (h > kHaloCap) h = kHaloCap;
+    if (h > t.maxlen && t.maxlen > 16) h = t.maxlen;
+    return align16(kTile + h);
 }
 
 // The launch parameters of automaton t and request r, all but the shared-
@@ -36,7 +41,7 @@ cudaError_t fill_params(const DevTables &t, const MatchRequest &r, OutMode mode,
     p.text = r.text;
     p.n = r.n;
     p.tile = kTile;
-    p.staged = staged_bytes(t);
+    p.staged = staged_bytes(t, tu);
     uint64_t tiles = 0;
     if (!batch) {
         const uint64_t head = reinterpret_cast<uintptr_t>(r.text) & 15u;
@@ -155,6 +160,15 @@ cudaError_t device_shape(DeviceShape *out) {
 
 }  // namespace
 
+uint32_t device_sm_count() {
+    DeviceShape ds;
+    if (device_shape(&ds) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return static_cast<uint32_t>(ds.sms);
+}
+
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                           cudaStream_t stream) {
     if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
@@ -187,7 +201,7 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
         return launch_filter_help(mode, p, t.B, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
     if (t.B == 8) {
         e = launch_filter8(mode, p, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
-        if (e == cudaSuccess && p.list) e = launch_survivors8(mode, p, t.gbits, static_cast<uint32_t>(ds.sms), stream);
+        if (e == cudaSuccess && p.list) e = launch_survivors8(mode, p, t.gbits, static_cast<uint32_t>(ds.sms), tu.per_thread, stream);
         return e;
     }
     if (t.B == 2) {

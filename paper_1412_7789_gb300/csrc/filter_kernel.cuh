@@ -72,7 +72,7 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr uint32_t kHelpTilesPerWarp = 16;
 // Entries of the phased form's lists a warp reserves at a time.
 constexpr uint32_t kListChunk = 1024;
-constexpr uint32_t kWalkChunk = 256;
+constexpr uint32_t kWalkChunk = kWalkChunkEntries;
 
 // Walks per lane in one round of a tile with many survivors: 8 (rounds of
 // 256); with 8-bit codes, whose tiles hold about a hundred survivors each and
@@ -126,7 +126,7 @@ struct FilterParams {
     uint4 *list;
     unsigned int *list_count;
     uint32_t list_cap;
-    uint4 *walks;
+    uint2 *walks;  // {(tile << 10) | position, state | d << 31}: next byte at position + k + d
     uint32_t walk_cap;
     // 8-bit codes: the codes are the bytes (256 columns), or classes from the
     // byte table; the filter index is the top bits of (window & wmask) *
@@ -357,8 +357,10 @@ __device__ __forceinline__ int chain_step(const FilterParams &p, const TileText 
 // The walk from state s at tile position q, text bytes from global memory;
 // out of line, for the few walks of 8-bit codes that the state hash leaves
 // open (a copy per call site would crowd the instruction cache).
+// (The structures go by value: a reference to the caller's would keep them in
+// local memory for the caller's whole run.)
 template <typename GT>
-__device__ __noinline__ int walk_far(const FilterParams &p, const uint8_t *cls8, const TileText &tt, int64_t gpb,
+__device__ __noinline__ int walk_far(const FilterParams &p, const uint8_t *cls8, const TileText tt, int64_t gpb,
                                      uint32_t s, uint32_t q);
 
 // Finish up to SLOTS * 32 queued survivors (queue[base .. base + avail)) of a
@@ -556,9 +558,10 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
 
 // One warp, a tile whose matches overflowed its slots: the survivors walked
 // again, 64 at a time (rare, so with few registers), the ids found written to
-// the unit's dense fallback (set to -1 by the caller).
+// the unit's dense fallback (set to -1 by the caller).  The structures go by
+// value (references would keep the caller's in local memory).
 template <int B, typename GT>
-__device__ __noinline__ void refill_fallback(const FilterParams &p, const TileText &tt, const WarpSmem &w,
+__device__ __noinline__ void refill_fallback(const FilterParams &p, const TileText tt, const WarpSmem w,
                                                 int64_t gpb, bool interior, bool clean, uint32_t total, int lane,
                                                 uint32_t su) {
     unsigned long long none = 0;
@@ -710,7 +713,7 @@ __device__ __forceinline__ int walk_global(const FilterParams &p, const uint8_t 
 }
 
 template <typename GT>
-__device__ __noinline__ int walk_far(const FilterParams &p, const uint8_t *cls8, const TileText &tt, int64_t gpb,
+__device__ __noinline__ int walk_far(const FilterParams &p, const uint8_t *cls8, const TileText tt, int64_t gpb,
                                      uint32_t s, uint32_t q) {
     return walk_global<GT>(p, cls8, tt, gpb, s, q);
 }
@@ -1016,10 +1019,12 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
         if (owner) {
             // The bit of window value v is bit 31 - (v & 31) of filter word
             // v >> 5: rotating the word left by v's low five bits brings it to
-            // bit 31, and a funnel shift appends it to acc (first position
-            // ends highest, hence the bit reversal).
+            // bit 31, and a funnel shift appends it to an accumulator (first
+            // position ends highest, hence the bit reversal).  Four
+            // accumulators of 8 positions each keep the appends out of one
+            // 32-long dependency chain.
             const uint8_t *fb = reinterpret_cast<const uint8_t *>(w.F);
-            uint32_t acc = 0;
+            uint32_t acc4[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
             for (uint32_t h = 0; h < 2; ++h) {
 #pragma unroll
@@ -1036,10 +1041,12 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                         win = ((__funnelshift_r(lo, hi, 8 * (r & 3)) & p.wmask) * kFilterHashMul) >> p.fshift;
                     }
                     const uint32_t word = *reinterpret_cast<const uint32_t *>(fb + ((win >> 3) & p.famask));
+                    uint32_t &acc = acc4[2 * h + (r >> 3)];
                     acc = __funnelshift_l(__funnelshift_l(word, word, win), acc, 1);
                 }
             }
-            sv = __brev(acc);
+            // positions 0-7, 8-15, 16-23, 24-31 from the highest byte down
+            sv = __brev((acc4[0] << 24) | (acc4[1] << 16) | (acc4[2] << 8) | acc4[3]);
         }
         if (!interior || !clean) {
             const uint32_t kbits = (1u << k) - 1u;
@@ -1386,85 +1393,110 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
 }
 
 // The second phase of the two-phase form (one text, 8-bit codes): one thread
-// per listed survivor, two at a time so that their loads overlap, at high
-// occupancy (five CTAs of 256 threads per SM).  Each survivor's state-hash
-// entry and the code after its window are loaded together; the entry settles
-// most survivors, the others walk on (chain records, goto rows, text from
-// global memory).  Ids found go to the dense output (its -1 are written by
+// per listed survivor, SPT at a time so that their loads overlap, at high
+// occupancy (48 warps per SM with 2 at a time, 32 with 4).  Each survivor's state-hash entry settles most survivors; a walk
+// from a depth-k state with several children takes its first goto step here
+// (the code after the window is in the entry), which ends most of them; the
+// walks left go to the walk list for the third step (it has room for all of
+// them; were it ever full, the error word says so).  Ids found go to the
+// dense output (its -1 are written by
 // the first phase), the count, or the unit's slots (no dense fallback: the
 // gather step matches a unit with more matches than slots again).
 constexpr int kSurvBlock = 256;
-constexpr int kSurvCtas = 5;
+template <int SPT>
+__host__ __device__ constexpr int surv_ctas() { return SPT <= 2 ? 6 : 4; }
+static_assert(surv_ctas<2>() * kSurvBlock / 32 <= static_cast<int>(kSurvWarpsPerSm) &&
+                  surv_ctas<4>() * kSurvBlock / 32 <= static_cast<int>(kSurvWarpsPerSm),
+              "the walk list's room assumes at most kSurvWarpsPerSm warps of step 2 per SM");
 
-template <typename GT, int MODE>
-__global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const __grid_constant__ FilterParams p) {
-    __shared__ uint8_t cls8[256];
+template <typename GT, int MODE, int SPT>
+__global__ void __launch_bounds__(kSurvBlock, surv_ctas<SPT>()) pfac_survivors8(const __grid_constant__ FilterParams p) {
     const int lane = threadIdx.x & 31;
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) cls8[i] = __ldg(p.cls8g + i);
-    __syncthreads();
+    const GT *G = static_cast<const GT *>(p.G);
     const uint32_t listed = *reinterpret_cast<volatile const unsigned int *>(p.list_count);
     const uint32_t m = listed < p.list_cap ? listed : p.list_cap;
     const uint32_t stride = gridDim.x * blockDim.x;
     const int64_t head = static_cast<int64_t>(reinterpret_cast<uintptr_t>(p.text) & 15u);
-    const int64_t n = static_cast<int64_t>(p.n);
     unsigned long long cnt = 0;
-    // the part [wnext, wend) of the walk list this warp reserved (wfull: no room)
+    // the part [wnext, wend) of the walk list this warp reserved
     uint32_t wnext = 0, wend = 0;
-    bool wfull = p.walk_cap == 0;
     // all lanes of a warp take part in every round (the walk list is filled
     // warp-wide): the loop runs on the warp's first index
-    for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < m; wb += 2u * stride) {
+    for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < m; wb += SPT * stride) {
         const uint32_t b0 = wb + static_cast<uint32_t>(lane);
-        uint4 e[2];
-        uint4 he[2];
-        uint32_t c[2];
+        uint4 e[SPT], he[SPT];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < SPT; ++t) {
             const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
             e[t] = idx < m ? __ldg(p.list + idx) : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
             he[t] = make_uint4(0u, 0u, 0u, 0u);
-            c[t] = e[t].z;  // the code after the window (0x100: none, or a byte in no keyword)
             if (e[t].x != 0xFFFFFFFFu) he[t] = __ldg(p.HK + hk_slot(p, e[t].y));
         }
+        // outcomes; the first step of the walks from a branching state
+        int r[SPT], g[SPT];
+        uint32_t s[SPT], q[SPT];
+        bool walk[SPT];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
+        for (int t = 0; t < SPT; ++t) {
             const bool on = e[t].x != 0xFFFFFFFFu;
+            const uint32_t i = e[t].x & 1023u, c = e[t].z;  // c: the code after the window (0x100: none)
+            r[t] = -1;
+            s[t] = 0;
+            q[t] = 0;
+            walk[t] = on && !hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c & 0xFFu, c < 0x100u, r[t], s[t], q[t]);
+            if (walk[t]) r[t] = -1;  // its id comes from the walk
+            // (every state has its goto row; the chain records only shortcut runs)
+            g[t] = 0;
+            if (walk[t] && q[t] == i + p.k) g[t] = goto_ld(G, s[t], p.W, c < 0x100u ? c : p.C);
+        }
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+            const uint32_t i = e[t].x & 1023u;
+            if (walk[t] && q[t] == i + p.k) {
+                if (g[t] < 0) {
+                    r[t] = decode_dead(g[t]);
+                    walk[t] = false;
+                } else {
+                    s[t] = static_cast<uint32_t>(g[t]);
+                    ++q[t];
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
             const uint32_t unit = e[t].x >> 10, i = e[t].x & 1023u;
             const int64_t gpb = static_cast<int64_t>(unit) * kTile - head;
-            int r = -1;
-            uint32_t s = 0, q = 0;
-            const bool walk = on && !hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c[t] & 0xFFu, c[t] < 0x100u, r, s, q);
-            if (walk) r = -1;  // its id comes from the walk (here, or in the third step)
-            // walks that go on: to the walk list (warp-wide), else walked here
-            const unsigned wm = __ballot_sync(kFull, walk);
-            bool listed_walk = false;
-            if (wm && !wfull) {
-                const uint32_t need = __popc(wm);
+            // walks that go on: to the walk list (warp-wide, in the warp's
+            // chunk; when it runs out, its rest takes the first walks and a
+            // new chunk the others, so that only each warp's last chunk has
+            // unused entries)
+            const unsigned wm = __ballot_sync(kFull, walk[t]);
+            if (wm) {
+                const uint32_t need = __popc(wm), rank = __popc(wm & ((1u << lane) - 1u));
+                uint32_t slot = wnext + rank;
                 if (wend - wnext < need) {
-                    for (uint32_t j = wnext + static_cast<uint32_t>(lane); j < wend; j += 32u)
-                        p.walks[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                    const uint32_t rest = wend - wnext;
                     uint32_t base = 0;
                     if (lane == 0) base = atomicAdd(p.list_count + 1, kWalkChunk);
                     base = __shfl_sync(kFull, base, 0);
-                    wnext = base;
+                    if (rank >= rest) slot = base + (rank - rest);
+                    wnext = base + (need - rest);
                     wend = base + kWalkChunk;
-                    if (static_cast<uint64_t>(base) + kWalkChunk > p.walk_cap) {
-                        for (uint32_t j = base + static_cast<uint32_t>(lane); j < p.walk_cap && j < wend; j += 32u)
-                            p.walks[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                    // the list has room for every walk and each warp's last chunk
+                    if (static_cast<uint64_t>(base) + kWalkChunk > p.walk_cap) {  // so this cannot happen
+                        if (lane == 0) atomicOr(p.err, static_cast<unsigned>(kErrWalk));
                         wnext = wend = 0;
-                        wfull = true;
                     }
-                }
-                if (!wfull) {
-                    if (walk) p.walks[wnext + __popc(wm & ((1u << lane) - 1u))] = make_uint4(e[t].x, s, q, 0u);
+                } else {
                     wnext += need;
-                    listed_walk = true;
                 }
+                if (walk[t] && wend != 0 && slot < p.walk_cap)
+                    p.walks[slot] = make_uint2(e[t].x, s[t] | ((q[t] - i - p.k) << 31));
             }
-            if (walk && !listed_walk) r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, s, q);
-            if (!on || r < 0) continue;
+            const int rr = r[t];
+            if (e[t].x == 0xFFFFFFFFu || rr < 0) continue;
             if (MODE == OUT_DENSE) {
-                p.out[gpb + i] = r;
+                p.out[gpb + i] = rr;
             } else if (MODE == OUT_COUNT) {
                 ++cnt;
             } else {
@@ -1472,13 +1504,12 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const _
                 const uint32_t k = atomicAdd(p.sl.counts + su, 1u);
                 if (k < kSlotCap)
                     p.sl.slots[static_cast<uint64_t>(su) * kSlotCap + k] =
-                        (static_cast<unsigned long long>(static_cast<uint32_t>(r)) << 32) |
+                        (static_cast<unsigned long long>(static_cast<uint32_t>(rr)) << 32) |
                         static_cast<uint32_t>(gpb + i);
             }
         }
     }
-    for (uint32_t j = wnext + static_cast<uint32_t>(lane); j < wend; j += 32u)
-        p.walks[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+    for (uint32_t j = wnext + static_cast<uint32_t>(lane); j < wend; j += 32u) p.walks[j] = make_uint2(0xFFFFFFFFu, 0u);
     if (MODE == OUT_COUNT) {
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(kFull, cnt, d);
@@ -1489,7 +1520,7 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_survivors8(const _
 // The third step of the phased form: one thread per listed walk (state, next
 // byte) at high occupancy; the ids found go out as in the second step.
 template <typename GT, int MODE>
-__global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_walks8(const __grid_constant__ FilterParams p) {
+__global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks8(const __grid_constant__ FilterParams p) {
     __shared__ uint8_t cls8[256];
     const int lane = threadIdx.x & 31;
     for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) cls8[i] = __ldg(p.cls8g + i);
@@ -1499,11 +1530,12 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_walks8(const __gri
     const int64_t head = static_cast<int64_t>(reinterpret_cast<uintptr_t>(p.text) & 15u);
     unsigned long long cnt = 0;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
-        const uint4 e = __ldg(p.walks + j);
+        const uint2 e = __ldg(p.walks + j);
         if (e.x == 0xFFFFFFFFu) continue;
         const uint32_t unit = e.x >> 10, i = e.x & 1023u;
         const int64_t gpb = static_cast<int64_t>(unit) * kTile - head;
-        const int r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, e.y, e.z);
+        const int r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, e.y & 0x7FFFFFFFu,
+                                      i + p.k + (e.y >> 31));
         if (r < 0) continue;
         if (MODE == OUT_DENSE) {
             p.out[gpb + i] = r;
@@ -1524,21 +1556,22 @@ __global__ void __launch_bounds__(kSurvBlock, kSurvCtas) pfac_walks8(const __gri
     }
 }
 
-template <typename GT>
+template <typename GT, int SPT>
 cudaError_t launch_survivors8(OutMode mode, const FilterParams &p, uint32_t sms, cudaStream_t stream) {
-    const uint32_t grid = sms * static_cast<uint32_t>(kSurvCtas);
+    const uint32_t grid = sms * static_cast<uint32_t>(surv_ctas<SPT>());
     switch (mode) {
-        case OUT_DENSE: pfac_survivors8<GT, OUT_DENSE><<<grid, kSurvBlock, 0, stream>>>(p); break;
-        case OUT_COUNT: pfac_survivors8<GT, OUT_COUNT><<<grid, kSurvBlock, 0, stream>>>(p); break;
-        case OUT_SLOTS: pfac_survivors8<GT, OUT_SLOTS><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_DENSE: pfac_survivors8<GT, OUT_DENSE, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_COUNT: pfac_survivors8<GT, OUT_COUNT, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_SLOTS: pfac_survivors8<GT, OUT_SLOTS, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.walks) return e;
+    const uint32_t wgrid = sms * static_cast<uint32_t>(surv_ctas<2>());
     switch (mode) {
-        case OUT_DENSE: pfac_walks8<GT, OUT_DENSE><<<grid, kSurvBlock, 0, stream>>>(p); break;
-        case OUT_COUNT: pfac_walks8<GT, OUT_COUNT><<<grid, kSurvBlock, 0, stream>>>(p); break;
-        default: pfac_walks8<GT, OUT_SLOTS><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_DENSE: pfac_walks8<GT, OUT_DENSE><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_COUNT: pfac_walks8<GT, OUT_COUNT><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
+        default: pfac_walks8<GT, OUT_SLOTS><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
     }
     return cudaGetLastError();
 }
@@ -1658,7 +1691,8 @@ cudaError_t launch_filter_help(OutMode mode, const filt::FilterParams &p, uint32
 // their two-phase form, filter8.cu.
 cudaError_t launch_filter8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t grid, uint32_t block,
                            uint32_t smem, int max_smem, cudaStream_t stream);
-cudaError_t launch_survivors8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t sms,
+// per_thread: survivors a thread of the second step takes at a time (2 or 4)
+cudaError_t launch_survivors8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t sms, int per_thread,
                               cudaStream_t stream);
 
 namespace filt {

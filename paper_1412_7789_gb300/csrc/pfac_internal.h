@@ -136,6 +136,25 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
 // window of 2- or 4-bit codes, one 64-bit window of 8-bit codes).
 inline uint32_t window_limit(uint32_t B) { return B == 2 ? 16u : 8u; }
 
+// The tables of the root filter kernel that depend on how much of it sits in
+// shared memory (its depth): computed by the builder, and again by the
+// autotuner for other depths from the goto table alone.
+struct RootTables {
+    uint32_t k = 0, k2 = 0, base_k = 0, count_k = 0;  // 2- and 4-bit codes
+    uint32_t fbits = 0;                                // 8-bit codes
+    std::vector<uint32_t> F;
+    std::vector<int32_t> JK, J2;
+};
+// 2- and 4-bit codes: the root filter and window table over windows of k codes
+// (1 <= k, B k <= kFilterBits), and the stride table from the depth-k states
+// (at most stride_bytes; none when 0 or 1).
+void window_tables(const HostTables &h, uint32_t k, uint64_t stride_bytes, RootTables *out);
+// 8-bit codes with the state hash: the hashed filter at 2^fbits bits (5 <=
+// fbits <= kFilterBits), from the windows in the state hash.
+void hashed_filter(const HostTables &h, uint32_t fbits, RootTables *out);
+// The widest window of B-bit codes whose filter fits `bytes`.
+uint32_t filter_window(uint32_t B, uint32_t maxlen, uint32_t bytes);
+
 // Device view of a compiled automaton.
 struct DevTables {
     const void *G = nullptr;         // goto table
@@ -228,7 +247,7 @@ struct MatchRequest {
     uint4 *list = nullptr;
     unsigned int *list_count = nullptr;      // zeroed, two words: survivors, walks
     uint32_t list_cap = 0;
-    uint4 *walks = nullptr;
+    uint2 *walks = nullptr;
     uint32_t walk_cap = 0;
 };
 
@@ -240,24 +259,32 @@ struct MatchRequest {
 //   2. one thread per survivor at full occupancy loads its state-hash entry,
 //      settles most survivors and writes the ids found; a survivor whose walk
 //      goes on is appended to a second list -- {(tile << 10) | position,
-//      state, tile index of the walk's next byte, 0};
+//      state | d << 31}, the walk's next byte at tile index position + k + d
+//      (d = 1 when the state hash already took the byte after the window);
 //   3. one thread per walk, at full occupancy, finishes the walks.
 // Warps reserve list space in chunks (entries they leave unused are marked
 // empty: x = 0xFFFFFFFF).  A tile whose survivors do not fit, or that holds a
-// window past the text end, is resolved by its warp as in the one-phase form,
-// and a walk that does not fit by its thread in step 2.
+// window past the text end, is resolved by its warp as in the one-phase form.
+// The walk list has room for one walk per listed survivor plus a chunk per
+// warp of step 2 (a warp leaves entries unused only in its last chunk), so
+// every walk fits.
+constexpr uint32_t kWalkChunkEntries = 256;  // walk-list entries a warp of step 2 reserves at a time
+constexpr uint32_t kSurvWarpsPerSm = 48;     // most warps of step 2 resident on one SM
+uint32_t device_sm_count();                  // of the current device (cached; 0 on error)
 struct SurvivorLists {
     uint32_t list_cap = 0, walk_cap = 0;
-    size_t bytes() const { return list_cap ? 32 + 16ull * list_cap + 16ull * walk_cap : 0; }
+    size_t bytes() const { return list_cap ? 32 + 16ull * list_cap + 8ull * walk_cap : 0; }
 };
 // The lists of a text of n bytes (none: the one-phase form, for short texts
 // and for texts of more tiles than the entries can name).  Scratch layout:
-// two counters (32 bytes, zeroed) | list_cap uint4 | walk_cap uint4.
+// two counters (32 bytes, zeroed) | list_cap uint4 | walk_cap uint2.
 inline SurvivorLists survivor_lists(const DevTables &t, uint64_t n) {
     SurvivorLists s;
     if (!t.hashed || n < (4ull << 20) || n / 992 >= (1ull << 22)) return s;
-    s.list_cap = static_cast<uint32_t>(n / 8);   // 12.5 % of the positions
-    s.walk_cap = static_cast<uint32_t>(n / 32);  // 3.1 %
+    const uint64_t sms = device_sm_count();
+    if (sms == 0) return s;
+    s.list_cap = static_cast<uint32_t>(n / 8);  // 12.5 % of the positions
+    s.walk_cap = static_cast<uint32_t>(s.list_cap + sms * kSurvWarpsPerSm * kWalkChunkEntries);
     return s;
 }
 inline void set_lists(MatchRequest &r, void *scratch, const SurvivorLists &s) {
@@ -265,7 +292,7 @@ inline void set_lists(MatchRequest &r, void *scratch, const SurvivorLists &s) {
     r.list_count = reinterpret_cast<unsigned int *>(b);
     r.list = reinterpret_cast<uint4 *>(b + 32);
     r.list_cap = s.list_cap;
-    r.walks = reinterpret_cast<uint4 *>(b + 32 + 16ull * s.list_cap);
+    r.walks = reinterpret_cast<uint2 *>(b + 32 + 16ull * s.list_cap);
     r.walk_cap = s.walk_cap;
 }
 
@@ -279,6 +306,10 @@ struct Tuning {
                           // 2 = one thread per position with the jump table in shared
                           // memory (jump8.cu), 0 or 3 = the same at full occupancy with
                           // the table read through L1 (the default)
+    int per_thread = 0;   // 8-bit codes, long texts: survivors a thread of the second
+                          // step takes at a time (2, or 4 with fewer threads; 0 = 2)
+    int halo = 0;         // bytes staged after each tile: 0 = the 16 the filter reads,
+                          // or up to kHaloCap (a wider halo reaches L2 ahead of the walks)
     unsigned long long wait_ns = 0;  // bounded waits give up after this (0 = kWaitNs)
     int stall_help = 0;   // test aid: owners wait for one chunk more than their heavy tile has
 };

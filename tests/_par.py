@@ -119,3 +119,24 @@ def check_compact(pos_dev, ids_dev, total: int, wpos: np.ndarray, wids: np.ndarr
         bad = np.nonzero((gp != wpos.astype(np.uint32)) | (gi != wids.astype(np.uint32)))[0][:6]
         raise AssertionError("%s compact differs at entries %s: got %s / %s want %s / %s" % (
             what, bad.tolist(), gp[bad].tolist(), gi[bad].tolist(), wpos[bad].tolist(), wids[bad].tolist()))
+
+
+def check_outputs(h: int, t, n: int, wpos: np.ndarray, wids: np.ndarray, what: str = ""):
+    """Dense ids, count and compacted list of handle h on device text t[:n]
+    through the C ABI, against the oracle's list (wpos, wids)."""
+    import torch
+
+    from paper_1412_7789_gb300 import api
+
+    out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    api.ac_match(h, t, n, out)
+    check_dense(out[:n], wpos, wids, what)
+    del out
+    cnt = torch.full((1,), 12345, dtype=torch.int64, device="cuda")
+    api.ac_count(h, t, n, cnt)
+    assert int(cnt.item()) == wpos.size, (what, int(cnt.item()), wpos.size)
+    cap = max(1, wpos.size)
+    pos = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    ids = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    api.ac_match_compact(h, t, n, pos, ids, cap, cnt)
+    check_compact(pos, ids, int(cnt.item()), wpos, wids, what)

@@ -191,6 +191,7 @@ def test_struct_layouts_match_the_header(tmp_path):
         "ac_server_options": api.ac_server_options,
         "ac_options": api.ac_options,
         "ac_info_t": api.ac_info_t,
+        "ac_tuning": api.ac_tuning,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ac.h"', "int main(void) {"]
     for name, m in mirrors.items():
@@ -402,11 +403,15 @@ def test_root_filter_and_window_table(lib, alpha, lmin, lmax):
     pats = [bytes(a[g.integers(0, a.size, size=int(g.integers(lmin, lmax + 1)))]) for _ in range(300)]
     h = api.ac_compile(pats, host_only=True)
     try:
-        B, k, F, JK = api.ac_export_filter(h)
-        cls, G, depth = api.ac_export_tables(h)
-        info = api.ac_info(h)
+        _check_window_tables(h)
     finally:
         api.ac_destroy(h)
+
+
+def _check_window_tables(h):
+    B, k, F, JK = api.ac_export_filter(h)
+    cls, G, depth = api.ac_export_tables(h)
+    info = api.ac_info(h)
     assert B in (2, 4) and k >= 1 and JK.size == 1 << (B * k)
     C, W = info["n_classes"], info["row_width"]
     G = G.reshape(info["n_states"], W).astype(np.int64)
@@ -431,7 +436,8 @@ def test_root_filter_and_window_table(lib, alpha, lmin, lmax):
         r = win & 31
         rot = ((words << r) | (words >> ((32 - r) & 31))) & 0xFFFFFFFF
         rot = np.where(r == 0, words, rot)
-        assert np.array_equal((rot >> 31) & 1, want.astype(np.int64)), (alpha, garbage)
+        assert np.array_equal((rot >> 31) & 1, want.astype(np.int64)), garbage
+    return k
 
 
 @pytest.mark.parametrize("alpha,lmin,lmax", [(b"ACGT", 12, 40), (b"abcdefghijkl", 6, 20)])
@@ -443,13 +449,20 @@ def test_stride_table(lib, alpha, lmin, lmax):
     pats = [bytes(a[g.integers(0, a.size, size=int(g.integers(lmin, lmax + 1)))]) for _ in range(400)]
     h = api.ac_compile(pats, host_only=True)
     try:
-        B, k, F, JK = api.ac_export_filter(h)
-        k2, base_k, count_k, J2 = api.ac_export_stride(h)
-        cls, G, depth = api.ac_export_tables(h)
-        info = api.ac_info(h)
+        assert _check_stride_table(h) >= 2
     finally:
         api.ac_destroy(h)
-    assert k2 >= 2 and J2.size == count_k << (B * k2)
+
+
+def _check_stride_table(h):
+    B, k, F, JK = api.ac_export_filter(h)
+    k2, base_k, count_k, J2 = api.ac_export_stride(h)
+    cls, G, depth = api.ac_export_tables(h)
+    info = api.ac_info(h)
+    if k2 == 0:
+        assert J2.size == 0
+        return 0
+    assert J2.size == count_k << (B * k2)
     assert base_k == int(depth[:k].sum()) and count_k == int(depth[k])
     C, W = info["n_classes"], info["row_width"]
     G = G.reshape(info["n_states"], W).astype(np.int64)
@@ -465,6 +478,64 @@ def test_stride_table(lib, alpha, lmin, lmax):
         res[stop] = -e[stop] - 2
         s = np.where(live & (e > 0), e, s)
     assert np.array_equal(J2, np.where(res == -2, s, -(res + 2)))
+    return k2
+
+
+@pytest.mark.parametrize("alpha,lmin,lmax", [(b"ACGT", 12, 40), (b"abcdefghijkl", 4, 20)])
+def test_shared_table_depth(lib, alpha, lmin, lmax):
+    """ac_set_tuning(filter_bytes) rebuilds the root filter, window table and
+    stride table for the largest window whose filter fits, from the goto table
+    alone: at every size they pass the same checks against goto-table walks,
+    the window shrinks with the budget, and a size that fits no filter, or a
+    bad field, is refused without changing anything."""
+    g = np.random.Generator(np.random.PCG64(len(alpha) * 11 + lmin))
+    a = np.frombuffer(alpha, dtype=np.uint8)
+    pats = [bytes(a[g.integers(0, a.size, size=int(g.integers(lmin, lmax + 1)))]) for _ in range(400)]
+    with api.Automaton(pats, host_only=True) as au:
+        B, k0, F0, JK0 = api.ac_export_filter(au.handle)
+        assert au.tuning()["filter_bytes"] == F0.nbytes
+        seen = []
+        for fb in (F0.nbytes // (1 << B), F0.nbytes // (1 << (2 * B)), 16, F0.nbytes):
+            au.set_tuning(filter_bytes=fb)
+            k = _check_window_tables(au.handle)
+            _check_stride_table(au.handle)
+            # the widest window whose filter (2^(B k) bits, at least 16 bytes) fits
+            assert max(4, (1 << (B * k)) // 32) * 4 <= max(fb, 16)
+            assert (1 << (B * (k + 1))) // 8 > fb or k == au.info()["max_len"]
+            assert au.tuning()["filter_bytes"] == max(16, (1 << (B * k)) // 8)
+            seen.append(k)
+        assert seen[-1] == k0 and seen[0] == k0 - 1 and len(set(seen)) >= 3
+        before = au.tuning()
+        for bad in ({"filter_bytes": 8}, {"block": 48}, {"stages": 5}, {"per_thread": 3}, {"halo": 512}):
+            with pytest.raises(api.AcError):
+                au.set_tuning(**bad)
+            assert au.tuning() == before
+        au.set_tuning(block=256, stages=2, halo=64, per_thread=4)
+        t = au.tuning()
+        assert (t["block"], t["stages"], t["halo"], t["per_thread"]) == (256, 2, 64, 4)
+
+
+def test_shared_table_depth_hashed(lib):
+    """8-bit codes: the hashed filter rebuilt at 2^fbits bits from the state
+    hash sets exactly the bits of the depth-kh states' windows."""
+    _, pats = workloads.zipf_byte(1 << 18, seed=5, n_keywords=2000)
+    with api.Automaton(pats, host_only=True) as au:
+        kh, fbits0, hk_bits, probes, F0, HK = api.ac_export_hash(au.handle)
+        assert fbits0 == 20
+        wins = HK[HK[:, 1] != 0, 0].astype(np.int64)
+        for fb in (1 << 15, 1 << 13, 4, 1 << 17):
+            au.set_tuning(filter_bytes=fb)
+            kh2, fbits, _, _, F, HK2 = api.ac_export_hash(au.handle)
+            assert kh2 == kh and np.array_equal(HK2, HK)
+            assert (1 << fbits) // 8 <= fb < (1 << (fbits + 1)) // 8 or fbits == 20
+            f = ((wins * 0x9E3779B1) & 0xFFFFFFFF) >> (32 - fbits)
+            want = np.zeros(F.size * 32, dtype=bool)
+            want[f] = True
+            bits = np.unpackbits(F.view(np.uint8).reshape(-1, 4)[:, ::-1], axis=1).reshape(-1).astype(bool)
+            assert np.array_equal(bits, want), fb
+            assert au.tuning()["filter_bytes"] == F.nbytes
+        with pytest.raises(api.AcError):
+            au.set_tuning(filter_bytes=3)
 
 
 @pytest.mark.parametrize("kw", [{}, {"class_compress": False}])

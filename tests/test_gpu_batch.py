@@ -225,13 +225,33 @@ def test_batch_workload_sample(automata):
 
 
 def test_autotune_keeps_results(automata):
+    """Every knob the autotuner searches changes only the time: at each
+    shared-table depth it tries, threads per CTA and stages, the halo and
+    chars per thread, and then with the shape it chose, dense ids, count and
+    compacted list of a 6 MiB text (long enough for the phased form of 8-bit
+    codes) are the oracle's."""
+    from tests import _par
+
     sets, hs = automata
-    for j in (0, 2):
-        text = _text_for(j, 3 << 20, 40 + j, sets)
+    for j in (0, 1, 2):
+        a = hs[j]
+        text = _text_for(j, 6 << 20, 40 + j, sets)
         t = _gpu.to_dev(text)
-        block, stages, kernel = hs[j].autotune(t, reps=2)
+        wpos, wids = _par.oracle_compact(sets[j], text)
+        base = a.tuning()
+        fb = base["filter_bytes"]
+        # the autotuner's smaller depths: one and two window codes fewer (8-bit
+        # codes: a hashed filter of 2 and 4 bits fewer)
+        shrink = 4 if j == 2 else 1 << a.info()["code_bits"]
+        for knobs in ({"filter_bytes": fb // shrink}, {"filter_bytes": fb // (shrink * shrink)},
+                      {"block": 256, "stages": 2}, {"block": 384, "stages": 4}, {"halo": 256}, {"per_thread": 4},
+                      {"filter_bytes": fb, "block": 512, "stages": base["stages"], "halo": 0, "per_thread": 0}):
+            a.set_tuning(**knobs)
+            _par.check_outputs(a.handle, t, text.size, wpos, wids, "automaton %d %s" % (j, knobs))
+        assert a.tuning() == base
+        block, stages, kernel = a.autotune(t, reps=2)
         assert block in (256, 384, 512) and stages in (0, 2, 3, 4)
-        assert kernel in (("tiled",) if j == 0 else ("thread_jump_l1", "thread_jump", "walk_slots"))
-        want = oracle.pfac_ids(sets[j], text[: 1 << 20])
-        got = _gpu.dense(hs[j].handle, t[: 1 << 20]).cpu().numpy()
-        assert np.array_equal(got, want)
+        assert kernel in (("tiled",) if j < 2 else ("tiled", "thread_jump_l1", "thread_jump", "walk_slots"))
+        tuned = a.tuning()
+        assert tuned["filter_bytes"] in (fb, fb // shrink, fb // (shrink * shrink))
+        _par.check_outputs(a.handle, t, text.size, wpos, wids, "automaton %d autotuned %s" % (j, tuned))

@@ -52,20 +52,7 @@ def sweep():
 
 def _all_outputs(a, t, n, wpos, wids, what):
     """Dense ids, count and compacted list of text t[:n] against the oracle's list."""
-    import torch
-
-    out = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
-    api.ac_match(a.handle, t, n, out)
-    _par.check_dense(out[:n], wpos, wids, what)
-    del out
-    cnt = torch.full((1,), 12345, dtype=torch.int64, device="cuda")
-    api.ac_count(a.handle, t, n, cnt)
-    assert int(cnt.item()) == wpos.size, (what, int(cnt.item()), wpos.size)
-    cap = max(1, wpos.size)
-    pos = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
-    ids = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
-    api.ac_match_compact(a.handle, t, n, pos, ids, cap, cnt)
-    _par.check_compact(pos, ids, int(cnt.item()), wpos, wids, what)
+    _par.check_outputs(a.handle, t, n, wpos, wids, what)
 
 
 def test_sweep_1gib_every_position(sweep):
