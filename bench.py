@@ -45,8 +45,8 @@ def kernel_name(info: dict, out_kind: str, kernel: str, phased: bool = False) ->
         return "pfac_simple"
     if info["code_bits"] <= 4 or kernel == "tiled":
         name = "pfac_filter_pipe"  # 8-bit codes: its hashed-filter form
-        if phased:  # long texts with 8-bit codes: the survivor and walk steps after it
-            name += "+pfac_survivors8+pfac_walks8"
+        if phased:  # long texts: the survivor and walk steps of the phased form after it
+            name += "+pfac_survivors+pfac_walks"
     else:
         name = {"thread_jump": "pfac_jump8", "walk_slots": "pfac_walk8"}.get(kernel, "pfac_jump8g")
     # the compacted list: the matcher in slot mode, then scan and gather; the
@@ -289,11 +289,20 @@ def replica_gbs(bytes_per_rank: float, steps: int, world: int, t_ms: float) -> f
 # ----------------------------------------------------------------------------
 def matching_launches(a, n: int, kernel: str, out_kind: str) -> int:
     """Kernels one matching call launches before any compaction: the filter
-    kernel, plus the survivor and walk steps of the phased form (8-bit codes
-    with the hashed filter, texts of 4 MiB or more, dense/count/compact)."""
-    phased = (kernel == "tiled" and out_kind in ("dense", "count", "compact") and a.info()["code_bits"] == 8
-              and a.tuning()["filter_bytes"] > 0 and n >= (4 << 20) and n // 992 < (1 << 22))
-    return 3 if phased else 1
+    kernel, plus the survivor and walk steps of its phased form (single texts
+    with dense, count or compacted output: 8-bit codes from 4 MiB on, 2- and
+    4-bit codes beyond the texts whose heavy tiles are shared within the CTA)."""
+    import torch
+
+    info, tun = a.info(), a.tuning()
+    if kernel != "tiled" or out_kind not in ("dense", "count", "compact") or tun["filter_bytes"] == 0:
+        return 1
+    if n // 992 >= (1 << 22) - 1:
+        return 1
+    if info["code_bits"] == 8:
+        return 3 if n >= (4 << 20) else 1
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    return 3 if n // 992 > 16 * sms * (tun["block"] // 32) else 1
 
 
 def run_ours(args, rank: int, world: int, local_rank: int):
@@ -512,7 +521,7 @@ def zipf_summary(steps: int, warmup: int) -> dict:
             "value": n / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms, "steps": steps, "matches": matches,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
                          "frac": achieved / peak, "algorithmic_bytes_per_step": n + 8 * matches},
-            "kernels": "pfac_filter_pipe (hashed filter, survivors listed) + pfac_survivors8 + scan + gather"}
+            "kernels": "pfac_filter_pipe (hashed filter, survivors listed) + pfac_survivors + pfac_walks + scan + gather"}
 
 
 def extra_figures(args) -> dict:

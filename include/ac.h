@@ -334,7 +334,13 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
  *                 ac_destroy, so launches captured before still read valid
  *                 tables.  AC_ERR_INVALID_ARG for an automaton without a
  *                 root filter, or a size below the smallest filter.
- *   reserved      0.
+ *   survivor_list how the filter kernel resolves its survivors on long single
+ *                 texts (dense, count, compacted): 0 = default (listed for a
+ *                 second kernel with 8-bit codes from 4 MiB on, else in the
+ *                 warp that filtered them, pipelined across its tiles); 1 =
+ *                 listed also for 2- and 4-bit codes (texts beyond those
+ *                 whose heavy tiles are shared within the CTA, about 38 MB
+ *                 at 512 threads on 152 SMs); 2 = always in the warp.
  * ac_set_tuning validates every field before changing any; do not call it
  * while work on h is being enqueued from another thread.  Batch plans and
  * servers read the tuning of their handles at each launch (a captured batch
@@ -346,7 +352,7 @@ typedef struct {
     uint32_t halo;
     uint32_t per_thread;
     uint32_t filter_bytes;
-    uint32_t reserved;
+    uint32_t survivor_list;
 } ac_tuning;
 
 ac_status ac_get_tuning(ac_handle h, ac_tuning *out);
@@ -487,8 +493,9 @@ ac_status ac_batch_destroy(ac_batch b);
  * ones (windows of one and two codes fewer, or a hashed filter of a quarter
  * and a sixteenth of the bits) -- x threads per CTA {256, 384, 512} x text
  * stages {2, 3, 4} (the shapes that fit shared memory); then, at the best of
- * those, the halo (16 bytes or the longest keyword, up to 256) and, for 8-bit
- * codes, chars per thread {2, 4}; with 8-bit codes also the kernels
+ * those, the halo (16 bytes or the longest keyword, up to 256), the survivor
+ * list on and off (when the sample is long enough for it) and, with the list,
+ * chars per thread {2, 4}; with 8-bit codes also the kernels
  * AC_KERNEL_THREAD_JUMP_L1, AC_KERNEL_THREAD_JUMP and AC_KERNEL_WALK_SLOTS (the
  * last with each shape).  Each candidate runs `reps` times (0 = 5) after one
  * warm-up; the median is compared.  Writes the choice to *block, *stages and

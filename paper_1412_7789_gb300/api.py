@@ -83,7 +83,7 @@ class ac_info_t(ctypes.Structure):
 
 class ac_tuning(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint32) for name in ("block", "stages", "halo", "per_thread", "filter_bytes",
-                                                     "reserved")]
+                                                     "survivor_list")]
 
 
 _lock = threading.Lock()
@@ -405,7 +405,7 @@ def ac_get_tuning(h: int) -> dict:
     """The filter kernel's launch shape for h (ac_tuning fields but reserved)."""
     t = ac_tuning()
     _check(lib().ac_get_tuning(h, ctypes.byref(t)), "ac_get_tuning")
-    return {name: int(getattr(t, name)) for name, _ in ac_tuning._fields_ if name != "reserved"}
+    return {name: int(getattr(t, name)) for name, _ in ac_tuning._fields_}
 
 
 def ac_set_tuning(h: int, **fields) -> None:

@@ -265,7 +265,7 @@ using pfac::scratch_pool;
 cudaError_t run_tiled(ac_automaton *h, pfac::MatchRequest r, pfac::OutMode mode, cudaStream_t st) {
     // 8-bit codes, long text: the phased form's lists after the counter
     pfac::SurvivorLists sl;
-    if (!r.batch && pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, r.n);
+    if (!r.batch && pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, h->tuning, r.n);
     const bool le = sl.list_cap != 0;
     if (!r.batch && r.n <= (16u << 20) && !le) {
         pfac::MatchRequest r0 = r;
@@ -299,7 +299,7 @@ cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const 
     if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
     // 8-bit codes, long text: room for the phased form's lists too
     pfac::SurvivorLists sl;
-    if (pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, n);
+    if (pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, h->tuning, n);
     const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, true) + sl.bytes();
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);
@@ -665,6 +665,7 @@ ac_status ac_get_tuning(ac_handle h, ac_tuning *out) {
     out->halo = h->tuning.halo > 16 ? static_cast<uint32_t>(h->tuning.halo) : 16u;
     out->per_thread = h->tuning.per_thread == 4 ? 4u : 2u;
     out->filter_bytes = has_root(h->host) ? static_cast<uint32_t>(h->host.F.size() * sizeof(uint32_t)) : 0u;
+    out->survivor_list = static_cast<uint32_t>(h->tuning.survivor_list);
     return AC_OK;
 }
 
@@ -672,7 +673,7 @@ ac_status ac_set_tuning(ac_handle h, const ac_tuning *tu) {
     if (!h || !tu) return AC_ERR_INVALID_ARG;
     if (tu->block < 32 || tu->block > 512 || (tu->block & 31u) || (tu->stages != 0 && (tu->stages < 2 || tu->stages > 4)) ||
         tu->halo > pfac::kHaloCap || (tu->per_thread != 0 && tu->per_thread != 2 && tu->per_thread != 4) ||
-        tu->reserved != 0)
+        tu->survivor_list > 2)
         return AC_ERR_INVALID_ARG;
     if (tu->filter_bytes != 0) {
         if (!has_root(h->host)) return AC_ERR_INVALID_ARG;
@@ -685,6 +686,7 @@ ac_status ac_set_tuning(ac_handle h, const ac_tuning *tu) {
     h->tuning.stages = static_cast<int>(tu->stages);
     h->tuning.halo = static_cast<int>(tu->halo);
     h->tuning.per_thread = static_cast<int>(tu->per_thread);
+    h->tuning.survivor_list = static_cast<int>(tu->survivor_list);
     return AC_OK;
 }
 
@@ -1012,6 +1014,7 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
         tu.grid = 0;
         tu.halo = 0;
         tu.per_thread = 0;
+        tu.survivor_list = 0;
         if (v == 2 || v == 3) {
             time_one(tu);
             continue;
@@ -1027,24 +1030,33 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
                 }
         }
     }
-    // at the best shape: the halo, and chars per thread of the survivor step
+    // at the best shape: the halo, how survivors are resolved on long texts
+    // (listed for a second kernel or in the warp), and chars per thread of
+    // that second kernel
     if (e == cudaSuccess && fail == AC_OK && best.variant == 0 && root) {
         fail = use_root(h, best_key);
         const pfac::Tuning base = best;
         const int hmax = static_cast<int>(std::min<uint32_t>(pfac::kHaloCap, (h->host.maxlen + 15u) & ~15u));
         std::vector<int> halos{0};
         if (hmax > 16) halos.push_back(hmax);
-        std::vector<int> pts{0};
-        if (h->host.hashed && n >= (4u << 20)) pts.push_back(4);
+        pfac::Tuning listed = base;
+        listed.survivor_list = 1;
+        const bool can_list = pfac::filter_phased(h->dev, listed, n);
+        // 8-bit codes list by default, small alphabets try it
+        std::vector<int> lists{0};
+        if (can_list) lists.push_back(h->host.hashed ? 2 : 1);
         for (int hv : halos)
-            for (int pt : pts) {
-                if (hv == 0 && pt == 0) continue;  // timed above
-                if (fail != AC_OK) break;
-                pfac::Tuning tu = base;
-                tu.halo = hv;
-                tu.per_thread = pt;
-                time_one(tu);
-            }
+            for (int sl : lists)
+                for (int pt : {0, 4}) {
+                    if (hv == 0 && sl == 0 && pt == 0) continue;  // timed above
+                    if (pt == 4 && !(can_list && (h->host.hashed ? sl == 0 : sl == 1))) continue;  // no second kernel
+                    if (fail != AC_OK) break;
+                    pfac::Tuning tu = base;
+                    tu.halo = hv;
+                    tu.survivor_list = sl;
+                    tu.per_thread = pt;
+                    time_one(tu);
+                }
     }
     if (e == cudaSuccess && fail == AC_OK) {
         if (root) fail = use_root(h, best_key);

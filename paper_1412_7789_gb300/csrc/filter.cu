@@ -97,7 +97,7 @@ cudaError_t fill_params(const DevTables &t, const MatchRequest &r, OutMode mode,
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;
-    if (hashed && !batch && r.list && r.list_count && r.list_cap && p.ntiles < (1u << 22)) {
+    if (!batch && r.list && r.list_count && r.list_cap && p.ntiles < (1u << 22)) {
         p.list = r.list;
         p.list_count = r.list_count;
         p.list_cap = r.list_cap;
@@ -160,6 +160,19 @@ cudaError_t device_shape(DeviceShape *out) {
 
 }  // namespace
 
+bool filter_phased(const DevTables &t, const Tuning &tu, uint64_t n) {
+    if (!served(t) || n / kTile >= (1ull << 22) - 1 || tu.survivor_list == 2) return false;
+    if (t.B == 8) return n >= (4ull << 20);
+    if (tu.survivor_list != 1) return false;
+    // small alphabets: beyond the texts that take the forms sharing heavy
+    // tiles within the CTA (the launcher's test, with the most tiles the
+    // text's alignment can give)
+    const uint64_t sms = device_sm_count();
+    if (sms == 0 || tu.block < 32) return false;
+    const uint64_t grid = tu.grid > 0 ? static_cast<uint64_t>(tu.grid) : sms, nw = static_cast<uint64_t>(tu.block) / 32;
+    return n / kTile > static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw;
+}
+
 uint32_t device_sm_count() {
     DeviceShape ds;
     if (device_shape(&ds) != cudaSuccess) {
@@ -195,21 +208,22 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     if (grid == 0) return cudaSuccess;
     // a text short next to the grid: its heavy tiles (many survivors, long
     // walks) would be one warp's work each while most warps have run out of
-    // tiles, so those forms share them within the CTA (small alphabets)
-    if (!batch && t.B <= 4 &&
+    // tiles, so those forms share them within the CTA (small alphabets; the
+    // phased form lists heavy tiles like any other)
+    if (!batch && t.B <= 4 && !p.list &&
         static_cast<uint64_t>(p.ntiles) <= static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw)
         return launch_filter_help(mode, p, t.B, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
-    if (t.B == 8) {
+    if (t.B == 8)
         e = launch_filter8(mode, p, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
-        if (e == cudaSuccess && p.list) e = launch_survivors8(mode, p, t.gbits, static_cast<uint32_t>(ds.sms), tu.per_thread, stream);
-        return e;
-    }
-    if (t.B == 2) {
-        if (t.gbits == 16) return launch_modes<2, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
-        return launch_modes<2, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
-    }
-    if (t.gbits == 16) return launch_modes<4, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
-    return launch_modes<4, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+    else if (t.B == 2)
+        e = t.gbits == 16 ? launch_modes<2, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream)
+                          : launch_modes<2, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+    else
+        e = t.gbits == 16 ? launch_modes<4, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream)
+                          : launch_modes<4, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+    if (e == cudaSuccess && p.list)
+        e = launch_survivors(mode, p, t.B, t.gbits, static_cast<uint32_t>(ds.sms), tu.per_thread, stream);
+    return e;
 }
 
 bool filter_multi_serves(const DevTables *const *ts, uint32_t nh) {

@@ -13,13 +13,4 @@ cudaError_t launch_filter8(OutMode mode, const filt::FilterParams &p, uint32_t g
                        : launch_modes<8, int32_t, false>(mode, p, grid, block, smem, max_smem, stream);
 }
 
-cudaError_t launch_survivors8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t sms, int per_thread,
-                              cudaStream_t stream) {
-    if (per_thread == 4)
-        return gbits == 16 ? filt::launch_survivors8<int16_t, 4>(mode, p, sms, stream)
-                           : filt::launch_survivors8<int32_t, 4>(mode, p, sms, stream);
-    return gbits == 16 ? filt::launch_survivors8<int16_t, 2>(mode, p, sms, stream)
-                       : filt::launch_survivors8<int32_t, 2>(mode, p, sms, stream);
-}
-
 }  // namespace pfac

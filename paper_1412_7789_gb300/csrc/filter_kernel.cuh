@@ -1101,11 +1101,15 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
         }
         __syncwarp();
 
-        if constexpr (B == 8 && !BATCH) {
-            // two-phase form: the tile's survivors go to the list (their
-            // windows with them) and the tile counts as one without survivors
-            // here; a window past the text end, or no room, keeps them here
-            if (p.list && !lfull && total > 0 && !__any_sync(kFull, (slowm & sv) != 0u)) {
+        if constexpr (!BATCH) {
+            // phased form: the tile's survivors go to the list (their windows
+            // with them) and the tile counts as one without survivors here.
+            // With 8-bit codes a window past the text end keeps them here;
+            // with 2- and 4-bit codes any tile but an interior one of keyword
+            // bytes only (whose windows and stride windows are all known);
+            // and so does no room.
+            const bool listable = B == 8 ? !__any_sync(kFull, (slowm & sv) != 0u) : interior && clean;
+            if (p.list && !lfull && total > 0 && listable) {
                 if (lend - lnext < total) {
                     // a new chunk of list space (the rest of the old one: empty)
                     for (uint32_t j = lnext + static_cast<uint32_t>(lane); j < lend; j += 32u)
@@ -1127,13 +1131,19 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                 if (!lfull) {
                     for (uint32_t j = static_cast<uint32_t>(lane); j < total; j += 32u) {
                         const uint32_t i = w.queue[j] & 0x7FFFu;
-                        // the code after the window (0x100: the text ends, or a
-                        // byte in no keyword); i + k < kCodeSpan
-                        const uint32_t ja = i + k;
-                        const uint32_t ca = ((w.inv[ja >> 4] >> (ja & 15u)) & 1u)
-                                                ? 0x100u
-                                                : (w.packed[ja >> 2] >> (8u * (ja & 3u))) & 0xFFu;
-                        p.list[lnext + j] = make_uint4((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask, ca, 0u);
+                        if constexpr (B == 8) {
+                            // the code after the window (0x100: the text ends, or a
+                            // byte in no keyword); i + k < kCodeSpan
+                            const uint32_t ja = i + k;
+                            const uint32_t ca = ((w.inv[ja >> 4] >> (ja & 15u)) & 1u)
+                                                    ? 0x100u
+                                                    : (w.packed[ja >> 2] >> (8u * (ja & 3u))) & 0xFFu;
+                            p.list[lnext + j] =
+                                make_uint4((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask, ca, 0u);
+                        } else {
+                            // the window's and the stride window's codes (i + k + k2 < kCodeSpan)
+                            p.list[lnext + j] = make_uint4((tile << 10) | i, code_window<B>(w.packed, i), 0u, 0u);
+                        }
                     }
                     lnext += total;
                     total = 0;
@@ -1322,7 +1332,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     flight_finish<B, GT>(p, wk, w.cls8, f1);
     flight_output<MODE>(p, wk, w, f1, lane, cnt);
     // phased form: the unfilled rest of this warp's list chunk is empty
-    if (B == 8 && p.list)
+    if (!BATCH && p.list)
         for (uint32_t j = lnext + static_cast<uint32_t>(lane); j < lend; j += 32u)
             p.list[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     // the stages issued past this warp's last unit hold end marks (an arrival
@@ -1392,16 +1402,18 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
     }
 }
 
-// The second phase of the two-phase form (one text, 8-bit codes): one thread
-// per listed survivor, SPT at a time so that their loads overlap, at high
-// occupancy (48 warps per SM with 2 at a time, 32 with 4).  Each survivor's state-hash entry settles most survivors; a walk
-// from a depth-k state with several children takes its first goto step here
-// (the code after the window is in the entry), which ends most of them; the
-// walks left go to the walk list for the third step (it has room for all of
-// them; were it ever full, the error word says so).  Ids found go to the
-// dense output (its -1 are written by
-// the first phase), the count, or the unit's slots (no dense fallback: the
-// gather step matches a unit with more matches than slots again).
+// The second phase of the phased form (one long text): one thread per listed
+// survivor, SPT at a time so that their loads overlap, at high occupancy (48
+// warps per SM with 2 at a time, 32 with 4).  8-bit codes: the survivor's
+// state-hash entry settles most survivors; a walk from a depth-k state with
+// several children takes its first goto step here (the code after the window
+// is in the entry), which ends most of them.  2- and 4-bit codes: the window
+// table, then the stride table (the codes of both windows are in the entry).
+// The walks left go to the walk list for the third step (it has room for all
+// of them; were it ever full, the error word says so).  Ids found go to the
+// dense output (its -1 are written by the first phase), the count, or the
+// unit's slots (no dense fallback: the gather step matches a unit with more
+// matches than slots again).
 constexpr int kSurvBlock = 256;
 template <int SPT>
 __host__ __device__ constexpr int surv_ctas() { return SPT <= 2 ? 6 : 4; }
@@ -1409,8 +1421,8 @@ static_assert(surv_ctas<2>() * kSurvBlock / 32 <= static_cast<int>(kSurvWarpsPer
                   surv_ctas<4>() * kSurvBlock / 32 <= static_cast<int>(kSurvWarpsPerSm),
               "the walk list's room assumes at most kSurvWarpsPerSm warps of step 2 per SM");
 
-template <typename GT, int MODE, int SPT>
-__global__ void __launch_bounds__(kSurvBlock, surv_ctas<SPT>()) pfac_survivors8(const __grid_constant__ FilterParams p) {
+template <int B, typename GT, int MODE, int SPT>
+__global__ void __launch_bounds__(kSurvBlock, surv_ctas<SPT>()) pfac_survivors(const __grid_constant__ FilterParams p) {
     const int lane = threadIdx.x & 31;
     const GT *G = static_cast<const GT *>(p.G);
     const uint32_t listed = *reinterpret_cast<volatile const unsigned int *>(p.list_count);
@@ -1424,41 +1436,86 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<SPT>()) pfac_survivors8(
     // warp-wide): the loop runs on the warp's first index
     for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < m; wb += SPT * stride) {
         const uint32_t b0 = wb + static_cast<uint32_t>(lane);
-        uint4 e[SPT], he[SPT];
-#pragma unroll
-        for (int t = 0; t < SPT; ++t) {
-            const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
-            e[t] = idx < m ? __ldg(p.list + idx) : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
-            he[t] = make_uint4(0u, 0u, 0u, 0u);
-            if (e[t].x != 0xFFFFFFFFu) he[t] = __ldg(p.HK + hk_slot(p, e[t].y));
-        }
-        // outcomes; the first step of the walks from a branching state
-        int r[SPT], g[SPT];
+        uint4 e[SPT];
+        int r[SPT];
         uint32_t s[SPT], q[SPT];
         bool walk[SPT];
+        if constexpr (B == 8) {
+            uint4 he[SPT];
 #pragma unroll
-        for (int t = 0; t < SPT; ++t) {
-            const bool on = e[t].x != 0xFFFFFFFFu;
-            const uint32_t i = e[t].x & 1023u, c = e[t].z;  // c: the code after the window (0x100: none)
-            r[t] = -1;
-            s[t] = 0;
-            q[t] = 0;
-            walk[t] = on && !hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c & 0xFFu, c < 0x100u, r[t], s[t], q[t]);
-            if (walk[t]) r[t] = -1;  // its id comes from the walk
-            // (every state has its goto row; the chain records only shortcut runs)
-            g[t] = 0;
-            if (walk[t] && q[t] == i + p.k) g[t] = goto_ld(G, s[t], p.W, c < 0x100u ? c : p.C);
-        }
+            for (int t = 0; t < SPT; ++t) {
+                const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
+                e[t] = idx < m ? __ldg(p.list + idx) : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                he[t] = make_uint4(0u, 0u, 0u, 0u);
+                if (e[t].x != 0xFFFFFFFFu) he[t] = __ldg(p.HK + hk_slot(p, e[t].y));
+            }
+            // outcomes; the first step of the walks from a branching state
+            int g[SPT];
 #pragma unroll
-        for (int t = 0; t < SPT; ++t) {
-            const uint32_t i = e[t].x & 1023u;
-            if (walk[t] && q[t] == i + p.k) {
-                if (g[t] < 0) {
-                    r[t] = decode_dead(g[t]);
-                    walk[t] = false;
+            for (int t = 0; t < SPT; ++t) {
+                const bool on = e[t].x != 0xFFFFFFFFu;
+                const uint32_t i = e[t].x & 1023u, c = e[t].z;  // c: the code after the window (0x100: none)
+                r[t] = -1;
+                s[t] = 0;
+                q[t] = 0;
+                walk[t] = on && !hk_outcome(p, hk_find(p, e[t].y, he[t]), i, c & 0xFFu, c < 0x100u, r[t], s[t], q[t]);
+                if (walk[t]) r[t] = -1;  // its id comes from the walk
+                // (every state has its goto row; the chain records only shortcut runs)
+                g[t] = 0;
+                if (walk[t] && q[t] == i + p.k) g[t] = goto_ld(G, s[t], p.W, c < 0x100u ? c : p.C);
+            }
+#pragma unroll
+            for (int t = 0; t < SPT; ++t) {
+                const uint32_t i = e[t].x & 1023u;
+                if (walk[t] && q[t] == i + p.k) {
+                    if (g[t] < 0) {
+                        r[t] = decode_dead(g[t]);
+                        walk[t] = false;
+                    } else {
+                        s[t] = static_cast<uint32_t>(g[t]);
+                        ++q[t];
+                    }
+                }
+            }
+        } else {
+            // the window table, then the stride table
+            const uint32_t kmask = (1u << (B * p.k)) - 1u, k2mask = (1u << (B * p.k2)) - 1u;
+            int j1[SPT], j2[SPT];
+#pragma unroll
+            for (int t = 0; t < SPT; ++t) {
+                const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
+                e[t] = idx < m ? __ldg(p.list + idx) : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+                j1[t] = e[t].x != 0xFFFFFFFFu ? __ldg(p.JK + (e[t].y & kmask)) : -1;
+            }
+#pragma unroll
+            for (int t = 0; t < SPT; ++t) {
+                const uint32_t i = e[t].x & 1023u;
+                r[t] = -1;
+                s[t] = 0;
+                q[t] = 0;
+                walk[t] = false;
+                j2[t] = -1;
+                if (e[t].x == 0xFFFFFFFFu) continue;
+                if (j1[t] < 0) {
+                    r[t] = decode_dead(j1[t]);
+                } else if (p.k2) {
+                    j2[t] = __ldg(p.J2 + ((static_cast<uint64_t>(static_cast<uint32_t>(j1[t]) - p.base_k) << (B * p.k2)) |
+                                          ((e[t].y >> (B * p.k)) & k2mask)));
                 } else {
-                    s[t] = static_cast<uint32_t>(g[t]);
-                    ++q[t];
+                    walk[t] = true;
+                    s[t] = static_cast<uint32_t>(j1[t]);
+                    q[t] = i + p.k;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < SPT; ++t) {
+                if (e[t].x == 0xFFFFFFFFu || j1[t] < 0 || !p.k2) continue;
+                if (j2[t] < 0) {
+                    r[t] = decode_dead(j2[t]);
+                } else {
+                    walk[t] = true;
+                    s[t] = static_cast<uint32_t>(j2[t]);
+                    q[t] = (e[t].x & 1023u) + p.k + p.k2;
                 }
             }
         }
@@ -1491,7 +1548,7 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<SPT>()) pfac_survivors8(
                     wnext += need;
                 }
                 if (walk[t] && wend != 0 && slot < p.walk_cap)
-                    p.walks[slot] = make_uint2(e[t].x, s[t] | ((q[t] - i - p.k) << 31));
+                    p.walks[slot] = make_uint2(e[t].x, s[t] | ((q[t] - i - p.k - p.k2) << 31));
             }
             const int rr = r[t];
             if (e[t].x == 0xFFFFFFFFu || rr < 0) continue;
@@ -1520,7 +1577,7 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<SPT>()) pfac_survivors8(
 // The third step of the phased form: one thread per listed walk (state, next
 // byte) at high occupancy; the ids found go out as in the second step.
 template <typename GT, int MODE>
-__global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks8(const __grid_constant__ FilterParams p) {
+__global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks(const __grid_constant__ FilterParams p) {
     __shared__ uint8_t cls8[256];
     const int lane = threadIdx.x & 31;
     for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) cls8[i] = __ldg(p.cls8g + i);
@@ -1535,7 +1592,7 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks8(const 
         const uint32_t unit = e.x >> 10, i = e.x & 1023u;
         const int64_t gpb = static_cast<int64_t>(unit) * kTile - head;
         const int r = walk_global<GT>(p, cls8, make_text(p.text, p.out, p.n, unit), gpb, e.y & 0x7FFFFFFFu,
-                                      i + p.k + (e.y >> 31));
+                                      i + p.k + p.k2 + (e.y >> 31));
         if (r < 0) continue;
         if (MODE == OUT_DENSE) {
             p.out[gpb + i] = r;
@@ -1556,22 +1613,22 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks8(const 
     }
 }
 
-template <typename GT, int SPT>
-cudaError_t launch_survivors8(OutMode mode, const FilterParams &p, uint32_t sms, cudaStream_t stream) {
+template <int B, typename GT, int SPT>
+cudaError_t launch_survivors(OutMode mode, const FilterParams &p, uint32_t sms, cudaStream_t stream) {
     const uint32_t grid = sms * static_cast<uint32_t>(surv_ctas<SPT>());
     switch (mode) {
-        case OUT_DENSE: pfac_survivors8<GT, OUT_DENSE, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
-        case OUT_COUNT: pfac_survivors8<GT, OUT_COUNT, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
-        case OUT_SLOTS: pfac_survivors8<GT, OUT_SLOTS, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_DENSE: pfac_survivors<B, GT, OUT_DENSE, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_COUNT: pfac_survivors<B, GT, OUT_COUNT, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_SLOTS: pfac_survivors<B, GT, OUT_SLOTS, SPT><<<grid, kSurvBlock, 0, stream>>>(p); break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !p.walks) return e;
     const uint32_t wgrid = sms * static_cast<uint32_t>(surv_ctas<2>());
     switch (mode) {
-        case OUT_DENSE: pfac_walks8<GT, OUT_DENSE><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
-        case OUT_COUNT: pfac_walks8<GT, OUT_COUNT><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
-        default: pfac_walks8<GT, OUT_SLOTS><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_DENSE: pfac_walks<GT, OUT_DENSE><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
+        case OUT_COUNT: pfac_walks<GT, OUT_COUNT><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
+        default: pfac_walks<GT, OUT_SLOTS><<<wgrid, kSurvBlock, 0, stream>>>(p); break;
     }
     return cudaGetLastError();
 }
@@ -1691,9 +1748,10 @@ cudaError_t launch_filter_help(OutMode mode, const filt::FilterParams &p, uint32
 // their two-phase form, filter8.cu.
 cudaError_t launch_filter8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t grid, uint32_t block,
                            uint32_t smem, int max_smem, cudaStream_t stream);
-// per_thread: survivors a thread of the second step takes at a time (2 or 4)
-cudaError_t launch_survivors8(OutMode mode, const filt::FilterParams &p, uint32_t gbits, uint32_t sms, int per_thread,
-                              cudaStream_t stream);
+// The second and third steps of the phased form (survivors.cu); per_thread:
+// survivors a thread of the second step takes at a time (2 or 4; 8-bit codes).
+cudaError_t launch_survivors(OutMode mode, const filt::FilterParams &p, uint32_t B, uint32_t gbits, uint32_t sms,
+                             int per_thread, cudaStream_t stream);
 
 namespace filt {
 template <int MODE>

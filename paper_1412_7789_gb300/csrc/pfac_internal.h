@@ -241,9 +241,9 @@ struct MatchRequest {
     SlotOut slots;                           // OUT_SLOTS
     void *scratch = nullptr;                 // zeroed: tile counter (16 bytes)
     size_t scratch_bytes = 0;
-    // One text, 8-bit codes (hashed filter): the lists of the phased form
-    // (survivor_lists); list = nullptr: every tile's survivors are resolved
-    // by the warp that filtered it.
+    // One long text: the lists of the phased form (survivor_lists); list =
+    // nullptr: every tile's survivors are resolved by the warp that filtered
+    // it.
     uint4 *list = nullptr;
     unsigned int *list_count = nullptr;      // zeroed, two words: survivors, walks
     uint32_t list_cap = 0;
@@ -251,36 +251,46 @@ struct MatchRequest {
     uint32_t walk_cap = 0;
 };
 
-// The phased form of the filter kernel for one text with 8-bit codes:
+// The phased form of the filter kernel for one long text:
 //   1. the filter kernel stages, filters and writes the -1 of every tile, and
-//      appends each survivor to a list -- {(tile << 10) | tile position,
-//      window, code of the character after it (0x100: none), 0} -- instead of
-//      resolving it;
-//   2. one thread per survivor at full occupancy loads its state-hash entry,
-//      settles most survivors and writes the ids found; a survivor whose walk
-//      goes on is appended to a second list -- {(tile << 10) | position,
-//      state | d << 31}, the walk's next byte at tile index position + k + d
-//      (d = 1 when the state hash already took the byte after the window);
+//      appends each survivor to a list instead of resolving it -- 8-bit
+//      codes: {(tile << 10) | tile position, window, code of the character
+//      after it (0x100: none), 0}; 2- and 4-bit codes: {(tile << 10) |
+//      position, the codes from the position on (window and stride
+//      window), 0, 0};
+//   2. one thread per survivor at full occupancy resolves it -- 8-bit codes:
+//      its state-hash entry, and for a branching state the first goto step;
+//      2- and 4-bit codes: the window table, then the stride table -- and
+//      writes the ids found; a survivor whose walk goes on is appended to a
+//      second list -- {(tile << 10) | position, state | d << 31}, the walk's
+//      next byte at tile index position + k + k2 + d;
 //   3. one thread per walk, at full occupancy, finishes the walks.
 // Warps reserve list space in chunks (entries they leave unused are marked
-// empty: x = 0xFFFFFFFF).  A tile whose survivors do not fit, or that holds a
-// window past the text end, is resolved by its warp as in the one-phase form.
-// The walk list has room for one walk per listed survivor plus a chunk per
-// warp of step 2 (a warp leaves entries unused only in its last chunk), so
-// every walk fits.
-constexpr uint32_t kWalkChunkEntries = 256;  // walk-list entries a warp of step 2 reserves at a time
+// empty: x = 0xFFFFFFFF).  A tile whose survivors do not fit -- or, with
+// 8-bit codes, that holds a window past the text end; with 2- and 4-bit
+// codes, any tile but an interior one of keyword bytes only -- is resolved
+// by its warp as in the one-phase form.  The walk list has room for one walk
+// per listed survivor plus a chunk per warp of step 2 (a warp leaves entries
+// unused only in its last chunk), so every walk fits.
+constexpr uint32_t kWalkChunkEntries = 64;   // walk-list entries a warp of step 2 reserves at a time
 constexpr uint32_t kSurvWarpsPerSm = 48;     // most warps of step 2 resident on one SM
 uint32_t device_sm_count();                  // of the current device (cached; 0 on error)
+struct Tuning;
+// Whether the filter kernel takes the phased form for a text of n bytes
+// (filter.cu): 8-bit codes from 4 MiB on; 2- and 4-bit codes, when the
+// tuning asks for it, beyond the texts short enough for the forms that share
+// heavy tiles within the CTA.  Never for texts of more tiles than the entries
+// can name.
+bool filter_phased(const DevTables &t, const Tuning &tu, uint64_t n);
 struct SurvivorLists {
     uint32_t list_cap = 0, walk_cap = 0;
     size_t bytes() const { return list_cap ? 32 + 16ull * list_cap + 8ull * walk_cap : 0; }
 };
-// The lists of a text of n bytes (none: the one-phase form, for short texts
-// and for texts of more tiles than the entries can name).  Scratch layout:
-// two counters (32 bytes, zeroed) | list_cap uint4 | walk_cap uint2.
-inline SurvivorLists survivor_lists(const DevTables &t, uint64_t n) {
+// The lists of a text of n bytes (none: the one-phase form).  Scratch
+// layout: two counters (32 bytes, zeroed) | list_cap uint4 | walk_cap uint2.
+inline SurvivorLists survivor_lists(const DevTables &t, const Tuning &tu, uint64_t n) {
     SurvivorLists s;
-    if (!t.hashed || n < (4ull << 20) || n / 992 >= (1ull << 22)) return s;
+    if (!filter_phased(t, tu, n)) return s;
     const uint64_t sms = device_sm_count();
     if (sms == 0) return s;
     s.list_cap = static_cast<uint32_t>(n / 8);  // 12.5 % of the positions
@@ -310,6 +320,8 @@ struct Tuning {
                           // step takes at a time (2, or 4 with fewer threads; 0 = 2)
     int halo = 0;         // bytes staged after each tile: 0 = the 16 the filter reads,
                           // or up to kHaloCap (a wider halo reaches L2 ahead of the walks)
+    int survivor_list = 0;  // long single texts: 0 = the phased form for 8-bit codes only,
+                            // 1 = also for 2- and 4-bit codes, 2 = never
     unsigned long long wait_ns = 0;  // bounded waits give up after this (0 = kWaitNs)
     int stall_help = 0;   // test aid: owners wait for one chunk more than their heavy tile has
 };

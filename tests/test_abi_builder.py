@@ -506,13 +506,14 @@ def test_shared_table_depth(lib, alpha, lmin, lmax):
             seen.append(k)
         assert seen[-1] == k0 and seen[0] == k0 - 1 and len(set(seen)) >= 3
         before = au.tuning()
-        for bad in ({"filter_bytes": 8}, {"block": 48}, {"stages": 5}, {"per_thread": 3}, {"halo": 512}):
+        for bad in ({"filter_bytes": 8}, {"block": 48}, {"stages": 5}, {"per_thread": 3}, {"halo": 512},
+                    {"survivor_list": 3}):
             with pytest.raises(api.AcError):
                 au.set_tuning(**bad)
             assert au.tuning() == before
-        au.set_tuning(block=256, stages=2, halo=64, per_thread=4)
+        au.set_tuning(block=256, stages=2, halo=64, per_thread=4, survivor_list=1)
         t = au.tuning()
-        assert (t["block"], t["stages"], t["halo"], t["per_thread"]) == (256, 2, 64, 4)
+        assert (t["block"], t["stages"], t["halo"], t["per_thread"], t["survivor_list"]) == (256, 2, 64, 4, 1)
 
 
 def test_shared_table_depth_hashed(lib):

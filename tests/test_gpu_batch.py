@@ -245,7 +245,9 @@ def test_autotune_keeps_results(automata):
         shrink = 4 if j == 2 else 1 << a.info()["code_bits"]
         for knobs in ({"filter_bytes": fb // shrink}, {"filter_bytes": fb // (shrink * shrink)},
                       {"block": 256, "stages": 2}, {"block": 384, "stages": 4}, {"halo": 256}, {"per_thread": 4},
-                      {"filter_bytes": fb, "block": 512, "stages": base["stages"], "halo": 0, "per_thread": 0}):
+                      {"survivor_list": 2}, {"survivor_list": 1},
+                      {"filter_bytes": fb, "block": 512, "stages": base["stages"], "halo": 0, "per_thread": 0,
+                       "survivor_list": 0}):
             a.set_tuning(**knobs)
             _par.check_outputs(a.handle, t, text.size, wpos, wids, "automaton %d %s" % (j, knobs))
         assert a.tuning() == base

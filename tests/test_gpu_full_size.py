@@ -56,10 +56,17 @@ def _all_outputs(a, t, n, wpos, wids, what):
 
 
 def test_sweep_1gib_every_position(sweep):
-    """The benchmark's step (ac_match on the 1 GiB text, default launch)."""
+    """The benchmark's step (ac_match on the 1 GiB text, default launch:
+    survivors resolved in the warps), and the same with the survivors listed
+    for the second kernel."""
     text, pats, wpos, wids, t, a = sweep
     assert wpos.size > 1000
     _all_outputs(a, t, text.size, wpos, wids, "1 GiB")
+    a.set_tuning(survivor_list=1)
+    try:
+        _all_outputs(a, t, text.size, wpos, wids, "1 GiB, survivors listed")
+    finally:
+        a.set_tuning(survivor_list=0)
 
 
 def test_sweep_sizes_every_position(sweep):
@@ -72,17 +79,23 @@ def test_sweep_sizes_every_position(sweep):
 def test_shared_and_plain_forms_boundary(sweep):
     """Texts of exactly the largest tile count that takes the forms sharing
     heavy tiles within the CTA (16 tiles per warp of the grid), one tile
-    fewer and one more (plain forms), each with a ragged last tile; the heavy
-    tiles of the sweep set's first 4 KiB run in both forms."""
+    fewer, one and two more (plain forms; with the survivor list asked for,
+    two more is the first that lists them for the second kernel), each with a
+    ragged last tile; the heavy tiles of the sweep set's first 4 KiB run in
+    every form."""
     import torch
 
     text, pats, wpos, wids, t, a = sweep
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     edge = HELP_TILES_PER_WARP * sms * WARPS_PER_CTA
-    for tiles in (edge - 1, edge, edge + 1):
+    for tiles, listed in ((edge - 1, 0), (edge, 0), (edge + 1, 0), (edge + 2, 0), (edge + 1, 1), (edge + 2, 1)):
         n = tiles * TILE - 37
         p, i = _par.window_compact(wpos, wids, pats, text, 0, n)
-        _all_outputs(a, t[:n], n, p, i, "%d tiles" % tiles)
+        a.set_tuning(survivor_list=listed)
+        try:
+            _all_outputs(a, t[:n], n, p, i, "%d tiles, survivor list %d" % (tiles, listed))
+        finally:
+            a.set_tuning(survivor_list=0)
 
 
 @pytest.fixture(scope="module")
@@ -122,6 +135,38 @@ def test_match_host_every_position():
         p, i = _par.window_compact(wpos, wids, pats, text, 0, small.size)
         got = a.match_host(torch.from_numpy(small.copy()))
         _par.check_dense(got, p, i, "host small")
+
+
+@pytest.mark.parametrize("kind", ["short_keywords", "dense_matches"])
+def test_phased_small_alphabet_and_list_overflow(kind):
+    """2- and 4-bit codes on texts long enough for the phased form (asked
+    for with the survivor_list knob): ACGT
+    keywords of 1-3 bytes (nearly every position survives, so the survivor
+    list fills and most tiles fall back to their warps), and a 12-letter set
+    whose windows often reach the stride table and beyond (the walk list),
+    with non-keyword bytes sprinkled in (tiles that stay with their warps).
+    Dense ids, count and compacted list, every position, against the oracle."""
+    import torch
+
+    g = np.random.default_rng(31)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = (HELP_TILES_PER_WARP * sms * WARPS_PER_CTA + 300) * TILE + 77
+    if kind == "short_keywords":
+        text = workloads.acgt_text(n, 32)
+        acgt = np.frombuffer(b"ACGT", dtype=np.uint8)
+        pats = [bytes(acgt[g.integers(0, 4, size=int(g.integers(1, 4)))]) for _ in range(60)]
+    else:
+        alpha = np.frombuffer(b"abcdefghijkl", dtype=np.uint8)
+        text = alpha[g.integers(0, 3, size=n)].copy()  # three letters: long walks
+        text[g.integers(0, n, size=n // 5000)] = ord("z")
+        pats = [bytes(alpha[g.integers(0, 3, size=int(g.integers(6, 30)))]) for _ in range(2000)]
+        pats += [bytes(alpha[g.integers(0, 12, size=int(g.integers(2, 9)))]) for _ in range(500)]
+    wpos, wids = _par.oracle_compact(pats, text)
+    t = _gpu_tensor(text)
+    with api.Automaton(pats) as a:
+        assert a.info()["code_bits"] in (2, 4)
+        a.set_tuning(survivor_list=1)
+        _all_outputs(a, t, text.size, wpos, wids, kind)
 
 
 @pytest.mark.parametrize("kind", ["short_keywords", "zipf_sparse"])
