@@ -290,17 +290,20 @@ def replica_gbs(bytes_per_rank: float, steps: int, world: int, t_ms: float) -> f
 def matching_launches(a, n: int, kernel: str, out_kind: str) -> int:
     """Kernels one matching call launches before any compaction: the filter
     kernel, plus the survivor and walk steps of its phased form (single texts
-    with dense, count or compacted output: 8-bit codes from 4 MiB on, 2- and
-    4-bit codes beyond the texts whose heavy tiles are shared within the CTA)."""
+    with dense, count or compacted output: 8-bit codes from 4 MiB on unless
+    the tuning says never, 2- and 4-bit codes when the tuning asks for it,
+    beyond the texts whose heavy tiles are shared within the CTA)."""
     import torch
 
     info, tun = a.info(), a.tuning()
     if kernel != "tiled" or out_kind not in ("dense", "count", "compact") or tun["filter_bytes"] == 0:
         return 1
-    if n // 992 >= (1 << 22) - 1:
+    if n // 992 >= (1 << 22) - 1 or tun["survivor_list"] == 2:
         return 1
     if info["code_bits"] == 8:
         return 3 if n >= (4 << 20) else 1
+    if tun["survivor_list"] != 1:
+        return 1
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     return 3 if n // 992 > 16 * sms * (tun["block"] // 32) else 1
 
@@ -877,6 +880,11 @@ def batch_line(args) -> dict:
 
     plan = api.BatchPlan(handles, max_items=len(texts))
     nitems = len(texts)
+    # the phased form for the 8-bit-code sets: lists sized for all their text
+    list_bytes = 0
+    if not args.no_batch_lists:
+        list_bytes = int(sum(int(lens[i]) for i in range(nitems) if autos[which[i]].info()["code_bits"] == 8))
+        plan.reserve_lists(list_bytes)
 
     def graph_step():
         plan.replay(stream)
@@ -992,12 +1000,15 @@ def batch_line(args) -> dict:
         "dtype": "u8", "data": "synthetic",
         "config": {"workload": "batch: %d texts log-uniform 1 KiB-4 MiB (%d B), 50%% ACGT / 50%% Zipf-256, "
                                "8 keyword sets %s of length 8-64, dense int32 ids" % (nitems, total, list(counts)),
-                   "l2": "inputs larger than L2 (%.1f GB per step)" % (5 * total / 1e9)},
+                   "l2": "inputs larger than L2 (%.1f GB per step)" % (5 * total / 1e9),
+                   "survivor_lists_for_bytes": list_bytes},
         "roofline": {"bound": "hbm", "achieved": 5 * total / (gm * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": 5 * total / (gm * 1e-3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": 5 * total, "kernel": "batch graph (all launches)"},
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": args.steps * 2,  # the planning kernel and the one matching launch
+        # the planning kernel and the one matching launch (with survivor lists
+        # also the survivor and walk steps)
+        "gpu_launches": args.steps * (4 if list_bytes else 2),
         "batch": {
             "graph_ms_median": gm, "graph_gbs": total / (gm * 1e-3) / 1e9,
             "text_done_ms_p50": gm, "text_done_ms_p99": gm,
@@ -1181,6 +1192,8 @@ def main():
                     help="batched workload (4,096 texts, eight automata) instead of the throughput line")
     ap.add_argument("--batch-texts", type=int, default=4096)
     ap.add_argument("--autotune", action="store_true", help="batch: autotune each automaton first")
+    ap.add_argument("--no-batch-lists", action="store_true",
+                    help="batch: resolve the 8-bit-code sets' survivors in their warps (no survivor lists)")
     ap.add_argument("--serve", action="store_true",
                     help="served workload (Poisson arrivals, 16 automata) instead of the throughput line")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[1000, 3000, 10000, 30000, 100000])

@@ -421,8 +421,10 @@ ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text, uint64_t n
  * tail, and no launch boundary drains the GPU between automata.  That launch
  * serves up to 32 automata with root filters (every automaton has one unless
  * built with jump_bytes below 4); it runs the filter kernel for each, whatever
- * kernel ac_set_kernel or ac_autotune chose for its single texts.  Otherwise
- * the batch takes one persistent launch per automaton.  Results are exactly
+ * kernel ac_set_kernel or ac_autotune chose for its single texts (and, with a
+ * plan's survivor lists, lists the survivors of its 8-bit-code automata for
+ * two more launches: ac_batch_reserve_lists).  Otherwise the batch takes one
+ * persistent launch per automaton.  Results are exactly
  * those of ac_match on each text alone: walks stop at the end of their own
  * text.
  *
@@ -472,10 +474,24 @@ ac_status ac_match_batch(const ac_handle *hs, uint32_t nh, const uint8_t *d_text
  *                    AC_ERR_INVALID_ARG when nothing was captured.
  *   ac_batch_destroy frees the plan (not the handles); no work using it may be
  *                    in flight.
+ *   ac_batch_reserve_lists
+ *                    sizes the plan's survivor lists for the phased form of
+ *                    its 8-bit-code automata: with the one persistent launch,
+ *                    their survivors (up to text_bytes / 8 of them per run)
+ *                    are listed and resolved by two further launches at full
+ *                    occupancy, as ac_match does for one long text; tiles
+ *                    whose survivors no longer fit are resolved in their
+ *                    warps.  Takes about 4 bytes of device memory per byte of
+ *                    text_bytes (cudaMalloc); 0 frees the lists (the default:
+ *                    none, every survivor is resolved in its warp).  It drops
+ *                    a captured graph (capture again after it); no work
+ *                    using the plan may be in flight.  Results do not depend
+ *                    on it.
  * A plan must not run on two streams at once (its scratch is shared).
  */
 typedef struct ac_batch_plan *ac_batch;
 ac_status ac_batch_create(const ac_handle *hs, uint32_t nh, uint32_t max_items, ac_batch *out);
+ac_status ac_batch_reserve_lists(ac_batch b, uint64_t text_bytes);
 ac_status ac_batch_run(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
                        int32_t *d_out, void *stream);
 ac_status ac_batch_capture(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
@@ -525,14 +541,20 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
  *     and the scratch of its tiles of about 1 KiB (a match count, a prefix, 32
  *     match slots and a dense fallback of 4 bytes per position, which a tile
  *     writes only when its matches overflow the slots): about 4.4 bytes per
- *     text byte.  A request larger than the whole budget is refused with
- *     AC_ERR_BUDGET at submission, and a server whose automata alone exceed
- *     the budget at creation;
+ *     text byte; with an automaton of 8-bit codes in one-launch waves (below)
+ *     4 more per text byte for its share of the wave's survivor lists.  A
+ *     request larger than the whole budget is refused with AC_ERR_BUDGET at
+ *     submission, and a server whose automata alone exceed the budget at
+ *     creation;
  *   - every admitted request that is not yet on the GPU joins the next wave:
  *     one persistent matching launch over the tiles of all its requests and
  *     automata (as a batch: up to 32 automata with root filters; else one
  *     launch per automaton), then one scan and a gather per automaton, so
- *     requests of any size share the launches;
+ *     requests of any size share the launches.  In the one launch the
+ *     survivors of 8-bit-code automata are listed and resolved by two more
+ *     launches (the phased form of ac_match); such a wave's tiles then keep
+ *     no dense fallback, and the gather matches a tile with more than 32
+ *     matches again;
  *   - up to waves_in_flight waves run at once on their own streams: requests
  *     that arrive while a wave is on the GPU go into the next one and overlap
  *     it as SMs free up; a wave's requests complete when its last kernel ends.

@@ -125,6 +125,7 @@ _SIGS = {
     "ac_batch_capture": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32, _P]),
     "ac_batch_replay": (ctypes.c_int, [_P, _P]),
     "ac_batch_destroy": (ctypes.c_int, [_P]),
+    "ac_batch_reserve_lists": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "ac_autotune": (ctypes.c_int, [_H, _P, _U64, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_uint32),
                                    ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "ac_server_create": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.POINTER(ctypes.c_void_p)]),
@@ -445,6 +446,11 @@ class BatchPlan:
                                      ctypes.byref(p)), "ac_batch_create")
         self.plan = int(p.value)
         self.max_items = max_items
+
+    def reserve_lists(self, text_bytes: int):
+        """Survivor lists for the phased form of the plan's 8-bit-code automata
+        (ac_batch_reserve_lists); drops a captured graph."""
+        _check(lib().ac_batch_reserve_lists(self.plan, int(text_bytes)), "ac_batch_reserve_lists")
 
     def run(self, texts, items, nitems: int, out, stream=None):
         _check(lib().ac_batch_run(self.plan, _dev_ptr(texts), _dev_ptr(items), nitems, _dev_ptr(out, 4),

@@ -51,6 +51,8 @@ struct ac_batch_plan {
     int device = 0;
     uint32_t max_items = 0;
     void *scratch = nullptr;
+    void *lists = nullptr;  // the phased form's lists (ac_batch_reserve_lists)
+    uint32_t list_cap = 0;
     cudaStream_t capture = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -357,7 +359,8 @@ ac_status check_handles(const ac_handle *hs, uint32_t nh) {
 // launch boundary drains the GPU between them); otherwise one persistent
 // launch per automaton, one after another.
 cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const uint8_t *texts,
-                          const ac_batch_item *items, uint32_t nitems, int32_t *out, cudaStream_t st) {
+                          const ac_batch_item *items, uint32_t nitems, int32_t *out, cudaStream_t st,
+                          void *surv_lists = nullptr, uint32_t list_cap = 0) {
     uint8_t *base = static_cast<uint8_t *>(scratch);
     pfac::BatchHead *heads = reinterpret_cast<pfac::BatchHead *>(base);
     uint8_t *counters = base + static_cast<size_t>(nh) * 16u;
@@ -380,8 +383,10 @@ cudaError_t enqueue_batch(const ac_handle *hs, uint32_t nh, void *scratch, const
             rs[a].scratch = counters + 16u * a;
             rs[a].scratch_bytes = 16;
         }
+        if (e == cudaSuccess && surv_lists && list_cap) e = cudaMemsetAsync(surv_lists, 0, 32, st);
         if (e == cudaSuccess)
-            e = pfac::launch_filter_multi(ts.data(), rs.data(), nh, pfac::OUT_DENSE, hs[0]->tuning.wait_ns, st);
+            e = pfac::launch_filter_multi(ts.data(), rs.data(), nh, pfac::OUT_DENSE, hs[0]->tuning.wait_ns, st,
+                                          list_cap ? surv_lists : nullptr, list_cap);
         return e;
     }
     for (uint32_t a = 0; a < nh && e == cudaSuccess; ++a) {
@@ -849,6 +854,7 @@ ac_status ac_batch_destroy(ac_batch b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->capture) cudaStreamDestroy(b->capture);
     if (b->scratch) cudaFree(b->scratch);
+    if (b->lists) cudaFree(b->lists);
     delete b;
     return AC_OK;
 }
@@ -876,11 +882,41 @@ ac_status ac_batch_create(const ac_handle *hs, uint32_t nh, uint32_t max_items, 
     return AC_OK;
 }
 
+ac_status ac_batch_reserve_lists(ac_batch b, uint64_t text_bytes) {
+    if (!b) return AC_ERR_INVALID_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return AC_ERR_CUDA;
+    if (dev != b->device) return AC_ERR_INVALID_ARG;
+    const uint64_t cap = text_bytes / 8;
+    if (cap >= 0x7FFFFFFFull) return AC_ERR_INVALID_ARG;
+    // a graph captured with the old lists would read freed memory: it goes
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if (b->lists) {
+        cudaError_t e = cudaFree(b->lists);
+        b->lists = nullptr;
+        b->list_cap = 0;
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (cap == 0) return AC_OK;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, pfac::multi_lists_bytes(static_cast<uint32_t>(cap)));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? AC_ERR_OOM : cuda_status(e);
+    }
+    b->lists = p;
+    b->list_cap = static_cast<uint32_t>(cap);
+    return AC_OK;
+}
+
 namespace {
 ac_status batch_enqueue(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,
                         int32_t *d_out, cudaStream_t st) {
     return cuda_status(enqueue_batch(b->hs.data(), static_cast<uint32_t>(b->hs.size()), b->scratch, d_texts, d_items,
-                                     nitems, d_out, st));
+                                     nitems, d_out, st, b->lists, b->list_cap));
 }
 
 ac_status check_plan_args(ac_batch b, const uint8_t *d_texts, const ac_batch_item *d_items, uint32_t nitems,

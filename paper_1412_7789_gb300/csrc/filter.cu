@@ -233,8 +233,14 @@ bool filter_multi_serves(const DevTables *const *ts, uint32_t nh) {
     return true;
 }
 
+size_t multi_lists_bytes(uint32_t list_cap) {
+    const uint64_t walk_cap = static_cast<uint64_t>(list_cap) + static_cast<uint64_t>(device_sm_count()) *
+                                                                    kSurvWarpsPerSm * kWalkChunkEntries;
+    return 32 + 16ull * list_cap + 16ull * walk_cap;
+}
+
 cudaError_t launch_filter_multi(const DevTables *const *ts, const MatchRequest *rs, uint32_t nh, OutMode mode,
-                                unsigned long long wait_ns, cudaStream_t stream) {
+                                unsigned long long wait_ns, cudaStream_t stream, void *lists, uint32_t list_cap) {
     if (!filter_multi_serves(ts, nh) || (mode != OUT_DENSE && mode != OUT_SLOTS)) return cudaErrorInvalidValue;
     DeviceShape ds;
     cudaError_t e = device_shape(&ds);
@@ -247,10 +253,33 @@ cudaError_t launch_filter_multi(const DevTables *const *ts, const MatchRequest *
     uint32_t staged = 0, B = 0, fbytes = 0;
     Tuning tu;
     tu.wait_ns = wait_ns;
+    // the phased form's lists (8-bit-code automata), when given
+    mp.list = nullptr;
+    mp.list_count = nullptr;
+    mp.list_cap = mp.walk_cap = 0;
+    mp.walks4 = nullptr;
+    bool listed = false;
+    for (uint32_t a = 0; a < nh; ++a) listed = listed || ts[a]->B == 8;
+    if (lists && list_cap && listed) {
+        uint8_t *b = static_cast<uint8_t *>(lists);
+        mp.list_count = reinterpret_cast<unsigned int *>(b);
+        mp.list = reinterpret_cast<uint4 *>(b + 32);
+        mp.list_cap = list_cap;
+        mp.walks4 = reinterpret_cast<uint4 *>(b + 32 + 16ull * list_cap);
+        mp.walk_cap = static_cast<uint32_t>((multi_lists_bytes(list_cap) - 32 - 16ull * list_cap) / 16);
+    }
     for (uint32_t a = 0; a < nh; ++a) {
         if (!rs[a].batch || !rs[a].lists || !rs[a].scratch || rs[a].scratch_bytes < 16) return cudaErrorInvalidValue;
         e = fill_params(*ts[a], rs[a], mode, tu, mp.a[a]);
         if (e != cudaSuccess) return e;
+        mp.a[a].aidx = a;
+        if (mp.list && ts[a]->B == 8) {
+            mp.a[a].list = mp.list;
+            mp.a[a].list_count = mp.list_count;
+            mp.a[a].list_cap = mp.list_cap;
+            mp.a[a].walks4 = mp.walks4;
+            mp.a[a].walk_cap = mp.walk_cap;
+        }
         staged = staged > mp.a[a].staged ? staged : mp.a[a].staged;
         B = B > ts[a]->B ? B : ts[a]->B;
         fbytes = fbytes > ts[a]->fbytes ? fbytes : ts[a]->fbytes;

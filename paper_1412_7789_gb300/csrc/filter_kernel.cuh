@@ -121,13 +121,19 @@ struct FilterParams {
     unsigned long long wait_ns;
     uint32_t stall_help;
     uint32_t kind;  // (B << 8) | goto-entry bits, for the multi-automaton launch
-    // one text, 8-bit codes: the lists of the phased form (null: one phase);
-    // list_count[0] survivors, list_count[1] walks
+    // the lists of the phased form (null: one phase); list_count[0]
+    // survivors, list_count[1] walks.  One text: walks {(tile << 10) |
+    // position, state | d << 31}, the next byte at position + k + k2 + d.  A
+    // batch (8-bit codes; one list for the launch's automata): survivors carry
+    // aidx << 16 in their third word and the unit's planned-list entry in the
+    // fourth, walks4 {(unit << 10) | position, state | d << 31, aidx, entry}.
     uint4 *list;
     unsigned int *list_count;
     uint32_t list_cap;
-    uint2 *walks;  // {(tile << 10) | position, state | d << 31}: next byte at position + k + d
+    uint2 *walks;
+    uint4 *walks4;
     uint32_t walk_cap;
+    uint32_t aidx;  // the automaton's index in a multi-automaton launch
     // 8-bit codes: the codes are the bytes (256 columns), or classes from the
     // byte table; the filter index is the top bits of (window & wmask) *
     // kFilterHashMul (32 - fshift of them), the state hash's bucket the top
@@ -872,8 +878,9 @@ __device__ __forceinline__ void filter_load_tables(const FilterParams &p, uint8_
 // error is latched; the warp's copies in flight have landed or been waited
 // for, within the limit).
 // HELP: share heavy tiles within the CTA (the forms for one text that is short
-// next to the grid; see the heavy path below).
-template <int B, typename GT, int MODE, bool BATCH, bool HELP>
+// next to the grid; see the heavy path below).  LISTED: the first phase of the
+// phased form (p.list set; the forms without it carry none of its code).
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false>
 __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *smem, uint32_t it0, uint32_t jpar,
                                              unsigned long long &cnt, uint32_t *it_next) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -1101,14 +1108,16 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
         }
         __syncwarp();
 
-        if constexpr (!BATCH) {
+        if constexpr (LISTED) {
             // phased form: the tile's survivors go to the list (their windows
             // with them) and the tile counts as one without survivors here.
             // With 8-bit codes a window past the text end keeps them here;
             // with 2- and 4-bit codes any tile but an interior one of keyword
             // bytes only (whose windows and stride windows are all known);
-            // and so does no room.
-            const bool listable = B == 8 ? !__any_sync(kFull, (slowm & sv) != 0u) : interior && clean;
+            // and so do no room and, in a batch, unit numbers past 22 bits.
+            static_assert(!BATCH || B == 8, "batches list 8-bit codes only");
+            const bool listable = B == 8 ? !__any_sync(kFull, (slowm & sv) != 0u) && (!BATCH || wk.units < (1u << 22))
+                                         : interior && clean;
             if (p.list && !lfull && total > 0 && listable) {
                 if (lend - lnext < total) {
                     // a new chunk of list space (the rest of the old one: empty)
@@ -1138,8 +1147,8 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                             const uint32_t ca = ((w.inv[ja >> 4] >> (ja & 15u)) & 1u)
                                                     ? 0x100u
                                                     : (w.packed[ja >> 2] >> (8u * (ja & 3u))) & 0xFFu;
-                            p.list[lnext + j] =
-                                make_uint4((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask, ca, 0u);
+                            p.list[lnext + j] = make_uint4((tile << 10) | i, code_window<8>(w.packed, i) & p.wmask,
+                                                           ca | (BATCH ? p.aidx << 16 : 0u), BATCH ? item : 0u);
                         } else {
                             // the window's and the stride window's codes (i + k + k2 < kCodeSpan)
                             p.list[lnext + j] = make_uint4((tile << 10) | i, code_window<B>(w.packed, i), 0u, 0u);
@@ -1332,7 +1341,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     flight_finish<B, GT>(p, wk, w.cls8, f1);
     flight_output<MODE>(p, wk, w, f1, lane, cnt);
     // phased form: the unfilled rest of this warp's list chunk is empty
-    if (!BATCH && p.list)
+    if (LISTED && p.list)
         for (uint32_t j = lnext + static_cast<uint32_t>(lane); j < lend; j += 32u)
             p.list[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
     // the stages issued past this warp's last unit hold end marks (an arrival
@@ -1385,7 +1394,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     return true;
 }
 
-template <int B, typename GT, int MODE, bool BATCH, bool HELP>
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED>
 __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_constant__ FilterParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -1393,7 +1402,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_co
     if (threadIdx.x == 0) filter_load_tables(p, smem);
     unsigned long long cnt = 0;
     uint32_t it = 0;
-    if (!filter_units<B, GT, MODE, BATCH, HELP>(p, smem, 0, 0, cnt, &it)) return;
+    if (!filter_units<B, GT, MODE, BATCH, HELP, LISTED>(p, smem, 0, 0, cnt, &it)) return;
     if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
     if (MODE == OUT_COUNT) {
 #pragma unroll
@@ -1651,13 +1660,21 @@ struct MultiParams {
     FilterParams a[kMultiMax];
     uint32_t nh;
     uint32_t params_off;
+    // the phased form of the 8-bit-code automata (list null: none); the same
+    // lists are in their a[].list / walks4
+    uint4 *list;
+    unsigned int *list_count;
+    uint32_t list_cap;
+    uint4 *walks4;
+    uint32_t walk_cap;
 };
 static_assert(sizeof(FilterParams) % 4 == 0, "parameters are copied as words");
+static_assert(sizeof(MultiParams) <= 32764, "kernel parameters are limited to 32764 bytes");
 
 // FilterParams::kind of a form: (B << 8) | goto-entry bits.
 __host__ __device__ constexpr uint32_t filter_kind(uint32_t B, uint32_t gbits) { return (B << 8) | gbits; }
 
-template <int MODE>
+template <int MODE, bool LISTED>
 __global__ void __launch_bounds__(kMultiBlock, 1) pfac_filter_multi(const __grid_constant__ MultiParams mp) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -1681,8 +1698,8 @@ __global__ void __launch_bounds__(kMultiBlock, 1) pfac_filter_multi(const __grid
             case filter_kind(2, 32): ok = filter_units<2, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
             case filter_kind(4, 16): ok = filter_units<4, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
             case filter_kind(4, 32): ok = filter_units<4, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
-            case filter_kind(8, 16): ok = filter_units<8, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
-            default: ok = filter_units<8, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(8, 16): ok = filter_units<8, int16_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
+            default: ok = filter_units<8, int32_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
         }
         ++loads;
         bad |= ok ? 0 : 1;
@@ -1690,16 +1707,172 @@ __global__ void __launch_bounds__(kMultiBlock, 1) pfac_filter_multi(const __grid
     if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
 }
 
+// The second and third steps of a batch's phased form: the survivors that
+// the first phase (pfac_filter_multi) listed for the launch's 8-bit-code
+// automata, each with its automaton (third word, from bit 16) and its unit's
+// planned-list entry (fourth word); then the walks they leave.  Each CTA
+// copies the automata's parameters (and, for the walks, their byte tables)
+// to shared memory.  Results go out as the single-text steps write them, at
+// the unit's text.
+__device__ __forceinline__ void multi_params_to_smem(const MultiParams &mp, FilterParams *ps) {
+    for (uint32_t i = threadIdx.x; i < mp.nh * static_cast<uint32_t>(sizeof(FilterParams) / 4); i += blockDim.x)
+        reinterpret_cast<uint32_t *>(ps)[i] = reinterpret_cast<const uint32_t *>(mp.a)[i];
+}
+
+// The text of a listed unit (its planned-list entry `item`) and the tile's
+// first position in it.
+__device__ __forceinline__ TileText listed_text(const FilterParams &P, uint32_t unit, uint32_t item, int64_t &gpb) {
+    const Work wk = load_work(P.batch, P.lists, 0);
+    const TileText tt = batch_text(wk, P.text, P.out, item, unit);
+    gpb = static_cast<int64_t>(static_cast<uint64_t>(tt.tile) * kTile) - tt.head;
+    return tt;
+}
+
+template <int MODE>
+__device__ __forceinline__ void listed_output(const FilterParams &P, const TileText &tt, int64_t gpb, uint32_t unit,
+                                              uint32_t i, int r) {
+    if (MODE == OUT_DENSE) {
+        tt.out[gpb + i] = r;
+    } else {
+        const uint32_t su = P.sl.ubase + unit;
+        const uint32_t k = atomicAdd(P.sl.counts + su, 1u);
+        if (k < kSlotCap)
+            P.sl.slots[static_cast<uint64_t>(su) * kSlotCap + k] =
+                (static_cast<unsigned long long>(static_cast<uint32_t>(r)) << 32) | static_cast<uint32_t>(gpb + i);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_survivors_multi(const __grid_constant__ MultiParams mp) {
+    extern __shared__ __align__(16) uint8_t msm[];
+    FilterParams *ps = reinterpret_cast<FilterParams *>(msm);
+    multi_params_to_smem(mp, ps);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const uint32_t listed = *reinterpret_cast<volatile const unsigned int *>(mp.list_count);
+    const uint32_t m = listed < mp.list_cap ? listed : mp.list_cap;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    constexpr int SPT = 2;
+    uint32_t wnext = 0, wend = 0;
+    for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < m; wb += SPT * stride) {
+        const uint32_t b0 = wb + static_cast<uint32_t>(lane);
+        uint4 e[SPT], he[SPT];
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+            const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
+            e[t] = idx < m ? __ldg(mp.list + idx) : make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+            he[t] = make_uint4(0u, 0u, 0u, 0u);
+            if (e[t].x != 0xFFFFFFFFu) {
+                const FilterParams &P = ps[(e[t].z >> 16) & (kMultiMax - 1u)];
+                he[t] = __ldg(P.HK + hk_slot(P, e[t].y));
+            }
+        }
+        int r[SPT], g[SPT];
+        uint32_t s[SPT], q[SPT];
+        bool walk[SPT];
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+            const bool on = e[t].x != 0xFFFFFFFFu;
+            const FilterParams &P = ps[(e[t].z >> 16) & (kMultiMax - 1u)];
+            const uint32_t i = e[t].x & 1023u, c = e[t].z & 0x1FFu;
+            r[t] = -1;
+            s[t] = 0;
+            q[t] = 0;
+            walk[t] = on && !hk_outcome(P, hk_find(P, e[t].y, he[t]), i, c & 0xFFu, c < 0x100u, r[t], s[t], q[t]);
+            if (walk[t]) r[t] = -1;
+            g[t] = 0;
+            if (walk[t] && q[t] == i + P.k) {
+                const uint32_t col = c < 0x100u ? c : P.C;
+                g[t] = (P.kind & 0xFFu) == 16u ? goto_ld(static_cast<const int16_t *>(P.G), s[t], P.W, col)
+                                               : goto_ld(static_cast<const int32_t *>(P.G), s[t], P.W, col);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+            const FilterParams &P = ps[(e[t].z >> 16) & (kMultiMax - 1u)];
+            const uint32_t i = e[t].x & 1023u;
+            if (walk[t] && q[t] == i + P.k) {
+                if (g[t] < 0) {
+                    r[t] = decode_dead(g[t]);
+                    walk[t] = false;
+                } else {
+                    s[t] = static_cast<uint32_t>(g[t]);
+                    ++q[t];
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+            const uint32_t a = (e[t].z >> 16) & (kMultiMax - 1u);
+            const FilterParams &P = ps[a];
+            const uint32_t unit = e[t].x >> 10, i = e[t].x & 1023u;
+            const unsigned wm = __ballot_sync(kFull, walk[t]);
+            if (wm) {  // to the walk list, as in the single-text step
+                const uint32_t need = __popc(wm), rank = __popc(wm & ((1u << lane) - 1u));
+                uint32_t slot = wnext + rank;
+                if (wend - wnext < need) {
+                    const uint32_t rest = wend - wnext;
+                    uint32_t base = 0;
+                    if (lane == 0) base = atomicAdd(mp.list_count + 1, kWalkChunk);
+                    base = __shfl_sync(kFull, base, 0);
+                    if (rank >= rest) slot = base + (rank - rest);
+                    wnext = base + (need - rest);
+                    wend = base + kWalkChunk;
+                    if (static_cast<uint64_t>(base) + kWalkChunk > mp.walk_cap) {  // cannot happen (room for all)
+                        if (lane == 0) atomicOr(P.err, static_cast<unsigned>(kErrWalk));
+                        wnext = wend = 0;
+                    }
+                } else {
+                    wnext += need;
+                }
+                if (walk[t] && wend != 0 && slot < mp.walk_cap)
+                    mp.walks4[slot] = make_uint4(e[t].x, s[t] | ((q[t] - i - P.k - P.k2) << 31), a, e[t].w);
+            }
+            if (e[t].x == 0xFFFFFFFFu || r[t] < 0) continue;
+            int64_t gpb = 0;
+            const TileText tt = listed_text(P, unit, e[t].w, gpb);
+            listed_output<MODE>(P, tt, gpb, unit, i, r[t]);
+        }
+    }
+    for (uint32_t j = wnext + static_cast<uint32_t>(lane); j < wend; j += 32u)
+        mp.walks4[j] = make_uint4(0xFFFFFFFFu, 0u, 0u, 0u);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks_multi(const __grid_constant__ MultiParams mp) {
+    extern __shared__ __align__(16) uint8_t msm[];
+    FilterParams *ps = reinterpret_cast<FilterParams *>(msm);
+    uint8_t *cls = msm + mp.nh * sizeof(FilterParams);
+    multi_params_to_smem(mp, ps);
+    for (uint32_t i = threadIdx.x; i < mp.nh * 256u; i += blockDim.x) cls[i] = __ldg(mp.a[i >> 8].cls8g + (i & 255u));
+    __syncthreads();
+    const uint32_t listed = *reinterpret_cast<volatile const unsigned int *>(mp.list_count + 1);
+    const uint32_t m = listed < mp.walk_cap ? listed : mp.walk_cap;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+        const uint4 e = __ldg(mp.walks4 + j);
+        if (e.x == 0xFFFFFFFFu) continue;
+        const uint32_t a = e.z & (kMultiMax - 1u);
+        const FilterParams &P = ps[a];
+        const uint32_t unit = e.x >> 10, i = e.x & 1023u;
+        int64_t gpb = 0;
+        const TileText tt = listed_text(P, unit, e.w, gpb);
+        const uint32_t st = e.y & 0x7FFFFFFFu, q = i + P.k + P.k2 + (e.y >> 31);
+        const int r = (P.kind & 0xFFu) == 16u ? walk_global<int16_t>(P, cls + 256u * a, tt, gpb, st, q)
+                                              : walk_global<int32_t>(P, cls + 256u * a, tt, gpb, st, q);
+        if (r >= 0) listed_output<MODE>(P, tt, gpb, unit, i, r);
+    }
+}
+
 inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
 
-template <int B, typename GT, int MODE, bool BATCH, bool HELP>
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false>
 cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
                        cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH, HELP>;
+    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH, HELP, LISTED>;
     if (!configured[dev]) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
@@ -1720,6 +1893,17 @@ cudaError_t launch_modes(OutMode mode, const FilterParams &p, uint32_t grid, uin
                 return launch_one<B, GT, OUT_COUNT, false, true>(p, grid, block, smem, max_smem, stream);
             case OUT_SLOTS:
                 return launch_one<B, GT, OUT_SLOTS, false, true>(p, grid, block, smem, max_smem, stream);
+            default:
+                return cudaErrorInvalidValue;
+        }
+    } else if (p.list && !p.batch) {  // the first phase of the phased form
+        switch (mode) {
+            case OUT_DENSE:
+                return launch_one<B, GT, OUT_DENSE, false, false, true>(p, grid, block, smem, max_smem, stream);
+            case OUT_COUNT:
+                return launch_one<B, GT, OUT_COUNT, false, false, true>(p, grid, block, smem, max_smem, stream);
+            case OUT_SLOTS:
+                return launch_one<B, GT, OUT_SLOTS, false, false, true>(p, grid, block, smem, max_smem, stream);
             default:
                 return cudaErrorInvalidValue;
         }
@@ -1754,25 +1938,40 @@ cudaError_t launch_survivors(OutMode mode, const filt::FilterParams &p, uint32_t
                              int per_thread, cudaStream_t stream);
 
 namespace filt {
-template <int MODE>
-cudaError_t launch_multi(const MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem, cudaStream_t stream) {
+template <int MODE, bool LISTED>
+cudaError_t launch_multi_one(const MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem, cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!configured[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(pfac_filter_multi<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             max_smem);
+        cudaError_t e = cudaFuncSetAttribute(pfac_filter_multi<MODE, LISTED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
-    pfac_filter_multi<MODE><<<grid, kMultiBlock, smem, stream>>>(mp);
+    pfac_filter_multi<MODE, LISTED><<<grid, kMultiBlock, smem, stream>>>(mp);
+    return cudaGetLastError();
+}
+
+// The multi-automaton launch, and with lists the second and third steps.
+template <int MODE>
+cudaError_t launch_multi(const MultiParams &mp, uint32_t sms, uint32_t smem, int max_smem, cudaStream_t stream) {
+    if (!mp.list) return launch_multi_one<MODE, false>(mp, sms, smem, max_smem, stream);
+    cudaError_t e = launch_multi_one<MODE, true>(mp, sms, smem, max_smem, stream);
+    if (e != cudaSuccess) return e;
+    const uint32_t grid = sms * static_cast<uint32_t>(surv_ctas<2>());
+    const uint32_t ps = mp.nh * static_cast<uint32_t>(sizeof(FilterParams));
+    pfac_survivors_multi<MODE><<<grid, kSurvBlock, ps, stream>>>(mp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    pfac_walks_multi<MODE><<<grid, kSurvBlock, ps + 256u * mp.nh, stream>>>(mp);
     return cudaGetLastError();
 }
 }  // namespace filt
 
-// Launches of the multi-automaton kernel, filter_multi_dense.cu and
-// filter_multi_slots.cu.
+// Launches of the multi-automaton kernel (grid: the SM count; with lists also
+// the second and third steps), filter_multi_dense.cu and filter_multi_slots.cu.
 cudaError_t launch_filter_multi_dense(const filt::MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem,
                                       cudaStream_t stream);
 cudaError_t launch_filter_multi_slots(const filt::MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem,

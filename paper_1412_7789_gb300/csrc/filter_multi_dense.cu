@@ -5,7 +5,7 @@
 namespace pfac {
 
 cudaError_t launch_filter_multi_dense(const filt::MultiParams &mp, uint32_t grid, uint32_t smem, int max_smem,
-                                  cudaStream_t stream) {
+                                      cudaStream_t stream) {
     return filt::launch_multi<OUT_DENSE>(mp, grid, smem, max_smem, stream);
 }
 

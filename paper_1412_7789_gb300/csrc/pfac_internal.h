@@ -441,10 +441,18 @@ inline uint32_t unit_positions(const DevTables &t, const Tuning &tu) {
 // and nh is small enough for the launch's parameters), and the launch.  rs[a]:
 // automaton a's request (batch head, planned list, its tile counter as
 // scratch, dense output or slots).  Every automaton runs the filter kernel,
-// whatever kernel its tuning names for single texts.
+// whatever kernel its tuning names for single texts.  lists (optional, null:
+// none): scratch of multi_lists_bytes(list_cap) bytes whose first 32 are
+// zeroed, for the phased form of the batch's 8-bit-code automata: their
+// survivors go to one list of up to list_cap entries (tiles past that are
+// resolved in their warps), resolved by a second launch and a third for the
+// walks.  With slot output the units then keep no dense fallback (the gather
+// matches a unit with more matches than slots again).
 bool filter_multi_serves(const DevTables *const *ts, uint32_t nh);
+size_t multi_lists_bytes(uint32_t list_cap);
 cudaError_t launch_filter_multi(const DevTables *const *ts, const MatchRequest *rs, uint32_t nh, OutMode mode,
-                                unsigned long long wait_ns, cudaStream_t stream);
+                                unsigned long long wait_ns, cudaStream_t stream, void *lists = nullptr,
+                                uint32_t list_cap = 0);
 
 // A matching launch on the kernel that serves the automaton.
 inline cudaError_t launch_match(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,

@@ -117,12 +117,18 @@ uint64_t units_of(const ac_server_impl *s, const ac_server_request &r) {
     return (r.n + text_head(r) + T - 1) / T;
 }
 
+// Whether the waves list the survivors of automaton a's texts for the
+// phased form (one launch for the wave's automata, 8-bit codes).
+bool wave_lists(const ac_server_impl *s, uint32_t a) { return s->multi && s->tabs[a]->B == 8; }
+
 // Device bytes a request holds while admitted: its text (a host text's device
 // copy), its output and the scratch of its tiles (counts, prefix, slots,
-// dense fallback).
+// dense fallback), and with 8-bit codes in one-launch waves its share of the
+// wave's survivor lists (about 4 bytes per text byte).
 uint64_t request_bytes(const ac_server_impl *s, const ac_server_request &r) {
     const uint64_t per_unit = 4 + 8 + 8ull * pfac::kSlotCap + 4ull * pfac::kDenseStride;
-    return r.n + 8ull * r.cap + units_of(s, r) * per_unit + 64;
+    const uint64_t lists = wave_lists(s, r.automaton) ? 32ull * (r.n / 8) + 32 : 0;
+    return r.n + 8ull * r.cap + units_of(s, r) * per_unit + lists + 64;
 }
 
 // Device scratch of a wave: from the caller's allocator (freed when the wave
@@ -247,16 +253,26 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         outs[i] = pfac::CompactOut{r.d_pos, r.d_ids, r.cap, reinterpret_cast<unsigned long long *>(r.d_count)};
     }
 
+    // the survivor lists of the wave's 8-bit-code texts (the phased form of
+    // the one launch); with them no unit keeps a dense fallback (the gather
+    // matches a unit with more matches than slots again)
+    uint64_t list_text = 0;
+    for (uint32_t k = 0; k < L; ++k)
+        if (wave_lists(s, w.reqs[order[k]].r.automaton)) list_text += w.reqs[order[k]].r.n;
+    const uint32_t list_cap = static_cast<uint32_t>(std::min<uint64_t>(list_text / 8, 0x7FFFFFF0ull));
+    const size_t lsb = list_cap ? round256(pfac::multi_lists_bytes(list_cap)) : 0;
+
     // device: plan (heads | list | outs) | tile counters | counts | prefix |
-    // slots | partial sums | dense fallback | host-text copies
+    // slots | partial sums | dense fallback (none with survivor lists) |
+    // host-text copies | survivor lists
     const size_t hb = sizeof(pfac::BatchHead) * nh, lb = sizeof(pfac::BatchItemDev) * L,
                  ob = sizeof(pfac::CompactOut) * R;
     const size_t plan_bytes = round256(hb) + round256(lb) + round256(ob);
     const size_t cb = round256(16ull * nh), nb = round256(4 * U), pb = 8 * U, sb = 8ull * pfac::kSlotCap * U;
     const size_t db = round256(plan_bytes + cb + nb + pb + sb + 8ull * pfac::kScanCtas);  // dense fallback: aligned
-    const size_t stb = round256(db + 4ull * pfac::kDenseStride * U);
+    const size_t stb = round256(db + (list_cap ? 0 : 4ull * pfac::kDenseStride * U));
     void *dev = nullptr;
-    e = wave_alloc(s, w, stb + staged, &dev);
+    e = wave_alloc(s, w, stb + round256(staged) + lsb, &dev);
     if (e != cudaSuccess) return e;
     uint8_t *dp = static_cast<uint8_t *>(dev);
 
@@ -289,7 +305,8 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(counters + cb + nb);
     unsigned long long *slots = prefix + U;
     unsigned long long *partials = slots + static_cast<size_t>(pfac::kSlotCap) * U;
-    int32_t *dense = reinterpret_cast<int32_t *>(dp + db);
+    int32_t *dense = list_cap ? nullptr : reinterpret_cast<int32_t *>(dp + db);
+    void *surv_lists = list_cap ? static_cast<void *>(dp + stb + round256(staged)) : nullptr;
 
     e = cudaMemcpyAsync(dp, hp, plan_bytes, cudaMemcpyHostToDevice, w.stream);
     for (uint32_t k = 0; k < L && e == cudaSuccess; ++k) {  // host texts: one copy each
@@ -298,6 +315,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
                                               w.stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, cb + 4 * U, w.stream);
+    if (e == cudaSuccess && surv_lists) e = cudaMemsetAsync(surv_lists, 0, 32, w.stream);
     if (s->multi && e == cudaSuccess) {  // every automaton of the wave in one launch
         std::vector<pfac::MatchRequest> rs(nh);
         for (uint32_t a = 0; a < nh; ++a) {
@@ -312,7 +330,8 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
             m.scratch = counters + 16u * a;
             m.scratch_bytes = 16;
         }
-        e = pfac::launch_filter_multi(s->tabs.data(), rs.data(), nh, pfac::OUT_SLOTS, s->tune[0].wait_ns, w.stream);
+        e = pfac::launch_filter_multi(s->tabs.data(), rs.data(), nh, pfac::OUT_SLOTS, s->tune[0].wait_ns, w.stream,
+                                      surv_lists, list_cap);
     }
     for (uint32_t a = 0; a < nh && e == cudaSuccess && !s->multi; ++a) {
         if (heads[a].units == 0) continue;

@@ -162,6 +162,50 @@ def test_batch_plan_run_capture_replay(automata):
             assert np.all(got[~written] == SENTINEL)
 
 
+@pytest.mark.parametrize("reserve", [64 << 20, 4096])
+def test_batch_plan_survivor_lists(automata, reserve):
+    """The phased form inside the one persistent launch: the plan's 8-bit-code
+    automata list their survivors for the second and third launches.  The
+    edge batch and a batch of longer texts (every kind, Zipf ones up to 1.5
+    MB), run and captured: every text's ids are the oracle's, nothing outside
+    the output ranges is written.  A 4 KiB reservation (512 entries) overflows
+    at once, so nearly every tile falls back to its warp; reserving again
+    drops the captured graph."""
+    import torch
+
+    sets, hs = automata
+    handles = [a.handle for a in hs]
+    g = np.random.default_rng(77)
+    texts, kinds, text_off, out_off, buf_len, out_len = _edge_batch(sets, 5)
+    lens = [int(x) for x in g.integers(100_000, 1_500_000, size=10)]
+    kinds2 = [2, 3, 2, 3, 0, 1, 2, 4, 2, 3]
+    long_texts = [_text_for(k, n, 500 + i, sets) for i, (k, n) in enumerate(zip(kinds2, lens))]
+    text_off2 = list(np.cumsum([0] + lens[:-1]) + 5)
+    out_off2 = list(np.cumsum([0] + lens[:-1]) + 3)
+    with api.BatchPlan(handles, max_items=len(texts) + 5) as plan:
+        plan.reserve_lists(reserve)
+        for args in ((texts, kinds, text_off, out_off, buf_len, out_len),
+                     (long_texts, kinds2, text_off2, out_off2, sum(lens) + 64, sum(lens) + 64)):
+            _run_and_check(hs, sets, *args[:2], *args[2:],
+                           runner=lambda b, it, k, o: plan.run(b, it, k, o))
+        # capture with the lists, replay
+        buf = np.zeros(sum(lens) + 64, dtype=np.uint8)
+        for t, o in zip(long_texts, text_off2):
+            buf[o:o + t.size] = t
+        d_buf = _gpu.to_dev(buf)
+        d_items = api.items_to_device(api.batch_items(text_off2, lens, out_off2, kinds2))
+        out = torch.full((sum(lens) + 64,), SENTINEL, dtype=torch.int32, device="cuda")
+        plan.capture(d_buf, d_items, len(long_texts), out)
+        plan.replay()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        for i, (t, o) in enumerate(zip(long_texts, out_off2)):
+            assert np.array_equal(got[o:o + t.size], oracle.pfac_ids(sets[kinds2[i]], t)), i
+        plan.reserve_lists(reserve // 2)
+        with pytest.raises(api.AcError):
+            plan.replay()
+
+
 def test_batch_bad_automaton_is_reported(automata):
     import torch
 
