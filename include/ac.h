@@ -255,7 +255,11 @@ ac_status ac_export_jump(ac_handle h, int16_t *J, uint32_t *k, uint32_t *base_k,
  * any alignment (16-byte aligned buffers take the vectorised path).  n = 0 is
  * a no-op.  Takes 16 bytes of scratch (the tile counter) per call from the
  * library's stream-ordered pool, except for a text short enough that each of
- * its tiles is some warp's first (no counter, no allocation).
+ * its tiles is some warp's first (no counter, no allocation).  A text that
+ * takes the phased form of the filter kernel (8-bit codes from 4 MiB on; see
+ * ac_tuning.survivor_list) also takes its survivor and walk lists from the
+ * pool: about 3 bytes per text byte (16 per listed survivor, room for n / 8
+ * of them, and 8 per walk).
  */
 ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_out_ids, void *stream);
 
@@ -265,9 +269,11 @@ ac_status ac_match(ac_handle h, const uint8_t *d_text, uint64_t n, int32_t *d_ou
  * the true total to *d_count (a device uint64).  The caller compares the total
  * with cap and calls again with more room when it is larger.  n must be below
  * 2^32.  Takes its scratch (per tile a match count, a prefix sum, 32 match
- * slots and a dense fallback of 4 bytes per position) from the library's
- * stream-ordered pool (cudaMallocFromPoolAsync) on `stream`; the pool keeps the
- * memory it grows to until the process exits.
+ * slots and a dense fallback of 4 bytes per position; for the phased form
+ * the survivor and walk lists as for ac_match, and then no dense fallback:
+ * the gather matches a tile with more than 32 matches again) from the
+ * library's stream-ordered pool (cudaMallocFromPoolAsync) on `stream`; the
+ * pool keeps the memory it grows to until the process exits.
  */
 ac_status ac_match_compact(ac_handle h, const uint8_t *d_text, uint64_t n, uint32_t *d_pos,
                            uint32_t *d_ids, uint64_t cap, uint64_t *d_count, void *stream);
@@ -541,8 +547,8 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
  *     and the scratch of its tiles of about 1 KiB (a match count, a prefix, 32
  *     match slots and a dense fallback of 4 bytes per position, which a tile
  *     writes only when its matches overflow the slots): about 4.4 bytes per
- *     text byte; with an automaton of 8-bit codes in one-launch waves (below)
- *     4 more per text byte for its share of the wave's survivor lists.  A
+ *     text byte; with an automaton of 8-bit codes (in one-launch waves, below,
+ *     or FIFO) 4 more per text byte for its survivor lists.  A
  *     request larger than the whole budget is refused with AC_ERR_BUDGET at
  *     submission, and a server whose automata alone exceed the budget at
  *     creation;
@@ -550,11 +556,11 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
  *     one persistent matching launch over the tiles of all its requests and
  *     automata (as a batch: up to 32 automata with root filters; else one
  *     launch per automaton), then one scan and a gather per automaton, so
- *     requests of any size share the launches.  In the one launch the
- *     survivors of 8-bit-code automata are listed and resolved by two more
- *     launches (the phased form of ac_match); such a wave's tiles then keep
- *     no dense fallback, and the gather matches a tile with more than 32
- *     matches again;
+ *     requests of any size share the launches.  In the one launch, when a
+ *     wave holds 4 MiB or more of text for 8-bit-code automata, their
+ *     survivors are listed and resolved by two more launches (the phased form
+ *     of ac_match); their tiles then keep no dense fallback, and the gather
+ *     matches such a tile with more than 32 matches again;
  *   - up to waves_in_flight waves run at once on their own streams: requests
  *     that arrive while a wave is on the GPU go into the next one and overlap
  *     it as SMs free up; a wave's requests complete when its last kernel ends.

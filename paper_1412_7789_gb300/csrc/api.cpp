@@ -299,17 +299,19 @@ cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const 
                         cudaStream_t st) {
     const uint32_t units = pfac::compact_units(h->dev, h->tuning, text, n);
     if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
-    // 8-bit codes, long text: room for the phased form's lists too
+    // the phased form's lists instead of the dense fallback when it applies
+    // (the gather then matches an overflowing unit again)
     pfac::SurvivorLists sl;
     if (pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, h->tuning, n);
-    const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, true) + sl.bytes();
+    const bool dense = sl.list_cap == 0;
+    const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, dense) + sl.bytes();
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);
     if (e != cudaSuccess) return e;
     void *scratch = nullptr;
     e = cudaMallocFromPoolAsync(&scratch, bytes, pool, st);
     if (e != cudaSuccess) return e;
-    e = pfac::enqueue_compact(h->dev, h->tuning, text, n, out, scratch, bytes, true, st);
+    e = pfac::enqueue_compact(h->dev, h->tuning, text, n, out, scratch, bytes, dense, st);
     const cudaError_t e2 = cudaFreeAsync(scratch, st);
     return e != cudaSuccess ? e : e2;
 }

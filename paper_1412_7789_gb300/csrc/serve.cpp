@@ -117,9 +117,9 @@ uint64_t units_of(const ac_server_impl *s, const ac_server_request &r) {
     return (r.n + text_head(r) + T - 1) / T;
 }
 
-// Whether the waves list the survivors of automaton a's texts for the
-// phased form (one launch for the wave's automata, 8-bit codes).
-bool wave_lists(const ac_server_impl *s, uint32_t a) { return s->multi && s->tabs[a]->B == 8; }
+// Whether automaton a's texts may take survivor lists for the phased form:
+// 8-bit codes in one-launch waves, or (FIFO) as ac_match_compact takes them.
+bool wave_lists(const ac_server_impl *s, uint32_t a) { return (s->multi || s->fifo) && s->tabs[a]->B == 8; }
 
 // Device bytes a request holds while admitted: its text (a host text's device
 // copy), its output and the scratch of its tiles (counts, prefix, slots,
@@ -181,7 +181,11 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         // a host text: its copy at the front of the scratch (16-byte aligned)
         const size_t tb = host_text(q.r) ? round16(q.r.n) : 0;
         const uint32_t units = pfac::compact_units(t, tu, tb ? nullptr : q.r.d_text, q.r.n);
-        const size_t bytes = tb + pfac::compact_scratch_bytes(t, units, true);
+        // as ac_match_compact: the phased form's lists instead of the dense fallback when it applies
+        pfac::SurvivorLists sl;
+        if (pfac::uses_filter(t, tu)) sl = pfac::survivor_lists(t, tu, q.r.n);
+        const bool dense = sl.list_cap == 0;
+        const size_t bytes = tb + pfac::compact_scratch_bytes(t, units, dense) + sl.bytes();
         void *scratch = nullptr;
         e = wave_alloc(s, w, bytes, &scratch);
         if (e != cudaSuccess) return e;
@@ -192,7 +196,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         }
         const pfac::CompactOut out{q.r.d_pos, q.r.d_ids, q.r.cap, reinterpret_cast<unsigned long long *>(q.r.d_count)};
         if (e == cudaSuccess)
-            e = pfac::enqueue_compact(t, tu, text, q.r.n, out, static_cast<uint8_t *>(scratch) + tb, bytes - tb, true,
+            e = pfac::enqueue_compact(t, tu, text, q.r.n, out, static_cast<uint8_t *>(scratch) + tb, bytes - tb, dense,
                                       w.stream);
         const cudaError_t e2 = wave_release(s, w, scratch);
         return e != cudaSuccess ? e : e2;
@@ -254,23 +258,26 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     }
 
     // the survivor lists of the wave's 8-bit-code texts (the phased form of
-    // the one launch); with them no unit keeps a dense fallback (the gather
-    // matches a unit with more matches than slots again)
+    // the one launch), when they hold 4 MiB or more (below that the two extra
+    // launches cost more than they save); with them those automata's units
+    // keep no dense fallback (the gather matches a unit with more matches
+    // than slots again), the others' do
     uint64_t list_text = 0;
     for (uint32_t k = 0; k < L; ++k)
-        if (wave_lists(s, w.reqs[order[k]].r.automaton)) list_text += w.reqs[order[k]].r.n;
-    const uint32_t list_cap = static_cast<uint32_t>(std::min<uint64_t>(list_text / 8, 0x7FFFFFF0ull));
+        if (s->multi && wave_lists(s, w.reqs[order[k]].r.automaton)) list_text += w.reqs[order[k]].r.n;
+    const uint32_t list_cap =
+        list_text >= (4ull << 20) ? static_cast<uint32_t>(std::min<uint64_t>(list_text / 8, 0x7FFFFFF0ull)) : 0u;
     const size_t lsb = list_cap ? round256(pfac::multi_lists_bytes(list_cap)) : 0;
+    auto dense_for = [&](uint32_t a, int32_t *d) -> int32_t * { return list_cap && wave_lists(s, a) ? nullptr : d; };
 
     // device: plan (heads | list | outs) | tile counters | counts | prefix |
-    // slots | partial sums | dense fallback (none with survivor lists) |
-    // host-text copies | survivor lists
+    // slots | partial sums | dense fallback | host-text copies | survivor lists
     const size_t hb = sizeof(pfac::BatchHead) * nh, lb = sizeof(pfac::BatchItemDev) * L,
                  ob = sizeof(pfac::CompactOut) * R;
     const size_t plan_bytes = round256(hb) + round256(lb) + round256(ob);
     const size_t cb = round256(16ull * nh), nb = round256(4 * U), pb = 8 * U, sb = 8ull * pfac::kSlotCap * U;
     const size_t db = round256(plan_bytes + cb + nb + pb + sb + 8ull * pfac::kScanCtas);  // dense fallback: aligned
-    const size_t stb = round256(db + (list_cap ? 0 : 4ull * pfac::kDenseStride * U));
+    const size_t stb = round256(db + 4ull * pfac::kDenseStride * U);
     void *dev = nullptr;
     e = wave_alloc(s, w, stb + round256(staged) + lsb, &dev);
     if (e != cudaSuccess) return e;
@@ -305,7 +312,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     unsigned long long *prefix = reinterpret_cast<unsigned long long *>(counters + cb + nb);
     unsigned long long *slots = prefix + U;
     unsigned long long *partials = slots + static_cast<size_t>(pfac::kSlotCap) * U;
-    int32_t *dense = list_cap ? nullptr : reinterpret_cast<int32_t *>(dp + db);
+    int32_t *dense = reinterpret_cast<int32_t *>(dp + db);
     void *surv_lists = list_cap ? static_cast<void *>(dp + stb + round256(staged)) : nullptr;
 
     e = cudaMemcpyAsync(dp, hp, plan_bytes, cudaMemcpyHostToDevice, w.stream);
@@ -326,7 +333,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
             m.slots.counts = counts;
             m.slots.slots = slots;
             m.slots.ubase = ubase[a];
-            m.slots.dense = dense;
+            m.slots.dense = dense_for(a, dense);
             m.scratch = counters + 16u * a;
             m.scratch_bytes = 16;
         }
@@ -362,7 +369,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         g.prefix = prefix;
         g.slots = slots;
         g.ubase = ubase[a];
-        g.dense = dense;
+        g.dense = dense_for(a, dense);
         e = pfac::launch_compact_gather(*s->tabs[a], g, w.stream);
     }
     const cudaError_t e2 = wave_release(s, w, dev);
