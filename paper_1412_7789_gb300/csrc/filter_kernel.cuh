@@ -1108,13 +1108,17 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
         }
         __syncwarp();
 
+        bool listed = false;
         if constexpr (LISTED) {
             // phased form: the tile's survivors go to the list (their windows
-            // with them) and the tile counts as one without survivors here.
-            // With 8-bit codes a window past the text end keeps them here;
-            // with 2- and 4-bit codes any tile but an interior one of keyword
-            // bytes only (whose windows and stride windows are all known);
-            // and so do no room and, in a batch, unit numbers past 22 bits.
+            // with them; consecutive lanes write consecutive entries) and the
+            // tile counts as one without survivors here.  With 8-bit codes a
+            // window past the text end keeps them here; with 2- and 4-bit codes
+            // any tile but an interior one of keyword bytes only (whose windows
+            // and stride windows are all known); and so do no room and, in a
+            // batch, unit numbers past 22 bits.  (Each lane writing its own
+            // survivors' entries straight from its filter bits, without the
+            // queue, measured slower: the stores no longer coalesce.)
             static_assert(!BATCH || B == 8, "batches list 8-bit codes only");
             const bool listable = B == 8 ? !__any_sync(kFull, (slowm & sv) != 0u) && (!BATCH || wk.units < (1u << 22))
                                          : interior && clean;
@@ -1156,8 +1160,19 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                     }
                     lnext += total;
                     total = 0;
+                    listed = true;
                 }
             }
+        }
+        if (LISTED && listed && f1.tile == 0xFFFFFFFFu && f2.tile == 0xFFFFFFFFu) {
+            // a listed tile and none in flight: write (or count) it now
+            Flight fo = empty_flight();
+            fo.tile = tile;
+            fo.item = item;
+            fo.gpb = gpb;
+            fo.interior = interior ? 1u : 0u;
+            flight_output<MODE>(p, wk, w, fo, lane, cnt);
+            continue;
         }
 
         if (total > 32) {
@@ -1653,7 +1668,7 @@ cudaError_t launch_survivors(OutMode mode, const FilterParams &p, uint32_t sms, 
 // matched has its parameters copied to shared memory at params_off.
 constexpr uint32_t kMultiMax = 32;
 // Threads per CTA of the multi-automaton kernel: 12 warps, which leaves room
-// for the automaton loop's registers around the largest form without spills.
+// for the automaton loop's registers around the largest form with few spills.
 constexpr int kMultiBlock = 384;
 
 struct MultiParams {
@@ -1691,7 +1706,7 @@ __global__ void __launch_bounds__(kMultiBlock, 1) pfac_filter_multi(const __grid
             reinterpret_cast<uint32_t *>(&p)[i] = reinterpret_cast<const uint32_t *>(&mp.a[a])[i];
         __syncthreads();
         if (threadIdx.x == 0) filter_load_tables(p, smem);
-        unsigned long long cnt = 0;
+        unsigned long long cnt = 0;  // batches have no count mode
         bool ok = true;
         switch (p.kind) {
             case filter_kind(2, 16): ok = filter_units<2, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
