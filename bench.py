@@ -305,7 +305,7 @@ def matching_launches(a, n: int, kernel: str, out_kind: str) -> int:
     if tun["survivor_list"] != 1:
         return 1
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    return 3 if n // 992 > 16 * sms * (tun["block"] // 32) else 1
+    return 3 if n // 992 > 16 * sms * (min(tun["block"] or 512, 512) // 32) else 1
 
 
 def run_ours(args, rank: int, world: int, local_rank: int):

@@ -314,7 +314,11 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
 /*
  * Launch shape of the root filter kernel (AC_KERNEL_TILED; no counterpart in
  * the paper).  Results never depend on it, only the time does.
- *   block         threads per CTA: a multiple of 32, 32 .. 512 (default 512).
+ *   block         threads per CTA: 0 = the kernel's choice (default): 640 for
+ *                 the one-phase single-text forms of 2- and 4-bit codes (20
+ *                 warps per SM, compiled at 96 registers), 512 elsewhere; or
+ *                 a multiple of 32, 32 .. 640 (above 512 only those forms;
+ *                 the others then run at 512).
  *   stages        text tiles in flight per warp: 2 .. 4, 0 = 3 (fewer when
  *                 shared memory is short).
  *   halo          bytes bulk-copied after each tile of 992 text bytes: 0 or
@@ -513,8 +517,8 @@ ac_status ac_batch_destroy(ac_batch b);
  * batches and servers).  The candidates, for an automaton with a root filter
  * (ac_tuning): the shared-table depth -- the filter as built and two smaller
  * ones (windows of one and two codes fewer, or a hashed filter of a quarter
- * and a sixteenth of the bits) -- x threads per CTA {256, 384, 512} x text
- * stages {2, 3, 4} (the shapes that fit shared memory); then, at the best of
+ * and a sixteenth of the bits) -- x threads per CTA {256, 384, 512, and 640
+ * for small alphabets} x text stages {2, 3, 4} (the shapes that fit shared memory); then, at the best of
  * those, the halo (16 bytes or the longest keyword, up to 256), the survivor
  * list on and off (when the sample is long enough for it) and, with the list,
  * chars per thread {2, 4}; with 8-bit codes also the kernels

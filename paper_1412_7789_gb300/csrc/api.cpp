@@ -678,7 +678,8 @@ ac_status ac_get_tuning(ac_handle h, ac_tuning *out) {
 
 ac_status ac_set_tuning(ac_handle h, const ac_tuning *tu) {
     if (!h || !tu) return AC_ERR_INVALID_ARG;
-    if (tu->block < 32 || tu->block > 512 || (tu->block & 31u) || (tu->stages != 0 && (tu->stages < 2 || tu->stages > 4)) ||
+    if ((tu->block != 0 && tu->block < 32) || tu->block > 640 || (tu->block & 31u) ||
+        (tu->stages != 0 && (tu->stages < 2 || tu->stages > 4)) ||
         tu->halo > pfac::kHaloCap || (tu->per_thread != 0 && tu->per_thread != 2 && tu->per_thread != 4) ||
         tu->survivor_list > 2)
         return AC_ERR_INVALID_ARG;
@@ -1041,7 +1042,7 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
         for (uint32_t i = 1; i <= 2; ++i)
             if (keep_key >= lo + i * step) depths.push_back(keep_key - i * step);
     }
-    static const int kBlocks[3] = {256, 384, 512};
+    static const int kBlocks[4] = {256, 384, 512, 640};  // 640: small alphabets' one-phase forms only
     // small alphabets: the filter kernel only; 8-bit codes: the filter kernel
     // with the hashed filter (when built) and the three 8-bit kernels
     std::vector<int> variants{0};
@@ -1060,8 +1061,9 @@ ac_status ac_autotune(ac_handle h, const uint8_t *d_sample, uint64_t n, uint32_t
         const bool filtered = v == 0 && root;
         for (size_t di = 0; di < (filtered ? depths.size() : 1u) && e == cudaSuccess && fail == AC_OK; ++di) {
             if (filtered) fail = use_root(h, depths[di]);
-            for (int bi = 0; bi < 3 && fail == AC_OK; ++bi)
+            for (int bi = 0; bi < 4 && fail == AC_OK; ++bi)
                 for (int sg = 2; sg <= 4; ++sg) {
+                    if (kBlocks[bi] > 512 && (v != 0 || !h->host.filter)) continue;  // a form of 512 at most
                     tu.block = kBlocks[bi];
                     tu.stages = sg;
                     time_one(tu);

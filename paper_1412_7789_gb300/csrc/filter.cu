@@ -168,8 +168,10 @@ bool filter_phased(const DevTables &t, const Tuning &tu, uint64_t n) {
     // tiles within the CTA (the launcher's test, with the most tiles the
     // text's alignment can give)
     const uint64_t sms = device_sm_count();
-    if (sms == 0 || tu.block < 32) return false;
-    const uint64_t grid = tu.grid > 0 ? static_cast<uint64_t>(tu.grid) : sms, nw = static_cast<uint64_t>(tu.block) / 32;
+    if (sms == 0) return false;
+    // the launcher's test for the forms that share heavy tiles (at most 512 threads)
+    const uint64_t grid = tu.grid > 0 ? static_cast<uint64_t>(tu.grid) : sms;
+    const uint64_t nw = static_cast<uint64_t>(tu.block > 0 && tu.block < kStdBlock ? tu.block : kStdBlock) / 32;
     return n / kTile > static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw;
 }
 
@@ -184,7 +186,7 @@ uint32_t device_sm_count() {
 
 cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                           cudaStream_t stream) {
-    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
+    if (tu.block < 0 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
         tu.stages > kMaxStages)
         return cudaErrorInvalidValue;
     DeviceShape ds;
@@ -194,11 +196,25 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     e = fill_params(t, r, mode, tu, p);
     if (e != cudaSuccess) return e;
     const bool batch = r.batch != nullptr;
-    const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
+    const uint32_t grid0 = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(ds.sms);
+    // a text short next to the grid: its heavy tiles (many survivors, long
+    // walks) would be one warp's work each while most warps have run out of
+    // tiles, so those forms share them within the CTA (small alphabets; the
+    // phased form lists heavy tiles like any other)
+    const uint32_t nw_std = static_cast<uint32_t>(tu.block > 0 && tu.block < kStdBlock ? tu.block : kStdBlock) / 32u;
+    const bool help = !batch && t.B <= 4 && !p.list &&
+                      static_cast<uint64_t>(p.ntiles) <= static_cast<uint64_t>(kHelpTilesPerWarp) * grid0 * nw_std;
+    // threads per CTA: the tuning's (0: 640 for the one-phase single-text
+    // forms of 2- and 4-bit codes, 512 elsewhere); the other forms run at
+    // most 512
+    const bool wide_form = t.B <= 4 && !batch && !help && !p.list;
+    uint32_t block = tu.block > 0 ? static_cast<uint32_t>(tu.block) : (wide_form ? kMaxBlock : kStdBlock);
+    if (!wide_form && block > static_cast<uint32_t>(kStdBlock)) block = kStdBlock;
+    const uint32_t nw = block / 32u;
     uint32_t smem = 0;
     if (!layout(p, p.staged, t.B, t.fbytes, nw, tu.stages ? tu.stages : 3, ds.max_smem, &smem))
         return cudaErrorInvalidConfiguration;
-    uint32_t grid = tu.grid > 0 ? static_cast<uint32_t>(tu.grid) : static_cast<uint32_t>(ds.sms);
+    uint32_t grid = grid0;
     if (!batch) {  // a batch's units are counted on the device: every CTA starts
         const uint32_t need_ctas = (p.ntiles + nw - 1) / nw;
         if (grid > need_ctas) grid = need_ctas;
@@ -206,21 +222,15 @@ cudaError_t launch_filter(const DevTables &t, const MatchRequest &r, OutMode mod
     if (!p.counter && (batch || static_cast<uint64_t>(p.ntiles) > static_cast<uint64_t>(grid) * nw))
         return cudaErrorInvalidValue;
     if (grid == 0) return cudaSuccess;
-    // a text short next to the grid: its heavy tiles (many survivors, long
-    // walks) would be one warp's work each while most warps have run out of
-    // tiles, so those forms share them within the CTA (small alphabets; the
-    // phased form lists heavy tiles like any other)
-    if (!batch && t.B <= 4 && !p.list &&
-        static_cast<uint64_t>(p.ntiles) <= static_cast<uint64_t>(kHelpTilesPerWarp) * grid * nw)
-        return launch_filter_help(mode, p, t.B, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
+    if (help) return launch_filter_help(mode, p, t.B, t.gbits, grid, block, smem, ds.max_smem, stream);
     if (t.B == 8)
-        e = launch_filter8(mode, p, t.gbits, grid, tu.block, smem, ds.max_smem, stream);
+        e = launch_filter8(mode, p, t.gbits, grid, block, smem, ds.max_smem, stream);
     else if (t.B == 2)
-        e = t.gbits == 16 ? launch_modes<2, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream)
-                          : launch_modes<2, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+        e = t.gbits == 16 ? launch_modes<2, int16_t, false>(mode, p, grid, block, smem, ds.max_smem, stream)
+                          : launch_modes<2, int32_t, false>(mode, p, grid, block, smem, ds.max_smem, stream);
     else
-        e = t.gbits == 16 ? launch_modes<4, int16_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream)
-                          : launch_modes<4, int32_t, false>(mode, p, grid, tu.block, smem, ds.max_smem, stream);
+        e = t.gbits == 16 ? launch_modes<4, int16_t, false>(mode, p, grid, block, smem, ds.max_smem, stream)
+                          : launch_modes<4, int32_t, false>(mode, p, grid, block, smem, ds.max_smem, stream);
     if (e == cudaSuccess && p.list)
         e = launch_survivors(mode, p, t.B, t.gbits, static_cast<uint32_t>(ds.sms), tu.per_thread, stream);
     return e;

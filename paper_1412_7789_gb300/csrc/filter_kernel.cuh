@@ -49,7 +49,11 @@ namespace pfac {
 // filter_help.cu the forms whose heavy tiles are shared within the CTA.
 namespace filt {
 
-constexpr int kMaxBlock = 512;
+// Threads per CTA: up to 512 for every form (128 registers a thread), up to
+// 640 for the one-phase single-text forms of 2- and 4-bit codes, compiled
+// apart at 96 registers (20 warps per SM measured faster than 16 there).
+constexpr int kStdBlock = 512;
+constexpr int kMaxBlock = 640;
 constexpr int kMaxWarps = kMaxBlock / 32;
 constexpr int kMaxStages = 4;
 constexpr uint32_t kOwnLanes = 31;            // lanes that own start positions in a pass
@@ -60,12 +64,12 @@ constexpr uint32_t kCodeSpan = kTile + 16;    // positions classified per tile
 constexpr uint32_t kOffJBar = 0;
 constexpr uint32_t kOffStageBar = 64;
 constexpr uint32_t kOffStageTile = kOffStageBar + kMaxWarps * kMaxStages * 8;
-constexpr uint32_t kOffRetired = 1008;  // warps of the CTA done with their own tiles
-constexpr uint32_t kOffOffers = 1012;   // heavy tiles offered and not yet finished
-static_assert(kOffStageTile + kMaxWarps * kMaxStages * 4 <= kOffRetired && kOffOffers + 4 <= 1024,
+constexpr uint32_t kOffRetired = 1024;  // warps of the CTA done with their own tiles
+constexpr uint32_t kOffOffers = 1028;   // heavy tiles offered and not yet finished
+static_assert(kOffStageTile + kMaxWarps * kMaxStages * 4 <= kOffRetired && kOffOffers + 4 <= 1152,
               "CTA counters overlap the stage descriptors or the class map");
-constexpr uint32_t kOffCls = 1024;  // 256 x uint8
-constexpr uint32_t kOffF = 1280;    // root filter bits
+constexpr uint32_t kOffCls = 1152;  // 256 x uint8
+constexpr uint32_t kOffF = 1408;    // root filter bits
 constexpr unsigned kFull = 0xffffffffu;
 // Texts of at most this many tiles per warp of the grid take the forms that
 // share heavy tiles within the CTA.
@@ -1409,8 +1413,8 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     return true;
 }
 
-template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED>
-__global__ void __launch_bounds__(kMaxBlock, 1) pfac_filter_pipe(const __grid_constant__ FilterParams p) {
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) pfac_filter_pipe(const __grid_constant__ FilterParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
     filter_setup(p, smem);
@@ -1880,14 +1884,14 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks_multi(c
 
 inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
 
-template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false>
-cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
-                       cudaStream_t stream) {
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false, int MAXT = kStdBlock>
+cudaError_t launch_one_bounded(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
+                               cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH, HELP, LISTED>;
+    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH, HELP, LISTED, MAXT>;
     if (!configured[dev]) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
@@ -1895,6 +1899,19 @@ cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uin
     }
     kernel<<<grid, block, smem, stream>>>(p);
     return cudaGetLastError();
+}
+
+// The forms at up to 512 threads; more only for the one-phase single-text
+// forms of 2- and 4-bit codes.
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false>
+cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
+                       cudaStream_t stream) {
+    if (block <= static_cast<uint32_t>(kStdBlock))
+        return launch_one_bounded<B, GT, MODE, BATCH, HELP, LISTED>(p, grid, block, smem, max_smem, stream);
+    if constexpr (B <= 4 && !BATCH && !HELP && !LISTED)
+        return launch_one_bounded<B, GT, MODE, false, false, false, kMaxBlock>(p, grid, block, smem, max_smem,
+                                                                             stream);
+    return cudaErrorInvalidConfiguration;
 }
 
 template <int B, typename GT, bool HELP>

@@ -696,8 +696,8 @@ uint32_t tiled_tile_positions() { return kTW; }
 
 cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode, const Tuning &tu,
                          cudaStream_t stream) {
-    if (tu.block < 32 || tu.block > kMaxBlock || (tu.block & 31) || (tu.stages != 0 && tu.stages < 2) ||
-        tu.stages > kMaxStages)
+    const int blk = tu.block > 0 ? tu.block : kMaxBlock;  // 0: the default, 512
+    if (blk < 32 || blk > kMaxBlock || (blk & 31) || (tu.stages != 0 && tu.stages < 2) || tu.stages > kMaxStages)
         return cudaErrorInvalidValue;
     if (t.B != 8) return cudaErrorInvalidValue;  // small alphabets use the filter kernel
     // default (variant 0): the full-occupancy one-thread-per-position kernel,
@@ -724,7 +724,7 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     }
     p.ntiles = static_cast<uint32_t>(tiles);
     // per warp: stages, survivor queue, pass buffer, stage descriptors
-    const uint32_t nw = static_cast<uint32_t>(tu.block) / 32u;
+    const uint32_t nw = static_cast<uint32_t>(blk) / 32u;
     uint32_t smem = 0;
     bool fits = false;
     for (int st = tu.stages ? tu.stages : 3; st >= 2 && !fits; --st) {
@@ -761,7 +761,7 @@ cudaError_t launch_tiled(const DevTables &t, const MatchRequest &r, OutMode mode
     if (!p.counter && (batch || static_cast<uint64_t>(p.ntiles) > static_cast<uint64_t>(grid) * nw))
         return cudaErrorInvalidValue;
     if (grid == 0) return cudaSuccess;
-    const uint32_t block = static_cast<uint32_t>(tu.block);
+    const uint32_t block = static_cast<uint32_t>(blk);
     const bool inv = t.C < 256;
     if (t.gbits == 16) {
         if (inv) return launch_modes<true, int16_t>(mode, p, grid, block, smem, dp.max_smem, stream);

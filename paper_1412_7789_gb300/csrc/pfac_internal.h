@@ -308,7 +308,9 @@ inline void set_lists(MatchRequest &r, void *scratch, const SurvivorLists &s) {
 
 
 struct Tuning {
-    int block = 512;      // threads per CTA (multiple of 32, <= 512)
+    int block = 0;        // threads per CTA (multiple of 32, <= 640; 0 = the kernel's choice:
+                          // 640 for the one-phase single-text filter forms of 2- and
+                          // 4-bit codes, 512 elsewhere; above 512 only those forms)
     int stages = 0;       // text stages in flight per warp (2..4, 0 = the kernel's default;
                           // fewer when shared memory is short)
     int grid = 0;         // 0 = one CTA per SM
