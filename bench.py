@@ -34,10 +34,13 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the kernel as it stands, keyed by (workload, text bytes,
-# kernel): a capture of a 256 MiB launch of the same workload, scaled by 4 to
-# the 1 GiB launch (the traffic grows with the positions).  Drop an entry
-# whenever its kernel changes.
-KNOWN_TRAFFIC: dict = {}
+# kernel): a capture of a 256 MiB launch of the same workload and launch
+# form, scaled by 4 to the 1 GiB launch (the traffic grows with the positions;
+# profiles/pfac_filter_pipe_acgt_256mib_full.md: 344.2 MB read + 1019.9 MB
+# written).  Drop an entry whenever its kernel changes.
+KNOWN_TRAFFIC: dict = {
+    ("sweep", GIB, "pfac_filter_pipe"): 4 * (344.151040e6 + 1019.929e6),
+}
 
 
 def kernel_name(info: dict, out_kind: str, kernel: str, phased: bool = False) -> str:
@@ -434,7 +437,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     kname = kernel_name(info, out_kind, args.kernel, matching_launches(a, n, args.kernel, out_kind) > 1)
     traffic = args.traffic
     if traffic is None:
-        traffic = KNOWN_TRAFFIC.get((args.workload, n, kname))
+        # the captured launch form: the default tuning only
+        traffic = None if args.tune else KNOWN_TRAFFIC.get((args.workload, n, kname))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_kind": peak_kind,
             # context: the nominal HBM3e figure (7.9 TB/s) beside the measured copy peak
