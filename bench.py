@@ -707,12 +707,16 @@ def run_sweep(args):
     for key in ("gpu_kernel_s", "gpu_call_s", "gpu_e2e_s"):
         c = _crossing(coarse, key)
         if c is not None and c["below_range"]:
-            # extend below the smallest coarse size
+            # extend below the smallest coarse size (if the GPU loses there
+            # in every new point, keep the coarse answer: at or below 4 KiB)
+            c0 = c
             pts = [timer.point(n) for n in (16, 64, 256, 1024, 4096)]
             c = _crossing(pts, key)
             if c is not None and not c["below_range"]:
                 _, c2 = _refine(timer, c["bracket"][0], c["bracket"][1], key)
                 c = c2 or c
+            elif c is None:
+                c = c0
         elif c is not None:
             _, c2 = _refine(timer, c["bracket"][0], c["bracket"][1], key)
             c = c2 or c

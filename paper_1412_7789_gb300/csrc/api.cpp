@@ -321,7 +321,7 @@ cudaError_t run_full(ac_automaton *h, const uint8_t *text, uint64_t n, const pfa
                      cudaStream_t st) {
     const uint32_t units = pfac::compact_units(h->dev, h->tuning, text, n);
     if (units == 0xFFFFFFFFu) return cudaErrorInvalidValue;
-    const size_t bytes = pfac::full_scratch_bytes(h->dev, units);
+    const size_t bytes = pfac::full_scratch_bytes(h->dev, h->tuning, units, n);
     cudaMemPool_t pool = nullptr;
     cudaError_t e = scratch_pool(h->device, &pool);
     if (e != cudaSuccess) return e;

@@ -9,7 +9,8 @@
 // are prefixes of r (the builder's full-output records: r's string, its equal
 // keywords, and the chain of proper-prefix keywords).  After the slot-mode
 // matching kernel (per tile its match count and first 32 matches, plus its
-// dense ids when it has more):
+// dense ids when it has more; with the phased form's lists no tile keeps dense
+// ids, and a tile with more than 32 matches is matched again here):
 //   full_count   one warp per tile: the tile's occurrences, the sum of the
 //                chain lengths of its results;
 //   scan         the exclusive prefix of those counts over the tiles
@@ -31,10 +32,10 @@ constexpr int kFullThreads = 256;
 constexpr uint32_t kRows = 8;  // rows of 32 dense ids loaded together
 constexpr unsigned kFull = 0xffffffffu;
 
-struct FullParams {
+struct FullParams : RootWalk {
+    const uint8_t *text;
     uint64_t n;
     uint32_t units, tile, head, max_clen, nkw;
-    unsigned int *err;
     const uint32_t *counts;
     const unsigned long long *slots;
     const int32_t *dense;
@@ -55,13 +56,17 @@ __device__ __forceinline__ uint32_t chain_len(const FullParams &p, uint32_t id) 
     return __ldg(reinterpret_cast<const uint32_t *>(p.rec) + 4ull * id + 3u);
 }
 
-// The dense id of tile position i of unit u (-1 outside the text).
+// The dense id of tile position i of unit u (-1 outside the text): kept by
+// the matching kernel, or (no dense ids) the walk from the root again.
+template <typename GT>
 __device__ __forceinline__ int dense_id(const FullParams &p, uint32_t u, int64_t gpb, uint32_t i) {
     const int64_t gp = gpb + static_cast<int64_t>(i);
     if (gp < 0 || static_cast<uint64_t>(gp) >= p.n) return -1;
+    if (!p.dense) return walk_from_root<GT>(p, p.text, p.n, static_cast<uint64_t>(gp));
     return __ldg(p.dense + static_cast<uint64_t>(u) * kDenseStride + i);
 }
 
+template <typename GT>
 __global__ void __launch_bounds__(kFullThreads) full_count(const FullParams p) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(kFullThreads) full_count(const FullParams p) {
                     int id[kRows];
 #pragma unroll
                     for (uint32_t j = 0; j < kRows; ++j)
-                        id[j] = i0 + 32 * j < p.tile ? dense_id(p, u, gpb, i0 + 32 * j + lane) : -1;
+                        id[j] = i0 + 32 * j < p.tile ? dense_id<GT>(p, u, gpb, i0 + 32 * j + lane) : -1;
 #pragma unroll
                     for (uint32_t j = 0; j < kRows; ++j)
                         if (id[j] >= 0) sum += chain_len(p, static_cast<uint32_t>(id[j]));
@@ -122,6 +127,7 @@ __device__ __forceinline__ void put_chain(const FullParams &p, unsigned long lon
     }
 }
 
+template <typename GT>
 __global__ void __launch_bounds__(kFullThreads) full_gather(const FullParams p) {
     const int lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(kFullThreads) full_gather(const FullParams p) 
                     uint32_t cl[kRows];
 #pragma unroll
                     for (uint32_t j = 0; j < kRows; ++j)
-                        id[j] = i0 + 32 * j < p.tile ? dense_id(p, u, gpb, i0 + 32 * j + lane) : -1;
+                        id[j] = i0 + 32 * j < p.tile ? dense_id<GT>(p, u, gpb, i0 + 32 * j + lane) : -1;
 #pragma unroll
                     for (uint32_t j = 0; j < kRows; ++j)
                         cl[j] = id[j] >= 0 ? chain_len(p, static_cast<uint32_t>(id[j])) : 0u;
@@ -188,11 +194,17 @@ inline size_t round16(size_t v) { return (v + 15u) & ~static_cast<size_t>(15u); 
 
 }  // namespace
 
-// Layout: the compacted output's scratch with its dense fallback | occurrence
-// counts (4 per unit) | their prefix (8 per unit) | partial sums (8 * kScanCtas).
-size_t full_scratch_bytes(const DevTables &t, uint32_t units) {
+// Layout: the compacted output's scratch (with its dense fallback, or without
+// it when the phased form's lists follow) | occurrence counts (4 per unit) |
+// their prefix (8 per unit) | partial sums (8 * kScanCtas) | the lists.
+size_t full_scratch_bytes(const DevTables &t, const Tuning &tu, uint32_t units, uint64_t n) {
     const size_t U = units;
-    return round16(compact_scratch_bytes(t, units, true)) + round16(4 * U) + 8 * U + 8 * static_cast<size_t>(kScanCtas);
+    SurvivorLists sl;
+    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n);
+    const bool dense = sl.list_cap == 0;
+    return round16(round16(compact_scratch_bytes(t, units, dense)) + round16(4 * U) + 8 * U +
+                   8 * static_cast<size_t>(kScanCtas)) +
+           sl.bytes();
 }
 
 cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
@@ -200,14 +212,17 @@ cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *te
     const uint32_t U = compact_units(t, tu, text, n);
     if (U == 0xFFFFFFFFu || n == 0 || n > 0xFFFFFFFFull || !t.full_rec || !t.full_dups)
         return cudaErrorInvalidValue;
-    if (!scratch || scratch_bytes < full_scratch_bytes(t, U)) return cudaErrorInvalidValue;
+    if (!scratch || scratch_bytes < full_scratch_bytes(t, tu, U, n)) return cudaErrorInvalidValue;
+    SurvivorLists sl;
+    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n);
+    const bool dense = sl.list_cap == 0;
     uint8_t *b = static_cast<uint8_t *>(scratch);
     // the compacted output's layout (compact.cu): tile counter | counts | prefix | slots | partials | dense
     uint32_t *counts = reinterpret_cast<uint32_t *>(b + 16);
     unsigned long long *slots =
         reinterpret_cast<unsigned long long *>(b + 16 + round16(4 * size_t(U))) + static_cast<size_t>(U);
-    int32_t *dn = reinterpret_cast<int32_t *>(b + compact_dense_offset(U));
-    uint8_t *f = b + round16(compact_scratch_bytes(t, U, true));
+    int32_t *dn = dense ? reinterpret_cast<int32_t *>(b + compact_dense_offset(U)) : nullptr;
+    uint8_t *f = b + round16(compact_scratch_bytes(t, U, dense));
     uint32_t *fcounts = reinterpret_cast<uint32_t *>(f);
     unsigned long long *fprefix = reinterpret_cast<unsigned long long *>(f + round16(4 * size_t(U)));
     unsigned long long *fpartials = fprefix + U;
@@ -223,6 +238,12 @@ cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *te
     r.slots.dense = dn;
     r.scratch = b;
     r.scratch_bytes = 16;
+    if (!dense) {  // the phased form's lists after the rest
+        uint8_t *lb = f + round16(round16(4 * size_t(U)) + 8 * size_t(U) + 8 * static_cast<size_t>(kScanCtas));
+        e = cudaMemsetAsync(lb, 0, 32, stream);
+        if (e != cudaSuccess) return e;
+        set_lists(r, lb, sl);
+    }
     e = launch_match(t, r, OUT_SLOTS, tu, stream);
     if (e != cudaSuccess) return e;
 
@@ -231,6 +252,15 @@ cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *te
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     FullParams p{};
+    p.G = t.G;
+    p.cls8 = t.cls8;
+    p.W = t.W;
+    p.C = t.C;
+    p.maxlen = t.maxlen;
+    p.skip = t.skip;
+    p.chain = t.chain;
+    p.s_chain = t.skip ? t.s_chain : 0xFFFFFFFFu;
+    p.text = text;
     p.n = n;
     p.units = U;
     p.tile = unit_positions(t, tu);
@@ -251,12 +281,18 @@ cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *te
     uint32_t grid = static_cast<uint32_t>(sms) * 8u;  // grid-stride over units
     const uint32_t need = (U + per_cta - 1) / per_cta;
     if (grid > need) grid = need;
-    full_count<<<grid, kFullThreads, 0, stream>>>(p);
+    if (t.gbits == 16)
+        full_count<int16_t><<<grid, kFullThreads, 0, stream>>>(p);
+    else
+        full_count<int32_t><<<grid, kFullThreads, 0, stream>>>(p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = launch_compact_scan(fcounts, U, nullptr, fprefix, fpartials, stream);
     if (e != cudaSuccess) return e;
-    full_gather<<<grid, kFullThreads, 0, stream>>>(p);
+    if (t.gbits == 16)
+        full_gather<int16_t><<<grid, kFullThreads, 0, stream>>>(p);
+    else
+        full_gather<int32_t><<<grid, kFullThreads, 0, stream>>>(p);
     return cudaGetLastError();
 }
 

@@ -358,4 +358,52 @@ __device__ __forceinline__ int goto_ld_hint(const int16_t *G, uint32_t s, uint32
     return static_cast<int>(v);
 }
 
+// The tables a plain walk from the root needs (the compaction and full-output
+// steps match a unit again with it when it has no dense fallback).
+struct RootWalk {
+    const void *G;
+    const uint8_t *cls8;
+    uint32_t W, C, maxlen;
+    unsigned int *err;
+    const uint4 *skip;      // chain records from state s_chain on
+    const uint8_t *chain;
+    uint32_t s_chain;       // 0xFFFFFFFF: none
+};
+
+// The id of the longest keyword starting at text position gp: the walk from
+// the root through the goto table (and the chain records).
+template <typename GT>
+__device__ int walk_from_root(const RootWalk &p, const uint8_t *text, uint64_t n, uint64_t gp) {
+    const GT *G = static_cast<const GT *>(p.G);
+    uint32_t s = 0;
+    uint64_t q = gp;
+    for (uint32_t step = 0; step <= p.maxlen + 1; ++step, ++q) {
+        if (s >= p.s_chain) {  // a run of forced transitions, a leaf, or a branch
+            const uint4 rc = __ldg(p.skip + (s - p.s_chain));
+            if (rc.x != kSkipBranch) {
+                const bool ok = rc.x > 0 && q + rc.x <= n && run_equal(text + q, p.chain + rc.y, rc.x);
+                if (!ok) return static_cast<int>(rc.w);
+                s = rc.z;
+                q += rc.x - 1;  // the loop adds one
+                continue;
+            }
+        }
+        uint32_t c = p.C;
+        if (q < n) {
+            const uint32_t b = __ldg(text + q);
+            if (p.C >= 256) {
+                c = b;  // one column per byte value: every byte is a keyword byte
+            } else {
+                const uint32_t v = __ldg(p.cls8 + b);
+                if (v != 0xFFu) c = v;
+            }
+        }
+        const int e = goto_ld(G, s, p.W, c);
+        if (e < 0) return decode_dead(e);
+        s = static_cast<uint32_t>(e);
+    }
+    atomicOr(p.err, static_cast<unsigned>(kErrWalk));
+    return -1;
+}
+
 }  // namespace pfac

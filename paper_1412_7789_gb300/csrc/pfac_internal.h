@@ -382,8 +382,9 @@ constexpr uint32_t kMinTile = 992;
 // Full output of one text (full.cu): every keyword occurrence as (end, id)
 // into out.pos / out.ids, ordered by start, end, id; the slot-mode matching
 // kernel, per-unit occurrence counts, their scan, and the expansion.  Scratch:
-// full_scratch_bytes(t, units) bytes, units = compact_units(t, text, n).
-size_t full_scratch_bytes(const DevTables &t, uint32_t units);
+// full_scratch_bytes(t, tu, units, n) bytes, units = compact_units(t, tu,
+// text, n) (with the phased form's lists when the text takes that form).
+size_t full_scratch_bytes(const DevTables &t, const Tuning &tu, uint32_t units, uint64_t n);
 cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *text, uint64_t n,
                          const CompactOut &out, void *scratch, size_t scratch_bytes, cudaStream_t stream);
 

@@ -127,6 +127,29 @@ def test_full_8bit_kernels(kernel):
         check(a.handle, pats, text)
 
 
+@pytest.mark.parametrize("kind", ["zipf", "dense_bytes"])
+def test_full_phased_form(kind):
+    """Texts long enough for the phased form (8-bit codes, 5 MiB): its second
+    and third steps feed the expansion, and with no dense fallback a tile with
+    more than 32 matches is matched again by the expansion kernels.  Zipf
+    keywords with their prefixes; and every string of 1-2 bytes over a few
+    byte values (every position matches several times, so nearly every tile
+    is matched again)."""
+    g = np.random.default_rng(21)
+    if kind == "zipf":
+        text = workloads.zipf_text(5 << 20, 23)
+        pats = workloads.keywords_zipf(text[:1 << 20], 3000, 3, 40, 0.5, seed=24)
+        pats = pats + [p[:max(1, len(p) // 2)] for p in pats[:500]]
+    else:
+        vals = np.frombuffer(bytes(range(60, 80)), dtype=np.uint8)
+        text = vals[g.integers(0, vals.size, size=5 << 20)].copy()
+        text[g.integers(0, text.size, size=1000)] = 200  # bytes in no keyword
+        pats = [bytes([a]) for a in vals] + [bytes([a, b]) for a in vals[:8] for b in vals[:8]]  # 20 keyword bytes
+    with api.Automaton(pats) as a:
+        assert a.info()["code_bits"] == 8
+        check(a.handle, pats, text)
+
+
 def test_full_dense_tiles():
     """Every string of length 1..3 over ACGT is a keyword (with repeats): every
     position starts three occurrences, so every tile has more matches than its
