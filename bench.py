@@ -294,8 +294,10 @@ def matching_launches(a, n: int, kernel: str, out_kind: str) -> int:
     """Kernels one matching call launches before any compaction: the filter
     kernel, plus the survivor and walk steps of its phased form (single texts
     with dense, count or compacted output: 8-bit codes from 4 MiB on unless
-    the tuning says never, 2- and 4-bit codes when the tuning asks for it,
-    beyond the texts whose heavy tiles are shared within the CTA)."""
+    the tuning says never; 2- and 4-bit codes when the tuning asks for it or,
+    by default for dense ids and counts, when 500 per million or more of their
+    root windows end a keyword, beyond the texts whose heavy tiles are shared
+    within the CTA)."""
     import torch
 
     info, tun = a.info(), a.tuning()
@@ -305,7 +307,7 @@ def matching_launches(a, n: int, kernel: str, out_kind: str) -> int:
         return 1
     if info["code_bits"] == 8:
         return 3 if n >= (4 << 20) else 1
-    if tun["survivor_list"] != 1:
+    if tun["survivor_list"] != 1 and (info["match_windows_ppm"] < 500 or out_kind == "compact"):
         return 1
     sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     return 3 if n // 992 > 16 * sms * (min(tun["block"] or 512, 512) // 32) else 1

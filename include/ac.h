@@ -125,6 +125,10 @@ typedef struct {
     int32_t class_hash_shift; /* s when (byte >> s) & 7 tells the keyword bytes apart
                                  (at most 8 of them; bytes are then classified with
                                  byte permutes), else -1 (class table)             */
+    uint32_t match_windows_ppm; /* 2- and 4-bit codes: parts per million of the
+                                 jump_depth-code windows on whose walk from the root
+                                 a keyword ends (from 500 on, long texts list their
+                                 survivors for a second kernel by default), else 0 */
 } ac_info_t;
 
 void ac_default_options(ac_options *opt);
@@ -345,12 +349,18 @@ ac_status ac_set_kernel(ac_handle h, ac_kernel kernel);
  *                 tables.  AC_ERR_INVALID_ARG for an automaton without a
  *                 root filter, or a size below the smallest filter.
  *   survivor_list how the filter kernel resolves its survivors on long single
- *                 texts (dense, count, compacted): 0 = default (listed for a
- *                 second kernel with 8-bit codes from 4 MiB on, else in the
- *                 warp that filtered them, pipelined across its tiles); 1 =
- *                 listed also for 2- and 4-bit codes (texts beyond those
- *                 whose heavy tiles are shared within the CTA, about 38 MB
- *                 at 512 threads on 152 SMs); 2 = always in the warp.
+ *                 texts (dense, count, compacted; one-launch batches and
+ *                 server waves with lists follow the default rule):
+ *                 0 = default (small alphabets: dense ids and counts): listed for two more kernels with 8-bit codes
+ *                 (single texts from 4 MiB on), and with 2- and 4-bit codes
+ *                 when at least 500 per million of the root filter's windows
+ *                 already hold a match (keywords shorter than the window and
+ *                 stride depth, whose many matches the warps' pipeline writes
+ *                 position by position); else in the warp that filtered
+ *                 them, pipelined across its tiles.  1 = listed for every
+ *                 code width; 2 = always in the warp.  Small alphabets list
+ *                 only beyond the texts whose heavy tiles are shared within
+ *                 the CTA (about 38 MB at 512 threads on 152 SMs).
  * ac_set_tuning validates every field before changing any; do not call it
  * while work on h is being enqueued from another thread.  Batch plans and
  * servers read the tuning of their handles at each launch (a captured batch
@@ -432,7 +442,8 @@ ac_status ac_match_compact_static(ac_handle h, const uint8_t *d_text, uint64_t n
  * serves up to 32 automata with root filters (every automaton has one unless
  * built with jump_bytes below 4); it runs the filter kernel for each, whatever
  * kernel ac_set_kernel or ac_autotune chose for its single texts (and, with a
- * plan's survivor lists, lists the survivors of its 8-bit-code automata for
+ * plan's survivor lists, lists the survivors of its 8-bit-code automata, and
+ * of those with 2- or 4-bit codes whose match_windows_ppm is 500 or more, for
  * two more launches: ac_batch_reserve_lists).  Otherwise the batch takes one
  * persistent launch per automaton.  Results are exactly
  * those of ac_match on each text alone: walks stop at the end of their own
@@ -486,7 +497,9 @@ ac_status ac_match_batch(const ac_handle *hs, uint32_t nh, const uint8_t *d_text
  *                    in flight.
  *   ac_batch_reserve_lists
  *                    sizes the plan's survivor lists for the phased form of
- *                    its 8-bit-code automata: with the one persistent launch,
+ *                    its 8-bit-code automata (and the 2- and 4-bit ones
+ *                    with match_windows_ppm of 500 or more): with the one
+ *                    persistent launch,
  *                    their survivors (up to text_bytes / 8 of them per run)
  *                    are listed and resolved by two further launches at full
  *                    occupancy, as ac_match does for one long text; tiles

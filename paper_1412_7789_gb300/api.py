@@ -78,6 +78,7 @@ class ac_info_t(ctypes.Structure):
         ("depth_base_jump", ctypes.c_uint32),
         ("count_jump", ctypes.c_uint32),
         ("class_hash_shift", ctypes.c_int32),
+        ("match_windows_ppm", ctypes.c_uint32),
     ]
 
 

@@ -126,6 +126,7 @@ ac_status use_root(ac_automaton *h, uint32_t key) {
         b.t.base_k = t.base_k;
         b.t.count_k = t.count_k;
         b.t.fbits = t.fbits;
+        b.t.match_windows_ppm = t.match_windows_ppm;
         b.t.F = t.F;
         if (t.filter) {
             b.t.JK = t.JK;
@@ -177,6 +178,8 @@ ac_status use_root(ac_automaton *h, uint32_t key) {
         t.count_k = rs.t.count_k;
         t.JK = rs.t.JK;
         t.J2 = rs.t.J2;
+        t.match_windows_ppm = rs.t.match_windows_ppm;
+        d.list_prefer = t.match_windows_ppm >= pfac::kListMatchWindowsPpm;
         d.JK = rs.JK;
         d.J2 = rs.J2;
     } else {
@@ -302,7 +305,7 @@ cudaError_t run_compact(ac_automaton *h, const uint8_t *text, uint64_t n, const 
     // the phased form's lists instead of the dense fallback when it applies
     // (the gather then matches an overflowing unit again)
     pfac::SurvivorLists sl;
-    if (pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, h->tuning, n);
+    if (pfac::uses_filter(h->dev, h->tuning)) sl = pfac::survivor_lists(h->dev, h->tuning, n, true);
     const bool dense = sl.list_cap == 0;
     const size_t bytes = pfac::compact_scratch_bytes(h->dev, units, dense) + sl.bytes();
     cudaMemPool_t pool = nullptr;
@@ -472,6 +475,7 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     d.jbytes = static_cast<uint32_t>(t.J.size() * sizeof(int16_t));
     d.jslow = t.jslow;
     d.filter = t.filter;
+    d.list_prefer = t.filter && t.match_windows_ppm >= pfac::kListMatchWindowsPpm;
     d.hashed = t.hashed;
     d.kh = t.kh;
     d.fbits = t.fbits;
@@ -559,6 +563,7 @@ ac_status ac_info(ac_handle h, ac_info_t *info) {
     info->depth_base_jump = t.base_k;
     info->count_jump = t.count_k;
     info->class_hash_shift = t.hash_shift;
+    info->match_windows_ppm = t.B <= 4 ? t.match_windows_ppm : 0u;
     return AC_OK;
 }
 

@@ -215,13 +215,16 @@ void window_tables(const HostTables &h, uint32_t k, uint64_t stride_bytes, RootT
     // code stream.
     rt->F.assign(std::max<uint32_t>(nwin / 32u, 4u), 0u);
     rt->JK.assign(nwin, 0);
+    uint64_t found = 0;
     for (uint32_t w = 0; w < nwin; ++w) {
         int32_t e = 0;
         const bool alive = walk_window(h, 0, w, k, &e);
         rt->JK[w] = e;
+        found += e < -1 ? 1u : 0u;
         if (alive || e < -1)
             for (uint32_t v = w; v < std::max<uint32_t>(nwin, 32u); v += nwin) rt->F[v >> 5] |= 1u << (31u - (v & 31u));
     }
+    rt->match_windows_ppm = static_cast<uint32_t>(found * 1000000ull / nwin);
     stride_rows(h, rt, stride_bytes);
 }
 
@@ -440,6 +443,7 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             h.base_k = rt.base_k;
             h.count_k = rt.count_k;
             h.k2 = rt.k2;
+            h.match_windows_ppm = rt.match_windows_ppm;
             h.F = std::move(rt.F);
             h.JK = std::move(rt.JK);
             h.J2 = std::move(rt.J2);

@@ -287,7 +287,7 @@ cudaError_t enqueue_compact(const DevTables &t, const Tuning &tu, const uint8_t 
     // keep no dense fallback (the gather matches an overflowing unit again)
     const size_t lo = compact_scratch_bytes(t, U, dense);
     SurvivorLists sl;
-    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n);
+    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n, true);
     if (sl.list_cap && scratch_bytes >= lo + sl.bytes()) {
         e = cudaMemsetAsync(b + lo, 0, 32, stream);
         if (e != cudaSuccess) return e;

@@ -160,10 +160,10 @@ cudaError_t device_shape(DeviceShape *out) {
 
 }  // namespace
 
-bool filter_phased(const DevTables &t, const Tuning &tu, uint64_t n) {
+bool filter_phased(const DevTables &t, const Tuning &tu, uint64_t n, bool slots) {
     if (!served(t) || n / kTile >= (1ull << 22) - 1 || tu.survivor_list == 2) return false;
     if (t.B == 8) return n >= (4ull << 20);
-    if (tu.survivor_list != 1) return false;
+    if (tu.survivor_list != 1 && (slots || !t.list_prefer)) return false;
     // small alphabets: beyond the texts that take the forms sharing heavy
     // tiles within the CTA (the launcher's test, with the most tiles the
     // text's alignment can give)
@@ -263,13 +263,19 @@ cudaError_t launch_filter_multi(const DevTables *const *ts, const MatchRequest *
     uint32_t staged = 0, B = 0, fbytes = 0;
     Tuning tu;
     tu.wait_ns = wait_ns;
-    // the phased form's lists (8-bit-code automata), when given
+    // the phased form's lists, when given
     mp.list = nullptr;
     mp.list_count = nullptr;
     mp.list_cap = mp.walk_cap = 0;
     mp.walks4 = nullptr;
+    // the automata that list: 8-bit codes, and small alphabets that prefer it;
+    // with slots only those without a dense fallback (the listed survivors
+    // write none of it: the gather matches an overflowing unit again)
+    auto lists_for = [&](uint32_t a) {
+        return (ts[a]->B == 8 || ts[a]->list_prefer) && (mode == OUT_DENSE || !rs[a].slots.dense);
+    };
     bool listed = false;
-    for (uint32_t a = 0; a < nh; ++a) listed = listed || ts[a]->B == 8;
+    for (uint32_t a = 0; a < nh; ++a) listed = listed || lists_for(a);
     if (lists && list_cap && listed) {
         uint8_t *b = static_cast<uint8_t *>(lists);
         mp.list_count = reinterpret_cast<unsigned int *>(b);
@@ -283,7 +289,7 @@ cudaError_t launch_filter_multi(const DevTables *const *ts, const MatchRequest *
         e = fill_params(*ts[a], rs[a], mode, tu, mp.a[a]);
         if (e != cudaSuccess) return e;
         mp.a[a].aidx = a;
-        if (mp.list && ts[a]->B == 8) {
+        if (mp.list && lists_for(a)) {
             mp.a[a].list = mp.list;
             mp.a[a].list_count = mp.list_count;
             mp.a[a].list_cap = mp.list_cap;

@@ -1123,9 +1123,8 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
             // batch, unit numbers past 22 bits.  (Each lane writing its own
             // survivors' entries straight from its filter bits, without the
             // queue, measured slower: the stores no longer coalesce.)
-            static_assert(!BATCH || B == 8, "batches list 8-bit codes only");
-            const bool listable = B == 8 ? !__any_sync(kFull, (slowm & sv) != 0u) && (!BATCH || wk.units < (1u << 22))
-                                         : interior && clean;
+            const bool listable = (B == 8 ? !__any_sync(kFull, (slowm & sv) != 0u) : interior && clean) &&
+                                  (!BATCH || wk.units < (1u << 22));
             if (p.list && !lfull && total > 0 && listable) {
                 if (lend - lnext < total) {
                     // a new chunk of list space (the rest of the old one: empty)
@@ -1159,7 +1158,8 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                                                            ca | (BATCH ? p.aidx << 16 : 0u), BATCH ? item : 0u);
                         } else {
                             // the window's and the stride window's codes (i + k + k2 < kCodeSpan)
-                            p.list[lnext + j] = make_uint4((tile << 10) | i, code_window<B>(w.packed, i), 0u, 0u);
+                            p.list[lnext + j] = make_uint4((tile << 10) | i, code_window<B>(w.packed, i),
+                                                           BATCH ? p.aidx << 16 : 0u, BATCH ? item : 0u);
                         }
                     }
                     lnext += total;
@@ -1713,10 +1713,10 @@ __global__ void __launch_bounds__(kMultiBlock, 1) pfac_filter_multi(const __grid
         unsigned long long cnt = 0;  // batches have no count mode
         bool ok = true;
         switch (p.kind) {
-            case filter_kind(2, 16): ok = filter_units<2, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
-            case filter_kind(2, 32): ok = filter_units<2, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
-            case filter_kind(4, 16): ok = filter_units<4, int16_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
-            case filter_kind(4, 32): ok = filter_units<4, int32_t, MODE, true, false>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(2, 16): ok = filter_units<2, int16_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(2, 32): ok = filter_units<2, int32_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(4, 16): ok = filter_units<4, int16_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
+            case filter_kind(4, 32): ok = filter_units<4, int32_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
             case filter_kind(8, 16): ok = filter_units<8, int16_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
             default: ok = filter_units<8, int32_t, MODE, true, false, LISTED>(p, smem, it, loads & 1u, cnt, &it); break;
         }
@@ -1776,6 +1776,8 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_survivors_mul
     for (uint32_t wb = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wb < m; wb += SPT * stride) {
         const uint32_t b0 = wb + static_cast<uint32_t>(lane);
         uint4 e[SPT], he[SPT];
+        // first loads: 8-bit codes the state-hash bucket, small alphabets the
+        // window table (he[].x)
 #pragma unroll
         for (int t = 0; t < SPT; ++t) {
             const uint32_t idx = b0 + static_cast<uint32_t>(t) * stride;
@@ -1783,40 +1785,73 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_survivors_mul
             he[t] = make_uint4(0u, 0u, 0u, 0u);
             if (e[t].x != 0xFFFFFFFFu) {
                 const FilterParams &P = ps[(e[t].z >> 16) & (kMultiMax - 1u)];
-                he[t] = __ldg(P.HK + hk_slot(P, e[t].y));
+                if ((P.kind >> 8) == 8u)
+                    he[t] = __ldg(P.HK + hk_slot(P, e[t].y));
+                else
+                    he[t].x = static_cast<uint32_t>(__ldg(P.JK + (e[t].y & ((1u << ((P.kind >> 8) * P.k)) - 1u))));
             }
         }
         int r[SPT], g[SPT];
         uint32_t s[SPT], q[SPT];
         bool walk[SPT];
+        // second loads: 8-bit codes the first goto step of a branching state,
+        // small alphabets the stride table
 #pragma unroll
         for (int t = 0; t < SPT; ++t) {
             const bool on = e[t].x != 0xFFFFFFFFu;
             const FilterParams &P = ps[(e[t].z >> 16) & (kMultiMax - 1u)];
-            const uint32_t i = e[t].x & 1023u, c = e[t].z & 0x1FFu;
+            const uint32_t i = e[t].x & 1023u, c = e[t].z & 0x1FFu, Bq = P.kind >> 8;
             r[t] = -1;
             s[t] = 0;
             q[t] = 0;
-            walk[t] = on && !hk_outcome(P, hk_find(P, e[t].y, he[t]), i, c & 0xFFu, c < 0x100u, r[t], s[t], q[t]);
-            if (walk[t]) r[t] = -1;
             g[t] = 0;
-            if (walk[t] && q[t] == i + P.k) {
-                const uint32_t col = c < 0x100u ? c : P.C;
-                g[t] = (P.kind & 0xFFu) == 16u ? goto_ld(static_cast<const int16_t *>(P.G), s[t], P.W, col)
-                                               : goto_ld(static_cast<const int32_t *>(P.G), s[t], P.W, col);
+            if (Bq == 8u) {
+                walk[t] = on && !hk_outcome(P, hk_find(P, e[t].y, he[t]), i, c & 0xFFu, c < 0x100u, r[t], s[t], q[t]);
+                if (walk[t]) r[t] = -1;
+                if (walk[t] && q[t] == i + P.k) {
+                    const uint32_t col = c < 0x100u ? c : P.C;
+                    g[t] = (P.kind & 0xFFu) == 16u ? goto_ld(static_cast<const int16_t *>(P.G), s[t], P.W, col)
+                                                   : goto_ld(static_cast<const int32_t *>(P.G), s[t], P.W, col);
+                }
+            } else {
+                walk[t] = false;
+                if (!on) continue;
+                const int j1 = static_cast<int>(he[t].x);
+                if (j1 < 0) {
+                    r[t] = decode_dead(j1);
+                } else if (P.k2) {
+                    g[t] = __ldg(P.J2 + ((static_cast<uint64_t>(static_cast<uint32_t>(j1) - P.base_k) << (Bq * P.k2)) |
+                                         ((e[t].y >> (Bq * P.k)) & ((1u << (Bq * P.k2)) - 1u))));
+                    walk[t] = true;  // settled below by the stride entry
+                    s[t] = 0xFFFFFFFFu;
+                } else {
+                    walk[t] = true;
+                    s[t] = static_cast<uint32_t>(j1);
+                    q[t] = i + P.k;
+                }
             }
         }
 #pragma unroll
         for (int t = 0; t < SPT; ++t) {
             const FilterParams &P = ps[(e[t].z >> 16) & (kMultiMax - 1u)];
             const uint32_t i = e[t].x & 1023u;
-            if (walk[t] && q[t] == i + P.k) {
+            if ((P.kind >> 8) == 8u) {
+                if (walk[t] && q[t] == i + P.k) {
+                    if (g[t] < 0) {
+                        r[t] = decode_dead(g[t]);
+                        walk[t] = false;
+                    } else {
+                        s[t] = static_cast<uint32_t>(g[t]);
+                        ++q[t];
+                    }
+                }
+            } else if (walk[t] && s[t] == 0xFFFFFFFFu) {  // the stride entry
                 if (g[t] < 0) {
                     r[t] = decode_dead(g[t]);
                     walk[t] = false;
                 } else {
                     s[t] = static_cast<uint32_t>(g[t]);
-                    ++q[t];
+                    q[t] = i + P.k + P.k2;
                 }
             }
         }

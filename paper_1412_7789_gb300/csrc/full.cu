@@ -200,7 +200,7 @@ inline size_t round16(size_t v) { return (v + 15u) & ~static_cast<size_t>(15u); 
 size_t full_scratch_bytes(const DevTables &t, const Tuning &tu, uint32_t units, uint64_t n) {
     const size_t U = units;
     SurvivorLists sl;
-    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n);
+    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n, true);
     const bool dense = sl.list_cap == 0;
     return round16(round16(compact_scratch_bytes(t, units, dense)) + round16(4 * U) + 8 * U +
                    8 * static_cast<size_t>(kScanCtas)) +
@@ -214,7 +214,7 @@ cudaError_t enqueue_full(const DevTables &t, const Tuning &tu, const uint8_t *te
         return cudaErrorInvalidValue;
     if (!scratch || scratch_bytes < full_scratch_bytes(t, tu, U, n)) return cudaErrorInvalidValue;
     SurvivorLists sl;
-    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n);
+    if (uses_filter(t, tu)) sl = survivor_lists(t, tu, n, true);
     const bool dense = sl.list_cap == 0;
     uint8_t *b = static_cast<uint8_t *>(scratch);
     // the compacted output's layout (compact.cu): tile counter | counts | prefix | slots | partials | dense

@@ -98,6 +98,7 @@ struct HostTables {
     bool filter = false;             // B <= 4: root filter + window table instead of J
     std::vector<uint32_t> F;         // filter bits, 2^(B*k) (at least 4 words)
     std::vector<int32_t> JK;         // window table, 2^(B*k) entries
+    uint32_t match_windows_ppm = 0;  // windows of JK whose walk found a keyword, per million
     std::vector<int16_t> J;          // 2^(B*k) (padded to 8 entries)
     std::vector<int32_t> J2;         // count_k << (B*k2)
     std::vector<uint32_t> depth_count;  // maxlen + 1
@@ -144,7 +145,18 @@ struct RootTables {
     uint32_t fbits = 0;                                // 8-bit codes
     std::vector<uint32_t> F;
     std::vector<int32_t> JK, J2;
+    // 2- and 4-bit codes: the windows whose walk already found a keyword, per
+    // million windows (the share of positions where a match ends inside the
+    // window on uniform text)
+    uint32_t match_windows_ppm = 0;
 };
+// Windows with a match inside, per million, from which small-alphabet
+// automata resolve survivors in the phased form by default: with matches that
+// common the warps' in-tile pipeline writes ids position by position and
+// falls behind the listed form (1 GiB sweep set: 0 ppm, in the warps 1.11 ms
+// against 1.24 listed; 256 MiB batch sets with 8-byte keywords: 1,100-9,000
+// ppm, listed 8-66 % faster; 290 ppm, in the warps 6 % faster).
+constexpr uint32_t kListMatchWindowsPpm = 500;
 // 2- and 4-bit codes: the root filter and window table over windows of k codes
 // (1 <= k, B k <= kFilterBits), and the stride table from the depth-k states
 // (at most stride_bytes; none when 0 or 1).
@@ -163,6 +175,7 @@ struct DevTables {
     const int32_t *JK = nullptr;     // window table (filter mode)
     uint32_t fbytes = 0;             // bytes of F
     bool filter = false;             // 2- and 4-bit codes: root filter + window table
+    bool list_prefer = false;        // small alphabets: the phased form by default (kListMatchWindowsPpm)
     bool hashed = false;             // 8-bit codes: hashed root filter + state hash
     const uint4 *HK = nullptr;       // state hash buckets (hashed)
     uint32_t kh = 0, fbits = 0, hk_bits = 0, hk_probes = 0;
@@ -278,19 +291,22 @@ uint32_t device_sm_count();                  // of the current device (cached; 0
 struct Tuning;
 // Whether the filter kernel takes the phased form for a text of n bytes
 // (filter.cu): 8-bit codes from 4 MiB on; 2- and 4-bit codes, when the
-// tuning asks for it, beyond the texts short enough for the forms that share
-// heavy tiles within the CTA.  Never for texts of more tiles than the entries
-// can name.
-bool filter_phased(const DevTables &t, const Tuning &tu, uint64_t n);
+// tuning asks for it or, for dense ids and counts (not slots), when the
+// automaton prefers it (list_prefer), beyond the texts short enough for the
+// forms that share heavy tiles within the CTA.  Never for texts of more
+// tiles than the entries can name, nor when the tuning says never.  (Listed
+// units keep no dense fallback, and the sets that prefer listing have tiles
+// of many matches, which the gather would then match again.)
+bool filter_phased(const DevTables &t, const Tuning &tu, uint64_t n, bool slots = false);
 struct SurvivorLists {
     uint32_t list_cap = 0, walk_cap = 0;
     size_t bytes() const { return list_cap ? 32 + 16ull * list_cap + 8ull * walk_cap : 0; }
 };
 // The lists of a text of n bytes (none: the one-phase form).  Scratch
 // layout: two counters (32 bytes, zeroed) | list_cap uint4 | walk_cap uint2.
-inline SurvivorLists survivor_lists(const DevTables &t, const Tuning &tu, uint64_t n) {
+inline SurvivorLists survivor_lists(const DevTables &t, const Tuning &tu, uint64_t n, bool slots = false) {
     SurvivorLists s;
-    if (!filter_phased(t, tu, n)) return s;
+    if (!filter_phased(t, tu, n, slots)) return s;
     const uint64_t sms = device_sm_count();
     if (sms == 0) return s;
     s.list_cap = static_cast<uint32_t>(n / 8);  // 12.5 % of the positions
@@ -322,8 +338,8 @@ struct Tuning {
                           // step takes at a time (2, or 4 with fewer threads; 0 = 2)
     int halo = 0;         // bytes staged after each tile: 0 = the 16 the filter reads,
                           // or up to kHaloCap (a wider halo reaches L2 ahead of the walks)
-    int survivor_list = 0;  // long single texts: 0 = the phased form for 8-bit codes only,
-                            // 1 = also for 2- and 4-bit codes, 2 = never
+    int survivor_list = 0;  // long single texts: 0 = the phased form for 8-bit codes and for
+                            // small alphabets with list_prefer, 1 = for every code width, 2 = never
     unsigned long long wait_ns = 0;  // bounded waits give up after this (0 = kWaitNs)
     int stall_help = 0;   // test aid: owners wait for one chunk more than their heavy tile has
 };

@@ -119,6 +119,9 @@ uint64_t units_of(const ac_server_impl *s, const ac_server_request &r) {
 
 // Whether automaton a's texts may take survivor lists for the phased form:
 // 8-bit codes in one-launch waves, or (FIFO) as ac_match_compact takes them.
+// (Small alphabets keep their dense fallback: the sets whose windows often
+// end a keyword have tiles of many matches, which the gather would otherwise
+// match again.)
 bool wave_lists(const ac_server_impl *s, uint32_t a) { return (s->multi || s->fifo) && s->tabs[a]->B == 8; }
 
 // Device bytes a request holds while admitted: its text (a host text's device
@@ -183,7 +186,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
         const uint32_t units = pfac::compact_units(t, tu, tb ? nullptr : q.r.d_text, q.r.n);
         // as ac_match_compact: the phased form's lists instead of the dense fallback when it applies
         pfac::SurvivorLists sl;
-        if (pfac::uses_filter(t, tu)) sl = pfac::survivor_lists(t, tu, q.r.n);
+        if (pfac::uses_filter(t, tu)) sl = pfac::survivor_lists(t, tu, q.r.n, true);
         const bool dense = sl.list_cap == 0;
         const size_t bytes = tb + pfac::compact_scratch_bytes(t, units, dense) + sl.bytes();
         void *scratch = nullptr;
@@ -261,7 +264,7 @@ cudaError_t launch_wave(ac_server_impl *s, WaveSlot &w) {
     // the one launch), when they hold 4 MiB or more (below that the two extra
     // launches cost more than they save); with them those automata's units
     // keep no dense fallback (the gather matches a unit with more matches
-    // than slots again), the others' do
+    // than slots again), the others' do (and so list nothing)
     uint64_t list_text = 0;
     for (uint32_t k = 0; k < L; ++k)
         if (s->multi && wave_lists(s, w.reqs[order[k]].r.automaton)) list_text += w.reqs[order[k]].r.n;

@@ -427,6 +427,7 @@ def _check_window_tables(h):
         s = np.where(live & (e > 0), e, s)
     alive = res == -2
     assert np.array_equal(JK, np.where(alive, s, -(res + 2)))
+    assert info["match_windows_ppm"] == int((res >= 0).sum()) * 10**6 // v.size
     want = alive | (res >= 0)
     wb = B * k
     famask = (((1 << wb) if wb >= 5 else 32) // 8 - 1) & ~3

@@ -165,7 +165,9 @@ def test_batch_plan_run_capture_replay(automata):
 @pytest.mark.parametrize("reserve", [64 << 20, 4096])
 def test_batch_plan_survivor_lists(automata, reserve):
     """The phased form inside the one persistent launch: the plan's 8-bit-code
-    automata list their survivors for the second and third launches.  The
+    automata, and the 2- and 4-bit ones whose root windows often end a
+    keyword (the first two sets; not the long-keyword one), list their
+    survivors for the second and third launches.  The
     edge batch and a batch of longer texts (every kind, Zipf ones up to 1.5
     MB), run and captured: every text's ids are the oracle's, nothing outside
     the output ranges is written.  A 4 KiB reservation (512 entries) overflows
@@ -175,6 +177,8 @@ def test_batch_plan_survivor_lists(automata, reserve):
 
     sets, hs = automata
     handles = [a.handle for a in hs]
+    ppm = [a.info()["match_windows_ppm"] for a in hs]
+    assert ppm[0] >= 500 and ppm[1] >= 500 and ppm[4] < 500
     g = np.random.default_rng(77)
     texts, kinds, text_off, out_off, buf_len, out_len = _edge_batch(sets, 5)
     lens = [int(x) for x in g.integers(100_000, 1_500_000, size=10)]

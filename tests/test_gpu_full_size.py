@@ -137,10 +137,12 @@ def test_match_host_every_position():
         _par.check_dense(got, p, i, "host small")
 
 
+@pytest.mark.parametrize("listed", [0, 1])
 @pytest.mark.parametrize("kind", ["short_keywords", "dense_matches"])
-def test_phased_small_alphabet_and_list_overflow(kind):
-    """2- and 4-bit codes on texts long enough for the phased form (asked
-    for with the survivor_list knob): ACGT
+def test_phased_small_alphabet_and_list_overflow(kind, listed):
+    """2- and 4-bit codes on texts long enough for the phased form (by
+    default for dense ids and counts, as both sets' root windows often end a
+    keyword, and for every output when the survivor_list knob asks): ACGT
     keywords of 1-3 bytes (nearly every position survives, so the survivor
     list fills and most tiles fall back to their warps), and a 12-letter set
     whose windows often reach the stride table and beyond (the walk list),
@@ -164,8 +166,9 @@ def test_phased_small_alphabet_and_list_overflow(kind):
     wpos, wids = _par.oracle_compact(pats, text)
     t = _gpu_tensor(text)
     with api.Automaton(pats) as a:
-        assert a.info()["code_bits"] in (2, 4)
-        a.set_tuning(survivor_list=1)
+        info = a.info()
+        assert info["code_bits"] in (2, 4) and info["match_windows_ppm"] >= 500
+        a.set_tuning(survivor_list=listed)
         _all_outputs(a, t, text.size, wpos, wids, kind)
 
 
