@@ -36,10 +36,10 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 # ncu capture of the kernel as it stands, keyed by (workload, text bytes,
 # kernel): a capture of a 256 MiB launch of the same workload and launch
 # form, scaled by 4 to the 1 GiB launch (the traffic grows with the positions;
-# profiles/pfac_filter_pipe_acgt_256mib_full.md: 344.2 MB read + 1019.9 MB
-# written).  Drop an entry whenever its kernel changes.
+# the 256 MiB capture read 344.5 MB and wrote 1021.4 MB).  Drop an entry
+# whenever its kernel changes.
 KNOWN_TRAFFIC: dict = {
-    ("sweep", GIB, "pfac_filter_pipe"): 4 * (344.151040e6 + 1019.929e6),
+    ("sweep", GIB, "pfac_filter_pipe"): 4 * (344.534528e6 + 1021.447e6),
 }
 
 
@@ -890,10 +890,13 @@ def batch_line(args) -> dict:
 
     plan = api.BatchPlan(handles, max_items=len(texts))
     nitems = len(texts)
-    # the phased form for the 8-bit-code sets: lists sized for all their text
+    # the phased form for the sets that list (8-bit codes; 2- and 4-bit codes
+    # whose root windows often end a keyword): lists sized for all their text
     list_bytes = 0
     if not args.no_batch_lists:
-        list_bytes = int(sum(int(lens[i]) for i in range(nitems) if autos[which[i]].info()["code_bits"] == 8))
+        infos = [a.info() for a in autos]
+        lists = [f["code_bits"] == 8 or f["match_windows_ppm"] >= 500 for f in infos]
+        list_bytes = int(sum(int(lens[i]) for i in range(nitems) if lists[which[i]]))
         plan.reserve_lists(list_bytes)
 
     def graph_step():

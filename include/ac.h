@@ -129,6 +129,10 @@ typedef struct {
                                  jump_depth-code windows on whose walk from the root
                                  a keyword ends (from 500 on, long texts list their
                                  survivors for a second kernel by default), else 0 */
+    int32_t class_direct_shift; /* 1 when the four keyword bytes have class codes
+                                 (byte >> 1) & 3 (the DNA letters in either case:
+                                 the kernel then takes codes from one multiply per
+                                 four bytes), else -1                             */
 } ac_info_t;
 
 void ac_default_options(ac_options *opt);

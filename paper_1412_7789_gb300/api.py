@@ -79,6 +79,7 @@ class ac_info_t(ctypes.Structure):
         ("count_jump", ctypes.c_uint32),
         ("class_hash_shift", ctypes.c_int32),
         ("match_windows_ppm", ctypes.c_uint32),
+        ("class_direct_shift", ctypes.c_int32),
     ]
 
 

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(BUILD_DIR, "libpfac.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["builder.cpp", "api.cpp", "serve.cpp", "kernels.cu", "jump8.cu", "filter.cu", "filter8.cu", "noalloc.cu",
-           "batch.cu", "compact.cu", "full.cu", "filter_help.cu", "filter_multi_dense.cu", "filter_multi_slots.cu", "survivors.cu"]
+           "batch.cu", "compact.cu", "full.cu", "filter_help.cu", "filter_multi_dense.cu", "filter_multi_slots.cu", "survivors.cu",
+           "filter_direct.cu"]
 HEADERS = ["pfac_internal.h", "pfac_device.cuh", "filter_kernel.cuh"]
 
 

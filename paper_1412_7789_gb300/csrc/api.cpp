@@ -487,6 +487,16 @@ ac_status ac_compile(const uint8_t *const *patterns, const uint32_t *lens, uint3
     d.nkw = t.nkw;
     std::memcpy(d.hash_code, t.hash_code, 8);
     std::memcpy(d.hash_byte, t.hash_byte, 8);
+    d.direct_shift = t.direct_shift;
+    if (t.direct_shift == 1) {  // byte 2c of the pair
+        d.direct_sel[0] = t.direct_byte[0] | (static_cast<uint32_t>(t.direct_byte[1]) << 16);
+        d.direct_sel[1] = t.direct_byte[2] | (static_cast<uint32_t>(t.direct_byte[3]) << 16);
+        for (uint32_t b = 0; b < 256; ++b)
+            if (t.cls8[b] == 0xFF) {
+                d.direct_fill = b;
+                break;
+            }
+    }
     if (!h->host_only) {
         if (cudaGetDevice(&h->device) != cudaSuccess) {
             cudaGetLastError();
@@ -564,6 +574,7 @@ ac_status ac_info(ac_handle h, ac_info_t *info) {
     info->count_jump = t.count_k;
     info->class_hash_shift = t.hash_shift;
     info->match_windows_ppm = t.B <= 4 ? t.match_windows_ppm : 0u;
+    info->class_direct_shift = t.direct_shift;
     return AC_OK;
 }
 

@@ -271,6 +271,26 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             for (int b = 0; b < 256; ++b) h.cls[b] = static_cast<int16_t>(b);
             h.C = 256;
         }
+        // four keyword bytes that (byte >> 1) & 3 tells apart (the DNA
+        // letters in either case): that value becomes their class code
+        h.direct_shift = -1;
+        if (h.C == 4) {
+            int seen[4] = {-1, -1, -1, -1};
+            bool ok = true;
+            for (int b = 0; b < 256 && ok; ++b) {
+                if (h.cls[b] < 0) continue;
+                const int v = (b >> 1) & 3;
+                if (seen[v] >= 0) ok = false;
+                seen[v] = b;
+            }
+            if (ok) {
+                h.direct_shift = 1;
+                for (int v = 0; v < 4; ++v) {
+                    h.direct_byte[v] = static_cast<uint8_t>(seen[v]);
+                    h.cls[seen[v]] = static_cast<int16_t>(v);
+                }
+            }
+        }
         h.cls8.assign(256, 0xFF);
         for (int b = 0; b < 256; ++b)
             if (h.cls[b] >= 0) h.cls8[b] = static_cast<uint8_t>(h.cls[b]);

@@ -94,6 +94,10 @@ cudaError_t fill_params(const DevTables &t, const MatchRequest &r, OutMode mode,
     p.hcode_hi = t.hash_code[1];
     p.hbyte_lo = t.hash_byte[0];
     p.hbyte_hi = t.hash_byte[1];
+    p.direct_shift = t.B == 2 ? t.direct_shift : -1;
+    p.dsel_lo = t.direct_sel[0];
+    p.dsel_hi = t.direct_sel[1];
+    p.dfill = t.direct_fill;
     p.out = r.out;
     p.count = r.count;
     p.sl = r.slots;

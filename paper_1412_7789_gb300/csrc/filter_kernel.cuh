@@ -100,6 +100,9 @@ struct FilterParams {
     uint32_t famask;  // byte offsets of the root filter's words reached by a window
     int hash_shift;
     uint32_t hcode_lo, hcode_hi, hbyte_lo, hbyte_hi;
+    int direct_shift;            // 1: 2-bit codes (byte >> 1) & 3, else -1
+    uint32_t dsel_lo, dsel_hi;   // byte 2c of the pair: the keyword byte of code c
+    uint32_t dfill;              // a byte in no keyword
     int32_t *out;
     unsigned long long *count;
     SlotOut sl;
@@ -299,6 +302,29 @@ __device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
     return ((t & 0x80808080u) * 0x00204081u) >> 28;
 }
 
+
+// Flags (bit b) of the 16 positions g0 + b outside the text [0, n).
+__device__ __forceinline__ uint32_t outside_marks(int64_t g0, int64_t n) {
+    uint32_t iv = 0;
+    if (!(g0 >= 0 && g0 + 16 <= n)) {
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+            if (g0 + b < 0 || g0 + b >= n) iv |= 1u << b;
+    }
+    return iv;
+}
+
+// Flags (bit b) of the 16 bytes of raw in no keyword (class table entry
+// 0xFF).  Out of line: the kernels that call it do so rarely.
+static __device__ __noinline__ uint32_t unknown_flags16(const uint8_t *cls8, const uint4 raw) {
+    const uint32_t v[4] = {raw.x, raw.y, raw.z, raw.w};
+    uint32_t iv = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        if (cls8[(v[j >> 2] >> (8 * (j & 3))) & 0xFFu] == 0xFFu) iv |= 1u << j;
+    return iv;
+}
+
 // Pack the low B bits of the 4 byte codes of `codes` (4 B bits, first byte lowest).
 template <int B>
 __device__ __forceinline__ uint32_t pack4(uint32_t codes) {
@@ -314,6 +340,12 @@ template <int B>
 __device__ __forceinline__ uint32_t code_window(const uint32_t *packed, uint32_t i) {
     const uint32_t bo = B * i, w = bo >> 5;
     return __funnelshift_r(packed[w], packed[w + 1], bo & 31u);
+}
+
+// The "cannot extend a walk" flags of tile positions j, j + 1, ... (bit 0
+// for j; at least 17 of them): two 16-bit entries joined, then shifted.
+__device__ __forceinline__ uint32_t inv_flags(const WarpSmem &w, uint32_t j) {
+    return (static_cast<uint32_t>(w.inv[j >> 4]) | (static_cast<uint32_t>(w.inv[(j >> 4) + 1]) << 16)) >> (j & 15u);
 }
 
 // Code of tile position q; false when q cannot extend a walk.  Positions below
@@ -455,7 +487,7 @@ __device__ __forceinline__ bool finish_survivors(const FilterParams &p, const Ti
                 bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(ii[t] + k + k2) <= n);
                 if (ok2 && !clean) {
                     const uint32_t j = ii[t] + k;
-                    const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
+                    const uint32_t wi = inv_flags(w, j);
                     ok2 = (wi & ((1u << k2) - 1u)) == 0;
                 }
                 if (ok2) {
@@ -884,7 +916,7 @@ __device__ __forceinline__ void filter_load_tables(const FilterParams &p, uint8_
 // HELP: share heavy tiles within the CTA (the forms for one text that is short
 // next to the grid; see the heavy path below).  LISTED: the first phase of the
 // phased form (p.list set; the forms without it carry none of its code).
-template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false>
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false, bool DIRECT = false>
 __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *smem, uint32_t it0, uint32_t jpar,
                                              unsigned long long &cnt, uint32_t *it_next) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -961,60 +993,97 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
         const bool interior = gpb >= 0 && gpb + static_cast<int64_t>(p.staged) <= n;
         if (!interior) {
             load_text_fringe(tt, p.staged, st, tlo, lane);
+            if constexpr (B == 2 && DIRECT) {
+                // the staged bytes outside the text become a byte in no
+                // keyword, so the classification flags them as it does those
+                __syncwarp();
+                for (uint32_t q = static_cast<uint32_t>(lane); q < p.staged; q += 32u) {
+                    const int64_t g = gpb + static_cast<int64_t>(q);
+                    if (g < 0 || g >= n) st[q] = static_cast<uint8_t>(p.dfill);
+                }
+            }
             __syncwarp();
         }
 
         // 1. classify the tile's bytes (both halves), once per byte
         uint32_t plo[2], phi[2], inv[2];
         uint32_t p8[2][4];  // 8-bit codes: the lane's 16 codes of each half
+        if constexpr (B == 2 && DIRECT) {
+            // Class codes (byte >> 1) & 3: masked in place, one multiply
+            // gathers a word's four codes into its top byte (code j, at bit
+            // 8j + 1, times 2^(23 - 6j) lands at bit 24 + 2j; the other
+            // products land below bit 24 without carrying into it), and
+            // byte permutes join the four top bytes.  A byte is a keyword
+            // byte exactly when the keyword byte of its code equals it: a
+            // byte permute selected by 2 x code (the masked word with the
+            // next byte's bits moved to the high nibble, bytes 0 and 2
+            // joined) picks it from p.dsel_lo/hi.  Only a word pair that
+            // differs somewhere has its bytes flagged one by one (through
+            // the class table); positions outside the text hold p.dfill,
+            // a byte in no keyword.
+            constexpr uint32_t dmask = 0x06060606u, dmul = 0x01041040u >> 1;
 #pragma unroll
-        for (uint32_t h = 0; h < 2; ++h) {
-            const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
-            const uint4 raw = *reinterpret_cast<const uint4 *>(st + i0);
-            uint32_t c0, c1, c2, c3, u0, u1, u2, u3;
-            if constexpr (B == 8) {
-                classify_word8(p, w.cls8, raw.x, c0, u0);
-                classify_word8(p, w.cls8, raw.y, c1, u1);
-                classify_word8(p, w.cls8, raw.z, c2, u2);
-                classify_word8(p, w.cls8, raw.w, c3, u3);
-            } else {
-                classify_word(p, w.cls8, raw.x, c0, u0);
-                classify_word(p, w.cls8, raw.y, c1, u1);
-                classify_word(p, w.cls8, raw.z, c2, u2);
-                classify_word(p, w.cls8, raw.w, c3, u3);
-            }
-            uint32_t iv = 0;
-            if (u0 | u1 | u2 | u3)
-                iv = nonzero_bytes(u0) | (nonzero_bytes(u1) << 4) | (nonzero_bytes(u2) << 8) |
-                     (nonzero_bytes(u3) << 12);
-            if (!interior) {
-                const int64_t g0 = gpb + i0;
-                if (!(g0 >= 0 && g0 + 16 <= n)) {
-#pragma unroll
-                    for (int b = 0; b < 16; ++b)
-                        if (g0 + b < 0 || g0 + b >= n) iv |= 1u << b;
-                }
-            }
-            inv[h] = iv;
-            if constexpr (B == 2) {
-                plo[h] = pack4<2>(c0) | (pack4<2>(c1) << 8) | (pack4<2>(c2) << 16) | (pack4<2>(c3) << 24);
+            for (uint32_t h = 0; h < 2; ++h) {
+                const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
+                const uint4 raw = *reinterpret_cast<const uint4 *>(st + i0);
+                const uint32_t x0 = raw.x & dmask, x1 = raw.y & dmask, x2 = raw.z & dmask, x3 = raw.w & dmask;
+                plo[h] = __byte_perm(__byte_perm(x0 * dmul, x1 * dmul, 0x0073u),
+                                     __byte_perm(x2 * dmul, x3 * dmul, 0x0073u), 0x5410u);
                 phi[h] = 0;
+                const uint32_t any =
+                    (raw.x ^ __byte_perm(p.dsel_lo, p.dsel_hi, __byte_perm(x0 | (x0 >> 4), 0u, 0x4420u))) |
+                    (raw.y ^ __byte_perm(p.dsel_lo, p.dsel_hi, __byte_perm(x1 | (x1 >> 4), 0u, 0x4420u))) |
+                    (raw.z ^ __byte_perm(p.dsel_lo, p.dsel_hi, __byte_perm(x2 | (x2 >> 4), 0u, 0x4420u))) |
+                    (raw.w ^ __byte_perm(p.dsel_lo, p.dsel_hi, __byte_perm(x3 | (x3 >> 4), 0u, 0x4420u)));
+                uint32_t iv = 0;
+                if (any) iv = unknown_flags16(w.cls8, raw);
+                inv[h] = iv;
                 w.packed[i0 >> 4] = plo[h];
-            } else if constexpr (B == 4) {
-                plo[h] = pack4<4>(c0) | (pack4<4>(c1) << 16);
-                phi[h] = pack4<4>(c2) | (pack4<4>(c3) << 16);
-                w.packed[i0 >> 3] = plo[h];
-                w.packed[(i0 >> 3) + 1] = phi[h];
-            } else {
-                p8[h][0] = c0;
-                p8[h][1] = c1;
-                p8[h][2] = c2;
-                p8[h][3] = c3;
-                plo[h] = c0;
-                phi[h] = 0;
-                *reinterpret_cast<uint4 *>(w.packed + (i0 >> 2)) = make_uint4(c0, c1, c2, c3);
+                w.inv[i0 >> 4] = static_cast<uint16_t>(iv);
             }
-            w.inv[i0 >> 4] = static_cast<uint16_t>(iv);
+        } else {
+#pragma unroll
+            for (uint32_t h = 0; h < 2; ++h) {
+                const uint32_t i0 = h * kPass + 16u * static_cast<uint32_t>(lane);
+                const uint4 raw = *reinterpret_cast<const uint4 *>(st + i0);
+                uint32_t c0, c1, c2, c3, u0, u1, u2, u3;
+                if constexpr (B == 8) {
+                    classify_word8(p, w.cls8, raw.x, c0, u0);
+                    classify_word8(p, w.cls8, raw.y, c1, u1);
+                    classify_word8(p, w.cls8, raw.z, c2, u2);
+                    classify_word8(p, w.cls8, raw.w, c3, u3);
+                } else {
+                    classify_word(p, w.cls8, raw.x, c0, u0);
+                    classify_word(p, w.cls8, raw.y, c1, u1);
+                    classify_word(p, w.cls8, raw.z, c2, u2);
+                    classify_word(p, w.cls8, raw.w, c3, u3);
+                }
+                uint32_t iv = 0;
+                if (u0 | u1 | u2 | u3)
+                    iv = nonzero_bytes(u0) | (nonzero_bytes(u1) << 4) | (nonzero_bytes(u2) << 8) |
+                         (nonzero_bytes(u3) << 12);
+                if (!interior) iv |= outside_marks(gpb + i0, n);
+                inv[h] = iv;
+                if constexpr (B == 2) {
+                    plo[h] = pack4<2>(c0) | (pack4<2>(c1) << 8) | (pack4<2>(c2) << 16) | (pack4<2>(c3) << 24);
+                    phi[h] = 0;
+                    w.packed[i0 >> 4] = plo[h];
+                } else if constexpr (B == 4) {
+                    plo[h] = pack4<4>(c0) | (pack4<4>(c1) << 16);
+                    phi[h] = pack4<4>(c2) | (pack4<4>(c3) << 16);
+                    w.packed[i0 >> 3] = plo[h];
+                    w.packed[(i0 >> 3) + 1] = phi[h];
+                } else {
+                    p8[h][0] = c0;
+                    p8[h][1] = c1;
+                    p8[h][2] = c2;
+                    p8[h][3] = c3;
+                    plo[h] = c0;
+                    phi[h] = 0;
+                    *reinterpret_cast<uint4 *>(w.packed + (i0 >> 2)) = make_uint4(c0, c1, c2, c3);
+                }
+                w.inv[i0 >> 4] = static_cast<uint16_t>(iv);
+            }
         }
         const bool clean = !__any_sync(kFull, (inv[0] | inv[1]) != 0);
         __syncwarp();
@@ -1338,7 +1407,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                     bool ok2 = k2 > 0 && (interior || gpb + static_cast<int64_t>(i + k + k2) <= n);
                     if (ok2 && !clean) {
                         const uint32_t j = i + k;
-                        const uint32_t wi = __funnelshift_r(w.inv[j >> 4], w.inv[(j >> 4) + 1], j & 15u);
+                        const uint32_t wi = inv_flags(w, j);
                         ok2 = (wi & ((1u << k2) - 1u)) == 0;
                     }
                     f0.ok2 = ok2 ? 1u : 0u;
@@ -1413,7 +1482,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
     return true;
 }
 
-template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED, int MAXT>
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED, int MAXT, bool DIRECT>
 __global__ void __launch_bounds__(MAXT, 1) pfac_filter_pipe(const __grid_constant__ FilterParams p) {
     extern __shared__ __align__(128) uint8_t smem[];
     const int lane = threadIdx.x & 31;
@@ -1421,7 +1490,7 @@ __global__ void __launch_bounds__(MAXT, 1) pfac_filter_pipe(const __grid_constan
     if (threadIdx.x == 0) filter_load_tables(p, smem);
     unsigned long long cnt = 0;
     uint32_t it = 0;
-    if (!filter_units<B, GT, MODE, BATCH, HELP, LISTED>(p, smem, 0, 0, cnt, &it)) return;
+    if (!filter_units<B, GT, MODE, BATCH, HELP, LISTED, DIRECT>(p, smem, 0, 0, cnt, &it)) return;
     if (MODE == OUT_DENSE && lane == 0) bulk_wait_all();
     if (MODE == OUT_COUNT) {
 #pragma unroll
@@ -1919,14 +1988,15 @@ __global__ void __launch_bounds__(kSurvBlock, surv_ctas<2>()) pfac_walks_multi(c
 
 inline uint32_t align16(uint32_t v) { return (v + 15u) & ~15u; }
 
-template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false, int MAXT = kStdBlock>
+template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false, int MAXT = kStdBlock,
+          bool DIRECT = false>
 cudaError_t launch_one_bounded(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
                                cudaStream_t stream) {
     static bool configured[64] = {false};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH, HELP, LISTED, MAXT>;
+    void (*kernel)(const FilterParams) = pfac_filter_pipe<B, GT, MODE, BATCH, HELP, LISTED, MAXT, DIRECT>;
     if (!configured[dev]) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
@@ -1936,16 +2006,25 @@ cudaError_t launch_one_bounded(const FilterParams &p, uint32_t grid, uint32_t bl
     return cudaGetLastError();
 }
 
+// The one-phase single-text forms of 2-bit codes at more than 512 threads
+// whose codes come from (byte >> 1) & 3 (DIRECT), filter_direct.cu.
+cudaError_t launch_filter_direct(int mode, const FilterParams &p, uint32_t gbits, uint32_t grid, uint32_t block,
+                                 uint32_t smem, int max_smem, cudaStream_t stream);
+
 // The forms at up to 512 threads; more only for the one-phase single-text
-// forms of 2- and 4-bit codes.
+// forms of 2- and 4-bit codes (2-bit codes with p.direct_shift set: the
+// DIRECT forms).
 template <int B, typename GT, int MODE, bool BATCH, bool HELP, bool LISTED = false>
 cudaError_t launch_one(const FilterParams &p, uint32_t grid, uint32_t block, uint32_t smem, int max_smem,
                        cudaStream_t stream) {
     if (block <= static_cast<uint32_t>(kStdBlock))
         return launch_one_bounded<B, GT, MODE, BATCH, HELP, LISTED>(p, grid, block, smem, max_smem, stream);
-    if constexpr (B <= 4 && !BATCH && !HELP && !LISTED)
+    if constexpr (B <= 4 && !BATCH && !HELP && !LISTED) {
+        if (B == 2 && p.direct_shift == 1)
+            return launch_filter_direct(MODE, p, 8u * sizeof(GT), grid, block, smem, max_smem, stream);
         return launch_one_bounded<B, GT, MODE, false, false, false, kMaxBlock>(p, grid, block, smem, max_smem,
                                                                              stream);
+    }
     return cudaErrorInvalidConfiguration;
 }
 

@@ -94,6 +94,12 @@ struct HostTables {
     int hash_shift = -1;
     uint8_t hash_code[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint8_t hash_byte[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // Exactly four keyword bytes that (byte >> 1) & 3 tells apart (the DNA
+    // letters, either case): their class codes are that value, so the kernel
+    // computes four codes with one multiply (direct_shift = 1); direct_byte[c]
+    // is the keyword byte of code c.  Else direct_shift = -1.
+    int direct_shift = -1;
+    uint8_t direct_byte[4] = {0, 0, 0, 0};
     RawBytes G;                      // S * W entries of gbits
     bool filter = false;             // B <= 4: root filter + window table instead of J
     std::vector<uint32_t> F;         // filter bits, 2^(B*k) (at least 4 words)
@@ -195,6 +201,9 @@ struct DevTables {
     int hash_shift = -1;             // see HostTables
     uint32_t hash_code[2] = {0, 0};  // hash_code bytes, little-endian
     uint32_t hash_byte[2] = {0, 0};
+    int direct_shift = -1;           // see HostTables
+    uint32_t direct_sel[2] = {0, 0}; // byte 2c of the pair: the keyword byte of code c
+    uint32_t direct_fill = 0;        // a byte in no keyword
 };
 
 // OUT_SLOTS: per work unit, the number of matches and the first kSlotCap of

@@ -111,10 +111,16 @@ def test_builder_structure_against_oracle(lib, seed):
             assert info["n_states"] == m.n_states
             assert np.array_equal(depth.astype(np.uint64), m.depth_counts()[: depth.size])
             want = m.pfac_ids(text)
-        # class map: distinct keyword bytes, in byte order
+        # class map: distinct keyword bytes, in byte order (four that
+        # (byte >> s) & 3 tells apart: that value)
         present = sorted(set(b"".join(pats)))
         assert info["n_classes"] == len(present)
-        assert [int(cls[b]) for b in present] == list(range(len(present)))
+        s = _direct_shift(present)
+        assert info["class_direct_shift"] == s
+        if s >= 0:
+            assert [int(cls[b]) for b in present] == [(b >> s) & 3 for b in present]
+        else:
+            assert [int(cls[b]) for b in present] == list(range(len(present)))
         assert all(cls[b] == -1 for b in range(256) if b not in present)
         # 16-bit entries exactly when every state id and keyword id fits
         fits = info["n_states"] <= 32768 and len(pats) <= 32767
@@ -153,6 +159,43 @@ def test_builder_jump_and_stride_shapes(lib):
     info = api.ac_info(h)
     api.ac_destroy(h)
     assert info["code_bits"] == 8 and info["jump_depth"] == 2  # 2^16 int16 jump entries
+
+
+def _direct_shift(present):
+    """1 when (byte >> 1) & 3 tells four keyword bytes apart, else -1."""
+    return 1 if len(present) == 4 and len({(b >> 1) & 3 for b in present}) == 4 else -1
+
+
+@pytest.mark.parametrize("alphabet,shift", [
+    (b"ACGT", 1),
+    (b"acgt", 1),
+    (bytes([0x00, 0x02, 0x04, 0x06]), 1),
+    (bytes([0x10, 0x11, 0x12, 0x13]), -1),
+    (bytes([0x00, 0x01, 0x80, 0x81]), -1),
+    (b"AC", -1),
+    (b"ACGTN", -1),
+])
+def test_direct_class_codes(lib, alphabet, shift):
+    """Four keyword bytes that (byte >> 1) & 3 tells apart (the DNA letters
+    in either case) take that value as their class code; the tables built on
+    it walk as the oracle does."""
+    g = np.random.Generator(np.random.PCG64(len(alphabet) * 31 + shift + 1))
+    a = np.frombuffer(alphabet, dtype=np.uint8)
+    pats = [bytes(a[g.integers(0, a.size, size=int(g.integers(1, 9)))]) for _ in range(80)]
+    pats += [bytes([b]) for b in alphabet]
+    text = np.concatenate([a, np.frombuffer(b"NxE\x00\xff", dtype=np.uint8)])[g.integers(0, a.size + 5, size=4000)]
+    h = api.ac_compile(pats, host_only=True)
+    try:
+        info = api.ac_info(h)
+        cls, G, _ = api.ac_export_tables(h)
+        assert info["class_direct_shift"] == shift
+        if shift >= 0:
+            assert info["code_bits"] == 2
+            assert sorted(int(cls[b]) for b in alphabet) == [0, 1, 2, 3]
+            assert all(int(cls[b]) == (b >> shift) & 3 for b in alphabet)
+        assert np.array_equal(walk_table(cls, G, info["n_classes"], text), oracle.pfac_ids(pats, text))
+    finally:
+        api.ac_destroy(h)
 
 
 @pytest.mark.parametrize("alphabet,shift,bits", [

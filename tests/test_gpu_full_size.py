@@ -172,6 +172,43 @@ def test_phased_small_alphabet_and_list_overflow(kind, listed):
         _all_outputs(a, t, text.size, wpos, wids, kind)
 
 
+def test_direct_codes_long_text_with_other_bytes(sweep):
+    """Codes taken as (byte >> 1) & 3 in the one-phase forms at the widest
+    launch (texts beyond the forms that share heavy tiles): the sweep set on
+    48 MiB of its text with one byte in a thousand replaced by a byte in no
+    keyword ('N', or a keyword byte with a bit above its code bits flipped,
+    so the same code); and lowercase DNA keywords of 1-20 letters (nearly
+    every position survives the filter, most tiles are heavy) on 40 MiB with
+    one byte in a hundred replaced.  Dense ids, count and compacted list,
+    every position, against the oracle."""
+    import torch
+
+    text, pats, _, _, _, a = sweep
+    assert a.info()["class_direct_shift"] == 1
+    g = np.random.default_rng(41)
+    n = 48 << 20
+    t = text[:n].copy()
+    hit = np.nonzero(g.random(n) < 1e-3)[0]
+    t[hit] = np.frombuffer(b"NIKOV", dtype=np.uint8)[g.integers(0, 5, size=hit.size)]
+    wpos, wids = _par.oracle_compact(pats, t)
+    d = torch.from_numpy(t).cuda()
+    _all_outputs(a, d, n, wpos, wids, "48 MiB with other bytes")
+    del d
+
+    low = np.frombuffer(b"acgt", dtype=np.uint8)
+    n = 40 << 20
+    t = low[g.integers(0, 4, size=n)]
+    hit = np.nonzero(g.random(n) < 1e-2)[0]
+    t[hit] = np.frombuffer(b"qswdNbfu\x00\xff", dtype=np.uint8)[g.integers(0, 10, size=hit.size)]
+    kws = [bytes(low[g.integers(0, 4, size=int(g.integers(1, 21)))]) for _ in range(300)]
+    wpos, wids = _par.oracle_compact(kws, t)
+    d = torch.from_numpy(t).cuda()
+    with api.Automaton(kws) as b:
+        assert b.info()["class_direct_shift"] == 1
+        b.set_tuning(survivor_list=2)  # one phase for every output
+        _all_outputs(b, d, n, wpos, wids, "40 MiB lowercase with other bytes")
+
+
 @pytest.mark.parametrize("kind", ["short_keywords", "zipf_sparse"])
 def test_two_phase_byte_form_and_list_overflow(kind):
     """8-bit codes on texts long enough for the two-phase form: a keyword set

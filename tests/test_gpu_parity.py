@@ -157,6 +157,38 @@ def test_many_keywords_over_15_bits(kernel):
         _gpu.check_all_modes(a.handle, text, want)
 
 
+def _other_bytes(alphabet: bytes) -> np.ndarray:
+    """Bytes in no keyword: each keyword byte with a bit above its code bits
+    (bits 1-2) flipped (same code, another byte), 'N', 0x00 and 0xFF."""
+    extra = {b ^ 0x10 for b in alphabet} | {b ^ 0x01 for b in alphabet} | {ord("N"), 0x00, 0xFF}
+    return np.array(sorted(extra - set(alphabet)), dtype=np.uint8)
+
+
+@pytest.mark.parametrize("alphabet,shift", [(b"ACGT", 1), (b"acgt", 1), (bytes([0x00, 0x02, 0x04, 0x06]), 1),
+                                            (bytes([0x00, 0x01, 0x80, 0x81]), -1)])
+def test_direct_codes_and_other_bytes(alphabet, shift):
+    """2-bit codes computed as (byte >> 1) & 3 (and, for comparison, a
+    four-byte alphabet without them) on texts of the four keyword
+    bytes with other bytes mixed in (some with a keyword byte's code bits),
+    from none to one in three, at sizes across tiles with ragged ends and at
+    unaligned pointers: dense ids, count and compacted list against the
+    oracle."""
+    g = np.random.Generator(np.random.PCG64(shift * 7 + alphabet[0] + 10))
+    others = _other_bytes(alphabet)
+    for n, rate in ((5000, 0.3), (3 * 8192 + 77, 0.01), (100_003, 1e-4), (100_003, 0.0), (250_001, 0.002)):
+        text, pats = random_case(g, alphabet, n, 120, 24)
+        hit = g.random(n) < rate
+        text[hit] = others[g.integers(0, others.size, size=int(hit.sum()))]
+        want = oracle.pfac_ids(pats, text)
+        with compile_(pats) as a:
+            assert a.info()["class_direct_shift"] == shift and a.info()["code_bits"] == 2
+            _gpu.check_all_modes(a.handle, text, want)
+            base = _gpu.to_dev(text)
+            for off in (3, 13):
+                sub_want = oracle.pfac_ids(pats, text[off:])
+                _gpu.check_all_modes(a.handle, text[off:], sub_want, t=base[off:])
+
+
 def test_unaligned_pointers():
     import torch
 
