@@ -36,10 +36,10 @@ NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 # ncu capture of the kernel as it stands, keyed by (workload, text bytes,
 # kernel): a capture of a 256 MiB launch of the same workload and launch
 # form, scaled by 4 to the 1 GiB launch (the traffic grows with the positions;
-# the 256 MiB capture read 344.5 MB and wrote 1021.4 MB).  Drop an entry
+# the 256 MiB capture read 343.8 MB and wrote 1020.3 MB).  Drop an entry
 # whenever its kernel changes.
 KNOWN_TRAFFIC: dict = {
-    ("sweep", GIB, "pfac_filter_pipe"): 4 * (344.534528e6 + 1021.447e6),
+    ("sweep", GIB, "pfac_filter_pipe"): 4 * (343.750144e6 + 1020.311e6),
 }
 
 

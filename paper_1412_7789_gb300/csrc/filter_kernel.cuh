@@ -314,6 +314,17 @@ __device__ __forceinline__ uint32_t outside_marks(int64_t g0, int64_t n) {
     return iv;
 }
 
+// A warp: the staged bytes st[q] at text positions gpb + q outside the text
+// [0, n) become `fill`.  Out of line (fringe tiles only): inlined, it cost
+// the kernel it sits in registers on every tile.
+static __device__ __noinline__ void fill_outside(uint8_t *st, int64_t gpb, int64_t n, uint32_t staged, uint32_t fill,
+                                                 int lane) {
+    for (uint32_t q = static_cast<uint32_t>(lane); q < staged; q += 32u) {
+        const int64_t g = gpb + static_cast<int64_t>(q);
+        if (g < 0 || g >= n) st[q] = static_cast<uint8_t>(fill);
+    }
+}
+
 // Flags (bit b) of the 16 bytes of raw in no keyword (class table entry
 // 0xFF).  Out of line: the kernels that call it do so rarely.
 static __device__ __noinline__ uint32_t unknown_flags16(const uint8_t *cls8, const uint4 raw) {
@@ -997,10 +1008,7 @@ __device__ __forceinline__ bool filter_units(const FilterParams &p, uint8_t *sme
                 // the staged bytes outside the text become a byte in no
                 // keyword, so the classification flags them as it does those
                 __syncwarp();
-                for (uint32_t q = static_cast<uint32_t>(lane); q < p.staged; q += 32u) {
-                    const int64_t g = gpb + static_cast<int64_t>(q);
-                    if (g < 0 || g >= n) st[q] = static_cast<uint8_t>(p.dfill);
-                }
+                fill_outside(st, gpb, n, p.staged, p.dfill, lane);
             }
             __syncwarp();
         }

@@ -193,6 +193,10 @@ def test_direct_codes_long_text_with_other_bytes(sweep):
     wpos, wids = _par.oracle_compact(pats, t)
     d = torch.from_numpy(t).cuda()
     _all_outputs(a, d, n, wpos, wids, "48 MiB with other bytes")
+    # an unaligned start and a ragged end: fringe tiles at both ends
+    off, m = 5, n - 5 - 777
+    p, i = _par.window_compact(wpos, wids, pats, t, off, m)
+    _all_outputs(a, d[off:off + m], m, p, i, "48 MiB at offset 5")
     del d
 
     low = np.frombuffer(b"acgt", dtype=np.uint8)
