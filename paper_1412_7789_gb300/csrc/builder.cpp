@@ -5,9 +5,11 @@
 // Steps, in order:
 //   1. class map: each byte that occurs in a keyword gets a code 0..C-1 (in byte
 //      order); other bytes can never extend a walk.
-//   2. trie insertion of every keyword (the goto function);
+//   2. trie insertion of every keyword (the goto function), one subtrie per
+//      first code on the host's threads;
 //   3. breadth-first renumbering, children in code order, so depth d occupies
-//      a contiguous id range and the hot upper levels form a prefix;
+//      a contiguous id range and the hot upper levels form a prefix (each
+//      subtrie's BFS on its own thread, then joined depth by depth);
 //   4. per state, the longest keyword that is a prefix of the state's string
 //      (the output a walk ending there reports; equal strings -> lowest id);
 //   5. the dense table, one row per state: C goto columns plus one end column,
@@ -25,6 +27,7 @@
 //   9. the full-output records: for each keyword, the keywords that are
 //      prefixes of it (its sub-patterns on any walk that reaches it).
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -129,6 +132,33 @@ void parallel_ranges(uint64_t n, uint64_t min_per_thread, F body) {
             body(lo, hi);
         }
     }
+    for (std::thread &x : th) x.join();
+}
+
+// body(i) for every task i in [0, n), the tasks taken in order by up to the
+// host's thread count (at most 32) through a shared counter.
+template <typename F>
+void parallel_tasks(uint32_t n, F body) {
+    uint64_t t = std::thread::hardware_concurrency();
+    t = std::min<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(t, 1), 32), n);
+    std::atomic<uint32_t> next{0};
+    auto run = [&]() {
+        for (uint32_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) body(i);
+    };
+    if (t <= 1) {
+        run();
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve(t);
+    for (uint64_t i = 0; i < t; ++i) {
+        try {
+            th.emplace_back(run);
+        } catch (...) {
+            break;  // the threads started (or this one, below) take the rest
+        }
+    }
+    run();
     for (std::thread &x : th) x.join();
 }
 
@@ -322,33 +352,99 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             }
         }
 
-        // 2. trie insertion (provisional ids in creation order)
-        ChildTable child(std::min<uint64_t>(total, 1ull << 26) + 16);
-        std::vector<int32_t> kw_at{-1};   // lowest keyword id ending at each provisional state
-        std::vector<uint32_t> kw_state(nkw);  // each keyword's provisional state
-        std::vector<Edge> edges;
-        edges.reserve(static_cast<size_t>(std::min<uint64_t>(total, 1ull << 26)));
-        for (uint32_t id = 0; id < nkw; ++id) {
-            uint32_t s = 0;
-            for (uint32_t j = 0; j < lens[id]; ++j) {
-                uint32_t c = static_cast<uint32_t>(h.cls[patterns[id][j]]);
-                const uint64_t key = (static_cast<uint64_t>(s) << 8) | c;
-                bool inserted = false;
-                const uint32_t t = child.find_or_insert(key, static_cast<uint32_t>(kw_at.size()), &inserted);
-                if (inserted) {
-                    kw_at.push_back(-1);
-                    edges.push_back({s, c, t});
-                }
-                s = t;
-            }
-            if (kw_at[s] < 0) kw_at[s] = static_cast<int32_t>(id);  // ids arrive in increasing order
-            kw_state[id] = s;
+        // 2. trie insertion.  The keywords are grouped by their first code:
+        //    the subtries below the root's children are disjoint, so each
+        //    group's subtrie is built by one thread, its keywords in increasing
+        //    id (so a state's first keyword is its lowest).  Provisional ids:
+        //    the root, then one block per group in code order, a group's
+        //    depth-1 state first.
+        std::vector<uint32_t> gstart(h.C + 1, 0);  // keywords of first code c: gids[gstart[c] .. gstart[c + 1])
+        for (uint32_t id = 0; id < nkw; ++id) gstart[static_cast<uint32_t>(h.cls[patterns[id][0]]) + 1]++;
+        for (uint32_t c = 0; c < h.C; ++c) gstart[c + 1] += gstart[c];
+        std::vector<uint32_t> gids(nkw);
+        {
+            std::vector<uint32_t> fill(gstart.begin(), gstart.end() - 1);
+            for (uint32_t id = 0; id < nkw; ++id) gids[fill[static_cast<uint32_t>(h.cls[patterns[id][0]])]++] = id;
         }
-        child = ChildTable(0);  // release the table
-        const uint32_t S = static_cast<uint32_t>(kw_at.size());
+        std::vector<uint32_t> groups;  // first codes that start a keyword, largest group first
+        std::vector<uint64_t> glen(h.C, 0);
+        for (uint32_t c = 0; c < h.C; ++c) {
+            for (uint32_t i = gstart[c]; i < gstart[c + 1]; ++i) glen[c] += lens[gids[i]];
+            if (gstart[c + 1] > gstart[c]) groups.push_back(c);
+        }
+        std::sort(groups.begin(), groups.end(), [&](uint32_t a, uint32_t b) {
+            return glen[a] != glen[b] ? glen[a] > glen[b] : a < b;
+        });
+        struct Subtrie {
+            std::vector<int32_t> kw_at;  // local id -> lowest keyword id ending there (local 0: the depth-1 state)
+            std::vector<Edge> edges;     // local ids
+        };
+        std::vector<Subtrie> sub(h.C);
+        std::vector<uint32_t> kw_state(nkw);  // each keyword's state: local id first, then provisional
+        std::atomic<bool> oom{false};
+        parallel_tasks(static_cast<uint32_t>(groups.size()), [&](uint32_t gi) {
+            const uint32_t c0 = groups[gi];
+            try {
+                Subtrie &t = sub[c0];
+                const uint64_t expect = std::min<uint64_t>(glen[c0], 1ull << 26) + 16;
+                ChildTable child(expect);
+                t.kw_at.assign(1, -1);
+                t.edges.reserve(static_cast<size_t>(expect));
+                for (uint32_t i = gstart[c0]; i < gstart[c0 + 1]; ++i) {
+                    const uint32_t id = gids[i];
+                    uint32_t s = 0;
+                    for (uint32_t j = 1; j < lens[id]; ++j) {
+                        const uint32_t c = static_cast<uint32_t>(h.cls[patterns[id][j]]);
+                        const uint64_t key = (static_cast<uint64_t>(s) << 8) | c;
+                        bool inserted = false;
+                        const uint32_t u = child.find_or_insert(key, static_cast<uint32_t>(t.kw_at.size()), &inserted);
+                        if (inserted) {
+                            t.kw_at.push_back(-1);
+                            t.edges.push_back({s, c, u});
+                        }
+                        s = u;
+                    }
+                    if (t.kw_at[s] < 0) t.kw_at[s] = static_cast<int32_t>(id);
+                    kw_state[id] = s;
+                }
+            } catch (const std::bad_alloc &) {
+                oom = true;
+            }
+        });
+        if (oom) return AC_ERR_OOM;
+        std::vector<uint32_t> goff(h.C, 0), eoff(h.C, 0);  // each group's first provisional id, first edge
+        uint64_t S64 = 1, E64 = 0;
+        for (uint32_t c = 0; c < h.C; ++c) {
+            if (gstart[c + 1] == gstart[c]) continue;
+            goff[c] = static_cast<uint32_t>(S64);
+            eoff[c] = static_cast<uint32_t>(E64);
+            S64 += sub[c].kw_at.size();
+            E64 += sub[c].edges.size() + 1;  // its edges and the root's edge into it
+        }
+        if (S64 > 0x7FFFFFF0ull) return AC_ERR_TOO_MANY_STATES;
+        const uint32_t S = static_cast<uint32_t>(S64);
         h.S = S;
+        std::vector<int32_t> kw_at(S, -1);  // lowest keyword id ending at each provisional state
+        std::vector<Edge> edges(static_cast<size_t>(E64));
+        parallel_tasks(static_cast<uint32_t>(groups.size()), [&](uint32_t gi) {
+            const uint32_t c0 = groups[gi], o = goff[c0];
+            Subtrie &t = sub[c0];
+            std::copy(t.kw_at.begin(), t.kw_at.end(), kw_at.begin() + o);
+            Edge *e = edges.data() + eoff[c0];
+            e[0] = {0u, c0, o};
+            for (size_t i = 0; i < t.edges.size(); ++i) e[i + 1] = {t.edges[i].parent + o, t.edges[i].code, t.edges[i].child + o};
+            for (uint32_t i = gstart[c0]; i < gstart[c0 + 1]; ++i) kw_state[gids[i]] += o;
+            std::vector<int32_t>().swap(t.kw_at);
+            std::vector<Edge>().swap(t.edges);
+        });
 
-        // 3. breadth-first renumbering with children in code order
+        // 3. breadth-first renumbering with children in code order.  At every
+        //    depth the states of group c come after those of every group of a
+        //    lower code (a BFS keeps its parents' order, and the depth-1 states
+        //    are in code order), so each group's BFS runs on its own thread and
+        //    a state's new id is: the states above its depth, those of the
+        //    lower groups at its depth, then its rank in its group's BFS at
+        //    that depth.
         std::vector<uint32_t> first(S + 1, 0);
         for (const Edge &e : edges) first[e.parent + 1]++;
         for (uint32_t s = 0; s < S; ++s) first[s + 1] += first[s];
@@ -357,30 +453,81 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
             std::vector<uint32_t> fill(first.begin(), first.end() - 1);
             for (uint32_t i = 0; i < edges.size(); ++i) adj[fill[edges[i].parent]++] = i;
         }
-        for (uint32_t s = 0; s < S; ++s)
-            std::sort(adj.begin() + first[s], adj.begin() + first[s + 1],
-                      [&](uint32_t a, uint32_t b) { return edges[a].code < edges[b].code; });
-        std::vector<uint32_t> order;    // new id -> provisional id
-        order.reserve(S);
+        parallel_ranges(S, 16384, [&](uint64_t s0, uint64_t s1) {
+            for (uint64_t s = s0; s < s1; ++s)
+                if (first[s + 1] - first[s] > 1)
+                    std::sort(adj.begin() + first[s], adj.begin() + first[s + 1],
+                              [&](uint32_t a, uint32_t b) { return edges[a].code < edges[b].code; });
+        });
+        const uint32_t D = h.maxlen + 1;
+        std::vector<std::vector<uint32_t>> seq(h.C);     // each group's BFS: edge index into each state
+        std::vector<std::vector<uint32_t>> level(h.C);   // ... and where each depth starts in it (D + 1 entries)
+        parallel_tasks(static_cast<uint32_t>(groups.size()), [&](uint32_t gi) {
+            const uint32_t c0 = groups[gi];
+            std::vector<uint32_t> &q = seq[c0];
+            std::vector<uint32_t> &lv = level[c0];
+            try {
+                q.push_back(eoff[c0]);  // the root's edge into the group
+                lv.assign(D + 1, 0);
+                uint32_t d = 1;
+                size_t end_of_level = 1;
+                for (size_t qi = 0; qi < q.size(); ++qi) {
+                    if (qi == end_of_level) {  // every state of the next depth is queued
+                        ++d;
+                        lv[d] = static_cast<uint32_t>(qi);
+                        end_of_level = q.size();
+                    }
+                    const uint32_t old = edges[q[qi]].child;
+                    for (uint32_t a = first[old]; a < first[old + 1]; ++a) q.push_back(adj[a]);
+                }
+                for (uint32_t e = d + 1; e <= D; ++e) lv[e] = static_cast<uint32_t>(q.size());
+            } catch (const std::bad_alloc &) {
+                oom = true;
+            }
+        });
+        if (oom) return AC_ERR_OOM;
+        // states per depth, and each group's first rank at each depth
+        h.depth_count.assign(D, 0);
+        h.depth_count[0] = 1;
+        std::vector<uint32_t> gbase(static_cast<size_t>(h.C) * D, 0);
+        {
+            std::vector<uint64_t> run(D, 0);
+            for (uint32_t c = 0; c < h.C; ++c) {
+                if (gstart[c + 1] == gstart[c]) continue;
+                const std::vector<uint32_t> &lv = level[c];
+                for (uint32_t d = 1; d < D; ++d) {
+                    const uint32_t n_at = (d + 1 <= D ? lv[d + 1] : static_cast<uint32_t>(seq[c].size())) - lv[d];
+                    gbase[static_cast<size_t>(c) * D + d] = static_cast<uint32_t>(run[d]);
+                    run[d] += n_at;
+                }
+            }
+            for (uint32_t d = 1; d < D; ++d) h.depth_count[d] = static_cast<uint32_t>(run[d]);
+        }
+        std::vector<uint32_t> dbase(D + 1, 0);  // first new id at each depth
+        for (uint32_t d = 0; d < D; ++d) dbase[d + 1] = dbase[d] + h.depth_count[d];
+        std::vector<uint32_t> order(S);        // new id -> provisional id
         std::vector<uint32_t> newid(S, 0);
         std::vector<uint32_t> depth(S, 0);     // by new id
         std::vector<uint32_t> parent(S, 0);    // by new id
         std::vector<uint32_t> incode(S, 0);    // by new id: the code of the edge into the state
-        order.push_back(0);
-        for (size_t qi = 0; qi < order.size(); ++qi) {
-            uint32_t old = order[qi];
-            for (uint32_t a = first[old]; a < first[old + 1]; ++a) {
-                const Edge &e = edges[adj[a]];
-                uint32_t nid = static_cast<uint32_t>(order.size());
-                newid[e.child] = nid;
-                depth[nid] = depth[qi] + 1;
-                parent[nid] = static_cast<uint32_t>(qi);
+        order[0] = 0;
+        parallel_tasks(static_cast<uint32_t>(groups.size()), [&](uint32_t gi) {
+            const uint32_t c0 = groups[gi];
+            const std::vector<uint32_t> &q = seq[c0];
+            const std::vector<uint32_t> &lv = level[c0];
+            uint32_t d = 1;
+            for (size_t qi = 0; qi < q.size(); ++qi) {
+                while (d + 1 < D && qi >= lv[d + 1]) ++d;
+                const Edge &e = edges[q[qi]];
+                const uint32_t nid = dbase[d] + gbase[static_cast<size_t>(c0) * D + d] + static_cast<uint32_t>(qi - lv[d]);
+                newid[e.child] = nid;  // a parent's new id is set before its children's (BFS order)
+                order[nid] = e.child;
+                depth[nid] = d;
+                parent[nid] = newid[e.parent];
                 incode[nid] = e.code;
-                order.push_back(e.child);
             }
-        }
-        h.depth_count.assign(h.maxlen + 1, 0);
-        for (uint32_t s = 0; s < S; ++s) h.depth_count[depth[s]]++;
+            std::vector<uint32_t>().swap(seq[c0]);
+        });
 
         // 4. longest keyword on the path to each state (BFS order: parents first)
         std::vector<int32_t> pathbest(S, -1);
@@ -588,40 +735,66 @@ int build_tables(const uint8_t *const *patterns, const uint32_t *lens, uint32_t 
                 if (h.cls[b] >= 0) byte_of[static_cast<uint32_t>(h.cls[b])] = static_cast<uint8_t>(b);
             const uint32_t R = S - h.s_chain;
             h.skip.assign(static_cast<size_t>(R) * 4, 0);
-            std::vector<uint8_t> done(R, 0);
-            for (uint32_t s2 = h.s_chain; s2 < S; ++s2) {
-                uint32_t *rec = &h.skip[static_cast<size_t>(s2 - h.s_chain) * 4];
-                rec[3] = static_cast<uint32_t>(pathbest[s2]);
-                if (kids[s2] >= 2) {
-                    rec[0] = kSkipBranch;
-                    continue;
+            // A one-child state starts a run unless its parent is a one-child
+            // state of the records (so in a run) and it has no keyword of its
+            // own (then the parent's run goes through it).  Runs are found and
+            // measured in parallel, their bytes laid out in the order of their
+            // first states, then written in parallel.
+            std::vector<uint32_t> runlen(R, 0);  // a run's length at its first state, else 0
+            parallel_ranges(R, 16384, [&](uint64_t r0, uint64_t r1) {
+                for (uint64_t r = r0; r < r1; ++r) {
+                    const uint32_t s2 = h.s_chain + static_cast<uint32_t>(r);
+                    uint32_t *rec = &h.skip[r * 4];
+                    rec[3] = static_cast<uint32_t>(pathbest[s2]);
+                    if (kids[s2] >= 2) {
+                        rec[0] = kSkipBranch;
+                        continue;
+                    }
+                    if (kids[s2] == 0) {  // a leaf: the walk stops here
+                        rec[0] = 0;
+                        rec[2] = s2;
+                        continue;
+                    }
+                    const uint32_t p = parent[s2];
+                    if (p >= h.s_chain && kids[p] == 1 && kw_at[order[s2]] < 0) continue;  // inside a run
+                    uint32_t v = s2, L = 0;
+                    do {
+                        v = child1[v];
+                        ++L;
+                    } while (kids[v] == 1 && kw_at[order[v]] < 0);
+                    runlen[r] = L;
                 }
-                if (kids[s2] == 0) {  // a leaf: the walk stops here
-                    rec[0] = 0;
-                    rec[2] = s2;
-                    continue;
-                }
-                if (done[s2 - h.s_chain]) continue;  // inside a run built from an earlier state
-                const uint32_t off = static_cast<uint32_t>(h.chain.size());
-                uint32_t v = s2, L = 0;
-                do {
-                    h.chain.push_back(byte_of[code1[v]]);
-                    v = child1[v];
-                    ++L;
-                } while (kids[v] == 1 && kw_at[order[v]] < 0);
-                // the run's states: s2 and the one-child states inside it
-                uint32_t u = s2;
-                for (uint32_t j = 0; j < L; ++j) {
-                    uint32_t *r = &h.skip[static_cast<size_t>(u - h.s_chain) * 4];
-                    r[0] = L - j;
-                    r[1] = off + j;
-                    r[2] = v;
-                    r[3] = static_cast<uint32_t>(pathbest[u]);
-                    done[u - h.s_chain] = 1;
-                    u = child1[u];
-                }
+            });
+            std::vector<uint32_t> runoff(R, 0);
+            uint64_t total_bytes = 0;
+            for (uint32_t r = 0; r < R; ++r) {
+                runoff[r] = static_cast<uint32_t>(total_bytes);
+                total_bytes += runlen[r];
             }
-            h.chain.resize(std::max<size_t>(16, (h.chain.size() + 15) & ~static_cast<size_t>(15)), 0);
+            if (total_bytes > 0xFFFFFFF0ull) return AC_ERR_TOO_MANY_STATES;
+            h.chain.assign(std::max<size_t>(16, (static_cast<size_t>(total_bytes) + 15) & ~static_cast<size_t>(15)), 0);
+            parallel_ranges(R, 16384, [&](uint64_t r0, uint64_t r1) {
+                for (uint64_t r = r0; r < r1; ++r) {
+                    const uint32_t L = runlen[r];
+                    if (L == 0) continue;
+                    const uint32_t s2 = h.s_chain + static_cast<uint32_t>(r), off = runoff[r];
+                    uint32_t v = s2;
+                    for (uint32_t j = 0; j < L; ++j) {
+                        h.chain[off + j] = byte_of[code1[v]];
+                        v = child1[v];
+                    }
+                    // the run's states: s2 and the one-child states inside it
+                    uint32_t u = s2;
+                    for (uint32_t j = 0; j < L; ++j) {
+                        uint32_t *rc = &h.skip[static_cast<size_t>(u - h.s_chain) * 4];
+                        rc[0] = L - j;
+                        rc[1] = off + j;
+                        rc[2] = v;
+                        rc[3] = static_cast<uint32_t>(pathbest[u]);
+                        u = child1[u];
+                    }
+                }
+            });
         }
 
         // 9. full output (every keyword occurrence on a walk's path, the
