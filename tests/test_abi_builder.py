@@ -411,26 +411,76 @@ def test_full_expansion_equals_serial_machine(lib):
 
 
 def test_parallel_build_is_deterministic(lib):
-    """The goto table's rows are filled on several host threads: two builds of
-    the same large keyword set export byte-identical tables, and every entry
-    is either a larger child state or an encoded result."""
+    """The trie, its numbering, the goto table's rows and the chain records
+    are built on several host threads: two builds of the same large keyword
+    set export byte-identical tables and records, and every entry is either
+    a larger child state or an encoded result."""
     text, pats = workloads.zipf_byte(1 << 20, seed=5, n_keywords=3000)
-    tabs = []
+    tabs, chains = [], []
     for _ in range(2):
         h = api.ac_compile(pats, host_only=True)
         try:
             tabs.append(api.ac_export_tables(h))
+            chains.append(api.ac_export_chains(h))
             info = api.ac_info(h)
         finally:
             api.ac_destroy(h)
     (c0, g0, d0), (c1, g1, d1) = tabs
     assert np.array_equal(c0, c1) and np.array_equal(d0, d1) and np.array_equal(g0, g1)
+    for x, y in zip(chains[0], chains[1]):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
     G = g0.reshape(info["n_states"], info["row_width"]).astype(np.int64)
     rows = np.arange(info["n_states"])[:, None]
     live = G > 0
     assert np.all(G[live] > np.broadcast_to(rows, G.shape)[live])  # BFS order: children after parents
     assert np.all(G[~live] <= -1)  # encoded results -(id + 2), id >= -1
     assert np.all(-G[~live] - 2 < len(pats))
+
+
+@pytest.mark.parametrize("shape", ["one_group", "all_first_bytes", "skewed", "short_and_dups"])
+def test_parallel_build_group_shapes(lib, shape):
+    """The trie is built one subtrie per first byte class on the host's
+    threads and numbered depth by depth across them: keyword sets whose
+    first bytes form one group, all 256 groups, one group holding nine tenths
+    of the keywords, and keywords of one or two bytes with duplicates across
+    groups.  The exported goto table walks as the oracle does, BFS order
+    holds (depths contiguous and non-decreasing, children after parents and
+    in code order), and so do walks that take the chain records."""
+    g = np.random.Generator(np.random.PCG64(["one_group", "all_first_bytes", "skewed", "short_and_dups"].index(shape) + 90))
+    if shape == "one_group":
+        pats = [b"Q" + bytes(g.integers(0, 256, size=int(g.integers(0, 30)), dtype=np.uint8)) for _ in range(800)]
+    elif shape == "all_first_bytes":
+        pats = [bytes([b]) + bytes(g.integers(0, 256, size=int(g.integers(0, 20)), dtype=np.uint8)) for b in range(256)
+                for _ in range(3)]
+    elif shape == "skewed":
+        pats = [(b"e" if g.random() < 0.9 else bytes([int(g.integers(0, 256))])) +
+                bytes(g.integers(97, 101, size=int(g.integers(0, 25)), dtype=np.uint8)) for _ in range(1500)]
+    else:
+        pats = [bytes(g.integers(0, 6, size=int(g.integers(1, 3)), dtype=np.uint8)) for _ in range(200)]
+        pats += pats[::7]
+    alphabet = np.array(sorted(set(b"".join(pats))), dtype=np.uint8)
+    text = alphabet[g.integers(0, alphabet.size, size=6000)]
+    for o in g.integers(0, 5900, size=40):  # plant keywords
+        p = pats[int(g.integers(0, len(pats)))]
+        text[o:o + len(p)] = np.frombuffer(p, dtype=np.uint8)[:max(0, min(len(p), text.size - o))]
+    h = api.ac_compile(pats, host_only=True, class_compress=shape != "all_first_bytes")
+    try:
+        info = api.ac_info(h)
+        cls, G, depth = api.ac_export_tables(h)
+        s_chain, rec, byt = api.ac_export_chains(h)
+        want = oracle.pfac_ids(pats, text)
+        C = info["n_classes"]
+        assert np.array_equal(walk_table(cls, G, C, text), want)
+        starts = np.concatenate([[0], np.cumsum(depth)])
+        assert starts[-1] == info["n_states"] and depth[0] == 1
+        dep = np.repeat(np.arange(depth.size), depth)
+        for s in range(info["n_states"]):
+            kids = G[s, :C][G[s, :C] > 0]
+            assert np.all(dep[kids] == dep[s] + 1) and np.all(np.diff(kids) > 0)
+        got = np.array([_walk_with_chains(cls, G, s_chain, rec, byt, text, i) for i in range(text.size)], dtype=np.int32)
+        assert np.array_equal(got, want)
+    finally:
+        api.ac_destroy(h)
 
 
 @pytest.mark.parametrize("alpha,lmin,lmax", [(b"ACGT", 4, 40), (b"abcdefghijkl", 2, 12), (b"ACGT", 1, 2),
